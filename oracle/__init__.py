@@ -1,0 +1,318 @@
+"""FP64 CPU oracle for the log-polar thin-disk self-gravity path.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / reference leg of ``bench.py`` may import this package.  The
+product library never imports, loads or calls it, and it shares no code with
+the CUDA path (the seeded input generators live in ``workloads/``).
+
+What it computes follows Wang, Yen & Taam, "Self-gravitational force
+calculation of second order accuracy for infinitesimally thin gaseous disks in
+polar coordinates":
+
+* ``grid``               -- Sec. 3.2.1: log-spaced faces, arithmetic centres.
+* ``kernel_cells``       -- Eq. 30-32, A11-A13: the six exact cell integrals
+                            (C, adaptive Gauss-Legendre; see sg_oracle.c).
+* ``slopes``             -- Eq. 25 with central differences (Sec. 5.2).
+* ``three_sum``          -- Eq. 26-29 and A8-A10 on the single grid, the
+                            literal three-term form.
+* ``fold``               -- the same sums collapsed to one kernel per force
+                            component (the exact algebra in ``fold``'s doc).
+* ``direct_sum``         -- the O(N^2) convolution with the folded kernels.
+* ``direct_sum_T``       -- its transpose (adjoint), for the sigma-gradient.
+* ``fft_conv``           -- the same convolution with numpy's FFT as a
+                            library step (zero-padded in u, periodic in phi).
+* ``analytic``           -- closed-form disks used as truth (Sec. 5.1).
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "sg_oracle.c")
+_LIB = os.path.join(_HERE, "libsg_oracle.so")
+_lib = None
+
+NC = 6
+COMPONENTS = ("r0", "rr", "rphi", "phi0", "phir", "phiphi")
+
+
+def build(force: bool = False) -> str:
+    """Compile the C part of the oracle (plain gcc, OpenMP) in place."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        cmd = ["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-o", _LIB + ".tmp", _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(_LIB + ".tmp", _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB)
+        dp = ctypes.POINTER(ctypes.c_double)
+        lp = ctypes.POINTER(ctypes.c_long)
+        lib.sgo_cell.argtypes = [ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, dp]
+        lib.sgo_cell.restype = ctypes.c_int
+        lib.sgo_cells_table.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, dp, ctypes.c_int]
+        lib.sgo_cells_table.restype = ctypes.c_int
+        lib.sgo_direct_sum.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, dp, dp, dp, lp, ctypes.c_long,
+                                       dp, dp, ctypes.c_int]
+        lib.sgo_direct_sum.restype = None
+        lib.sgo_direct_sum_T.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, dp, dp, dp, dp, lp,
+                                         ctypes.c_long, dp, ctypes.c_int]
+        lib.sgo_direct_sum_T.restype = None
+        lib.sgo_max_threads.argtypes = []
+        lib.sgo_max_threads.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def max_threads() -> int:
+    return int(_load().sgo_max_threads())
+
+
+# --------------------------------------------------------------------------
+# Sec. 3.2.1 grid
+# --------------------------------------------------------------------------
+class Grid:
+    """Log-polar grid of Sec. 3.2.1 (0-based indices).
+
+    faces  r_{i-1/2} = e^{u_min} beta^i, i = 0..Nu      (beta = e^{du})
+    centre r_i = (r_{i-1/2} + r_{i+1/2}) / 2, i = 0..Nu-1  (arithmetic mean)
+    phi_j = (j + 1/2) dphi, dphi = 2 pi / Nphi
+    """
+
+    def __init__(self, nu: int, nphi: int, u_min: float, du: float):
+        self.nu, self.nphi, self.u_min, self.du = int(nu), int(nphi), float(u_min), float(du)
+        self.beta = math.exp(du)
+        self.dphi = 2.0 * math.pi / nphi
+        i = np.arange(nu + 1, dtype=np.float64)
+        self.faces = np.exp(u_min + du * i)
+        self.r = 0.5 * (self.faces[:-1] + self.faces[1:])
+        self.dr = self.faces[1:] - self.faces[:-1]
+        self.phi = (np.arange(nphi, dtype=np.float64) + 0.5) * self.dphi
+        self.area = self.r * self.dr * self.dphi  # exact cell area (arithmetic centre)
+
+    def centre(self, i):
+        """Centre radius of row i for any integer i (ghost rows included)."""
+        return 0.5 * math.exp(self.u_min + self.du * i) * (1.0 + self.beta)
+
+
+# --------------------------------------------------------------------------
+# Eq. 30-32, A11-A13: cell integrals
+# --------------------------------------------------------------------------
+def kernel_cell(du: float, nphi: int, k: int, q: int, rtol: float = 2e-14) -> np.ndarray:
+    """The six kernels K^{r,0}, K^{r,r}, K^{r,phi}, K^{phi,0}, K^{phi,r},
+    K^{phi,phi} for the offset (k, q) = (i - i', j - j')."""
+    out = np.zeros(NC)
+    bad = _load().sgo_cell(float(du), int(nphi), int(k), int(q), float(rtol), _dp(out))
+    if bad:
+        raise RuntimeError(f"oracle quadrature did not converge for k={k} q={q}")
+    return out
+
+
+def kernel_cells(nu: int, nphi: int, du: float, rtol: float = 2e-14, nthreads: int = 0) -> np.ndarray:
+    """Kernel table [6, 2Nu+1, Nphi] for k in [-Nu, Nu] (row k + Nu), q in [0, Nphi)."""
+    out = np.zeros((NC, 2 * nu + 1, nphi))
+    bad = _load().sgo_cells_table(int(nu), int(nphi), float(du), float(rtol), _dp(out), int(nthreads))
+    if bad:
+        raise RuntimeError(f"oracle quadrature did not converge for {bad} integrals")
+    return out
+
+
+# --------------------------------------------------------------------------
+# Eq. 25 slopes and the three-term sums of Eq. 26-29 / A8-A10
+# --------------------------------------------------------------------------
+def slopes(sigma: np.ndarray, grid: Grid):
+    """Central-difference slopes (Sec. 5.2 uses central differences).
+
+    sigma is zero outside the grid.  Returns (dr, dphi_slope, rows) where
+    dr[i'] = (sigma_{i'+1} - sigma_{i'-1}) / (r_{i'+1} - r_{i'-1}) for the
+    rows i' = -1 .. Nu (the two ghost rows the stencil touches included), and
+    dphi_slope[i', j'] = (sigma_{j'+1} - sigma_{j'-1}) / (2 dphi), periodic,
+    for the rows of the grid.
+    """
+    nu, nphi = sigma.shape
+    ext = np.zeros((nu + 4, nphi))  # rows -2 .. Nu+1
+    ext[2:nu + 2] = sigma
+    rows = np.arange(-1, nu + 1)
+    rc = np.array([grid.centre(i) for i in range(-2, nu + 2)])
+    dr = np.empty((nu + 2, nphi))
+    for n, ip in enumerate(rows):
+        e = ip + 2
+        dr[n] = (ext[e + 1] - ext[e - 1]) / (rc[e + 1] - rc[e - 1])
+    dphi_slope = (np.roll(sigma, -1, axis=1) - np.roll(sigma, 1, axis=1)) / (2.0 * grid.dphi)
+    return dr, dphi_slope, rows
+
+
+def three_sum(sigma: np.ndarray, cells: np.ndarray, grid: Grid, G: float = 1.0):
+    """Eq. 26-29 (radial) and A8-A10 (azimuthal) on the single grid, term by
+    term: F^r = F^{r,0} + r_i sum delta^r K^{r,r} + sum delta^phi K^{r,phi},
+    and the same for F^phi.  O(N^4); for small grids."""
+    nu, nphi = sigma.shape
+    dr, dph, rows = slopes(sigma, grid)
+    Fr = np.zeros((nu, nphi))
+    Fp = np.zeros((nu, nphi))
+    Frr = np.zeros((nu, nphi))
+    Fpr = np.zeros((nu, nphi))
+    i = np.arange(nu)[:, None]
+    j = np.arange(nphi)[None, :]
+    for ip in range(nu):
+        for jp in range(nphi):
+            k = i - ip + nu
+            q = (j - jp) % nphi
+            s, sp = sigma[ip, jp], dph[ip, jp]
+            Fr += s * cells[0][k, q] + sp * cells[2][k, q]
+            Fp += s * cells[3][k, q] + sp * cells[5][k, q]
+    for n, ip in enumerate(rows):
+        for jp in range(nphi):
+            d = dr[n, jp]
+            if d == 0.0:
+                continue
+            k = i - ip + nu
+            q = (j - jp) % nphi
+            Frr += d * cells[1][k, q]
+            Fpr += d * cells[4][k, q]
+    Fr += grid.r[:, None] * Frr
+    Fp += grid.r[:, None] * Fpr
+    return G * Fr, G * Fp
+
+
+def fold(cells: np.ndarray, beta: float, dphi: float):
+    """Collapse the three sums into one kernel per component.
+
+    With delta^r_{i'} = (sigma_{i'+1} - sigma_{i'-1}) / (r_{i'} (beta - 1/beta))
+    (r_{i'+-1} = beta^{+-1} r_{i'}) and r_i / r_{i'} = beta^{i-i'}, and the
+    periodic delta^phi, every term is linear in sigma and depends on (i-i',
+    j-j') only, so for k in [-(Nu-1), Nu-1]:
+      K^eff[k,q] = K^{.,0}[k,q]
+                   + (beta^{k+1} K^{.,r}[k+1,q] - beta^{k-1} K^{.,r}[k-1,q]) / (beta - 1/beta)
+                   + (K^{.,phi}[k,q+1] - K^{.,phi}[k,q-1]) / (2 dphi).
+    Input cells [6, 2Nu+1, Nphi] (k in [-Nu, Nu]); output Kr, Kphi
+    [2Nu-1, Nphi] (row k + Nu - 1).
+    """
+    nk = cells.shape[1]
+    nu = (nk - 1) // 2
+    k = np.arange(-(nu - 1), nu)[:, None].astype(np.float64)
+    mid = slice(1, nk - 1)
+    up = slice(2, nk)
+    dn = slice(0, nk - 2)
+    bb = beta - 1.0 / beta
+    out = []
+    for c0, cr, cp in ((0, 1, 2), (3, 4, 5)):
+        K = cells[c0][mid].copy()
+        K += (beta ** (k + 1) * cells[cr][up] - beta ** (k - 1) * cells[cr][dn]) / bb
+        K += (np.roll(cells[cp][mid], -1, axis=1) - np.roll(cells[cp][mid], 1, axis=1)) / (2.0 * dphi)
+        out.append(K)
+    return out[0], out[1]
+
+
+def direct_sum(sigma: np.ndarray, Kr: np.ndarray, Kp: np.ndarray, G: float = 1.0, targets=None, nthreads: int = 0):
+    """F_r, F_phi = G sum_{m,l} sigma[m,l] K[i-m, (j-l) mod Nphi] (direct O(N^2)).
+
+    targets: optional flat indices i*Nphi + j; returns flat arrays then."""
+    sigma = np.ascontiguousarray(sigma, dtype=np.float64)
+    nu, nphi = sigma.shape
+    Kr = np.ascontiguousarray(Kr, dtype=np.float64)
+    Kp = np.ascontiguousarray(Kp, dtype=np.float64)
+    assert Kr.shape == (2 * nu - 1, nphi) and Kp.shape == Kr.shape
+    lib = _load()
+    if targets is None:
+        Fr = np.zeros((nu, nphi))
+        Fp = np.zeros((nu, nphi))
+        lib.sgo_direct_sum(nu, nphi, float(G), _dp(Kr), _dp(Kp), _dp(sigma), None, 0, _dp(Fr), _dp(Fp), int(nthreads))
+        return Fr, Fp
+    t = np.ascontiguousarray(targets, dtype=np.int64)
+    Fr = np.zeros(t.size)
+    Fp = np.zeros(t.size)
+    lib.sgo_direct_sum(nu, nphi, float(G), _dp(Kr), _dp(Kp), _dp(sigma),
+                       t.ctypes.data_as(ctypes.POINTER(ctypes.c_long)), t.size, _dp(Fr), _dp(Fp), int(nthreads))
+    return Fr, Fp
+
+
+def direct_sum_T(gFr: np.ndarray, gFp: np.ndarray, Kr: np.ndarray, Kp: np.ndarray, G: float = 1.0,
+                 sources=None, nthreads: int = 0):
+    """Transpose of direct_sum: gsigma[m,l] = G sum_{i,j} (gFr[i,j] Kr[i-m,(j-l)] + gFphi[i,j] Kphi[i-m,(j-l)])."""
+    gFr = np.ascontiguousarray(gFr, dtype=np.float64)
+    gFp = np.ascontiguousarray(gFp, dtype=np.float64)
+    nu, nphi = gFr.shape
+    Kr = np.ascontiguousarray(Kr, dtype=np.float64)
+    Kp = np.ascontiguousarray(Kp, dtype=np.float64)
+    lib = _load()
+    if sources is None:
+        gs = np.zeros((nu, nphi))
+        lib.sgo_direct_sum_T(nu, nphi, float(G), _dp(Kr), _dp(Kp), _dp(gFr), _dp(gFp), None, 0, _dp(gs), int(nthreads))
+        return gs
+    s = np.ascontiguousarray(sources, dtype=np.int64)
+    gs = np.zeros(s.size)
+    lib.sgo_direct_sum_T(nu, nphi, float(G), _dp(Kr), _dp(Kp), _dp(gFr), _dp(gFp),
+                         s.ctypes.data_as(ctypes.POINTER(ctypes.c_long)), s.size, _dp(gs), int(nthreads))
+    return gs
+
+
+def fft_conv(sigma: np.ndarray, Kr: np.ndarray, Kp: np.ndarray, G: float = 1.0):
+    """The direct_sum convolution evaluated with numpy's FFT (a library step):
+    sigma zero-padded to 2Nu rows, the kernel placed cyclically at row k mod 2Nu
+    (row Nu left zero), periodic in phi; rows 0..Nu-1 of the cyclic result."""
+    nu, nphi = sigma.shape
+    L = 2 * nu
+    sp = np.zeros((L, nphi))
+    sp[:nu] = sigma
+    S = np.fft.rfft2(sp)
+    out = []
+    for K in (Kr, Kp):
+        Kc = np.zeros((L, nphi))
+        k = np.arange(-(nu - 1), nu)
+        Kc[k % L] = K
+        out.append(G * np.fft.irfft2(S * np.fft.rfft2(Kc), s=(L, nphi))[:nu])
+    return out[0], out[1]
+
+
+def fft_conv_T(gFr: np.ndarray, gFp: np.ndarray, Kr: np.ndarray, Kp: np.ndarray, G: float = 1.0):
+    """Transpose of fft_conv (correlation with the kernels), by numpy's FFT."""
+    nu, nphi = gFr.shape
+    L = 2 * nu
+    acc = np.zeros((L, nphi), dtype=np.complex128)
+    for g, K in ((gFr, Kr), (gFp, Kp)):
+        gp = np.zeros((L, nphi))
+        gp[:nu] = g
+        Kc = np.zeros((L, nphi))
+        k = np.arange(-(nu - 1), nu)
+        Kc[k % L] = K
+        acc += np.fft.fft2(gp) * np.conj(np.fft.fft2(Kc))
+    return G * np.real(np.fft.ifft2(acc))[:nu]
+
+
+def kernels(nu: int, nphi: int, du: float, rtol: float = 2e-14, nthreads: int = 0):
+    """Folded kernels (Kr, Kphi) for a grid; the one-time preparation step."""
+    cells = kernel_cells(nu, nphi, du, rtol=rtol, nthreads=nthreads)
+    return fold(cells, math.exp(du), 2.0 * math.pi / nphi)
+
+
+# --------------------------------------------------------------------------
+# Eq. 47-49 error norms and the relative L2 used for parity
+# --------------------------------------------------------------------------
+def norms(F_num: np.ndarray, F_ana: np.ndarray, mask=None):
+    """L1, L2, Linf of Eq. 47-49 (unweighted over the chosen cells)."""
+    d = np.abs(np.asarray(F_num) - np.asarray(F_ana))
+    if mask is not None:
+        d = d[mask]
+    return float(d.mean()), float(np.sqrt((d * d).mean())), float(d.max())
+
+
+def rel_l2(Fr, Fp, Fr_ref, Fp_ref) -> float:
+    """sqrt(sum dFr^2 + dFphi^2) / sqrt(sum Fr_ref^2 + Fphi_ref^2), both
+    components together, unweighted over cells."""
+    num = np.sum((np.asarray(Fr, np.float64) - Fr_ref) ** 2) + np.sum((np.asarray(Fp, np.float64) - Fp_ref) ** 2)
+    den = np.sum(np.asarray(Fr_ref) ** 2) + np.sum(np.asarray(Fp_ref) ** 2)
+    return float(math.sqrt(num / den))
