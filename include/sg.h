@@ -1,0 +1,172 @@
+/*
+ * sg.h -- C ABI of the GB300 thin-disk self-gravity library (libsgdisk.so).
+ *
+ * Computes the in-plane gravitational forces F_r, F_phi of an infinitesimally
+ * thin disk on a log-polar grid, following Wang, Yen & Taam, "Self-
+ * gravitational force calculation of second order accuracy for
+ * infinitesimally thin gaseous disks in polar coordinates":
+ *
+ *   grid (Sec. 3.2.1): row i has faces e^{u_min} beta^i, e^{u_min} beta^{i+1}
+ *     (beta = e^{du}) and centre r_i = e^{u_min} beta^i (1 + beta) / 2;
+ *     column j has centre phi_j = (j + 1/2) 2 pi / N_phi.
+ *   forces (Eq. 23-24, 26-29, A7-A10): the second-order sums with the
+ *     piecewise-linear density of Eq. 25 (central slopes; the density is zero
+ *     outside the grid) and the exact cell-integrated kernels of Eq. 30-32 and
+ *     A11-A13, whose singular self-cell values follow Sec. 4 / Eq. 33.
+ *     The slope terms fold into one kernel per component, so that
+ *       F_r[i,j]   = G sum_{m,l} sigma[m,l] Kr  [i-m, (j-l) mod N_phi]
+ *       F_phi[i,j] = G sum_{m,l} sigma[m,l] Kphi[i-m, (j-l) mod N_phi],
+ *     a convolution that is zero-padded in u = ln r and periodic in phi
+ *     (Eq. 27-29 in convolution form, evaluated by FFT as in Sec. 2).
+ *
+ * Layout of every field (sigma, F_r, F_phi and their gradients): row-major
+ * [N_u][N_phi], phi fastest, in the plan's dtype (float for SG_F32, double
+ * for SG_F64), 16-byte aligned, caller-owned device memory (or host memory
+ * for the *_host entry points).
+ *
+ * Execution: every call that takes a stream enqueues asynchronous work on it
+ * and returns without synchronising, except where stated.  sg_forces,
+ * sg_forces_backward and sg_forces_batched allocate nothing and may be
+ * captured in a CUDA graph.  A plan must not be used by two streams at once.
+ *
+ * Errors: no exception crosses this boundary; every call returns an
+ * sg_status.  A CUDA launch error is reported as SG_ERR_CUDA; errors of
+ * already enqueued work surface at the caller's next synchronisation.
+ */
+#ifndef SG_H
+#define SG_H
+
+#include <stddef.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SG_OK = 0,
+    SG_ERR_ARG = 1,         /* null pointer, bad size, misaligned buffer, mismatched plan */
+    SG_ERR_ALLOC = 2,       /* device or host allocation failed */
+    SG_ERR_CUDA = 3,        /* a CUDA call or launch failed */
+    SG_ERR_UNSUPPORTED = 4, /* sizes outside the supported set (see sg_plan_create) */
+    SG_ERR_NOT_BUILT = 5,   /* forces requested before sg_kernels_build */
+    SG_ERR_TIMEOUT = 6      /* a bounded device-side wait gave up */
+} sg_status;
+
+typedef enum { SG_F32 = 0, SG_F64 = 1 } sg_dtype;
+
+typedef struct sg_plan sg_plan;
+
+/* Options of the one-time kernel preparation (Sec. 2: "prepared only once
+   for a fixed grid").  Pass NULL for the defaults. */
+typedef struct {
+    double rtol;  /* relative tolerance of the cell quadrature; default 1e-14 */
+    int weight_p; /* weighting exponent p of sigma e^{p u} (the kernels carry
+                     beta^{p k}, the result e^{-p u}); algebraically neutral;
+                     default 2 */
+    int reserved[6];
+} sg_build_opts;
+
+/*
+ * Create a plan for an N_u x N_phi grid.
+ *   N_u, N_phi : powers of two; 4 <= N_u <= 4096 and 4 <= N_phi <= 8192
+ *                for SG_F32, 4 <= N_u <= 2048 and 4 <= N_phi <= 4096 for
+ *                SG_F64 (one transform must fit one block's registers and
+ *                shared memory); anything else returns SG_ERR_UNSUPPORTED.
+ *   u_min      : ln of the inner face radius (Sec. 3.2.1, M_in).
+ *   du         : log-radial step, beta = e^{du} > 1.
+ *   G          : gravitational constant (the paper uses G = 1).
+ *   dtype      : working precision of the forward/backward passes and of
+ *                the stored kernel spectra.  The kernels are always built in
+ *                FP64.
+ * Allocates the plan's device memory (spectra, workspace, twiddle tables) on
+ * the current device; the plan owns it until sg_plan_destroy.  *out is set
+ * only on SG_OK.
+ */
+sg_status sg_plan_create(sg_plan** out, int N_u, int N_phi, double u_min, double du, double G, sg_dtype dtype);
+
+/*
+ * Build the cell-integrated kernels (Eq. 30-32, A11-A13; self cell per
+ * Sec. 4), fold the slope terms, apply G beta^{p k} and transform to spectra
+ * (FP64, stored in the plan's dtype).  opts may be NULL.  Runs on stream
+ * and blocks the host until it completes; must be called once before
+ * sg_forces.  Returns SG_ERR_TIMEOUT (the plan is still usable) if a cell
+ * integral could not reach the tolerance within the quadrature's budget.
+ * Allocates and frees FP64 scratch for the spectra.
+ */
+sg_status sg_kernels_build(sg_plan* plan, const sg_build_opts* opts, cudaStream_t stream);
+
+/*
+ * Forward pass: F_r, F_phi from sigma (device pointers, layout above).
+ * F_r and F_phi are overwritten.  sigma may not alias F_r or F_phi.
+ * SG_ERR_NOT_BUILT before sg_kernels_build.
+ */
+sg_status sg_forces(sg_plan* plan, const void* sigma, void* F_r, void* F_phi, cudaStream_t stream);
+
+/*
+ * Adjoint: gsigma = A^T (gF_r, gF_phi) where A is the linear map of
+ * sg_forces, i.e. gsigma[m,l] = G sum_{i,j} gF_r[i,j] Kr[i-m, j-l]
+ *                                      + gF_phi[i,j] Kphi[i-m, j-l].
+ * gsigma is overwritten (not accumulated).
+ */
+sg_status sg_forces_backward(sg_plan* plan, const void* gF_r, const void* gF_phi, void* gsigma,
+                             cudaStream_t stream);
+
+/*
+ * Same as sg_forces with HOST buffers: copies sigma to the device, runs the
+ * forward pass and copies F_r, F_phi back, all on stream, then synchronises
+ * the stream.  Uses plan-owned device staging buffers (allocated on first
+ * use).  Host buffers should be pinned for full copy bandwidth.
+ */
+sg_status sg_forces_host(sg_plan* plan, const void* sigma_h, void* F_r_h, void* F_phi_h, cudaStream_t stream);
+
+/* One disk of a batch: its plan (built) and its device fields. */
+typedef struct {
+    sg_plan* plan;
+    const void* sigma;
+    void* F_r;
+    void* F_phi;
+} sg_batch_item;
+
+/*
+ * Forward pass for n disks of possibly different sizes, all SG_F32 or all
+ * SG_F64, enqueued in item order on stream.  items is a host array; every
+ * item is validated before any work is enqueued.  Allocates nothing;
+ * capturable in a CUDA graph.
+ */
+sg_status sg_forces_batched(const sg_batch_item* items, int n, cudaStream_t stream);
+
+/* Reserve batch resources for up to n items (currently none are needed). */
+sg_status sg_batch_reserve(int n);
+
+sg_status sg_plan_destroy(sg_plan* plan);
+
+const char* sg_status_string(sg_status s);
+
+/* ---- plan introspection (host-side; no GPU work) ---------------------- */
+
+/* Fills dims[0..3] = N_u, N_phi, dtype, built (0/1). */
+sg_status sg_plan_info(const sg_plan* plan, int dims[4]);
+
+/*
+ * Copies the plan's folded FP64 kernels to host memory (for checking the
+ * kernel builder): Kr, Kphi each [(2 N_u - 1) * N_phi] doubles, row k + N_u
+ * - 1 for k in [-(N_u-1), N_u-1], column q in [0, N_phi); these are
+ * K^eff (without G and without the beta^{pk} weight).  Synchronises stream.
+ */
+sg_status sg_plan_kernels(sg_plan* plan, double* Kr_h, double* Kphi_h, cudaStream_t stream);
+
+/*
+ * Copies the six raw FP64 cell kernels [6][(2 N_u + 1) * N_phi] (k in
+ * [-N_u, N_u], q in [0, N_phi); order K^{r,0}, K^{r,r}, K^{r,phi},
+ * K^{phi,0}, K^{phi,r}, K^{phi,phi}) to host memory.  Synchronises stream.
+ */
+sg_status sg_plan_cells(sg_plan* plan, double* cells_h, cudaStream_t stream);
+
+/* Bytes of device memory the plan holds. */
+size_t sg_plan_device_bytes(const sg_plan* plan);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SG_H */

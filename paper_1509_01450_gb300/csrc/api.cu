@@ -1,0 +1,353 @@
+// api.cu -- the extern "C" entry points of libsgdisk.so (declared in
+// include/sg.h): plan lifecycle, the one-time kernel build, and dispatch of
+// the forward / adjoint passes.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <vector>
+
+#include "sg_internal.cuh"
+
+using namespace sg;
+
+#define SG_TRY(call)                           \
+    do {                                       \
+        cudaError_t e_ = (call);               \
+        if (e_ != cudaSuccess) return SG_ERR_CUDA; \
+    } while (0)
+
+static bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+static sg_status dev_alloc(sg_plan* p, void** ptr, size_t bytes)
+{
+    if (cudaMalloc(ptr, bytes) != cudaSuccess) {
+        *ptr = nullptr;
+        cudaGetLastError();
+        return SG_ERR_ALLOC;
+    }
+    p->bytes += bytes;
+    return SG_OK;
+}
+
+static void free_plan(sg_plan* p)
+{
+    void* bufs[] = {p->tw, p->wa, p->wb, p->wc, p->kr, p->kp, p->wpre, p->wpost, p->tw64, p->cells, p->keff,
+                    p->h_sigma, p->h_fr, p->h_fp};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
+    free(p);
+}
+
+// exp(-2 pi i j / SG_NMAX) in double.  Every angle is reduced to a in
+// [0, pi/4] by exact octant identities, so cos and sin are evaluated only
+// where libm is accurate to about half an ulp.
+static void twiddles(std::vector<double>& re, std::vector<double>& im)
+{
+    const int N = SG_NMAX, E8 = SG_NMAX / 8;
+    re.resize(N);
+    im.resize(N);
+    for (int j = 0; j < N; j++) {
+        const int o = j / E8, r = j - o * E8;
+        double cc, ss;  // cos and sin of 2 pi j / N
+        if ((o & 1) == 0) {  // theta = o pi/4 + a
+            const double a = 2.0 * M_PI * r / N, c = cos(a), s = sin(a);
+            switch (o) {
+                case 0: cc = c; ss = s; break;
+                case 2: cc = -s; ss = c; break;
+                case 4: cc = -c; ss = -s; break;
+                default: cc = s; ss = -c; break;  // o == 6
+            }
+        } else {  // theta = (o + 1) pi/4 - a
+            const double a = 2.0 * M_PI * (E8 - r) / N, c = cos(a), s = sin(a);
+            switch (o) {
+                case 1: cc = s; ss = c; break;
+                case 3: cc = -c; ss = s; break;
+                case 5: cc = -s; ss = -c; break;
+                default: cc = c; ss = -s; break;  // o == 7
+            }
+        }
+        re[j] = cc;
+        im[j] = -ss;
+    }
+}
+
+extern "C" {
+
+const char* sg_status_string(sg_status s)
+{
+    switch (s) {
+        case SG_OK: return "ok";
+        case SG_ERR_ARG: return "invalid argument";
+        case SG_ERR_ALLOC: return "allocation failed";
+        case SG_ERR_CUDA: return "CUDA error";
+        case SG_ERR_UNSUPPORTED: return "unsupported size";
+        case SG_ERR_NOT_BUILT: return "kernels not built (call sg_kernels_build)";
+        case SG_ERR_TIMEOUT: return "quadrature or device wait did not converge";
+    }
+    return "unknown status";
+}
+
+sg_status sg_plan_create(sg_plan** out, int nu, int nphi, double u_min, double du, double G, sg_dtype dtype)
+{
+    if (!out) return SG_ERR_ARG;
+    if (!(du > 0.0) || !isfinite(du) || !isfinite(u_min) || !isfinite(G)) return SG_ERR_ARG;
+    if (dtype != SG_F32 && dtype != SG_F64) return SG_ERR_ARG;
+    if (!is_pow2(nu) || !is_pow2(nphi)) return SG_ERR_UNSUPPORTED;
+    const int numax = dtype == SG_F32 ? 4096 : 2048;
+    const int nphimax = dtype == SG_F32 ? 8192 : 4096;
+    if (nu < 4 || nu > numax || nphi < 4 || nphi > nphimax) return SG_ERR_UNSUPPORTED;
+
+    sg_plan* p = (sg_plan*)calloc(1, sizeof(sg_plan));
+    if (!p) return SG_ERR_ALLOC;
+    p->nu = nu;
+    p->nphi = nphi;
+    p->dtype = dtype;
+    p->u_min = u_min;
+    p->du = du;
+    p->G = G;
+    p->weight_p = 2;
+    p->elem = dtype == SG_F32 ? sizeof(float) : sizeof(double);
+    const size_t cx = 2 * p->elem;
+    int cb = dtype == SG_F32 ? 4 : 2;
+    if (cb > nphi / 2) cb = nphi / 2;
+    p->cb = cb;
+    cudaGetDevice(&p->device);
+
+    const size_t nhalf = (size_t)nu * (nphi / 2);
+    const size_t nk = (size_t)(nphi / 2 + 1) * (nu + 2);
+    sg_status st;
+    if ((st = dev_alloc(p, &p->tw, SG_NMAX * cx)) || (st = dev_alloc(p, &p->tw64, SG_NMAX * sizeof(double2))) ||
+        (st = dev_alloc(p, &p->wa, nhalf * cx)) || (st = dev_alloc(p, &p->wb, nhalf * cx)) ||
+        (st = dev_alloc(p, &p->wc, nhalf * cx)) || (st = dev_alloc(p, &p->kr, nk * cx)) ||
+        (st = dev_alloc(p, &p->kp, nk * cx)) || (st = dev_alloc(p, &p->wpre, nu * p->elem)) ||
+        (st = dev_alloc(p, &p->wpost, nu * p->elem)) ||
+        (st = dev_alloc(p, (void**)&p->cells, (size_t)6 * (2 * nu + 1) * nphi * sizeof(double))) ||
+        (st = dev_alloc(p, (void**)&p->keff, (size_t)2 * (2 * nu - 1) * nphi * sizeof(double)))) {
+        free_plan(p);
+        return st;
+    }
+    std::vector<double> re, im;
+    twiddles(re, im);
+    std::vector<double> t64(2 * SG_NMAX);
+    for (int j = 0; j < SG_NMAX; j++) {
+        t64[2 * j] = re[j];
+        t64[2 * j + 1] = im[j];
+    }
+    if (cudaMemcpy(p->tw64, t64.data(), SG_NMAX * sizeof(double2), cudaMemcpyHostToDevice) != cudaSuccess) {
+        free_plan(p);
+        return SG_ERR_CUDA;
+    }
+    cudaError_t ce;
+    if (dtype == SG_F32) {
+        std::vector<float> t32(2 * SG_NMAX);
+        for (int j = 0; j < 2 * SG_NMAX; j++) t32[j] = (float)t64[j];
+        ce = cudaMemcpy(p->tw, t32.data(), SG_NMAX * sizeof(float2), cudaMemcpyHostToDevice);
+    } else {
+        ce = cudaMemcpy(p->tw, t64.data(), SG_NMAX * sizeof(double2), cudaMemcpyHostToDevice);
+    }
+    if (ce != cudaSuccess) {
+        free_plan(p);
+        return SG_ERR_CUDA;
+    }
+    *out = p;
+    return SG_OK;
+}
+
+sg_status sg_plan_destroy(sg_plan* p)
+{
+    if (!p) return SG_ERR_ARG;
+    free_plan(p);
+    return SG_OK;
+}
+
+sg_status sg_plan_info(const sg_plan* p, int dims[4])
+{
+    if (!p || !dims) return SG_ERR_ARG;
+    dims[0] = p->nu;
+    dims[1] = p->nphi;
+    dims[2] = (int)p->dtype;
+    dims[3] = p->built;
+    return SG_OK;
+}
+
+size_t sg_plan_device_bytes(const sg_plan* p) { return p ? p->bytes : 0; }
+
+sg_status sg_kernels_build(sg_plan* p, const sg_build_opts* opts, cudaStream_t stream)
+{
+    if (!p) return SG_ERR_ARG;
+    double rtol = 1e-14;
+    int wp = 2;
+    if (opts) {
+        if (opts->rtol > 0.0) rtol = opts->rtol;
+        wp = opts->weight_p;
+        if (wp < -8 || wp > 8) return SG_ERR_ARG;
+    }
+    // beta^{p (i - i_ref)} must stay in range for both dtypes
+    if (fabs((double)wp * p->du * p->nu) > 60.0) return SG_ERR_UNSUPPORTED;
+    p->weight_p = wp;
+    const int nu = p->nu, nphi = p->nphi, L = 2 * nu;
+
+    // row weights
+    {
+        std::vector<double> pre(nu), post(nu);
+        const int iref = nu / 2;
+        for (int i = 0; i < nu; i++) {
+            pre[i] = exp(wp * (i - iref) * p->du);
+            post[i] = exp(-wp * (i - iref) * p->du);
+        }
+        if (p->dtype == SG_F32) {
+            std::vector<float> a(nu), b(nu);
+            for (int i = 0; i < nu; i++) {
+                a[i] = (float)pre[i];
+                b[i] = (float)post[i];
+            }
+            SG_TRY(cudaMemcpyAsync(p->wpre, a.data(), nu * sizeof(float), cudaMemcpyHostToDevice, stream));
+            SG_TRY(cudaMemcpyAsync(p->wpost, b.data(), nu * sizeof(float), cudaMemcpyHostToDevice, stream));
+            SG_TRY(cudaStreamSynchronize(stream));
+        } else {
+            SG_TRY(cudaMemcpyAsync(p->wpre, pre.data(), nu * sizeof(double), cudaMemcpyHostToDevice, stream));
+            SG_TRY(cudaMemcpyAsync(p->wpost, post.data(), nu * sizeof(double), cudaMemcpyHostToDevice, stream));
+            SG_TRY(cudaStreamSynchronize(stream));
+        }
+    }
+    int* flag = nullptr;
+    double *nsr = nullptr, *nsp = nullptr;
+    double2* W = nullptr;
+    sg_status ret = SG_OK;
+    if (cudaMalloc(&flag, sizeof(int)) != cudaSuccess || cudaMalloc(&nsr, (size_t)L * nphi * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&nsp, (size_t)L * nphi * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&W, (size_t)(nphi / 2 + 1) * L * sizeof(double2)) != cudaSuccess) {
+        cudaGetLastError();
+        ret = SG_ERR_ALLOC;
+        goto done;
+    }
+    if (cudaMemsetAsync(flag, 0, sizeof(int), stream) != cudaSuccess) {
+        ret = SG_ERR_CUDA;
+        goto done;
+    }
+    if (launch_cells(nu, nphi, p->du, rtol, p->cells, flag, stream) != cudaSuccess ||
+        launch_fold(nu, nphi, p->du, p->G, wp, p->cells, p->keff, nsr, nsp, stream) != cudaSuccess) {
+        ret = SG_ERR_CUDA;
+        goto done;
+    }
+    {
+        PlanView v = view(p);
+        cudaError_t e = p->dtype == SG_F32
+                            ? launch_spectra<float2>(v, nsr, nsp, W, (float2*)p->kr, (float2*)p->kp, stream)
+                            : launch_spectra<double2>(v, nsr, nsp, W, (double2*)p->kr, (double2*)p->kp, stream);
+        if (e != cudaSuccess) {
+            ret = SG_ERR_CUDA;
+            goto done;
+        }
+    }
+    {
+        int hflag = 0;
+        if (cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+            cudaStreamSynchronize(stream) != cudaSuccess) {
+            ret = SG_ERR_CUDA;
+            goto done;
+        }
+        p->built = 1;
+        if (hflag) ret = SG_ERR_TIMEOUT;
+    }
+done:
+    if (flag) cudaFree(flag);
+    if (nsr) cudaFree(nsr);
+    if (nsp) cudaFree(nsp);
+    if (W) cudaFree(W);
+    return ret;
+}
+
+static sg_status check_fields(const sg_plan* p, const void* a, const void* b, const void* c)
+{
+    if (!p) return SG_ERR_ARG;
+    if (!p->built) return SG_ERR_NOT_BUILT;
+    const void* ptrs[3] = {a, b, c};
+    for (const void* q : ptrs)
+        if (!q || ((uintptr_t)q & 15)) return SG_ERR_ARG;
+    return SG_OK;
+}
+
+sg_status sg_forces(sg_plan* p, const void* sigma, void* Fr, void* Fp, cudaStream_t stream)
+{
+    sg_status st = check_fields(p, sigma, Fr, Fp);
+    if (st) return st;
+    if (sigma == Fr || sigma == Fp || Fr == Fp) return SG_ERR_ARG;
+    PlanView v = view(p);
+    cudaError_t e = p->dtype == SG_F32 ? launch_forward<float>(v, (const float*)sigma, (float*)Fr, (float*)Fp, stream)
+                                       : launch_forward<double>(v, (const double*)sigma, (double*)Fr, (double*)Fp, stream);
+    return e == cudaSuccess ? SG_OK : SG_ERR_CUDA;
+}
+
+sg_status sg_forces_backward(sg_plan* p, const void* gr, const void* gp, void* gs, cudaStream_t stream)
+{
+    sg_status st = check_fields(p, gr, gp, gs);
+    if (st) return st;
+    if (gs == gr || gs == gp) return SG_ERR_ARG;
+    PlanView v = view(p);
+    cudaError_t e = p->dtype == SG_F32
+                        ? launch_backward<float>(v, (const float*)gr, (const float*)gp, (float*)gs, stream)
+                        : launch_backward<double>(v, (const double*)gr, (const double*)gp, (double*)gs, stream);
+    return e == cudaSuccess ? SG_OK : SG_ERR_CUDA;
+}
+
+sg_status sg_forces_host(sg_plan* p, const void* sigma_h, void* Fr_h, void* Fp_h, cudaStream_t stream)
+{
+    if (!p || !sigma_h || !Fr_h || !Fp_h) return SG_ERR_ARG;
+    if (!p->built) return SG_ERR_NOT_BUILT;
+    const size_t bytes = (size_t)p->nu * p->nphi * p->elem;
+    sg_status st;
+    if (!p->h_sigma) {
+        if ((st = dev_alloc(p, &p->h_sigma, bytes)) || (st = dev_alloc(p, &p->h_fr, bytes)) ||
+            (st = dev_alloc(p, &p->h_fp, bytes)))
+            return st;
+    }
+    SG_TRY(cudaMemcpyAsync(p->h_sigma, sigma_h, bytes, cudaMemcpyHostToDevice, stream));
+    if ((st = sg_forces(p, p->h_sigma, p->h_fr, p->h_fp, stream))) return st;
+    SG_TRY(cudaMemcpyAsync(Fr_h, p->h_fr, bytes, cudaMemcpyDeviceToHost, stream));
+    SG_TRY(cudaMemcpyAsync(Fp_h, p->h_fp, bytes, cudaMemcpyDeviceToHost, stream));
+    SG_TRY(cudaStreamSynchronize(stream));
+    return SG_OK;
+}
+
+sg_status sg_batch_reserve(int n) { return n >= 0 ? SG_OK : SG_ERR_ARG; }
+
+sg_status sg_forces_batched(const sg_batch_item* items, int n, cudaStream_t stream)
+{
+    if (n < 0 || (n > 0 && !items)) return SG_ERR_ARG;
+    for (int b = 0; b < n; b++) {
+        if (!items[b].plan) return SG_ERR_ARG;
+        sg_status st = check_fields(items[b].plan, items[b].sigma, items[b].F_r, items[b].F_phi);
+        if (st) return st;
+        if (items[b].plan->dtype != items[0].plan->dtype) return SG_ERR_ARG;
+    }
+    for (int b = 0; b < n; b++) {
+        sg_status st = sg_forces(items[b].plan, items[b].sigma, items[b].F_r, items[b].F_phi, stream);
+        if (st) return st;
+    }
+    return SG_OK;
+}
+
+sg_status sg_plan_kernels(sg_plan* p, double* Kr_h, double* Kp_h, cudaStream_t stream)
+{
+    if (!p || !Kr_h || !Kp_h) return SG_ERR_ARG;
+    if (!p->built) return SG_ERR_NOT_BUILT;
+    const size_t n = (size_t)(2 * p->nu - 1) * p->nphi;
+    SG_TRY(cudaMemcpyAsync(Kr_h, p->keff, n * sizeof(double), cudaMemcpyDeviceToHost, stream));
+    SG_TRY(cudaMemcpyAsync(Kp_h, p->keff + n, n * sizeof(double), cudaMemcpyDeviceToHost, stream));
+    SG_TRY(cudaStreamSynchronize(stream));
+    return SG_OK;
+}
+
+sg_status sg_plan_cells(sg_plan* p, double* cells_h, cudaStream_t stream)
+{
+    if (!p || !cells_h) return SG_ERR_ARG;
+    if (!p->built) return SG_ERR_NOT_BUILT;
+    const size_t n = (size_t)6 * (2 * p->nu + 1) * p->nphi;
+    SG_TRY(cudaMemcpyAsync(cells_h, p->cells, n * sizeof(double), cudaMemcpyDeviceToHost, stream));
+    SG_TRY(cudaStreamSynchronize(stream));
+    return SG_OK;
+}
+
+}  // extern "C"

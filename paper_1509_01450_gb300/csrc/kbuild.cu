@@ -1,0 +1,368 @@
+// kbuild.cu -- FP64 construction of the cell-integrated force kernels
+// (run once per grid; Sec. 2 of the paper: the kernels are "prepared only
+// once ... and stored").
+//
+// In the dimensionless variables of Eq. 33, eta = rbar / r_i and
+// xi = phibar - phi_j, with F^2 = (eta - cos xi)^2 + sin^2 xi, the six
+// kernels of Eq. 30-32 and A11-A13 for the offset (k, q) = (i - i', j - j')
+// are integrals over the source cell
+//     eta in beta^-k [2/(beta+1), 2 beta/(beta+1)],
+//     xi  in [(-q - 1/2) dphi, (-q + 1/2) dphi]
+// of
+//     -eta (1 - eta cos xi) / F^3          times 1, (eta - beta^-k), (xi + q dphi)
+//      eta^2 sin xi / F^3                  times 1, (eta - beta^-k), (xi + q dphi).
+//
+// k_cells: one warp per offset, q in [0, N_phi/2] (the other half follows
+// from the mirror xi -> -xi: K^{r,0}, K^{r,r}, K^{phi,phi} even in q,
+// K^{r,phi}, K^{phi,0}, K^{phi,r} odd).  Each rectangle is integrated by the
+// 8- and 12-point tensor Gauss-Legendre rules; if they differ by more than
+// rtol times the integral of |f| the rectangle is split in four (a depth-first
+// stack in shared memory), otherwise the 12-point value is kept.
+//
+// k_self_cell: the self cell (k, q) = (0, 0) contains the point eta = 1,
+// xi = 0 where the integrand of K^{r,0} behaves like x / rho^3 (x = eta - 1):
+// integrable only as a principal value.  The cell is symmetric under
+// (x, xi) -> (-x, -xi), so it is integrated in polar coordinates about the
+// singular point over one triangle of each opposite pair (right/left: rays
+// to x = +-h; top/bottom: rays to xi = +-dphi/2) with f(p) + f(-p): the
+// odd 1/rho^2 part cancels and rho f is smooth, so Gauss-Legendre in
+// (angle, radius) converges fast.  K^{r,phi}, K^{phi,0}, K^{phi,r} vanish on
+// the self cell by symmetry (Sec. 3.2.2 and App. A).
+//
+// k_fold: the slope terms of Eq. 28-29 / A9-A10 with central differences
+// fold into one kernel per component:
+//   K^eff[k,q] = K^{.,0}[k,q] + (beta^{k+1} K^{.,r}[k+1,q]
+//                - beta^{k-1} K^{.,r}[k-1,q]) / (beta - 1/beta)
+//                + (K^{.,phi}[k,q+1] - K^{.,phi}[k,q-1]) / (2 dphi),
+// then the weighted, normalised kernel G beta^{p k} K^eff / (L N_phi) is
+// placed cyclically at row k mod L (L = 2 N_u, row N_u left zero).
+#include <math.h>
+#include <stdio.h>
+
+#include "sg_internal.cuh"
+
+namespace sg {
+
+__constant__ double c_x8[8], c_w8[8], c_x12[12], c_w12[12], c_x32[32], c_w32[32], c_x24[24], c_w24[24];
+
+// Gauss-Legendre nodes and weights on [-1, 1]: Newton iteration on the
+// three-term recurrence of P_n from the asymptotic first guess.
+void gauss_legendre(int n, double* x, double* w)
+{
+    for (int k = 1; k <= n; k++) {
+        double z = (1.0 - 1.0 / (8.0 * n * n) + 1.0 / (8.0 * n * n * n)) * cos(M_PI * (4.0 * k - 1.0) / (4.0 * n + 2.0));
+        double dp = 0.0;
+        for (int it = 0; it < 50; it++) {
+            double p0 = 1.0, p1 = z;
+            for (int j = 2; j <= n; j++) {
+                double p2 = ((2 * j - 1) * z * p1 - (j - 1) * p0) / j;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = n * (p0 - z * p1) / (1.0 - z * z);
+            double dz = p1 / dp;
+            z -= dz;
+            if (fabs(dz) <= 1e-16 * fabs(z) + 1e-300) break;
+        }
+        double p0 = 1.0, p1 = z;
+        for (int j = 2; j <= n; j++) {
+            double p2 = ((2 * j - 1) * z * p1 - (j - 1) * p0) / j;
+            p0 = p1;
+            p1 = p2;
+        }
+        dp = n * (p0 - z * p1) / (1.0 - z * z);
+        x[k - 1] = z;
+        w[k - 1] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+static cudaError_t upload_rules()
+{
+    static int done_dev = -1;
+    int dev;
+    cudaGetDevice(&dev);
+    if (done_dev == dev) return cudaSuccess;
+    double x[32], w[32];
+    cudaError_t e;
+    gauss_legendre(8, x, w);
+    if ((e = cudaMemcpyToSymbol(c_x8, x, 8 * sizeof(double))) != cudaSuccess) return e;
+    if ((e = cudaMemcpyToSymbol(c_w8, w, 8 * sizeof(double))) != cudaSuccess) return e;
+    gauss_legendre(12, x, w);
+    if ((e = cudaMemcpyToSymbol(c_x12, x, 12 * sizeof(double))) != cudaSuccess) return e;
+    if ((e = cudaMemcpyToSymbol(c_w12, w, 12 * sizeof(double))) != cudaSuccess) return e;
+    gauss_legendre(24, x, w);
+    if ((e = cudaMemcpyToSymbol(c_x24, x, 24 * sizeof(double))) != cudaSuccess) return e;
+    if ((e = cudaMemcpyToSymbol(c_w24, w, 24 * sizeof(double))) != cudaSuccess) return e;
+    gauss_legendre(32, x, w);
+    if ((e = cudaMemcpyToSymbol(c_x32, x, 32 * sizeof(double))) != cudaSuccess) return e;
+    if ((e = cudaMemcpyToSymbol(c_w32, w, 32 * sizeof(double))) != cudaSuccess) return e;
+    done_dev = dev;
+    return cudaSuccess;
+}
+
+// the six integrands at (eta, xi), accumulated with weight w
+__device__ __forceinline__ void acc6(double eta, double xi, double c, double s, double eta_c, double qd, double w,
+                                     double* I, double* A)
+{
+    const double d = eta - c;
+    const double F2 = d * d + s * s;
+    const double iF = 1.0 / sqrt(F2);
+    const double iF3 = iF * iF * iF;
+    const double ir0 = -eta * (1.0 - eta * c) * iF3;
+    const double ip0 = eta * eta * s * iF3;
+    const double dr = eta - eta_c, dp = xi + qd;
+    const double v[6] = {ir0, ir0 * dr, ir0 * dp, ip0, ip0 * dr, ip0 * dp};
+#pragma unroll
+    for (int c6 = 0; c6 < 6; c6++) {
+        I[c6] += w * v[c6];
+        if (A) A[c6] += w * fabs(v[c6]);
+    }
+}
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+#define SG_STACK 40
+#define SG_MAXRECT 4000
+
+__global__ void __launch_bounds__(128) k_cells(int nu, int nphi, double du, double rtol, double* __restrict__ cells,
+                                               int* __restrict__ flag)
+{
+    __shared__ double4 stack_all[4][SG_STACK];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    double4* stack = stack_all[wib];
+    const double beta = exp(du), dphi = 2.0 * M_PI / nphi;
+    const int nq = nphi / 2 + 1;
+    const long noff = (long)(2 * nu + 1) * nq;
+    const long per = (long)(2 * nu + 1) * nphi;
+    const long wstride = (long)gridDim.x * 4;
+    for (long off = (long)blockIdx.x * 4 + wib; off < noff; off += wstride) {
+        const int k = (int)(off / nq) - nu;
+        const int q = (int)(off % nq);
+        if (k == 0 && q == 0) continue;  // self cell: k_self_cell
+        const double eta_c = exp(-du * k);
+        const double qd = q * dphi;
+        double res[6] = {0, 0, 0, 0, 0, 0};
+        int sp = 0, nrect = 0, bad = 0;
+        stack[0] = make_double4(eta_c * 2.0 / (beta + 1.0), eta_c * 2.0 * beta / (beta + 1.0), (-q - 0.5) * dphi,
+                                (-q + 0.5) * dphi);
+        sp = 1;
+        while (sp > 0) {
+            __syncwarp();
+            const double4 R = stack[--sp];
+            __syncwarp();
+            nrect++;
+            const double he = 0.5 * (R.y - R.x), me = 0.5 * (R.y + R.x);
+            const double hx = 0.5 * (R.w - R.z), mx = 0.5 * (R.w + R.z);
+            double I8[6] = {0, 0, 0, 0, 0, 0}, I12[6] = {0, 0, 0, 0, 0, 0}, A12[6] = {0, 0, 0, 0, 0, 0};
+            for (int p = lane; p < 64; p += 32) {
+                const int a = p >> 3, b = p & 7;
+                const double eta = me + he * c_x8[a], xi = mx + hx * c_x8[b];
+                double s, c;
+                sincos(xi, &s, &c);
+                acc6(eta, xi, c, s, eta_c, qd, he * hx * c_w8[a] * c_w8[b], I8, nullptr);
+            }
+            for (int p = lane; p < 144; p += 32) {
+                const int a = p / 12, b = p % 12;
+                const double eta = me + he * c_x12[a], xi = mx + hx * c_x12[b];
+                double s, c;
+                sincos(xi, &s, &c);
+                acc6(eta, xi, c, s, eta_c, qd, he * hx * c_w12[a] * c_w12[b], I12, A12);
+            }
+            bool ok = true;
+#pragma unroll
+            for (int c6 = 0; c6 < 6; c6++) {
+                I8[c6] = warp_sum(I8[c6]);
+                I12[c6] = warp_sum(I12[c6]);
+                A12[c6] = warp_sum(A12[c6]);
+                if (fabs(I12[c6] - I8[c6]) > rtol * A12[c6]) ok = false;
+            }
+            if (!ok && (sp + 4 > SG_STACK || nrect >= SG_MAXRECT)) {
+                ok = true;
+                bad = 1;
+            }
+            if (ok) {
+#pragma unroll
+                for (int c6 = 0; c6 < 6; c6++) res[c6] += I12[c6];
+            } else {
+                __syncwarp();
+                if (lane == 0) {
+                    stack[sp + 0] = make_double4(R.x, me, R.z, mx);
+                    stack[sp + 1] = make_double4(me, R.y, R.z, mx);
+                    stack[sp + 2] = make_double4(R.x, me, mx, R.w);
+                    stack[sp + 3] = make_double4(me, R.y, mx, R.w);
+                }
+                sp += 4;
+            }
+        }
+        if (lane == 0) {
+            const long row = (long)(k + nu) * nphi;
+            const int qm = (nphi - q) & (nphi - 1);
+#pragma unroll
+            for (int c6 = 0; c6 < 6; c6++) {
+                cells[c6 * per + row + q] = res[c6];
+                const bool odd = (c6 == 2 || c6 == 3 || c6 == 4);
+                if (qm != q) cells[c6 * per + row + qm] = odd ? -res[c6] : res[c6];
+            }
+            if (bad) atomicOr(flag, 1);
+        }
+    }
+}
+
+// the three self-cell integrands at x = eta - 1, y = xi (accurate near 0)
+__device__ __forceinline__ void self3(double x, double y, double* v)
+{
+    double s, c;
+    sincos(y, &s, &c);
+    const double sh = sin(0.5 * y);
+    const double vc = 2.0 * sh * sh;  // 1 - cos y
+    const double eta = 1.0 + x;
+    const double d = x + vc;          // eta - cos y
+    const double F2 = d * d + s * s;
+    const double iF = 1.0 / sqrt(F2);
+    const double iF3 = iF * iF * iF;
+    const double om = vc - x * c;     // 1 - eta cos y
+    const double ir0 = -eta * om * iF3;
+    const double ip0 = eta * eta * s * iF3;
+    v[0] = ir0;
+    v[1] = ir0 * x;
+    v[2] = ip0 * y;
+}
+
+template <int NG>
+__device__ void self_rule(double h, double d, double* out)
+{
+    const double* gx = NG == 32 ? c_x32 : c_x24;
+    const double* gw = NG == 32 ? c_w32 : c_w24;
+    const double thc = atan2(d, h);
+    double acc[3] = {0, 0, 0};
+    for (int p = threadIdx.x; p < 2 * NG * NG; p += blockDim.x) {
+        const int reg = p / (NG * NG), a = (p / NG) % NG, b = p % NG;
+        double th, thw, rmax;
+        if (reg == 0) {  // right (and, by reflection, left) triangle
+            th = thc * gx[a];
+            thw = thc * gw[a];
+            rmax = h / cos(th);
+        } else {  // top (and bottom) triangle
+            const double hm = 0.5 * (M_PI - 2.0 * thc);
+            th = 0.5 * M_PI + hm * gx[a];
+            thw = hm * gw[a];
+            rmax = d / sin(th);
+        }
+        const double tau = 0.5 * (1.0 + gx[b]);
+        const double rho = rmax * tau;
+        const double w = thw * 0.5 * gw[b] * rmax * rmax * tau;
+        double ct, st;
+        sincos(th, &st, &ct);
+        double v1[3], v2[3];
+        self3(rho * ct, rho * st, v1);
+        self3(-rho * ct, -rho * st, v2);
+#pragma unroll
+        for (int c3 = 0; c3 < 3; c3++) acc[c3] += w * (v1[c3] + v2[c3]);
+    }
+    __shared__ double red[3][32];
+#pragma unroll
+    for (int c3 = 0; c3 < 3; c3++) {
+        double v = warp_sum(acc[c3]);
+        if ((threadIdx.x & 31) == 0) red[c3][threadIdx.x >> 5] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int c3 = 0; c3 < 3; c3++) {
+            double s = 0;
+            for (int w8 = 0; w8 < (int)(blockDim.x >> 5); w8++) s += red[c3][w8];
+            out[c3] = s;
+        }
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(256) k_self_cell(int nu, int nphi, double du, double rtol,
+                                                   double* __restrict__ cells, int* __restrict__ flag)
+{
+    const double beta = exp(du), dphi = 2.0 * M_PI / nphi;
+    const double h = (beta - 1.0) / (beta + 1.0), d = 0.5 * dphi;
+    __shared__ double r32[3], r24[3];
+    self_rule<32>(h, d, r32);
+    self_rule<24>(h, d, r24);
+    if (threadIdx.x == 0) {
+        const long per = (long)(2 * nu + 1) * nphi;
+        const long at = (long)nu * nphi;  // k = 0, q = 0
+        cells[0 * per + at] = r32[0];
+        cells[1 * per + at] = r32[1];
+        cells[2 * per + at] = 0.0;
+        cells[3 * per + at] = 0.0;
+        cells[4 * per + at] = 0.0;
+        cells[5 * per + at] = r32[2];
+        for (int c3 = 0; c3 < 3; c3++)
+            if (fabs(r32[c3] - r24[c3]) > fmax(rtol, 1e-13) * fabs(r32[c3])) atomicOr(flag, 2);
+    }
+}
+
+__global__ void k_fold(int nu, int nphi, double du, double G, int p, const double* __restrict__ cells,
+                       double* __restrict__ keff, double* __restrict__ nsr, double* __restrict__ nsp)
+{
+    const int L = 2 * nu;
+    const long total = (long)L * nphi;
+    const long per = (long)(2 * nu + 1) * nphi;
+    const long perk = (long)(2 * nu - 1) * nphi;
+    const double beta = exp(du), bb = beta - 1.0 / beta, dphi = 2.0 * M_PI / nphi;
+    const double norm = G / ((double)L * nphi);
+    for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+        const int kk = (int)(idx / nphi), q = (int)(idx % nphi);
+        if (kk == nu) {
+            nsr[idx] = 0.0;
+            nsp[idx] = 0.0;
+            continue;
+        }
+        const int k = kk < nu ? kk : kk - L;
+        const int qp = (q + 1) & (nphi - 1), qm = (q - 1) & (nphi - 1);
+        const double* C0 = cells + 0 * per;
+        const double* C1 = cells + 1 * per;
+        const double* C2 = cells + 2 * per;
+        const double* C3 = cells + 3 * per;
+        const double* C4 = cells + 4 * per;
+        const double* C5 = cells + 5 * per;
+        const long rk = (long)(k + nu) * nphi, ru = rk + nphi, rd = rk - nphi;
+        const double bu = exp((k + 1) * du), bd = exp((k - 1) * du);
+        const double Kr = C0[rk + q] + (bu * C1[ru + q] - bd * C1[rd + q]) / bb + (C2[rk + qp] - C2[rk + qm]) / (2.0 * dphi);
+        const double Kp = C3[rk + q] + (bu * C4[ru + q] - bd * C4[rd + q]) / bb + (C5[rk + qp] - C5[rk + qm]) / (2.0 * dphi);
+        keff[(long)(k + nu - 1) * nphi + q] = Kr;
+        keff[perk + (long)(k + nu - 1) * nphi + q] = Kp;
+        const double sc = norm * exp(p * k * du);
+        nsr[idx] = Kr * sc;
+        nsp[idx] = Kp * sc;
+    }
+}
+
+cudaError_t launch_cells(int nu, int nphi, double du, double rtol, double* cells, int* flag, cudaStream_t st)
+{
+    cudaError_t e = upload_rules();
+    if (e != cudaSuccess) return e;
+    int dev, nsm;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const long noff = (long)(2 * nu + 1) * (nphi / 2 + 1);
+    long blocks = (noff + 3) / 4;
+    const long cap = (long)nsm * 32;
+    if (blocks > cap) blocks = cap;
+    k_cells<<<(int)blocks, 128, 0, st>>>(nu, nphi, du, rtol, cells, flag);
+    k_self_cell<<<1, 256, 0, st>>>(nu, nphi, du, rtol, cells, flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fold(int nu, int nphi, double du, double G, int p, const double* cells, double* keff, double* nsr,
+                        double* nsp, cudaStream_t st)
+{
+    const long total = (long)2 * nu * nphi;
+    long blocks = (total + 255) / 256;
+    if (blocks > 65535) blocks = 65535;
+    k_fold<<<(int)blocks, 256, 0, st>>>(nu, nphi, du, G, p, cells, keff, nsr, nsp);
+    return cudaGetLastError();
+}
+
+}  // namespace sg

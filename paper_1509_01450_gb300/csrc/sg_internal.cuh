@@ -1,0 +1,83 @@
+// sg_internal.cuh -- plan object and launcher declarations shared by the
+// translation units of libsgdisk.so.
+#pragma once
+#include "../../include/sg.h"
+#include "sg_common.cuh"
+
+// The plan behind the opaque sg_plan handle.
+struct sg_plan {
+    int nu, nphi;
+    sg_dtype dtype;
+    double u_min, du, G;
+    int weight_p;
+    int built;
+    int cb;          // column-block width of the half-spectrum buffers
+    int device;      // device the plan's memory lives on
+    size_t elem;     // bytes of one real in the working dtype
+    // working-dtype device buffers
+    void* tw;        // twiddle table, SG_NMAX complex
+    void* wa;        // column-block half spectra, nu * nphi/2 complex
+    void* wb;        // row-major half spectra, nu * nphi/2 complex
+    void* wc;        // half spectra (row-major fwd / column-block bwd)
+    void* kr;        // Khat_r, (nphi/2 + 1) x (nu + 2) complex
+    void* kp;        // Khat_phi, same shape
+    void* wpre;      // beta^{p (i - i_ref)}, nu reals
+    void* wpost;     // beta^{-p (i - i_ref)}
+    // FP64 device buffers
+    void* tw64;      // twiddle table, SG_NMAX double complex
+    double* cells;   // 6 x (2 nu + 1) x nphi raw cell kernels (kept after build)
+    double* keff;    // 2 x (2 nu - 1) x nphi folded kernels K^eff
+    // host-API staging (allocated on first sg_forces_host)
+    void* h_sigma;
+    void* h_fr;
+    void* h_fp;
+    size_t bytes;    // device bytes held
+};
+
+namespace sg {
+
+// Plain view of a plan passed to the launchers.
+struct PlanView {
+    int nu, nphi, cb;
+    const void* tw;
+    const void* tw64;
+    void *wa, *wb, *wc;
+    const void* kr;
+    const void* kp;
+    const void* wpre;
+    const void* wpost;
+};
+
+inline PlanView view(const sg_plan* p)
+{
+    PlanView v;
+    v.nu = p->nu;
+    v.nphi = p->nphi;
+    v.cb = p->cb;
+    v.tw = p->tw;
+    v.tw64 = p->tw64;
+    v.wa = p->wa;
+    v.wb = p->wb;
+    v.wc = p->wc;
+    v.kr = p->kr;
+    v.kp = p->kp;
+    v.wpre = p->wpre;
+    v.wpost = p->wpost;
+    return v;
+}
+
+template <typename T>
+cudaError_t launch_forward(const PlanView& p, const T* sigma, T* Fr, T* Fp, cudaStream_t st);
+template <typename T>
+cudaError_t launch_backward(const PlanView& p, const T* gr, const T* gp, T* gs, cudaStream_t st);
+template <typename VO>
+cudaError_t launch_spectra(const PlanView& p, const double* nsr, const double* nsp, double2* W, VO* Kr, VO* Kp,
+                           cudaStream_t st);
+
+// kbuild.cu
+cudaError_t launch_cells(int nu, int nphi, double du, double rtol, double* cells, int* flag, cudaStream_t st);
+cudaError_t launch_fold(int nu, int nphi, double du, double G, int p, const double* cells, double* keff,
+                        double* nsr, double* nsp, cudaStream_t st);
+void gauss_legendre(int n, double* x, double* w);
+
+}  // namespace sg

@@ -1,0 +1,228 @@
+"""Thin Python binding of libsgdisk.so (include/sg.h).
+
+Argument marshalling only: every step of the force computation runs in the
+library's CUDA kernels.  PyTorch provides device memory and the current
+stream.  If the library has not been built the calls raise; there is no
+fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsgdisk.so")
+
+SG_OK, SG_ERR_ARG, SG_ERR_ALLOC, SG_ERR_CUDA, SG_ERR_UNSUPPORTED, SG_ERR_NOT_BUILT, SG_ERR_TIMEOUT = range(7)
+SG_F32, SG_F64 = 0, 1
+
+EXPORTS = ("sg_plan_create", "sg_kernels_build", "sg_forces", "sg_forces_backward", "sg_forces_host",
+           "sg_forces_batched", "sg_batch_reserve", "sg_plan_destroy", "sg_status_string", "sg_plan_info",
+           "sg_plan_kernels", "sg_plan_cells", "sg_plan_device_bytes")
+
+
+class SgError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {status_string(status)} ({status})")
+
+
+class BuildOpts(ctypes.Structure):
+    _fields_ = [("rtol", ctypes.c_double), ("weight_p", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
+
+
+class BatchItem(ctypes.Structure):
+    _fields_ = [("plan", ctypes.c_void_p), ("sigma", ctypes.c_void_p), ("F_r", ctypes.c_void_p),
+                ("F_phi", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libsgdisk.so (raises if it is missing: no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is not built; run `python -m paper_1509_01450_gb300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, ip, dp = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        L.sg_plan_create.argtypes = [ctypes.POINTER(vp), ip, ip, dp, dp, dp, ip]
+        L.sg_kernels_build.argtypes = [vp, ctypes.POINTER(BuildOpts), vp]
+        L.sg_forces.argtypes = [vp, vp, vp, vp, vp]
+        L.sg_forces_backward.argtypes = [vp, vp, vp, vp, vp]
+        L.sg_forces_host.argtypes = [vp, vp, vp, vp, vp]
+        L.sg_forces_batched.argtypes = [ctypes.POINTER(BatchItem), ip, vp]
+        L.sg_batch_reserve.argtypes = [ip]
+        L.sg_plan_destroy.argtypes = [vp]
+        L.sg_status_string.argtypes = [ip]
+        L.sg_status_string.restype = ctypes.c_char_p
+        L.sg_plan_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+        L.sg_plan_kernels.argtypes = [vp, ctypes.POINTER(dp), ctypes.POINTER(dp), vp]
+        L.sg_plan_cells.argtypes = [vp, ctypes.POINTER(dp), vp]
+        L.sg_plan_device_bytes.argtypes = [vp]
+        L.sg_plan_device_bytes.restype = ctypes.c_size_t
+        for name in EXPORTS:
+            if name not in ("sg_status_string", "sg_plan_device_bytes"):
+                getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def status_string(status: int) -> str:
+    return lib().sg_status_string(int(status)).decode()
+
+
+def _check(status: int, what: str):
+    if status != SG_OK:
+        raise SgError(status, what)
+
+
+def _stream(stream):
+    import torch
+
+    if stream is None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, torch.cuda.Stream):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Plan:
+    """A log-polar grid with its prepared kernel spectra (sg_plan)."""
+
+    def __init__(self, nu: int, nphi: int, u_min: float, du: float, G: float = 1.0, dtype="float32"):
+        import torch
+
+        self.dtype = torch.float32 if str(dtype) in ("float32", "torch.float32", "f32") else torch.float64
+        self.nu, self.nphi, self.u_min, self.du, self.G = int(nu), int(nphi), float(u_min), float(du), float(G)
+        h = ctypes.c_void_p()
+        code = SG_F32 if self.dtype == torch.float32 else SG_F64
+        _check(lib().sg_plan_create(ctypes.byref(h), self.nu, self.nphi, self.u_min, self.du, self.G, code),
+               "sg_plan_create")
+        self.handle = h
+
+    # -- one-time preparation ------------------------------------------------
+    def build(self, rtol: float = 1e-14, weight_p: int = 2, stream=None):
+        opts = BuildOpts(rtol, weight_p)
+        _check(lib().sg_kernels_build(self.handle, ctypes.byref(opts), _stream(stream)), "sg_kernels_build")
+        return self
+
+    # -- forward / adjoint ---------------------------------------------------
+    def _new(self):
+        import torch
+
+        return torch.empty((self.nu, self.nphi), dtype=self.dtype, device="cuda")
+
+    def forces(self, sigma, F_r=None, F_phi=None, stream=None):
+        F_r = self._new() if F_r is None else F_r
+        F_phi = self._new() if F_phi is None else F_phi
+        self._check_field(sigma)
+        _check(lib().sg_forces(self.handle, _ptr(sigma), _ptr(F_r), _ptr(F_phi), _stream(stream)), "sg_forces")
+        return F_r, F_phi
+
+    def backward(self, gF_r, gF_phi, gsigma=None, stream=None):
+        gsigma = self._new() if gsigma is None else gsigma
+        self._check_field(gF_r)
+        self._check_field(gF_phi)
+        _check(lib().sg_forces_backward(self.handle, _ptr(gF_r), _ptr(gF_phi), _ptr(gsigma), _stream(stream)),
+               "sg_forces_backward")
+        return gsigma
+
+    def forces_host(self, sigma_h, F_r_h, F_phi_h, stream=None):
+        """Host buffers (pinned torch CPU tensors); copies are inside the call."""
+        for t in (sigma_h, F_r_h, F_phi_h):
+            assert t.device.type == "cpu" and t.is_contiguous() and t.dtype == self.dtype
+        _check(lib().sg_forces_host(self.handle, _ptr(sigma_h), _ptr(F_r_h), _ptr(F_phi_h), _stream(stream)),
+               "sg_forces_host")
+        return F_r_h, F_phi_h
+
+    def _check_field(self, t):
+        if t.dtype != self.dtype or tuple(t.shape) != (self.nu, self.nphi) or not t.is_contiguous() or not t.is_cuda:
+            raise ValueError(f"field must be a contiguous CUDA {self.dtype} tensor of shape ({self.nu}, {self.nphi})")
+
+    # -- introspection ---------------------------------------------------------
+    def info(self):
+        d = (ctypes.c_int * 4)()
+        _check(lib().sg_plan_info(self.handle, d), "sg_plan_info")
+        return tuple(d)
+
+    def kernels(self, stream=None):
+        """Folded FP64 kernels K^eff (Kr, Kphi), each [2 Nu - 1, Nphi]."""
+        n = (2 * self.nu - 1) * self.nphi
+        kr = np.zeros(n)
+        kp = np.zeros(n)
+        dpp = ctypes.POINTER(ctypes.c_double)
+        _check(lib().sg_plan_kernels(self.handle, kr.ctypes.data_as(dpp), kp.ctypes.data_as(dpp), _stream(stream)),
+               "sg_plan_kernels")
+        return kr.reshape(2 * self.nu - 1, self.nphi), kp.reshape(2 * self.nu - 1, self.nphi)
+
+    def cells(self, stream=None):
+        """Raw FP64 cell kernels [6, 2 Nu + 1, Nphi]."""
+        out = np.zeros(6 * (2 * self.nu + 1) * self.nphi)
+        _check(lib().sg_plan_cells(self.handle, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                   _stream(stream)), "sg_plan_cells")
+        return out.reshape(6, 2 * self.nu + 1, self.nphi)
+
+    def device_bytes(self) -> int:
+        return int(lib().sg_plan_device_bytes(self.handle))
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            lib().sg_plan_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def forces_batched(items, stream=None):
+    """items: list of (plan, sigma, F_r, F_phi) with device tensors."""
+    arr = (BatchItem * len(items))()
+    for n, (p, s, fr, fp) in enumerate(items):
+        p._check_field(s)
+        arr[n] = BatchItem(p.handle.value, s.data_ptr(), fr.data_ptr(), fp.data_ptr())
+    _check(lib().sg_forces_batched(arr, len(items), _stream(stream)), "sg_forces_batched")
+
+
+def _autograd_fn():
+    import torch
+
+    class SelfGravity(torch.autograd.Function):
+        """(F_r, F_phi) = A sigma; backward gives A^T (gF_r, gF_phi) through
+        the library's adjoint passes."""
+
+        @staticmethod
+        def forward(ctx, sigma, plan):
+            ctx.plan = plan
+            return plan.forces(sigma.contiguous())
+
+        @staticmethod
+        def backward(ctx, gF_r, gF_phi):
+            plan = ctx.plan
+            gr = gF_r.contiguous() if gF_r is not None else torch.zeros((plan.nu, plan.nphi), dtype=plan.dtype,
+                                                                         device="cuda")
+            gp = gF_phi.contiguous() if gF_phi is not None else torch.zeros_like(gr)
+            return plan.backward(gr, gp), None
+
+    return SelfGravity
+
+
+_SG = None
+
+
+def self_gravity(sigma, plan):
+    """Differentiable forces: returns (F_r, F_phi)."""
+    global _SG
+    if _SG is None:
+        _SG = _autograd_fn()
+    return _SG.apply(sigma, plan)
