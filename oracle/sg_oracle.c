@@ -256,6 +256,7 @@ typedef struct {
 typedef struct {
     const cell_t* cell;
     double xi, c, s; /* outer node and cos, sin of it */
+    double vc;       /* 1 - cos xi = 2 sin^2(xi/2), without cancellation */
 } inner_t;
 
 /* The six integrands at (eta, xi); om = 1 - eta cos xi, F3 = F^3. */
@@ -277,10 +278,14 @@ static inline void six(double eta, double xi, double s, double om, double F3, do
 static void f_eta(double eta, const void* vctx, double out[NV])
 {
     const inner_t* ic = (const inner_t*)vctx;
-    double d = eta - ic->c;
+    /* eta - cos xi and 1 - eta cos xi from eta - 1 (exact near eta = 1) and
+       1 - cos xi, so that both keep their relative precision where they are
+       small */
+    double e1 = eta - 1.0;
+    double d = e1 + ic->vc;
     double F2 = d * d + ic->s * ic->s;
     double F3 = F2 * sqrt(F2);
-    double om = 1.0 - eta * ic->c;
+    double om = ic->vc - e1 * ic->c;
     six(eta, ic->xi, ic->s, om, F3, ic->cell->eta_c, ic->cell->qd, out);
 }
 
@@ -323,6 +328,7 @@ static void f_xi(double xi, const void* vctx, double out[NV])
     ic.xi = xi;
     ic.c = cos(xi);
     ic.s = sin(xi);
+    ic.vc = 2.0 * sin(0.5 * xi) * sin(0.5 * xi);
     double abs_[NV];
     int st;
     if (cell->self && ic.s != 0.0) {
@@ -402,11 +408,11 @@ int sgo_cell(double du, int nphi, int k, int q, double rtol, double out6[NC])
     if (cell.self) {
         /* rounding in the near-singular inner integrals, relative to a cell
            value that shrinks with the cell, sets a floor on what this cell
-           can resolve: try 1e-13, and 1e-12 where that does not converge */
+           can resolve: try 1e-14, then 1e-13, then 1e-12 */
         bp[nb++] = 0.0;
         bp[nb++] = cell.xi_hi;
-        double floors[2] = {1e-13, 1e-12};
-        for (int attempt = 0; attempt < 2; attempt++) {
+        double floors[3] = {1e-14, 1e-13, 1e-12};
+        for (int attempt = 0; attempt < 3; attempt++) {
             cell.rtol = rtol > floors[attempt] ? rtol : floors[attempt];
             bad = 0;
             st = adapt(f_xi_pair, &cell, bp, nb, cell.rtol, 0.0, 0, out, abs_);

@@ -177,7 +177,7 @@ sg_status sg_kernels_build(sg_plan* p, const sg_build_opts* opts, cudaStream_t s
 {
     if (!p) return SG_ERR_ARG;
     double rtol = 1e-14;
-    int wp = 2;
+    int wp = 0;
     if (opts) {
         if (opts->rtol > 0.0) rtol = opts->rtol;
         wp = opts->weight_p;

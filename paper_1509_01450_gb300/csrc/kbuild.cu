@@ -16,8 +16,10 @@
 // from the mirror xi -> -xi: K^{r,0}, K^{r,r}, K^{phi,phi} even in q,
 // K^{r,phi}, K^{phi,0}, K^{phi,r} odd).  Each rectangle is integrated by the
 // 8- and 12-point tensor Gauss-Legendre rules; if they differ by more than
-// rtol times the integral of |f| the rectangle is split in four (a depth-first
-// stack in shared memory), otherwise the 12-point value is kept.
+// rtol times the integral of |f| the rectangle is split (a depth-first stack
+// in shared memory): in two across its physically longer side when one side
+// is more than twice the other, else in four.  Otherwise the 12-point value
+// is kept.
 //
 // k_self_cell: the self cell (k, q) = (0, 0) contains the point eta = 1,
 // xi = 0 where the integrand of K^{r,0} behaves like x / rho^3 (x = eta - 1):
@@ -25,8 +27,9 @@
 // (x, xi) -> (-x, -xi), so it is integrated in polar coordinates about the
 // singular point over one triangle of each opposite pair (right/left: rays
 // to x = +-h; top/bottom: rays to xi = +-dphi/2) with f(p) + f(-p): the
-// odd 1/rho^2 part cancels and rho f is smooth, so Gauss-Legendre in
-// (angle, radius) converges fast.  K^{r,phi}, K^{phi,0}, K^{phi,r} vanish on
+// odd 1/rho^2 part cancels and rho f is smooth, so composite Gauss-Legendre
+// in (angle, radius) converges fast; the panels are doubled until two
+// levels agree.  K^{r,phi}, K^{phi,0}, K^{phi,r} vanish on
 // the self cell by symmetry (Sec. 3.2.2 and App. A).
 //
 // k_fold: the slope terms of Eq. 28-29 / A9-A10 with central differences
@@ -43,7 +46,7 @@
 
 namespace sg {
 
-__constant__ double c_x8[8], c_w8[8], c_x12[12], c_w12[12], c_x32[32], c_w32[32], c_x24[24], c_w24[24];
+__constant__ double c_x8[8], c_w8[8], c_x12[12], c_w12[12], c_x16[16], c_w16[16];
 
 // Gauss-Legendre nodes and weights on [-1, 1]: Newton iteration on the
 // three-term recurrence of P_n from the asymptotic first guess.
@@ -90,28 +93,34 @@ static cudaError_t upload_rules()
     gauss_legendre(12, x, w);
     if ((e = cudaMemcpyToSymbol(c_x12, x, 12 * sizeof(double))) != cudaSuccess) return e;
     if ((e = cudaMemcpyToSymbol(c_w12, w, 12 * sizeof(double))) != cudaSuccess) return e;
-    gauss_legendre(24, x, w);
-    if ((e = cudaMemcpyToSymbol(c_x24, x, 24 * sizeof(double))) != cudaSuccess) return e;
-    if ((e = cudaMemcpyToSymbol(c_w24, w, 24 * sizeof(double))) != cudaSuccess) return e;
-    gauss_legendre(32, x, w);
-    if ((e = cudaMemcpyToSymbol(c_x32, x, 32 * sizeof(double))) != cudaSuccess) return e;
-    if ((e = cudaMemcpyToSymbol(c_w32, w, 32 * sizeof(double))) != cudaSuccess) return e;
+    gauss_legendre(16, x, w);
+    if ((e = cudaMemcpyToSymbol(c_x16, x, 16 * sizeof(double))) != cudaSuccess) return e;
+    if ((e = cudaMemcpyToSymbol(c_w16, w, 16 * sizeof(double))) != cudaSuccess) return e;
     done_dev = dev;
     return cudaSuccess;
 }
 
-// the six integrands at (eta, xi), accumulated with weight w
-__device__ __forceinline__ void acc6(double eta, double xi, double c, double s, double eta_c, double qd, double w,
+// the six integrands at eta = eta_c + del and xi = xi_c + dp (dp is the
+// azimuth measured from the source-cell centre, the factor of K^{.,phi}),
+// accumulated with weight w; c, s = cos xi, sin xi.  em1 = eta_c - 1 (exact
+// for k = 0).  eta - 1, eta - cos xi and
+// 1 - eta cos xi are formed from 1 - cos xi = sin^2 xi / (1 + cos xi)
+// (or 1 - cos xi directly when cos xi <= 0) and eta - 1 = em1 + del, so they
+// keep full relative precision near the singular point eta = 1, xi = 0.
+__device__ __forceinline__ void acc6(double del, double eta_c, double em1, double dp, double c, double s, double w,
                                      double* I, double* A)
 {
-    const double d = eta - c;
+    const double vc = c > 0.0 ? s * s / (1.0 + c) : 1.0 - c;  // 1 - cos xi
+    const double e1 = em1 + del;                               // eta - 1
+    const double eta = eta_c + del;
+    const double d = e1 + vc;                                  // eta - cos xi
+    const double om = vc - e1 * c;                             // 1 - eta cos xi
     const double F2 = d * d + s * s;
     const double iF = 1.0 / sqrt(F2);
     const double iF3 = iF * iF * iF;
-    const double ir0 = -eta * (1.0 - eta * c) * iF3;
+    const double ir0 = -eta * om * iF3;
     const double ip0 = eta * eta * s * iF3;
-    const double dr = eta - eta_c, dp = xi + qd;
-    const double v[6] = {ir0, ir0 * dr, ir0 * dp, ip0, ip0 * dr, ip0 * dp};
+    const double v[6] = {ir0, ir0 * del, ir0 * dp, ip0, ip0 * del, ip0 * dp};
 #pragma unroll
     for (int c6 = 0; c6 < 6; c6++) {
         I[c6] += w * v[c6];
@@ -126,8 +135,8 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
-#define SG_STACK 40
-#define SG_MAXRECT 4000
+#define SG_STACK 64
+#define SG_MAXRECT 20000
 
 __global__ void __launch_bounds__(128) k_cells(int nu, int nphi, double du, double rtol, double* __restrict__ cells,
                                                int* __restrict__ flag)
@@ -144,12 +153,16 @@ __global__ void __launch_bounds__(128) k_cells(int nu, int nphi, double du, doub
         const int k = (int)(off / nq) - nu;
         const int q = (int)(off % nq);
         if (k == 0 && q == 0) continue;  // self cell: k_self_cell
-        const double eta_c = exp(-du * k);
-        const double qd = q * dphi;
+        const double eta_c = exp(-du * k), em1 = expm1(-du * k);
+        const double hw = eta_c * (beta - 1.0) / (beta + 1.0);  // half width in eta
+        // centre azimuth xi_c = -q dphi = -2 pi q / N_phi, its sine and cosine
+        // exact at the quarter points
+        double sc, cc;
+        sincospi(-2.0 * q / nphi, &sc, &cc);
         double res[6] = {0, 0, 0, 0, 0, 0};
         int sp = 0, nrect = 0, bad = 0;
-        stack[0] = make_double4(eta_c * 2.0 / (beta + 1.0), eta_c * 2.0 * beta / (beta + 1.0), (-q - 0.5) * dphi,
-                                (-q + 0.5) * dphi);
+        // rectangles in (eta - eta_c, xi - xi_c)
+        stack[0] = make_double4(-hw, hw, -0.5 * dphi, 0.5 * dphi);
         sp = 1;
         while (sp > 0) {
             __syncwarp();
@@ -161,17 +174,19 @@ __global__ void __launch_bounds__(128) k_cells(int nu, int nphi, double du, doub
             double I8[6] = {0, 0, 0, 0, 0, 0}, I12[6] = {0, 0, 0, 0, 0, 0}, A12[6] = {0, 0, 0, 0, 0, 0};
             for (int p = lane; p < 64; p += 32) {
                 const int a = p >> 3, b = p & 7;
-                const double eta = me + he * c_x8[a], xi = mx + hx * c_x8[b];
-                double s, c;
-                sincos(xi, &s, &c);
-                acc6(eta, xi, c, s, eta_c, qd, he * hx * c_w8[a] * c_w8[b], I8, nullptr);
+                const double del = me + he * c_x8[a], t = mx + hx * c_x8[b];
+                double st, ct;
+                sincos(t, &st, &ct);
+                acc6(del, eta_c, em1, t, ct * cc - st * sc, st * cc + ct * sc, he * hx * c_w8[a] * c_w8[b], I8,
+                     nullptr);
             }
             for (int p = lane; p < 144; p += 32) {
                 const int a = p / 12, b = p % 12;
-                const double eta = me + he * c_x12[a], xi = mx + hx * c_x12[b];
-                double s, c;
-                sincos(xi, &s, &c);
-                acc6(eta, xi, c, s, eta_c, qd, he * hx * c_w12[a] * c_w12[b], I12, A12);
+                const double del = me + he * c_x12[a], t = mx + hx * c_x12[b];
+                double st, ct;
+                sincos(t, &st, &ct);
+                acc6(del, eta_c, em1, t, ct * cc - st * sc, st * cc + ct * sc, he * hx * c_w12[a] * c_w12[b], I12,
+                     A12);
             }
             bool ok = true;
 #pragma unroll
@@ -179,7 +194,8 @@ __global__ void __launch_bounds__(128) k_cells(int nu, int nphi, double du, doub
                 I8[c6] = warp_sum(I8[c6]);
                 I12[c6] = warp_sum(I12[c6]);
                 A12[c6] = warp_sum(A12[c6]);
-                if (fabs(I12[c6] - I8[c6]) > rtol * A12[c6]) ok = false;
+                // tolerance plus the rounding level of a 144-term sum
+                if (fabs(I12[c6] - I8[c6]) > (rtol + 64.0 * 2.220446049250313e-16) * A12[c6]) ok = false;
             }
             if (!ok && (sp + 4 > SG_STACK || nrect >= SG_MAXRECT)) {
                 ok = true;
@@ -189,14 +205,32 @@ __global__ void __launch_bounds__(128) k_cells(int nu, int nphi, double du, doub
 #pragma unroll
                 for (int c6 = 0; c6 < 6; c6++) res[c6] += I12[c6];
             } else {
+                // split the side that is longer in physical length (the
+                // azimuthal side measures (xi extent) x eta); both when the
+                // rectangle is roughly square
+                const double le = R.y - R.x, lx = (R.w - R.z) * (eta_c + me);
                 __syncwarp();
-                if (lane == 0) {
-                    stack[sp + 0] = make_double4(R.x, me, R.z, mx);
-                    stack[sp + 1] = make_double4(me, R.y, R.z, mx);
-                    stack[sp + 2] = make_double4(R.x, me, mx, R.w);
-                    stack[sp + 3] = make_double4(me, R.y, mx, R.w);
+                if (le > 2.0 * lx) {
+                    if (lane == 0) {
+                        stack[sp + 0] = make_double4(R.x, me, R.z, R.w);
+                        stack[sp + 1] = make_double4(me, R.y, R.z, R.w);
+                    }
+                    sp += 2;
+                } else if (lx > 2.0 * le) {
+                    if (lane == 0) {
+                        stack[sp + 0] = make_double4(R.x, R.y, R.z, mx);
+                        stack[sp + 1] = make_double4(R.x, R.y, mx, R.w);
+                    }
+                    sp += 2;
+                } else {
+                    if (lane == 0) {
+                        stack[sp + 0] = make_double4(R.x, me, R.z, mx);
+                        stack[sp + 1] = make_double4(me, R.y, R.z, mx);
+                        stack[sp + 2] = make_double4(R.x, me, mx, R.w);
+                        stack[sp + 3] = make_double4(me, R.y, mx, R.w);
+                    }
+                    sp += 4;
                 }
-                sp += 4;
             }
         }
         if (lane == 0) {
@@ -233,31 +267,36 @@ __device__ __forceinline__ void self3(double x, double y, double* v)
     v[2] = ip0 * y;
 }
 
-template <int NG>
-__device__ void self_rule(double h, double d, double* out)
+// Composite 16-point Gauss-Legendre over np x np panels of (angle, radius)
+// in each triangle pair; returns K^{r,0}, K^{r,r}, K^{phi,phi} of the self
+// cell (block-wide reduction, result valid in every thread).
+__device__ void self_rule(double h, double d, int np, double* out)
 {
-    const double* gx = NG == 32 ? c_x32 : c_x24;
-    const double* gw = NG == 32 ? c_w32 : c_w24;
     const double thc = atan2(d, h);
     double acc[3] = {0, 0, 0};
-    for (int p = threadIdx.x; p < 2 * NG * NG; p += blockDim.x) {
-        const int reg = p / (NG * NG), a = (p / NG) % NG, b = p % NG;
-        double th, thw, rmax;
-        if (reg == 0) {  // right (and, by reflection, left) triangle
-            th = thc * gx[a];
-            thw = thc * gw[a];
-            rmax = h / cos(th);
-        } else {  // top (and bottom) triangle
-            const double hm = 0.5 * (M_PI - 2.0 * thc);
-            th = 0.5 * M_PI + hm * gx[a];
-            thw = hm * gw[a];
-            rmax = d / sin(th);
+    const int per_reg = np * np * 256;  // panels x 16 x 16 nodes
+    for (int p = threadIdx.x; p < 2 * per_reg; p += blockDim.x) {
+        const int reg = p / per_reg, rem = p % per_reg;
+        const int pan = rem >> 8, node = rem & 255;
+        const int pt = pan / np, pr = pan % np, a = node >> 4, b = node & 15;
+        // angle panel pt of the region, radius panel pr
+        double t0, t1;
+        if (reg == 0) {
+            t0 = -thc + 2.0 * thc * pt / np;
+            t1 = -thc + 2.0 * thc * (pt + 1) / np;
+        } else {
+            t0 = thc + (M_PI - 2.0 * thc) * pt / np;
+            t1 = thc + (M_PI - 2.0 * thc) * (pt + 1) / np;
         }
-        const double tau = 0.5 * (1.0 + gx[b]);
-        const double rho = rmax * tau;
-        const double w = thw * 0.5 * gw[b] * rmax * rmax * tau;
+        const double th = 0.5 * (t0 + t1) + 0.5 * (t1 - t0) * c_x16[a];
+        const double thw = 0.5 * (t1 - t0) * c_w16[a];
         double ct, st;
         sincos(th, &st, &ct);
+        const double rmax = reg == 0 ? h / ct : d / st;
+        const double u0 = (double)pr / np, u1 = (double)(pr + 1) / np;
+        const double tau = 0.5 * (u0 + u1) + 0.5 * (u1 - u0) * c_x16[b];
+        const double rho = rmax * tau;
+        const double w = thw * 0.5 * (u1 - u0) * c_w16[b] * rmax * rmax * tau;
         double v1[3], v2[3];
         self3(rho * ct, rho * st, v1);
         self3(-rho * ct, -rho * st, v2);
@@ -271,12 +310,10 @@ __device__ void self_rule(double h, double d, double* out)
         if ((threadIdx.x & 31) == 0) red[c3][threadIdx.x >> 5] = v;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int c3 = 0; c3 < 3; c3++) {
-            double s = 0;
-            for (int w8 = 0; w8 < (int)(blockDim.x >> 5); w8++) s += red[c3][w8];
-            out[c3] = s;
-        }
+    for (int c3 = 0; c3 < 3; c3++) {
+        double s = 0;
+        for (int w8 = 0; w8 < (int)(blockDim.x >> 5); w8++) s += red[c3][w8];
+        out[c3] = s;
     }
     __syncthreads();
 }
@@ -286,20 +323,27 @@ __global__ void __launch_bounds__(256) k_self_cell(int nu, int nphi, double du, 
 {
     const double beta = exp(du), dphi = 2.0 * M_PI / nphi;
     const double h = (beta - 1.0) / (beta + 1.0), d = 0.5 * dphi;
-    __shared__ double r32[3], r24[3];
-    self_rule<32>(h, d, r32);
-    self_rule<24>(h, d, r24);
+    double prev[3], cur[3];
+    self_rule(h, d, 1, prev);
+    bool conv = false;
+    for (int np = 2; np <= 16; np *= 2) {
+        self_rule(h, d, np, cur);
+        conv = true;
+        for (int c3 = 0; c3 < 3; c3++)
+            if (fabs(cur[c3] - prev[c3]) > fmax(rtol, 1e-14) * fabs(cur[c3])) conv = false;
+        for (int c3 = 0; c3 < 3; c3++) prev[c3] = cur[c3];
+        if (conv) break;
+    }
     if (threadIdx.x == 0) {
         const long per = (long)(2 * nu + 1) * nphi;
         const long at = (long)nu * nphi;  // k = 0, q = 0
-        cells[0 * per + at] = r32[0];
-        cells[1 * per + at] = r32[1];
+        cells[0 * per + at] = cur[0];
+        cells[1 * per + at] = cur[1];
         cells[2 * per + at] = 0.0;
         cells[3 * per + at] = 0.0;
         cells[4 * per + at] = 0.0;
-        cells[5 * per + at] = r32[2];
-        for (int c3 = 0; c3 < 3; c3++)
-            if (fabs(r32[c3] - r24[c3]) > fmax(rtol, 1e-13) * fabs(r32[c3])) atomicOr(flag, 2);
+        cells[5 * per + at] = cur[2];
+        if (!conv) atomicOr(flag, 2);
     }
 }
 

@@ -109,7 +109,7 @@ class Plan:
         self.handle = h
 
     # -- one-time preparation ------------------------------------------------
-    def build(self, rtol: float = 1e-14, weight_p: int = 2, stream=None):
+    def build(self, rtol: float = 1e-14, weight_p: int = 0, stream=None):
         opts = BuildOpts(rtol, weight_p)
         _check(lib().sg_kernels_build(self.handle, ctypes.byref(opts), _stream(stream)), "sg_kernels_build")
         return self

@@ -48,11 +48,12 @@ def make_plan(nu, nphi, r_in, r_out, dtype, p=2):
     return Plan(nu, nphi, u_min, du, 1.0, dtype).build(weight_p=p), u_min, du
 
 
-def cell_scale(cells):
-    """Per-cell scale |K^{r,0}| + |K^{phi,0}| plus the row's slope-kernel scale."""
+def cell_scale(cells, c):
+    """Scale of component c of each cell: its own magnitude plus
+    |K^{r,0}| + |K^{phi,0}| of the cell and 1e-3 of the row's largest."""
     base = np.abs(cells[0]) + np.abs(cells[3])
     row = base.max(axis=1, keepdims=True)
-    return base + 1e-3 * row
+    return np.abs(cells[c]) + base + 1e-3 * row
 
 
 @pytest.mark.parametrize("nu,nphi,r_in,r_out", [(4, 4, 0.5, 2.0), (8, 16, 0.1, 10.0), (16, 8, 0.1, 10.0),
@@ -62,10 +63,9 @@ def test_kernel_builder_matches_oracle(torch_cuda, oracle_mod, nu, nphi, r_in, r
     plan, u_min, du = make_plan(nu, nphi, r_in, r_out, "float64")
     got = plan.cells()
     ref, Kr, Kp = oracle_kernels(oracle_mod, nu, nphi, du)
-    s = cell_scale(ref)
     for c in range(6):
-        err = np.abs(got[c] - ref[c]) / s
-        assert err.max() < 1e-12, (c, err.max(), np.unravel_index(err.argmax(), err.shape))
+        err = np.abs(got[c] - ref[c]) / cell_scale(ref, c)
+        assert err.max() < 2e-12, (c, err.max(), np.unravel_index(err.argmax(), err.shape))
     gKr, gKp = plan.kernels()
     sk = np.abs(Kr).max() + np.abs(Kp).max()
     assert np.abs(gKr - Kr).max() < 1e-12 * sk
