@@ -1,0 +1,344 @@
+"""Benchmark: grid cells/s of the thin-disk forces F_r + F_phi on one GB300.
+
+Workload: the 2048 x 4096 log-polar disk (r in [0.01, 100]; sigma =
+exp(0.5 g) e^{-r/3}, g a seeded unit-variance k^-3 Gaussian field), FP32, with
+kernel spectra built once in FP64 before timing.  A timed step is one forward
+evaluation (sg_forces: rows -> columns -> inverse rows) of the whole grid;
+the adjoint (sg_forces_backward) and the FP64 path are timed the same way and
+reported beside it.  The L2 (126 MB) is flushed by a 256 MB write before
+every timed step, outside the step's event pair.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank solves its own disk (replicas: the path
+does not shard); the timed region is bracketed by barriers and the max over
+ranks is used.  --impl reference times the FP64 CPU oracle (direct O(N^2)
+sum over oracle-built kernels) on the host cores, on bounded samples of
+target cells, rank 0 only.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "grid cells/s of F_r+F_phi (FP32 vs FP64, 1 GB300) at stated rel-L2; % HBM roofline"
+WORKLOAD = "lognormal-grf-2048x4096"
+NU, NPHI, R_IN, R_OUT, SEED = 2048, 4096, 0.01, 100.0, 1509
+# algorithmic bytes per cell of the three forward passes in FP32 (reads and
+# writes of the minimal data each pass must move, symmetry-reduced spectra)
+BYTES_PER_CELL = {"rows": 8.0, "cols": 20.0, "inv_rows": 16.0}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.rows = []
+        if self.proc is None:
+            return
+        time.sleep(0.2)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        for line in out.splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def summary(self):
+        rows = getattr(self, "rows", [])
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_baseline(n_targets: int = 2048, seed: int = 0):
+    """FP64 oracle (direct sum over oracle-built kernels) on the host cores,
+    on n_targets sampled cells of the same 2048 x 4096 workload."""
+    import numpy as np
+
+    import oracle
+    import workloads
+
+    u_min, du = workloads.grid_params(NU, R_IN, R_OUT)
+    r, phi = workloads.centres(NU, NPHI, u_min, du)
+    sigma = workloads.lognormal_disk(r, phi, SEED)
+    t0 = time.time()
+    Kr, Kp = oracle.kernels(NU, NPHI, du)
+    t_table = time.time() - t0
+    tg = np.random.default_rng(seed).choice(NU * NPHI, n_targets, replace=False)
+    t0 = time.time()
+    oracle.direct_sum(sigma, Kr, Kp, targets=tg)
+    dt = time.time() - t0
+    return {"value": n_targets / dt, "unit": "cells/s", "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": f"{n_targets} target cells of the {NU}x{NPHI} grid, FP64 direct sum over all "
+                      f"{NU * NPHI} source cells; oracle kernel table built once beforehand ({t_table:.1f} s)"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import numpy as np
+
+    import oracle
+    import workloads
+
+    u_min, du = workloads.grid_params(NU, R_IN, R_OUT)
+    r, phi = workloads.centres(NU, NPHI, u_min, du)
+    sigma = workloads.lognormal_disk(r, phi, SEED)
+    Kr, Kp = oracle.kernels(NU, NPHI, du)
+    per_step = max(8, 4096 // max(args.steps, 1))
+    rng = np.random.default_rng(0)
+    for _ in range(args.warmup):
+        oracle.direct_sum(sigma, Kr, Kp, targets=rng.choice(NU * NPHI, per_step, replace=False))
+    t0 = time.time()
+    for _ in range(args.steps):
+        oracle.direct_sum(sigma, Kr, Kp, targets=rng.choice(NU * NPHI, per_step, replace=False))
+    dt = time.time() - t0
+    value = per_step * args.steps / dt
+    line = {"metric": METRIC, "impl": "reference", "value": value, "unit": "cells/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nu": NU, "nphi": NPHI, "r_in": R_IN, "r_out": R_OUT, "seed": SEED},
+            "cpu_baseline": {"value": value, "unit": "cells/s", "cores": oracle.max_threads(), "kind": "oracle",
+                             "sample": f"{per_step} sampled target cells per step, FP64 direct sum"},
+            "e2e": {"value": value, "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+
+    import workloads
+    from paper_1509_01450_gb300 import Plan, build as cuda_build
+
+    cuda_build.build()
+    u_min, du = workloads.grid_params(NU, R_IN, R_OUT)
+    r, phi = workloads.centres(NU, NPHI, u_min, du)
+    sigma_np = workloads.lognormal_disk(r, phi, SEED + rank)
+    t0 = time.time()
+    plan = Plan(NU, NPHI, u_min, du, 1.0, "float32").build()
+    torch.cuda.synchronize()
+    build_s = time.time() - t0
+    sigma = torch.tensor(sigma_np, dtype=torch.float32, device=dev)
+    Fr = torch.empty_like(sigma)
+    Fp = torch.empty_like(sigma)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):
+        plan.forces(sigma, Fr, Fp)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K forward steps, each bracketed by its own events --
+    stream = torch.cuda.current_stream()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    with ClockSampler(dev.index) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        w0 = time.time()
+        for k in range(args.steps):
+            flush.zero_()
+            starts[k].record(stream)
+            plan.forces(sigma, Fr, Fp)
+            ends[k].record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        wall = time.time() - w0
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    ms = sum(step_ms) / len(step_ms)
+    if ws > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    cells = NU * NPHI
+    value = ws * cells / (ms * 1e-3)
+
+    # ---- per-pass durations (roofline of the dominant kernel) -------------
+    passes = []
+    for _ in range(max(20, min(args.steps, 200))):
+        flush.zero_()
+        passes.append(plan.forces_timed(sigma, Fr, Fp))
+    p_rows = statistics.mean(p[0] for p in passes)
+    p_cols = statistics.mean(p[1] for p in passes)
+    p_inv = statistics.mean(p[2] for p in passes)
+    peaks, peak_kind = measured_peaks()
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    dom_name, dom_ms = max((("cols", p_cols), ("rows", p_rows), ("inv_rows", p_inv)), key=lambda x: x[1])
+    achieved = BYTES_PER_CELL[dom_name] * cells / (dom_ms * 1e-3) / 1e9
+    total_bytes = sum(BYTES_PER_CELL.values()) * cells
+
+    # ---- adjoint and FP64, same protocol ----------------------------------
+    def timed(fn, n):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+        for s, e in ev:
+            flush.zero_()
+            s.record()
+            fn()
+            e.record()
+        torch.cuda.synchronize()
+        return statistics.mean(s.elapsed_time(e) for s, e in ev)
+
+    gr = torch.randn_like(sigma)
+    gp = torch.randn_like(sigma)
+    gs = torch.empty_like(sigma)
+    for _ in range(3):
+        plan.backward(gr, gp, gs)
+    bwd_ms = timed(lambda: plan.backward(gr, gp, gs), max(20, min(args.steps, 200)))
+    plan64 = Plan(NU, min(NPHI, 4096), u_min, du, 1.0, "float64").build()
+    s64 = sigma.double()
+    f64r, f64p = torch.empty_like(s64), torch.empty_like(s64)
+    for _ in range(3):
+        plan64.forces(s64, f64r, f64p)
+    fp64_ms = timed(lambda: plan64.forces(s64, f64r, f64p), 20)
+    # FP32 accuracy against the FP64 GPU path on the same input
+    plan.forces(sigma, Fr, Fp)
+    plan64.forces(s64, f64r, f64p)
+    torch.cuda.synchronize()
+    num = float(((Fr.double() - f64r) ** 2).sum() + ((Fp.double() - f64p) ** 2).sum())
+    den = float((f64r ** 2).sum() + (f64p ** 2).sum())
+    rel_fp32_vs_fp64 = math.sqrt(num / den)
+    del plan64, s64, f64r, f64p
+
+    # ---- end to end through the C ABI with host buffers --------------------
+    sig_h = torch.tensor(sigma_np, dtype=torch.float32).pin_memory()
+    fr_h = torch.empty_like(sig_h).pin_memory()
+    fp_h = torch.empty_like(sig_h).pin_memory()
+    for _ in range(3):
+        plan.forces_host(sig_h, fr_h, fp_h)
+    n_e2e = max(10, min(args.steps, 100))
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(n_e2e):
+        plan.forces_host(sig_h, fr_h, fp_h)
+    e1.record()
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / n_e2e
+    e2e_value = ws * cells / (e2e_ms * 1e-3)
+
+    if rank == 0:
+        clocks = clk.summary()
+        line = {
+            "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nu": NU, "nphi": NPHI, "r_in": R_IN, "r_out": R_OUT, "seed": SEED,
+                       "kernel_weight_p": 0, "l2": "flushed by a 256 MB write before every timed step",
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+            "roofline": {"bound": "hbm", "kernel": f"forward {dom_name} pass", "achieved": achieved, "peak": peak,
+                         "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                         "algorithmic_bytes_per_cell": BYTES_PER_CELL[dom_name]},
+            "path_roofline": {"bytes_per_cell": sum(BYTES_PER_CELL.values()),
+                              "achieved_gbs": total_bytes / (ms * 1e-3) / 1e9,
+                              "frac": total_bytes / (ms * 1e-3) / 1e9 / peak},
+            "pass_ms": {"rows": p_rows, "cols": p_cols, "inv_rows": p_inv},
+            "backward": {"value": ws * cells / (bwd_ms * 1e-3), "unit": "cells/s", "ms_per_step": bwd_ms},
+            "fp64": {"value": ws * cells / (fp64_ms * 1e-3), "unit": "cells/s", "ms_per_step": fp64_ms,
+                     "fp32_speedup": fp64_ms / ms},
+            "accuracy": {"fp32_vs_fp64_gpu_rel_l2": rel_fp32_vs_fp64},
+            "build_s": build_s,
+            "e2e": {"value": e2e_value, "unit": "cells/s", "ms_per_step": e2e_ms,
+                    "h2d_bytes_per_step": cells * 4, "d2h_bytes_per_step": 2 * cells * 4},
+            "gpu_launches": 3 * args.steps,
+            "clocks": clocks,
+            "wall_s_timed_region": wall,
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(args.cpu_targets)
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--cpu-targets", type=int, default=2048)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--size", default=None, help="NUxNPHI override (profiling runs only; not a bench line)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.size:
+        global NU, NPHI, WORKLOAD
+        NU, NPHI = (int(x) for x in args.size.lower().split("x"))
+        WORKLOAD = f"lognormal-grf-{NU}x{NPHI} (profiling size)"
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -120,6 +120,17 @@ sg_status sg_forces_backward(sg_plan* plan, const void* gF_r, const void* gF_phi
  */
 sg_status sg_forces_host(sg_plan* plan, const void* sigma_h, void* F_r_h, void* F_phi_h, cudaStream_t stream);
 
+/*
+ * sg_forces with per-pass timing: records CUDA events (owned by the plan,
+ * created on first use) on stream before the row pass, between the passes
+ * and after the inverse row pass, synchronises the stream and writes the
+ * three pass durations in milliseconds to ms[0..2] (rows, columns, inverse
+ * rows) and the whole span to ms[3].  For measurement; same results as
+ * sg_forces.
+ */
+sg_status sg_forces_timed(sg_plan* plan, const void* sigma, void* F_r, void* F_phi, cudaStream_t stream,
+                          float ms[4]);
+
 /* One disk of a batch: its plan (built) and its device fields. */
 typedef struct {
     sg_plan* plan;

@@ -32,6 +32,8 @@ static sg_status dev_alloc(sg_plan* p, void** ptr, size_t bytes)
 
 static void free_plan(sg_plan* p)
 {
+    if (p->have_ev)
+        for (int i = 0; i < 4; i++) cudaEventDestroy(p->ev[i]);
     void* bufs[] = {p->tw, p->wa, p->wb, p->wc, p->kr, p->kp, p->wpre, p->wpost, p->tw64, p->cells, p->keff,
                     p->h_sigma, p->h_fr, p->h_fp};
     for (void* b : bufs)
@@ -278,6 +280,31 @@ sg_status sg_forces(sg_plan* p, const void* sigma, void* Fr, void* Fp, cudaStrea
     cudaError_t e = p->dtype == SG_F32 ? launch_forward<float>(v, (const float*)sigma, (float*)Fr, (float*)Fp, stream)
                                        : launch_forward<double>(v, (const double*)sigma, (double*)Fr, (double*)Fp, stream);
     return e == cudaSuccess ? SG_OK : SG_ERR_CUDA;
+}
+
+sg_status sg_forces_timed(sg_plan* p, const void* sigma, void* Fr, void* Fp, cudaStream_t stream, float ms[4])
+{
+    sg_status st = check_fields(p, sigma, Fr, Fp);
+    if (st) return st;
+    if (!ms || sigma == Fr || sigma == Fp || Fr == Fp) return SG_ERR_ARG;
+    if (!p->have_ev) {
+        for (int i = 0; i < 4; i++)
+            if (cudaEventCreate(&p->ev[i]) != cudaSuccess) {
+                for (int j = 0; j < i; j++) cudaEventDestroy(p->ev[j]);
+                return SG_ERR_CUDA;
+            }
+        p->have_ev = 1;
+    }
+    PlanView v = view(p);
+    cudaError_t e =
+        p->dtype == SG_F32
+            ? launch_forward<float>(v, (const float*)sigma, (float*)Fr, (float*)Fp, stream, p->ev)
+            : launch_forward<double>(v, (const double*)sigma, (double*)Fr, (double*)Fp, stream, p->ev);
+    if (e != cudaSuccess) return SG_ERR_CUDA;
+    SG_TRY(cudaEventSynchronize(p->ev[3]));
+    for (int i = 0; i < 3; i++) SG_TRY(cudaEventElapsedTime(&ms[i], p->ev[i], p->ev[i + 1]));
+    SG_TRY(cudaEventElapsedTime(&ms[3], p->ev[0], p->ev[3]));
+    return SG_OK;
 }
 
 sg_status sg_forces_backward(sg_plan* p, const void* gr, const void* gp, void* gs, cudaStream_t stream)

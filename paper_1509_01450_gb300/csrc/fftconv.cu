@@ -537,7 +537,7 @@ static cudaError_t set_smem(K kernel, size_t smem)
     } while (0)
 
 template <typename T>
-cudaError_t launch_forward(const PlanView& p, const T* sigma, T* Fr, T* Fp, cudaStream_t st)
+cudaError_t launch_forward(const PlanView& p, const T* sigma, T* Fr, T* Fp, cudaStream_t st, cudaEvent_t* ev)
 {
     typedef typename CX<T>::t V;
     const V* tw = (const V*)p.tw;
@@ -546,6 +546,7 @@ cudaError_t launch_forward(const PlanView& p, const T* sigma, T* Fr, T* Fp, cuda
     V* C = (V*)p.wc;
     const int ln = sg_ilog2(p.nphi), lL = sg_ilog2(2 * p.nu);
     cudaError_t err;
+    if (ev && (err = cudaEventRecord(ev[0], st)) != cudaSuccess) return err;
     {
         Shape s = shape_for<V>(p.nphi, 64);
         const int grid = (p.nu / 2 + s.slots - 1) / s.slots;
@@ -555,6 +556,7 @@ cudaError_t launch_forward(const PlanView& p, const T* sigma, T* Fr, T* Fp, cuda
             k<<<grid, s.threads, s.smem, st>>>(sigma, (const T*)p.wpre, A, p.nu, p.nphi, ln, p.cb, tw);
         });
     }
+    if (ev && (err = cudaEventRecord(ev[1], st)) != cudaSuccess) return err;
     {
         Shape s = shape_for<V>(2 * p.nu, 64);
         const int grid = (p.nphi / 2 + s.slots - 1) / s.slots;
@@ -564,6 +566,7 @@ cudaError_t launch_forward(const PlanView& p, const T* sigma, T* Fr, T* Fp, cuda
             k<<<grid, s.threads, s.smem, st>>>(A, (const V*)p.kr, (const V*)p.kp, B, C, p.nu, p.nphi, lL, p.cb, tw);
         });
     }
+    if (ev && (err = cudaEventRecord(ev[2], st)) != cudaSuccess) return err;
     {
         Shape s = shape_for<V>(p.nphi, 64);
         const int grid = (p.nu + s.slots - 1) / s.slots;
@@ -573,6 +576,7 @@ cudaError_t launch_forward(const PlanView& p, const T* sigma, T* Fr, T* Fp, cuda
             k<<<grid, s.threads, s.smem, st>>>(B, C, (const T*)p.wpost, Fr, Fp, p.nu, p.nphi, ln, tw);
         });
     }
+    if (ev && (err = cudaEventRecord(ev[3], st)) != cudaSuccess) return err;
     return cudaGetLastError();
 }
 
@@ -645,8 +649,9 @@ cudaError_t launch_spectra(const PlanView& p, const double* nsr, const double* n
     return cudaGetLastError();
 }
 
-template cudaError_t launch_forward<float>(const PlanView&, const float*, float*, float*, cudaStream_t);
-template cudaError_t launch_forward<double>(const PlanView&, const double*, double*, double*, cudaStream_t);
+template cudaError_t launch_forward<float>(const PlanView&, const float*, float*, float*, cudaStream_t, cudaEvent_t*);
+template cudaError_t launch_forward<double>(const PlanView&, const double*, double*, double*, cudaStream_t,
+                                              cudaEvent_t*);
 template cudaError_t launch_backward<float>(const PlanView&, const float*, const float*, float*, cudaStream_t);
 template cudaError_t launch_backward<double>(const PlanView&, const double*, const double*, double*, cudaStream_t);
 template cudaError_t launch_spectra<float2>(const PlanView&, const double*, const double*, double2*, float2*,

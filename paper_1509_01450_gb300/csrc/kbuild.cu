@@ -25,11 +25,12 @@
 // xi = 0 where the integrand of K^{r,0} behaves like x / rho^3 (x = eta - 1):
 // integrable only as a principal value.  The cell is symmetric under
 // (x, xi) -> (-x, -xi), so it is integrated in polar coordinates about the
-// singular point over one triangle of each opposite pair (right/left: rays
-// to x = +-h; top/bottom: rays to xi = +-dphi/2) with f(p) + f(-p): the
-// odd 1/rho^2 part cancels and rho f is smooth, so composite Gauss-Legendre
-// in (angle, radius) converges fast; the panels are doubled until two
-// levels agree.  K^{r,phi}, K^{phi,0}, K^{phi,r} vanish on
+// singular point with the pair sum f(p) + f(-p) written so that the odd
+// 1/rho^2 part cancels algebraically: over the square of side 2 min(h, d)
+// about the point (one triangle of each opposite pair, composite
+// Gauss-Legendre in angle and radius, where rho f is smooth) and over the
+// two strips beyond it (geometric panels along the long side).  A coarse
+// and a fine rule must agree.  K^{r,phi}, K^{phi,0}, K^{phi,r} vanish on
 // the self cell by symmetry (Sec. 3.2.2 and App. A).
 //
 // k_fold: the slope terms of Eq. 28-29 / A9-A10 with central differences
@@ -154,7 +155,7 @@ __global__ void __launch_bounds__(128) k_cells(int nu, int nphi, double du, doub
         const int q = (int)(off % nq);
         if (k == 0 && q == 0) continue;  // self cell: k_self_cell
         const double eta_c = exp(-du * k), em1 = expm1(-du * k);
-        const double hw = eta_c * (beta - 1.0) / (beta + 1.0);  // half width in eta
+        const double hw = eta_c * tanh(0.5 * du);  // half width in eta, (beta - 1)/(beta + 1) exactly
         // centre azimuth xi_c = -q dphi = -2 pi q / N_phi, its sine and cosine
         // exact at the quarter points
         double sc, cc;
@@ -247,62 +248,34 @@ __global__ void __launch_bounds__(128) k_cells(int nu, int nphi, double du, doub
     }
 }
 
-// the three self-cell integrands at x = eta - 1, y = xi (accurate near 0)
-__device__ __forceinline__ void self3(double x, double y, double* v)
+// The self-cell integrands of K^{r,0}, K^{r,r}, K^{phi,phi} summed over the
+// point pair p = (x, y) and -p (x = eta - 1, y = xi), written so that the
+// odd 1/rho^2 parts cancel algebraically rather than in rounding.  With
+// vc = 1 - cos y, F_+-^2 = (x +- vc)^2 + sin^2 y, A = (F_+^2 + F_-^2)/2,
+// B = 2 x vc, N_+- = (1 +- x)(vc -+ x cos y):
+//   f(p) + f(-p) = -2 (Ns Gs + Nd Gd),  f(p) - f(-p) = -2 (Ns Gd + Nd Gs),
+// Ns = vc - x^2 cos y, Nd = -x (1 - 2 vc), Gs = (F_+^-3 + F_-^-3) / 2 and
+// Gd = (F_+^-3 - F_-^-3) / 2 = -B (3 A^2 + B^2) / ((F_+^3 + F_-^3) F_+^3 F_-^3).
+__device__ __forceinline__ void self_pair(double x, double y, double* v)
 {
-    double s, c;
-    sincos(y, &s, &c);
-    const double sh = sin(0.5 * y);
-    const double vc = 2.0 * sh * sh;  // 1 - cos y
-    const double eta = 1.0 + x;
-    const double d = x + vc;          // eta - cos y
-    const double F2 = d * d + s * s;
-    const double iF = 1.0 / sqrt(F2);
-    const double iF3 = iF * iF * iF;
-    const double om = vc - x * c;     // 1 - eta cos y
-    const double ir0 = -eta * om * iF3;
-    const double ip0 = eta * eta * s * iF3;
-    v[0] = ir0;
-    v[1] = ir0 * x;
-    v[2] = ip0 * y;
+    const double s = sin(y), sh = sin(0.5 * y);
+    const double vc = 2.0 * sh * sh;
+    const double c = 1.0 - vc;
+    const double P = (x + vc) * (x + vc) + s * s;
+    const double M = (x - vc) * (x - vc) + s * s;
+    const double Fp3 = P * sqrt(P), Fm3 = M * sqrt(M);
+    const double A = 0.5 * (P + M), B = 2.0 * x * vc;
+    const double Gs = 0.5 * (1.0 / Fp3 + 1.0 / Fm3);
+    const double Gd = -B * (3.0 * A * A + B * B) / ((Fp3 + Fm3) * Fp3 * Fm3);
+    const double Ns = vc - x * x * c, Nd = -x * (1.0 - 2.0 * vc);
+    v[0] = -2.0 * (Ns * Gs + Nd * Gd);                                   // K^{r,0}
+    v[1] = x * (-2.0 * (Ns * Gd + Nd * Gs));                             // K^{r,r}: x (f(p) - f(-p))
+    v[2] = s * y * ((1.0 + x) * (1.0 + x) / Fp3 + (1.0 - x) * (1.0 - x) / Fm3);  // K^{phi,phi}
 }
 
-// Composite 16-point Gauss-Legendre over np x np panels of (angle, radius)
-// in each triangle pair; returns K^{r,0}, K^{r,r}, K^{phi,phi} of the self
-// cell (block-wide reduction, result valid in every thread).
-__device__ void self_rule(double h, double d, int np, double* out)
+// block-wide sum of three doubles; the result is valid in every thread
+__device__ void block_sum3(double* acc, double* out)
 {
-    const double thc = atan2(d, h);
-    double acc[3] = {0, 0, 0};
-    const int per_reg = np * np * 256;  // panels x 16 x 16 nodes
-    for (int p = threadIdx.x; p < 2 * per_reg; p += blockDim.x) {
-        const int reg = p / per_reg, rem = p % per_reg;
-        const int pan = rem >> 8, node = rem & 255;
-        const int pt = pan / np, pr = pan % np, a = node >> 4, b = node & 15;
-        // angle panel pt of the region, radius panel pr
-        double t0, t1;
-        if (reg == 0) {
-            t0 = -thc + 2.0 * thc * pt / np;
-            t1 = -thc + 2.0 * thc * (pt + 1) / np;
-        } else {
-            t0 = thc + (M_PI - 2.0 * thc) * pt / np;
-            t1 = thc + (M_PI - 2.0 * thc) * (pt + 1) / np;
-        }
-        const double th = 0.5 * (t0 + t1) + 0.5 * (t1 - t0) * c_x16[a];
-        const double thw = 0.5 * (t1 - t0) * c_w16[a];
-        double ct, st;
-        sincos(th, &st, &ct);
-        const double rmax = reg == 0 ? h / ct : d / st;
-        const double u0 = (double)pr / np, u1 = (double)(pr + 1) / np;
-        const double tau = 0.5 * (u0 + u1) + 0.5 * (u1 - u0) * c_x16[b];
-        const double rho = rmax * tau;
-        const double w = thw * 0.5 * (u1 - u0) * c_w16[b] * rmax * rmax * tau;
-        double v1[3], v2[3];
-        self3(rho * ct, rho * st, v1);
-        self3(-rho * ct, -rho * st, v2);
-#pragma unroll
-        for (int c3 = 0; c3 < 3; c3++) acc[c3] += w * (v1[c3] + v2[c3]);
-    }
     __shared__ double red[3][32];
 #pragma unroll
     for (int c3 = 0; c3 < 3; c3++) {
@@ -311,38 +284,111 @@ __device__ void self_rule(double h, double d, int np, double* out)
     }
     __syncthreads();
     for (int c3 = 0; c3 < 3; c3++) {
-        double s = 0;
-        for (int w8 = 0; w8 < (int)(blockDim.x >> 5); w8++) s += red[c3][w8];
-        out[c3] = s;
+        double t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += red[c3][w];
+        out[c3] = t;
     }
     __syncthreads();
+}
+
+// Square [-m, m]^2 about the singular point, in polar coordinates: one
+// triangle of each opposite pair (rays to x = m for |theta| < pi/4, to
+// y = m for pi/4 < theta < 3 pi/4), np x np composite 16-point panels in
+// (angle, radius), integrand self_pair.
+__device__ void self_square(double m, int np, double* out)
+{
+    const double thc = 0.25 * M_PI;
+    double acc[3] = {0, 0, 0};
+    const int per_reg = np * np * 256;
+    for (int p = threadIdx.x; p < 2 * per_reg; p += blockDim.x) {
+        const int reg = p / per_reg, rem = p % per_reg;
+        const int pan = rem >> 8, node = rem & 255;
+        const int pt = pan / np, pr = pan % np, a = node >> 4, b = node & 15;
+        const double t0 = (reg == 0 ? -thc : thc) + 2.0 * thc * pt / np;
+        const double t1 = (reg == 0 ? -thc : thc) + 2.0 * thc * (pt + 1) / np;
+        const double th = 0.5 * (t0 + t1) + 0.5 * (t1 - t0) * c_x16[a];
+        const double thw = 0.5 * (t1 - t0) * c_w16[a];
+        double ct, st;
+        sincos(th, &st, &ct);
+        const double rmax = reg == 0 ? m / ct : m / st;
+        const double u0 = (double)pr / np, u1 = (double)(pr + 1) / np;
+        const double tau = 0.5 * (u0 + u1) + 0.5 * (u1 - u0) * c_x16[b];
+        const double rho = rmax * tau;
+        const double w = thw * 0.5 * (u1 - u0) * c_w16[b] * rmax * rmax * tau;
+        double v[3];
+        self_pair(rho * ct, rho * st, v);
+#pragma unroll
+        for (int c3 = 0; c3 < 3; c3++) acc[c3] += w * v[c3];
+    }
+    block_sum3(acc, out);
+}
+
+// Strip at distance >= m from the singular point: the long coordinate runs
+// over [m, L] in geometric panels (ratio), the short one over [-w, w] in
+// nshort panels; radial = 1 means the long coordinate is x = eta - 1.
+// (Its point reflection is the opposite strip, which self_pair includes.)
+__device__ void self_strip(double m, double L, double w, double ratio, int nshort, int radial, double* out)
+{
+    double acc[3] = {0, 0, 0};
+    double a = m;
+    while (a < L) {  // uniform across the block: same arithmetic in every thread
+        double b = fmin(a * ratio, L);
+        if (L - b < 0.25 * (b - a)) b = L;
+        for (int p = threadIdx.x; p < nshort * 256; p += blockDim.x) {
+            const int j = p >> 8, node = p & 255, ia = node >> 4, ib = node & 15;
+            const double s0 = -w + 2.0 * w * j / nshort, s1 = -w + 2.0 * w * (j + 1) / nshort;
+            const double l = 0.5 * (a + b) + 0.5 * (b - a) * c_x16[ia];
+            const double sh = 0.5 * (s0 + s1) + 0.5 * (s1 - s0) * c_x16[ib];
+            const double wt = 0.5 * (b - a) * c_w16[ia] * 0.5 * (s1 - s0) * c_w16[ib];
+            double v[3];
+            if (radial)
+                self_pair(l, sh, v);
+            else
+                self_pair(sh, l, v);
+#pragma unroll
+            for (int c3 = 0; c3 < 3; c3++) acc[c3] += wt * v[c3];
+        }
+        a = b;
+    }
+    block_sum3(acc, out);
+}
+
+// The self cell [-h, h] x [-d, d] (x = eta - 1, y = xi) as the square of
+// side 2 min(h, d) about the singular point plus the two strips beyond it,
+// at a coarse and a fine resolution; the fine value is kept and the two
+// must agree.
+__device__ void self_cell_rule(double h, double d, int fine, double* out)
+{
+    const double m = fmin(h, d);
+    double sq[3], st[3] = {0, 0, 0};
+    self_square(m, fine ? 8 : 4, sq);
+    const double ratio = fine ? 1.4142135623730951 : 2.0;
+    const int ns = fine ? 8 : 4;
+    if (h > m) self_strip(m, h, d, ratio, ns, 1, st);
+    if (d > m) self_strip(m, d, h, ratio, ns, 0, st);
+    for (int c3 = 0; c3 < 3; c3++) out[c3] = sq[c3] + st[c3];
 }
 
 __global__ void __launch_bounds__(256) k_self_cell(int nu, int nphi, double du, double rtol,
                                                    double* __restrict__ cells, int* __restrict__ flag)
 {
-    const double beta = exp(du), dphi = 2.0 * M_PI / nphi;
-    const double h = (beta - 1.0) / (beta + 1.0), d = 0.5 * dphi;
-    double prev[3], cur[3];
-    self_rule(h, d, 1, prev);
-    bool conv = false;
-    for (int np = 2; np <= 16; np *= 2) {
-        self_rule(h, d, np, cur);
-        conv = true;
-        for (int c3 = 0; c3 < 3; c3++)
-            if (fabs(cur[c3] - prev[c3]) > fmax(rtol, 1e-14) * fabs(cur[c3])) conv = false;
-        for (int c3 = 0; c3 < 3; c3++) prev[c3] = cur[c3];
-        if (conv) break;
-    }
+    const double dphi = 2.0 * M_PI / nphi;
+    const double h = tanh(0.5 * du), d = 0.5 * dphi;  // (beta - 1)/(beta + 1) without cancellation
+    double coarse[3], fine[3];
+    self_cell_rule(h, d, 0, coarse);
+    self_cell_rule(h, d, 1, fine);
     if (threadIdx.x == 0) {
         const long per = (long)(2 * nu + 1) * nphi;
         const long at = (long)nu * nphi;  // k = 0, q = 0
-        cells[0 * per + at] = cur[0];
-        cells[1 * per + at] = cur[1];
+        cells[0 * per + at] = fine[0];
+        cells[1 * per + at] = fine[1];
         cells[2 * per + at] = 0.0;
         cells[3 * per + at] = 0.0;
         cells[4 * per + at] = 0.0;
-        cells[5 * per + at] = cur[2];
+        cells[5 * per + at] = fine[2];
+        bool conv = true;
+        for (int c3 = 0; c3 < 3; c3++)
+            if (fabs(fine[c3] - coarse[c3]) > fmax(rtol, 1e-14) * fabs(fine[c3])) conv = false;
         if (!conv) atomicOr(flag, 2);
     }
 }
@@ -354,7 +400,7 @@ __global__ void k_fold(int nu, int nphi, double du, double G, int p, const doubl
     const long total = (long)L * nphi;
     const long per = (long)(2 * nu + 1) * nphi;
     const long perk = (long)(2 * nu - 1) * nphi;
-    const double beta = exp(du), bb = beta - 1.0 / beta, dphi = 2.0 * M_PI / nphi;
+    const double bb = 2.0 * sinh(du), dphi = 2.0 * M_PI / nphi;  // beta - 1/beta without cancellation
     const double norm = G / ((double)L * nphi);
     for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
         const int kk = (int)(idx / nphi), q = (int)(idx % nphi);

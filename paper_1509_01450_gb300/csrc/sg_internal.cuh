@@ -32,6 +32,8 @@ struct sg_plan {
     void* h_fr;
     void* h_fp;
     size_t bytes;    // device bytes held
+    cudaEvent_t ev[4];  // pass timing (sg_forces_timed), created on first use
+    int have_ev;
 };
 
 namespace sg {
@@ -66,8 +68,10 @@ inline PlanView view(const sg_plan* p)
     return v;
 }
 
+// ev: optional 4 events recorded before P1, after P1, after P2, after P3
 template <typename T>
-cudaError_t launch_forward(const PlanView& p, const T* sigma, T* Fr, T* Fp, cudaStream_t st);
+cudaError_t launch_forward(const PlanView& p, const T* sigma, T* Fr, T* Fp, cudaStream_t st,
+                           cudaEvent_t* ev = nullptr);
 template <typename T>
 cudaError_t launch_backward(const PlanView& p, const T* gr, const T* gp, T* gs, cudaStream_t st);
 template <typename VO>

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libsgdisk.so")
 SG_OK, SG_ERR_ARG, SG_ERR_ALLOC, SG_ERR_CUDA, SG_ERR_UNSUPPORTED, SG_ERR_NOT_BUILT, SG_ERR_TIMEOUT = range(7)
 SG_F32, SG_F64 = 0, 1
 
-EXPORTS = ("sg_plan_create", "sg_kernels_build", "sg_forces", "sg_forces_backward", "sg_forces_host",
+EXPORTS = ("sg_plan_create", "sg_kernels_build", "sg_forces", "sg_forces_backward", "sg_forces_host", "sg_forces_timed",
            "sg_forces_batched", "sg_batch_reserve", "sg_plan_destroy", "sg_status_string", "sg_plan_info",
            "sg_plan_kernels", "sg_plan_cells", "sg_plan_device_bytes")
 
@@ -54,6 +54,7 @@ def lib():
         L.sg_forces.argtypes = [vp, vp, vp, vp, vp]
         L.sg_forces_backward.argtypes = [vp, vp, vp, vp, vp]
         L.sg_forces_host.argtypes = [vp, vp, vp, vp, vp]
+        L.sg_forces_timed.argtypes = [vp, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_float)]
         L.sg_forces_batched.argtypes = [ctypes.POINTER(BatchItem), ip, vp]
         L.sg_batch_reserve.argtypes = [ip]
         L.sg_plan_destroy.argtypes = [vp]
@@ -126,6 +127,15 @@ class Plan:
         self._check_field(sigma)
         _check(lib().sg_forces(self.handle, _ptr(sigma), _ptr(F_r), _ptr(F_phi), _stream(stream)), "sg_forces")
         return F_r, F_phi
+
+    def forces_timed(self, sigma, F_r, F_phi, stream=None):
+        """sg_forces with per-pass CUDA-event timing; returns (rows, cols,
+        inverse rows, span) in ms (synchronises the stream)."""
+        self._check_field(sigma)
+        ms = (ctypes.c_float * 4)()
+        _check(lib().sg_forces_timed(self.handle, _ptr(sigma), _ptr(F_r), _ptr(F_phi), _stream(stream), ms),
+               "sg_forces_timed")
+        return tuple(ms)
 
     def backward(self, gF_r, gF_phi, gsigma=None, stream=None):
         gsigma = self._new() if gsigma is None else gsigma

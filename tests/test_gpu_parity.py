@@ -41,7 +41,7 @@ def torch_cuda():
     return torch
 
 
-def make_plan(nu, nphi, r_in, r_out, dtype, p=2):
+def make_plan(nu, nphi, r_in, r_out, dtype, p=0):
     from paper_1509_01450_gb300 import Plan
 
     u_min, du = workloads.grid_params(nu, r_in, r_out)
@@ -131,8 +131,11 @@ def test_adjoint_dot_identity_fp64(torch_cuda):
     assert abs(lhs - rhs) < 1e-13 * (float(gs.abs().sum() * s.abs().max()))
 
 
-@pytest.mark.parametrize("p", [0, 1, 2])
-def test_weighting_is_neutral(torch_cuda, oracle_mod, p):
+@pytest.mark.parametrize("p,tol", [(0, FP64_TOL), (1, FP64_TOL), (2, 1e-10)])
+def test_weighting_is_neutral(torch_cuda, oracle_mod, p, tol):
+    """sigma e^{pu} with kernels beta^{pk} and result e^{-pu} is algebraically
+    the same map; rounding is amplified by up to beta^{p N_u} (1.6e5 for
+    p = 2 on r in [0.05, 20]), which is why p = 0 is the default."""
     cfg = workloads.KUZMIN_64
     plan, u_min, du = make_plan(cfg.nu, cfg.nphi, cfg.r_in, cfg.r_out, "float64", p=p)
     r, phi = cfg.centres()
@@ -140,7 +143,7 @@ def test_weighting_is_neutral(torch_cuda, oracle_mod, p):
     _, Kr, Kp = oracle_kernels(oracle_mod, cfg.nu, cfg.nphi, du)
     Fr_ref, Fp_ref = oracle_mod.direct_sum(sigma, Kr, Kp)
     Fr, Fp = _forward(torch_cuda, plan, sigma)
-    assert oracle_mod.rel_l2(Fr, Fp, Fr_ref, Fp_ref) < FP64_TOL
+    assert oracle_mod.rel_l2(Fr, Fp, Fr_ref, Fp_ref) < tol
 
 
 def test_batched_equals_single(torch_cuda):
