@@ -174,6 +174,15 @@ sg_status sg_plan_kernels(sg_plan* plan, double* Kr_h, double* Kphi_h, cudaStrea
  */
 sg_status sg_plan_cells(sg_plan* plan, double* cells_h, cudaStream_t stream);
 
+/*
+ * Convergence report of the last sg_kernels_build: report[0] = bit 1 if some
+ * cell integrals stopped at the quadrature budget, bit 2 if the self-cell
+ * rule did not reach its tolerance; report[1] = number of such offsets;
+ * report[2], report[3] = (k, q) of one of them.  All zero after a clean
+ * build.
+ */
+sg_status sg_plan_build_report(const sg_plan* plan, int report[4]);
+
 /* Bytes of device memory the plan holds. */
 size_t sg_plan_device_bytes(const sg_plan* plan);
 

@@ -135,10 +135,14 @@ static void panel_eval(vfun f, const void* ctx, panel_t* p)
     for (int c = 0; c < NV; c++) {
         p->val[c] = v1[c] + v2[c];
         p->av[c] = a1[c] + a2[c];
-        /* a change below the rounding level of the panel sums is noise: once
-           the one-panel rule agrees with the two half panels that closely,
-           the half panels are exact to rounding */
-        double e = fabs(p->val[c] - p->whole[c]) - NOISE * p->av[c];
+        p->err[c] = fabs(p->val[c] - p->whole[c]);
+    }
+    /* a change below the rounding level of the panel sums is noise: once
+       the one-panel rule agrees with the two half panels that closely, the
+       half panels are exact to rounding.  The level is that of the force
+       vector (radial and azimuthal kernel of the same kind together). */
+    for (int c = 0; c < NC; c++) {
+        double e = p->err[c] - NOISE * (p->av[c] + p->av[(c + 3) % NC]);
         p->err[c] = e > 0.0 ? e : 0.0;
     }
 }
@@ -147,9 +151,11 @@ static void panel_eval(vfun f, const void* ctx, panel_t* p)
  * Globally adaptive quadrature of the vector f over the partition
  * bp[0] < bp[1] < ... < bp[nbp-1].  Panels are bisected, worst first, until
  * for each value component c < NC the summed error estimate is at most
- * rtol * S_c + atol, where S_c is the integral of |f_c| (aux == 0) or the
- * integral of the scale component f_{NC+c} (aux == 1; the caller supplies
- * there the integral of |integrand| over the inner variable).  res gets the
+ * rtol * (S_c + S_c') + atol, where c' = (c + 3) mod 6 is the other
+ * component of the same force vector (radial / azimuthal) and S_c is the
+ * integral of |f_c| (aux == 0) or of the scale component f_{NC+c} (aux ==
+ * 1; the caller supplies there the integral of |integrand| over the inner
+ * variable).  res gets the
  * NV integrals, resabs the integrals of |f|.  Returns the number of panels,
  * or a negative number if the panel budget ran out (the result is then the
  * best estimate).
@@ -180,7 +186,10 @@ static int adapt(vfun f, const void* ctx, const double* bp, int nbp, double rtol
         double tol[NC];
         int done = 1;
         for (int c = 0; c < NC; c++) {
-            tol[c] = rtol * (aux ? fabs(V[NC + c]) : A[c]) + atol;
+            /* scale of the force vector: radial and azimuthal kernels of the
+               same kind (components c and c +- 3) together */
+            const int cp = (c + 3) % NC;
+            tol[c] = rtol * (aux ? fabs(V[NC + c]) + fabs(V[NC + cp]) : A[c] + A[cp]) + atol;
             if (E[c] > tol[c]) done = 0;
         }
         if (done) {

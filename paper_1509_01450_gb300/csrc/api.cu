@@ -217,14 +217,14 @@ sg_status sg_kernels_build(sg_plan* p, const sg_build_opts* opts, cudaStream_t s
     double *nsr = nullptr, *nsp = nullptr;
     double2* W = nullptr;
     sg_status ret = SG_OK;
-    if (cudaMalloc(&flag, sizeof(int)) != cudaSuccess || cudaMalloc(&nsr, (size_t)L * nphi * sizeof(double)) != cudaSuccess ||
+    if (cudaMalloc(&flag, 4 * sizeof(int)) != cudaSuccess || cudaMalloc(&nsr, (size_t)L * nphi * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&nsp, (size_t)L * nphi * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&W, (size_t)(nphi / 2 + 1) * L * sizeof(double2)) != cudaSuccess) {
         cudaGetLastError();
         ret = SG_ERR_ALLOC;
         goto done;
     }
-    if (cudaMemsetAsync(flag, 0, sizeof(int), stream) != cudaSuccess) {
+    if (cudaMemsetAsync(flag, 0, 4 * sizeof(int), stream) != cudaSuccess) {
         ret = SG_ERR_CUDA;
         goto done;
     }
@@ -244,14 +244,13 @@ sg_status sg_kernels_build(sg_plan* p, const sg_build_opts* opts, cudaStream_t s
         }
     }
     {
-        int hflag = 0;
-        if (cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+        if (cudaMemcpyAsync(p->report, flag, 4 * sizeof(int), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
             cudaStreamSynchronize(stream) != cudaSuccess) {
             ret = SG_ERR_CUDA;
             goto done;
         }
         p->built = 1;
-        if (hflag) ret = SG_ERR_TIMEOUT;
+        if (p->report[0]) ret = SG_ERR_TIMEOUT;
     }
 done:
     if (flag) cudaFree(flag);
@@ -353,6 +352,13 @@ sg_status sg_forces_batched(const sg_batch_item* items, int n, cudaStream_t stre
         sg_status st = sg_forces(items[b].plan, items[b].sigma, items[b].F_r, items[b].F_phi, stream);
         if (st) return st;
     }
+    return SG_OK;
+}
+
+sg_status sg_plan_build_report(const sg_plan* p, int report[4])
+{
+    if (!p || !report) return SG_ERR_ARG;
+    for (int i = 0; i < 4; i++) report[i] = p->report[i];
     return SG_OK;
 }
 

@@ -16,7 +16,8 @@
 // from the mirror xi -> -xi: K^{r,0}, K^{r,r}, K^{phi,phi} even in q,
 // K^{r,phi}, K^{phi,0}, K^{phi,r} odd).  Each rectangle is integrated by the
 // 8- and 12-point tensor Gauss-Legendre rules; if they differ by more than
-// rtol times the integral of |f| the rectangle is split (a depth-first stack
+// rtol times the integral of |f_r| + |f_phi| of the same kind (the force
+// vector's size) the rectangle is split (a depth-first stack
 // in shared memory): in two across its physically longer side when one side
 // is more than twice the other, else in four.  Otherwise the 12-point value
 // is kept.
@@ -195,8 +196,16 @@ __global__ void __launch_bounds__(128) k_cells(int nu, int nphi, double du, doub
                 I8[c6] = warp_sum(I8[c6]);
                 I12[c6] = warp_sum(I12[c6]);
                 A12[c6] = warp_sum(A12[c6]);
-                // tolerance plus the rounding level of a 144-term sum
-                if (fabs(I12[c6] - I8[c6]) > (rtol + 64.0 * 2.220446049250313e-16) * A12[c6]) ok = false;
+            }
+#pragma unroll
+            for (int c6 = 0; c6 < 6; c6++) {
+                // the radial and azimuthal kernels of each kind form one force
+                // vector: measure both against its size (so a component that
+                // nearly vanishes, on the curve eta cos xi = 1, needs no more
+                // than the vector's precision), plus the rounding level of a
+                // 144-term sum
+                const double scale = A12[c6] + A12[(c6 + 3) % 6];
+                if (fabs(I12[c6] - I8[c6]) > (rtol + 64.0 * 2.220446049250313e-16) * scale) ok = false;
             }
             if (!ok && (sp + 4 > SG_STACK || nrect >= SG_MAXRECT)) {
                 ok = true;
@@ -243,7 +252,12 @@ __global__ void __launch_bounds__(128) k_cells(int nu, int nphi, double du, doub
                 const bool odd = (c6 == 2 || c6 == 3 || c6 == 4);
                 if (qm != q) cells[c6 * per + row + qm] = odd ? -res[c6] : res[c6];
             }
-            if (bad) atomicOr(flag, 1);
+            if (bad) {
+                atomicOr(flag, 1);
+                atomicAdd(flag + 1, 1);
+                atomicExch(flag + 2, k);
+                atomicExch(flag + 3, q);
+            }
         }
     }
 }

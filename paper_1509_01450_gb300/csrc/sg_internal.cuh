@@ -34,6 +34,7 @@ struct sg_plan {
     size_t bytes;    // device bytes held
     cudaEvent_t ev[4];  // pass timing (sg_forces_timed), created on first use
     int have_ev;
+    int report[4];      // last build: flag bits, failed offsets, one failed (k, q)
 };
 
 namespace sg {
