@@ -30,9 +30,10 @@
  *
  *     The integrals are the exact cell integrals (the limit the paper's
  *     N_tpz-trapezoid rule of Eq. 41-43 tends to).  They are computed as
- *     iterated integrals, eta inside and xi outside, each by globally
- *     adaptive Gauss-Legendre quadrature (12 nodes per panel, error taken as
- *     the change when a panel is halved).  For the self cell (k, q) = (0, 0)
+ *     iterated integrals, eta inside and xi outside (as offsets from the
+ *     cell centre, eta - beta^-k and xi + q dphi), each by globally adaptive
+ *     Gauss-Legendre quadrature (12 nodes per panel, error taken as the
+ *     change when a panel is halved).  For the self cell (k, q) = (0, 0)
  *     the point eta = 1, xi = 0 is singular (Sec. 4): the xi range is split
  *     at 0 and the inner eta integral uses the substitution
  *     eta = cos xi + |sin xi| sinh t, which turns the near-singular peak of
@@ -160,11 +161,16 @@ static void panel_eval(vfun f, const void* ctx, panel_t* p)
  * or a negative number if the panel budget ran out (the result is then the
  * best estimate).
  */
-static int adapt(vfun f, const void* ctx, const double* bp, int nbp, double rtol, double atol, int aux,
-                 double res[NV], double resabs[NV])
+static int adapt_n(vfun f, const void* ctx, const double* bp, int nbp, double rtol, double atol, int aux,
+                   int maxpan, double res[NV], double resabs[NV])
 {
-    int cap = nbp + 32, np = 0, status = 0;
-    panel_t* P = (panel_t*)malloc(sizeof(panel_t) * cap);
+    panel_t local[48];
+    int cap = 48, np = 0, status = 0;
+    panel_t* P = local;
+    if (nbp + 32 > cap) {
+        cap = nbp + 32;
+        P = (panel_t*)malloc(sizeof(panel_t) * cap);
+    }
     for (int s = 0; s + 1 < nbp; s++) {
         if (!(bp[s + 1] > bp[s])) continue;
         panel_t* p = &P[np++];
@@ -200,7 +206,7 @@ static int adapt(vfun f, const void* ctx, const double* bp, int nbp, double rtol
             status = np;
             break;
         }
-        if (np + 1 >= MAXPAN) {
+        if (np + 1 >= maxpan) {
             for (int c = 0; c < NV; c++) {
                 res[c] = V[c];
                 resabs[c] = A[c];
@@ -230,7 +236,12 @@ static int adapt(vfun f, const void* ctx, const double* bp, int nbp, double rtol
         }
         if (np + 1 > cap) {
             cap *= 2;
-            P = (panel_t*)realloc(P, sizeof(panel_t) * cap);
+            if (P == local) {
+                P = (panel_t*)malloc(sizeof(panel_t) * cap);
+                memcpy(P, local, sizeof(local));
+            } else {
+                P = (panel_t*)realloc(P, sizeof(panel_t) * cap);
+            }
         }
         panel_t* L = &P[worst];
         panel_t* R = &P[np++];
@@ -244,8 +255,14 @@ static int adapt(vfun f, const void* ctx, const double* bp, int nbp, double rtol
         panel_eval(f, ctx, L);
         panel_eval(f, ctx, R);
     }
-    free(P);
+    if (P != local) free(P);
     return status;
+}
+
+static int adapt(vfun f, const void* ctx, const double* bp, int nbp, double rtol, double atol, int aux,
+                 double res[NV], double resabs[NV])
+{
+    return adapt_n(f, ctx, bp, nbp, rtol, atol, aux, MAXPAN, res, resabs);
 }
 
 /* ---------------------------------------------------------------------- */
@@ -254,72 +271,72 @@ static int adapt(vfun f, const void* ctx, const double* bp, int nbp, double rtol
 
 typedef struct {
     double eta_lo, eta_hi; /* source cell in eta */
-    double xi_lo, xi_hi;   /* source cell in xi */
     double eta_c;          /* beta^-k: the source centre r_{i'} / r_i */
+    double em1;            /* eta_c - 1, exact for k = 0 */
+    double hw;             /* half width in eta: eta_c (beta - 1)/(beta + 1) */
+    double sc, cc;         /* sine and cosine of the centre azimuth -q dphi */
+    double half_dphi;
     double qd;             /* q * dphi, q taken in (-N/2, N/2] */
     int self;              /* k == 0 and q == 0 */
     double rtol;
     int* bad; /* count of integrals that ran out of panels */
 } cell_t;
 
+/* The inner variable is del = eta - eta_c (so eta - eta_c is exact) and the
+   outer one t = xi - xi_c with xi_c = -q dphi the centre azimuth (so the
+   local azimuth of K^{.,phi} is t itself and sin xi, cos xi follow from t
+   and the exact centre values by angle addition). */
 typedef struct {
     const cell_t* cell;
-    double xi, c, s; /* outer node and cos, sin of it */
-    double vc;       /* 1 - cos xi = 2 sin^2(xi/2), without cancellation */
+    double t, c, s; /* outer node t and cos, sin of xi = xi_c + t */
+    double vc;      /* 1 - cos xi without cancellation */
 } inner_t;
 
-/* The six integrands at (eta, xi); om = 1 - eta cos xi, F3 = F^3. */
-static inline void six(double eta, double xi, double s, double om, double F3, double eta_c, double qd,
-                       double out[NC])
-{
-    double ir0 = -eta * om / F3;
-    double ip0 = eta * eta * s / F3;
-    double dr = eta - eta_c, dp = xi + qd;
-    out[0] = ir0;
-    out[1] = ir0 * dr;
-    out[2] = ir0 * dp;
-    out[3] = ip0;
-    out[4] = ip0 * dr;
-    out[5] = ip0 * dp;
-}
-
-/* inner integrand in eta (ordinary cells) */
-static void f_eta(double eta, const void* vctx, double out[NV])
+/* inner integrand in del = eta - eta_c (ordinary cells) */
+static void f_eta(double del, const void* vctx, double out[NV])
 {
     const inner_t* ic = (const inner_t*)vctx;
-    /* eta - cos xi and 1 - eta cos xi from eta - 1 (exact near eta = 1) and
+    const cell_t* cl = ic->cell;
+    /* eta - cos xi and 1 - eta cos xi from eta - 1 = (eta_c - 1) + del and
        1 - cos xi, so that both keep their relative precision where they are
        small */
-    double e1 = eta - 1.0;
+    double eta = cl->eta_c + del;
+    double e1 = cl->em1 + del;
     double d = e1 + ic->vc;
     double F2 = d * d + ic->s * ic->s;
     double F3 = F2 * sqrt(F2);
     double om = ic->vc - e1 * ic->c;
-    six(eta, ic->xi, ic->s, om, F3, ic->cell->eta_c, ic->cell->qd, out);
+    double ir0 = -eta * om / F3;
+    double ip0 = eta * eta * ic->s / F3;
+    out[0] = ir0;
+    out[1] = ir0 * del;
+    out[2] = ir0 * ic->t;
+    out[3] = ip0;
+    out[4] = ip0 * del;
+    out[5] = ip0 * ic->t;
 }
 
-/* inner integrand in t for the self cell: eta = c + |s| sinh t,
-   F = |s| cosh t, d eta = |s| cosh t dt, 1 - eta c = s^2 - c |s| sinh t. */
-static void f_t(double t, const void* vctx, double out[NV])
+/* inner integrand in tau for the self cell (xi_c = 0, eta_c = 1, so xi = t):
+   eta = c + |s| sinh tau, F = |s| cosh tau, d eta = |s| cosh tau d tau,
+   1 - eta c = s^2 - c |s| sinh tau, eta - 1 = |s| sinh tau - (1 - c). */
+static void f_tau(double tau, const void* vctx, double out[NV])
 {
     const inner_t* ic = (const inner_t*)vctx;
-    double as = fabs(ic->s), sh = sinh(t), ch = cosh(t);
+    double as = fabs(ic->s), sh = sinh(tau), ch = cosh(tau);
     double eta = ic->c + as * sh;
     double F = as * ch;
     double F3 = F * F * F;
     double om = ic->s * ic->s - ic->c * as * sh;
-    double v[NC];
-    /* eta - 1 for the self cell, written without cancellation */
-    double sh2 = sin(0.5 * ic->xi);
-    six(eta, ic->xi, ic->s, om, F3, 1.0, ic->cell->qd, v);
-    /* replace the (eta - eta_c) factor by the accurate form */
-    double dr = -2.0 * sh2 * sh2 + as * sh;
+    double dr = as * sh - ic->vc;
     double ir0 = -eta * om / F3, ip0 = eta * eta * ic->s / F3;
-    v[1] = ir0 * dr;
-    v[4] = ip0 * dr;
-    for (int c = 0; c < NC; c++) out[c] = v[c] * F; /* Jacobian |s| cosh t */
-    /* K^{r,0}: with eta = c + |s| sinh t,
-         f d eta = [-eta / cosh^2 t + c tanh^2 t] dt + (c^2/|s|) sinh t / cosh^2 t dt.
+    out[0] = ir0 * F;
+    out[1] = ir0 * dr * F;
+    out[2] = ir0 * ic->t * F;
+    out[3] = ip0 * F;
+    out[4] = ip0 * dr * F;
+    out[5] = ip0 * ic->t * F;
+    /* K^{r,0}: f d eta = [-eta / cosh^2 tau + c tanh^2 tau] d tau
+                          + (c^2/|s|) sinh tau / cosh^2 tau d tau.
        The last term is an odd pair of lobes of height 1/|s| whose sum is
        small; its integral, c^2 (1/F(eta_lo) - 1/F(eta_hi)), is added by the
        caller, and only the bounded remainder is integrated here. */
@@ -327,45 +344,47 @@ static void f_t(double t, const void* vctx, double out[NV])
     out[0] = -eta / (ch * ch) + ic->c * th * th;
 }
 
-/* outer integrand in xi: the inner eta integrals (out[0..5]) and the inner
-   integrals of their absolute integrands (out[6..11], the error scale) */
-static void f_xi(double xi, const void* vctx, double out[NV])
+/* outer integrand in t = xi - xi_c: the inner integrals (out[0..5]) and the
+   inner integrals of their absolute integrands (out[6..11], the error scale) */
+static void f_xi(double t, const void* vctx, double out[NV])
 {
     const cell_t* cell = (const cell_t*)vctx;
     inner_t ic;
     ic.cell = cell;
-    ic.xi = xi;
-    ic.c = cos(xi);
-    ic.s = sin(xi);
-    ic.vc = 2.0 * sin(0.5 * xi) * sin(0.5 * xi);
+    ic.t = t;
+    double st = sin(t), ct = cos(t);
+    ic.c = cell->cc * ct - cell->sc * st;
+    ic.s = cell->sc * ct + cell->cc * st;
+    ic.vc = ic.c > 0.0 ? ic.s * ic.s / (1.0 + ic.c) : 1.0 - ic.c;
     double abs_[NV];
-    int st;
+    int st_;
     if (cell->self && ic.s != 0.0) {
         double as = fabs(ic.s);
         double ta = asinh((cell->eta_lo - ic.c) / as);
         double tb = asinh((cell->eta_hi - ic.c) / as);
-        /* initial partition into panels of width <= 1 in t */
+        /* initial partition into panels of width <= 1 in tau */
         int npan = (int)ceil(tb - ta);
         if (npan < 1) npan = 1;
         if (npan > 200) npan = 200;
         double bp[202];
         for (int i = 0; i <= npan; i++) bp[i] = ta + (tb - ta) * i / npan;
         bp[npan] = tb;
-        st = adapt(f_t, &ic, bp, npan + 1, INNER_FRAC * cell->rtol, 0.0, 0, out, abs_);
-        /* the lobe term of K^{r,0} removed from the integrand in f_t */
+        st_ = adapt(f_tau, &ic, bp, npan + 1, INNER_FRAC * cell->rtol, 0.0, 0, out, abs_);
+        /* the lobe term of K^{r,0} removed from the integrand in f_tau */
         double Fa = sqrt((cell->eta_lo - ic.c) * (cell->eta_lo - ic.c) + ic.s * ic.s);
         double Fb = sqrt((cell->eta_hi - ic.c) * (cell->eta_hi - ic.c) + ic.s * ic.s);
         out[0] += ic.c * ic.c * (1.0 / Fa - 1.0 / Fb);
     } else {
         double bp[3];
         int nb = 0;
-        bp[nb++] = cell->eta_lo;
-        if (ic.c > cell->eta_lo && ic.c < cell->eta_hi) bp[nb++] = ic.c; /* nearest point to the pole */
-        bp[nb++] = cell->eta_hi;
-        st = adapt(f_eta, &ic, bp, nb, INNER_FRAC * cell->rtol, 0.0, 0, out, abs_);
+        bp[nb++] = -cell->hw;
+        double peak = -ic.vc - cell->em1; /* eta = cos xi: the point nearest the pole */
+        if (peak > -cell->hw && peak < cell->hw) bp[nb++] = peak;
+        bp[nb++] = cell->hw;
+        st_ = adapt(f_eta, &ic, bp, nb, INNER_FRAC * cell->rtol, 0.0, 0, out, abs_);
     }
     for (int c = 0; c < NC; c++) out[NC + c] = abs_[c];
-    if (st < 0) {
+    if (st_ < 0) {
 #ifdef _OPENMP
 #pragma omp atomic
 #endif
@@ -377,13 +396,13 @@ static void f_xi(double xi, const void* vctx, double out[NV])
    components odd in xi (K^{r,phi}, K^{phi,0}, K^{phi,r}) behave like 1/xi,
    so the xi integral exists as a principal value.  Integrate g(xi) + g(-xi)
    over [0, dphi/2]: the odd parts cancel pointwise, the even parts double. */
-static void f_xi_pair(double xi, const void* vctx, double out[NV])
+static void f_xi_pair(double t, const void* vctx, double out[NV])
 {
     double a[NV], b[NV];
     for (int c = 0; c < NV; c++) out[c] = 0.0;
-    if (!(fabs(sin(xi)) > 1e-200)) return; /* measure-zero neighbourhood of the pole */
-    f_xi(xi, vctx, a);
-    f_xi(-xi, vctx, b);
+    if (!(fabs(sin(t)) > 1e-200)) return; /* measure-zero neighbourhood of the pole */
+    f_xi(t, vctx, a);
+    f_xi(-t, vctx, b);
     /* the inner |integrand| integrals grow like 1/|xi| here, so the scale
        comes from |g| itself (aux == 0 in the outer call) */
     for (int c = 0; c < NC; c++) out[c] = a[c] + b[c];
@@ -395,23 +414,72 @@ static void f_xi_pair(double xi, const void* vctx, double out[NV])
  * caller through qd.  Returns 0, or the number of sub-integrals that ran out
  * of panels.
  */
+/* sin and cos of 2 pi num / den (den a power of two, |num| <= den) with the
+   argument reduced exactly to the first octant */
+static void sincos_2pi_frac(long num, long den, double* s, double* c)
+{
+    long n = ((num % den) + den) % den; /* [0, den) */
+    long e8 = den / 8 > 0 ? den / 8 : 0;
+    if (e8 == 0) { /* den < 8: direct */
+        *s = sin(2.0 * M_PI * (double)n / den);
+        *c = cos(2.0 * M_PI * (double)n / den);
+        return;
+    }
+    int o = (int)(n / e8);
+    long r = n - o * e8;
+    double a, sa, ca;
+    if ((o & 1) == 0) {
+        a = 2.0 * M_PI * r / den;
+        sa = sin(a);
+        ca = cos(a);
+        switch (o) {
+            case 0: *c = ca; *s = sa; break;
+            case 2: *c = -sa; *s = ca; break;
+            case 4: *c = -ca; *s = -sa; break;
+            default: *c = sa; *s = -ca; break;
+        }
+    } else {
+        a = 2.0 * M_PI * (e8 - r) / den;
+        sa = sin(a);
+        ca = cos(a);
+        switch (o) {
+            case 1: *c = sa; *s = ca; break;
+            case 3: *c = -ca; *s = sa; break;
+            case 5: *c = -sa; *s = -ca; break;
+            default: *c = ca; *s = -sa; break;
+        }
+    }
+}
+
+static void cell_setup(cell_t* cell, double du, int nphi, int k, int qs, double rtol, int* bad)
+{
+    double beta = exp(du), dphi = 2.0 * M_PI / nphi;
+    cell->eta_c = exp(-du * k);
+    cell->em1 = expm1(-du * k);
+    cell->hw = cell->eta_c * tanh(0.5 * du);
+    cell->eta_lo = cell->eta_c * 2.0 / (beta + 1.0);
+    cell->eta_hi = cell->eta_c * 2.0 * beta / (beta + 1.0);
+    sincos_2pi_frac(-(long)qs, nphi, &cell->sc, &cell->cc);
+    cell->half_dphi = 0.5 * dphi;
+    cell->qd = qs * dphi;
+    cell->self = (k == 0 && qs == 0);
+    cell->rtol = rtol;
+    cell->bad = bad;
+}
+
+/*
+ * The six kernel values for offset (k, q) on a grid with beta = e^du and
+ * dphi = 2 pi / N_phi.  q is any integer (reduced to (-N/2, N/2]).  Returns
+ * 0, or the number of sub-integrals that ran out of panels.
+ */
 int sgo_cell(double du, int nphi, int k, int q, double rtol, double out6[NC])
 {
     gl_init();
-    double beta = exp(du), dphi = 2.0 * M_PI / nphi;
     int qs = ((q % nphi) + nphi) % nphi;
     if (2 * qs > nphi) qs -= nphi;
     int bad = 0;
     cell_t cell;
-    cell.eta_c = exp(-du * k);
-    cell.eta_lo = cell.eta_c * 2.0 / (beta + 1.0);
-    cell.eta_hi = cell.eta_c * 2.0 * beta / (beta + 1.0);
-    cell.xi_lo = (-qs - 0.5) * dphi;
-    cell.xi_hi = (-qs + 0.5) * dphi;
-    cell.qd = qs * dphi;
-    cell.self = (k == 0 && qs == 0);
-    cell.rtol = rtol;
-    cell.bad = &bad;
+    cell_setup(&cell, du, nphi, k, qs, rtol, &bad);
     double bp[3], abs_[NV], out[NV];
     int nb = 0, st;
     if (cell.self) {
@@ -419,18 +487,19 @@ int sgo_cell(double du, int nphi, int k, int q, double rtol, double out6[NC])
            value that shrinks with the cell, sets a floor on what this cell
            can resolve: try 1e-14, then 1e-13, then 1e-12 */
         bp[nb++] = 0.0;
-        bp[nb++] = cell.xi_hi;
+        bp[nb++] = cell.half_dphi;
         double floors[3] = {1e-14, 1e-13, 1e-12};
         for (int attempt = 0; attempt < 3; attempt++) {
             cell.rtol = rtol > floors[attempt] ? rtol : floors[attempt];
             bad = 0;
-            st = adapt(f_xi_pair, &cell, bp, nb, cell.rtol, 0.0, 0, out, abs_);
+            /* a log-singular endpoint needs about 60 bisections; more
+               panels than that only chase rounding */
+            st = adapt_n(f_xi_pair, &cell, bp, nb, cell.rtol, 0.0, 0, attempt < 2 ? 400 : MAXPAN, out, abs_);
             if (st > 0 && bad == 0) break;
         }
     } else {
-        bp[nb++] = cell.xi_lo;
-        if (cell.xi_lo < 0.0 && cell.xi_hi > 0.0) bp[nb++] = 0.0;
-        bp[nb++] = cell.xi_hi;
+        bp[nb++] = -cell.half_dphi;
+        bp[nb++] = cell.half_dphi;
         st = adapt(f_xi, &cell, bp, nb, rtol, 0.0, 1, out, abs_);
     }
     if (st < 0) bad++;
@@ -440,24 +509,31 @@ int sgo_cell(double du, int nphi, int k, int q, double rtol, double out6[NC])
 
 /*
  * Kernel table for k in [-Nu, Nu], q in [0, Nphi):
- * out[c][(k + Nu) * Nphi + q], c = 0..5.  Returns the number of integrals
- * that ran out of panels (0 when all converged).
+ * out[c][(k + Nu) * Nphi + q], c = 0..5.  The cells with q in (Nphi/2, Nphi)
+ * are the mirror images xi -> -xi of those with Nphi - q (K^{r,0}, K^{r,r},
+ * K^{phi,phi} even, K^{r,phi}, K^{phi,0}, K^{phi,r} odd).  Returns the number
+ * of integrals that ran out of panels (0 when all converged).
  */
 int sgo_cells_table(int nu, int nphi, double du, double rtol, double* out, int nthreads)
 {
     gl_init();
-    long nk = 2L * nu + 1, per = nk * nphi;
+    long nk = 2L * nu + 1, per = nk * nphi, nq = nphi / 2 + 1;
     int bad = 0;
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
 #pragma omp parallel for schedule(dynamic, 16) reduction(+ : bad)
 #endif
-    for (long idx = 0; idx < per; idx++) {
-        int k = (int)(idx / nphi) - nu;
-        int q = (int)(idx % nphi);
+    for (long idx = 0; idx < nk * nq; idx++) {
+        int k = (int)(idx / nq) - nu;
+        int q = (int)(idx % nq);
         double v[NC];
         bad += sgo_cell(du, nphi, k, q, rtol, v);
-        for (int c = 0; c < NC; c++) out[c * per + idx] = v[c];
+        long row = (long)(k + nu) * nphi;
+        int qm = (nphi - q) % nphi;
+        for (int c = 0; c < NC; c++) {
+            out[c * per + row + q] = v[c];
+            if (qm != q) out[c * per + row + qm] = (c == 2 || c == 3 || c == 4) ? -v[c] : v[c];
+        }
     }
     return bad;
 }
@@ -540,24 +616,16 @@ int sgo_max_threads(void)
 #endif
 }
 
-/* The inner eta integral at one xi (for the tests of the quadrature). */
-int sgo_inner(double du, int nphi, int k, int q, double xi, double rtol, double out[NV])
+/* The inner integral at one outer node t = xi - xi_c (for the tests of the
+   quadrature). */
+int sgo_inner(double du, int nphi, int k, int q, double t, double rtol, double out[NV])
 {
     gl_init();
-    double beta = exp(du), dphi = 2.0 * M_PI / nphi;
     int qs = ((q % nphi) + nphi) % nphi;
     if (2 * qs > nphi) qs -= nphi;
     int bad = 0;
     cell_t cell;
-    cell.eta_c = exp(-du * k);
-    cell.eta_lo = cell.eta_c * 2.0 / (beta + 1.0);
-    cell.eta_hi = cell.eta_c * 2.0 * beta / (beta + 1.0);
-    cell.xi_lo = (-qs - 0.5) * dphi;
-    cell.xi_hi = (-qs + 0.5) * dphi;
-    cell.qd = qs * dphi;
-    cell.self = (k == 0 && qs == 0);
-    cell.rtol = rtol;
-    cell.bad = &bad;
-    f_xi(xi, &cell, out);
+    cell_setup(&cell, du, nphi, k, qs, rtol, &bad);
+    f_xi(t, &cell, out);
     return bad;
 }
