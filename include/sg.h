@@ -131,6 +131,27 @@ sg_status sg_forces_host(sg_plan* plan, const void* sigma_h, void* F_r_h, void* 
 sg_status sg_forces_timed(sg_plan* plan, const void* sigma, void* F_r, void* F_phi, cudaStream_t stream,
                           float ms[4]);
 
+/*
+ * sg_forces for callers that cannot allocate device memory when they compute
+ * forces (their memory belongs to another framework's allocator, or their
+ * loop may not allocate or synchronise): the scratch that sg_forces takes
+ * from the plan comes instead from a fixed 24 MiB array that the library
+ * reserves on every device it is loaded on, until the process exits.  The
+ * paper has no counterpart; this is a deployment variant of sg_forces with
+ * the same arguments and results.
+ *   - Allocates nothing.  The plan must be built (that allocated earlier).
+ *   - Supported up to 3 N_u (N_phi/2) complex values of scratch: N_u N_phi <=
+ *     2^21 cells in SG_F32, 2^20 in SG_F64; larger plans get
+ *     SG_ERR_UNSUPPORTED.  The plan's device must be the current device
+ *     (SG_ERR_ARG otherwise).
+ *   - The first call on each device looks up the array's device address
+ *     with that device current; make it before any stream capture.
+ *   - All calls on a device share the array: calls whose work overlaps on
+ *     the GPU (other streams, other threads) race and must be serialised.
+ *     Nothing in it needs to start at zero.
+ */
+sg_status sg_forces_noalloc(sg_plan* plan, const void* sigma, void* F_r, void* F_phi, cudaStream_t stream);
+
 /* One disk of a batch: its plan (built) and its device fields. */
 typedef struct {
     sg_plan* plan;

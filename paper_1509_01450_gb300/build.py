@@ -17,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsgdisk.so")
-SOURCES = ["api.cu", "kbuild.cu", "fftconv.cu"]
+SOURCES = ["api.cu", "kbuild.cu", "fftconv.cu", "noalloc.cu"]
 HEADERS = ["sg_common.cuh", "sg_internal.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -1,0 +1,82 @@
+// noalloc.cu -- sg_forces_noalloc: the forward pass with its scratch in a
+// fixed, statically reserved device array instead of the plan's workspace.
+//
+// Who needs this: code that must not call cudaMalloc at the moment it
+// computes forces -- for example a host application whose device memory is
+// handed out by another framework's allocator, a real-time loop where an
+// allocation (and the implicit synchronisation it can cause) is not
+// allowed, or a pool-limited process that has already committed its memory.
+// Such a caller still creates and builds a plan beforehand (that allocates);
+// this call then allocates nothing.
+//
+// The scratch is SG_NOALLOC_BYTES of __device__ memory that every GPU which
+// loads this library reserves until the process exits.  All calls on a
+// device share it, so calls whose work overlaps on the GPU (two streams, or
+// two threads) race on it and must be serialised by the caller.  The first
+// call on each device looks up the array's device address
+// (cudaGetSymbolAddress) with that device current; make that first call
+// before any stream capture.  No part of the scratch needs to start at
+// zero: the row pass writes every element the column pass reads, and the
+// column pass writes every element the inverse row pass reads.
+#include <mutex>
+
+#include "sg_internal.cuh"
+
+using namespace sg;
+
+// 24 MiB: three half-spectrum buffers of N_u x N_phi/2 complex values, i.e.
+// 12 bytes per grid cell in FP32 (up to 2^21 cells, e.g. 1024 x 2048) or 24
+// bytes per cell in FP64 (up to 2^20 cells).
+#define SG_NOALLOC_BYTES (24u << 20)
+#define SG_NOALLOC_MAX_DEVICES 64
+
+static __device__ __align__(256) unsigned char sg_noalloc_scratch[SG_NOALLOC_BYTES];
+
+static void* g_scratch[SG_NOALLOC_MAX_DEVICES];
+static std::mutex g_scratch_mutex;
+
+// Device address of the scratch on the current device (looked up once per
+// device; host code cannot use the symbol's host-side name as an address).
+static sg_status scratch_address(void** out)
+{
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return SG_ERR_CUDA;
+    if (dev < 0 || dev >= SG_NOALLOC_MAX_DEVICES) return SG_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_scratch_mutex);
+    if (!g_scratch[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, sg_noalloc_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return SG_ERR_CUDA;
+        }
+        g_scratch[dev] = p;
+    }
+    *out = g_scratch[dev];
+    return SG_OK;
+}
+
+extern "C" sg_status sg_forces_noalloc(sg_plan* p, const void* sigma, void* F_r, void* F_phi, cudaStream_t stream)
+{
+    if (!p) return SG_ERR_ARG;
+    if (!p->built) return SG_ERR_NOT_BUILT;
+    const void* ptrs[3] = {sigma, F_r, F_phi};
+    for (const void* q : ptrs)
+        if (!q || ((uintptr_t)q & 15)) return SG_ERR_ARG;
+    if (sigma == F_r || sigma == F_phi || F_r == F_phi) return SG_ERR_ARG;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return SG_ERR_CUDA;
+    if (dev != p->device) return SG_ERR_ARG;  // the plan's spectra live on p->device
+    const size_t half = (size_t)p->nu * (p->nphi / 2) * 2 * p->elem;  // one half-spectrum buffer
+    if (3 * half > SG_NOALLOC_BYTES) return SG_ERR_UNSUPPORTED;
+    void* scratch = nullptr;
+    sg_status st = scratch_address(&scratch);
+    if (st) return st;
+    PlanView v = view(p);
+    v.wa = scratch;
+    v.wb = (unsigned char*)scratch + half;
+    v.wc = (unsigned char*)scratch + 2 * half;
+    cudaError_t e = p->dtype == SG_F32
+                        ? launch_forward<float>(v, (const float*)sigma, (float*)F_r, (float*)F_phi, stream)
+                        : launch_forward<double>(v, (const double*)sigma, (double*)F_r, (double*)F_phi, stream);
+    return e == cudaSuccess ? SG_OK : SG_ERR_CUDA;
+}

@@ -20,7 +20,7 @@ SG_F32, SG_F64 = 0, 1
 
 EXPORTS = ("sg_plan_create", "sg_kernels_build", "sg_forces", "sg_forces_backward", "sg_forces_host", "sg_forces_timed",
            "sg_forces_batched", "sg_batch_reserve", "sg_plan_destroy", "sg_status_string", "sg_plan_info",
-           "sg_plan_kernels", "sg_plan_cells", "sg_plan_device_bytes", "sg_plan_build_report")
+           "sg_plan_kernels", "sg_plan_cells", "sg_plan_device_bytes", "sg_plan_build_report", "sg_forces_noalloc")
 
 
 class SgError(RuntimeError):
@@ -55,6 +55,7 @@ def lib():
         L.sg_forces_backward.argtypes = [vp, vp, vp, vp, vp]
         L.sg_forces_host.argtypes = [vp, vp, vp, vp, vp]
         L.sg_forces_timed.argtypes = [vp, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_float)]
+        L.sg_forces_noalloc.argtypes = [vp, vp, vp, vp, vp]
         L.sg_forces_batched.argtypes = [ctypes.POINTER(BatchItem), ip, vp]
         L.sg_batch_reserve.argtypes = [ip]
         L.sg_plan_destroy.argtypes = [vp]
@@ -127,6 +128,16 @@ class Plan:
         F_phi = self._new() if F_phi is None else F_phi
         self._check_field(sigma)
         _check(lib().sg_forces(self.handle, _ptr(sigma), _ptr(F_r), _ptr(F_phi), _stream(stream)), "sg_forces")
+        return F_r, F_phi
+
+    def forces_noalloc(self, sigma, F_r, F_phi, stream=None):
+        """sg_forces using the library's fixed scratch array: no device
+        allocation in the call (for callers that may not allocate then).
+        Calls that overlap on the GPU share that scratch and must not run
+        concurrently."""
+        self._check_field(sigma)
+        _check(lib().sg_forces_noalloc(self.handle, _ptr(sigma), _ptr(F_r), _ptr(F_phi), _stream(stream)),
+               "sg_forces_noalloc")
         return F_r, F_phi
 
     def forces_timed(self, sigma, F_r, F_phi, stream=None):
