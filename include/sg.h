@@ -99,7 +99,10 @@ sg_status sg_kernels_build(sg_plan* plan, const sg_build_opts* opts, cudaStream_
 /*
  * Forward pass: F_r, F_phi from sigma (device pointers, layout above).
  * F_r and F_phi are overwritten.  sigma may not alias F_r or F_phi.
- * SG_ERR_NOT_BUILT before sg_kernels_build.
+ * SG_ERR_NOT_BUILT before sg_kernels_build.  The column pass waits for its
+ * asynchronous input copies with a time limit (about a second); if that
+ * ever runs out the outputs are invalid and the plan's error flag is set
+ * (sg_plan_check).
  */
 sg_status sg_forces(sg_plan* plan, const void* sigma, void* F_r, void* F_phi, cudaStream_t stream);
 
@@ -115,8 +118,9 @@ sg_status sg_forces_backward(sg_plan* plan, const void* gF_r, const void* gF_phi
 /*
  * Same as sg_forces with HOST buffers: copies sigma to the device, runs the
  * forward pass and copies F_r, F_phi back, all on stream, then synchronises
- * the stream.  Uses plan-owned device staging buffers (allocated on first
- * use).  Host buffers should be pinned for full copy bandwidth.
+ * the stream and returns what sg_plan_check returns.  Uses plan-owned device
+ * staging buffers (allocated on first use).  Host buffers should be pinned
+ * for full copy bandwidth.
  */
 sg_status sg_forces_host(sg_plan* plan, const void* sigma_h, void* F_r_h, void* F_phi_h, cudaStream_t stream);
 
@@ -203,6 +207,14 @@ sg_status sg_plan_cells(sg_plan* plan, double* cells_h, cudaStream_t stream);
  * build.
  */
 sg_status sg_plan_build_report(const sg_plan* plan, int report[4]);
+
+/*
+ * Device-side status of the work enqueued so far with this plan: reads (and
+ * clears) the plan's error flags after synchronising stream.  SG_ERR_TIMEOUT
+ * means a pass gave up waiting for its asynchronous input copies (its
+ * results are invalid); SG_OK otherwise.
+ */
+sg_status sg_plan_check(sg_plan* plan, cudaStream_t stream);
 
 /* Bytes of device memory the plan holds. */
 size_t sg_plan_device_bytes(const sg_plan* plan);

@@ -35,7 +35,7 @@ static void free_plan(sg_plan* p)
     if (p->have_ev)
         for (int i = 0; i < 4; i++) cudaEventDestroy(p->ev[i]);
     void* bufs[] = {p->tw, p->wa, p->wb, p->wc, p->kr, p->kp, p->wpre, p->wpost, p->tw64, p->cells, p->keff,
-                    p->h_sigma, p->h_fr, p->h_fp};
+                    p->h_sigma, p->h_fr, p->h_fp, p->derr};
     for (void* b : bufs)
         if (b) cudaFree(b);
     free(p);
@@ -111,9 +111,6 @@ sg_status sg_plan_create(sg_plan** out, int nu, int nphi, double u_min, double d
     p->weight_p = 2;
     p->elem = dtype == SG_F32 ? sizeof(float) : sizeof(double);
     const size_t cx = 2 * p->elem;
-    int cb = dtype == SG_F32 ? 4 : 2;
-    if (cb > nphi / 2) cb = nphi / 2;
-    p->cb = cb;
     cudaGetDevice(&p->device);
 
     const size_t nhalf = (size_t)nu * (nphi / 2);
@@ -123,11 +120,15 @@ sg_status sg_plan_create(sg_plan** out, int nu, int nphi, double u_min, double d
         (st = dev_alloc(p, &p->wa, nhalf * cx)) || (st = dev_alloc(p, &p->wb, nhalf * cx)) ||
         (st = dev_alloc(p, &p->wc, nhalf * cx)) || (st = dev_alloc(p, &p->kr, nk * cx)) ||
         (st = dev_alloc(p, &p->kp, nk * cx)) || (st = dev_alloc(p, &p->wpre, nu * p->elem)) ||
-        (st = dev_alloc(p, &p->wpost, nu * p->elem)) ||
+        (st = dev_alloc(p, &p->wpost, nu * p->elem)) || (st = dev_alloc(p, (void**)&p->derr, 16)) ||
         (st = dev_alloc(p, (void**)&p->cells, (size_t)6 * (2 * nu + 1) * nphi * sizeof(double))) ||
         (st = dev_alloc(p, (void**)&p->keff, (size_t)2 * (2 * nu - 1) * nphi * sizeof(double)))) {
         free_plan(p);
         return st;
+    }
+    if (cudaMemset(p->derr, 0, 16) != cudaSuccess) {
+        free_plan(p);
+        return SG_ERR_CUDA;
     }
     std::vector<double> re, im;
     twiddles(re, im);
@@ -333,8 +334,7 @@ sg_status sg_forces_host(sg_plan* p, const void* sigma_h, void* Fr_h, void* Fp_h
     if ((st = sg_forces(p, p->h_sigma, p->h_fr, p->h_fp, stream))) return st;
     SG_TRY(cudaMemcpyAsync(Fr_h, p->h_fr, bytes, cudaMemcpyDeviceToHost, stream));
     SG_TRY(cudaMemcpyAsync(Fp_h, p->h_fp, bytes, cudaMemcpyDeviceToHost, stream));
-    SG_TRY(cudaStreamSynchronize(stream));
-    return SG_OK;
+    return sg_plan_check(p, stream);  // synchronises; reports a device-side timeout
 }
 
 sg_status sg_batch_reserve(int n) { return n >= 0 ? SG_OK : SG_ERR_ARG; }
@@ -351,6 +351,20 @@ sg_status sg_forces_batched(const sg_batch_item* items, int n, cudaStream_t stre
     for (int b = 0; b < n; b++) {
         sg_status st = sg_forces(items[b].plan, items[b].sigma, items[b].F_r, items[b].F_phi, stream);
         if (st) return st;
+    }
+    return SG_OK;
+}
+
+sg_status sg_plan_check(sg_plan* p, cudaStream_t stream)
+{
+    if (!p) return SG_ERR_ARG;
+    int h = 0;
+    SG_TRY(cudaMemcpyAsync(&h, p->derr, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    SG_TRY(cudaStreamSynchronize(stream));
+    if (h) {
+        SG_TRY(cudaMemsetAsync(p->derr, 0, sizeof(int), stream));
+        SG_TRY(cudaStreamSynchronize(stream));
+        return SG_ERR_TIMEOUT;
     }
     return SG_OK;
 }

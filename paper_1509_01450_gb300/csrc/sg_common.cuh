@@ -189,6 +189,31 @@ __device__ __forceinline__ void sg_dft(V* a)
 // radix-R DFT and writes y[(b - b mod Ns) R + b mod Ns + r Ns].  Thread t does
 // the butterflies b = t + s NT, s < E/R, on registers e = s + r E/R.
 // ---------------------------------------------------------------------------
+// Twiddles w^r, r = 1..R-1, of a butterfly from w = w^1 alone: a product
+// tree of depth <= 4 (w^2 = w w, w^3 = w^2 w, w^4 = w^2 w^2, ...), so each
+// power carries a few roundings instead of costing a table load.
+template <int R, typename V>
+__device__ __forceinline__ void sg_twiddle_powers(V* a, V w1)
+{
+    V w[R];
+    w[1] = w1;
+    if (R > 2) w[2] = cmul(w1, w1);
+    if (R > 3) w[3] = cmul(w[2], w1);
+    if (R > 4) {
+        w[4] = cmul(w[2], w[2]);
+        w[5] = cmul(w[4], w1);
+        w[6] = cmul(w[4], w[2]);
+        w[7] = cmul(w[4], w[3]);
+    }
+    if (R > 8) {
+        w[8] = cmul(w[4], w[4]);
+#pragma unroll
+        for (int r = 9; r < 16; r++) w[r] = cmul(w[8], w[r - 8]);
+    }
+#pragma unroll
+    for (int r = 1; r < R; r++) a[r] = cmul(a[r], w[r]);
+}
+
 template <int R, int E, int DIR, typename V>
 __device__ __forceinline__ void sg_pass_compute(V (&v)[E], int t, int NT, int Ns, const V* __restrict__ tw)
 {
@@ -200,13 +225,188 @@ __device__ __forceinline__ void sg_pass_compute(V (&v)[E], int t, int NT, int Ns
         if (Ns > 1) {
             const int k = (t + s * NT) & (Ns - 1);
             const int stride = SG_NMAX / (Ns * R);
+            if (sizeof(a[0].x) == 4) {
+                // FP32: one table load, the other powers by multiplication
+                sg_twiddle_powers<R>(a, sg_tw<DIR>(tw, k * stride));
+            } else {
+                // FP64 arithmetic is the scarce resource: load every power
 #pragma unroll
-            for (int r = 1; r < R; r++) a[r] = cmul(a[r], sg_tw<DIR>(tw, r * k * stride));
+                for (int r = 1; r < R; r++) a[r] = cmul(a[r], sg_tw<DIR>(tw, r * k * stride));
+            }
         }
         sg_dft<R, DIR>(a);
 #pragma unroll
         for (int r = 0; r < R; r++) v[s + r * (E / R)] = a[r];
     }
+}
+
+// ---------------------------------------------------------------------------
+// Bulk asynchronous copies (TMA, cp.async.bulk) into shared memory, completed
+// on an mbarrier.  Addresses and sizes must be multiples of 16 bytes.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t sg_smem_u32(const void* p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void sg_mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sg_smem_u32(bar)), "r"(count) : "memory");
+    // make the initialised barrier visible to the asynchronous (bulk copy) proxy
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void sg_mbar_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(sg_smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void sg_bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            sg_smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(sg_smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool sg_mbar_try_wait(uint64_t* bar, uint32_t phase)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(sg_smem_u32(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t sg_globaltimer_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bulk copy with an L2 eviction-priority policy (sg_policy_*).
+__device__ __forceinline__ void sg_bulk_g2s_hint(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
+                                                 uint64_t policy)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+            sg_smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(sg_smem_u32(bar)), "l"(policy)
+        : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// L2 eviction priorities.  The half-spectrum intermediates are written by one
+// pass and read, transposed, by the next; they are kept in L2 (evict_last)
+// while the streamed inputs (density, kernel spectra, consumed intermediates)
+// are marked evict_first.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t sg_policy_evict_first()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t sg_policy_evict_last()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ void sg_st_hint(float2* a, float2 v, uint64_t pol)
+{
+    asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(a), "f"(v.x), "f"(v.y), "l"(pol)
+                 : "memory");
+}
+__device__ __forceinline__ void sg_st_hint(double2* a, double2 v, uint64_t pol)
+{
+    asm volatile("st.global.L2::cache_hint.v2.f64 [%0], {%1, %2}, %3;" ::"l"(a), "d"(v.x), "d"(v.y), "l"(pol)
+                 : "memory");
+}
+__device__ __forceinline__ void sg_st_hint(float4* a, float4 v, uint64_t pol)
+{
+    asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(a), "f"(v.x), "f"(v.y),
+                 "f"(v.z), "f"(v.w), "l"(pol)
+                 : "memory");
+}
+// read-only loads (data not written during the kernel)
+__device__ __forceinline__ float4 sg_ld_hint(const float4* a, uint64_t pol)
+{
+    float4 r;
+    asm("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+        : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
+        : "l"(a), "l"(pol));
+    return r;
+}
+__device__ __forceinline__ float2 sg_ld_hint(const float2* a, uint64_t pol)
+{
+    float2 r;
+    asm("ld.global.nc.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;" : "=f"(r.x), "=f"(r.y) : "l"(a), "l"(pol));
+    return r;
+}
+__device__ __forceinline__ double2 sg_ld_hint(const double2* a, uint64_t pol)
+{
+    double2 r;
+    asm("ld.global.nc.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;" : "=d"(r.x), "=d"(r.y) : "l"(a), "l"(pol));
+    return r;
+}
+__device__ __forceinline__ float sg_ld_hint(const float* a, uint64_t pol)
+{
+    float r;
+    asm("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(r) : "l"(a), "l"(pol));
+    return r;
+}
+__device__ __forceinline__ double sg_ld_hint(const double* a, uint64_t pol)
+{
+    double r;
+    asm("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(r) : "l"(a), "l"(pol));
+    return r;
+}
+
+// Asynchronous global -> shared copies of 16 (or 8) bytes (cp.async), with
+// an L2 policy; complete them with sg_cp_async_wait_all and a block barrier.
+__device__ __forceinline__ void sg_cp_async16(void* dst, const void* src, uint64_t policy)
+{
+    asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;" ::"r"(sg_smem_u32(dst)), "l"(src),
+                 "l"(policy)
+                 : "memory");
+}
+__device__ __forceinline__ void sg_cp_async8(void* dst, const void* src, uint64_t policy)
+{
+    asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], 8, %2;" ::"r"(sg_smem_u32(dst)), "l"(src),
+                 "l"(policy)
+                 : "memory");
+}
+__device__ __forceinline__ void sg_cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Wait for phase `phase` of the barrier, giving up after about a second (or
+// an iteration cap, whichever comes first).  On that timeout the error flag
+// gets `code`, a second wait of the same length gives the copies in flight a
+// last chance to land, and the call returns false: the caller then leaves
+// the block early (uniformly, via __syncthreads_or) and the host reads the
+// flag.  Returns true when the data arrived in time.
+#define SG_WAIT_NS 1000000000ull
+#define SG_WAIT_ITERS (1 << 24)
+__device__ __forceinline__ bool sg_mbar_wait_once(uint64_t* bar, uint32_t phase)
+{
+    const uint64_t t0 = sg_globaltimer_ns();
+    for (int it = 0; it < SG_WAIT_ITERS; it++) {
+        if (sg_mbar_try_wait(bar, phase)) return true;
+        if ((it & 255) == 255 && sg_globaltimer_ns() - t0 > SG_WAIT_NS) break;
+    }
+    return false;
+}
+__device__ __forceinline__ bool sg_mbar_wait_bounded(uint64_t* bar, uint32_t phase, int* err, int code)
+{
+    if (sg_mbar_wait_once(bar, phase)) return true;
+    if (err) atomicOr(err, code);
+    sg_mbar_wait_once(bar, phase);
+    return false;
 }
 
 template <int R, int E, typename V>
@@ -278,6 +478,86 @@ __device__ __forceinline__ void sg_fft(V (&v)[E], V* sm, int N, int log2N, int t
         __syncthreads();
         sg_pass_compute<16, E, DIR>(v, t, NT, Ns, tw);
         Rprev = 16;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The same transform with its twiddles held in registers (E == 16): each of
+// a thread's radix-16 passes after the first needs one base twiddle
+// w = e^{-2 pi i k / (16 Ns)}, k = t mod Ns, whose powers the pass forms by
+// multiplication.  sg_fft_twiddles loads those (at most three) bases once;
+// every transform of that length in the kernel then reuses them, in either
+// direction, with no further table loads.
+// ---------------------------------------------------------------------------
+template <typename V>
+struct SgTwid {
+    V w[3];
+};
+
+template <typename V>
+__device__ __forceinline__ SgTwid<V> sg_fft_twiddles(int log2N, int t, const V* __restrict__ tw)
+{
+    SgTwid<V> r;
+    const int rem = log2N & 3;
+    const int n16 = (log2N >> 2) - (rem == 0 ? 1 : 0);
+    int Ns = rem == 0 ? 16 : (1 << rem);
+#pragma unroll
+    for (int p = 0; p < 3; p++) {
+        r.w[p] = V{1, 0};
+        if (p < n16) r.w[p] = __ldg(&tw[(t & (Ns - 1)) * (SG_NMAX / (Ns * 16))]);
+        Ns *= 16;
+    }
+    return r;
+}
+
+template <int DIR, typename V>
+__device__ __forceinline__ void sg_pass16_tw(V (&v)[16], V w)
+{
+    if (DIR > 0) w = cconj(w);
+    sg_twiddle_powers<16>(v, w);
+    sg_dft<16, DIR>(v);
+}
+
+template <int E, int DIR, typename V>
+__device__ __forceinline__ void sg_fft(V (&v)[E], V* sm, int N, int log2N, int t, const SgTwid<V>& tws)
+{
+    static_assert(E == 16, "register twiddles need 16 elements per thread");
+    const int NT = N / E;
+    const int rem = log2N & 3;
+    const int n16 = (log2N >> 2) - (rem == 0 ? 1 : 0);
+    const V* none = nullptr;
+    if (rem == 1)
+        sg_pass_compute<2, E, DIR>(v, t, NT, 1, none);
+    else if (rem == 2)
+        sg_pass_compute<4, E, DIR>(v, t, NT, 1, none);
+    else if (rem == 3)
+        sg_pass_compute<8, E, DIR>(v, t, NT, 1, none);
+    else
+        sg_pass_compute<16, E, DIR>(v, t, NT, 1, none);
+    int Ns = 1;
+#pragma unroll
+    for (int p = 0; p < 3; p++) {
+        if (p < n16) {
+            if (p == 0) {
+                __syncthreads();  // the caller may have just read sm
+                if (rem == 1)
+                    sg_pass_store<2, E>(v, sm, t, NT, 1);
+                else if (rem == 2)
+                    sg_pass_store<4, E>(v, sm, t, NT, 1);
+                else if (rem == 3)
+                    sg_pass_store<8, E>(v, sm, t, NT, 1);
+                else
+                    sg_pass_store<16, E>(v, sm, t, NT, 1);
+                Ns = rem == 0 ? 16 : (1 << rem);
+            } else {
+                sg_pass_store<16, E>(v, sm, t, NT, Ns);
+                Ns *= 16;
+            }
+            __syncthreads();
+            sg_pass_load<16, E>(v, sm, t, NT, N);
+            __syncthreads();
+            sg_pass16_tw<DIR>(v, tws.w[p]);
+        }
     }
 }
 

@@ -11,18 +11,18 @@ struct sg_plan {
     double u_min, du, G;
     int weight_p;
     int built;
-    int cb;          // column-block width of the half-spectrum buffers
     int device;      // device the plan's memory lives on
     size_t elem;     // bytes of one real in the working dtype
     // working-dtype device buffers
     void* tw;        // twiddle table, SG_NMAX complex
-    void* wa;        // column-block half spectra, nu * nphi/2 complex
-    void* wb;        // row-major half spectra, nu * nphi/2 complex
-    void* wc;        // half spectra (row-major fwd / column-block bwd)
+    void* wa;        // half spectra, mode-major X[m nu + i], nu * nphi/2 complex
+    void* wb;        // same
+    void* wc;        // same
     void* kr;        // Khat_r, (nphi/2 + 1) x (nu + 2) complex
     void* kp;        // Khat_phi, same shape
     void* wpre;      // beta^{p (i - i_ref)}, nu reals
     void* wpost;     // beta^{-p (i - i_ref)}
+    int* derr;       // device error flags of the passes (bounded waits)
     // FP64 device buffers
     void* tw64;      // twiddle table, SG_NMAX double complex
     double* cells;   // 6 x (2 nu + 1) x nphi raw cell kernels (kept after build)
@@ -41,7 +41,7 @@ namespace sg {
 
 // Plain view of a plan passed to the launchers.
 struct PlanView {
-    int nu, nphi, cb;
+    int nu, nphi;
     const void* tw;
     const void* tw64;
     void *wa, *wb, *wc;
@@ -49,6 +49,7 @@ struct PlanView {
     const void* kp;
     const void* wpre;
     const void* wpost;
+    int* err;
 };
 
 inline PlanView view(const sg_plan* p)
@@ -56,7 +57,6 @@ inline PlanView view(const sg_plan* p)
     PlanView v;
     v.nu = p->nu;
     v.nphi = p->nphi;
-    v.cb = p->cb;
     v.tw = p->tw;
     v.tw64 = p->tw64;
     v.wa = p->wa;
@@ -66,6 +66,7 @@ inline PlanView view(const sg_plan* p)
     v.kp = p->kp;
     v.wpre = p->wpre;
     v.wpost = p->wpost;
+    v.err = p->derr;
     return v;
 }
 

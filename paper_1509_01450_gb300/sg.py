@@ -20,7 +20,7 @@ SG_F32, SG_F64 = 0, 1
 
 EXPORTS = ("sg_plan_create", "sg_kernels_build", "sg_forces", "sg_forces_backward", "sg_forces_host", "sg_forces_timed",
            "sg_forces_batched", "sg_batch_reserve", "sg_plan_destroy", "sg_status_string", "sg_plan_info",
-           "sg_plan_kernels", "sg_plan_cells", "sg_plan_device_bytes", "sg_plan_build_report", "sg_forces_noalloc")
+           "sg_plan_kernels", "sg_plan_cells", "sg_plan_device_bytes", "sg_plan_build_report", "sg_forces_noalloc", "sg_plan_check")
 
 
 class SgError(RuntimeError):
@@ -65,6 +65,7 @@ def lib():
         L.sg_plan_kernels.argtypes = [vp, ctypes.POINTER(dp), ctypes.POINTER(dp), vp]
         L.sg_plan_cells.argtypes = [vp, ctypes.POINTER(dp), vp]
         L.sg_plan_build_report.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+        L.sg_plan_check.argtypes = [vp, vp]
         L.sg_plan_device_bytes.argtypes = [vp]
         L.sg_plan_device_bytes.restype = ctypes.c_size_t
         for name in EXPORTS:
@@ -174,6 +175,11 @@ class Plan:
         d = (ctypes.c_int * 4)()
         _check(lib().sg_plan_info(self.handle, d), "sg_plan_info")
         return tuple(d)
+
+    def check(self, stream=None):
+        """Raise if a pass of the enqueued work reported a device-side
+        timeout (synchronises the stream)."""
+        _check(lib().sg_plan_check(self.handle, _stream(stream)), "sg_plan_check")
 
     def build_report(self):
         """(flag bits, failed offsets, k, q) of the last build (all 0 if clean)."""

@@ -100,6 +100,7 @@ def test_forward_sizes_random_density(torch_cuda, oracle_mod, nu, nphi, dtype, t
     _, Kr, Kp = oracle_kernels(oracle_mod, nu, nphi, du)
     Fr_ref, Fp_ref = oracle_mod.direct_sum(sigma, Kr, Kp)
     Fr, Fp = _forward(torch_cuda, plan, sigma)
+    plan.check()  # no pass timed out waiting for its input copies
     assert oracle_mod.rel_l2(Fr, Fp, Fr_ref, Fp_ref) < tol
 
 
@@ -114,6 +115,7 @@ def test_backward_matches_transposed_sum(torch_cuda, oracle_mod, nu, nphi, dtype
     ref = oracle_mod.direct_sum_T(gr, gp, Kr, Kp)
     gs = plan.backward(torch.tensor(gr, dtype=plan.dtype, device="cuda"),
                        torch.tensor(gp, dtype=plan.dtype, device="cuda"))
+    plan.check()
     got = gs.double().cpu().numpy()
     assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < tol
 
