@@ -111,7 +111,11 @@ sg_status sg_plan_create(sg_plan** out, int nu, int nphi, double u_min, double d
     p->weight_p = 2;
     p->elem = dtype == SG_F32 ? sizeof(float) : sizeof(double);
     const size_t cx = 2 * p->elem;
-    cudaGetDevice(&p->device);
+    if (cudaGetDevice(&p->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess) {
+        free(p);
+        return SG_ERR_CUDA;
+    }
 
     const size_t nhalf = (size_t)nu * (nphi / 2);
     const size_t nk = (size_t)(nphi / 2 + 1) * (nu + 2);
@@ -129,6 +133,10 @@ sg_status sg_plan_create(sg_plan** out, int nu, int nphi, double u_min, double d
     if (cudaMemset(p->derr, 0, 16) != cudaSuccess) {
         free_plan(p);
         return SG_ERR_CUDA;
+    }
+    {
+        void* const bufs[3] = {p->wa, p->wb, p->wc};
+        make_row_maps(nu, nphi, p->elem, bufs, p->maps);
     }
     std::vector<double> re, im;
     twiddles(re, im);

@@ -30,6 +30,8 @@
 // 0..N_u of the L-point spectrum; Khat_r is Hermitian in kappa
 // (Khat_r[L - kappa] = conj Khat_r[kappa]) and Khat_phi anti-Hermitian.
 // Khat_phi vanishes at modes 0 and N_phi/2 (odd kernel).
+#include <mutex>
+
 #include "sg_internal.cuh"
 
 namespace sg {
@@ -82,13 +84,21 @@ __device__ __forceinline__ Twd<E, V> make_twd(int log2N, int t, const V* __restr
     if constexpr (E == 16 && sizeof(V) == 8) w.h = sg_fft_twiddles(log2N, t, tab);
     return w;
 }
-template <int E, int DIR, typename V>
-__device__ __forceinline__ void fft(V (&v)[E], V* sm, int N, int log2N, int t, const Twd<E, V>& w)
+template <int E, int DIR, typename V, typename Sync = SgSyncBlock>
+__device__ __forceinline__ void fft(V (&v)[E], V* sm, int N, int log2N, int t, const Twd<E, V>& w,
+                                    const Sync& sync = Sync())
 {
     if constexpr (E == 16 && sizeof(V) == 8)
-        sg_fft<E, DIR>(v, sm, N, log2N, t, w.h);
+        sg_fft<E, DIR>(v, sm, N, log2N, t, w.h, sync);
     else
-        sg_fft<E, DIR>(v, sm, N, log2N, t, w.tab);
+        sg_fft<E, DIR>(v, sm, N, log2N, t, w.tab, sync);
+}
+
+// The slot barrier of a row pass: a named barrier per slot when the slots
+// are whole warps and few enough (ids 1..8), else the whole block.
+__device__ __forceinline__ SgSyncSlot slot_sync(int slot, int NT, int slots)
+{
+    return (NT >= 64 && slots <= 8) ? SgSyncSlot{slot + 1, NT} : SgSyncSlot{0, 0};
 }
 
 // ===========================================================================
@@ -135,66 +145,189 @@ __device__ __forceinline__ void stage_load(V* S, const V* __restrict__ X, int nu
 }
 
 // ===========================================================================
-// Forward P1: rows (i0, i1) packed as z = w_i0 + i w_i1, FFT along phi,
-// split X_i0[m] = (Z[m] + conj Z[N-m]) / 2, X_i1[m] = (Z[m] - conj Z[N-m]) / 2i,
-// staged and stored mode-major (R = 2 slots rows per block).
+// Row passes: persistent blocks over row blocks of R consecutive rows, with
+// two shared-memory buffers: while one block of rows is transformed in one
+// buffer (its FFT exchanges included), the inputs of the block after it
+// arrive in the other.  Whole rows (density, adjoint seeds) come by one bulk
+// copy; the mode-major spectra come and go by 2-D tensor copies (boxes of
+// R rows x MB modes, staged as S[m R + r]) when the plan has tensor maps
+// for them (use_map), else by cp.async gathers and 16-byte stores.  Results
+// that are whole rows leave by bulk stores (use_map) or direct stores.
 // ===========================================================================
-template <typename T, int E>
-__global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 512) k_fwd_rows(const T* __restrict__ sigma, const T* __restrict__ wpre,
-                                                  typename CX<T>::t* __restrict__ A, int nu, int nphi, int log2n,
-                                                  const typename CX<T>::t* __restrict__ tw)
+// elements (V) of one row-pass buffer: the FFT exchange areas of all slots,
+// rounded to 128 bytes
+template <typename V>
+__host__ __device__ __forceinline__ size_t row_buf_elems(int N, int slots)
 {
-    typedef typename CX<T>::t V;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    V* small = reinterpret_cast<V*>(smraw);
-    const int N = nphi, NT = N / E, half = N / 2;
-    const int slot = threadIdx.x / NT, t = threadIdx.x % NT;
-    const Twd<E, V> twd = make_twd<E>(log2n, t, tw);
-    const int slots = blockDim.x / NT;
-    V* sm = small + slot * sg_padded(N);
-    const int pair = blockIdx.x * slots + slot;
-    const bool live = pair < nu / 2;
-    const int i0 = 2 * (live ? pair : 0), i1 = i0 + 1;
-    const T w0 = wpre[i0], w1 = wpre[i1];
-    const uint64_t stream = sg_policy_evict_first();
-    V v[E];
-#pragma unroll
-    for (int e = 0; e < E; e++) {
-        const int n = t + e * NT;
-        v[e] = V{sg_ld_hint(sigma + (size_t)i0 * N + n, stream) * w0, sg_ld_hint(sigma + (size_t)i1 * N + n, stream) * w1};
-    }
-    fft<E, -1>(v, sm, N, log2n, t, twd);
+    const size_t per = 128 / sizeof(V);
+    return ((size_t)slots * sg_padded(N) + per - 1) / per * per;
+}
+// Row blocks cycle through a ring of SG_RING buffers: the inputs of block
+// j + 1 land in one buffer while block j is transformed in the next, and
+// the bulk stores out of block j - 1's buffer finish reading it meanwhile.
+#define SG_RING 3
+// dynamic shared memory of a row pass: the ring plus alignment slack
+template <typename V>
+__host__ __device__ __forceinline__ size_t row_smem_bytes(int N, int slots)
+{
+    return SG_RING * row_buf_elems<V>(N, slots) * sizeof(V) + 128;
+}
+__device__ __forceinline__ unsigned char* align128(unsigned char* p)
+{
+    return reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(p) + 127) & ~(uintptr_t)127);
+}
+// modes per tensor-copy box
+__host__ __device__ __forceinline__ int row_box_modes(int half) { return half < 256 ? half : 256; }
+
+__device__ __forceinline__ void sg_cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// wait until at most the latest bulk-store group of this thread is still reading shared memory
+__device__ __forceinline__ void sg_bulk_wait_read_prev() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+__device__ __forceinline__ void sg_cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// Split Z = FFT(z_a + i z_b) of two real sequences into their half spectra
+// X_a[m], X_b[m] (m = t + e NT < N/2; mode 0 packs (DC, Nyquist)).  sm is
+// the slot's exchange area, free on entry; every thread of the slot calls.
+template <int E, typename V, typename T>
+__device__ __forceinline__ void split_real_pair(const V (&v)[E], V* sm, int N, int t, V (&xa)[E / 2], V (&xb)[E / 2],
+                                                const SgSyncSlot& sync)
+{
+    const int NT = N / E;
 #pragma unroll
     for (int e = 0; e < E; e++) sm[sg_pad(t + e * NT)] = v[e];
-    __syncthreads();
+    sync();
     const T h = (T)0.5;
-    V x0[E / 2], x1[E / 2];
 #pragma unroll
     for (int e = 0; e < E / 2; e++) {
         const int m = t + e * NT;
         const V z = v[e], zc = cconj(sm[sg_pad((N - m) & (N - 1))]);
         if (m == 0) {
             const V zn = sm[sg_pad(N / 2)];
-            x0[e] = V{z.x, zn.x};
-            x1[e] = V{z.y, zn.y};
+            xa[e] = V{z.x, zn.x};
+            xb[e] = V{z.y, zn.y};
         } else {
-            x0[e] = cscale(cadd(z, zc), h);
+            xa[e] = cscale(cadd(z, zc), h);
             const V d = csub(z, zc);
-            x1[e] = V{d.y * h, -d.x * h};  // d / 2i
+            xb[e] = V{d.y * h, -d.x * h};  // d / 2i
         }
     }
-    __syncthreads();  // every mirror read is done: the buffers become the stage
-    const int R = 2 * slots;
-    if (live) {
+    sync();  // every mirror read is done: the slot's area is free
+}
+
+// Tensor stores of a staged mode-major block S[m R + r], box j issued by
+// lane j mod 32 of the calling warp (each lane then commits its own group).
+template <typename V>
+__device__ __forceinline__ void stage_store_map(const CUtensorMap* map, const V* S, int half, int ib, int R, int lane)
+{
+    constexpr int c = sizeof(V) / 8;  // 8-byte elements per complex value
+    const int MB = row_box_modes(half);
+    const uint64_t keep = sg_policy_evict_last();  // the next pass reads it from L2
+    for (int j = lane; j < half / MB; j += 32) sg_tma_store_2d(map, c * ib, j * MB, S + (size_t)j * MB * R, keep);
+}
+// Tensor loads of a mode-major block into S[m R + r], completing on bar
+// (whose expected bytes the caller has set); box j issued by lane j mod 32.
+template <typename V>
+__device__ __forceinline__ void stage_load_map(V* S, const CUtensorMap* map, int half, int ib, int R, uint64_t* bar,
+                                               int lane)
+{
+    constexpr int c = sizeof(V) / 8;
+    const int MB = row_box_modes(half);
+    const uint64_t drop = sg_policy_evict_first();
+    for (int j = lane; j < half / MB; j += 32) sg_tma_load_2d(S + (size_t)j * MB * R, map, c * ib, j * MB, bar, drop);
+}
+
+// Common prologue of the mbarrier-fed row passes: barriers initialised and
+// the first row block requested.  Returns through the loop helpers below.
+#define SG_ROWS_BARRIER_INIT()                      \
+    if (threadIdx.x == 0)                           \
+        for (int q = 0; q < SG_RING; q++) sg_mbar_init(&bar[q], 1); \
+    __syncthreads()
+
+// ===========================================================================
+// Forward P1: rows (i0, i1) packed as z = w_i0 + i w_i1, FFT along phi,
+// split into X_i0, X_i1, staged and stored mode-major.  R = 2 slots rows per
+// row block; the block's density rows arrive as one bulk copy.
+// ===========================================================================
+template <typename T, int E>
+__global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 512) k_fwd_rows(const T* __restrict__ sigma, const T* __restrict__ wpre,
+                                                  typename CX<T>::t* __restrict__ A, int nu, int nphi, int log2n,
+                                                  const typename CX<T>::t* __restrict__ tw, int* err,
+                                                  const __grid_constant__ CUtensorMap mapA, int use_map)
+{
+    typedef typename CX<T>::t V;
+    extern __shared__ __align__(128) unsigned char smraw[];
+    __shared__ __align__(8) uint64_t bar[SG_RING];
+    const int N = nphi, NT = N / E, half = N / 2;
+    const int slot = threadIdx.x / NT, t = threadIdx.x % NT;
+    const int slots = blockDim.x / NT;
+    const int R = 2 * slots, nblk = (nu + R - 1) / R;
+    const int lane = threadIdx.x & 31;
+    const bool producer = threadIdx.x < 32;
+    const size_t bufE = row_buf_elems<V>(N, slots);
+    V* const ring = reinterpret_cast<V*>(align128(smraw));
+    const Twd<E, V> twd = make_twd<E>(log2n, t, tw);
+    const SgSyncSlot ssync = slot_sync(slot, NT, slots);
+    SG_ROWS_BARRIER_INIT();
+    auto issue = [&](int rb, int q) {  // thread 0: the block's density rows into buffer q
+        const int rows = min(R, nu - rb * R);
+        const uint32_t bytes = (uint32_t)((size_t)rows * N * sizeof(T));
+        sg_mbar_expect_tx(&bar[q], bytes);
+        sg_bulk_g2s_hint(ring + q * bufE, sigma + (size_t)rb * R * N, bytes, &bar[q], sg_policy_evict_first());
+    };
+    if (threadIdx.x == 0 && blockIdx.x < nblk) issue(blockIdx.x, 0);
+    int it = 0;
+    for (int rb = blockIdx.x; rb < nblk; rb += gridDim.x, it++) {
+        const int q = it % SG_RING, qn = (it + 1) % SG_RING;
+        V* const cur = ring + q * bufE;
+        const bool more = rb + (int)gridDim.x < nblk;
+        __syncthreads();  // nobody reads or writes buffer qn any more
+        if (producer) {
+            if (use_map) sg_bulk_wait_read_prev();  // the tensor stores out of buffer qn have read it
+            __syncwarp();
+            if (threadIdx.x == 0 && more) {
+                sg_fence_proxy_async();
+                issue(rb + gridDim.x, qn);
+            }
+        }
+        if (__syncthreads_or(!sg_mbar_wait_bounded(&bar[q], (it / SG_RING) & 1, err, 1))) {
+            if (more) sg_mbar_wait_bounded(&bar[qn], ((it + 1) / SG_RING) & 1, err, 1);
+            if (use_map && producer) sg_bulk_wait_read();
+            return;  // inputs never arrived
+        }
+        const int pair = rb * slots + slot;
+        const bool live = pair < nu / 2;
+        const int i0 = 2 * (live ? pair : 0);
+        const T w0 = wpre[i0], w1 = wpre[i0 + 1];
+        const T* rows = reinterpret_cast<const T*>(cur) + (size_t)(2 * slot) * N;
+        V v[E];
 #pragma unroll
-        for (int e = 0; e < E / 2; e++) {
-            V* d = small + (t + e * NT) * R + 2 * slot;
-            d[0] = x0[e];
-            d[1] = x1[e];
+        for (int e = 0; e < E; e++) {
+            const int n = t + e * NT;
+            v[e] = V{rows[n] * w0, rows[N + n] * w1};
+        }
+        V* sm = cur + slot * sg_padded(N);
+        __syncthreads();  // the rows overlap other slots' exchange areas: all read before any slot transforms
+        fft<E, -1>(v, sm, N, log2n, t, twd, ssync);
+        V x0[E / 2], x1[E / 2];
+        split_real_pair<E, V, T>(v, sm, N, t, x0, x1, ssync);
+        __syncthreads();  // the stage spans every slot's area
+        if (live) {
+#pragma unroll
+            for (int e = 0; e < E / 2; e++) {
+                V* d = cur + (t + e * NT) * R + 2 * slot;
+                d[0] = x0[e];
+                d[1] = x1[e];
+            }
+        }
+        if (use_map) sg_fence_proxy_async();
+        __syncthreads();
+        if (!use_map) {
+            stage_store(A, cur, nu, half, rb * R, R);
+        } else if (producer) {
+            stage_store_map(&mapA, cur, half, rb * R, R, lane);
+            sg_bulk_commit();
         }
     }
-    __syncthreads();
-    stage_store(A, small, nu, half, blockIdx.x * R, R);
+    if (use_map && producer) sg_bulk_wait_read();
 }
 
 // ===========================================================================
@@ -212,10 +345,11 @@ __host__ __device__ __forceinline__ size_t cols_smem_bytes(int nu)
 }
 
 // NTB: the block size the kernel is compiled for (L / E threads); FP32
-// blocks of 256 threads are held to SG_COLS_MINB per SM (3: registers <= 80,
-// which the shared memory of N_u = 2048 also allows)
+// blocks of 256 threads are compiled for SG_COLS_MINB per SM (2: up to 128
+// registers, no spills; 3 would fit the shared memory of N_u = 2048 but
+// forces spills)
 #ifndef SG_COLS_MINB
-#define SG_COLS_MINB 3
+#define SG_COLS_MINB 2
 #endif
 #define SG_COLS_BOUNDS(T, NTB) __launch_bounds__(NTB, (sizeof(T) == 4 && NTB == 256) ? SG_COLS_MINB : 1)
 
@@ -263,177 +397,261 @@ __global__ void SG_COLS_BOUNDS(T, NTB) k_fwd_cols(const typename CX<T>::t* __res
     V v[E];
 #pragma unroll
     for (int e = 0; e < E; e++) v[e] = (e < E / 2) ? sm[t + e * NT] : V{0, 0};  // rows >= nu: zero pad
-    fft<E, -1>(v, sm, L, log2L, t, twd);  // the spectra land meanwhile
-    if (__syncthreads_or(!sg_mbar_wait_bounded(&bar[1], 0, err, 1))) return;
-    if (m == 0) {
-        // v holds the FFT of (DC + i Nyquist): separate the two real
-        // sequences and apply the kernels of modes 0 and N_phi/2
+    // Three transforms share one copy of the FFT code: the forward one, then
+    // the two inverse ones as conj(FFT(conj Y)).
+#pragma unroll 1
+    for (int pass = 0; pass < 3; pass++) {
+        fft<E, -1>(v, sm, L, log2L, t, twd);  // pass 0: the spectra land meanwhile
+        if (pass == 0) {
+            if (__syncthreads_or(!sg_mbar_wait_bounded(&bar[1], 0, err, 1))) return;
+            if (m == 0) {
+                // v holds the FFT of (DC + i Nyquist): separate the two real
+                // sequences and apply the kernels of modes 0 and N_phi/2; the
+                // phi force of both modes vanishes
 #pragma unroll
-        for (int e = 0; e < E; e++) sm[sg_pad(t + e * NT)] = v[e];
-        __syncthreads();
-        V y[E];
+                for (int e = 0; e < E; e++) sm[sg_pad(t + e * NT)] = v[e];
+                __syncthreads();
 #pragma unroll
-        for (int e = 0; e < E; e++) {
-            const int k = t + e * NT;
-            const V z = v[e], zc = cconj(sm[sg_pad((L - k) & (L - 1))]);
-            const V a = cscale(cadd(z, zc), (T)0.5);
-            const V d = csub(z, zc);
-            const V b = V{d.y * (T)0.5, -d.x * (T)0.5};
-            y[e] = cadd(cmul(a, khat_r_s(kr_s, k, L, nu)), cmuli(cmul(b, khat_r_s(kp_s, k, L, nu))));
+                for (int e = 0; e < E; e++) {
+                    const int k = t + e * NT;
+                    const V z = v[e], zc = cconj(sm[sg_pad((L - k) & (L - 1))]);
+                    const V a = cscale(cadd(z, zc), (T)0.5);
+                    const V d = csub(z, zc);
+                    const V b = V{d.y * (T)0.5, -d.x * (T)0.5};
+                    v[e] = cconj(cadd(cmul(a, khat_r_s(kr_s, k, L, nu)), cmuli(cmul(b, khat_r_s(kp_s, k, L, nu)))));
+                }
+                __syncthreads();  // every read of the spectra is done
+#pragma unroll
+                for (int e = 0; e < E; e++) ks[t + e * NT] = V{0, 0};
+            } else {
+                // conj of the phi product parked in the exchange buffer, then
+                // copied over the spectra; conj of the r product in place
+#pragma unroll
+                for (int e = 0; e < E; e++) {
+                    const int k = t + e * NT;
+                    sm[sg_pad(k)] = cconj(cmul(v[e], khat_p_s(kp_s, k, L, nu)));
+                    v[e] = cconj(cmul(v[e], khat_r_s(kr_s, k, L, nu)));
+                }
+                __syncthreads();  // every read of the spectra is done
+#pragma unroll
+                for (int e = 0; e < E; e++) ks[t + e * NT] = sm[sg_pad(t + e * NT)];
+            }
+        } else {
+            V* out = (pass == 1 ? Br : Cp) + (size_t)m * nu;
+#pragma unroll
+            for (int e = 0; e < E / 2; e++) sg_st_hint(out + t + e * NT, cconj(v[e]), keep);  // crop to N_u rows
+            if (pass == 1) {
+#pragma unroll
+                for (int e = 0; e < E; e++) v[e] = ks[t + e * NT];
+            }
         }
-        fft<E, +1>(y, sm, L, log2L, t, twd);
-#pragma unroll
-        for (int e = 0; e < E / 2; e++) {
-            sg_st_hint(Br + t + e * NT, y[e], keep);
-            sg_st_hint(Cp + t + e * NT, V{0, 0}, keep);
-        }
-        return;
     }
-    // phi product into the (now free) exchange buffer, r product in place
-#pragma unroll
-    for (int e = 0; e < E; e++) {
-        const int k = t + e * NT;
-        sm[sg_pad(k)] = cmul(v[e], khat_p_s(kp_s, k, L, nu));
-        v[e] = cmul(v[e], khat_r_s(kr_s, k, L, nu));
-    }
-    __syncthreads();  // every read of the spectra is done
-#pragma unroll
-    for (int e = 0; e < E; e++) ks[t + e * NT] = sm[sg_pad(t + e * NT)];  // park the phi product
-    fft<E, +1>(v, sm, L, log2L, t, twd);
-#pragma unroll
-    for (int e = 0; e < E / 2; e++) sg_st_hint(Br + (size_t)m * nu + t + e * NT, v[e], keep);
-#pragma unroll
-    for (int e = 0; e < E; e++) v[e] = ks[t + e * NT];
-    fft<E, +1>(v, sm, L, log2L, t, twd);
-#pragma unroll
-    for (int e = 0; e < E / 2; e++) sg_st_hint(Cp + (size_t)m * nu + t + e * NT, v[e], keep);
 }
 
 // ===========================================================================
 // Forward P3: row i, Zhat = Fhat_r + i Fhat_phi (Hermitian halves expanded),
-// inverse FFT, F_r = Re, F_phi = Im, times beta^{-p i}.
+// inverse FFT, F_r = Re, F_phi = Im, times beta^{-p i}.  Each slot takes two
+// rows of a row block (R = 2 slots rows), one after the other.  Shared
+// memory: the stage of the block's B and C rows (S[m R + r], C after B) and
+// the slots' FFT exchange areas apart from it, so that once both of its
+// rows are read into registers the stage takes the next block's inputs
+// (tensor copies, or cp.async gathers without maps) during the second FFT.
 // ===========================================================================
-template <typename T, int E>
-__global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 512) k_fwd_rows_inv(const typename CX<T>::t* __restrict__ Br,
+template <typename V>
+__host__ __device__ __forceinline__ size_t rows_inv_smem_bytes(int N, int slots)
+{
+    const size_t stage = (size_t)2 * slots * N * sizeof(V);  // B and C, R = 2 slots rows
+    return stage + (size_t)slots * sg_padded(N) * sizeof(V) + 128;
+}
+
+template <typename T, int E, int NTB>
+__global__ void __launch_bounds__(NTB, (sizeof(T) == 4 && NTB == 256) ? 2 : 1) k_fwd_rows_inv(const typename CX<T>::t* __restrict__ Br,
                                                       const typename CX<T>::t* __restrict__ Cp,
                                                       const T* __restrict__ wpost, T* __restrict__ Fr,
                                                       T* __restrict__ Fp, int nu, int nphi, int log2n,
-                                                      const typename CX<T>::t* __restrict__ tw)
+                                                      const typename CX<T>::t* __restrict__ tw, int* err,
+                                                      const __grid_constant__ CUtensorMap mapB,
+                                                      const __grid_constant__ CUtensorMap mapC, int use_map)
 {
     typedef typename CX<T>::t V;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    V* small = reinterpret_cast<V*>(smraw);
+    extern __shared__ __align__(128) unsigned char smraw[];
+    __shared__ __align__(8) uint64_t bar;
     const int N = nphi, NT = N / E, half = N / 2;
     const int slot = threadIdx.x / NT, t = threadIdx.x % NT;
-    const Twd<E, V> twd = make_twd<E>(log2n, t, tw);
     const int slots = blockDim.x / NT;
-    V* sm = small + slot * sg_padded(N);
-    const int i0 = blockIdx.x * slots + slot;
-    const bool live = i0 < nu;
-    const int i = live ? i0 : 0;
-    // stage rows [ib, ib + R) of both half spectra: Sb[m R + r], Sc[m R + r]
-    const int R = slots, ib = blockIdx.x * slots;
-    V* Sb = small;
-    V* Sc = small + (size_t)R * half;
-    stage_load(Sb, Br, nu, half, ib, R);
-    stage_load(Sc, Cp, nu, half, ib, R);
-    sg_cp_async_wait_all();
+    const int R = 2 * slots, nblk = (nu + R - 1) / R;
+    const int lane = threadIdx.x & 31;
+    V* const Sb = reinterpret_cast<V*>(align128(smraw));
+    V* const Sc = Sb + (size_t)R * half;
+    V* const sm = Sc + (size_t)R * half + (size_t)slot * sg_padded(N);  // this slot's exchange area
+    const Twd<E, V> twd = make_twd<E>(log2n, t, tw);
+    const SgSyncSlot ssync = slot_sync(slot, NT, slots);
+    if (threadIdx.x == 0) sg_mbar_init(&bar, 1);
     __syncthreads();
-    V v[E];
-#pragma unroll
-    for (int e = 0; e < E; e++) {
-        const int n = t + e * NT;
-        V z;
-        if (e < E / 2) {
-            if (n == 0) {
-                z = V{Sb[slot].x, 0};
-            } else {
-                const V a = Sb[n * R + slot], b = Sc[n * R + slot];
-                z = V{a.x - b.y, a.y + b.x};  // a + i b
-            }
+    auto issue = [&](int rb) {  // use_map: warp 0; else every thread
+        if (use_map) {
+            if (lane == 0) sg_mbar_expect_tx(&bar, (uint32_t)(2 * (size_t)half * R * sizeof(V)));
+            __syncwarp();
+            stage_load_map(Sb, &mapB, half, rb * R, R, &bar, lane);
+            stage_load_map(Sc, &mapC, half, rb * R, R, &bar, lane);
         } else {
-            if (n == half) {
-                z = V{Sb[slot].y, 0};
-            } else {
-                const V a = Sb[(N - n) * R + slot], b = Sc[(N - n) * R + slot];
-                z = V{a.x + b.y, -a.y + b.x};  // conj a + i conj b
+            stage_load(Sb, Br, nu, half, rb * R, R);
+            stage_load(Sc, Cp, nu, half, rb * R, R);
+            sg_cp_async_commit();
+        }
+    };
+    if (blockIdx.x < nblk && (!use_map || threadIdx.x < 32)) issue(blockIdx.x);
+    int it = 0;
+    for (int rb = blockIdx.x; rb < nblk; rb += gridDim.x, it++) {
+        const bool more = rb + (int)gridDim.x < nblk;
+        if (use_map) {
+            if (__syncthreads_or(!sg_mbar_wait_bounded(&bar, it & 1, err, 1))) return;  // inputs never arrived
+        } else {
+            asm volatile("cp.async.wait_all;" ::: "memory");
+            __syncthreads();
+        }
+#pragma unroll 1
+        for (int h = 0; h < 2; h++) {
+            const int r = 2 * slot + h;  // row of the block
+            V v[E];
+#pragma unroll
+            for (int e = 0; e < E; e++) {
+                const int n = t + e * NT;
+                V z;
+                if (e < E / 2) {
+                    if (n == 0) {
+                        z = V{Sb[r].x, 0};
+                    } else {
+                        const V a = Sb[n * R + r], b = Sc[n * R + r];
+                        z = V{a.x - b.y, a.y + b.x};  // a + i b
+                    }
+                } else {
+                    if (n == half) {
+                        z = V{Sb[r].y, 0};
+                    } else {
+                        const V a = Sb[(N - n) * R + r], b = Sc[(N - n) * R + r];
+                        z = V{a.x + b.y, -a.y + b.x};  // conj a + i conj b
+                    }
+                }
+                v[e] = z;
+            }
+            if (h == 1) {
+                __syncthreads();  // the stage is read: it takes the next block's rows
+                if (more && (!use_map || threadIdx.x < 32)) {
+                    if (use_map) sg_fence_proxy_async();
+                    issue(rb + gridDim.x);
+                }
+            }
+            fft<E, +1>(v, sm, N, log2n, t, twd, ssync);
+            const int i = rb * R + r;
+            if (i < nu) {
+                const T w = wpost[i];
+#pragma unroll
+                for (int e = 0; e < E; e++) {
+                    const int n = t + e * NT;
+                    Fr[(size_t)i * N + n] = v[e].x * w;
+                    Fp[(size_t)i * N + n] = v[e].y * w;
+                }
             }
         }
-        v[e] = z;
     }
-    fft<E, +1>(v, sm, N, log2n, t, twd);  // its first exchange waits for every thread's stage reads
-    if (!live) return;
-    const T w = wpost[i];
-#pragma unroll
-    for (int e = 0; e < E; e++) {
-        const int n = t + e * NT;
-        Fr[(size_t)i * N + n] = v[e].x * w;
-        Fp[(size_t)i * N + n] = v[e].y * w;
-    }
+    if (!use_map) asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
 // ===========================================================================
 // Backward P1b: row i, z = (gF_r + i gF_phi) beta^{-p i}, FFT, split into
-// the half spectra of gF_r (-> A) and gF_phi (-> C), mode-major.
+// the half spectra of gF_r (-> A) and gF_phi (-> C), staged and stored
+// mode-major.  R = slots rows per row block, arriving as two bulk copies.
 // ===========================================================================
 template <typename T, int E>
 __global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 512) k_bwd_rows(const T* __restrict__ gr, const T* __restrict__ gp,
                                                   const T* __restrict__ wpost, typename CX<T>::t* __restrict__ A,
                                                   typename CX<T>::t* __restrict__ C, int nu, int nphi, int log2n,
-                                                  const typename CX<T>::t* __restrict__ tw)
+                                                  const typename CX<T>::t* __restrict__ tw, int* err,
+                                                  const __grid_constant__ CUtensorMap mapA,
+                                                  const __grid_constant__ CUtensorMap mapC, int use_map)
 {
     typedef typename CX<T>::t V;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    V* small = reinterpret_cast<V*>(smraw);
-    const int N = nphi, NT = N / E;
+    extern __shared__ __align__(128) unsigned char smraw[];
+    __shared__ __align__(8) uint64_t bar[SG_RING];
+    const int N = nphi, NT = N / E, half = N / 2;
     const int slot = threadIdx.x / NT, t = threadIdx.x % NT;
-    const Twd<E, V> twd = make_twd<E>(log2n, t, tw);
     const int slots = blockDim.x / NT;
-    V* sm = small + slot * sg_padded(N);
-    const int i0 = blockIdx.x * slots + slot;
-    const bool live = i0 < nu;
-    const int i = live ? i0 : 0;
-    const T w = wpost[i];
-    V v[E];
+    const int R = slots, nblk = (nu + R - 1) / R;
+    const int lane = threadIdx.x & 31;
+    const bool producer = threadIdx.x < 32;
+    const size_t bufE = row_buf_elems<V>(N, slots);
+    V* const ring = reinterpret_cast<V*>(align128(smraw));
+    const Twd<E, V> twd = make_twd<E>(log2n, t, tw);
+    const SgSyncSlot ssync = slot_sync(slot, NT, slots);
+    SG_ROWS_BARRIER_INIT();
+    auto issue = [&](int rb, int q) {  // thread 0: gF_r rows, then gF_phi rows, into buffer q
+        const int rows = min(R, nu - rb * R);
+        const uint32_t bytes = (uint32_t)((size_t)rows * N * sizeof(T));
+        const uint64_t pol = sg_policy_evict_first();
+        V* dst = ring + q * bufE;
+        sg_mbar_expect_tx(&bar[q], 2 * bytes);
+        sg_bulk_g2s_hint(dst, gr + (size_t)rb * R * N, bytes, &bar[q], pol);
+        sg_bulk_g2s_hint(reinterpret_cast<T*>(dst) + (size_t)R * N, gp + (size_t)rb * R * N, bytes, &bar[q], pol);
+    };
+    if (threadIdx.x == 0 && blockIdx.x < nblk) issue(blockIdx.x, 0);
+    int it = 0;
+    for (int rb = blockIdx.x; rb < nblk; rb += gridDim.x, it++) {
+        const int q = it % SG_RING, qn = (it + 1) % SG_RING;
+        V* const cur = ring + q * bufE;
+        const bool more = rb + (int)gridDim.x < nblk;
+        __syncthreads();
+        if (producer) {
+            if (use_map) sg_bulk_wait_read_prev();
+            __syncwarp();
+            if (threadIdx.x == 0 && more) {
+                sg_fence_proxy_async();
+                issue(rb + gridDim.x, qn);
+            }
+        }
+        if (__syncthreads_or(!sg_mbar_wait_bounded(&bar[q], (it / SG_RING) & 1, err, 1))) {
+            if (more) sg_mbar_wait_bounded(&bar[qn], ((it + 1) / SG_RING) & 1, err, 1);
+            if (use_map && producer) sg_bulk_wait_read();
+            return;
+        }
+        const int i = rb * R + slot;
+        const bool live = i < nu;
+        const T w = wpost[live ? i : 0];
+        const T* rr = reinterpret_cast<const T*>(cur) + (size_t)slot * N;
+        const T* rp = rr + (size_t)R * N;
+        V v[E];
 #pragma unroll
-    for (int e = 0; e < E; e++) {
-        const int n = t + e * NT;
-        v[e] = V{gr[(size_t)i * N + n] * w, gp[(size_t)i * N + n] * w};
-    }
-    fft<E, -1>(v, sm, N, log2n, t, twd);
+        for (int e = 0; e < E; e++) {
+            const int n = t + e * NT;
+            v[e] = V{rr[n] * w, rp[n] * w};
+        }
+        V* sm = cur + slot * sg_padded(N);
+        __syncthreads();  // the rows overlap other slots' exchange areas: all read before any slot transforms
+        fft<E, -1>(v, sm, N, log2n, t, twd, ssync);
+        V x0[E / 2], x1[E / 2];
+        split_real_pair<E, V, T>(v, sm, N, t, x0, x1, ssync);
+        __syncthreads();  // the stages span every slot's area
+        V* Sa = cur;
+        V* Sc = cur + (size_t)R * half;
+        if (live) {
 #pragma unroll
-    for (int e = 0; e < E; e++) sm[sg_pad(t + e * NT)] = v[e];
-    __syncthreads();
-    const T h = (T)0.5;
-    V x0[E / 2], x1[E / 2];
-#pragma unroll
-    for (int e = 0; e < E / 2; e++) {
-        const int m = t + e * NT;
-        const V z = v[e], zc = cconj(sm[sg_pad((N - m) & (N - 1))]);
-        if (m == 0) {
-            const V zn = sm[sg_pad(N / 2)];
-            x0[e] = V{z.x, zn.x};
-            x1[e] = V{z.y, zn.y};
-        } else {
-            x0[e] = cscale(cadd(z, zc), h);
-            const V d = csub(z, zc);
-            x1[e] = V{d.y * h, -d.x * h};
+            for (int e = 0; e < E / 2; e++) {
+                Sa[(t + e * NT) * R + slot] = x0[e];
+                Sc[(t + e * NT) * R + slot] = x1[e];
+            }
+        }
+        if (use_map) sg_fence_proxy_async();
+        __syncthreads();
+        if (!use_map) {
+            stage_store(A, Sa, nu, half, rb * R, R);
+            stage_store(C, Sc, nu, half, rb * R, R);
+        } else if (producer) {
+            stage_store_map(&mapA, Sa, half, rb * R, R, lane);
+            stage_store_map(&mapC, Sc, half, rb * R, R, lane);
+            sg_bulk_commit();
         }
     }
-    __syncthreads();  // mirror reads done: the buffers become the stages of A and C
-    const int R = slots, half = N / 2;
-    V* Sa = small;
-    V* Sc = small + (size_t)R * half;
-    if (live) {
-#pragma unroll
-        for (int e = 0; e < E / 2; e++) {
-            Sa[(t + e * NT) * R + slot] = x0[e];
-            Sc[(t + e * NT) * R + slot] = x1[e];
-        }
-    }
-    __syncthreads();
-    stage_store(A, Sa, nu, half, blockIdx.x * R, R);
-    stage_store(C, Sc, nu, half, blockIdx.x * R, R);
+    if (use_map && producer) sg_bulk_wait_read();
 }
 
 // ===========================================================================
@@ -489,98 +707,188 @@ __global__ void SG_COLS_BOUNDS(T, NTB) k_bwd_cols(const typename CX<T>::t* __res
         sg_mbar_wait_bounded(&bar[1], 0, err, 1);
         return;
     }
-    V v[E], y[E];
+    V v[E];
 #pragma unroll
     for (int e = 0; e < E; e++) v[e] = (e < E / 2) ? sm[t + e * NT] : V{0, 0};
-    fft<E, -1>(v, sm, L, log2L, t, twd);
-    if (__syncthreads_or(!sg_mbar_wait_bounded(&bar[1], 0, err, 1))) return;
-    if (m == 0) {
-#pragma unroll
-        for (int e = 0; e < E; e++) sm[sg_pad(t + e * NT)] = v[e];
-        __syncthreads();
-#pragma unroll
-        for (int e = 0; e < E; e++) {
-            const int k = t + e * NT;
-            const V z = v[e], zc = cconj(sm[sg_pad((L - k) & (L - 1))]);
-            const V a = cscale(cadd(z, zc), (T)0.5);
-            const V d = csub(z, zc);
-            const V b = V{d.y * (T)0.5, -d.x * (T)0.5};
-            y[e] = cadd(cmul(a, cconj(khat_r_s(kr_s, k, L, nu))), cmuli(cmul(b, cconj(khat_r_s(kp_s, k, L, nu)))));
-        }
-    } else {
-#pragma unroll
-        for (int e = 0; e < E; e++) y[e] = cmul(v[e], cconj(khat_r_s(kr_s, t + e * NT, L, nu)));
-#pragma unroll
-        for (int e = 0; e < E; e++) v[e] = (e < E / 2) ? cs[t + e * NT] : V{0, 0};
+    // Three transforms share one copy of the FFT code: FFT of the A column,
+    // FFT of the C column, inverse FFT of the sum as conj(FFT(conj Y)).  The
+    // partial sum Y_r = X_a conj(Khat_r) is parked at st[0, L), over the C
+    // column (read first, element by element by the same thread) and the
+    // dead Khat_r.
+    V* st = cs;
+#pragma unroll 1
+    for (int pass = 0; pass < 3; pass++) {
         fft<E, -1>(v, sm, L, log2L, t, twd);
+        if (pass == 0) {
+            if (__syncthreads_or(!sg_mbar_wait_bounded(&bar[1], 0, err, 1))) return;
+            if (m == 0) {
 #pragma unroll
-        for (int e = 0; e < E; e++) y[e] = cadd(y[e], cmul(v[e], cconj(khat_p_s(kp_s, t + e * NT, L, nu))));
+                for (int e = 0; e < E; e++) sm[sg_pad(t + e * NT)] = v[e];
+                __syncthreads();
+#pragma unroll
+                for (int e = 0; e < E; e++) {
+                    const int k = t + e * NT;
+                    const V z = v[e], zc = cconj(sm[sg_pad((L - k) & (L - 1))]);
+                    const V a = cscale(cadd(z, zc), (T)0.5);
+                    const V d = csub(z, zc);
+                    const V b = V{d.y * (T)0.5, -d.x * (T)0.5};
+                    v[e] = cadd(cmul(a, cconj(khat_r_s(kr_s, k, L, nu))), cmuli(cmul(b, cconj(khat_r_s(kp_s, k, L, nu)))));
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < E; e++) v[e] = cmul(v[e], cconj(khat_r_s(kr_s, t + e * NT, L, nu)));
+            }
+            __syncthreads();  // Khat_r (and the mirror buffer) fully read
+#pragma unroll
+            for (int e = 0; e < E; e++) {
+                const int k = t + e * NT;
+                if (e < E / 2) {
+                    const V c = cs[k];
+                    st[k] = v[e];
+                    v[e] = c;
+                } else {
+                    st[k] = v[e];
+                    v[e] = V{0, 0};
+                }
+            }
+        } else if (pass == 1) {
+            // mode 0: the phi kernel vanishes at modes 0 and N_phi/2
+#pragma unroll
+            for (int e = 0; e < E; e++) {
+                const int k = t + e * NT;
+                const V y = m == 0 ? st[k] : cadd(st[k], cmul(v[e], cconj(khat_p_s(kp_s, k, L, nu))));
+                v[e] = cconj(y);
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < E / 2; e++) sg_st_hint(B + (size_t)m * nu + t + e * NT, cconj(v[e]), keep);
+        }
     }
-    fft<E, +1>(y, sm, L, log2L, t, twd);
-#pragma unroll
-    for (int e = 0; e < E / 2; e++) sg_st_hint(B + (size_t)m * nu + t + e * NT, y[e], keep);
 }
 
 // ===========================================================================
 // Backward P3b: rows (i0, i1): Zhat = S_i0 + i S_i1 with S the Hermitian
 // extension of each half spectrum; inverse FFT gives rows i0 (Re), i1 (Im).
+// R = 2 slots rows per row block, gathered from the mode-major B.
 // ===========================================================================
 template <typename T, int E>
 __global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 512) k_bwd_rows_inv(const typename CX<T>::t* __restrict__ B,
                                                       const T* __restrict__ wpre, T* __restrict__ gs, int nu,
-                                                      int nphi, int log2n, const typename CX<T>::t* __restrict__ tw)
+                                                      int nphi, int log2n, const typename CX<T>::t* __restrict__ tw,
+                                                      int* err, const __grid_constant__ CUtensorMap mapB, int use_map)
 {
     typedef typename CX<T>::t V;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    V* small = reinterpret_cast<V*>(smraw);
+    extern __shared__ __align__(128) unsigned char smraw[];
+    __shared__ __align__(8) uint64_t bar[SG_RING];
     const int N = nphi, NT = N / E, half = N / 2;
     const int slot = threadIdx.x / NT, t = threadIdx.x % NT;
-    const Twd<E, V> twd = make_twd<E>(log2n, t, tw);
     const int slots = blockDim.x / NT;
-    V* sm = small + slot * sg_padded(N);
-    const int pair = blockIdx.x * slots + slot;
-    const bool live = pair < nu / 2;
-    const int i0 = 2 * (live ? pair : 0), i1 = i0 + 1;
-    // stage rows [ib, ib + R) of B as Sb[m R + r]; this pair is r = 2 slot, 2 slot + 1
-    const int R = 2 * slots, ib = blockIdx.x * R;
-    V* Sb = small;
-    stage_load(Sb, B, nu, half, ib, R);
-    sg_cp_async_wait_all();
-    __syncthreads();
-    const V* b0 = Sb + 2 * slot;
-    const V* b1 = b0 + 1;
-    V v[E];
-#pragma unroll
-    for (int e = 0; e < E; e++) {
-        const int n = t + e * NT;
-        V s0, s1;
-        if (e < E / 2) {
-            if (n == 0) {
-                s0 = V{b0[0].x, 0};
-                s1 = V{b1[0].x, 0};
-            } else {
-                s0 = b0[n * R];
-                s1 = b1[n * R];
+    const int R = 2 * slots, nblk = (nu + R - 1) / R;
+    const int lane = threadIdx.x & 31;
+    const bool producer = threadIdx.x < 32;
+    const size_t bufE = row_buf_elems<V>(N, slots);
+    V* const ring = reinterpret_cast<V*>(align128(smraw));
+    const Twd<E, V> twd = make_twd<E>(log2n, t, tw);
+    const SgSyncSlot ssync = slot_sync(slot, NT, slots);
+    SG_ROWS_BARRIER_INIT();
+    auto issue = [&](int rb, int q) {
+        V* dst = ring + q * bufE;
+        if (use_map) {  // warp 0
+            if (lane == 0) sg_mbar_expect_tx(&bar[q], (uint32_t)((size_t)half * R * sizeof(V)));
+            __syncwarp();
+            stage_load_map(dst, &mapB, half, rb * R, R, &bar[q], lane);
+        } else {
+            stage_load(dst, B, nu, half, rb * R, R);
+        }
+    };
+    if (blockIdx.x < nblk && (!use_map || producer)) issue(blockIdx.x, 0);
+    if (!use_map) sg_cp_async_commit();
+    int it = 0;
+    for (int rb = blockIdx.x; rb < nblk; rb += gridDim.x, it++) {
+        const int q = it % SG_RING, qn = (it + 1) % SG_RING;
+        V* const cur = ring + q * bufE;
+        const bool more = rb + (int)gridDim.x < nblk;
+        __syncthreads();
+        if (use_map) {
+            if (producer) {
+                if (threadIdx.x == 0) sg_bulk_wait_read_prev();
+                __syncwarp();
+                if (more) {
+                    sg_fence_proxy_async();
+                    issue(rb + gridDim.x, qn);
+                }
+            }
+            if (__syncthreads_or(!sg_mbar_wait_bounded(&bar[q], (it / SG_RING) & 1, err, 1))) {
+                if (more) sg_mbar_wait_bounded(&bar[qn], ((it + 1) / SG_RING) & 1, err, 1);
+                if (threadIdx.x == 0) sg_bulk_wait_read();
+                return;
             }
         } else {
-            if (n == half) {
-                s0 = V{b0[0].y, 0};
-                s1 = V{b1[0].y, 0};
+            if (more) issue(rb + gridDim.x, qn);
+            sg_cp_async_commit();
+            sg_cp_async_wait_prev();
+            __syncthreads();
+        }
+        const V* b0s = cur + 2 * slot;  // this pair's rows are r = 2 slot, 2 slot + 1
+        const V* b1s = b0s + 1;
+        V v[E];
+#pragma unroll
+        for (int e = 0; e < E; e++) {
+            const int n = t + e * NT;
+            V s0, s1;
+            if (e < E / 2) {
+                if (n == 0) {
+                    s0 = V{b0s[0].x, 0};
+                    s1 = V{b1s[0].x, 0};
+                } else {
+                    s0 = b0s[n * R];
+                    s1 = b1s[n * R];
+                }
             } else {
-                s0 = cconj(b0[(N - n) * R]);
-                s1 = cconj(b1[(N - n) * R]);
+                if (n == half) {
+                    s0 = V{b0s[0].y, 0};
+                    s1 = V{b1s[0].y, 0};
+                } else {
+                    s0 = cconj(b0s[(N - n) * R]);
+                    s1 = cconj(b1s[(N - n) * R]);
+                }
+            }
+            v[e] = cadd(s0, cmuli(s1));
+        }
+        __syncthreads();  // the stage spans every slot's exchange area: all read before any slot transforms
+        fft<E, +1>(v, cur + slot * sg_padded(N), N, log2n, t, twd, ssync);
+        const int pair = rb * slots + slot;
+        const bool live = pair < nu / 2;
+        const int i0 = 2 * (live ? pair : 0);
+        const T w0 = wpre[i0], w1 = wpre[i0 + 1];
+        if (use_map) {
+            __syncthreads();  // every slot's transform is done before the rows are staged over their areas
+            T* g = reinterpret_cast<T*>(cur);  // rows [rb R, rb R + R) of gsigma, contiguous
+#pragma unroll
+            for (int e = 0; e < E; e++) {
+                const int n = t + e * NT;
+                g[(size_t)(2 * slot) * N + n] = v[e].x * w0;
+                g[(size_t)(2 * slot + 1) * N + n] = v[e].y * w1;
+            }
+            sg_fence_proxy_async();
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                sg_bulk_s2g(gs + (size_t)rb * R * N, g, (uint32_t)((size_t)min(R, nu - rb * R) * N * sizeof(T)));
+                sg_bulk_commit();
+            }
+        } else if (live) {
+#pragma unroll
+            for (int e = 0; e < E; e++) {
+                const int n = t + e * NT;
+                gs[(size_t)i0 * N + n] = v[e].x * w0;
+                gs[(size_t)(i0 + 1) * N + n] = v[e].y * w1;
             }
         }
-        v[e] = cadd(s0, cmuli(s1));
     }
-    fft<E, +1>(v, sm, N, log2n, t, twd);
-    if (!live) return;
-    const T w0 = wpre[i0], w1 = wpre[i1];
-#pragma unroll
-    for (int e = 0; e < E; e++) {
-        const int n = t + e * NT;
-        gs[(size_t)i0 * N + n] = v[e].x * w0;
-        gs[(size_t)i1 * N + n] = v[e].y * w1;
+    if (use_map) {
+        if (threadIdx.x == 0) sg_bulk_wait_read();
+    } else {
+        asm volatile("cp.async.wait_all;" ::: "memory");
     }
 }
 
@@ -697,6 +1005,81 @@ static cudaError_t set_smem(K kernel, size_t smem, bool carveout = false)
     return e;
 }
 
+// Grid of a persistent row pass: as many blocks as fit on the GPU at once
+// (each loops over row blocks), at most one per row block.
+template <typename K>
+static int persistent_grid(K kernel, int threads, size_t smem, int nblk, int sms)
+{
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, smem) != cudaSuccess || occ < 1) {
+        cudaGetLastError();
+        occ = 1;
+    }
+    const int g = occ * (sms > 0 ? sms : 1);
+    return nblk < g ? nblk : g;
+}
+
+// threads a row-pass block should have at least (several slots per block)
+static int row_min_threads(size_t elem) { return elem == 4 ? 512 : 64; }
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// cuTensorMapEncodeTiled through the runtime's driver entry points (no
+// link-time dependency on the driver library); null if unavailable
+static EncodeTiledFn tensor_map_encoder()
+{
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(f);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+void make_row_maps(int nu, int nphi, size_t elem, void* const bufs[3], SgRowMaps out[2])
+{
+    out[0].R = out[1].R = 0;
+    EncodeTiledFn enc = tensor_map_encoder();
+    if (!enc) return;
+    const int S = elem == 4 ? shape_for<float2>(nphi, row_min_threads(elem)).slots
+                            : shape_for<double2>(nphi, row_min_threads(elem)).slots;
+    const int half = nphi / 2, c = (int)(2 * elem / 8), MB = row_box_modes(half);
+    for (int k = 0; k < 2; k++) {
+        const int R = k == 0 ? S : 2 * S;
+        // inner box of at least 16 bytes and at most 256 elements; 128-byte
+        // aligned boxes in shared memory
+        if (nphi < 32 || c * R < 2 || c * R > 256 || R > nu || ((size_t)MB * c * R * 8) % 128) continue;
+        const cuuint64_t dims[2] = {(cuuint64_t)c * nu, (cuuint64_t)half};
+        const cuuint64_t strides[1] = {(cuuint64_t)c * nu * 8};
+        const cuuint32_t box[2] = {(cuuint32_t)(c * R), (cuuint32_t)MB};
+        const cuuint32_t estr[2] = {1, 1};
+        bool ok = true;
+        for (int b = 0; b < 3 && ok; b++)
+            ok = enc(&out[k].m[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, bufs[b], dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+        if (ok) out[k].R = R;
+    }
+}
+
+// the map of buffer b for row blocks of R rows, or null
+static const CUtensorMap* row_map(const PlanView& p, int R, int b, int nphi)
+{
+    if (!p.maps || nphi < 32) return nullptr;
+    for (int k = 0; k < 2; k++)
+        if (p.maps[k].R == R) return &p.maps[k].m[b];
+    return nullptr;
+}
+
 #define SG_DISPATCH_E(E, ...)                   \
     do {                                        \
         if ((E) == 16) {                        \
@@ -723,12 +1106,15 @@ cudaError_t launch_forward(const PlanView& p, const T* sigma, T* Fr, T* Fp, cuda
     cudaError_t err;
     if (ev && (err = cudaEventRecord(ev[0], st)) != cudaSuccess) return err;
     {
-        Shape s = shape_for<V>(p.nphi, sizeof(T) == 8 ? 64 : 512);
-        const int grid = (p.nu / 2 + s.slots - 1) / s.slots;
+        Shape s = shape_for<V>(p.nphi, row_min_threads(sizeof(T)));
+        const int R = 2 * s.slots, nblk = (p.nu + R - 1) / R;
+        const size_t smem = row_smem_bytes<V>(p.nphi, s.slots);
+        const CUtensorMap* mA = row_map(p, R, 0, p.nphi);
         SG_DISPATCH_E(s.E, {
             auto k = k_fwd_rows<T, EE>;
-            if ((err = set_smem(k, s.smem)) != cudaSuccess) return err;
-            k<<<grid, s.threads, s.smem, st>>>(sigma, (const T*)p.wpre, A, p.nu, p.nphi, ln, tw);
+            if ((err = set_smem(k, smem, true)) != cudaSuccess) return err;
+            k<<<persistent_grid(k, s.threads, smem, nblk, p.sms), s.threads, smem, st>>>(
+                sigma, (const T*)p.wpre, A, p.nu, p.nphi, ln, tw, p.err, mA ? *mA : CUtensorMap{}, mA != nullptr);
         });
     }
     if (ev && (err = cudaEventRecord(ev[1], st)) != cudaSuccess) return err;
@@ -745,12 +1131,20 @@ cudaError_t launch_forward(const PlanView& p, const T* sigma, T* Fr, T* Fp, cuda
     }
     if (ev && (err = cudaEventRecord(ev[2], st)) != cudaSuccess) return err;
     {
-        Shape s = shape_for<V>(p.nphi, sizeof(T) == 8 ? 64 : 512);
-        const int grid = (p.nu + s.slots - 1) / s.slots;
+        Shape s = shape_for<V>(p.nphi, sizeof(T) == 8 ? 64 : 256);
+        const int R = 2 * s.slots, nblk = (p.nu + R - 1) / R;
+        const size_t smem = rows_inv_smem_bytes<V>(p.nphi, s.slots);
+        const CUtensorMap* mB = row_map(p, R, 1, p.nphi);
+        const CUtensorMap* mC = row_map(p, R, 2, p.nphi);
+        const bool um = mB && mC;
         SG_DISPATCH_E(s.E, {
-            auto k = k_fwd_rows_inv<T, EE>;
-            if ((err = set_smem(k, s.smem)) != cudaSuccess) return err;
-            k<<<grid, s.threads, s.smem, st>>>(B, C, (const T*)p.wpost, Fr, Fp, p.nu, p.nphi, ln, tw);
+            auto k = k_fwd_rows_inv<T, EE, 256>;
+            if constexpr (sizeof(T) == 4)  // FP64 blocks are at most 256 threads
+                if (s.threads > 256) k = k_fwd_rows_inv<T, EE, 512>;
+            if ((err = set_smem(k, smem, true)) != cudaSuccess) return err;
+            k<<<persistent_grid(k, s.threads, smem, nblk, p.sms), s.threads, smem, st>>>(
+                B, C, (const T*)p.wpost, Fr, Fp, p.nu, p.nphi, ln, tw, p.err, um ? *mB : CUtensorMap{},
+                um ? *mC : CUtensorMap{}, um);
         });
     }
     if (ev && (err = cudaEventRecord(ev[3], st)) != cudaSuccess) return err;
@@ -768,12 +1162,18 @@ cudaError_t launch_backward(const PlanView& p, const T* gr, const T* gp, T* gs, 
     const int ln = sg_ilog2(p.nphi), lL = sg_ilog2(2 * p.nu);
     cudaError_t err;
     {
-        Shape s = shape_for<V>(p.nphi, sizeof(T) == 8 ? 64 : 512);
-        const int grid = (p.nu + s.slots - 1) / s.slots;
+        Shape s = shape_for<V>(p.nphi, row_min_threads(sizeof(T)));
+        const int R = s.slots, nblk = (p.nu + R - 1) / R;
+        const size_t smem = row_smem_bytes<V>(p.nphi, s.slots);
+        const CUtensorMap* mA = row_map(p, R, 0, p.nphi);
+        const CUtensorMap* mC = row_map(p, R, 2, p.nphi);
+        const bool um = mA && mC;
         SG_DISPATCH_E(s.E, {
             auto k = k_bwd_rows<T, EE>;
-            if ((err = set_smem(k, s.smem)) != cudaSuccess) return err;
-            k<<<grid, s.threads, s.smem, st>>>(gr, gp, (const T*)p.wpost, A, C, p.nu, p.nphi, ln, tw);
+            if ((err = set_smem(k, smem, true)) != cudaSuccess) return err;
+            k<<<persistent_grid(k, s.threads, smem, nblk, p.sms), s.threads, smem, st>>>(
+                gr, gp, (const T*)p.wpost, A, C, p.nu, p.nphi, ln, tw, p.err, um ? *mA : CUtensorMap{},
+                um ? *mC : CUtensorMap{}, um);
         });
     }
     {
@@ -788,12 +1188,15 @@ cudaError_t launch_backward(const PlanView& p, const T* gr, const T* gp, T* gs, 
         });
     }
     {
-        Shape s = shape_for<V>(p.nphi, sizeof(T) == 8 ? 64 : 512);
-        const int grid = (p.nu / 2 + s.slots - 1) / s.slots;
+        Shape s = shape_for<V>(p.nphi, row_min_threads(sizeof(T)));
+        const int R = 2 * s.slots, nblk = (p.nu + R - 1) / R;
+        const size_t smem = row_smem_bytes<V>(p.nphi, s.slots);
+        const CUtensorMap* mB = row_map(p, R, 1, p.nphi);
         SG_DISPATCH_E(s.E, {
             auto k = k_bwd_rows_inv<T, EE>;
-            if ((err = set_smem(k, s.smem)) != cudaSuccess) return err;
-            k<<<grid, s.threads, s.smem, st>>>(B, (const T*)p.wpre, gs, p.nu, p.nphi, ln, tw);
+            if ((err = set_smem(k, smem, true)) != cudaSuccess) return err;
+            k<<<persistent_grid(k, s.threads, smem, nblk, p.sms), s.threads, smem, st>>>(
+                B, (const T*)p.wpre, gs, p.nu, p.nphi, ln, tw, p.err, mB ? *mB : CUtensorMap{}, mB != nullptr);
         });
     }
     return cudaGetLastError();

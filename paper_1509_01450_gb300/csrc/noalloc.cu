@@ -75,6 +75,16 @@ extern "C" sg_status sg_forces_noalloc(sg_plan* p, const void* sigma, void* F_r,
     v.wa = scratch;
     v.wb = (unsigned char*)scratch + half;
     v.wc = (unsigned char*)scratch + 2 * half;
+    {
+        // tensor maps of the row passes over the scratch (host-side encoding only)
+        std::lock_guard<std::mutex> lock(g_scratch_mutex);
+        if (!p->have_na_maps) {
+            void* const bufs[3] = {v.wa, v.wb, v.wc};
+            make_row_maps(p->nu, p->nphi, p->elem, bufs, p->na_maps);
+            p->have_na_maps = 1;
+        }
+    }
+    v.maps = p->na_maps;
     cudaError_t e = p->dtype == SG_F32
                         ? launch_forward<float>(v, (const float*)sigma, (float*)F_r, (float*)F_phi, stream)
                         : launch_forward<double>(v, (const double*)sigma, (double*)F_r, (double*)F_phi, stream);

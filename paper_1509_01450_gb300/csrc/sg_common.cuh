@@ -10,6 +10,7 @@
 // padded shared-memory buffer of N + N/16 elements.  Twiddles come from a
 // table tw[j] = exp(-2 pi i j / SG_NMAX) in global memory.
 #pragma once
+#include <cuda.h>  // CUtensorMap (the descriptor type only; no driver calls here)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -51,6 +52,25 @@ __device__ __forceinline__ V sg_tw(const V* __restrict__ tw, int idx)
     if (DIR > 0) w.y = -w.y;
     return w;
 }
+
+// ---------------------------------------------------------------------------
+// Barriers of one transform's threads: the whole block (SgSyncBlock), or only
+// the n threads of one slot (named barrier id, n a multiple of 32), so that
+// the slots of a block run their transforms independently.
+// ---------------------------------------------------------------------------
+struct SgSyncBlock {
+    __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
+struct SgSyncSlot {
+    int id, n;  // id 0: the whole block
+    __device__ __forceinline__ void operator()() const
+    {
+        if (id == 0)
+            __syncthreads();
+        else
+            asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+    }
+};
 
 // ---------------------------------------------------------------------------
 // Butterflies in registers: natural-order DFT of R points, sign DIR.
@@ -301,6 +321,40 @@ __device__ __forceinline__ void sg_bulk_g2s_hint(void* dst, const void* src, uin
 }
 
 // ---------------------------------------------------------------------------
+// Tensor (tiled) and bulk copies through the TMA unit.  Shared-memory ends of
+// tensor copies are 128-byte aligned; every copy's global start obeys the
+// 16-byte rule (inner coordinate x element size a multiple of 16).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void sg_tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar,
+                                               uint64_t policy)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(sg_smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(sg_smem_u32(bar)), "l"(policy)
+        : "memory");
+}
+__device__ __forceinline__ void sg_tma_store_2d(const CUtensorMap* map, int x, int y, const void* src, uint64_t policy)
+{
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group.L2::cache_hint [%0, {%1, %2}], [%3], %4;" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(x), "r"(y), "r"(sg_smem_u32(src)), "l"(policy)
+                 : "memory");
+}
+// contiguous bulk store shared -> global (both 16-byte aligned, size a multiple of 16)
+__device__ __forceinline__ void sg_bulk_s2g(void* dst, const void* src, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(sg_smem_u32(src)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void sg_bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// wait until the bulk stores issued by this thread have read their shared memory
+__device__ __forceinline__ void sg_bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// order this thread's generic shared-memory accesses with later asynchronous-proxy ones
+__device__ __forceinline__ void sg_fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// ---------------------------------------------------------------------------
 // L2 eviction priorities.  The half-spectrum intermediates are written by one
 // pass and read, transposed, by the next; they are kept in L2 (evict_last)
 // while the streamed inputs (density, kernel spectra, consumed intermediates)
@@ -436,8 +490,9 @@ __device__ __forceinline__ void sg_pass_load(V (&v)[E], const V* sm, int t, int 
 // Whole transform.  All threads of the block must call it together (it uses
 // __syncthreads); sm is this transform's exchange buffer (sg_padded(N)
 // elements).  On exit the buffer is free for reuse.
-template <int E, int DIR, typename V>
-__device__ __forceinline__ void sg_fft(V (&v)[E], V* sm, int N, int log2N, int t, const V* __restrict__ tw)
+template <int E, int DIR, typename V, typename Sync = SgSyncBlock>
+__device__ __forceinline__ void sg_fft(V (&v)[E], V* sm, int N, int log2N, int t, const V* __restrict__ tw,
+                                       const Sync& sync = Sync())
 {
     const int NT = N / E;
     if (E < 16) {  // N == E: one pass in registers
@@ -463,7 +518,7 @@ __device__ __forceinline__ void sg_fft(V (&v)[E], V* sm, int N, int log2N, int t
     }
     Ns = 1;
     for (int p = 0; p < n16; p++) {
-        if (p == 0) __syncthreads();  // the caller may have just read sm
+        if (p == 0) sync();  // the caller may have just read sm
         if (Rprev == 2)
             sg_pass_store<2, E>(v, sm, t, NT, Ns);
         else if (Rprev == 4)
@@ -473,9 +528,9 @@ __device__ __forceinline__ void sg_fft(V (&v)[E], V* sm, int N, int log2N, int t
         else
             sg_pass_store<16, E>(v, sm, t, NT, Ns);
         Ns *= Rprev;
-        __syncthreads();
+        sync();
         sg_pass_load<16, E>(v, sm, t, NT, N);
-        __syncthreads();
+        sync();
         sg_pass_compute<16, E, DIR>(v, t, NT, Ns, tw);
         Rprev = 16;
     }
@@ -518,8 +573,9 @@ __device__ __forceinline__ void sg_pass16_tw(V (&v)[16], V w)
     sg_dft<16, DIR>(v);
 }
 
-template <int E, int DIR, typename V>
-__device__ __forceinline__ void sg_fft(V (&v)[E], V* sm, int N, int log2N, int t, const SgTwid<V>& tws)
+template <int E, int DIR, typename V, typename Sync = SgSyncBlock>
+__device__ __forceinline__ void sg_fft(V (&v)[E], V* sm, int N, int log2N, int t, const SgTwid<V>& tws,
+                                       const Sync& sync = Sync())
 {
     static_assert(E == 16, "register twiddles need 16 elements per thread");
     const int NT = N / E;
@@ -534,30 +590,29 @@ __device__ __forceinline__ void sg_fft(V (&v)[E], V* sm, int N, int log2N, int t
         sg_pass_compute<8, E, DIR>(v, t, NT, 1, none);
     else
         sg_pass_compute<16, E, DIR>(v, t, NT, 1, none);
-    int Ns = 1;
-#pragma unroll
-    for (int p = 0; p < 3; p++) {
-        if (p < n16) {
-            if (p == 0) {
-                __syncthreads();  // the caller may have just read sm
-                if (rem == 1)
-                    sg_pass_store<2, E>(v, sm, t, NT, 1);
-                else if (rem == 2)
-                    sg_pass_store<4, E>(v, sm, t, NT, 1);
-                else if (rem == 3)
-                    sg_pass_store<8, E>(v, sm, t, NT, 1);
-                else
-                    sg_pass_store<16, E>(v, sm, t, NT, 1);
-                Ns = rem == 0 ? 16 : (1 << rem);
-            } else {
-                sg_pass_store<16, E>(v, sm, t, NT, Ns);
-                Ns *= 16;
-            }
-            __syncthreads();
-            sg_pass_load<16, E>(v, sm, t, NT, N);
-            __syncthreads();
-            sg_pass16_tw<DIR>(v, tws.w[p]);
+    if (n16 == 0) return;
+    sync();  // the caller may have just read sm
+    if (rem == 1)
+        sg_pass_store<2, E>(v, sm, t, NT, 1);
+    else if (rem == 2)
+        sg_pass_store<4, E>(v, sm, t, NT, 1);
+    else if (rem == 3)
+        sg_pass_store<8, E>(v, sm, t, NT, 1);
+    else
+        sg_pass_store<16, E>(v, sm, t, NT, 1);
+    int Ns = rem == 0 ? 16 : (1 << rem);
+    // the radix-16 passes share one copy of their code (a small instruction
+    // footprint matters more here than the loop overhead)
+#pragma unroll 1
+    for (int p = 0; p < n16; p++) {
+        if (p > 0) {
+            sg_pass_store<16, E>(v, sm, t, NT, Ns);
+            Ns *= 16;
         }
+        sync();
+        sg_pass_load<16, E>(v, sm, t, NT, N);
+        sync();
+        sg_pass16_tw<DIR>(v, p == 0 ? tws.w[0] : (p == 1 ? tws.w[1] : tws.w[2]));
     }
 }
 

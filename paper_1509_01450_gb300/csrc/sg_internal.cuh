@@ -4,6 +4,14 @@
 #include "../../include/sg.h"
 #include "sg_common.cuh"
 
+// 2-D tensor maps over the three mode-major half-spectrum buffers (wa, wb,
+// wc), for the row passes' tensor copies of R rows x up to 256 modes; R = 0
+// when there are none (the passes then use cp.async and plain stores).
+struct SgRowMaps {
+    CUtensorMap m[3];
+    int R;
+};
+
 // The plan behind the opaque sg_plan handle.
 struct sg_plan {
     int nu, nphi;
@@ -12,6 +20,7 @@ struct sg_plan {
     int weight_p;
     int built;
     int device;      // device the plan's memory lives on
+    int sms;         // its multiprocessor count
     size_t elem;     // bytes of one real in the working dtype
     // working-dtype device buffers
     void* tw;        // twiddle table, SG_NMAX complex
@@ -32,6 +41,9 @@ struct sg_plan {
     void* h_fr;
     void* h_fp;
     size_t bytes;    // device bytes held
+    SgRowMaps maps[2];     // for R = slots and 2 slots rows per row block
+    SgRowMaps na_maps[2];  // the same over the allocation-free scratch
+    int have_na_maps;
     cudaEvent_t ev[4];  // pass timing (sg_forces_timed), created on first use
     int have_ev;
     int report[4];      // last build: flag bits, failed offsets, one failed (k, q)
@@ -42,6 +54,7 @@ namespace sg {
 // Plain view of a plan passed to the launchers.
 struct PlanView {
     int nu, nphi;
+    int sms;
     const void* tw;
     const void* tw64;
     void *wa, *wb, *wc;
@@ -50,6 +63,7 @@ struct PlanView {
     const void* wpre;
     const void* wpost;
     int* err;
+    const SgRowMaps* maps;  // [2] over wa, wb, wc, or null
 };
 
 inline PlanView view(const sg_plan* p)
@@ -57,6 +71,7 @@ inline PlanView view(const sg_plan* p)
     PlanView v;
     v.nu = p->nu;
     v.nphi = p->nphi;
+    v.sms = p->sms;
     v.tw = p->tw;
     v.tw64 = p->tw64;
     v.wa = p->wa;
@@ -67,6 +82,7 @@ inline PlanView view(const sg_plan* p)
     v.wpre = p->wpre;
     v.wpost = p->wpost;
     v.err = p->derr;
+    v.maps = p->maps;
     return v;
 }
 
@@ -76,6 +92,9 @@ cudaError_t launch_forward(const PlanView& p, const T* sigma, T* Fr, T* Fp, cuda
                            cudaEvent_t* ev = nullptr);
 template <typename T>
 cudaError_t launch_backward(const PlanView& p, const T* gr, const T* gp, T* gs, cudaStream_t st);
+// Tensor maps of the row passes over the buffers bufs[3] (the layout of wa,
+// wb, wc); out[k].R = 0 where a map cannot be made.
+void make_row_maps(int nu, int nphi, size_t elem, void* const bufs[3], SgRowMaps out[2]);
 template <typename VO>
 cudaError_t launch_spectra(const PlanView& p, const double* nsr, const double* nsp, double2* W, VO* Kr, VO* Kp,
                            cudaStream_t st);
