@@ -244,76 +244,80 @@ __device__ __forceinline__ void stage_load_map(V* S, const CUtensorMap* map, int
 
 // ===========================================================================
 // Forward P1: rows (i0, i1) packed as z = w_i0 + i w_i1, FFT along phi,
-// split into X_i0, X_i1, staged and stored mode-major.  R = 2 slots rows per
-// row block; the block's density rows arrive as one bulk copy.
+// split into X_i0, X_i1, staged and stored mode-major.  Each slot takes one
+// pair of a row block (R = 2 slots rows).  Shared memory: the output stage
+// S[m R + r], the input stage (the block's density rows, one bulk copy) and
+// the slots' exchange areas: once the pair is in registers the input stage
+// takes the next block's rows, and the output stage is only written again
+// after its tensor stores have read it.
 // ===========================================================================
-template <typename T, int E>
-__global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 512) k_fwd_rows(const T* __restrict__ sigma, const T* __restrict__ wpre,
+template <typename V>
+__host__ __device__ __forceinline__ size_t rows_fwd_smem_bytes(int N, int slots)
+{
+    // output stage R half = slots N, input stage R N reals = slots N, exchange areas
+    return ((size_t)2 * slots * N + (size_t)slots * sg_padded(N)) * sizeof(V) + 128;
+}
+
+template <typename T, int E, int NTB>
+__global__ void __launch_bounds__(NTB, (sizeof(T) == 4 && NTB == 256) ? 2 : 1) k_fwd_rows(const T* __restrict__ sigma, const T* __restrict__ wpre,
                                                   typename CX<T>::t* __restrict__ A, int nu, int nphi, int log2n,
                                                   const typename CX<T>::t* __restrict__ tw, int* err,
                                                   const __grid_constant__ CUtensorMap mapA, int use_map)
 {
     typedef typename CX<T>::t V;
     extern __shared__ __align__(128) unsigned char smraw[];
-    __shared__ __align__(8) uint64_t bar[SG_RING];
+    __shared__ __align__(8) uint64_t bar;
     const int N = nphi, NT = N / E, half = N / 2;
     const int slot = threadIdx.x / NT, t = threadIdx.x % NT;
     const int slots = blockDim.x / NT;
     const int R = 2 * slots, nblk = (nu + R - 1) / R;
     const int lane = threadIdx.x & 31;
-    const bool producer = threadIdx.x < 32;
-    const size_t bufE = row_buf_elems<V>(N, slots);
-    V* const ring = reinterpret_cast<V*>(align128(smraw));
+    V* const So = reinterpret_cast<V*>(align128(smraw));        // output stage, R half
+    T* const Si = reinterpret_cast<T*>(So + (size_t)slots * N);  // input rows, R N reals
+    V* const sm = So + (size_t)2 * slots * N + (size_t)slot * sg_padded(N);
     const Twd<E, V> twd = make_twd<E>(log2n, t, tw);
     const SgSyncSlot ssync = slot_sync(slot, NT, slots);
-    SG_ROWS_BARRIER_INIT();
-    auto issue = [&](int rb, int q) {  // thread 0: the block's density rows into buffer q
+    if (threadIdx.x == 0) sg_mbar_init(&bar, 1);
+    __syncthreads();
+    auto issue = [&](int rb) {  // thread 0
         const int rows = min(R, nu - rb * R);
         const uint32_t bytes = (uint32_t)((size_t)rows * N * sizeof(T));
-        sg_mbar_expect_tx(&bar[q], bytes);
-        sg_bulk_g2s_hint(ring + q * bufE, sigma + (size_t)rb * R * N, bytes, &bar[q], sg_policy_evict_first());
+        sg_mbar_expect_tx(&bar, bytes);
+        sg_bulk_g2s_hint(Si, sigma + (size_t)rb * R * N, bytes, &bar, sg_policy_evict_first());
     };
-    if (threadIdx.x == 0 && blockIdx.x < nblk) issue(blockIdx.x, 0);
+    if (threadIdx.x == 0 && blockIdx.x < nblk) issue(blockIdx.x);
     int it = 0;
     for (int rb = blockIdx.x; rb < nblk; rb += gridDim.x, it++) {
-        const int q = it % SG_RING, qn = (it + 1) % SG_RING;
-        V* const cur = ring + q * bufE;
         const bool more = rb + (int)gridDim.x < nblk;
-        __syncthreads();  // nobody reads or writes buffer qn any more
-        if (producer) {
-            if (use_map) sg_bulk_wait_read_prev();  // the tensor stores out of buffer qn have read it
-            __syncwarp();
-            if (threadIdx.x == 0 && more) {
-                sg_fence_proxy_async();
-                issue(rb + gridDim.x, qn);
-            }
-        }
-        if (__syncthreads_or(!sg_mbar_wait_bounded(&bar[q], (it / SG_RING) & 1, err, 1))) {
-            if (more) sg_mbar_wait_bounded(&bar[qn], ((it + 1) / SG_RING) & 1, err, 1);
-            if (use_map && producer) sg_bulk_wait_read();
+        if (__syncthreads_or(!sg_mbar_wait_bounded(&bar, it & 1, err, 1))) {
+            if (use_map && threadIdx.x < 32) sg_bulk_wait_read();
             return;  // inputs never arrived
         }
         const int pair = rb * slots + slot;
         const bool live = pair < nu / 2;
         const int i0 = 2 * (live ? pair : 0);
         const T w0 = wpre[i0], w1 = wpre[i0 + 1];
-        const T* rows = reinterpret_cast<const T*>(cur) + (size_t)(2 * slot) * N;
+        const T* rows = Si + (size_t)(2 * slot) * N;
         V v[E];
 #pragma unroll
         for (int e = 0; e < E; e++) {
             const int n = t + e * NT;
             v[e] = V{rows[n] * w0, rows[N + n] * w1};
         }
-        V* sm = cur + slot * sg_padded(N);
-        __syncthreads();  // the rows overlap other slots' exchange areas: all read before any slot transforms
+        __syncthreads();  // the input stage is read: it takes the next block's rows
+        if (threadIdx.x == 0 && more) {
+            sg_fence_proxy_async();
+            issue(rb + gridDim.x);
+        }
         fft<E, -1>(v, sm, N, log2n, t, twd, ssync);
         V x0[E / 2], x1[E / 2];
         split_real_pair<E, V, T>(v, sm, N, t, x0, x1, ssync);
-        __syncthreads();  // the stage spans every slot's area
+        if (use_map && threadIdx.x < 32) sg_bulk_wait_read();  // the last tensor stores have read So
+        __syncthreads();
         if (live) {
 #pragma unroll
             for (int e = 0; e < E / 2; e++) {
-                V* d = cur + (t + e * NT) * R + 2 * slot;
+                V* d = So + (t + e * NT) * R + 2 * slot;
                 d[0] = x0[e];
                 d[1] = x1[e];
             }
@@ -321,13 +325,13 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 512) k_fwd_rows(const T
         if (use_map) sg_fence_proxy_async();
         __syncthreads();
         if (!use_map) {
-            stage_store(A, cur, nu, half, rb * R, R);
-        } else if (producer) {
-            stage_store_map(&mapA, cur, half, rb * R, R, lane);
+            stage_store(A, So, nu, half, rb * R, R);
+        } else if (threadIdx.x < 32) {
+            stage_store_map(&mapA, So, half, rb * R, R, lane);
             sg_bulk_commit();
         }
     }
-    if (use_map && producer) sg_bulk_wait_read();
+    if (use_map && threadIdx.x < 32) sg_bulk_wait_read();
 }
 
 // ===========================================================================
@@ -362,7 +366,7 @@ __global__ void SG_COLS_BOUNDS(T, NTB) k_fwd_cols(const typename CX<T>::t* __res
                                                   const typename CX<T>::t* __restrict__ tw, int* err)
 {
     typedef typename CX<T>::t V;
-    extern __shared__ __align__(16) unsigned char smraw[];
+    extern __shared__ __align__(128) unsigned char smraw[];
     __shared__ __align__(8) uint64_t bar[2];  // [0]: the column, [1]: the spectra
     const int L = 2 * nu, NT = L / E, half = nphi / 2, KS = nu + 2;
     const int t = threadIdx.x;
@@ -677,7 +681,7 @@ __global__ void SG_COLS_BOUNDS(T, NTB) k_bwd_cols(const typename CX<T>::t* __res
                                                   const typename CX<T>::t* __restrict__ tw, int* err)
 {
     typedef typename CX<T>::t V;
-    extern __shared__ __align__(16) unsigned char smraw[];
+    extern __shared__ __align__(128) unsigned char smraw[];
     __shared__ __align__(8) uint64_t bar[2];  // [0]: the A column, [1]: the C column and the spectra
     const int L = 2 * nu, NT = L / E, half = nphi / 2, KS = nu + 2;
     const int t = threadIdx.x;
@@ -769,67 +773,56 @@ __global__ void SG_COLS_BOUNDS(T, NTB) k_bwd_cols(const typename CX<T>::t* __res
 // ===========================================================================
 // Backward P3b: rows (i0, i1): Zhat = S_i0 + i S_i1 with S the Hermitian
 // extension of each half spectrum; inverse FFT gives rows i0 (Re), i1 (Im).
-// R = 2 slots rows per row block, gathered from the mode-major B.
+// Each slot takes one pair of a row block (R = 2 slots rows); the stage of
+// the block's B rows takes the next block's rows once the pair is read.
 // ===========================================================================
-template <typename T, int E>
-__global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 512) k_bwd_rows_inv(const typename CX<T>::t* __restrict__ B,
+template <typename V>
+__host__ __device__ __forceinline__ size_t rows_bwd_inv_smem_bytes(int N, int slots)
+{
+    return ((size_t)slots * N + (size_t)slots * sg_padded(N)) * sizeof(V) + 128;
+}
+
+template <typename T, int E, int NTB>
+__global__ void __launch_bounds__(NTB, (sizeof(T) == 4 && NTB == 256) ? 2 : 1) k_bwd_rows_inv(const typename CX<T>::t* __restrict__ B,
                                                       const T* __restrict__ wpre, T* __restrict__ gs, int nu,
                                                       int nphi, int log2n, const typename CX<T>::t* __restrict__ tw,
                                                       int* err, const __grid_constant__ CUtensorMap mapB, int use_map)
 {
     typedef typename CX<T>::t V;
     extern __shared__ __align__(128) unsigned char smraw[];
-    __shared__ __align__(8) uint64_t bar[SG_RING];
+    __shared__ __align__(8) uint64_t bar;
     const int N = nphi, NT = N / E, half = N / 2;
     const int slot = threadIdx.x / NT, t = threadIdx.x % NT;
     const int slots = blockDim.x / NT;
     const int R = 2 * slots, nblk = (nu + R - 1) / R;
     const int lane = threadIdx.x & 31;
-    const bool producer = threadIdx.x < 32;
-    const size_t bufE = row_buf_elems<V>(N, slots);
-    V* const ring = reinterpret_cast<V*>(align128(smraw));
+    V* const Sb = reinterpret_cast<V*>(align128(smraw));
+    V* const sm = Sb + (size_t)R * half + (size_t)slot * sg_padded(N);
     const Twd<E, V> twd = make_twd<E>(log2n, t, tw);
     const SgSyncSlot ssync = slot_sync(slot, NT, slots);
-    SG_ROWS_BARRIER_INIT();
-    auto issue = [&](int rb, int q) {
-        V* dst = ring + q * bufE;
-        if (use_map) {  // warp 0
-            if (lane == 0) sg_mbar_expect_tx(&bar[q], (uint32_t)((size_t)half * R * sizeof(V)));
+    if (threadIdx.x == 0) sg_mbar_init(&bar, 1);
+    __syncthreads();
+    auto issue = [&](int rb) {  // use_map: warp 0; else every thread
+        if (use_map) {
+            if (lane == 0) sg_mbar_expect_tx(&bar, (uint32_t)((size_t)half * R * sizeof(V)));
             __syncwarp();
-            stage_load_map(dst, &mapB, half, rb * R, R, &bar[q], lane);
+            stage_load_map(Sb, &mapB, half, rb * R, R, &bar, lane);
         } else {
-            stage_load(dst, B, nu, half, rb * R, R);
+            stage_load(Sb, B, nu, half, rb * R, R);
+            sg_cp_async_commit();
         }
     };
-    if (blockIdx.x < nblk && (!use_map || producer)) issue(blockIdx.x, 0);
-    if (!use_map) sg_cp_async_commit();
+    if (blockIdx.x < nblk && (!use_map || threadIdx.x < 32)) issue(blockIdx.x);
     int it = 0;
     for (int rb = blockIdx.x; rb < nblk; rb += gridDim.x, it++) {
-        const int q = it % SG_RING, qn = (it + 1) % SG_RING;
-        V* const cur = ring + q * bufE;
         const bool more = rb + (int)gridDim.x < nblk;
-        __syncthreads();
         if (use_map) {
-            if (producer) {
-                if (threadIdx.x == 0) sg_bulk_wait_read_prev();
-                __syncwarp();
-                if (more) {
-                    sg_fence_proxy_async();
-                    issue(rb + gridDim.x, qn);
-                }
-            }
-            if (__syncthreads_or(!sg_mbar_wait_bounded(&bar[q], (it / SG_RING) & 1, err, 1))) {
-                if (more) sg_mbar_wait_bounded(&bar[qn], ((it + 1) / SG_RING) & 1, err, 1);
-                if (threadIdx.x == 0) sg_bulk_wait_read();
-                return;
-            }
+            if (__syncthreads_or(!sg_mbar_wait_bounded(&bar, it & 1, err, 1))) return;
         } else {
-            if (more) issue(rb + gridDim.x, qn);
-            sg_cp_async_commit();
-            sg_cp_async_wait_prev();
+            asm volatile("cp.async.wait_all;" ::: "memory");
             __syncthreads();
         }
-        const V* b0s = cur + 2 * slot;  // this pair's rows are r = 2 slot, 2 slot + 1
+        const V* b0s = Sb + 2 * slot;  // this pair's rows are r = 2 slot, 2 slot + 1
         const V* b1s = b0s + 1;
         V v[E];
 #pragma unroll
@@ -855,28 +848,16 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 512) k_bwd_rows_inv(con
             }
             v[e] = cadd(s0, cmuli(s1));
         }
-        __syncthreads();  // the stage spans every slot's exchange area: all read before any slot transforms
-        fft<E, +1>(v, cur + slot * sg_padded(N), N, log2n, t, twd, ssync);
+        __syncthreads();  // the stage is read: it takes the next block's rows
+        if (more && (!use_map || threadIdx.x < 32)) {
+            if (use_map) sg_fence_proxy_async();
+            issue(rb + gridDim.x);
+        }
+        fft<E, +1>(v, sm, N, log2n, t, twd, ssync);
         const int pair = rb * slots + slot;
-        const bool live = pair < nu / 2;
-        const int i0 = 2 * (live ? pair : 0);
-        const T w0 = wpre[i0], w1 = wpre[i0 + 1];
-        if (use_map) {
-            __syncthreads();  // every slot's transform is done before the rows are staged over their areas
-            T* g = reinterpret_cast<T*>(cur);  // rows [rb R, rb R + R) of gsigma, contiguous
-#pragma unroll
-            for (int e = 0; e < E; e++) {
-                const int n = t + e * NT;
-                g[(size_t)(2 * slot) * N + n] = v[e].x * w0;
-                g[(size_t)(2 * slot + 1) * N + n] = v[e].y * w1;
-            }
-            sg_fence_proxy_async();
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                sg_bulk_s2g(gs + (size_t)rb * R * N, g, (uint32_t)((size_t)min(R, nu - rb * R) * N * sizeof(T)));
-                sg_bulk_commit();
-            }
-        } else if (live) {
+        if (pair < nu / 2) {
+            const int i0 = 2 * pair;
+            const T w0 = wpre[i0], w1 = wpre[i0 + 1];
 #pragma unroll
             for (int e = 0; e < E; e++) {
                 const int n = t + e * NT;
@@ -885,11 +866,7 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 512) k_bwd_rows_inv(con
             }
         }
     }
-    if (use_map) {
-        if (threadIdx.x == 0) sg_bulk_wait_read();
-    } else {
-        asm volatile("cp.async.wait_all;" ::: "memory");
-    }
+    if (!use_map) asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
 // ===========================================================================
@@ -903,7 +880,7 @@ __global__ void __launch_bounds__(512) k_spec_rows(const double* __restrict__ kr
                                                    const double2* __restrict__ tw)
 {
     typedef double2 V;
-    extern __shared__ __align__(16) unsigned char smraw[];
+    extern __shared__ __align__(128) unsigned char smraw[];
     V* small = reinterpret_cast<V*>(smraw);
     const int N = nphi, NT = N / E;
     const int slot = threadIdx.x / NT, t = threadIdx.x % NT;
@@ -942,7 +919,7 @@ __global__ void __launch_bounds__(512) k_spec_cols(const double2* __restrict__ W
                                                    const double2* __restrict__ tw)
 {
     typedef double2 V;
-    extern __shared__ __align__(16) unsigned char smraw[];
+    extern __shared__ __align__(128) unsigned char smraw[];
     V* small = reinterpret_cast<V*>(smraw);
     const int L = 2 * nu, NT = L / E, KS = nu + 2;
     const int slot = threadIdx.x / NT, t = threadIdx.x % NT;
@@ -1106,12 +1083,14 @@ cudaError_t launch_forward(const PlanView& p, const T* sigma, T* Fr, T* Fp, cuda
     cudaError_t err;
     if (ev && (err = cudaEventRecord(ev[0], st)) != cudaSuccess) return err;
     {
-        Shape s = shape_for<V>(p.nphi, row_min_threads(sizeof(T)));
+        Shape s = shape_for<V>(p.nphi, sizeof(T) == 8 ? 64 : 256);
         const int R = 2 * s.slots, nblk = (p.nu + R - 1) / R;
-        const size_t smem = row_smem_bytes<V>(p.nphi, s.slots);
+        const size_t smem = rows_fwd_smem_bytes<V>(p.nphi, s.slots);
         const CUtensorMap* mA = row_map(p, R, 0, p.nphi);
         SG_DISPATCH_E(s.E, {
-            auto k = k_fwd_rows<T, EE>;
+            auto k = k_fwd_rows<T, EE, 256>;
+            if constexpr (sizeof(T) == 4)  // FP64 blocks are at most 256 threads
+                if (s.threads > 256) k = k_fwd_rows<T, EE, 512>;
             if ((err = set_smem(k, smem, true)) != cudaSuccess) return err;
             k<<<persistent_grid(k, s.threads, smem, nblk, p.sms), s.threads, smem, st>>>(
                 sigma, (const T*)p.wpre, A, p.nu, p.nphi, ln, tw, p.err, mA ? *mA : CUtensorMap{}, mA != nullptr);
@@ -1188,12 +1167,14 @@ cudaError_t launch_backward(const PlanView& p, const T* gr, const T* gp, T* gs, 
         });
     }
     {
-        Shape s = shape_for<V>(p.nphi, row_min_threads(sizeof(T)));
+        Shape s = shape_for<V>(p.nphi, sizeof(T) == 8 ? 64 : 256);
         const int R = 2 * s.slots, nblk = (p.nu + R - 1) / R;
-        const size_t smem = row_smem_bytes<V>(p.nphi, s.slots);
+        const size_t smem = rows_bwd_inv_smem_bytes<V>(p.nphi, s.slots);
         const CUtensorMap* mB = row_map(p, R, 1, p.nphi);
         SG_DISPATCH_E(s.E, {
-            auto k = k_bwd_rows_inv<T, EE>;
+            auto k = k_bwd_rows_inv<T, EE, 256>;
+            if constexpr (sizeof(T) == 4)
+                if (s.threads > 256) k = k_bwd_rows_inv<T, EE, 512>;
             if ((err = set_smem(k, smem, true)) != cudaSuccess) return err;
             k<<<persistent_grid(k, s.threads, smem, nblk, p.sms), s.threads, smem, st>>>(
                 B, (const T*)p.wpre, gs, p.nu, p.nphi, ln, tw, p.err, mB ? *mB : CUtensorMap{}, mB != nullptr);
