@@ -36,6 +36,20 @@ NU, NPHI, R_IN, R_OUT, SEED = 2048, 4096, 0.01, 100.0, 1509
 # algorithmic bytes per cell of the three forward passes in FP32 (reads and
 # writes of the minimal data each pass must move, symmetry-reduced spectra)
 BYTES_PER_CELL = {"rows": 8.0, "cols": 20.0, "inv_rows": 16.0}
+# DRAM bytes (read + write) of one column-pass launch at 2048 x 4096 FP32, from
+# one ncu capture (profiles/k_fwd_cols_2048x4096_full.md), valid only for the
+# kernel sources it was taken on (sha256 prefix of fftconv.cu + sg_common.cuh).
+COLS_TRAFFIC = {"sources_sha256": "b4a8478e556f390a", "bytes_per_launch": 100.802048e6 + 7.158016e6}
+
+
+def kernel_sources_sha() -> str:
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in ("fftconv.cu", "sg_common.cuh"):
+        with open(os.path.join(ROOT, "paper_1509_01450_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def dist_env():
@@ -233,6 +247,9 @@ def run_ours(args):
     dom_name, dom_ms = max((("cols", p_cols), ("rows", p_rows), ("inv_rows", p_inv)), key=lambda x: x[1])
     achieved = BYTES_PER_CELL[dom_name] * cells / (dom_ms * 1e-3) / 1e9
     total_bytes = sum(BYTES_PER_CELL.values()) * cells
+    traffic = None
+    if dom_name == "cols" and (NU, NPHI) == (2048, 4096) and kernel_sources_sha() == COLS_TRAFFIC["sources_sha256"]:
+        traffic = COLS_TRAFFIC["bytes_per_launch"]
 
     # ---- adjoint and FP64, same protocol ----------------------------------
     def timed(fn, n):
@@ -294,7 +311,7 @@ def run_ours(args):
                        "kernel_weight_p": 0, "l2": "flushed by a 256 MB write before every timed step",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
             "roofline": {"bound": "hbm", "kernel": f"forward {dom_name} pass", "achieved": achieved, "peak": peak,
-                         "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                         "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                          "algorithmic_bytes_per_cell": BYTES_PER_CELL[dom_name]},
             "path_roofline": {"bytes_per_cell": sum(BYTES_PER_CELL.values()),
                               "achieved_gbs": total_bytes / (ms * 1e-3) / 1e9,
