@@ -59,6 +59,25 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(x: float, device=None) -> float:
+    """Largest x over the ranks of the default process group (x itself when
+    there is no group or it has one rank).  Every rank must call it."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(world_size: int, cells_per_rank: int, ms_max: float) -> float:
+    """cells/s of the whole job: every rank processes its own disk of
+    cells_per_rank cells per step; the slowest rank's step time counts."""
+    return world_size * cells_per_rank / (ms_max * 1e-3)
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -226,13 +245,9 @@ def run_ours(args):
         barrier()
         wall = time.time() - w0
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    ms = sum(step_ms) / len(step_ms)
-    if ws > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(sum(step_ms) / len(step_ms), dev)
     cells = NU * NPHI
-    value = ws * cells / (ms * 1e-3)
+    value = whole_job_value(ws, cells, ms)
 
     # ---- per-pass durations (roofline of the dominant kernel) -------------
     passes = []
