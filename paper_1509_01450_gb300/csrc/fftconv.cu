@@ -30,7 +30,9 @@
 // 0..N_u of the L-point spectrum; Khat_r is Hermitian in kappa
 // (Khat_r[L - kappa] = conj Khat_r[kappa]) and Khat_phi anti-Hermitian.
 // Khat_phi vanishes at modes 0 and N_phi/2 (odd kernel).
+#include <map>
 #include <mutex>
+#include <tuple>
 
 #include "sg_internal.cuh"
 
@@ -971,14 +973,42 @@ static Shape shape_for(int n, int min_threads)
 
 // Dynamic shared memory above the 48 KB default needs an opt-in; carveout
 // asks for the largest shared-memory split of L1 (several blocks of a
-// shared-memory-heavy kernel per SM).
+// shared-memory-heavy kernel per SM).  Done once per kernel, device and
+// size: later launches (for example while a stream is being captured) make
+// no attribute calls.
+struct LaunchCache {
+    std::mutex mu;
+    std::map<std::tuple<const void*, int, int, size_t>, int> occ;  // (kernel, device, threads, smem) -> blocks/SM
+    std::map<std::tuple<const void*, int>, size_t> smem;            // (kernel, device) -> opted-in bytes
+};
+static LaunchCache& launch_cache()
+{
+    static LaunchCache c;
+    return c;
+}
+static int current_device()
+{
+    int d = 0;
+    if (cudaGetDevice(&d) != cudaSuccess) {
+        cudaGetLastError();
+        d = 0;
+    }
+    return d;
+}
+
 template <typename K>
 static cudaError_t set_smem(K kernel, size_t smem, bool carveout = false)
 {
+    LaunchCache& c = launch_cache();
+    const auto key = std::make_tuple((const void*)kernel, current_device());
+    std::lock_guard<std::mutex> lock(c.mu);
+    auto it = c.smem.find(key);
+    if (it != c.smem.end() && it->second >= smem) return cudaSuccess;
     cudaError_t e = cudaSuccess;
     if (smem > 48 * 1024) e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess && carveout)
         e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e == cudaSuccess) c.smem[key] = it != c.smem.end() && it->second > smem ? it->second : smem;
     return e;
 }
 
@@ -987,10 +1017,21 @@ static cudaError_t set_smem(K kernel, size_t smem, bool carveout = false)
 template <typename K>
 static int persistent_grid(K kernel, int threads, size_t smem, int nblk, int sms)
 {
+    LaunchCache& c = launch_cache();
+    const auto key = std::make_tuple((const void*)kernel, current_device(), threads, smem);
     int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, smem) != cudaSuccess || occ < 1) {
-        cudaGetLastError();
-        occ = 1;
+    {
+        std::lock_guard<std::mutex> lock(c.mu);
+        auto it = c.occ.find(key);
+        if (it != c.occ.end()) occ = it->second;
+    }
+    if (occ == 0) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, smem) != cudaSuccess || occ < 1) {
+            cudaGetLastError();
+            occ = 1;
+        }
+        std::lock_guard<std::mutex> lock(c.mu);
+        c.occ[key] = occ;
     }
     const int g = occ * (sms > 0 ? sms : 1);
     return nblk < g ? nblk : g;

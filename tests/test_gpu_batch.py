@@ -1,0 +1,113 @@
+"""Batching workload: 256 exponential disks of uneven sizes (N_u in
+{128..1024}, N_phi in {256..2048}, m = 1..4 spirals) through
+sg_forces_batched, one stream.
+
+Each disk's forces must equal its own sg_forces call bit for bit (same
+passes, same plan); the smallest disks are compared with the FP64 oracle's
+direct sum on sampled targets; and the whole batch, captured once in a CUDA
+graph and replayed on new densities, must give the eager results.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1509_01450_gb300 import build
+
+    build.build()
+    return torch
+
+
+@pytest.fixture(scope="module")
+def batch(torch_cuda):
+    torch = torch_cuda
+    from paper_1509_01450_gb300 import Plan
+
+    disks = workloads.batch_disks(256, 1450)
+    plans = {}
+    for d in disks:
+        if (d.nu, d.nphi) not in plans:
+            plans[(d.nu, d.nphi)] = Plan(d.nu, d.nphi, d.u_min, d.du, 1.0, "float32").build()
+    sig = [torch.tensor(d.sigma(), dtype=torch.float32, device="cuda") for d in disks]
+    return disks, plans, sig
+
+
+def _outputs(torch, sig):
+    return [torch.empty_like(s) for s in sig], [torch.empty_like(s) for s in sig]
+
+
+def test_batch_equals_single_calls(torch_cuda, batch):
+    torch = torch_cuda
+    from paper_1509_01450_gb300 import forces_batched
+
+    disks, plans, sig = batch
+    assert len(plans) <= 16
+    Fr, Fp = _outputs(torch, sig)
+    forces_batched([(plans[(d.nu, d.nphi)], s, a, b) for d, s, a, b in zip(disks, sig, Fr, Fp)])
+    for d, s, a, b in zip(disks, sig, Fr, Fp):
+        er, ep = plans[(d.nu, d.nphi)].forces(s)
+        assert torch.equal(a, er) and torch.equal(b, ep)
+    for p in plans.values():
+        p.check()
+
+
+def test_smallest_disks_match_oracle(torch_cuda, batch, oracle_mod):
+    torch = torch_cuda
+    from paper_1509_01450_gb300 import forces_batched
+
+    disks, plans, sig = batch
+    small = [n for n, d in enumerate(disks) if (d.nu, d.nphi) == (128, 256)][:3]
+    assert small
+    d0 = disks[small[0]]
+    cells = oracle_mod.kernel_cells(d0.nu, d0.nphi, d0.du)
+    Kr, Kp = oracle_mod.fold(cells, math.exp(d0.du), 2 * math.pi / d0.nphi)
+    Fr, Fp = _outputs(torch, [sig[n] for n in small])
+    forces_batched([(plans[(128, 256)], sig[n], a, b) for n, a, b in zip(small, Fr, Fp)])
+    rng = np.random.default_rng(11)
+    targets = rng.choice(d0.nu * d0.nphi, 2048, replace=False)
+    for n, a, b in zip(small, Fr, Fp):
+        rr, rp = oracle_mod.direct_sum(disks[n].sigma(), Kr, Kp, targets=targets)
+        gr = a.double().cpu().numpy().reshape(-1)[targets]
+        gp = b.double().cpu().numpy().reshape(-1)[targets]
+        num = np.sum((gr - rr) ** 2 + (gp - rp) ** 2)
+        den = np.sum(rr ** 2 + rp ** 2)
+        assert math.sqrt(num / den) < 1e-5
+
+
+def test_batch_replays_from_a_cuda_graph(torch_cuda, batch):
+    torch = torch_cuda
+    from paper_1509_01450_gb300 import forces_batched
+
+    disks, plans, sig = batch
+    n = 32  # a slice of the batch keeps the graph small
+    src = [s.clone() for s in sig[:n]]
+    Fr, Fp = _outputs(torch, src)
+    items = [(plans[(d.nu, d.nphi)], s, a, b) for d, s, a, b in zip(disks[:n], src, Fr, Fp)]
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):  # warm-up outside capture: attributes, occupancy queries
+        forces_batched(items, stream=side)
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        forces_batched(items, stream=torch.cuda.current_stream())
+    rng = np.random.default_rng(5)
+    for rep in range(2):
+        for s in src:
+            s.mul_(float(rng.uniform(0.5, 1.5)))
+        g.replay()
+        torch.cuda.synchronize()
+        for d, s, a, b in zip(disks[:n], src, Fr, Fp):
+            er, ep = plans[(d.nu, d.nphi)].forces(s)
+            assert torch.equal(a, er) and torch.equal(b, ep)
