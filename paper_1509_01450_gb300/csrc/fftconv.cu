@@ -340,14 +340,24 @@ __global__ void __launch_bounds__(NTB, (sizeof(T) == 4 && NTB == 256) ? 2 : 1) k
 // Forward P2: one phi-mode column m per block.  Shared memory: the FFT
 // exchange buffer (its first N_u entries double as the landing area of the
 // column), then Khat_r[m] and Khat_phi[m] (for m = 0: Khat_r of modes 0 and
-// N_phi/2), which are later reused to park the phi product.
+// N_phi/2).  FP32 with 16 points per thread: the two inverse transforms run
+// in lockstep on paired FP32 instructions, F_r's in the low lanes and
+// F_phi's in the high ones, through an exchange area of C2 elements over
+// the whole block of shared memory (entered once every spectrum read is
+// done).  Otherwise: the phi product is parked over the spectra and the
+// inverse transforms run one after the other.
 // ===========================================================================
 template <typename T>
 __host__ __device__ __forceinline__ size_t cols_smem_bytes(int nu)
 {
     typedef typename CX<T>::t V;
     const int L = 2 * nu, KS = nu + 2;
-    return sg_align16(sg_padded(L) * sizeof(V)) + 2 * (size_t)KS * sizeof(V);
+    const size_t b = sg_align16(sg_padded(L) * sizeof(V)) + 2 * (size_t)KS * sizeof(V);
+    if (sizeof(T) == 4 && L >= 16) {  // the paired inverse transforms' exchange area (C2 elements)
+        const size_t pb = sg_padded(L) * sizeof(C2);
+        return pb > b ? pb : b;
+    }
+    return b;
 }
 
 // NTB: the block size the kernel is compiled for (L / E threads); FP32
@@ -403,6 +413,43 @@ __global__ void SG_COLS_BOUNDS(T, NTB) k_fwd_cols(const typename CX<T>::t* __res
     V v[E];
 #pragma unroll
     for (int e = 0; e < E; e++) v[e] = (e < E / 2) ? sm[t + e * NT] : V{0, 0};  // rows >= nu: zero pad
+    if constexpr (sizeof(T) == 4 && E == 16) {
+        fft<E, -1>(v, sm, L, log2L, t, twd);  // the spectra land meanwhile
+        if (__syncthreads_or(!sg_mbar_wait_bounded(&bar[1], 0, err, 1))) return;
+        C2 w[E];  // (Y_r, Y_phi) of each frequency, paired
+        if (m == 0) {
+            // v holds the FFT of (DC + i Nyquist): separate the two real
+            // sequences and apply the kernels of modes 0 and N_phi/2; the phi
+            // force of both modes vanishes
+#pragma unroll
+            for (int e = 0; e < E; e++) sm[sg_pad(t + e * NT)] = v[e];
+            __syncthreads();
+#pragma unroll
+            for (int e = 0; e < E; e++) {
+                const int k = t + e * NT;
+                const V z = v[e], zc = cconj(sm[sg_pad((L - k) & (L - 1))]);
+                const V a = cscale(cadd(z, zc), (T)0.5);
+                const V d = csub(z, zc);
+                const V b = V{d.y * (T)0.5, -d.x * (T)0.5};
+                w[e] = c2(cadd(cmul(a, khat_r_s(kr_s, k, L, nu)), cmuli(cmul(b, khat_r_s(kp_s, k, L, nu)))),
+                          V{0, 0});
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < E; e++) {
+                const int k = t + e * NT;
+                w[e] = c2(cmul(v[e], khat_r_s(kr_s, k, L, nu)), cmul(v[e], khat_p_s(kp_s, k, L, nu)));
+            }
+        }
+        // both inverse transforms; their first exchange waits for every spectrum read
+        sg_fft_pair<+1>(w, reinterpret_cast<C2*>(smraw), L, log2L, t, twd.h);
+#pragma unroll
+        for (int e = 0; e < E / 2; e++) {  // crop to N_u rows
+            sg_st_hint(Br + (size_t)m * nu + t + e * NT, c2_lo(w[e]), keep);
+            sg_st_hint(Cp + (size_t)m * nu + t + e * NT, c2_hi(w[e]), keep);
+        }
+        return;
+    } else {
     // Three transforms share one copy of the FFT code: the forward one, then
     // the two inverse ones as conj(FFT(conj Y)).
 #pragma unroll 1
@@ -451,6 +498,7 @@ __global__ void SG_COLS_BOUNDS(T, NTB) k_fwd_cols(const typename CX<T>::t* __res
                 for (int e = 0; e < E; e++) v[e] = ks[t + e * NT];
             }
         }
+    }
     }
 }
 
@@ -664,13 +712,19 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 512) k_bwd_rows(const T
 // Backward P2b: column m: FFT of both zero-padded columns, times conj(Khat),
 // summed, inverse FFT, crop, to B.  Shared memory: exchange
 // buffer (first N_u entries: landing area of the A column), the C column,
-// Khat_r[m] and Khat_phi[m] (m = 0: Khat_r of modes 0 and N_phi/2).
+// Khat_r[m] and Khat_phi[m] (m = 0: Khat_r of modes 0 and N_phi/2).  FP32
+// with 16 points per thread: the two forward transforms run in lockstep on
+// paired FP32 instructions (A in the low lanes, C in the high ones) through
+// an exchange area of C2 elements that also holds both landing columns; the
+// spectra lie after it.
 // ===========================================================================
 template <typename T>
 __host__ __device__ __forceinline__ size_t bcols_smem_bytes(int nu)
 {
     typedef typename CX<T>::t V;
     const int L = 2 * nu, KS = nu + 2;
+    if (sizeof(T) == 4 && L >= 16)  // paired exchange area (holding both landing columns), then the spectra
+        return sg_align16(sg_padded(L) * sizeof(C2)) + 2 * (size_t)KS * sizeof(V);
     return sg_align16(sg_padded(L) * sizeof(V)) + (size_t)nu * sizeof(V) + 2 * (size_t)KS * sizeof(V);
 }
 
@@ -688,9 +742,10 @@ __global__ void SG_COLS_BOUNDS(T, NTB) k_bwd_cols(const typename CX<T>::t* __res
     const int L = 2 * nu, NT = L / E, half = nphi / 2, KS = nu + 2;
     const int t = threadIdx.x;
     const int m = blockIdx.x;
+    constexpr bool paired = sizeof(T) == 4 && E == 16;
     V* sm = reinterpret_cast<V*>(smraw);
-    V* cs = reinterpret_cast<V*>(smraw + sg_align16(sg_padded(L) * sizeof(V)));  // nu entries
-    V* kr_s = cs + nu;
+    V* cs = paired ? sm + nu : reinterpret_cast<V*>(smraw + sg_align16(sg_padded(L) * sizeof(V)));  // nu entries
+    V* kr_s = paired ? reinterpret_cast<V*>(smraw + sg_align16(sg_padded(L) * sizeof(C2))) : cs + nu;
     V* kp_s = kr_s + KS;
     if (t == 0) {
         sg_mbar_init(&bar[0], 1);
@@ -713,6 +768,42 @@ __global__ void SG_COLS_BOUNDS(T, NTB) k_bwd_cols(const typename CX<T>::t* __res
         sg_mbar_wait_bounded(&bar[1], 0, err, 1);
         return;
     }
+    if constexpr (paired) {
+        if (__syncthreads_or(!sg_mbar_wait_bounded(&bar[1], 0, err, 1))) return;
+        C2 w[E];  // (X_a, X_c) of each frequency, paired
+#pragma unroll
+        for (int e = 0; e < E; e++)
+            w[e] = (e < E / 2) ? c2(sm[t + e * NT], cs[t + e * NT]) : c2(V{0, 0}, V{0, 0});
+        sg_fft_pair<-1>(w, reinterpret_cast<C2*>(smraw), L, log2L, t, twd.h);  // waits for the landing reads
+        V y[E];
+        if (m == 0) {
+            // X_a is the FFT of (DC + i Nyquist); the phi kernel vanishes at
+            // modes 0 and N_phi/2, so X_c is not needed
+#pragma unroll
+            for (int e = 0; e < E; e++) sm[sg_pad(t + e * NT)] = c2_lo(w[e]);
+            __syncthreads();
+#pragma unroll
+            for (int e = 0; e < E; e++) {
+                const int k = t + e * NT;
+                const V z = c2_lo(w[e]), zc = cconj(sm[sg_pad((L - k) & (L - 1))]);
+                const V a = cscale(cadd(z, zc), (T)0.5);
+                const V d = csub(z, zc);
+                const V b = V{d.y * (T)0.5, -d.x * (T)0.5};
+                y[e] = cadd(cmul(a, cconj(khat_r_s(kr_s, k, L, nu))), cmuli(cmul(b, cconj(khat_r_s(kp_s, k, L, nu)))));
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < E; e++) {
+                const int k = t + e * NT;
+                y[e] = cadd(cmul(c2_lo(w[e]), cconj(khat_r_s(kr_s, k, L, nu))),
+                            cmul(c2_hi(w[e]), cconj(khat_p_s(kp_s, k, L, nu))));
+            }
+        }
+        fft<E, +1>(y, sm, L, log2L, t, twd);  // waits for the mirror reads
+#pragma unroll
+        for (int e = 0; e < E / 2; e++) sg_st_hint(B + (size_t)m * nu + t + e * NT, y[e], keep);
+        return;
+    } else {
     V v[E];
 #pragma unroll
     for (int e = 0; e < E; e++) v[e] = (e < E / 2) ? sm[t + e * NT] : V{0, 0};
@@ -769,6 +860,7 @@ __global__ void SG_COLS_BOUNDS(T, NTB) k_bwd_cols(const typename CX<T>::t* __res
 #pragma unroll
             for (int e = 0; e < E / 2; e++) sg_st_hint(B + (size_t)m * nu + t + e * NT, cconj(v[e]), keep);
         }
+    }
     }
 }
 

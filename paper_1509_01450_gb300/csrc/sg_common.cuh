@@ -14,6 +14,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #define SG_NMAX 16384  // longest transform length; twiddle table length
 
 template <typename T>
@@ -471,8 +473,19 @@ __device__ __forceinline__ void sg_pass_store(const V (&v)[E], V* sm, int t, int
         const int b = t + s * NT;
         const int k = b & (Ns - 1);
         const int base = (b - k) * R + k;
+        if (Ns == 1 || (Ns & 15) == 0) {
+            // the padding commutes with the stride: pad(base + r Ns) =
+            // pad(base) + r (Ns + Ns/16) for Ns a multiple of 16, and
+            // pad(base) + r for Ns = 1 (R divides 16, so base..base+R-1 stay
+            // in one 16-element group): one index computation per butterfly
+            V* p = sm + sg_pad(base);
+            const int st = Ns == 1 ? 1 : Ns + (Ns >> 4);
 #pragma unroll
-        for (int r = 0; r < R; r++) sm[sg_pad(base + r * Ns)] = v[s + r * (E / R)];
+            for (int r = 0; r < R; r++) p[r * st] = v[s + r * (E / R)];
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; r++) sm[sg_pad(base + r * Ns)] = v[s + r * (E / R)];
+        }
     }
 }
 
@@ -480,10 +493,19 @@ template <int R, int E, typename V>
 __device__ __forceinline__ void sg_pass_load(V (&v)[E], const V* sm, int t, int NT, int N)
 {
 #pragma unroll
+    const int M = N / R;
+#pragma unroll
     for (int s = 0; s < E / R; s++) {
         const int b = t + s * NT;
+        if ((M & 15) == 0) {  // as in sg_pass_store: pad(b + r M) = pad(b) + r (M + M/16)
+            const V* p = sm + sg_pad(b);
+            const int st = M + (M >> 4);
 #pragma unroll
-        for (int r = 0; r < R; r++) v[s + r * (E / R)] = sm[sg_pad(b + r * (N / R))];
+            for (int r = 0; r < R; r++) v[s + r * (E / R)] = p[r * st];
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; r++) v[s + r * (E / R)] = sm[sg_pad(b + r * M)];
+        }
     }
 }
 
@@ -613,6 +635,204 @@ __device__ __forceinline__ void sg_fft(V (&v)[E], V* sm, int N, int log2N, int t
         sg_pass_load<16, E>(v, sm, t, NT, N);
         sync();
         sg_pass16_tw<DIR>(v, p == 0 ? tws.w[0] : (p == 1 ? tws.w[1] : tws.w[2]));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Two FP32 transforms in lockstep.  F2 holds two floats in one 64-bit
+// register pair, and its arithmetic uses the paired FP32 instructions of
+// sm_100 and later (add/sub/mul/fma .f32x2): one instruction does the same
+// operation for both transforms.  C2 holds element e of both transforms:
+// real parts in x, imaginary parts in y.  Every step of a transform is the
+// same for the two, so nothing is ever moved between the lanes.
+// ---------------------------------------------------------------------------
+struct F2 {
+    unsigned long long v;
+};
+__device__ __forceinline__ F2 f2(float a, float b)
+{
+    F2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float f2_lo(F2 a)
+{
+    float x, y;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(x), "=f"(y) : "l"(a.v));
+    return x;
+}
+__device__ __forceinline__ float f2_hi(F2 a)
+{
+    float x, y;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(x), "=f"(y) : "l"(a.v));
+    return y;
+}
+__device__ __forceinline__ F2 operator+(F2 a, F2 b)
+{
+    F2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+__device__ __forceinline__ F2 operator-(F2 a, F2 b)
+{
+    F2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+__device__ __forceinline__ F2 operator*(F2 a, F2 b)
+{
+    F2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+__device__ __forceinline__ F2 f2_fma(F2 a, F2 b, F2 c)  // a b + c
+{
+    F2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+    return r;
+}
+
+struct __align__(16) C2 {
+    F2 x, y;
+};
+__device__ __forceinline__ C2 c2(float2 a, float2 b) { return C2{f2(a.x, b.x), f2(a.y, b.y)}; }
+__device__ __forceinline__ float2 c2_lo(C2 a) { return make_float2(f2_lo(a.x), f2_lo(a.y)); }
+__device__ __forceinline__ float2 c2_hi(C2 a) { return make_float2(f2_hi(a.x), f2_hi(a.y)); }
+__device__ __forceinline__ C2 c2_bcast(float2 w) { return C2{f2(w.x, w.x), f2(w.y, w.y)}; }
+__device__ __forceinline__ C2 cadd(C2 a, C2 b) { return C2{a.x + b.x, a.y + b.y}; }
+__device__ __forceinline__ C2 csub(C2 a, C2 b) { return C2{a.x - b.x, a.y - b.y}; }
+// (a.x + i a.y)(b.x + i b.y): five paired instructions for the two products
+__device__ __forceinline__ C2 cmul(C2 a, C2 b) { return C2{a.x * b.x - a.y * b.y, f2_fma(a.x, b.y, a.y * b.x)}; }
+
+template <int DIR>
+__device__ __forceinline__ void sg_dft4v(C2& a0, C2& a1, C2& a2, C2& a3)
+{
+    // as the scalar one, with the factor DIR i of the odd difference folded
+    // into the final additions (no negation instructions)
+    const C2 t0 = cadd(a0, a2), t1 = csub(a0, a2), t2 = cadd(a1, a3), d = csub(a1, a3);
+    a0 = cadd(t0, t2);
+    a2 = csub(t0, t2);
+    if (DIR > 0) {  // t3 = i d = (-d.y, d.x)
+        a1 = C2{t1.x - d.y, t1.y + d.x};
+        a3 = C2{t1.x + d.y, t1.y - d.x};
+    } else {  // t3 = -i d = (d.y, -d.x)
+        a1 = C2{t1.x + d.y, t1.y - d.x};
+        a3 = C2{t1.x - d.y, t1.y + d.x};
+    }
+}
+
+// e^{DIR 2 pi i j / 16} a for the constant twiddles of the radix-16 butterfly
+template <int DIR, int J>
+__device__ __forceinline__ C2 sg_mulw16(C2 a)
+{
+    const float C1 = 0.92387953251128675613f, S1 = 0.38268343236508977173f, R2 = 0.70710678118654752440f;
+    float c = 1.f, s = 0.f;
+    switch (J) {
+        case 1: c = C1; s = S1; break;
+        case 2: c = R2; s = R2; break;
+        case 3: c = S1; s = C1; break;
+        case 6: c = -R2; s = R2; break;
+        case 9: c = -C1; s = -S1; break;
+        default: break;
+    }
+    s = DIR * s;
+    if (J == 0) return a;
+    if (J == 4) {  // times DIR i: one negation
+        const F2 z = f2(0.f, 0.f);
+        return DIR > 0 ? C2{z - a.y, a.x} : C2{a.y, z - a.x};
+    }
+    const F2 cc = f2(c, c), ss = f2(s, s);
+    return C2{a.x * cc - a.y * ss, f2_fma(a.x, ss, a.y * cc)};
+}
+
+// e^{DIR i pi k / 4} a, k = 1, 3, for the radix-8 butterfly
+template <int DIR, int K>
+__device__ __forceinline__ C2 sg_mulw8(C2 a)
+{
+    const float r = 0.70710678118654752440f;
+    const F2 rr = f2(r, r), nr = f2(-r, -r);
+    if (K == 1) return DIR > 0 ? C2{(a.x - a.y) * rr, (a.y + a.x) * rr} : C2{(a.x + a.y) * rr, (a.y - a.x) * rr};
+    return DIR > 0 ? C2{(a.x + a.y) * nr, (a.x - a.y) * rr} : C2{(a.x - a.y) * nr, (a.x + a.y) * nr};
+}
+
+template <int DIR>
+__device__ __forceinline__ void sg_dft8(C2* a)
+{
+    sg_dft4v<DIR>(a[0], a[2], a[4], a[6]);
+    sg_dft4v<DIR>(a[1], a[3], a[5], a[7]);
+    const C2 o1 = sg_mulw8<DIR, 1>(a[3]);
+    const C2 o3 = sg_mulw8<DIR, 3>(a[7]);
+    const C2 e0 = a[0], e1 = a[2], e2 = a[4], e3 = a[6], o0 = a[1], d = a[5];
+    a[0] = cadd(e0, o0);
+    a[4] = csub(e0, o0);
+    a[1] = cadd(e1, o1);
+    a[5] = csub(e1, o1);
+    if (DIR > 0) {  // o2 = i d
+        a[2] = C2{e2.x - d.y, e2.y + d.x};
+        a[6] = C2{e2.x + d.y, e2.y - d.x};
+    } else {
+        a[2] = C2{e2.x + d.y, e2.y - d.x};
+        a[6] = C2{e2.x - d.y, e2.y + d.x};
+    }
+    a[3] = cadd(e3, o3);
+    a[7] = csub(e3, o3);
+}
+
+// Two transforms of length N (E = 16 points per thread each), twiddles from
+// the registers of sg_fft_twiddles (the same for both).  Same exchange
+// pattern as sg_fft; sm holds sg_padded(N) C2 elements (16 bytes each).
+template <int DIR, typename Sync = SgSyncBlock>
+__device__ __forceinline__ void sg_fft_pair(C2 (&v)[16], C2* sm, int N, int log2N, int t, const SgTwid<float2>& tws,
+                                            const Sync& sync = Sync())
+{
+    constexpr int E = 16;
+    const int NT = N / E;
+    const int rem = log2N & 3;
+    const int n16 = (log2N >> 2) - (rem == 0 ? 1 : 0);
+    auto first = [&](auto Rc) {
+        constexpr int R = decltype(Rc)::value;
+#pragma unroll
+        for (int s = 0; s < E / R; s++) {
+            C2 a[R];
+#pragma unroll
+            for (int r = 0; r < R; r++) a[r] = v[s + r * (E / R)];
+            sg_dft<R, DIR>(a);
+#pragma unroll
+            for (int r = 0; r < R; r++) v[s + r * (E / R)] = a[r];
+        }
+    };
+    if (rem == 1)
+        first(std::integral_constant<int, 2>());
+    else if (rem == 2)
+        first(std::integral_constant<int, 4>());
+    else if (rem == 3)
+        first(std::integral_constant<int, 8>());
+    else
+        first(std::integral_constant<int, 16>());
+    if (n16 == 0) return;
+    sync();  // the caller may have just read sm
+    if (rem == 1)
+        sg_pass_store<2, E>(v, sm, t, NT, 1);
+    else if (rem == 2)
+        sg_pass_store<4, E>(v, sm, t, NT, 1);
+    else if (rem == 3)
+        sg_pass_store<8, E>(v, sm, t, NT, 1);
+    else
+        sg_pass_store<16, E>(v, sm, t, NT, 1);
+    int Ns = rem == 0 ? 16 : (1 << rem);
+#pragma unroll 1
+    for (int p = 0; p < n16; p++) {
+        if (p > 0) {
+            sg_pass_store<16, E>(v, sm, t, NT, Ns);
+            Ns *= 16;
+        }
+        sync();
+        sg_pass_load<16, E>(v, sm, t, NT, N);
+        sync();
+        float2 w = p == 0 ? tws.w[0] : (p == 1 ? tws.w[1] : tws.w[2]);
+        if (DIR > 0) w.y = -w.y;
+        sg_twiddle_powers<16>(v, c2_bcast(w));
+        sg_dft<16, DIR>(v);
     }
 }
 
