@@ -191,6 +191,55 @@ def run_reference(args):
     return 0
 
 
+def batch_throughput(torch, dev, flush, n_disks: int = 256, seed: int = 1450, reps: int = 10):
+    """cells/s of the batching form: n_disks exponential disks with spirals,
+    N_u in {128..1024} and N_phi in {256..2048} drawn per disk, one plan per
+    distinct size, all enqueued by one sg_forces_batched call; timed eagerly
+    and as a replayed CUDA graph of that call (L2 flushed before each)."""
+    import workloads
+    from paper_1509_01450_gb300 import Plan, forces_batched
+
+    disks = workloads.batch_disks(n_disks, seed)
+    plans = {}
+    for d in disks:
+        if (d.nu, d.nphi) not in plans:
+            plans[(d.nu, d.nphi)] = Plan(d.nu, d.nphi, d.u_min, d.du, 1.0, "float32").build()
+    sig = [torch.tensor(d.sigma(), dtype=torch.float32, device=dev) for d in disks]
+    outs = [(torch.empty_like(s), torch.empty_like(s)) for s in sig]
+    items = [(plans[(d.nu, d.nphi)], s, a, b) for d, s, (a, b) in zip(disks, sig, outs)]
+    cells = sum(d.nu * d.nphi for d in disks)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for a, b in ev:
+            flush.zero_()
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize()
+        return statistics.mean(a.elapsed_time(b) for a, b in ev)
+
+    for _ in range(3):
+        forces_batched(items, stream=stream)
+    eager_ms = timed(lambda: forces_batched(items, stream=stream))
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        forces_batched(items, stream=side)
+    stream.wait_stream(side)
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g):
+        forces_batched(items, stream=torch.cuda.current_stream())
+    g.replay()
+    torch.cuda.synchronize()
+    graph_ms = timed(g.replay)
+    return {"workload": f"{n_disks} disks, seed {seed}, {len(plans)} sizes, {cells} cells", "unit": "cells/s",
+            "value": cells / (eager_ms * 1e-3), "ms": eager_ms,
+            "graph_value": cells / (graph_ms * 1e-3), "graph_ms": graph_ms, "launches": 3 * n_disks}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -316,6 +365,9 @@ def run_ours(args):
     e2e_ms = e0.elapsed_time(e1) / n_e2e
     e2e_value = ws * cells / (e2e_ms * 1e-3)
 
+    # ---- batching form: 256 uneven disks through sg_forces_batched ----------
+    batch = None if args.no_batch else batch_throughput(torch, dev, flush)
+
     if rank == 0:
         clocks = clk.summary()
         line = {
@@ -337,6 +389,7 @@ def run_ours(args):
                      "fp32_speedup": fp64_ms / ms},
             "accuracy": {"fp32_vs_fp64_gpu_rel_l2": rel_fp32_vs_fp64},
             "build_s": build_s,
+            "batched": batch,
             "e2e": {"value": e2e_value, "unit": "cells/s", "ms_per_step": e2e_ms,
                     "h2d_bytes_per_step": cells * 4, "d2h_bytes_per_step": 2 * cells * 4},
             "gpu_launches": 3 * args.steps,
@@ -359,6 +412,7 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--cpu-targets", type=int, default=2048)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 256-disk batching measurement")
     ap.add_argument("--size", default=None, help="NUxNPHI override (profiling runs only; not a bench line)")
     args = ap.parse_args()
     if args.warmup < 3:

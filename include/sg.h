@@ -166,9 +166,14 @@ typedef struct {
 
 /*
  * Forward pass for n disks of possibly different sizes, all SG_F32 or all
- * SG_F64, enqueued in item order on stream.  items is a host array; every
- * item is validated before any work is enqueued.  Allocates nothing;
- * capturable in a CUDA graph.
+ * SG_F64.  items is a host array; every item is validated before any work
+ * is enqueued.  Items that share a plan share its workspace and run in item
+ * order.  When the items use several plans, each plan's items run on that
+ * plan's own stream, forked from `stream` and joined back to it by events,
+ * so disks of different sizes run concurrently; work enqueued on `stream`
+ * afterwards waits for all of them.  Allocates nothing; capturable in a
+ * CUDA graph (the forks become parallel branches).  A plan may appear in
+ * only one batch or call in flight at a time.
  */
 sg_status sg_forces_batched(const sg_batch_item* items, int n, cudaStream_t stream);
 

@@ -5,6 +5,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "sg_internal.cuh"
@@ -34,6 +35,9 @@ static void free_plan(sg_plan* p)
 {
     if (p->have_ev)
         for (int i = 0; i < 4; i++) cudaEventDestroy(p->ev[i]);
+    if (p->bjoin) cudaEventDestroy(p->bjoin);
+    if (p->bfork) cudaEventDestroy(p->bfork);
+    if (p->bstream) cudaStreamDestroy(p->bstream);
     void* bufs[] = {p->tw, p->wa, p->wb, p->wc, p->kr, p->kp, p->wpre, p->wpost, p->tw64, p->cells, p->keff,
                     p->h_sigma, p->h_fr, p->h_fp, p->derr};
     for (void* b : bufs)
@@ -130,7 +134,11 @@ sg_status sg_plan_create(sg_plan** out, int nu, int nphi, double u_min, double d
         free_plan(p);
         return st;
     }
-    if (cudaMemset(p->derr, 0, 16) != cudaSuccess) {
+    if (cudaMemset(p->derr, 0, 16) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&p->bstream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->bfork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->bjoin, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
         free_plan(p);
         return SG_ERR_CUDA;
     }
@@ -356,9 +364,31 @@ sg_status sg_forces_batched(const sg_batch_item* items, int n, cudaStream_t stre
         if (st) return st;
         if (items[b].plan->dtype != items[0].plan->dtype) return SG_ERR_ARG;
     }
-    for (int b = 0; b < n; b++) {
-        sg_status st = sg_forces(items[b].plan, items[b].sigma, items[b].F_r, items[b].F_phi, stream);
-        if (st) return st;
+    // Items of one plan share its workspace and run in item order; items of
+    // different plans are independent.  With several plans, each plan's items
+    // go to the plan's own stream, forked from `stream` and joined back to it
+    // by events (in a captured graph: parallel branches), so that the small
+    // launches of different sizes share the GPU.
+    std::vector<sg_plan*> plans;
+    for (int b = 0; b < n; b++)
+        if (std::find(plans.begin(), plans.end(), items[b].plan) == plans.end()) plans.push_back(items[b].plan);
+    if (plans.size() <= 1) {
+        for (int b = 0; b < n; b++) {
+            sg_status st = sg_forces(items[b].plan, items[b].sigma, items[b].F_r, items[b].F_phi, stream);
+            if (st) return st;
+        }
+        return SG_OK;
+    }
+    SG_TRY(cudaEventRecord(plans[0]->bfork, stream));
+    for (sg_plan* p : plans) {
+        SG_TRY(cudaStreamWaitEvent(p->bstream, plans[0]->bfork, 0));
+        for (int b = 0; b < n; b++) {
+            if (items[b].plan != p) continue;
+            sg_status st = sg_forces(p, items[b].sigma, items[b].F_r, items[b].F_phi, p->bstream);
+            if (st) return st;
+        }
+        SG_TRY(cudaEventRecord(p->bjoin, p->bstream));
+        SG_TRY(cudaStreamWaitEvent(stream, p->bjoin, 0));
     }
     return SG_OK;
 }

@@ -505,16 +505,22 @@ __global__ void SG_COLS_BOUNDS(T, NTB) k_fwd_cols(const typename CX<T>::t* __res
 // ===========================================================================
 // Forward P3: row i, Zhat = Fhat_r + i Fhat_phi (Hermitian halves expanded),
 // inverse FFT, F_r = Re, F_phi = Im, times beta^{-p i}.  Each slot takes two
-// rows of a row block (R = 2 slots rows), one after the other.  Shared
-// memory: the stage of the block's B and C rows (S[m R + r], C after B) and
-// the slots' FFT exchange areas apart from it, so that once both of its
-// rows are read into registers the stage takes the next block's inputs
+// rows of a row block (R = 2 slots rows).  FP32 with 16 points per thread:
+// both rows go through one paired transform whose exchange areas lie over
+// the stage of the block's B and C rows (S[m R + r], C after B); the next
+// block's rows are requested after the transform, while this block's
+// forces are stored.  Otherwise the rows go one after the other with
+// exchange areas apart from the stage, which takes the next block's inputs
 // (tensor copies, or cp.async gathers without maps) during the second FFT.
 // ===========================================================================
 template <typename V>
 __host__ __device__ __forceinline__ size_t rows_inv_smem_bytes(int N, int slots)
 {
     const size_t stage = (size_t)2 * slots * N * sizeof(V);  // B and C, R = 2 slots rows
+    if (sizeof(V) == 8 && N >= 16) {  // FP32, 16 points per thread: paired areas over the stage
+        const size_t pa = (size_t)slots * sg_padded(N) * sizeof(C2);
+        return (pa > stage ? pa : stage) + 128;
+    }
     return stage + (size_t)slots * sg_padded(N) * sizeof(V) + 128;
 }
 
@@ -563,6 +569,47 @@ __global__ void __launch_bounds__(NTB, (sizeof(T) == 4 && NTB == 256) ? 2 : 1) k
         } else {
             asm volatile("cp.async.wait_all;" ::: "memory");
             __syncthreads();
+        }
+        // Z of row r of the block at frequency n = t + e NT, from the stage
+        auto zrow = [&](int r, int e) -> V {
+            const int n = t + e * NT;
+            if (e < E / 2) {
+                if (n == 0) return V{Sb[r].x, 0};
+                const V a = Sb[n * R + r], b = Sc[n * R + r];
+                return V{a.x - b.y, a.y + b.x};  // a + i b
+            }
+            if (n == half) return V{Sb[r].y, 0};
+            const V a = Sb[(N - n) * R + r], b = Sc[(N - n) * R + r];
+            return V{a.x + b.y, -a.y + b.x};  // conj a + i conj b
+        };
+        if constexpr (sizeof(T) == 4 && E == 16) {
+            // both rows of the slot in one paired transform, its exchange
+            // area laid over the stage once every stage read is done
+            C2 w[E];
+#pragma unroll
+            for (int e = 0; e < E; e++) w[e] = c2(zrow(2 * slot, e), zrow(2 * slot + 1, e));
+            __syncthreads();
+            sg_fft_pair<+1>(w, reinterpret_cast<C2*>(Sb) + (size_t)slot * sg_padded(N), N, log2n, t, twd.h, ssync);
+            __syncthreads();  // every slot is done with its area: the stage takes the next block's rows
+            if (more && (!use_map || threadIdx.x < 32)) {
+                if (use_map) sg_fence_proxy_async();
+                issue(rb + gridDim.x);
+            }
+#pragma unroll 1
+            for (int h = 0; h < 2; h++) {
+                const int i = rb * R + 2 * slot + h;
+                if (i < nu) {
+                    const T wt = wpost[i];
+#pragma unroll
+                    for (int e = 0; e < E; e++) {
+                        const int n = t + e * NT;
+                        const V z = h ? c2_hi(w[e]) : c2_lo(w[e]);
+                        Fr[(size_t)i * N + n] = z.x * wt;
+                        Fp[(size_t)i * N + n] = z.y * wt;
+                    }
+                }
+            }
+            continue;
         }
 #pragma unroll 1
         for (int h = 0; h < 2; h++) {

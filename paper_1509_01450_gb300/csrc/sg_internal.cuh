@@ -44,6 +44,8 @@ struct sg_plan {
     SgRowMaps maps[2];     // for R = slots and 2 slots rows per row block
     SgRowMaps na_maps[2];  // the same over the allocation-free scratch
     int have_na_maps;
+    cudaStream_t bstream;         // this plan's items of a batch run here, concurrently with other plans'
+    cudaEvent_t bfork, bjoin;     // fork from / join back to the batch caller's stream
     cudaEvent_t ev[4];  // pass timing (sg_forces_timed), created on first use
     int have_ev;
     int report[4];      // last build: flag bits, failed offsets, one failed (k, q)
