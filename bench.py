@@ -39,7 +39,7 @@ BYTES_PER_CELL = {"rows": 8.0, "cols": 20.0, "inv_rows": 16.0}
 # DRAM bytes (read + write) of one column-pass launch at 2048 x 4096 FP32, from
 # one ncu capture (profiles/k_fwd_cols_2048x4096_full.md), valid only for the
 # kernel sources it was taken on (sha256 prefix of fftconv.cu + sg_common.cuh).
-COLS_TRAFFIC = {"sources_sha256": "b4a8478e556f390a", "bytes_per_launch": 100.802048e6 + 7.158016e6}
+COLS_TRAFFIC = {"sources_sha256": "3f08bbb2f2b6d90e", "bytes_per_launch": 100.829696e6 + 7.202560e6}
 
 
 def kernel_sources_sha() -> str:
