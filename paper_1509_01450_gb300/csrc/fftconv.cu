@@ -174,6 +174,28 @@ __host__ __device__ __forceinline__ size_t row_smem_bytes(int N, int slots)
 {
     return SG_RING * row_buf_elems<V>(N, slots) * sizeof(V) + 128;
 }
+// two adjacent complex values in one 16-byte access (FP32; FP64 takes two)
+__device__ __forceinline__ void ld_pair(const float2* p, float2& a, float2& b)
+{
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    a = make_float2(q.x, q.y);
+    b = make_float2(q.z, q.w);
+}
+__device__ __forceinline__ void ld_pair(const double2* p, double2& a, double2& b)
+{
+    a = p[0];
+    b = p[1];
+}
+__device__ __forceinline__ void st_pair(float2* p, float2 a, float2 b)
+{
+    *reinterpret_cast<float4*>(p) = make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ void st_pair(double2* p, double2 a, double2 b)
+{
+    p[0] = a;
+    p[1] = b;
+}
+
 __device__ __forceinline__ unsigned char* align128(unsigned char* p)
 {
     return reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(p) + 127) & ~(uintptr_t)127);
@@ -319,9 +341,7 @@ __global__ void __launch_bounds__(NTB, (sizeof(T) == 4 && NTB == 256) ? 2 : 1) k
         if (live) {
 #pragma unroll
             for (int e = 0; e < E / 2; e++) {
-                V* d = So + (t + e * NT) * R + 2 * slot;
-                d[0] = x0[e];
-                d[1] = x1[e];
+                st_pair(So + (t + e * NT) * R + 2 * slot, x0[e], x1[e]);
             }
         }
         if (use_map) sg_fence_proxy_async();
@@ -585,9 +605,31 @@ __global__ void __launch_bounds__(NTB, (sizeof(T) == 4 && NTB == 256) ? 2 : 1) k
         if constexpr (sizeof(T) == 4 && E == 16) {
             // both rows of the slot in one paired transform, its exchange
             // area laid over the stage once every stage read is done
+            // the slot's rows r0, r0 + 1 are adjacent in the stage: one
+            // 16-byte read gives both, and Z = B + i C (or its mirror
+            // conj B + i conj C) of both rows is two paired operations
             C2 w[E];
+            const int r0 = 2 * slot;
 #pragma unroll
-            for (int e = 0; e < E; e++) w[e] = c2(zrow(2 * slot, e), zrow(2 * slot + 1, e));
+            for (int e = 0; e < E; e++) {
+                const int n = t + e * NT;
+                const F2 zero = f2(0.f, 0.f);
+                if (e < E / 2 && n == 0) {
+                    const float4 b = *reinterpret_cast<const float4*>(Sb + r0);
+                    w[e] = C2{f2(b.x, b.z), zero};
+                } else if (e >= E / 2 && n == half) {
+                    const float4 b = *reinterpret_cast<const float4*>(Sb + r0);
+                    w[e] = C2{f2(b.y, b.w), zero};
+                } else {
+                    const int mo = (e < E / 2 ? n : N - n) * R + r0;
+                    const float4 a = *reinterpret_cast<const float4*>(Sb + mo);
+                    const float4 b = *reinterpret_cast<const float4*>(Sc + mo);
+                    if (e < E / 2)
+                        w[e] = C2{f2(a.x, a.z) - f2(b.y, b.w), f2(a.y, a.w) + f2(b.x, b.z)};
+                    else
+                        w[e] = C2{f2(a.x, a.z) + f2(b.y, b.w), f2(b.x, b.z) - f2(a.y, a.w)};
+                }
+            }
             __syncthreads();
             sg_fft_pair<+1>(w, reinterpret_cast<C2*>(Sb) + (size_t)slot * sg_padded(N), N, log2n, t, twd.h, ssync);
             __syncthreads();  // every slot is done with its area: the stage takes the next block's rows
@@ -975,16 +1017,16 @@ __global__ void __launch_bounds__(NTB, (sizeof(T) == 4 && NTB == 256) ? 2 : 1) k
                     s0 = V{b0s[0].x, 0};
                     s1 = V{b1s[0].x, 0};
                 } else {
-                    s0 = b0s[n * R];
-                    s1 = b1s[n * R];
+                    ld_pair(b0s + n * R, s0, s1);
                 }
             } else {
                 if (n == half) {
                     s0 = V{b0s[0].y, 0};
                     s1 = V{b1s[0].y, 0};
                 } else {
-                    s0 = cconj(b0s[(N - n) * R]);
-                    s1 = cconj(b1s[(N - n) * R]);
+                    ld_pair(b0s + (N - n) * R, s0, s1);
+                    s0 = cconj(s0);
+                    s1 = cconj(s1);
                 }
             }
             v[e] = cadd(s0, cmuli(s1));
