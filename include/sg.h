@@ -116,11 +116,14 @@ sg_status sg_forces_backward(sg_plan* plan, const void* gF_r, const void* gF_phi
                              cudaStream_t stream);
 
 /*
- * Same as sg_forces with HOST buffers: copies sigma to the device, runs the
- * forward pass and copies F_r, F_phi back, all on stream, then synchronises
- * the stream and returns what sg_plan_check returns.  Uses plan-owned device
- * staging buffers (allocated on first use).  Host buffers should be pinned
- * for full copy bandwidth.
+ * Same as sg_forces with HOST buffers, then synchronises the stream and
+ * returns what sg_plan_check returns.  When all three buffers are pinned and
+ * mapped into the device's address space (cudaHostAlloc, cudaHostRegister
+ * with mapping, torch pin_memory), the row pass reads sigma and the
+ * inverse-row pass writes F_r and F_phi over the host link directly, with
+ * no staging copies.  Otherwise sigma is copied to plan-owned device staging
+ * buffers (allocated on first use), the forward pass runs there, and F_r,
+ * F_phi are copied back, all on stream.
  */
 sg_status sg_forces_host(sg_plan* plan, const void* sigma_h, void* F_r_h, void* F_phi_h, cudaStream_t stream);
 

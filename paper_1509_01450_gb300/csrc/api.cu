@@ -335,11 +335,40 @@ sg_status sg_forces_backward(sg_plan* p, const void* gr, const void* gp, void* g
     return e == cudaSuccess ? SG_OK : SG_ERR_CUDA;
 }
 
+// Device address of a host buffer that the GPU of the plan can read and
+// write directly (pinned and mapped, e.g. cudaHostAlloc or torch pin_memory),
+// or null for pageable memory.
+static void* mapped_host(const void* h, int device)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, h) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
+    (void)device;
+    return a.devicePointer;
+}
+
 sg_status sg_forces_host(sg_plan* p, const void* sigma_h, void* Fr_h, void* Fp_h, cudaStream_t stream)
 {
     if (!p || !sigma_h || !Fr_h || !Fp_h) return SG_ERR_ARG;
     if (!p->built) return SG_ERR_NOT_BUILT;
     const size_t bytes = (size_t)p->nu * p->nphi * p->elem;
+    // Pinned, mapped buffers: the row pass reads sigma and the inverse-row
+    // pass writes F_r, F_phi over the host link directly (no staging copies).
+    void* ds = mapped_host(sigma_h, p->device);
+    void* dr = ds ? mapped_host(Fr_h, p->device) : nullptr;
+    void* dp = dr ? mapped_host(Fp_h, p->device) : nullptr;
+    if (dp && !(((uintptr_t)ds | (uintptr_t)dr | (uintptr_t)dp) & 15) && ds != dr && ds != dp && dr != dp) {
+        PlanView v = view(p);
+        cudaError_t e =
+            p->dtype == SG_F32
+                ? launch_forward<float>(v, (const float*)ds, (float*)dr, (float*)dp, stream, nullptr, true)
+                : launch_forward<double>(v, (const double*)ds, (double*)dr, (double*)dp, stream, nullptr, true);
+        if (e != cudaSuccess) return SG_ERR_CUDA;
+        return sg_plan_check(p, stream);  // synchronises; reports a device-side timeout
+    }
     sg_status st;
     if (!p->h_sigma) {
         if ((st = dev_alloc(p, &p->h_sigma, bytes)) || (st = dev_alloc(p, &p->h_fr, bytes)) ||

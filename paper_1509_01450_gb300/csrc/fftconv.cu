@@ -286,7 +286,7 @@ template <typename T, int E, int NTB>
 __global__ void __launch_bounds__(NTB, (sizeof(T) == 4 && NTB == 256) ? 2 : 1) k_fwd_rows(const T* __restrict__ sigma, const T* __restrict__ wpre,
                                                   typename CX<T>::t* __restrict__ A, int nu, int nphi, int log2n,
                                                   const typename CX<T>::t* __restrict__ tw, int* err,
-                                                  const __grid_constant__ CUtensorMap mapA, int use_map)
+                                                  const __grid_constant__ CUtensorMap mapA, int use_map, int direct)
 {
     typedef typename CX<T>::t V;
     extern __shared__ __align__(128) unsigned char smraw[];
@@ -309,11 +309,13 @@ __global__ void __launch_bounds__(NTB, (sizeof(T) == 4 && NTB == 256) ? 2 : 1) k
         sg_mbar_expect_tx(&bar, bytes);
         sg_bulk_g2s_hint(Si, sigma + (size_t)rb * R * N, bytes, &bar, sg_policy_evict_first());
     };
-    if (threadIdx.x == 0 && blockIdx.x < nblk) issue(blockIdx.x);
+    // direct: sigma is read straight from memory the GPU reaches only by
+    // plain loads (pinned host memory), without the bulk copies
+    if (!direct && threadIdx.x == 0 && blockIdx.x < nblk) issue(blockIdx.x);
     int it = 0;
     for (int rb = blockIdx.x; rb < nblk; rb += gridDim.x, it++) {
         const bool more = rb + (int)gridDim.x < nblk;
-        if (__syncthreads_or(!sg_mbar_wait_bounded(&bar, it & 1, err, 1))) {
+        if (!direct && __syncthreads_or(!sg_mbar_wait_bounded(&bar, it & 1, err, 1))) {
             if (use_map && threadIdx.x < 32) sg_bulk_wait_read();
             return;  // inputs never arrived
         }
@@ -321,7 +323,7 @@ __global__ void __launch_bounds__(NTB, (sizeof(T) == 4 && NTB == 256) ? 2 : 1) k
         const bool live = pair < nu / 2;
         const int i0 = 2 * (live ? pair : 0);
         const T w0 = wpre[i0], w1 = wpre[i0 + 1];
-        const T* rows = Si + (size_t)(2 * slot) * N;
+        const T* rows = direct ? sigma + (size_t)i0 * N : Si + (size_t)(2 * slot) * N;
         V v[E];
 #pragma unroll
         for (int e = 0; e < E; e++) {
@@ -329,7 +331,7 @@ __global__ void __launch_bounds__(NTB, (sizeof(T) == 4 && NTB == 256) ? 2 : 1) k
             v[e] = V{rows[n] * w0, rows[N + n] * w1};
         }
         __syncthreads();  // the input stage is read: it takes the next block's rows
-        if (threadIdx.x == 0 && more) {
+        if (!direct && threadIdx.x == 0 && more) {
             sg_fence_proxy_async();
             issue(rb + gridDim.x);
         }
@@ -1294,7 +1296,8 @@ static const CUtensorMap* row_map(const PlanView& p, int R, int b, int nphi)
     } while (0)
 
 template <typename T>
-cudaError_t launch_forward(const PlanView& p, const T* sigma, T* Fr, T* Fp, cudaStream_t st, cudaEvent_t* ev)
+cudaError_t launch_forward(const PlanView& p, const T* sigma, T* Fr, T* Fp, cudaStream_t st, cudaEvent_t* ev,
+                           bool sigma_direct)
 {
     typedef typename CX<T>::t V;
     const V* tw = (const V*)p.tw;
@@ -1315,7 +1318,8 @@ cudaError_t launch_forward(const PlanView& p, const T* sigma, T* Fr, T* Fp, cuda
                 if (s.threads > 256) k = k_fwd_rows<T, EE, 512>;
             if ((err = set_smem(k, smem, true)) != cudaSuccess) return err;
             k<<<persistent_grid(k, s.threads, smem, nblk, p.sms), s.threads, smem, st>>>(
-                sigma, (const T*)p.wpre, A, p.nu, p.nphi, ln, tw, p.err, mA ? *mA : CUtensorMap{}, mA != nullptr);
+                sigma, (const T*)p.wpre, A, p.nu, p.nphi, ln, tw, p.err, mA ? *mA : CUtensorMap{}, mA != nullptr,
+                sigma_direct ? 1 : 0);
         });
     }
     if (ev && (err = cudaEventRecord(ev[1], st)) != cudaSuccess) return err;
@@ -1434,9 +1438,10 @@ cudaError_t launch_spectra(const PlanView& p, const double* nsr, const double* n
     return cudaGetLastError();
 }
 
-template cudaError_t launch_forward<float>(const PlanView&, const float*, float*, float*, cudaStream_t, cudaEvent_t*);
+template cudaError_t launch_forward<float>(const PlanView&, const float*, float*, float*, cudaStream_t, cudaEvent_t*,
+                                           bool);
 template cudaError_t launch_forward<double>(const PlanView&, const double*, double*, double*, cudaStream_t,
-                                              cudaEvent_t*);
+                                              cudaEvent_t*, bool);
 template cudaError_t launch_backward<float>(const PlanView&, const float*, const float*, float*, cudaStream_t);
 template cudaError_t launch_backward<double>(const PlanView&, const double*, const double*, double*, cudaStream_t);
 template cudaError_t launch_spectra<float2>(const PlanView&, const double*, const double*, double2*, float2*,

@@ -90,8 +90,10 @@ inline PlanView view(const sg_plan* p)
 
 // ev: optional 4 events recorded before P1, after P1, after P2, after P3
 template <typename T>
+// sigma_direct: sigma is memory that the GPU reaches only by plain loads
+// (mapped pinned host memory); the row pass then reads it without bulk copies
 cudaError_t launch_forward(const PlanView& p, const T* sigma, T* Fr, T* Fp, cudaStream_t st,
-                           cudaEvent_t* ev = nullptr);
+                           cudaEvent_t* ev = nullptr, bool sigma_direct = false);
 template <typename T>
 cudaError_t launch_backward(const PlanView& p, const T* gr, const T* gp, T* gs, cudaStream_t st);
 // Tensor maps of the row passes over the buffers bufs[3] (the layout of wa,
