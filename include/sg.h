@@ -50,7 +50,8 @@ typedef enum {
     SG_ERR_CUDA = 3,        /* a CUDA call or launch failed */
     SG_ERR_UNSUPPORTED = 4, /* sizes outside the supported set (see sg_plan_create) */
     SG_ERR_NOT_BUILT = 5,   /* forces requested before sg_kernels_build */
-    SG_ERR_TIMEOUT = 6      /* a bounded device-side wait gave up */
+    SG_ERR_TIMEOUT = 6,     /* a bounded device-side wait gave up */
+    SG_ERR_IO = 7           /* a plan file could not be written or read, or is not one */
 } sg_status;
 
 typedef enum { SG_F32 = 0, SG_F64 = 1 } sg_dtype;
@@ -223,6 +224,32 @@ sg_status sg_plan_build_report(const sg_plan* plan, int report[4]);
  * results are invalid); SG_OK otherwise.
  */
 sg_status sg_plan_check(sg_plan* plan, cudaStream_t stream);
+
+/*
+ * Budget of the device-side waits of the passes for their asynchronous input
+ * copies, in seconds (default 1; at most 60).  A pass whose copies do not
+ * arrive within it sets the plan's error flag (sg_plan_check returns
+ * SG_ERR_TIMEOUT), waits up to one more second for the copies still in
+ * flight, and leaves its outputs unwritten.  0 makes every pass give up at
+ * once: a test of that error path.  Synchronous; not for use while work of
+ * the plan is in flight.
+ */
+sg_status sg_plan_set_wait_limit(sg_plan* plan, double seconds);
+
+/*
+ * Checkpoint of a built plan (the paper prepares its kernels once and keeps
+ * them in memory, Sec. 2): sg_plan_save writes the kernel spectra and the
+ * weight rows in the working dtype, with the plan's sizes, grid, G,
+ * weighting exponent and build tolerance, to a file (synchronises stream).
+ * sg_plan_load creates a built plan from such a file (on the current
+ * device; synchronises stream), which computes the same forces bit for bit
+ * without rebuilding.  A loaded plan holds no FP64 build tables:
+ * sg_plan_kernels and sg_plan_cells return SG_ERR_UNSUPPORTED for it.
+ * SG_ERR_IO: the file cannot be written or read, is truncated or too long,
+ * or is not a plan file of this library.
+ */
+sg_status sg_plan_save(const sg_plan* plan, const char* path, cudaStream_t stream);
+sg_status sg_plan_load(sg_plan** out, const char* path, cudaStream_t stream);
 
 /* Bytes of device memory the plan holds. */
 size_t sg_plan_device_bytes(const sg_plan* plan);

@@ -2,6 +2,8 @@
 // include/sg.h): plan lifecycle, the one-time kernel build, and dispatch of
 // the forward / adjoint passes.
 #include <math.h>
+#include <stdint.h>
+#include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -90,6 +92,7 @@ const char* sg_status_string(sg_status s)
         case SG_ERR_UNSUPPORTED: return "unsupported size";
         case SG_ERR_NOT_BUILT: return "kernels not built (call sg_kernels_build)";
         case SG_ERR_TIMEOUT: return "quadrature or device wait did not converge";
+        case SG_ERR_IO: return "plan file could not be written or read, or is not a plan file of this library";
     }
     return "unknown status";
 }
@@ -134,7 +137,8 @@ sg_status sg_plan_create(sg_plan** out, int nu, int nphi, double u_min, double d
         free_plan(p);
         return st;
     }
-    if (cudaMemset(p->derr, 0, 16) != cudaSuccess ||
+    const unsigned long long flag_block[2] = {0ull, SG_WAIT_NS};  // flags, first-wait budget (ns)
+    if (cudaMemcpy(p->derr, flag_block, 16, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaStreamCreateWithFlags(&p->bstream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&p->bfork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&p->bjoin, cudaEventDisableTiming) != cudaSuccess) {
@@ -192,6 +196,102 @@ sg_status sg_plan_info(const sg_plan* p, int dims[4])
 
 size_t sg_plan_device_bytes(const sg_plan* p) { return p ? p->bytes : 0; }
 
+sg_status sg_plan_set_wait_limit(sg_plan* p, double seconds)
+{
+    if (!p || !(seconds >= 0.0) || !(seconds <= 60.0)) return SG_ERR_ARG;
+    const unsigned long long ns = (unsigned long long)(seconds * 1e9);
+    SG_TRY(cudaMemcpy(reinterpret_cast<unsigned char*>(p->derr) + 8, &ns, sizeof(ns), cudaMemcpyHostToDevice));
+    return SG_OK;
+}
+
+// Plan file: a fixed header, then K̂_r, K̂_phi and the two weight rows in the
+// working dtype, exactly as they sit on the device.
+struct PlanFileHeader {
+    char magic[8];  // "SGPLAN01"
+    int32_t version, nu, nphi, dtype, weight_p, reserved[3];
+    double u_min, du, G, rtol;
+    uint64_t spectrum_bytes, weight_bytes;
+};
+static const char kPlanMagic[8] = {'S', 'G', 'P', 'L', 'A', 'N', '0', '1'};
+
+static size_t spectrum_bytes(const sg_plan* p) { return (size_t)(p->nphi / 2 + 1) * (p->nu + 2) * 2 * p->elem; }
+
+sg_status sg_plan_save(const sg_plan* p, const char* path, cudaStream_t stream)
+{
+    if (!p || !path) return SG_ERR_ARG;
+    if (!p->built) return SG_ERR_NOT_BUILT;
+    const size_t kb = spectrum_bytes(p), wb = (size_t)p->nu * p->elem;
+    std::vector<unsigned char> buf(2 * kb + 2 * wb);
+    SG_TRY(cudaMemcpyAsync(buf.data(), p->kr, kb, cudaMemcpyDeviceToHost, stream));
+    SG_TRY(cudaMemcpyAsync(buf.data() + kb, p->kp, kb, cudaMemcpyDeviceToHost, stream));
+    SG_TRY(cudaMemcpyAsync(buf.data() + 2 * kb, p->wpre, wb, cudaMemcpyDeviceToHost, stream));
+    SG_TRY(cudaMemcpyAsync(buf.data() + 2 * kb + wb, p->wpost, wb, cudaMemcpyDeviceToHost, stream));
+    SG_TRY(cudaStreamSynchronize(stream));
+    PlanFileHeader h;
+    memset(&h, 0, sizeof(h));
+    memcpy(h.magic, kPlanMagic, 8);
+    h.version = 1;
+    h.nu = p->nu;
+    h.nphi = p->nphi;
+    h.dtype = (int32_t)p->dtype;
+    h.weight_p = p->weight_p;
+    h.u_min = p->u_min;
+    h.du = p->du;
+    h.G = p->G;
+    h.rtol = p->rtol;
+    h.spectrum_bytes = kb;
+    h.weight_bytes = wb;
+    FILE* f = fopen(path, "wb");
+    if (!f) return SG_ERR_IO;
+    const bool ok = fwrite(&h, sizeof(h), 1, f) == 1 && fwrite(buf.data(), 1, buf.size(), f) == buf.size();
+    if (fclose(f) != 0 || !ok) return SG_ERR_IO;
+    return SG_OK;
+}
+
+sg_status sg_plan_load(sg_plan** out, const char* path, cudaStream_t stream)
+{
+    if (!out || !path) return SG_ERR_ARG;
+    *out = nullptr;
+    FILE* f = fopen(path, "rb");
+    if (!f) return SG_ERR_IO;
+    PlanFileHeader h;
+    if (fread(&h, sizeof(h), 1, f) != 1 || memcmp(h.magic, kPlanMagic, 8) != 0 || h.version != 1 ||
+        (h.dtype != SG_F32 && h.dtype != SG_F64)) {
+        fclose(f);
+        return SG_ERR_IO;
+    }
+    sg_plan* p = nullptr;
+    sg_status st = sg_plan_create(&p, h.nu, h.nphi, h.u_min, h.du, h.G, (sg_dtype)h.dtype);
+    if (st) {
+        fclose(f);
+        return st;
+    }
+    const size_t kb = spectrum_bytes(p), wb = (size_t)p->nu * p->elem;
+    std::vector<unsigned char> buf(2 * kb + 2 * wb);
+    const bool ok = h.spectrum_bytes == kb && h.weight_bytes == wb && fread(buf.data(), 1, buf.size(), f) == buf.size() &&
+                    fgetc(f) == EOF;
+    fclose(f);
+    if (!ok) {
+        sg_plan_destroy(p);
+        return SG_ERR_IO;
+    }
+    if (cudaMemcpyAsync(p->kr, buf.data(), kb, cudaMemcpyHostToDevice, stream) != cudaSuccess ||
+        cudaMemcpyAsync(p->kp, buf.data() + kb, kb, cudaMemcpyHostToDevice, stream) != cudaSuccess ||
+        cudaMemcpyAsync(p->wpre, buf.data() + 2 * kb, wb, cudaMemcpyHostToDevice, stream) != cudaSuccess ||
+        cudaMemcpyAsync(p->wpost, buf.data() + 2 * kb + wb, wb, cudaMemcpyHostToDevice, stream) != cudaSuccess ||
+        cudaStreamSynchronize(stream) != cudaSuccess) {
+        cudaGetLastError();
+        sg_plan_destroy(p);
+        return SG_ERR_CUDA;
+    }
+    p->weight_p = h.weight_p;
+    p->rtol = h.rtol;
+    p->loaded = 1;
+    p->built = 1;
+    *out = p;
+    return SG_OK;
+}
+
 sg_status sg_kernels_build(sg_plan* p, const sg_build_opts* opts, cudaStream_t stream)
 {
     if (!p) return SG_ERR_ARG;
@@ -205,6 +305,7 @@ sg_status sg_kernels_build(sg_plan* p, const sg_build_opts* opts, cudaStream_t s
     // beta^{p (i - i_ref)} must stay in range for both dtypes
     if (fabs((double)wp * p->du * p->nu) > 60.0) return SG_ERR_UNSUPPORTED;
     p->weight_p = wp;
+    p->rtol = rtol;
     const int nu = p->nu, nphi = p->nphi, L = 2 * nu;
 
     // row weights
@@ -447,6 +548,7 @@ sg_status sg_plan_kernels(sg_plan* p, double* Kr_h, double* Kp_h, cudaStream_t s
 {
     if (!p || !Kr_h || !Kp_h) return SG_ERR_ARG;
     if (!p->built) return SG_ERR_NOT_BUILT;
+    if (p->loaded) return SG_ERR_UNSUPPORTED;  // plan files carry the spectra only
     const size_t n = (size_t)(2 * p->nu - 1) * p->nphi;
     SG_TRY(cudaMemcpyAsync(Kr_h, p->keff, n * sizeof(double), cudaMemcpyDeviceToHost, stream));
     SG_TRY(cudaMemcpyAsync(Kp_h, p->keff + n, n * sizeof(double), cudaMemcpyDeviceToHost, stream));
@@ -458,6 +560,7 @@ sg_status sg_plan_cells(sg_plan* p, double* cells_h, cudaStream_t stream)
 {
     if (!p || !cells_h) return SG_ERR_ARG;
     if (!p->built) return SG_ERR_NOT_BUILT;
+    if (p->loaded) return SG_ERR_UNSUPPORTED;
     const size_t n = (size_t)6 * (2 * p->nu + 1) * p->nphi;
     SG_TRY(cudaMemcpyAsync(cells_h, p->cells, n * sizeof(double), cudaMemcpyDeviceToHost, stream));
     SG_TRY(cudaStreamSynchronize(stream));

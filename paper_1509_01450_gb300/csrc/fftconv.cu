@@ -34,6 +34,8 @@
 #include <mutex>
 #include <tuple>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "sg_internal.cuh"
 
 namespace sg {
@@ -288,6 +290,7 @@ __global__ void __launch_bounds__(NTB, (sizeof(T) == 4 && NTB == 256) ? 2 : 1) k
                                                   const typename CX<T>::t* __restrict__ tw, int* err,
                                                   const __grid_constant__ CUtensorMap mapA, int use_map, int direct)
 {
+    const unsigned long long wlim = sg_wait_budget(err);  // read once, early
     typedef typename CX<T>::t V;
     extern __shared__ __align__(128) unsigned char smraw[];
     __shared__ __align__(8) uint64_t bar;
@@ -315,7 +318,7 @@ __global__ void __launch_bounds__(NTB, (sizeof(T) == 4 && NTB == 256) ? 2 : 1) k
     int it = 0;
     for (int rb = blockIdx.x; rb < nblk; rb += gridDim.x, it++) {
         const bool more = rb + (int)gridDim.x < nblk;
-        if (!direct && __syncthreads_or(!sg_mbar_wait_bounded(&bar, it & 1, err, 1))) {
+        if (!direct && __syncthreads_or(!sg_mbar_wait_bounded(&bar, it & 1, err, 1, wlim))) {
             if (use_map && threadIdx.x < 32) sg_bulk_wait_read();
             return;  // inputs never arrived
         }
@@ -399,6 +402,7 @@ __global__ void SG_COLS_BOUNDS(T, NTB) k_fwd_cols(const typename CX<T>::t* __res
                                                   typename CX<T>::t* __restrict__ Cp, int nu, int nphi, int log2L,
                                                   const typename CX<T>::t* __restrict__ tw, int* err)
 {
+    const unsigned long long wlim = sg_wait_budget(err);  // read once, early
     typedef typename CX<T>::t V;
     extern __shared__ __align__(128) unsigned char smraw[];
     __shared__ __align__(8) uint64_t bar[2];  // [0]: the column, [1]: the spectra
@@ -428,8 +432,8 @@ __global__ void SG_COLS_BOUNDS(T, NTB) k_fwd_cols(const typename CX<T>::t* __res
     const Twd<E, V> twd = make_twd<E>(log2L, t, tw);
     const uint64_t keep = sg_policy_evict_last();  // the row pass reads B and C from L2
     // inputs that never arrive: leave (all threads together) after a last wait for the spectra
-    if (__syncthreads_or(!sg_mbar_wait_bounded(&bar[0], 0, err, 1))) {
-        sg_mbar_wait_bounded(&bar[1], 0, err, 1);
+    if (__syncthreads_or(!sg_mbar_wait_bounded(&bar[0], 0, err, 1, wlim))) {
+        sg_mbar_wait_bounded(&bar[1], 0, err, 1, wlim);
         return;
     }
     V v[E];
@@ -437,7 +441,7 @@ __global__ void SG_COLS_BOUNDS(T, NTB) k_fwd_cols(const typename CX<T>::t* __res
     for (int e = 0; e < E; e++) v[e] = (e < E / 2) ? sm[t + e * NT] : V{0, 0};  // rows >= nu: zero pad
     if constexpr (sizeof(T) == 4 && E == 16) {
         fft<E, -1>(v, sm, L, log2L, t, twd);  // the spectra land meanwhile
-        if (__syncthreads_or(!sg_mbar_wait_bounded(&bar[1], 0, err, 1))) return;
+        if (__syncthreads_or(!sg_mbar_wait_bounded(&bar[1], 0, err, 1, wlim))) return;
         C2 w[E];  // (Y_r, Y_phi) of each frequency, paired
         if (m == 0) {
             // v holds the FFT of (DC + i Nyquist): separate the two real
@@ -478,7 +482,7 @@ __global__ void SG_COLS_BOUNDS(T, NTB) k_fwd_cols(const typename CX<T>::t* __res
     for (int pass = 0; pass < 3; pass++) {
         fft<E, -1>(v, sm, L, log2L, t, twd);  // pass 0: the spectra land meanwhile
         if (pass == 0) {
-            if (__syncthreads_or(!sg_mbar_wait_bounded(&bar[1], 0, err, 1))) return;
+            if (__syncthreads_or(!sg_mbar_wait_bounded(&bar[1], 0, err, 1, wlim))) return;
             if (m == 0) {
                 // v holds the FFT of (DC + i Nyquist): separate the two real
                 // sequences and apply the kernels of modes 0 and N_phi/2; the
@@ -555,6 +559,7 @@ __global__ void __launch_bounds__(NTB, (sizeof(T) == 4 && NTB == 256) ? 2 : 1) k
                                                       const __grid_constant__ CUtensorMap mapB,
                                                       const __grid_constant__ CUtensorMap mapC, int use_map)
 {
+    const unsigned long long wlim = sg_wait_budget(err);  // read once, early
     typedef typename CX<T>::t V;
     extern __shared__ __align__(128) unsigned char smraw[];
     __shared__ __align__(8) uint64_t bar;
@@ -587,7 +592,7 @@ __global__ void __launch_bounds__(NTB, (sizeof(T) == 4 && NTB == 256) ? 2 : 1) k
     for (int rb = blockIdx.x; rb < nblk; rb += gridDim.x, it++) {
         const bool more = rb + (int)gridDim.x < nblk;
         if (use_map) {
-            if (__syncthreads_or(!sg_mbar_wait_bounded(&bar, it & 1, err, 1))) return;  // inputs never arrived
+            if (__syncthreads_or(!sg_mbar_wait_bounded(&bar, it & 1, err, 1, wlim))) return;  // inputs never arrived
         } else {
             asm volatile("cp.async.wait_all;" ::: "memory");
             __syncthreads();
@@ -716,6 +721,7 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 512) k_bwd_rows(const T
                                                   const __grid_constant__ CUtensorMap mapA,
                                                   const __grid_constant__ CUtensorMap mapC, int use_map)
 {
+    const unsigned long long wlim = sg_wait_budget(err);  // read once, early
     typedef typename CX<T>::t V;
     extern __shared__ __align__(128) unsigned char smraw[];
     __shared__ __align__(8) uint64_t bar[SG_RING];
@@ -754,8 +760,8 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 512) k_bwd_rows(const T
                 issue(rb + gridDim.x, qn);
             }
         }
-        if (__syncthreads_or(!sg_mbar_wait_bounded(&bar[q], (it / SG_RING) & 1, err, 1))) {
-            if (more) sg_mbar_wait_bounded(&bar[qn], ((it + 1) / SG_RING) & 1, err, 1);
+        if (__syncthreads_or(!sg_mbar_wait_bounded(&bar[q], (it / SG_RING) & 1, err, 1, wlim))) {
+            if (more) sg_mbar_wait_bounded(&bar[qn], ((it + 1) / SG_RING) & 1, err, 1, wlim);
             if (use_map && producer) sg_bulk_wait_read();
             return;
         }
@@ -827,6 +833,7 @@ __global__ void SG_COLS_BOUNDS(T, NTB) k_bwd_cols(const typename CX<T>::t* __res
                                                   typename CX<T>::t* __restrict__ B, int nu, int nphi, int log2L,
                                                   const typename CX<T>::t* __restrict__ tw, int* err)
 {
+    const unsigned long long wlim = sg_wait_budget(err);  // read once, early
     typedef typename CX<T>::t V;
     extern __shared__ __align__(128) unsigned char smraw[];
     __shared__ __align__(8) uint64_t bar[2];  // [0]: the A column, [1]: the C column and the spectra
@@ -855,12 +862,12 @@ __global__ void SG_COLS_BOUNDS(T, NTB) k_bwd_cols(const typename CX<T>::t* __res
     }
     const Twd<E, V> twd = make_twd<E>(log2L, t, tw);
     const uint64_t keep = sg_policy_evict_last();
-    if (__syncthreads_or(!sg_mbar_wait_bounded(&bar[0], 0, err, 1))) {
-        sg_mbar_wait_bounded(&bar[1], 0, err, 1);
+    if (__syncthreads_or(!sg_mbar_wait_bounded(&bar[0], 0, err, 1, wlim))) {
+        sg_mbar_wait_bounded(&bar[1], 0, err, 1, wlim);
         return;
     }
     if constexpr (paired) {
-        if (__syncthreads_or(!sg_mbar_wait_bounded(&bar[1], 0, err, 1))) return;
+        if (__syncthreads_or(!sg_mbar_wait_bounded(&bar[1], 0, err, 1, wlim))) return;
         C2 w[E];  // (X_a, X_c) of each frequency, paired
 #pragma unroll
         for (int e = 0; e < E; e++)
@@ -908,7 +915,7 @@ __global__ void SG_COLS_BOUNDS(T, NTB) k_bwd_cols(const typename CX<T>::t* __res
     for (int pass = 0; pass < 3; pass++) {
         fft<E, -1>(v, sm, L, log2L, t, twd);
         if (pass == 0) {
-            if (__syncthreads_or(!sg_mbar_wait_bounded(&bar[1], 0, err, 1))) return;
+            if (__syncthreads_or(!sg_mbar_wait_bounded(&bar[1], 0, err, 1, wlim))) return;
             if (m == 0) {
 #pragma unroll
                 for (int e = 0; e < E; e++) sm[sg_pad(t + e * NT)] = v[e];
@@ -973,6 +980,7 @@ __global__ void __launch_bounds__(NTB, (sizeof(T) == 4 && NTB == 256) ? 2 : 1) k
                                                       int nphi, int log2n, const typename CX<T>::t* __restrict__ tw,
                                                       int* err, const __grid_constant__ CUtensorMap mapB, int use_map)
 {
+    const unsigned long long wlim = sg_wait_budget(err);  // read once, early
     typedef typename CX<T>::t V;
     extern __shared__ __align__(128) unsigned char smraw[];
     __shared__ __align__(8) uint64_t bar;
@@ -1002,7 +1010,7 @@ __global__ void __launch_bounds__(NTB, (sizeof(T) == 4 && NTB == 256) ? 2 : 1) k
     for (int rb = blockIdx.x; rb < nblk; rb += gridDim.x, it++) {
         const bool more = rb + (int)gridDim.x < nblk;
         if (use_map) {
-            if (__syncthreads_or(!sg_mbar_wait_bounded(&bar, it & 1, err, 1))) return;
+            if (__syncthreads_or(!sg_mbar_wait_bounded(&bar, it & 1, err, 1, wlim))) return;
         } else {
             asm volatile("cp.async.wait_all;" ::: "memory");
             __syncthreads();
@@ -1195,6 +1203,13 @@ static cudaError_t set_smem(K kernel, size_t smem, bool carveout = false)
     return e;
 }
 
+// NVTX range around the enqueue of one pass (visible in Nsight timelines;
+// near-free when no tool is attached)
+struct PassRange {
+    explicit PassRange(const char* name) { nvtxRangePushA(name); }
+    ~PassRange() { nvtxRangePop(); }
+};
+
 // Grid of a persistent row pass: as many blocks as fit on the GPU at once
 // (each loops over row blocks), at most one per row block.
 template <typename K>
@@ -1308,6 +1323,7 @@ cudaError_t launch_forward(const PlanView& p, const T* sigma, T* Fr, T* Fp, cuda
     cudaError_t err;
     if (ev && (err = cudaEventRecord(ev[0], st)) != cudaSuccess) return err;
     {
+        PassRange range_("sg forward rows");
         Shape s = shape_for<V>(p.nphi, sizeof(T) == 8 ? 64 : 256);
         const int R = 2 * s.slots, nblk = (p.nu + R - 1) / R;
         const size_t smem = rows_fwd_smem_bytes<V>(p.nphi, s.slots);
@@ -1324,6 +1340,7 @@ cudaError_t launch_forward(const PlanView& p, const T* sigma, T* Fr, T* Fp, cuda
     }
     if (ev && (err = cudaEventRecord(ev[1], st)) != cudaSuccess) return err;
     {
+        PassRange range_("sg forward columns");
         const int L = 2 * p.nu, E = L >= 16 ? 16 : L;
         const size_t smem = cols_smem_bytes<T>(p.nu);
         SG_DISPATCH_E(E, {
@@ -1336,6 +1353,7 @@ cudaError_t launch_forward(const PlanView& p, const T* sigma, T* Fr, T* Fp, cuda
     }
     if (ev && (err = cudaEventRecord(ev[2], st)) != cudaSuccess) return err;
     {
+        PassRange range_("sg forward inverse rows");
         Shape s = shape_for<V>(p.nphi, sizeof(T) == 8 ? 64 : 256);
         const int R = 2 * s.slots, nblk = (p.nu + R - 1) / R;
         const size_t smem = rows_inv_smem_bytes<V>(p.nphi, s.slots);
@@ -1367,6 +1385,7 @@ cudaError_t launch_backward(const PlanView& p, const T* gr, const T* gp, T* gs, 
     const int ln = sg_ilog2(p.nphi), lL = sg_ilog2(2 * p.nu);
     cudaError_t err;
     {
+        PassRange range_("sg adjoint rows");
         Shape s = shape_for<V>(p.nphi, row_min_threads(sizeof(T)));
         const int R = s.slots, nblk = (p.nu + R - 1) / R;
         const size_t smem = row_smem_bytes<V>(p.nphi, s.slots);
@@ -1382,6 +1401,7 @@ cudaError_t launch_backward(const PlanView& p, const T* gr, const T* gp, T* gs, 
         });
     }
     {
+        PassRange range_("sg adjoint columns");
         const int L = 2 * p.nu, E = L >= 16 ? 16 : L;
         const size_t smem = bcols_smem_bytes<T>(p.nu);
         SG_DISPATCH_E(E, {
@@ -1393,6 +1413,7 @@ cudaError_t launch_backward(const PlanView& p, const T* gr, const T* gp, T* gs, 
         });
     }
     {
+        PassRange range_("sg adjoint inverse rows");
         Shape s = shape_for<V>(p.nphi, sizeof(T) == 8 ? 64 : 256);
         const int R = 2 * s.slots, nblk = (p.nu + R - 1) / R;
         const size_t smem = rows_bwd_inv_smem_bytes<V>(p.nphi, s.slots);

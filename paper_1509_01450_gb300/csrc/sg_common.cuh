@@ -440,28 +440,38 @@ __device__ __forceinline__ void sg_cp_async8(void* dst, const void* src, uint64_
 }
 __device__ __forceinline__ void sg_cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
-// Wait for phase `phase` of the barrier, giving up after about a second (or
-// an iteration cap, whichever comes first).  On that timeout the error flag
-// gets `code`, a second wait of the same length gives the copies in flight a
-// last chance to land, and the call returns false: the caller then leaves
-// the block early (uniformly, via __syncthreads_or) and the host reads the
-// flag.  Returns true when the data arrived in time.
+// Wait for phase `phase` of the barrier, giving up after a time budget (or
+// an iteration cap, whichever comes first).  The budget of the first wait,
+// `limit`, comes from the flag block (sg_wait_budget: nanoseconds, about a
+// second unless a test sets it; 0 gives up at once).  On that timeout the error flag gets
+// `code`, a second wait of the full default budget gives the copies in
+// flight the time to land (no block leaves with copies still writing its
+// shared memory), and the call returns false: the caller then leaves the
+// block early (uniformly, via __syncthreads_or) and the host reads the flag.
+// Returns true when the data arrived in time.
 #define SG_WAIT_NS 1000000000ull
 #define SG_WAIT_ITERS (1 << 24)
-__device__ __forceinline__ bool sg_mbar_wait_once(uint64_t* bar, uint32_t phase)
+__device__ __forceinline__ bool sg_mbar_wait_once(uint64_t* bar, uint32_t phase, unsigned long long limit_ns)
 {
+    if (limit_ns == 0) return false;
     const uint64_t t0 = sg_globaltimer_ns();
     for (int it = 0; it < SG_WAIT_ITERS; it++) {
         if (sg_mbar_try_wait(bar, phase)) return true;
-        if ((it & 255) == 255 && sg_globaltimer_ns() - t0 > SG_WAIT_NS) break;
+        if ((it & 255) == 255 && sg_globaltimer_ns() - t0 > limit_ns) break;
     }
     return false;
 }
-__device__ __forceinline__ bool sg_mbar_wait_bounded(uint64_t* bar, uint32_t phase, int* err, int code)
+// the first-wait budget of the plan's flag block; read once per kernel
+__device__ __forceinline__ unsigned long long sg_wait_budget(const int* err)
 {
-    if (sg_mbar_wait_once(bar, phase)) return true;
+    return err ? __ldg(reinterpret_cast<const unsigned long long*>(err + 2)) : SG_WAIT_NS;
+}
+__device__ __forceinline__ bool sg_mbar_wait_bounded(uint64_t* bar, uint32_t phase, int* err, int code,
+                                                     unsigned long long limit)
+{
+    if (sg_mbar_wait_once(bar, phase, limit)) return true;
     if (err) atomicOr(err, code);
-    sg_mbar_wait_once(bar, phase);
+    sg_mbar_wait_once(bar, phase, SG_WAIT_NS);
     return false;
 }
 

@@ -19,6 +19,8 @@ struct sg_plan {
     double u_min, du, G;
     int weight_p;
     int built;
+    int loaded;      // spectra read from a plan file: the FP64 build tables are absent
+    double rtol;     // quadrature tolerance of the build
     int device;      // device the plan's memory lives on
     int sms;         // its multiprocessor count
     size_t elem;     // bytes of one real in the working dtype
@@ -31,7 +33,8 @@ struct sg_plan {
     void* kp;        // Khat_phi, same shape
     void* wpre;      // beta^{p (i - i_ref)}, nu reals
     void* wpost;     // beta^{-p (i - i_ref)}
-    int* derr;       // device error flags of the passes (bounded waits)
+    int* derr;       // device: int flags of the passes' bounded waits, then (at +8 bytes)
+                     // the first-wait budget in ns (unsigned long long)
     // FP64 device buffers
     void* tw64;      // twiddle table, SG_NMAX double complex
     double* cells;   // 6 x (2 nu + 1) x nphi raw cell kernels (kept after build)

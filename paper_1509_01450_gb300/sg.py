@@ -15,12 +15,13 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libsgdisk.so")
 
-SG_OK, SG_ERR_ARG, SG_ERR_ALLOC, SG_ERR_CUDA, SG_ERR_UNSUPPORTED, SG_ERR_NOT_BUILT, SG_ERR_TIMEOUT = range(7)
+SG_OK, SG_ERR_ARG, SG_ERR_ALLOC, SG_ERR_CUDA, SG_ERR_UNSUPPORTED, SG_ERR_NOT_BUILT, SG_ERR_TIMEOUT, SG_ERR_IO = range(8)
 SG_F32, SG_F64 = 0, 1
 
 EXPORTS = ("sg_plan_create", "sg_kernels_build", "sg_forces", "sg_forces_backward", "sg_forces_host", "sg_forces_timed",
            "sg_forces_batched", "sg_batch_reserve", "sg_plan_destroy", "sg_status_string", "sg_plan_info",
-           "sg_plan_kernels", "sg_plan_cells", "sg_plan_device_bytes", "sg_plan_build_report", "sg_forces_noalloc", "sg_plan_check")
+           "sg_plan_kernels", "sg_plan_cells", "sg_plan_device_bytes", "sg_plan_build_report", "sg_forces_noalloc", "sg_plan_check",
+           "sg_plan_set_wait_limit", "sg_plan_save", "sg_plan_load")
 
 
 class SgError(RuntimeError):
@@ -66,6 +67,9 @@ def lib():
         L.sg_plan_cells.argtypes = [vp, ctypes.POINTER(dp), vp]
         L.sg_plan_build_report.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
         L.sg_plan_check.argtypes = [vp, vp]
+        L.sg_plan_set_wait_limit.argtypes = [vp, dp]
+        L.sg_plan_save.argtypes = [vp, ctypes.c_char_p, vp]
+        L.sg_plan_load.argtypes = [ctypes.POINTER(vp), ctypes.c_char_p, vp]
         L.sg_plan_device_bytes.argtypes = [vp]
         L.sg_plan_device_bytes.restype = ctypes.c_size_t
         for name in EXPORTS:
@@ -175,6 +179,31 @@ class Plan:
         d = (ctypes.c_int * 4)()
         _check(lib().sg_plan_info(self.handle, d), "sg_plan_info")
         return tuple(d)
+
+    def set_wait_limit(self, seconds: float):
+        """Budget of the passes' device-side waits for their input copies
+        (default 1 s); 0 makes every pass give up at once (tests that path)."""
+        _check(lib().sg_plan_set_wait_limit(self.handle, float(seconds)), "sg_plan_set_wait_limit")
+
+    def save(self, path: str, stream=None):
+        """Write the built plan's spectra and parameters to a file."""
+        _check(lib().sg_plan_save(self.handle, os.fsencode(path), _stream(stream)), "sg_plan_save")
+
+    @classmethod
+    def load(cls, path: str, stream=None):
+        """A built plan from a file written by save (no rebuild)."""
+        import torch
+
+        h = ctypes.c_void_p()
+        _check(lib().sg_plan_load(ctypes.byref(h), os.fsencode(path), _stream(stream)), "sg_plan_load")
+        self = cls.__new__(cls)
+        self.handle = h
+        d = (ctypes.c_int * 4)()
+        _check(lib().sg_plan_info(h, d), "sg_plan_info")
+        self.nu, self.nphi = int(d[0]), int(d[1])
+        self.dtype = torch.float32 if d[2] == SG_F32 else torch.float64
+        self.u_min = self.du = self.G = None  # kept in the file and the plan, not needed here
+        return self
 
     def check(self, stream=None):
         """Raise if a pass of the enqueued work reported a device-side
