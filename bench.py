@@ -345,7 +345,13 @@ def run_ours(args):
     num = float(((Fr.double() - f64r) ** 2).sum() + ((Fp.double() - f64p) ** 2).sum())
     den = float((f64r ** 2).sum() + (f64p ** 2).sum())
     rel_fp32_vs_fp64 = math.sqrt(num / den)
-    del plan64, s64, f64r, f64p
+    # the same with the kernels stored at weighting p = 2 (the e^{2u} form)
+    plan_p2 = Plan(NU, NPHI, u_min, du, 1.0, "float32").build(weight_p=2)
+    plan_p2.forces(sigma, Fr, Fp)
+    torch.cuda.synchronize()
+    num = float(((Fr.double() - f64r) ** 2).sum() + ((Fp.double() - f64p) ** 2).sum())
+    rel_fp32_p2 = math.sqrt(num / den)
+    del plan64, plan_p2, s64, f64r, f64p
 
     # ---- end to end through the C ABI with host buffers --------------------
     sig_h = torch.tensor(sigma_np, dtype=torch.float32).pin_memory()
@@ -387,7 +393,7 @@ def run_ours(args):
             "backward": {"value": ws * cells / (bwd_ms * 1e-3), "unit": "cells/s", "ms_per_step": bwd_ms},
             "fp64": {"value": ws * cells / (fp64_ms * 1e-3), "unit": "cells/s", "ms_per_step": fp64_ms,
                      "fp32_speedup": fp64_ms / ms},
-            "accuracy": {"fp32_vs_fp64_gpu_rel_l2": rel_fp32_vs_fp64},
+            "accuracy": {"fp32_vs_fp64_gpu_rel_l2": rel_fp32_vs_fp64, "fp32_weight_p2_vs_fp64_gpu_rel_l2": rel_fp32_p2},
             "build_s": build_s,
             "batched": batch,
             "e2e": {"value": e2e_value, "unit": "cells/s", "ms_per_step": e2e_ms,
