@@ -37,9 +37,9 @@ NU, NPHI, R_IN, R_OUT, SEED = 2048, 4096, 0.01, 100.0, 1509
 # writes of the minimal data each pass must move, symmetry-reduced spectra)
 BYTES_PER_CELL = {"rows": 8.0, "cols": 20.0, "inv_rows": 16.0}
 # DRAM bytes (read + write) of one column-pass launch at 2048 x 4096 FP32, from
-# one ncu capture (profiles/k_fwd_cols_2048x4096_full.md), valid only for the
+# one ncu capture (profiles/k_fwd_2048x4096_full.md), valid only for the
 # kernel sources it was taken on (sha256 prefix of fftconv.cu + sg_common.cuh).
-COLS_TRAFFIC = {"sources_sha256": "3f08bbb2f2b6d90e", "bytes_per_launch": 100.829696e6 + 7.202560e6}
+COLS_TRAFFIC = {"sources_sha256": "821e469683c97880", "bytes_per_launch": 100.807424e6 + 7.038208e6}
 
 
 def kernel_sources_sha() -> str:
