@@ -42,20 +42,9 @@ namespace sg {
 
 // ---------------------------------------------------------------------------
 // Kernel spectrum at index kappa in [0, L) from the symmetry-reduced store
+// (a copy of one mode's row in shared memory): Khat_r is Hermitian in kappa,
+// Khat_phi anti-Hermitian
 // ---------------------------------------------------------------------------
-template <typename V>
-__device__ __forceinline__ V khat_r(const V* __restrict__ K, int kappa, int L, int nu)
-{
-    return kappa <= nu ? __ldg(&K[kappa]) : cconj(__ldg(&K[L - kappa]));
-}
-template <typename V>
-__device__ __forceinline__ V khat_p(const V* __restrict__ K, int kappa, int L, int nu)
-{
-    if (kappa <= nu) return __ldg(&K[kappa]);
-    V a = __ldg(&K[L - kappa]);
-    return V{-a.x, a.y};  // -conj
-}
-// the same from a copy in shared memory
 template <typename V>
 __device__ __forceinline__ V khat_r_s(const V* K, int kappa, int L, int nu)
 {
@@ -208,7 +197,6 @@ __host__ __device__ __forceinline__ int row_box_modes(int half) { return half < 
 __device__ __forceinline__ void sg_cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 // wait until at most the latest bulk-store group of this thread is still reading shared memory
 __device__ __forceinline__ void sg_bulk_wait_read_prev() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
-__device__ __forceinline__ void sg_cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 // Split Z = FFT(z_a + i z_b) of two real sequences into their half spectra
 // X_a[m], X_b[m] (m = t + e NT < N/2; mode 0 packs (DC, Nyquist)).  sm is

@@ -1,5 +1,8 @@
 // sg_common.cuh -- shared device helpers of the GB300 thin-disk force library:
-// complex arithmetic on float2/double2 and a register-resident Stockham FFT.
+// complex arithmetic on float2/double2; a register-resident Stockham FFT for
+// one transform, or for two FP32 transforms in lockstep on the paired f32x2
+// instructions (C2, sg_fft_pair); bulk and tensor copies through the TMA
+// unit with bounded mbarrier waits; L2 eviction policies.
 //
 // FFT engine.  A transform of length N = 2^m is held by NT = N / E threads,
 // E = min(16, N) elements each: thread t owns x[t + e NT], e = 0..E-1, on
@@ -284,15 +287,6 @@ __device__ __forceinline__ void sg_mbar_expect_tx(uint64_t* bar, uint32_t bytes)
                  : "memory");
 }
 
-__device__ __forceinline__ void sg_bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
-{
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            sg_smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(sg_smem_u32(bar))
-        : "memory");
-}
-
 __device__ __forceinline__ bool sg_mbar_try_wait(uint64_t* bar, uint32_t phase)
 {
     uint32_t ok;
@@ -341,13 +335,6 @@ __device__ __forceinline__ void sg_tma_store_2d(const CUtensorMap* map, int x, i
     asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group.L2::cache_hint [%0, {%1, %2}], [%3], %4;" ::"l"(
                      reinterpret_cast<uint64_t>(map)),
                  "r"(x), "r"(y), "r"(sg_smem_u32(src)), "l"(policy)
-                 : "memory");
-}
-// contiguous bulk store shared -> global (both 16-byte aligned, size a multiple of 16)
-__device__ __forceinline__ void sg_bulk_s2g(void* dst, const void* src, uint32_t bytes)
-{
-    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(sg_smem_u32(src)),
-                 "r"(bytes)
                  : "memory");
 }
 __device__ __forceinline__ void sg_bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
