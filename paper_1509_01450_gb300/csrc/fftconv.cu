@@ -300,6 +300,8 @@ __global__ void __launch_bounds__(NTB, (sizeof(T) == 4 && NTB == 256) ? 2 : 1) k
         sg_mbar_expect_tx(&bar, bytes);
         sg_bulk_g2s_hint(Si, sigma + (size_t)rb * R * N, bytes, &bar, sg_policy_evict_first());
     };
+    sg_grid_dep_launch();
+    sg_grid_dep_wait();  // sigma may come from the previous kernel on the stream
     // direct: sigma is read straight from memory the GPU reaches only by
     // plain loads (pinned host memory), without the bulk copies
     if (!direct && threadIdx.x == 0 && blockIdx.x < nblk) issue(blockIdx.x);
@@ -406,16 +408,21 @@ __global__ void SG_COLS_BOUNDS(T, NTB) k_fwd_cols(const typename CX<T>::t* __res
         sg_mbar_init(&bar[1], 1);
     }
     __syncthreads();
+    const uint32_t ab = (uint32_t)(nu * sizeof(V)), kb = (uint32_t)(KS * sizeof(V));
+    const uint64_t drop = sg_policy_evict_first();
     if (t == 0) {
-        const uint32_t ab = (uint32_t)(nu * sizeof(V)), kb = (uint32_t)(KS * sizeof(V));
-        const uint64_t drop = sg_policy_evict_first();
-        sg_mbar_expect_tx(&bar[0], ab);
-        sg_bulk_g2s_hint(sm, A + (size_t)m * nu, ab, &bar[0], drop);
+        // the spectra (written only by the build) before the previous pass ends
         sg_mbar_expect_tx(&bar[1], 2 * kb);
         sg_bulk_g2s_hint(kr_s, Kr + (size_t)m * KS, kb, &bar[1], drop);
         // mode 0 holds (DC, Nyquist): bring the Nyquist mode's Khat_r instead
         // of Khat_phi, which vanishes at both
         sg_bulk_g2s_hint(kp_s, (m == 0 ? Kr + (size_t)half * KS : Kp + (size_t)m * KS), kb, &bar[1], drop);
+    }
+    sg_grid_dep_launch();
+    sg_grid_dep_wait();  // A is the previous pass's result
+    if (t == 0) {
+        sg_mbar_expect_tx(&bar[0], ab);
+        sg_bulk_g2s_hint(sm, A + (size_t)m * nu, ab, &bar[0], drop);
     }
     const Twd<E, V> twd = make_twd<E>(log2L, t, tw);
     const uint64_t keep = sg_policy_evict_last();  // the row pass reads B and C from L2
@@ -575,6 +582,8 @@ __global__ void __launch_bounds__(NTB, (sizeof(T) == 4 && NTB == 256) ? 2 : 1) k
             sg_cp_async_commit();
         }
     };
+    sg_grid_dep_launch();
+    sg_grid_dep_wait();  // B and C are the previous pass's results
     if (blockIdx.x < nblk && (!use_map || threadIdx.x < 32)) issue(blockIdx.x);
     int it = 0;
     for (int rb = blockIdx.x; rb < nblk; rb += gridDim.x, it++) {
@@ -733,6 +742,8 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 512) k_bwd_rows(const T
         sg_bulk_g2s_hint(dst, gr + (size_t)rb * R * N, bytes, &bar[q], pol);
         sg_bulk_g2s_hint(reinterpret_cast<T*>(dst) + (size_t)R * N, gp + (size_t)rb * R * N, bytes, &bar[q], pol);
     };
+    sg_grid_dep_launch();
+    sg_grid_dep_wait();  // the seeds may come from the previous kernel on the stream
     if (threadIdx.x == 0 && blockIdx.x < nblk) issue(blockIdx.x, 0);
     int it = 0;
     for (int rb = blockIdx.x; rb < nblk; rb += gridDim.x, it++) {
@@ -838,15 +849,19 @@ __global__ void SG_COLS_BOUNDS(T, NTB) k_bwd_cols(const typename CX<T>::t* __res
         sg_mbar_init(&bar[1], 1);
     }
     __syncthreads();
-    if (t == 0) {
-        const uint32_t ab = (uint32_t)(nu * sizeof(V)), kb = (uint32_t)(KS * sizeof(V));
-        const uint64_t drop = sg_policy_evict_first();
-        sg_mbar_expect_tx(&bar[0], ab);
-        sg_bulk_g2s_hint(sm, A + (size_t)m * nu, ab, &bar[0], drop);
+    const uint32_t ab = (uint32_t)(nu * sizeof(V)), kb = (uint32_t)(KS * sizeof(V));
+    const uint64_t drop = sg_policy_evict_first();
+    if (t == 0) {  // the spectra first (written only by the build)
         sg_mbar_expect_tx(&bar[1], ab + 2 * kb);
-        sg_bulk_g2s_hint(cs, C + (size_t)m * nu, ab, &bar[1], drop);
         sg_bulk_g2s_hint(kr_s, Kr + (size_t)m * KS, kb, &bar[1], drop);
         sg_bulk_g2s_hint(kp_s, (m == 0 ? Kr + (size_t)half * KS : Kp + (size_t)m * KS), kb, &bar[1], drop);
+    }
+    sg_grid_dep_launch();
+    sg_grid_dep_wait();  // A and C are the previous pass's results
+    if (t == 0) {
+        sg_mbar_expect_tx(&bar[0], ab);
+        sg_bulk_g2s_hint(sm, A + (size_t)m * nu, ab, &bar[0], drop);
+        sg_bulk_g2s_hint(cs, C + (size_t)m * nu, ab, &bar[1], drop);
     }
     const Twd<E, V> twd = make_twd<E>(log2L, t, tw);
     const uint64_t keep = sg_policy_evict_last();
@@ -993,6 +1008,8 @@ __global__ void __launch_bounds__(NTB, (sizeof(T) == 4 && NTB == 256) ? 2 : 1) k
             sg_cp_async_commit();
         }
     };
+    sg_grid_dep_launch();
+    sg_grid_dep_wait();  // B is the previous pass's result
     if (blockIdx.x < nblk && (!use_map || threadIdx.x < 32)) issue(blockIdx.x);
     int it = 0;
     for (int rb = blockIdx.x; rb < nblk; rb += gridDim.x, it++) {
@@ -1198,6 +1215,26 @@ struct PassRange {
     ~PassRange() { nvtxRangePop(); }
 };
 
+// Launch with programmatic stream serialization: the kernel may start while
+// the previous one on the stream finishes; it waits (sg_grid_dep_wait)
+// before it reads that kernel's results.
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int block, size_t smem, cudaStream_t st,
+                              Args&&... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 // Grid of a persistent row pass: as many blocks as fit on the GPU at once
 // (each loops over row blocks), at most one per row block.
 template <typename K>
@@ -1321,9 +1358,9 @@ cudaError_t launch_forward(const PlanView& p, const T* sigma, T* Fr, T* Fp, cuda
             if constexpr (sizeof(T) == 4)  // FP64 blocks are at most 256 threads
                 if (s.threads > 256) k = k_fwd_rows<T, EE, 512>;
             if ((err = set_smem(k, smem, true)) != cudaSuccess) return err;
-            k<<<persistent_grid(k, s.threads, smem, nblk, p.sms), s.threads, smem, st>>>(
+            if ((err = launch_pdl(k, persistent_grid(k, s.threads, smem, nblk, p.sms), s.threads, smem, st, 
                 sigma, (const T*)p.wpre, A, p.nu, p.nphi, ln, tw, p.err, mA ? *mA : CUtensorMap{}, mA != nullptr,
-                sigma_direct ? 1 : 0);
+                sigma_direct ? 1 : 0)) != cudaSuccess) return err;
         });
     }
     if (ev && (err = cudaEventRecord(ev[1], st)) != cudaSuccess) return err;
@@ -1336,7 +1373,7 @@ cudaError_t launch_forward(const PlanView& p, const T* sigma, T* Fr, T* Fp, cuda
             if constexpr (sizeof(T) == 4)  // FP64 columns are at most 256 threads
                 if (L / EE > 256) k = k_fwd_cols<T, EE, 512>;
             if ((err = set_smem(k, smem, true)) != cudaSuccess) return err;
-            k<<<p.nphi / 2, L / EE, smem, st>>>(A, (const V*)p.kr, (const V*)p.kp, B, C, p.nu, p.nphi, lL, tw, p.err);
+            if ((err = launch_pdl(k, p.nphi / 2, L / EE, smem, st, A, (const V*)p.kr, (const V*)p.kp, B, C, p.nu, p.nphi, lL, tw, p.err)) != cudaSuccess) return err;
         });
     }
     if (ev && (err = cudaEventRecord(ev[2], st)) != cudaSuccess) return err;
@@ -1353,9 +1390,9 @@ cudaError_t launch_forward(const PlanView& p, const T* sigma, T* Fr, T* Fp, cuda
             if constexpr (sizeof(T) == 4)  // FP64 blocks are at most 256 threads
                 if (s.threads > 256) k = k_fwd_rows_inv<T, EE, 512>;
             if ((err = set_smem(k, smem, true)) != cudaSuccess) return err;
-            k<<<persistent_grid(k, s.threads, smem, nblk, p.sms), s.threads, smem, st>>>(
+            if ((err = launch_pdl(k, persistent_grid(k, s.threads, smem, nblk, p.sms), s.threads, smem, st, 
                 B, C, (const T*)p.wpost, Fr, Fp, p.nu, p.nphi, ln, tw, p.err, um ? *mB : CUtensorMap{},
-                um ? *mC : CUtensorMap{}, um);
+                um ? *mC : CUtensorMap{}, um)) != cudaSuccess) return err;
         });
     }
     if (ev && (err = cudaEventRecord(ev[3], st)) != cudaSuccess) return err;
@@ -1383,9 +1420,9 @@ cudaError_t launch_backward(const PlanView& p, const T* gr, const T* gp, T* gs, 
         SG_DISPATCH_E(s.E, {
             auto k = k_bwd_rows<T, EE>;
             if ((err = set_smem(k, smem, true)) != cudaSuccess) return err;
-            k<<<persistent_grid(k, s.threads, smem, nblk, p.sms), s.threads, smem, st>>>(
+            if ((err = launch_pdl(k, persistent_grid(k, s.threads, smem, nblk, p.sms), s.threads, smem, st, 
                 gr, gp, (const T*)p.wpost, A, C, p.nu, p.nphi, ln, tw, p.err, um ? *mA : CUtensorMap{},
-                um ? *mC : CUtensorMap{}, um);
+                um ? *mC : CUtensorMap{}, um)) != cudaSuccess) return err;
         });
     }
     {
@@ -1397,7 +1434,7 @@ cudaError_t launch_backward(const PlanView& p, const T* gr, const T* gp, T* gs, 
             if constexpr (sizeof(T) == 4)  // FP64 columns are at most 256 threads
                 if (L / EE > 256) k = k_bwd_cols<T, EE, 512>;
             if ((err = set_smem(k, smem, true)) != cudaSuccess) return err;
-            k<<<p.nphi / 2, L / EE, smem, st>>>(A, C, (const V*)p.kr, (const V*)p.kp, B, p.nu, p.nphi, lL, tw, p.err);
+            if ((err = launch_pdl(k, p.nphi / 2, L / EE, smem, st, A, C, (const V*)p.kr, (const V*)p.kp, B, p.nu, p.nphi, lL, tw, p.err)) != cudaSuccess) return err;
         });
     }
     {
@@ -1411,8 +1448,8 @@ cudaError_t launch_backward(const PlanView& p, const T* gr, const T* gp, T* gs, 
             if constexpr (sizeof(T) == 4)
                 if (s.threads > 256) k = k_bwd_rows_inv<T, EE, 512>;
             if ((err = set_smem(k, smem, true)) != cudaSuccess) return err;
-            k<<<persistent_grid(k, s.threads, smem, nblk, p.sms), s.threads, smem, st>>>(
-                B, (const T*)p.wpre, gs, p.nu, p.nphi, ln, tw, p.err, mB ? *mB : CUtensorMap{}, mB != nullptr);
+            if ((err = launch_pdl(k, persistent_grid(k, s.threads, smem, nblk, p.sms), s.threads, smem, st, 
+                B, (const T*)p.wpre, gs, p.nu, p.nphi, ln, tw, p.err, mB ? *mB : CUtensorMap{}, mB != nullptr)) != cudaSuccess) return err;
         });
     }
     return cudaGetLastError();

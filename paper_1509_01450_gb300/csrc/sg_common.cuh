@@ -344,6 +344,15 @@ __device__ __forceinline__ void sg_bulk_wait_read() { asm volatile("cp.async.bul
 __device__ __forceinline__ void sg_fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 // ---------------------------------------------------------------------------
+// Programmatic dependent launch: a pass lets the next one launch early
+// (its blocks are placed once every block of this grid has started) and
+// waits for the previous pass's results only where it reads them.  Both are
+// no-ops for launches without the programmatic-serialization attribute.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void sg_grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void sg_grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// ---------------------------------------------------------------------------
 // L2 eviction priorities.  The half-spectrum intermediates are written by one
 // pass and read, transposed, by the next; they are kept in L2 (evict_last)
 // while the streamed inputs (density, kernel spectra, consumed intermediates)
