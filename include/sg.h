@@ -58,14 +58,41 @@ typedef enum { SG_F32 = 0, SG_F64 = 1 } sg_dtype;
 
 typedef struct sg_plan sg_plan;
 
+/* Which force kernels the plan convolves with (Sec. 3.2 and 5.2).  All
+   of them feed the same fold, spectra and passes; only the table of the six
+   per-offset kernels differs.  Source cell (i', j') of target (i, j), offset
+   (k, q) = (i - i', j - j'); M = sigma A' is the source cell's mass with
+   A' = r_i' (r_i'+1/2 - r_i'-1/2) dphi its exact area. */
+typedef enum {
+    SG_KERNEL_SIM = 0,           /* second order: the exact cell integrals of
+                                    Eq. 30-32 and A11-A13 with the central
+                                    slopes of Eq. 28-29, self cell by the
+                                    singular integral of Sec. 4 */
+    SG_KERNEL_PARTICLE = 1,      /* the particle method: the mass M at the
+                                    source centre (Eq. 35), no slopes, nothing
+                                    from the target's own cell */
+    SG_KERNEL_PARTICLE_PLUS = 2, /* the modified particle method (Eq. 36-37):
+                                    the particle kernel plus the target cell's
+                                    own exact terms sigma K^{.,0}_{0,0} +
+                                    r_i delta^r K^{.,r}_{0,0} + delta^phi
+                                    K^{.,phi}_{0,0} */
+    SG_KERNEL_SOFTENED = 3       /* the particle kernel with a softening length
+                                    eps = soften * r_i added in quadrature to
+                                    the distance (the BM08 comparison method of
+                                    Sec. 5.2), own cell included */
+} sg_kernel_kind;
+
 /* Options of the one-time kernel preparation (Sec. 2: "prepared only once
-   for a fixed grid").  Pass NULL for the defaults. */
+   for a fixed grid").  Pass NULL for the defaults; a zero-filled struct
+   gives them too. */
 typedef struct {
-    double rtol;  /* relative tolerance of the cell quadrature; default 1e-14 */
-    int weight_p; /* weighting exponent p of sigma e^{p u} (the kernels carry
-                     beta^{p k}, the result e^{-p u}); algebraically neutral;
-                     default 2 */
-    int reserved[6];
+    double rtol;   /* relative tolerance of the cell quadrature; default 1e-14 */
+    int weight_p;  /* weighting exponent p of sigma e^{p u} (the kernels carry
+                      beta^{p k}, the result e^{-p u}); algebraically neutral;
+                      default 0 */
+    int kind;      /* sg_kernel_kind; default SG_KERNEL_SIM (0) */
+    double soften; /* SG_KERNEL_SOFTENED: eps / r_i, > 0; ignored otherwise */
+    int reserved[4];
 } sg_build_opts;
 
 /*
@@ -89,11 +116,15 @@ sg_status sg_plan_create(sg_plan** out, int N_u, int N_phi, double u_min, double
 /*
  * Build the cell-integrated kernels (Eq. 30-32, A11-A13; self cell per
  * Sec. 4), fold the slope terms, apply G beta^{p k} and transform to spectra
- * (FP64, stored in the plan's dtype).  opts may be NULL.  Runs on stream
- * and blocks the host until it completes; must be called once before
- * sg_forces.  Returns SG_ERR_TIMEOUT (the plan is still usable) if a cell
- * integral could not reach the tolerance within the quadrature's budget.
- * Allocates and frees FP64 scratch for the spectra.
+ * (FP64, stored in the plan's dtype).  opts may be NULL.  opts->kind
+ * selects the particle-method kernels of sg_kernel_kind instead; they go
+ * through the same fold (their slope cells are zero away from the own
+ * cell).  Runs on stream and blocks the host until it completes; must be
+ * called once before sg_forces (again to rebuild with other options).
+ * Returns SG_ERR_TIMEOUT (the plan is still usable) if a cell integral
+ * could not reach the tolerance within the quadrature's budget, and
+ * SG_ERR_ARG for an unknown kind, soften <= 0 with SG_KERNEL_SOFTENED or
+ * |weight_p| > 8.  Allocates and frees FP64 scratch for the spectra.
  */
 sg_status sg_kernels_build(sg_plan* plan, const sg_build_opts* opts, cudaStream_t stream);
 
@@ -205,6 +236,9 @@ sg_status sg_plan_kernels(sg_plan* plan, double* Kr_h, double* Kphi_h, cudaStrea
  * Copies the six raw FP64 cell kernels [6][(2 N_u + 1) * N_phi] (k in
  * [-N_u, N_u], q in [0, N_phi); order K^{r,0}, K^{r,r}, K^{r,phi},
  * K^{phi,0}, K^{phi,r}, K^{phi,phi}) to host memory.  Synchronises stream.
+ * For the particle kinds, K^{r,0} and K^{phi,0} hold the point kernels
+ * M K^{.,p} / sigma and the other four are zero, except the own cell's
+ * exact values at (0, 0) for SG_KERNEL_PARTICLE_PLUS.
  */
 sg_status sg_plan_cells(sg_plan* plan, double* cells_h, cudaStream_t stream);
 

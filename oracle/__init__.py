@@ -15,6 +15,10 @@ polar coordinates":
 * ``slopes``             -- Eq. 25 with central differences (Sec. 5.2).
 * ``three_sum``          -- Eq. 26-29 and A8-A10 on the single grid, the
                             literal three-term form.
+* ``particle_cells``     -- Eq. 35-37 and Sec. 5.2: the particle method, the
+                            modified particle method and the softened
+                            particle kernel of the comparison (BM08), as
+                            cell tables of the same shape.
 * ``fold``               -- the same sums collapsed to one kernel per force
                             component (the exact algebra in ``fold``'s doc).
 * ``direct_sum``         -- the O(N^2) convolution with the folded kernels.
@@ -128,6 +132,65 @@ def kernel_cells(nu: int, nphi: int, du: float, rtol: float = 2e-14, nthreads: i
     if bad:
         raise RuntimeError(f"oracle quadrature did not converge for {bad} integrals")
     return out
+
+
+PARTICLE_KINDS = ("particle", "particle+", "softened")
+
+
+def particle_cells(nu: int, nphi: int, du: float, kind: str, soften: float = 0.0, rtol: float = 2e-14) -> np.ndarray:
+    """Cell table [6, 2Nu+1, Nphi] of the particle methods (Sec. 3.2.2 for
+    the Cartesian form, Eq. 35-37 in polar coordinates).
+
+    Each source cell is a point of mass M = sigma A' at its centre.  With the
+    target radius r_i as the unit, the source centre is r' = beta^{-k} (the
+    ratio of two arithmetic centres), its faces r' 2/(1+beta) and
+    r' 2 beta/(1+beta), A' = r' (r'_+ - r'_-) dphi its area, and the angle to
+    it Delta = phi_{j'} - phi_j = -q dphi.  Eq. 35 and its azimuthal
+    counterpart (the point form of Eq. A11) per unit sigma:
+        K^{r,0}   <- -A' (1 - r' cos Delta) / d^3,
+        K^{phi,0} <-  A' r' sin Delta / d^3,
+    with d^2 = 1 + r'^2 - 2 r' cos Delta (law of cosines, written as
+    (1 - r')^2 + 4 r' sin^2(Delta/2), and 1 - r' cos Delta as
+    (1 - r') + 2 r' sin^2(Delta/2), so that neighbouring cells keep their
+    digits).  The slope kernels are zero.
+
+    kind "particle":  nothing from the target's own cell (Eq. 35, the (0, 0)
+                      entry is 0).
+    kind "particle+": the modified method of Eq. 36-37: the own cell's exact
+                      K^{.,0}_{0,0}, K^{.,r}_{0,0}, K^{.,phi}_{0,0} (from
+                      ``kernel_cell``) at (0, 0); ``fold`` turns the slope
+                      ones into the sigma differences of delta^r, delta^phi.
+    kind "softened":  eps^2 = (soften r_i)^2 added to d^2, own cell included
+                      (the comparison method of Sec. 5.2).
+    """
+    if kind not in PARTICLE_KINDS:
+        raise ValueError(kind)
+    beta = math.exp(du)
+    dphi = 2.0 * math.pi / nphi
+    out = np.zeros((NC, 2 * nu + 1, nphi))
+    delta = -np.arange(nphi, dtype=np.float64) * dphi
+    s2 = np.sin(0.5 * delta) ** 2
+    for kk in range(2 * nu + 1):
+        k = kk - nu
+        rp = beta ** (-k)
+        area = rp * (rp * 2.0 * beta / (1.0 + beta) - rp * 2.0 / (1.0 + beta)) * dphi
+        d2 = (1.0 - rp) ** 2 + 4.0 * rp * s2
+        if kind == "softened":
+            d2 = d2 + soften * soften
+        with np.errstate(divide="ignore", invalid="ignore"):
+            d3 = d2 * np.sqrt(d2)
+            out[0, kk] = -area * ((1.0 - rp) + 2.0 * rp * s2) / d3
+            out[3, kk] = area * rp * np.sin(delta) / d3
+    if kind != "softened":
+        out[0, nu, 0] = out[3, nu, 0] = 0.0  # the own cell holds no point mass
+    if kind == "particle+":
+        out[:, nu, 0] = kernel_cell(du, nphi, 0, 0, rtol)
+    return out
+
+
+def particle_kernels(nu: int, nphi: int, du: float, kind: str, soften: float = 0.0):
+    """Folded kernels (Kr, Kphi) of a particle method."""
+    return fold(particle_cells(nu, nphi, du, kind, soften), math.exp(du), 2.0 * math.pi / nphi)
 
 
 # --------------------------------------------------------------------------

@@ -34,6 +34,21 @@
 // and a fine rule must agree.  K^{r,phi}, K^{phi,0}, K^{phi,r} vanish on
 // the self cell by symmetry (Sec. 3.2.2 and App. A).
 //
+// k_point_cells: the particle kinds of sg_kernel_kind (Eq. 35-37 and the
+// softened comparison method of Sec. 5.2).  The source centre of offset
+// (k, q) sits at eta_c = beta^-k, xi_c = -q' dphi (q' = q taken into
+// (-N_phi/2, N_phi/2]); its mass in units of sigma r_i^2 is
+// a = eta_c^2 2 tanh(du/2) dphi (A' / r_i^2 of the cell with arithmetic
+// centre r_i'), and
+//     K^{r,0}   <- -a (1 - eta_c cos xi_c) / D^3,
+//     K^{phi,0} <-  a eta_c sin xi_c / D^3,
+//     D^2 = (1 - eta_c)^2 + 4 eta_c sin^2(xi_c / 2)  (+ s^2 softened),
+// with 1 - eta_c = -expm1(-k du) and 1 - cos xi = 2 sin^2(xi / 2), so the
+// neighbouring cells lose no digits.  The four slope cells are zero; the own
+// cell (0, 0) is zero for the particle kinds (k_self_cell then writes the
+// exact own-cell values for the modified method) and has D = s, with both
+// numerators zero, when softened.
+//
 // k_fold: the slope terms of Eq. 28-29 / A9-A10 with central differences
 // fold into one kernel per component:
 //   K^eff[k,q] = K^{.,0}[k,q] + (beta^{k+1} K^{.,r}[k+1,q]
@@ -407,6 +422,34 @@ __global__ void __launch_bounds__(256) k_self_cell(int nu, int nphi, double du, 
     }
 }
 
+__global__ void k_point_cells(int nu, int nphi, double du, int kind, double s, double* __restrict__ cells)
+{
+    const long per = (long)(2 * nu + 1) * nphi;
+    const double a0 = 2.0 * tanh(0.5 * du) * (2.0 * M_PI / nphi);
+    for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < per; idx += (long)gridDim.x * blockDim.x) {
+        const int k = (int)(idx / nphi) - nu, q = (int)(idx % nphi);
+        const int qr = q <= nphi / 2 ? q : q - nphi;
+        double sx, cx, sh, ch;
+        sincospi(-2.0 * qr / nphi, &sx, &cx);  // xi_c
+        sincospi(-1.0 * qr / nphi, &sh, &ch);  // xi_c / 2
+        const double eta = exp(-k * du), om = -expm1(-k * du);
+        double D2 = om * om + 4.0 * eta * sh * sh;
+        if (kind == SG_KERNEL_SOFTENED) D2 += s * s;
+        double kr = 0.0, kp = 0.0;
+        if (kind == SG_KERNEL_SOFTENED || k != 0 || q != 0) {
+            const double a = eta * eta * a0, inv = 1.0 / (D2 * sqrt(D2));
+            kr = -a * (om + 2.0 * eta * sh * sh) * inv;
+            kp = a * eta * sx * inv;
+        }
+        cells[idx] = kr;
+        cells[per + idx] = 0.0;
+        cells[2 * per + idx] = 0.0;
+        cells[3 * per + idx] = kp;
+        cells[4 * per + idx] = 0.0;
+        cells[5 * per + idx] = 0.0;
+    }
+}
+
 __global__ void k_fold(int nu, int nphi, double du, double G, int p, const double* __restrict__ cells,
                        double* __restrict__ keff, double* __restrict__ nsr, double* __restrict__ nsp)
 {
@@ -456,6 +499,21 @@ cudaError_t launch_cells(int nu, int nphi, double du, double rtol, double* cells
     if (blocks > cap) blocks = cap;
     k_cells<<<(int)blocks, 128, 0, st>>>(nu, nphi, du, rtol, cells, flag);
     k_self_cell<<<1, 256, 0, st>>>(nu, nphi, du, rtol, cells, flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_point_cells(int nu, int nphi, double du, int kind, double soften, double rtol, double* cells,
+                               int* flag, cudaStream_t st)
+{
+    const long per = (long)(2 * nu + 1) * nphi;
+    long blocks = (per + 255) / 256;
+    if (blocks > 65535) blocks = 65535;
+    k_point_cells<<<(int)blocks, 256, 0, st>>>(nu, nphi, du, kind, soften, cells);
+    if (kind == SG_KERNEL_PARTICLE_PLUS) {
+        cudaError_t e = upload_rules();  // the own cell's Gauss-Legendre rules
+        if (e != cudaSuccess) return e;
+        k_self_cell<<<1, 256, 0, st>>>(nu, nphi, du, rtol, cells, flag);
+    }
     return cudaGetLastError();
 }
 

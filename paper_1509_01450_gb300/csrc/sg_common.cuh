@@ -498,7 +498,6 @@ __device__ __forceinline__ void sg_pass_store(const V (&v)[E], V* sm, int t, int
 template <int R, int E, typename V>
 __device__ __forceinline__ void sg_pass_load(V (&v)[E], const V* sm, int t, int NT, int N)
 {
-#pragma unroll
     const int M = N / R;
 #pragma unroll
     for (int s = 0; s < E / R; s++) {

@@ -108,6 +108,9 @@ cudaError_t launch_spectra(const PlanView& p, const double* nsr, const double* n
 
 // kbuild.cu
 cudaError_t launch_cells(int nu, int nphi, double du, double rtol, double* cells, int* flag, cudaStream_t st);
+// the particle kinds' tables (sg_kernel_kind 1-3; for 2 with the exact own cell)
+cudaError_t launch_point_cells(int nu, int nphi, double du, int kind, double soften, double rtol, double* cells,
+                               int* flag, cudaStream_t st);
 cudaError_t launch_fold(int nu, int nphi, double du, double G, int p, const double* cells, double* keff,
                         double* nsr, double* nsp, cudaStream_t st);
 void gauss_legendre(int n, double* x, double* w);

@@ -30,8 +30,18 @@ class SgError(RuntimeError):
         super().__init__(f"{what}: {status_string(status)} ({status})")
 
 
+# sg_kernel_kind: which force kernels a plan is built with (Sec. 3.2, 5.2)
+SG_KERNEL_SIM = 0            # second order: exact cell integrals, central slopes, singular own cell
+SG_KERNEL_PARTICLE = 1       # point mass at each source centre (Eq. 35)
+SG_KERNEL_PARTICLE_PLUS = 2  # point masses plus the own cell's exact terms (Eq. 36-37)
+SG_KERNEL_SOFTENED = 3       # point masses with softening eps = soften r_i (BM08 comparison)
+KERNEL_KINDS = {"sim": SG_KERNEL_SIM, "particle": SG_KERNEL_PARTICLE, "particle+": SG_KERNEL_PARTICLE_PLUS,
+                "softened": SG_KERNEL_SOFTENED}
+
+
 class BuildOpts(ctypes.Structure):
-    _fields_ = [("rtol", ctypes.c_double), ("weight_p", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
+    _fields_ = [("rtol", ctypes.c_double), ("weight_p", ctypes.c_int), ("kind", ctypes.c_int),
+                ("soften", ctypes.c_double), ("reserved", ctypes.c_int * 4)]
 
 
 class BatchItem(ctypes.Structure):
@@ -117,8 +127,11 @@ class Plan:
         self.handle = h
 
     # -- one-time preparation ------------------------------------------------
-    def build(self, rtol: float = 1e-14, weight_p: int = 0, stream=None):
-        opts = BuildOpts(rtol, weight_p)
+    def build(self, rtol: float = 1e-14, weight_p: int = 0, kind="sim", soften: float = 0.0, stream=None):
+        """Build the kernels.  kind: "sim" (default), "particle", "particle+"
+        or "softened" (with soften = eps / r_i), or an SG_KERNEL_* code."""
+        code = KERNEL_KINDS[kind] if isinstance(kind, str) else int(kind)
+        opts = BuildOpts(rtol, weight_p, code, soften)
         _check(lib().sg_kernels_build(self.handle, ctypes.byref(opts), _stream(stream)), "sg_kernels_build")
         return self
 

@@ -1,0 +1,118 @@
+"""The particle-method kernels (Eq. 35-37, and the softened comparison method
+of Sec. 5.2) built by the CUDA kernel builder, against the oracle's
+particle tables: the raw tables, the folded kernels, the forces (FP64 within
+1e-12 relative L2, FP32 within 1e-5) and the convergence orders of Table 1
+through the CUDA path."""
+import math
+
+import numpy as np
+import pytest
+
+import workloads
+from oracle import analytic as A
+from tests.conftest import load_golden
+
+pytestmark = pytest.mark.gpu
+
+KINDS = ("particle", "particle+", "softened")
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1509_01450_gb300 import build
+
+    build.build()
+    return torch
+
+
+def _plan(nu, nphi, r_in, r_out, dtype, kind, soften):
+    from paper_1509_01450_gb300 import Plan
+
+    u_min, du = workloads.grid_params(nu, r_in, r_out)
+    return Plan(nu, nphi, u_min, du, 1.0, dtype).build(kind=kind, soften=soften), u_min, du
+
+
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("nu,nphi", [(4, 8), (16, 64), (64, 32), (128, 128)])
+def test_tables_and_folded_kernels(torch_cuda, oracle_mod, kind, nu, nphi):
+    plan, u_min, du = _plan(nu, nphi, 0.05, 20.0, "float64", kind, 0.03)
+    assert plan.build_report() == (0, 0, 0, 0)
+    ref = oracle_mod.particle_cells(nu, nphi, du, kind, soften=0.03)
+    got = plan.cells()
+    scale = np.abs(ref[0]) + np.abs(ref[3])
+    scale = scale + 1e-3 * scale.max()
+    for c in range(6):
+        assert np.all(np.abs(got[c] - ref[c]) <= 2e-12 * scale), (c, np.abs(got[c] - ref[c]).max())
+    Kr, Kp = oracle_mod.fold(ref, math.exp(du), 2 * math.pi / nphi)
+    gKr, gKp = plan.kernels()
+    sk = np.abs(Kr).max() + np.abs(Kp).max()
+    assert np.abs(gKr - Kr).max() < 1e-12 * sk and np.abs(gKp - Kp).max() < 1e-12 * sk
+
+
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("nu,nphi", [(8, 16), (32, 128), (256, 64)])
+@pytest.mark.parametrize("dtype,tol", [("float64", 1e-12), ("float32", 1e-5)])
+def test_forces_against_the_oracle(torch_cuda, oracle_mod, kind, nu, nphi, dtype, tol):
+    torch = torch_cuda
+    plan, u_min, du = _plan(nu, nphi, 0.01, 100.0, dtype, kind, 0.02)
+    r, phi = workloads.centres(nu, nphi, u_min, du)
+    sigma = workloads.spiral_clump(r, phi) + 0.01 * np.abs(workloads.random_field(nu, nphi, 3))
+    Kr, Kp = oracle_mod.particle_kernels(nu, nphi, du, kind, soften=0.02)
+    Fr_ref, Fp_ref = oracle_mod.direct_sum(sigma, Kr, Kp)
+    s = torch.tensor(sigma, dtype=plan.dtype, device="cuda")
+    Fr, Fp = plan.forces(s)
+    torch.cuda.synchronize()
+    plan.check()
+    assert oracle_mod.rel_l2(Fr.double().cpu().numpy(), Fp.double().cpu().numpy(), Fr_ref, Fp_ref) < tol
+    # the adjoint is the transposed sum of the same kernels
+    gr, gp = workloads.random_field(nu, nphi, 8), workloads.random_field(nu, nphi, 9)
+    gs = plan.backward(torch.tensor(gr, dtype=plan.dtype, device="cuda"),
+                       torch.tensor(gp, dtype=plan.dtype, device="cuda"))
+    ref = oracle_mod.direct_sum_T(gr, gp, Kr, Kp)
+    assert np.linalg.norm(gs.double().cpu().numpy() - ref) / np.linalg.norm(ref) < tol
+
+
+def test_orders_through_the_cuda_path(torch_cuda):
+    """Table 1's particle, particle+ and BM08 columns for the sigma_{D_5}
+    disk, from FP64 forces computed by the library."""
+    torch = torch_cuda
+    want = {(d, n, c): (float(p), float(pp), float(bm))
+            for d, n, c, p, pp, bm in load_golden("table1_particle_orders.txt")}
+    for ki, kind in enumerate(KINDS):
+        errs = []
+        for N in (128, 256, 512):
+            plan, u_min, du = _plan(N, N, 0.01, 1.0, "float64", kind, 0.015 * 64 / N)
+            r, phi = workloads.centres(N, N, u_min, du)
+            sig = workloads.sigma_dn(5, 0.25, 0.5, 0.1, r, phi)
+            Fr, Fp = plan.forces(torch.tensor(sig, device="cuda"))
+            torch.cuda.synchronize()
+            Ar, Ap = A.dn_offcentre_forces(5, 0.25, 0.5, 0.1, r, phi)
+            d = (np.abs(Fr.cpu().numpy() - Ar), np.abs(Fp.cpu().numpy() - Ap))
+            errs.append({("L1", "r"): d[0].mean(), ("L1", "phi"): d[1].mean(),
+                         ("Linf", "r"): d[0].max(), ("Linf", "phi"): d[1].max()})
+        for key, e in errs[-1].items():
+            got = math.log2(errs[-2][key] / e)
+            tol = 0.15 if kind != "particle+" else 0.3
+            assert abs(got - want[("D5",) + key][ki]) < tol, (kind, key, got)
+
+
+def test_bad_options(torch_cuda):
+    from paper_1509_01450_gb300 import Plan, SgError, sg
+
+    plan = Plan(16, 16, 0.0, 0.1, 1.0, "float32")
+    for kw in ({"kind": 7}, {"kind": -1}, {"kind": "softened", "soften": 0.0},
+               {"kind": "softened", "soften": -1.0}):
+        with pytest.raises(SgError) as ei:
+            plan.build(**kw)
+        assert ei.value.status == sg.SG_ERR_ARG
+    # a plan rebuilt with another kind computes with the new kernels
+    s = np.abs(workloads.random_field(16, 16, 1))
+    torch = torch_cuda
+    st = torch.tensor(s, dtype=torch.float32, device="cuda")
+    a = plan.build(kind="particle").forces(st)[0].clone()
+    b = plan.build(kind="sim").forces(st)[0].clone()
+    c = plan.build(kind="particle").forces(st)[0].clone()
+    assert torch.equal(a, c) and not torch.equal(a, b)
