@@ -92,7 +92,13 @@ typedef struct {
                       default 0 */
     int kind;      /* sg_kernel_kind; default SG_KERNEL_SIM (0) */
     double soften; /* SG_KERNEL_SOFTENED: eps / r_i, > 0; ignored otherwise */
-    int reserved[4];
+    int n_tpz;     /* SG_KERNEL_SIM: 0 (default) for the exact cell integrals;
+                      N in [1, 1024] for the trapezoidal rule of Eq. 41-43
+                      with N trapezoids per cell in phi (exact in r) for
+                      K^{r,0}, K^{r,r}, K^{r,phi} and K^{phi,phi}, the own
+                      cell still exact (Sec. 4; the paper's SIM uses 19);
+                      ignored by the particle kinds */
+    int reserved[3];
 } sg_build_opts;
 
 /*
@@ -123,8 +129,9 @@ sg_status sg_plan_create(sg_plan** out, int N_u, int N_phi, double u_min, double
  * called once before sg_forces (again to rebuild with other options).
  * Returns SG_ERR_TIMEOUT (the plan is still usable) if a cell integral
  * could not reach the tolerance within the quadrature's budget, and
- * SG_ERR_ARG for an unknown kind, soften <= 0 with SG_KERNEL_SOFTENED or
- * |weight_p| > 8.  Allocates and frees FP64 scratch for the spectra.
+ * SG_ERR_ARG for an unknown kind, soften <= 0 with SG_KERNEL_SOFTENED,
+ * n_tpz outside [0, 1024] or |weight_p| > 8.  Allocates and frees FP64
+ * scratch for the spectra.
  */
 sg_status sg_kernels_build(sg_plan* plan, const sg_build_opts* opts, cudaStream_t stream);
 

@@ -15,6 +15,8 @@ polar coordinates":
 * ``slopes``             -- Eq. 25 with central differences (Sec. 5.2).
 * ``three_sum``          -- Eq. 26-29 and A8-A10 on the single grid, the
                             literal three-term form.
+* ``kernel_cells_tpz``   -- Eq. 41-43: the same kernels with the trapezoidal
+                            rule in phi (the paper's SIM with N_tpz).
 * ``particle_cells``     -- Eq. 35-37 and Sec. 5.2: the particle method, the
                             modified particle method and the softened
                             particle kernel of the comparison (BM08), as
@@ -65,6 +67,9 @@ def _load():
         lib.sgo_cell.restype = ctypes.c_int
         lib.sgo_cells_table.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, dp, ctypes.c_int]
         lib.sgo_cells_table.restype = ctypes.c_int
+        lib.sgo_cells_table_tpz.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                            ctypes.c_double, dp, ctypes.c_int]
+        lib.sgo_cells_table_tpz.restype = ctypes.c_int
         lib.sgo_direct_sum.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, dp, dp, dp, lp, ctypes.c_long,
                                        dp, dp, ctypes.c_int]
         lib.sgo_direct_sum.restype = None
@@ -191,6 +196,26 @@ def particle_cells(nu: int, nphi: int, du: float, kind: str, soften: float = 0.0
 def particle_kernels(nu: int, nphi: int, du: float, kind: str, soften: float = 0.0):
     """Folded kernels (Kr, Kphi) of a particle method."""
     return fold(particle_cells(nu, nphi, du, kind, soften), math.exp(du), 2.0 * math.pi / nphi)
+
+
+def kernel_cells_tpz(nu: int, nphi: int, du: float, n_tpz: int, rtol: float = 2e-14, nthreads: int = 0) -> np.ndarray:
+    """Kernel table [6, 2Nu+1, Nphi] of the trapezoidal form (Eq. 41-43;
+    the paper's SIM with N_tpz trapezoids per cell in phi): K^{r,0},
+    K^{r,r}, K^{r,phi}, K^{phi,phi} by the trapezoidal rule over N_tpz + 1
+    azimuths of exact eta-integrals, K^{phi,0}, K^{phi,r} and the own cell
+    exact (sg_oracle.c)."""
+    out = np.zeros((NC, 2 * nu + 1, nphi))
+    bad = _load().sgo_cells_table_tpz(int(nu), int(nphi), float(du), int(n_tpz), float(rtol), _dp(out),
+                                      int(nthreads))
+    if bad:
+        raise RuntimeError(f"oracle quadrature did not converge for {bad} integrals")
+    return out
+
+
+def kernels_tpz(nu: int, nphi: int, du: float, n_tpz: int, rtol: float = 2e-14, nthreads: int = 0):
+    """Folded kernels (Kr, Kphi) of the trapezoidal form."""
+    cells = kernel_cells_tpz(nu, nphi, du, n_tpz, rtol=rtol, nthreads=nthreads)
+    return fold(cells, math.exp(du), 2.0 * math.pi / nphi)
 
 
 # --------------------------------------------------------------------------

@@ -539,6 +539,52 @@ int sgo_cells_table(int nu, int nphi, double du, double rtol, double* out, int n
 }
 
 /*
+ * The trapezoidal form of the kernels (Eq. 41-43 for K^{r,0}, K^{r,r},
+ * K^{r,phi}, the same rule for K^{phi,phi} of App. A): for every cell but
+ * the own one, the eta-integrals at the N_tpz + 1 azimuths
+ * phi'_m = phi_{j'-1/2} + m dtheta, dtheta = dphi / N_tpz, of the source cell
+ * (f_xi: adaptive, exact to rtol) combined by the trapezoidal rule.
+ * K^{phi,0}, K^{phi,r} are exact in the paper too, and the own cell is the
+ * singular integral of Sec. 4: those entries keep the exact table of
+ * sgo_cells_table, which this fills first.  Same layout and return value.
+ */
+int sgo_cells_table_tpz(int nu, int nphi, double du, int ntpz, double rtol, double* out, int nthreads)
+{
+    int bad = sgo_cells_table(nu, nphi, du, rtol, out, nthreads);
+    long nk = 2L * nu + 1, per = nk * nphi, nq = nphi / 2 + 1;
+    const int comp[4] = {0, 1, 2, 5};
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : bad)
+#endif
+    for (long idx = 0; idx < nk * nq; idx++) {
+        int k = (int)(idx / nq) - nu;
+        int q = (int)(idx % nq);
+        if (k == 0 && q == 0) continue;
+        int cbad = 0;
+        cell_t cell;
+        cell_setup(&cell, du, nphi, k, q, rtol, &cbad);
+        double dth = 2.0 * cell.half_dphi / ntpz, sum[NC] = {0, 0, 0, 0, 0, 0};
+        for (int m = 0; m <= ntpz; m++) {
+            double t = (m == ntpz) ? cell.half_dphi : -cell.half_dphi + m * dth;
+            double g[NV];
+            f_xi(t, &cell, g);
+            double w = (m == 0 || m == ntpz) ? 0.5 : 1.0;
+            for (int c = 0; c < NC; c++) sum[c] += w * g[c];
+        }
+        bad += cbad;
+        long row = (long)(k + nu) * nphi;
+        int qm = (nphi - q) % nphi;
+        for (int i = 0; i < 4; i++) {
+            int c = comp[i];
+            out[c * per + row + q] = sum[c] * dth;
+            if (qm != q) out[c * per + row + qm] = (c == 2) ? -sum[c] * dth : sum[c] * dth;
+        }
+    }
+    return bad;
+}
+
+/*
  * Direct O(N^2) sum (the convolution form of Eq. 27-29 and A8-A10 after the
  * slope terms are folded into one kernel per component):
  *   F_r[i,j]   = G sum_{m,l} sigma[m,l] Kr  [i-m, (j-l) mod Nphi]

@@ -296,7 +296,7 @@ sg_status sg_kernels_build(sg_plan* p, const sg_build_opts* opts, cudaStream_t s
 {
     if (!p) return SG_ERR_ARG;
     double rtol = 1e-14, soften = 0.0;
-    int wp = 0, kind = SG_KERNEL_SIM;
+    int wp = 0, kind = SG_KERNEL_SIM, ntpz = 0;
     if (opts) {
         if (opts->rtol > 0.0) rtol = opts->rtol;
         wp = opts->weight_p;
@@ -305,6 +305,8 @@ sg_status sg_kernels_build(sg_plan* p, const sg_build_opts* opts, cudaStream_t s
         if (kind < SG_KERNEL_SIM || kind > SG_KERNEL_SOFTENED) return SG_ERR_ARG;
         soften = opts->soften;
         if (kind == SG_KERNEL_SOFTENED && !(soften > 0.0 && soften < 1e3)) return SG_ERR_ARG;
+        ntpz = opts->n_tpz;
+        if (ntpz < 0 || ntpz > 1024) return SG_ERR_ARG;
     }
     // beta^{p (i - i_ref)} must stay in range for both dtypes
     if (fabs((double)wp * p->du * p->nu) > 60.0) return SG_ERR_UNSUPPORTED;
@@ -353,6 +355,8 @@ sg_status sg_kernels_build(sg_plan* p, const sg_build_opts* opts, cudaStream_t s
     if ((kind == SG_KERNEL_SIM ? launch_cells(nu, nphi, p->du, rtol, p->cells, flag, stream)
                                : launch_point_cells(nu, nphi, p->du, kind, soften, rtol, p->cells, flag, stream)) !=
             cudaSuccess ||
+        (kind == SG_KERNEL_SIM && ntpz > 0 &&
+         launch_cells_tpz(nu, nphi, p->du, ntpz, rtol, p->cells, flag, stream) != cudaSuccess) ||
         launch_fold(nu, nphi, p->du, p->G, wp, p->cells, p->keff, nsr, nsp, stream) != cudaSuccess) {
         ret = SG_ERR_CUDA;
         goto done;

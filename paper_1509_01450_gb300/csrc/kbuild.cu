@@ -49,6 +49,16 @@
 // exact own-cell values for the modified method) and has D = s, with both
 // numerators zero, when softened.
 //
+// k_cells_tpz: the trapezoidal form of the cell integrals (Eq. 41-43 for
+// K^{r,0}, K^{r,r}, K^{r,phi}; the same rule for K^{phi,phi}, App. A), which
+// the paper's SIM uses with N_tpz = 19: at the N_tpz + 1 equally spaced
+// azimuths xi - xi_c = -dphi/2 + m dphi / N_tpz of the source cell the
+// eta-integrals are taken exactly (adaptively: 8- and 12-point
+// Gauss-Legendre per panel, bisected until they agree, with a breakpoint at
+// eta = cos xi where the integrand peaks) and combined by the trapezoidal
+// rule.  K^{phi,0}, K^{phi,r} (exact in the paper too) and the own cell
+// (Sec. 4) keep the values of k_cells and k_self_cell.
+//
 // k_fold: the slope terms of Eq. 28-29 / A9-A10 with central differences
 // fold into one kernel per component:
 //   K^eff[k,q] = K^{.,0}[k,q] + (beta^{k+1} K^{.,r}[k+1,q]
@@ -266,6 +276,107 @@ __global__ void __launch_bounds__(128) k_cells(int nu, int nphi, double du, doub
                 cells[c6 * per + row + q] = res[c6];
                 const bool odd = (c6 == 2 || c6 == 3 || c6 == 4);
                 if (qm != q) cells[c6 * per + row + qm] = odd ? -res[c6] : res[c6];
+            }
+            if (bad) {
+                atomicOr(flag, 1);
+                atomicAdd(flag + 1, 1);
+                atomicExch(flag + 2, k);
+                atomicExch(flag + 3, q);
+            }
+        }
+    }
+}
+
+// eta-integrals of the six integrands over the source cell (del = eta -
+// eta_c in [-hw, hw]) at one azimuth xi = xi_c + t (c, s = cos xi, sin xi);
+// returns 1 if a panel could not meet the tolerance.
+#define SG_TSTACK 48
+#define SG_TMAXPAN 4000
+__device__ int eta_integral(double eta_c, double em1, double hw, double t, double c, double s, double rtol, double* I)
+{
+    double2 stk[SG_TSTACK];
+    int sp = 0, npan = 0, bad = 0;
+#pragma unroll
+    for (int c6 = 0; c6 < 6; c6++) I[c6] = 0.0;
+    const double vc = c > 0.0 ? s * s / (1.0 + c) : 1.0 - c;
+    const double peak = -vc - em1;  // del of eta = cos xi
+    if (peak > -hw && peak < hw) {
+        stk[sp++] = make_double2(peak, hw);
+        stk[sp++] = make_double2(-hw, peak);
+    } else {
+        stk[sp++] = make_double2(-hw, hw);
+    }
+    while (sp > 0) {
+        const double2 P = stk[--sp];
+        const double h = 0.5 * (P.y - P.x), mid = 0.5 * (P.x + P.y);
+        double I8[6] = {0, 0, 0, 0, 0, 0}, I12[6] = {0, 0, 0, 0, 0, 0}, A12[6] = {0, 0, 0, 0, 0, 0};
+        for (int a = 0; a < 8; a++) acc6(mid + h * c_x8[a], eta_c, em1, t, c, s, h * c_w8[a], I8, nullptr);
+        for (int a = 0; a < 12; a++) acc6(mid + h * c_x12[a], eta_c, em1, t, c, s, h * c_w12[a], I12, A12);
+        bool ok = true;
+#pragma unroll
+        for (int c6 = 0; c6 < 6; c6++) {
+            const double scale = A12[c6] + A12[(c6 + 3) % 6];  // the force vector's size, as in k_cells
+            if (fabs(I12[c6] - I8[c6]) > (rtol + 64.0 * 2.220446049250313e-16) * scale) ok = false;
+        }
+        if (!ok && (sp + 2 > SG_TSTACK || ++npan > SG_TMAXPAN)) {
+            ok = true;
+            bad = 1;
+        }
+        if (ok) {
+#pragma unroll
+            for (int c6 = 0; c6 < 6; c6++) I[c6] += I12[c6];
+        } else {
+            stk[sp++] = make_double2(mid, P.y);
+            stk[sp++] = make_double2(P.x, mid);
+        }
+    }
+    return bad;
+}
+
+// One warp per offset (q in [0, N_phi/2], the rest by the mirror xi -> -xi),
+// one lane per azimuth node.
+__global__ void __launch_bounds__(128) k_cells_tpz(int nu, int nphi, double du, int ntpz, double rtol,
+                                                   double* __restrict__ cells, int* __restrict__ flag)
+{
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const double dphi = 2.0 * M_PI / nphi, dth = dphi / ntpz;
+    const int nq = nphi / 2 + 1;
+    const long noff = (long)(2 * nu + 1) * nq;
+    const long per = (long)(2 * nu + 1) * nphi;
+    const long wstride = (long)gridDim.x * 4;
+    for (long off = (long)blockIdx.x * 4 + wib; off < noff; off += wstride) {
+        const int k = (int)(off / nq) - nu;
+        const int q = (int)(off % nq);
+        if (k == 0 && q == 0) continue;  // own cell: exact (k_self_cell)
+        const double eta_c = exp(-du * k), em1 = expm1(-du * k);
+        const double hw = eta_c * tanh(0.5 * du);
+        double sc, cc;
+        sincospi(-2.0 * q / nphi, &sc, &cc);
+        double acc[4] = {0, 0, 0, 0};
+        int bad = 0;
+        for (int m = lane; m <= ntpz; m += 32) {
+            const double t = m == ntpz ? 0.5 * dphi : -0.5 * dphi + m * dth;
+            double st, ct;
+            sincos(t, &st, &ct);
+            double I[6];
+            bad |= eta_integral(eta_c, em1, hw, t, ct * cc - st * sc, st * cc + ct * sc, rtol, I);
+            const double w = (m == 0 || m == ntpz) ? 0.5 * dth : dth;
+            acc[0] += w * I[0];  // K^{r,0}
+            acc[1] += w * I[1];  // K^{r,r}
+            acc[2] += w * I[2];  // K^{r,phi}
+            acc[3] += w * I[5];  // K^{phi,phi}
+        }
+#pragma unroll
+        for (int c4 = 0; c4 < 4; c4++) acc[c4] = warp_sum(acc[c4]);
+        bad = __any_sync(0xffffffffu, bad);
+        if (lane == 0) {
+            const long row = (long)(k + nu) * nphi;
+            const int qm = (nphi - q) & (nphi - 1);
+            const int comp[4] = {0, 1, 2, 5};
+#pragma unroll
+            for (int c4 = 0; c4 < 4; c4++) {
+                cells[comp[c4] * per + row + q] = acc[c4];
+                if (qm != q) cells[comp[c4] * per + row + qm] = comp[c4] == 2 ? -acc[c4] : acc[c4];
             }
             if (bad) {
                 atomicOr(flag, 1);
@@ -499,6 +610,20 @@ cudaError_t launch_cells(int nu, int nphi, double du, double rtol, double* cells
     if (blocks > cap) blocks = cap;
     k_cells<<<(int)blocks, 128, 0, st>>>(nu, nphi, du, rtol, cells, flag);
     k_self_cell<<<1, 256, 0, st>>>(nu, nphi, du, rtol, cells, flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cells_tpz(int nu, int nphi, double du, int ntpz, double rtol, double* cells, int* flag,
+                             cudaStream_t st)
+{
+    int dev, nsm;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const long noff = (long)(2 * nu + 1) * (nphi / 2 + 1);
+    long blocks = (noff + 3) / 4;
+    const long cap = (long)nsm * 32;
+    if (blocks > cap) blocks = cap;
+    k_cells_tpz<<<(int)blocks, 128, 0, st>>>(nu, nphi, du, ntpz, rtol, cells, flag);
     return cudaGetLastError();
 }
 

@@ -108,6 +108,9 @@ cudaError_t launch_spectra(const PlanView& p, const double* nsr, const double* n
 
 // kbuild.cu
 cudaError_t launch_cells(int nu, int nphi, double du, double rtol, double* cells, int* flag, cudaStream_t st);
+// the trapezoidal variant of the cell integrals over a table launch_cells made
+cudaError_t launch_cells_tpz(int nu, int nphi, double du, int ntpz, double rtol, double* cells, int* flag,
+                             cudaStream_t st);
 // the particle kinds' tables (sg_kernel_kind 1-3; for 2 with the exact own cell)
 cudaError_t launch_point_cells(int nu, int nphi, double du, int kind, double soften, double rtol, double* cells,
                                int* flag, cudaStream_t st);

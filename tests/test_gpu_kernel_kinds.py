@@ -1,8 +1,8 @@
-"""The particle-method kernels (Eq. 35-37, and the softened comparison method
-of Sec. 5.2) built by the CUDA kernel builder, against the oracle's
-particle tables: the raw tables, the folded kernels, the forces (FP64 within
-1e-12 relative L2, FP32 within 1e-5) and the convergence orders of Table 1
-through the CUDA path."""
+"""The kernel variants built by the CUDA kernel builder: the particle-method
+kernels (Eq. 35-37, and the softened comparison method of Sec. 5.2) and the
+trapezoidal SIM kernels (Eq. 41-43), against the oracle's tables: the raw
+tables, the folded kernels, the forces (FP64 within 1e-12 relative L2, FP32
+within 1e-5) and the convergence orders of Table 1 through the CUDA path."""
 import math
 
 import numpy as np
@@ -116,3 +116,77 @@ def test_bad_options(torch_cuda):
     b = plan.build(kind="sim").forces(st)[0].clone()
     c = plan.build(kind="particle").forces(st)[0].clone()
     assert torch.equal(a, c) and not torch.equal(a, b)
+
+
+@pytest.mark.parametrize("ntpz", [1, 2, 19])
+@pytest.mark.parametrize("nu,nphi", [(4, 8), (16, 64), (64, 32), (128, 128)])
+def test_tpz_tables_and_folded_kernels(torch_cuda, oracle_mod, ntpz, nu, nphi):
+    from paper_1509_01450_gb300 import Plan
+
+    u_min, du = workloads.grid_params(nu, 0.05, 20.0)
+    plan = Plan(nu, nphi, u_min, du, 1.0, "float64").build(n_tpz=ntpz)
+    assert plan.build_report() == (0, 0, 0, 0)
+    ref = oracle_mod.kernel_cells_tpz(nu, nphi, du, ntpz)
+    got = plan.cells()
+    base = np.abs(ref[0]) + np.abs(ref[3])
+    row = base.max(axis=1, keepdims=True)
+    for c in range(6):
+        err = np.abs(got[c] - ref[c]) / (np.abs(ref[c]) + base + 1e-3 * row)
+        assert err.max() < 2e-12, (ntpz, c, err.max(), np.unravel_index(err.argmax(), err.shape))
+    Kr, Kp = oracle_mod.fold(ref, math.exp(du), 2 * math.pi / nphi)
+    gKr, gKp = plan.kernels()
+    sk = np.abs(Kr).max() + np.abs(Kp).max()
+    assert np.abs(gKr - Kr).max() < 1e-12 * sk and np.abs(gKp - Kp).max() < 1e-12 * sk
+
+
+@pytest.mark.parametrize("nu,nphi", [(32, 128), (256, 64)])
+@pytest.mark.parametrize("dtype,tol", [("float64", 1e-12), ("float32", 1e-5)])
+def test_tpz_forces_against_the_oracle(torch_cuda, oracle_mod, nu, nphi, dtype, tol):
+    from paper_1509_01450_gb300 import Plan
+
+    torch = torch_cuda
+    u_min, du = workloads.grid_params(nu, 0.01, 100.0)
+    plan = Plan(nu, nphi, u_min, du, 1.0, dtype).build(n_tpz=19)
+    r, phi = workloads.centres(nu, nphi, u_min, du)
+    sigma = workloads.spiral_clump(r, phi)
+    Kr, Kp = oracle_mod.kernels_tpz(nu, nphi, du, 19)
+    Fr_ref, Fp_ref = oracle_mod.direct_sum(sigma, Kr, Kp)
+    Fr, Fp = plan.forces(torch.tensor(sigma, dtype=plan.dtype, device="cuda"))
+    torch.cuda.synchronize()
+    plan.check()
+    assert oracle_mod.rel_l2(Fr.double().cpu().numpy(), Fp.double().cpu().numpy(), Fr_ref, Fp_ref) < tol
+
+
+def test_sim_tpz19_orders_through_the_cuda_path(torch_cuda):
+    """Table 1's SIM column (N_tpz = 19, Sec. 5.2) for the sigma_{D_5} disk
+    from FP64 forces computed by the library."""
+    from paper_1509_01450_gb300 import Plan
+
+    torch = torch_cuda
+    paper = {(d, n, c): float(v) for d, n, c, v in load_golden("table1_sim_orders.txt")}
+    errs = []
+    for N in (128, 256, 512):
+        u_min, du = workloads.grid_params(N, 0.01, 1.0)
+        plan = Plan(N, N, u_min, du, 1.0, "float64").build(n_tpz=19)
+        r, phi = workloads.centres(N, N, u_min, du)
+        sig = workloads.sigma_dn(5, 0.25, 0.5, 0.1, r, phi)
+        Fr, Fp = plan.forces(torch.tensor(sig, device="cuda"))
+        torch.cuda.synchronize()
+        Ar, Ap = A.dn_offcentre_forces(5, 0.25, 0.5, 0.1, r, phi)
+        d = (np.abs(Fr.cpu().numpy() - Ar), np.abs(Fp.cpu().numpy() - Ap))
+        errs.append({("L1", "r"): d[0].mean(), ("L1", "phi"): d[1].mean(), ("L2", "r"): np.sqrt((d[0] ** 2).mean()),
+                     ("L2", "phi"): np.sqrt((d[1] ** 2).mean()), ("Linf", "r"): d[0].max(),
+                     ("Linf", "phi"): d[1].max()})
+    for key, e in errs[-1].items():
+        got = math.log2(errs[-2][key] / e)
+        assert got > 1.7 and abs(got - paper[("D5",) + key]) < 0.3, (key, got)
+
+
+def test_bad_tpz(torch_cuda):
+    from paper_1509_01450_gb300 import Plan, SgError, sg
+
+    plan = Plan(16, 16, 0.0, 0.1, 1.0, "float32")
+    for n in (-1, 1025):
+        with pytest.raises(SgError) as ei:
+            plan.build(n_tpz=n)
+        assert ei.value.status == sg.SG_ERR_ARG
