@@ -98,7 +98,17 @@ typedef struct {
                       K^{r,0}, K^{r,r}, K^{r,phi} and K^{phi,phi}, the own
                       cell still exact (Sec. 4; the paper's SIM uses 19);
                       ignored by the particle kinds */
-    int reserved[3];
+    int radial_edges; /* 0 (default): sigma is zero outside the grid and the
+                      central radial slopes of Eq. 25 apply wherever the
+                      stencil touches it, ghost rows 0 and N_u + 1 included
+                      (a pure convolution); 1: no ghost rows, and the slopes
+                      of the first and last rows are one-sided, (sigma_2 -
+                      sigma_1) / (r_2 - r_1) and (sigma_N - sigma_{N-1}) /
+                      (r_N - r_{N-1}).  With 1 a rank-4 correction per phi
+                      mode runs after the column pass (and its transpose in
+                      the adjoint), and the forces keep second order up to
+                      the radial edges when sigma does not vanish there */
+    int reserved[2];
 } sg_build_opts;
 
 /*
@@ -130,8 +140,10 @@ sg_status sg_plan_create(sg_plan** out, int N_u, int N_phi, double u_min, double
  * Returns SG_ERR_TIMEOUT (the plan is still usable) if a cell integral
  * could not reach the tolerance within the quadrature's budget, and
  * SG_ERR_ARG for an unknown kind, soften <= 0 with SG_KERNEL_SOFTENED,
- * n_tpz outside [0, 1024] or |weight_p| > 8.  Allocates and frees FP64
- * scratch for the spectra.
+ * n_tpz outside [0, 1024], radial_edges not 0 or 1, or |weight_p| > 8.
+ * Allocates and frees FP64 scratch for the spectra; radial_edges = 1 also
+ * allocates the plan's edge tables, 2 (N_phi/2 + 1)(2 N_u + 1) values of
+ * the working dtype.
  */
 sg_status sg_kernels_build(sg_plan* plan, const sg_build_opts* opts, cudaStream_t stream);
 
@@ -287,7 +299,8 @@ sg_status sg_plan_set_wait_limit(sg_plan* plan, double seconds);
  * without rebuilding.  A loaded plan holds no FP64 build tables:
  * sg_plan_kernels and sg_plan_cells return SG_ERR_UNSUPPORTED for it.
  * SG_ERR_IO: the file cannot be written or read, is truncated or too long,
- * or is not a plan file of this library.
+ * or is not a plan file of this library.  A plan built with radial_edges = 1
+ * is not saved (SG_ERR_UNSUPPORTED).
  */
 sg_status sg_plan_save(const sg_plan* plan, const char* path, cudaStream_t stream);
 sg_status sg_plan_load(sg_plan** out, const char* path, cudaStream_t stream);

@@ -221,16 +221,32 @@ def kernels_tpz(nu: int, nphi: int, du: float, n_tpz: int, rtol: float = 2e-14, 
 # --------------------------------------------------------------------------
 # Eq. 25 slopes and the three-term sums of Eq. 26-29 / A8-A10
 # --------------------------------------------------------------------------
-def slopes(sigma: np.ndarray, grid: Grid):
-    """Central-difference slopes (Sec. 5.2 uses central differences).
+def slopes(sigma: np.ndarray, grid: Grid, edges: str = "ghost"):
+    """Slopes of the piecewise-linear density (Eq. 25; Sec. 5.2 uses central
+    differences).
 
-    sigma is zero outside the grid.  Returns (dr, dphi_slope, rows) where
-    dr[i'] = (sigma_{i'+1} - sigma_{i'-1}) / (r_{i'+1} - r_{i'-1}) for the
-    rows i' = -1 .. Nu (the two ghost rows the stencil touches included), and
-    dphi_slope[i', j'] = (sigma_{j'+1} - sigma_{j'-1}) / (2 dphi), periodic,
-    for the rows of the grid.
+    edges = "ghost" (the default): sigma is zero outside the grid and the
+    central stencil is applied wherever it touches the grid, so the returned
+    rows are i' = -1 .. Nu (the two ghost rows included):
+        dr[i'] = (sigma_{i'+1} - sigma_{i'-1}) / (r_{i'+1} - r_{i'-1}).
+    edges = "onesided": only the grid's rows i' = 0 .. Nu-1 carry slopes,
+    central inside and one-sided at the first and last rows:
+        dr[0] = (sigma_1 - sigma_0) / (r_1 - r_0),
+        dr[Nu-1] = (sigma_{Nu-1} - sigma_{Nu-2}) / (r_{Nu-1} - r_{Nu-2}).
+    Returns (dr, dphi_slope, rows) with dr[n] the slope of row rows[n] and
+    dphi_slope[i', j'] = (sigma_{j'+1} - sigma_{j'-1}) / (2 dphi), periodic.
     """
     nu, nphi = sigma.shape
+    dphi_slope = (np.roll(sigma, -1, axis=1) - np.roll(sigma, 1, axis=1)) / (2.0 * grid.dphi)
+    if edges == "onesided":
+        rows = np.arange(nu)
+        dr = np.empty((nu, nphi))
+        for i in range(nu):
+            lo, hi = max(i - 1, 0), min(i + 1, nu - 1)
+            dr[i] = (sigma[hi] - sigma[lo]) / (grid.r[hi] - grid.r[lo])
+        return dr, dphi_slope, rows
+    if edges != "ghost":
+        raise ValueError(edges)
     ext = np.zeros((nu + 4, nphi))  # rows -2 .. Nu+1
     ext[2:nu + 2] = sigma
     rows = np.arange(-1, nu + 1)
@@ -239,16 +255,16 @@ def slopes(sigma: np.ndarray, grid: Grid):
     for n, ip in enumerate(rows):
         e = ip + 2
         dr[n] = (ext[e + 1] - ext[e - 1]) / (rc[e + 1] - rc[e - 1])
-    dphi_slope = (np.roll(sigma, -1, axis=1) - np.roll(sigma, 1, axis=1)) / (2.0 * grid.dphi)
     return dr, dphi_slope, rows
 
 
-def three_sum(sigma: np.ndarray, cells: np.ndarray, grid: Grid, G: float = 1.0):
+def three_sum(sigma: np.ndarray, cells: np.ndarray, grid: Grid, G: float = 1.0, edges: str = "ghost"):
     """Eq. 26-29 (radial) and A8-A10 (azimuthal) on the single grid, term by
     term: F^r = F^{r,0} + r_i sum delta^r K^{r,r} + sum delta^phi K^{r,phi},
-    and the same for F^phi.  O(N^4); for small grids."""
+    and the same for F^phi, with the slopes of ``slopes(..., edges)``.
+    O(N^4); for small grids."""
     nu, nphi = sigma.shape
-    dr, dph, rows = slopes(sigma, grid)
+    dr, dph, rows = slopes(sigma, grid, edges)
     Fr = np.zeros((nu, nphi))
     Fp = np.zeros((nu, nphi))
     Frr = np.zeros((nu, nphi))
@@ -274,6 +290,34 @@ def three_sum(sigma: np.ndarray, cells: np.ndarray, grid: Grid, G: float = 1.0):
     Fr += grid.r[:, None] * Frr
     Fp += grid.r[:, None] * Fpr
     return G * Fr, G * Fp
+
+
+def onesided_forces(sigma: np.ndarray, cells: np.ndarray, grid: Grid, G: float = 1.0):
+    """The sums of ``three_sum(..., edges="onesided")`` for any grid size: the
+    convolution with the folded kernels (the ghost-row slopes) plus the
+    radial slope terms of Eq. 28 / A9 for the difference of the two slope
+    sets, which is non-zero on the rows -1, 0, Nu-1 and Nu only:
+        r_i sum_{i', j'} (dr_onesided - dr_ghost)[i', j'] K^{.,r}[i - i', j - j']."""
+    nu, nphi = sigma.shape
+    Kr, Kp = fold(cells, grid.beta, grid.dphi)
+    Fr, Fp = fft_conv(sigma, Kr, Kp, G)
+    dg, _, rows_g = slopes(sigma, grid, "ghost")
+    do, _, _ = slopes(sigma, grid, "onesided")
+    diff = -dg
+    diff[1:nu + 1] += do  # rows_g[n] = n - 1
+    i = np.arange(nu)[:, None]
+    j = np.arange(nphi)[None, :]
+    Frr = np.zeros((nu, nphi))
+    Fpr = np.zeros((nu, nphi))
+    for n, ip in enumerate(rows_g):
+        if not np.any(diff[n]):
+            continue
+        for jp in range(nphi):
+            k = i - ip + nu
+            q = (j - jp) % nphi
+            Frr += diff[n, jp] * cells[1][k, q]
+            Fpr += diff[n, jp] * cells[4][k, q]
+    return Fr + G * grid.r[:, None] * Frr, Fp + G * grid.r[:, None] * Fpr
 
 
 def fold(cells: np.ndarray, beta: float, dphi: float):

@@ -41,7 +41,7 @@ static void free_plan(sg_plan* p)
     if (p->bfork) cudaEventDestroy(p->bfork);
     if (p->bstream) cudaStreamDestroy(p->bstream);
     void* bufs[] = {p->tw, p->wa, p->wb, p->wc, p->kr, p->kp, p->wpre, p->wpost, p->tw64, p->cells, p->keff,
-                    p->h_sigma, p->h_fr, p->h_fp, p->derr};
+                    p->h_sigma, p->h_fr, p->h_fp, p->derr, p->egr, p->egp};
     for (void* b : bufs)
         if (b) cudaFree(b);
     free(p);
@@ -220,6 +220,7 @@ sg_status sg_plan_save(const sg_plan* p, const char* path, cudaStream_t stream)
 {
     if (!p || !path) return SG_ERR_ARG;
     if (!p->built) return SG_ERR_NOT_BUILT;
+    if (p->edges) return SG_ERR_UNSUPPORTED;  // the file holds no edge tables
     const size_t kb = spectrum_bytes(p), wb = (size_t)p->nu * p->elem;
     std::vector<unsigned char> buf(2 * kb + 2 * wb);
     SG_TRY(cudaMemcpyAsync(buf.data(), p->kr, kb, cudaMemcpyDeviceToHost, stream));
@@ -296,7 +297,7 @@ sg_status sg_kernels_build(sg_plan* p, const sg_build_opts* opts, cudaStream_t s
 {
     if (!p) return SG_ERR_ARG;
     double rtol = 1e-14, soften = 0.0;
-    int wp = 0, kind = SG_KERNEL_SIM, ntpz = 0;
+    int wp = 0, kind = SG_KERNEL_SIM, ntpz = 0, edges = 0;
     if (opts) {
         if (opts->rtol > 0.0) rtol = opts->rtol;
         wp = opts->weight_p;
@@ -307,6 +308,8 @@ sg_status sg_kernels_build(sg_plan* p, const sg_build_opts* opts, cudaStream_t s
         if (kind == SG_KERNEL_SOFTENED && !(soften > 0.0 && soften < 1e3)) return SG_ERR_ARG;
         ntpz = opts->n_tpz;
         if (ntpz < 0 || ntpz > 1024) return SG_ERR_ARG;
+        edges = opts->radial_edges;
+        if (edges != 0 && edges != 1) return SG_ERR_ARG;
     }
     // beta^{p (i - i_ref)} must stay in range for both dtypes
     if (fabs((double)wp * p->du * p->nu) > 60.0) return SG_ERR_UNSUPPORTED;
@@ -337,6 +340,24 @@ sg_status sg_kernels_build(sg_plan* p, const sg_build_opts* opts, cudaStream_t s
             SG_TRY(cudaStreamSynchronize(stream));
         }
     }
+    // one-sided edge slopes: s_a = sum_b c[a][b] sigma_b for the slope change
+    // r_a (delta^onesided - delta^ghost) of the rows a = -1, 0, N-1, N
+    // (bb = beta - 1/beta, beta - 1, 1 - 1/beta), divided by the weights of
+    // the rows b = 0, 1, N-2, N-1 that the passes hold sigma with
+    p->edges = 0;
+    if (edges) {
+        const double bb = 2.0 * sinh(p->du), bm = expm1(p->du), bi = -expm1(-p->du);
+        const double c[16] = {-1.0 / bb, 0.0, 0.0, 0.0,                 // a = -1: ghost slope removed
+                              -1.0 / bm, 1.0 / bm - 1.0 / bb, 0.0, 0.0,  // a = 0
+                              0.0, 0.0, 1.0 / bb - 1.0 / bi, 1.0 / bi,   // a = N-1
+                              0.0, 0.0, 0.0, 1.0 / bb};                 // a = N: ghost slope removed
+        const int brow[4] = {0, 1, nu - 2, nu - 1};
+        for (int a = 0; a < 4; a++)
+            for (int b = 0; b < 4; b++) p->ecoef[4 * a + b] = c[4 * a + b] * exp(-wp * (brow[b] - nu / 2) * p->du);
+        const size_t n = (size_t)(nphi / 2 + 1) * (2 * nu + 1) * p->elem;
+        sg_status st = SG_OK;
+        if ((!p->egr && (st = dev_alloc(p, &p->egr, n))) || (!p->egp && (st = dev_alloc(p, &p->egp, n)))) return st;
+    }
     int* flag = nullptr;
     double *nsr = nullptr, *nsp = nullptr;
     double2* W = nullptr;
@@ -357,7 +378,12 @@ sg_status sg_kernels_build(sg_plan* p, const sg_build_opts* opts, cudaStream_t s
             cudaSuccess ||
         (kind == SG_KERNEL_SIM && ntpz > 0 &&
          launch_cells_tpz(nu, nphi, p->du, ntpz, rtol, p->cells, flag, stream) != cudaSuccess) ||
-        launch_fold(nu, nphi, p->du, p->G, wp, p->cells, p->keff, nsr, nsp, stream) != cudaSuccess) {
+        launch_fold(nu, nphi, p->du, p->G, wp, p->cells, p->keff, nsr, nsp, stream) != cudaSuccess ||
+        (edges && (p->dtype == SG_F32 ? launch_edge_spectra<float>(nu, nphi, p->du, p->G, p->cells, p->tw64,
+                                                                   (float*)p->egr, (float*)p->egp, stream)
+                                      : launch_edge_spectra<double>(nu, nphi, p->du, p->G, p->cells, p->tw64,
+                                                                    (double*)p->egr, (double*)p->egp, stream)) !=
+                     cudaSuccess)) {
         ret = SG_ERR_CUDA;
         goto done;
     }
@@ -378,6 +404,7 @@ sg_status sg_kernels_build(sg_plan* p, const sg_build_opts* opts, cudaStream_t s
             goto done;
         }
         p->built = 1;
+        p->edges = edges;
         if (p->report[0]) ret = SG_ERR_TIMEOUT;
     }
 done:

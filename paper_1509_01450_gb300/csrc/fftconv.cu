@@ -706,6 +706,142 @@ __global__ void __launch_bounds__(NTB, (sizeof(T) == 4 && NTB == 256) ? 2 : 1) k
 }
 
 // ===========================================================================
+// One-sided radial slopes at the first and last rows (radial_edges = 1).
+// Against the ghost-row slopes of the convolution, the radial slope terms of
+// Eq. 28 / A9 change only for the source rows a in {-1, 0, N_u-1, N_u}:
+//   dF_i = sum_a beta^{i-a} K^{.,r}[i - a, .] (*)_phi s_a,
+// where s_a = r_a (delta_a^onesided - delta_a^ghost) is a combination of
+// sigma's rows {0, 1, N_u-2, N_u-1} (zero for the ghost rows' one-sided
+// counterparts, which do not exist).  Per phi mode that is a rank-4 update of
+// the column: in the weighted frame of the passes
+//   B[m][i] += wpre[i] sum_a gr_m[i - a] s^_a,  C[m][i] += wpre[i] sum_a (-i gp_m[i - a]) s^_a,
+// with s^_a = sum_b coef[a][b] A[m][b] (coef holds the 1 / wpre[b]).  Mode 0
+// packs (DC, Nyquist): its real parts use the DC spectra, its imaginary parts
+// the Nyquist ones, and both azimuthal spectra vanish there.
+// ===========================================================================
+template <typename T>
+struct EdgeCoef {
+    T c[16];
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_edge_fwd(const typename CX<T>::t* __restrict__ A, typename CX<T>::t* B,
+                                                  typename CX<T>::t* C, const T* __restrict__ gr,
+                                                  const T* __restrict__ gp, const T* __restrict__ wpre,
+                                                  EdgeCoef<T> coef, int nu, int nphi)
+{
+    typedef typename CX<T>::t V;
+    const int m = blockIdx.x, half = nphi / 2, K = 2 * nu + 1;
+    const int brow[4] = {0, 1, nu - 2, nu - 1};
+    V ab[4], sa[4];
+#pragma unroll
+    for (int b = 0; b < 4; b++) ab[b] = A[(size_t)m * nu + brow[b]];
+#pragma unroll
+    for (int a = 0; a < 4; a++) {
+        sa[a] = V{0, 0};
+#pragma unroll
+        for (int b = 0; b < 4; b++) sa[a] = V{sa[a].x + coef.c[4 * a + b] * ab[b].x, sa[a].y + coef.c[4 * a + b] * ab[b].y};
+    }
+    // k + N_u = i - a + N_u for a = -1, 0, N_u - 1, N_u
+    const T* g0 = gr + (size_t)m * K;
+    const T* gN = gr + (size_t)half * K;  // Nyquist (mode 0 only)
+    const T* p0 = gp + (size_t)m * K;
+    for (int i = threadIdx.x; i < nu; i += blockDim.x) {
+        const int idx[4] = {i + 1 + nu, i + nu, i + 1, i};
+        const T w = wpre[i];
+        V dr{0, 0}, dp{0, 0};
+        if (m == 0) {
+#pragma unroll
+            for (int a = 0; a < 4; a++) {
+                dr.x += g0[idx[a]] * sa[a].x;
+                dr.y += gN[idx[a]] * sa[a].y;
+            }
+        } else {
+#pragma unroll
+            for (int a = 0; a < 4; a++) {
+                dr.x += g0[idx[a]] * sa[a].x;
+                dr.y += g0[idx[a]] * sa[a].y;
+                dp.x += p0[idx[a]] * sa[a].y;  // -i gp s = gp (s.y - i s.x)
+                dp.y -= p0[idx[a]] * sa[a].x;
+            }
+            V c = C[(size_t)m * nu + i];
+            C[(size_t)m * nu + i] = V{c.x + w * dp.x, c.y + w * dp.y};
+        }
+        V b = B[(size_t)m * nu + i];
+        B[(size_t)m * nu + i] = V{b.x + w * dr.x, b.y + w * dr.y};
+    }
+}
+
+// The transpose for the adjoint: with A, C the column spectra of the weighted
+// seeds gF_r, gF_phi (the backward row pass's outputs) and B the backward
+// column pass's result,
+//   t_a = sum_i wpre[i] (gr_m[i - a] A[m][i] + i gp_m[i - a] C[m][i]),
+//   B[m][b] += sum_a coef[a][b] t_a   for b in {0, 1, N_u-2, N_u-1}.
+template <typename T>
+__global__ void __launch_bounds__(256) k_edge_bwd(const typename CX<T>::t* __restrict__ A,
+                                                  const typename CX<T>::t* __restrict__ C, typename CX<T>::t* B,
+                                                  const T* __restrict__ gr, const T* __restrict__ gp,
+                                                  const T* __restrict__ wpre, EdgeCoef<T> coef, int nu, int nphi)
+{
+    typedef typename CX<T>::t V;
+    __shared__ T red[8][8];
+    const int m = blockIdx.x, half = nphi / 2, K = 2 * nu + 1;
+    const T* g0 = gr + (size_t)m * K;
+    const T* gN = gr + (size_t)half * K;
+    const T* p0 = gp + (size_t)m * K;
+    T acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // t_a = (acc[2a], acc[2a + 1])
+    for (int i = threadIdx.x; i < nu; i += blockDim.x) {
+        const int idx[4] = {i + 1 + nu, i + nu, i + 1, i};
+        const T w = wpre[i];
+        const V a = A[(size_t)m * nu + i];
+        if (m == 0) {
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                acc[2 * q] += w * g0[idx[q]] * a.x;
+                acc[2 * q + 1] += w * gN[idx[q]] * a.y;
+            }
+        } else {
+            const V c = C[(size_t)m * nu + i];
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const T r = w * g0[idx[q]], p = w * p0[idx[q]];
+                acc[2 * q] += r * a.x - p * c.y;  // i gp c = gp (-c.y + i c.x)
+                acc[2 * q + 1] += r * a.y + p * c.x;
+            }
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < 8; v++)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc[v] += __shfl_xor_sync(0xffffffffu, acc[v], o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0)
+#pragma unroll
+        for (int v = 0; v < 8; v++) red[wid][v] = acc[v];
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        const int b = threadIdx.x;
+        const int brow[4] = {0, 1, nu - 2, nu - 1};
+        T tx[4] = {0, 0, 0, 0}, ty[4] = {0, 0, 0, 0};
+        for (int w = 0; w < nw; w++)
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                tx[q] += red[w][2 * q];
+                ty[q] += red[w][2 * q + 1];
+            }
+        T dx = 0, dy = 0;
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            dx += coef.c[4 * q + b] * tx[q];
+            dy += coef.c[4 * q + b] * ty[q];
+        }
+        // the rows b are distinct (N_u >= 4): one thread each
+        V o = B[(size_t)m * nu + brow[b]];
+        B[(size_t)m * nu + brow[b]] = V{o.x + dx, o.y + dy};
+    }
+}
+
+// ===========================================================================
 // Backward P1b: row i, z = (gF_r + i gF_phi) beta^{-p i}, FFT, split into
 // the half spectra of gF_r (-> A) and gF_phi (-> C), staged and stored
 // mode-major.  R = slots rows per row block, arriving as two bulk copies.
@@ -1336,6 +1472,22 @@ static const CUtensorMap* row_map(const PlanView& p, int R, int b, int nphi)
     } while (0)
 
 template <typename T>
+static cudaError_t launch_edges(const PlanView& p, bool adjoint, cudaStream_t st)
+{
+    typedef typename CX<T>::t V;
+    PassRange range_(adjoint ? "sg adjoint edge slopes" : "sg forward edge slopes");
+    EdgeCoef<T> coef;
+    for (int j = 0; j < 16; j++) coef.c[j] = (T)p.ecoef[j];
+    if (adjoint)
+        k_edge_bwd<T><<<p.nphi / 2, 256, 0, st>>>((const V*)p.wa, (const V*)p.wc, (V*)p.wb, (const T*)p.egr,
+                                                  (const T*)p.egp, (const T*)p.wpre, coef, p.nu, p.nphi);
+    else
+        k_edge_fwd<T><<<p.nphi / 2, 256, 0, st>>>((const V*)p.wa, (V*)p.wb, (V*)p.wc, (const T*)p.egr,
+                                                  (const T*)p.egp, (const T*)p.wpre, coef, p.nu, p.nphi);
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_forward(const PlanView& p, const T* sigma, T* Fr, T* Fp, cudaStream_t st, cudaEvent_t* ev,
                            bool sigma_direct)
 {
@@ -1376,6 +1528,7 @@ cudaError_t launch_forward(const PlanView& p, const T* sigma, T* Fr, T* Fp, cuda
             if ((err = launch_pdl(k, p.nphi / 2, L / EE, smem, st, A, (const V*)p.kr, (const V*)p.kp, B, C, p.nu, p.nphi, lL, tw, p.err)) != cudaSuccess) return err;
         });
     }
+    if (p.edges && (err = launch_edges<T>(p, false, st)) != cudaSuccess) return err;
     if (ev && (err = cudaEventRecord(ev[2], st)) != cudaSuccess) return err;
     {
         PassRange range_("sg forward inverse rows");
@@ -1437,6 +1590,7 @@ cudaError_t launch_backward(const PlanView& p, const T* gr, const T* gp, T* gs, 
             if ((err = launch_pdl(k, p.nphi / 2, L / EE, smem, st, A, C, (const V*)p.kr, (const V*)p.kp, B, p.nu, p.nphi, lL, tw, p.err)) != cudaSuccess) return err;
         });
     }
+    if (p.edges && (err = launch_edges<T>(p, true, st)) != cudaSuccess) return err;
     {
         PassRange range_("sg adjoint inverse rows");
         Shape s = shape_for<V>(p.nphi, sizeof(T) == 8 ? 64 : 256);

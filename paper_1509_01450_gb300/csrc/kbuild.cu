@@ -613,6 +613,48 @@ cudaError_t launch_cells(int nu, int nphi, double du, double rtol, double* cells
     return cudaGetLastError();
 }
 
+// k_edge_spec: the phi-spectra of the radial slope kernels for the
+// one-sided edge slopes.  For k in [-N_u, N_u] and mode m in [0, N_phi/2]:
+//   gr[m][k + N_u] = G beta^k / N_phi  sum_q K^{r,r}[k, q]   cos(2 pi m q / N_phi),
+//   gp[m][k + N_u] = G beta^k / N_phi  sum_q K^{phi,r}[k, q] sin(2 pi m q / N_phi),
+// the forward phi-DFTs of the two kernels being gr and -i gp (K^{r,r} is even
+// in q, K^{phi,r} odd).  FP64 sums over q in [0, N_phi/2] with the mirror
+// folded in; cosines and sines from the FP64 twiddle table.  One block per
+// k, one thread per mode.
+template <typename T>
+__global__ void k_edge_spec(int nu, int nphi, double du, double G, const double* __restrict__ cells,
+                            const double2* __restrict__ tw64, T* __restrict__ gr, T* __restrict__ gp)
+{
+    const int kk = blockIdx.x, k = kk - nu, half = nphi / 2;
+    const long per = (long)(2 * nu + 1) * nphi;
+    const double* K1 = cells + 1 * per + (long)kk * nphi;  // K^{r,r}[k, .]
+    const double* K4 = cells + 4 * per + (long)kk * nphi;  // K^{phi,r}[k, .]
+    const int stride = SG_NMAX / nphi;
+    const double sc = G * exp(k * du) / nphi;
+    for (int m = threadIdx.x; m <= half; m += blockDim.x) {
+        double c = K1[0] + ((m & 1) ? -K1[half] : K1[half]), s = 0.0;
+        for (int q = 1; q < half; q++) {
+            const double2 w = tw64[(long)((m * q) & (nphi - 1)) * stride];  // e^{-2 pi i m q / N_phi}
+            c += 2.0 * K1[q] * w.x;
+            s -= 2.0 * K4[q] * w.y;
+        }
+        gr[(long)m * (2 * nu + 1) + kk] = (T)(sc * c);
+        gp[(long)m * (2 * nu + 1) + kk] = (T)(sc * s);
+    }
+}
+
+template <typename T>
+cudaError_t launch_edge_spectra(int nu, int nphi, double du, double G, const double* cells, const void* tw64, T* gr,
+                                T* gp, cudaStream_t st)
+{
+    k_edge_spec<T><<<2 * nu + 1, 256, 0, st>>>(nu, nphi, du, G, cells, (const double2*)tw64, gr, gp);
+    return cudaGetLastError();
+}
+template cudaError_t launch_edge_spectra<float>(int, int, double, double, const double*, const void*, float*, float*,
+                                                cudaStream_t);
+template cudaError_t launch_edge_spectra<double>(int, int, double, double, const double*, const void*, double*,
+                                                 double*, cudaStream_t);
+
 cudaError_t launch_cells_tpz(int nu, int nphi, double du, int ntpz, double rtol, double* cells, int* flag,
                              cudaStream_t st)
 {

@@ -52,6 +52,12 @@ struct sg_plan {
     cudaEvent_t ev[4];  // pass timing (sg_forces_timed), created on first use
     int have_ev;
     int report[4];      // last build: flag bits, failed offsets, one failed (k, q)
+    // one-sided radial slopes at the first and last rows (radial_edges = 1)
+    int edges;
+    void* egr;          // working dtype, [nphi/2 + 1][2 nu + 1]: G beta^k / N_phi times the
+    void* egp;          // phi-DFT of K^{r,r}[k, .] (cosine sum) and of K^{phi,r}[k, .] (sine sum)
+    double ecoef[16];   // [a][b]: slope change of row a in {-1, 0, nu-1, nu} per weighted
+                        // sigma of row b in {0, 1, nu-2, nu-1}
 };
 
 namespace sg {
@@ -69,6 +75,10 @@ struct PlanView {
     const void* wpost;
     int* err;
     const SgRowMaps* maps;  // [2] over wa, wb, wc, or null
+    int edges;              // one-sided radial edge slopes: egr, egp, ecoef below
+    const void* egr;
+    const void* egp;
+    const double* ecoef;
 };
 
 inline PlanView view(const sg_plan* p)
@@ -88,6 +98,10 @@ inline PlanView view(const sg_plan* p)
     v.wpost = p->wpost;
     v.err = p->derr;
     v.maps = p->maps;
+    v.edges = p->edges;
+    v.egr = p->egr;
+    v.egp = p->egp;
+    v.ecoef = p->ecoef;
     return v;
 }
 
@@ -108,6 +122,10 @@ cudaError_t launch_spectra(const PlanView& p, const double* nsr, const double* n
 
 // kbuild.cu
 cudaError_t launch_cells(int nu, int nphi, double du, double rtol, double* cells, int* flag, cudaStream_t st);
+// the phi-spectra of the radial slope kernels for the one-sided edge slopes
+template <typename T>
+cudaError_t launch_edge_spectra(int nu, int nphi, double du, double G, const double* cells, const void* tw64, T* gr,
+                                T* gp, cudaStream_t st);
 // the trapezoidal variant of the cell integrals over a table launch_cells made
 cudaError_t launch_cells_tpz(int nu, int nphi, double du, int ntpz, double rtol, double* cells, int* flag,
                              cudaStream_t st);

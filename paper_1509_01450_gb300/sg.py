@@ -41,7 +41,8 @@ KERNEL_KINDS = {"sim": SG_KERNEL_SIM, "particle": SG_KERNEL_PARTICLE, "particle+
 
 class BuildOpts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("weight_p", ctypes.c_int), ("kind", ctypes.c_int),
-                ("soften", ctypes.c_double), ("n_tpz", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
+                ("soften", ctypes.c_double), ("n_tpz", ctypes.c_int), ("radial_edges", ctypes.c_int),
+                ("reserved", ctypes.c_int * 2)]
 
 
 class BatchItem(ctypes.Structure):
@@ -128,13 +129,14 @@ class Plan:
 
     # -- one-time preparation ------------------------------------------------
     def build(self, rtol: float = 1e-14, weight_p: int = 0, kind="sim", soften: float = 0.0, n_tpz: int = 0,
-              stream=None):
+              radial_edges: int = 0, stream=None):
         """Build the kernels.  kind: "sim" (default; n_tpz > 0 for the
         trapezoidal rule of Eq. 41-43 with n_tpz trapezoids), "particle",
         "particle+" or "softened" (with soften = eps / r_i), or an
-        SG_KERNEL_* code."""
+        SG_KERNEL_* code.  radial_edges = 1: one-sided radial slopes at the
+        first and last rows instead of ghost rows."""
         code = KERNEL_KINDS[kind] if isinstance(kind, str) else int(kind)
-        opts = BuildOpts(rtol, weight_p, code, soften, n_tpz)
+        opts = BuildOpts(rtol, weight_p, code, soften, n_tpz, radial_edges)
         _check(lib().sg_kernels_build(self.handle, ctypes.byref(opts), _stream(stream)), "sg_kernels_build")
         return self
 

@@ -118,7 +118,10 @@ def test_rotation_equivariance(oracle_mod, small):
 # Brute force: piecewise-linear sigma (Eq. 25, central slopes, zero outside
 # the grid) integrated against the point kernel of Eq. 23-24 by scipy.
 # ---------------------------------------------------------------------------
-def _brute_force(sigma, u_min, du, nphi, ti, tj):
+def _brute_force(sigma, u_min, du, nphi, ti, tj, edges="ghost"):
+    """edges = "ghost": central radial slopes wherever the stencil touches the
+    grid (ghost rows -1 and Nu included); "onesided": the grid's rows only,
+    one-sided radial slopes at the first and last rows."""
     from scipy.integrate import quad
 
     nu = sigma.shape[0]
@@ -129,11 +132,16 @@ def _brute_force(sigma, u_min, du, nphi, ti, tj):
     sig = lambda i, j: sigma[i, j % nphi] if 0 <= i < nu else 0.0
     ri, pj = cen(ti), (tj + 0.5) * dphi
     Fr = Fp = 0.0
-    for ip in range(-1, nu + 1):
+    rows = range(-1, nu + 1) if edges == "ghost" else range(nu)
+    for ip in rows:
         lo, hi, rc = face(ip), face(ip + 1), cen(ip)
         for jp in range(nphi):
             s0 = sig(ip, jp)
-            sr = (sig(ip + 1, jp) - sig(ip - 1, jp)) / (cen(ip + 1) - cen(ip - 1))
+            if edges == "ghost":
+                sr = (sig(ip + 1, jp) - sig(ip - 1, jp)) / (cen(ip + 1) - cen(ip - 1))
+            else:
+                a, b = max(ip - 1, 0), min(ip + 1, nu - 1)
+                sr = (sig(b, jp) - sig(a, jp)) / (cen(b) - cen(a))
             sp = (sig(ip, jp + 1) - sig(ip, jp - 1)) / (2 * dphi) if 0 <= ip < nu else 0.0
             if s0 == 0.0 and sr == 0.0 and sp == 0.0:
                 continue
@@ -179,6 +187,24 @@ def test_brute_force_tiny_grid(oracle_mod):
     Fr, Fp = oracle_mod.direct_sum(sigma, Kr, Kp)
     for ti, tj in ((0, 0), (2, 3), (3, 5)):
         br, bp = _brute_force(sigma, u_min, du, nphi, ti, tj)
+        scale = abs(br) + abs(bp)
+        assert abs(Fr[ti, tj] - br) < 1e-8 * scale, (ti, tj, Fr[ti, tj], br)
+        assert abs(Fp[ti, tj] - bp) < 1e-8 * scale, (ti, tj, Fp[ti, tj], bp)
+
+
+@pytest.mark.slow
+def test_brute_force_tiny_grid_onesided_edges(oracle_mod):
+    """The one-sided edge slopes (no ghost rows) of onesided_forces against the
+    same brute force with those slopes, at edge and interior targets."""
+    nu, nphi = 4, 6
+    u_min, du = workloads.grid_params(nu, 0.5, 2.0)
+    grid = oracle_mod.Grid(nu, nphi, u_min, du)
+    cells, _, _ = _tables(oracle_mod, nu, nphi, du)
+    r, phi = workloads.centres(nu, nphi, u_min, du)
+    sigma = 1.0 + 0.3 * np.cos(phi)[None, :] + 0.2 * r[:, None]
+    Fr, Fp = oracle_mod.onesided_forces(sigma, cells, grid)
+    for ti, tj in ((0, 0), (1, 2), (3, 5)):
+        br, bp = _brute_force(sigma, u_min, du, nphi, ti, tj, edges="onesided")
         scale = abs(br) + abs(bp)
         assert abs(Fr[ti, tj] - br) < 1e-8 * scale, (ti, tj, Fr[ti, tj], br)
         assert abs(Fp[ti, tj] - bp) < 1e-8 * scale, (ti, tj, Fp[ti, tj], bp)
