@@ -39,7 +39,7 @@ BYTES_PER_CELL = {"rows": 8.0, "cols": 20.0, "inv_rows": 16.0}
 # DRAM bytes (read + write) of one column-pass launch at 2048 x 4096 FP32, from
 # one ncu capture (profiles/k_fwd_2048x4096_full.md), valid only for the
 # kernel sources it was taken on (sha256 prefix of fftconv.cu + sg_common.cuh).
-COLS_TRAFFIC = {"sources_sha256": "821e469683c97880", "bytes_per_launch": 100.807424e6 + 7.038208e6}
+COLS_TRAFFIC = {"sources_sha256": "a2fc56b65fa2ad0b", "bytes_per_launch": 100.805376e6 + 6.955264e6}
 
 
 def kernel_sources_sha() -> str:
@@ -353,6 +353,26 @@ def run_ours(args):
     rel_fp32_p2 = math.sqrt(num / den)
     del plan64, plan_p2, s64, f64r, f64p
 
+    # ---- build options: one-sided edge slopes (one more kernel per step) and
+    # the kernel variants (same passes; only the one-time build differs) ------
+    variants = {}
+    for name, kw in (("sim_ntpz19", {"n_tpz": 19}), ("particle", {"kind": "particle"}),
+                     ("particle_plus", {"kind": "particle+"}),
+                     ("softened", {"kind": "softened", "soften": 0.015 * 64 / NU}),
+                     ("radial_edges_onesided", {"radial_edges": 1})):
+        t0 = time.time()
+        pv = Plan(NU, NPHI, u_min, du, 1.0, "float32").build(**kw)
+        torch.cuda.synchronize()
+        entry = {"build_s": time.time() - t0}
+        if name == "radial_edges_onesided":
+            for _ in range(3):
+                pv.forces(sigma, Fr, Fp)
+            ems = timed(lambda: pv.forces(sigma, Fr, Fp), max(20, min(args.steps, 200)))
+            entry.update({"value": ws * cells / (ems * 1e-3), "unit": "cells/s", "ms_per_step": ems,
+                          "extra_ms_vs_default": ems - ms})
+        variants[name] = entry
+        del pv
+
     # ---- end to end through the C ABI with host buffers --------------------
     sig_h = torch.tensor(sigma_np, dtype=torch.float32).pin_memory()
     fr_h = torch.empty_like(sig_h).pin_memory()
@@ -395,6 +415,7 @@ def run_ours(args):
                      "fp32_speedup": fp64_ms / ms},
             "accuracy": {"fp32_vs_fp64_gpu_rel_l2": rel_fp32_vs_fp64, "fp32_weight_p2_vs_fp64_gpu_rel_l2": rel_fp32_p2},
             "build_s": build_s,
+            "build_options": variants,
             "batched": batch,
             "e2e": {"value": e2e_value, "unit": "cells/s", "ms_per_step": e2e_ms,
                     "h2d_bytes_per_step": cells * 4, "d2h_bytes_per_step": 2 * cells * 4},
