@@ -58,6 +58,27 @@ __device__ __forceinline__ V khat_p_s(const V* K, int kappa, int L, int nu)
     return V{-a.x, a.y};
 }
 
+// Khat_r and Khat_phi at the frequency k = t + e NT of a column transform
+// with E points per thread (L = E NT): the lower half of the e's lies below
+// N_u and the upper half at or above it (N_u itself only at t = 0,
+// e = E/2), so with e unrolled the mirror test costs nothing.
+template <int E, typename V>
+__device__ __forceinline__ void khat_at(const V* kr, const V* kp, int t, int e, int NT, V& a, V& b)
+{
+    if (e < E / 2) {
+        a = kr[t + e * NT];
+        b = kp[t + e * NT];
+        return;
+    }
+    const int j = (E - e) * NT - t;  // L - k
+    a = kr[j];
+    b = kp[j];
+    if (e > E / 2 || t != 0) {
+        a.y = -a.y;  // Khat_r(L - k) = conj Khat_r(k)
+        b.x = -b.x;  // Khat_phi(L - k) = -conj Khat_phi(k)
+    }
+}
+
 // shared-memory carve-up of the column kernels (16-byte aligned regions)
 __host__ __device__ __forceinline__ size_t sg_align16(size_t b) { return (b + 15) & ~(size_t)15; }
 
@@ -458,8 +479,9 @@ __global__ void SG_COLS_BOUNDS(T, NTB) k_fwd_cols(const typename CX<T>::t* __res
         } else {
 #pragma unroll
             for (int e = 0; e < E; e++) {
-                const int k = t + e * NT;
-                w[e] = c2(cmul(v[e], khat_r_s(kr_s, k, L, nu)), cmul(v[e], khat_p_s(kp_s, k, L, nu)));
+                V a, b;
+                khat_at<E>(kr_s, kp_s, t, e, NT, a, b);
+                w[e] = c2(cmul(v[e], a), cmul(v[e], b));
             }
         }
         // both inverse transforms; their first exchange waits for every spectrum read
@@ -1031,9 +1053,9 @@ __global__ void SG_COLS_BOUNDS(T, NTB) k_bwd_cols(const typename CX<T>::t* __res
         } else {
 #pragma unroll
             for (int e = 0; e < E; e++) {
-                const int k = t + e * NT;
-                y[e] = cadd(cmul(c2_lo(w[e]), cconj(khat_r_s(kr_s, k, L, nu))),
-                            cmul(c2_hi(w[e]), cconj(khat_p_s(kp_s, k, L, nu))));
+                V a, b;
+                khat_at<E>(kr_s, kp_s, t, e, NT, a, b);
+                y[e] = cadd(cmul(c2_lo(w[e]), cconj(a)), cmul(c2_hi(w[e]), cconj(b)));
             }
         }
         fft<E, +1>(y, sm, L, log2L, t, twd);  // waits for the mirror reads
