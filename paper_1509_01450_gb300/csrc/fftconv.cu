@@ -98,12 +98,14 @@ __device__ __forceinline__ Twd<E, V> make_twd(int log2N, int t, const V* __restr
     if constexpr (E == 16 && sizeof(V) == 8) w.h = sg_fft_twiddles(log2N, t, tab);
     return w;
 }
-template <int E, int DIR, typename V, typename Sync = SgSyncBlock>
+// LG > 0: the transform length 2^LG is fixed at compile time (FP32, 16
+// points per thread), see sg_fft
+template <int E, int DIR, int LG = 0, typename V, typename Sync = SgSyncBlock>
 __device__ __forceinline__ void fft(V (&v)[E], V* sm, int N, int log2N, int t, const Twd<E, V>& w,
                                     const Sync& sync = Sync())
 {
     if constexpr (E == 16 && sizeof(V) == 8)
-        sg_fft<E, DIR>(v, sm, N, log2N, t, w.h, sync);
+        sg_fft<E, DIR, LG>(v, sm, N, log2N, t, w.h, sync);
     else
         sg_fft<E, DIR>(v, sm, N, log2N, t, w.tab, sync);
 }
@@ -293,13 +295,17 @@ __host__ __device__ __forceinline__ size_t rows_fwd_smem_bytes(int N, int slots)
     return ((size_t)2 * slots * N + (size_t)slots * sg_padded(N)) * sizeof(V) + 128;
 }
 
-template <typename T, int E, int NTB>
+template <typename T, int E, int NTB, int LG = 0>
 __global__ void __launch_bounds__(NTB, (sizeof(T) == 4 && NTB == 256) ? 2 : 1) k_fwd_rows(const T* __restrict__ sigma, const T* __restrict__ wpre,
                                                   typename CX<T>::t* __restrict__ A, int nu, int nphi, int log2n,
                                                   const typename CX<T>::t* __restrict__ tw, int* err,
                                                   const __grid_constant__ CUtensorMap mapA, int use_map, int direct)
 {
     const unsigned long long wlim = sg_wait_budget(err);  // read once, early
+    if constexpr (LG > 0) {  // the length is a compile-time constant
+        nphi = 1 << LG;
+        log2n = LG;
+    }
     typedef typename CX<T>::t V;
     extern __shared__ __align__(128) unsigned char smraw[];
     __shared__ __align__(8) uint64_t bar;
@@ -349,7 +355,7 @@ __global__ void __launch_bounds__(NTB, (sizeof(T) == 4 && NTB == 256) ? 2 : 1) k
             sg_fence_proxy_async();
             issue(rb + gridDim.x);
         }
-        fft<E, -1>(v, sm, N, log2n, t, twd, ssync);
+        fft<E, -1, LG>(v, sm, N, log2n, t, twd, ssync);
         V x0[E / 2], x1[E / 2];
         split_real_pair<E, V, T>(v, sm, N, t, x0, x1, ssync);
         if (use_map && threadIdx.x < 32) sg_bulk_wait_read();  // the last tensor stores have read So
@@ -404,9 +410,13 @@ __host__ __device__ __forceinline__ size_t cols_smem_bytes(int nu)
 #define SG_COLS_MINB 2
 #endif
 #define SG_COLS_BOUNDS(T, NTB) __launch_bounds__(NTB, (sizeof(T) == 4 && NTB == 256) ? SG_COLS_MINB : 1)
+// the forward column pass with its length fixed at 4096: 80 registers fit
+// three blocks per SM (the shared memory of N_u = 2048 allows three)
+#define SG_FCOLS_BOUNDS(T, NTB, LG) \
+    __launch_bounds__(NTB, (sizeof(T) == 4 && NTB == 256) ? (LG == 12 ? 3 : SG_COLS_MINB) : 1)
 
-template <typename T, int E, int NTB>
-__global__ void SG_COLS_BOUNDS(T, NTB) k_fwd_cols(const typename CX<T>::t* __restrict__ A,
+template <typename T, int E, int NTB, int LG = 0>
+__global__ void SG_FCOLS_BOUNDS(T, NTB, LG) k_fwd_cols(const typename CX<T>::t* __restrict__ A,
                                                   const typename CX<T>::t* __restrict__ Kr,
                                                   const typename CX<T>::t* __restrict__ Kp,
                                                   typename CX<T>::t* __restrict__ Br,
@@ -414,6 +424,10 @@ __global__ void SG_COLS_BOUNDS(T, NTB) k_fwd_cols(const typename CX<T>::t* __res
                                                   const typename CX<T>::t* __restrict__ tw, int* err)
 {
     const unsigned long long wlim = sg_wait_budget(err);  // read once, early
+    if constexpr (LG > 0) {  // the length is a compile-time constant
+        nu = 1 << (LG - 1);
+        log2L = LG;
+    }
     typedef typename CX<T>::t V;
     extern __shared__ __align__(128) unsigned char smraw[];
     __shared__ __align__(8) uint64_t bar[2];  // [0]: the column, [1]: the spectra
@@ -456,7 +470,7 @@ __global__ void SG_COLS_BOUNDS(T, NTB) k_fwd_cols(const typename CX<T>::t* __res
 #pragma unroll
     for (int e = 0; e < E; e++) v[e] = (e < E / 2) ? sm[t + e * NT] : V{0, 0};  // rows >= nu: zero pad
     if constexpr (sizeof(T) == 4 && E == 16) {
-        fft<E, -1>(v, sm, L, log2L, t, twd);  // the spectra land meanwhile
+        fft<E, -1, LG>(v, sm, L, log2L, t, twd);  // the spectra land meanwhile
         if (__syncthreads_or(!sg_mbar_wait_bounded(&bar[1], 0, err, 1, wlim))) return;
         C2 w[E];  // (Y_r, Y_phi) of each frequency, paired
         if (m == 0) {
@@ -485,7 +499,7 @@ __global__ void SG_COLS_BOUNDS(T, NTB) k_fwd_cols(const typename CX<T>::t* __res
             }
         }
         // both inverse transforms; their first exchange waits for every spectrum read
-        sg_fft_pair<+1>(w, reinterpret_cast<C2*>(smraw), L, log2L, t, twd.h);
+        sg_fft_pair<+1, LG>(w, reinterpret_cast<C2*>(smraw), L, log2L, t, twd.h);
 #pragma unroll
         for (int e = 0; e < E / 2; e++) {  // crop to N_u rows
             sg_st_hint(Br + (size_t)m * nu + t + e * NT, c2_lo(w[e]), keep);
@@ -497,7 +511,7 @@ __global__ void SG_COLS_BOUNDS(T, NTB) k_fwd_cols(const typename CX<T>::t* __res
     // the two inverse ones as conj(FFT(conj Y)).
 #pragma unroll 1
     for (int pass = 0; pass < 3; pass++) {
-        fft<E, -1>(v, sm, L, log2L, t, twd);  // pass 0: the spectra land meanwhile
+        fft<E, -1, LG>(v, sm, L, log2L, t, twd);  // pass 0: the spectra land meanwhile
         if (pass == 0) {
             if (__syncthreads_or(!sg_mbar_wait_bounded(&bar[1], 0, err, 1, wlim))) return;
             if (m == 0) {
@@ -567,7 +581,7 @@ __host__ __device__ __forceinline__ size_t rows_inv_smem_bytes(int N, int slots)
     return stage + (size_t)slots * sg_padded(N) * sizeof(V) + 128;
 }
 
-template <typename T, int E, int NTB>
+template <typename T, int E, int NTB, int LG = 0>
 __global__ void __launch_bounds__(NTB, (sizeof(T) == 4 && NTB == 256) ? 2 : 1) k_fwd_rows_inv(const typename CX<T>::t* __restrict__ Br,
                                                       const typename CX<T>::t* __restrict__ Cp,
                                                       const T* __restrict__ wpost, T* __restrict__ Fr,
@@ -577,6 +591,10 @@ __global__ void __launch_bounds__(NTB, (sizeof(T) == 4 && NTB == 256) ? 2 : 1) k
                                                       const __grid_constant__ CUtensorMap mapC, int use_map)
 {
     const unsigned long long wlim = sg_wait_budget(err);  // read once, early
+    if constexpr (LG > 0) {  // the length is a compile-time constant
+        nphi = 1 << LG;
+        log2n = LG;
+    }
     typedef typename CX<T>::t V;
     extern __shared__ __align__(128) unsigned char smraw[];
     __shared__ __align__(8) uint64_t bar;
@@ -657,7 +675,7 @@ __global__ void __launch_bounds__(NTB, (sizeof(T) == 4 && NTB == 256) ? 2 : 1) k
                 }
             }
             __syncthreads();
-            sg_fft_pair<+1>(w, reinterpret_cast<C2*>(Sb) + (size_t)slot * sg_padded(N), N, log2n, t, twd.h, ssync);
+            sg_fft_pair<+1, LG>(w, reinterpret_cast<C2*>(Sb) + (size_t)slot * sg_padded(N), N, log2n, t, twd.h, ssync);
             __syncthreads();  // every slot is done with its area: the stage takes the next block's rows
             if (more && (!use_map || threadIdx.x < 32)) {
                 if (use_map) sg_fence_proxy_async();
@@ -711,7 +729,7 @@ __global__ void __launch_bounds__(NTB, (sizeof(T) == 4 && NTB == 256) ? 2 : 1) k
                     issue(rb + gridDim.x);
                 }
             }
-            fft<E, +1>(v, sm, N, log2n, t, twd, ssync);
+            fft<E, +1, LG>(v, sm, N, log2n, t, twd, ssync);
             const int i = rb * R + r;
             if (i < nu) {
                 const T w = wpost[i];
@@ -868,7 +886,7 @@ __global__ void __launch_bounds__(256) k_edge_bwd(const typename CX<T>::t* __res
 // the half spectra of gF_r (-> A) and gF_phi (-> C), staged and stored
 // mode-major.  R = slots rows per row block, arriving as two bulk copies.
 // ===========================================================================
-template <typename T, int E>
+template <typename T, int E, int LG = 0>
 __global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 512) k_bwd_rows(const T* __restrict__ gr, const T* __restrict__ gp,
                                                   const T* __restrict__ wpost, typename CX<T>::t* __restrict__ A,
                                                   typename CX<T>::t* __restrict__ C, int nu, int nphi, int log2n,
@@ -877,6 +895,10 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 512) k_bwd_rows(const T
                                                   const __grid_constant__ CUtensorMap mapC, int use_map)
 {
     const unsigned long long wlim = sg_wait_budget(err);  // read once, early
+    if constexpr (LG > 0) {  // the length is a compile-time constant
+        nphi = 1 << LG;
+        log2n = LG;
+    }
     typedef typename CX<T>::t V;
     extern __shared__ __align__(128) unsigned char smraw[];
     __shared__ __align__(8) uint64_t bar[SG_RING];
@@ -935,7 +957,7 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 512) k_bwd_rows(const T
         }
         V* sm = cur + slot * sg_padded(N);
         __syncthreads();  // the rows overlap other slots' exchange areas: all read before any slot transforms
-        fft<E, -1>(v, sm, N, log2n, t, twd, ssync);
+        fft<E, -1, LG>(v, sm, N, log2n, t, twd, ssync);
         V x0[E / 2], x1[E / 2];
         split_real_pair<E, V, T>(v, sm, N, t, x0, x1, ssync);
         __syncthreads();  // the stages span every slot's area
@@ -982,7 +1004,7 @@ __host__ __device__ __forceinline__ size_t bcols_smem_bytes(int nu)
     return sg_align16(sg_padded(L) * sizeof(V)) + (size_t)nu * sizeof(V) + 2 * (size_t)KS * sizeof(V);
 }
 
-template <typename T, int E, int NTB>
+template <typename T, int E, int NTB, int LG = 0>
 __global__ void SG_COLS_BOUNDS(T, NTB) k_bwd_cols(const typename CX<T>::t* __restrict__ A,
                                                   const typename CX<T>::t* __restrict__ C,
                                                   const typename CX<T>::t* __restrict__ Kr,
@@ -991,6 +1013,10 @@ __global__ void SG_COLS_BOUNDS(T, NTB) k_bwd_cols(const typename CX<T>::t* __res
                                                   const typename CX<T>::t* __restrict__ tw, int* err)
 {
     const unsigned long long wlim = sg_wait_budget(err);  // read once, early
+    if constexpr (LG > 0) {  // the length is a compile-time constant
+        nu = 1 << (LG - 1);
+        log2L = LG;
+    }
     typedef typename CX<T>::t V;
     extern __shared__ __align__(128) unsigned char smraw[];
     __shared__ __align__(8) uint64_t bar[2];  // [0]: the A column, [1]: the C column and the spectra
@@ -1033,7 +1059,7 @@ __global__ void SG_COLS_BOUNDS(T, NTB) k_bwd_cols(const typename CX<T>::t* __res
 #pragma unroll
         for (int e = 0; e < E; e++)
             w[e] = (e < E / 2) ? c2(sm[t + e * NT], cs[t + e * NT]) : c2(V{0, 0}, V{0, 0});
-        sg_fft_pair<-1>(w, reinterpret_cast<C2*>(smraw), L, log2L, t, twd.h);  // waits for the landing reads
+        sg_fft_pair<-1, LG>(w, reinterpret_cast<C2*>(smraw), L, log2L, t, twd.h);  // waits for the landing reads
         V y[E];
         if (m == 0) {
             // X_a is the FFT of (DC + i Nyquist); the phi kernel vanishes at
@@ -1058,7 +1084,7 @@ __global__ void SG_COLS_BOUNDS(T, NTB) k_bwd_cols(const typename CX<T>::t* __res
                 y[e] = cadd(cmul(c2_lo(w[e]), cconj(a)), cmul(c2_hi(w[e]), cconj(b)));
             }
         }
-        fft<E, +1>(y, sm, L, log2L, t, twd);  // waits for the mirror reads
+        fft<E, +1, LG>(y, sm, L, log2L, t, twd);  // waits for the mirror reads
 #pragma unroll
         for (int e = 0; e < E / 2; e++) sg_st_hint(B + (size_t)m * nu + t + e * NT, y[e], keep);
         return;
@@ -1074,7 +1100,7 @@ __global__ void SG_COLS_BOUNDS(T, NTB) k_bwd_cols(const typename CX<T>::t* __res
     V* st = cs;
 #pragma unroll 1
     for (int pass = 0; pass < 3; pass++) {
-        fft<E, -1>(v, sm, L, log2L, t, twd);
+        fft<E, -1, LG>(v, sm, L, log2L, t, twd);
         if (pass == 0) {
             if (__syncthreads_or(!sg_mbar_wait_bounded(&bar[1], 0, err, 1, wlim))) return;
             if (m == 0) {
@@ -1135,13 +1161,17 @@ __host__ __device__ __forceinline__ size_t rows_bwd_inv_smem_bytes(int N, int sl
     return ((size_t)slots * N + (size_t)slots * sg_padded(N)) * sizeof(V) + 128;
 }
 
-template <typename T, int E, int NTB>
+template <typename T, int E, int NTB, int LG = 0>
 __global__ void __launch_bounds__(NTB, (sizeof(T) == 4 && NTB == 256) ? 2 : 1) k_bwd_rows_inv(const typename CX<T>::t* __restrict__ B,
                                                       const T* __restrict__ wpre, T* __restrict__ gs, int nu,
                                                       int nphi, int log2n, const typename CX<T>::t* __restrict__ tw,
                                                       int* err, const __grid_constant__ CUtensorMap mapB, int use_map)
 {
     const unsigned long long wlim = sg_wait_budget(err);  // read once, early
+    if constexpr (LG > 0) {  // the length is a compile-time constant
+        nphi = 1 << LG;
+        log2n = LG;
+    }
     typedef typename CX<T>::t V;
     extern __shared__ __align__(128) unsigned char smraw[];
     __shared__ __align__(8) uint64_t bar;
@@ -1209,7 +1239,7 @@ __global__ void __launch_bounds__(NTB, (sizeof(T) == 4 && NTB == 256) ? 2 : 1) k
             if (use_map) sg_fence_proxy_async();
             issue(rb + gridDim.x);
         }
-        fft<E, +1>(v, sm, N, log2n, t, twd, ssync);
+        fft<E, +1, LG>(v, sm, N, log2n, t, twd, ssync);
         const int pair = rb * slots + slot;
         if (pair < nu / 2) {
             const int i0 = 2 * pair;
@@ -1531,6 +1561,8 @@ cudaError_t launch_forward(const PlanView& p, const T* sigma, T* Fr, T* Fp, cuda
             auto k = k_fwd_rows<T, EE, 256>;
             if constexpr (sizeof(T) == 4)  // FP64 blocks are at most 256 threads
                 if (s.threads > 256) k = k_fwd_rows<T, EE, 512>;
+            if constexpr (sizeof(T) == 4 && EE == 16)  // the 4096-point rows, length fixed at compile time
+                if (p.nphi == 4096 && s.threads == 256) k = k_fwd_rows<T, 16, 256, 12>;
             if ((err = set_smem(k, smem, true)) != cudaSuccess) return err;
             if ((err = launch_pdl(k, persistent_grid(k, s.threads, smem, nblk, p.sms), s.threads, smem, st, 
                 sigma, (const T*)p.wpre, A, p.nu, p.nphi, ln, tw, p.err, mA ? *mA : CUtensorMap{}, mA != nullptr,
@@ -1546,6 +1578,8 @@ cudaError_t launch_forward(const PlanView& p, const T* sigma, T* Fr, T* Fp, cuda
             auto k = k_fwd_cols<T, EE, 256>;
             if constexpr (sizeof(T) == 4)  // FP64 columns are at most 256 threads
                 if (L / EE > 256) k = k_fwd_cols<T, EE, 512>;
+            if constexpr (sizeof(T) == 4 && EE == 16)
+                if (L == 4096) k = k_fwd_cols<T, 16, 256, 12>;
             if ((err = set_smem(k, smem, true)) != cudaSuccess) return err;
             if ((err = launch_pdl(k, p.nphi / 2, L / EE, smem, st, A, (const V*)p.kr, (const V*)p.kp, B, C, p.nu, p.nphi, lL, tw, p.err)) != cudaSuccess) return err;
         });
@@ -1564,6 +1598,8 @@ cudaError_t launch_forward(const PlanView& p, const T* sigma, T* Fr, T* Fp, cuda
             auto k = k_fwd_rows_inv<T, EE, 256>;
             if constexpr (sizeof(T) == 4)  // FP64 blocks are at most 256 threads
                 if (s.threads > 256) k = k_fwd_rows_inv<T, EE, 512>;
+            if constexpr (sizeof(T) == 4 && EE == 16)
+                if (p.nphi == 4096 && s.threads == 256) k = k_fwd_rows_inv<T, 16, 256, 12>;
             if ((err = set_smem(k, smem, true)) != cudaSuccess) return err;
             if ((err = launch_pdl(k, persistent_grid(k, s.threads, smem, nblk, p.sms), s.threads, smem, st, 
                 B, C, (const T*)p.wpost, Fr, Fp, p.nu, p.nphi, ln, tw, p.err, um ? *mB : CUtensorMap{},
@@ -1594,6 +1630,8 @@ cudaError_t launch_backward(const PlanView& p, const T* gr, const T* gp, T* gs, 
         const bool um = mA && mC;
         SG_DISPATCH_E(s.E, {
             auto k = k_bwd_rows<T, EE>;
+            if constexpr (sizeof(T) == 4 && EE == 16)
+                if (p.nphi == 4096 && s.threads == 512) k = k_bwd_rows<T, 16, 12>;
             if ((err = set_smem(k, smem, true)) != cudaSuccess) return err;
             if ((err = launch_pdl(k, persistent_grid(k, s.threads, smem, nblk, p.sms), s.threads, smem, st, 
                 gr, gp, (const T*)p.wpost, A, C, p.nu, p.nphi, ln, tw, p.err, um ? *mA : CUtensorMap{},
@@ -1608,6 +1646,8 @@ cudaError_t launch_backward(const PlanView& p, const T* gr, const T* gp, T* gs, 
             auto k = k_bwd_cols<T, EE, 256>;
             if constexpr (sizeof(T) == 4)  // FP64 columns are at most 256 threads
                 if (L / EE > 256) k = k_bwd_cols<T, EE, 512>;
+            if constexpr (sizeof(T) == 4 && EE == 16)
+                if (L == 4096) k = k_bwd_cols<T, 16, 256, 12>;
             if ((err = set_smem(k, smem, true)) != cudaSuccess) return err;
             if ((err = launch_pdl(k, p.nphi / 2, L / EE, smem, st, A, C, (const V*)p.kr, (const V*)p.kp, B, p.nu, p.nphi, lL, tw, p.err)) != cudaSuccess) return err;
         });
@@ -1623,6 +1663,8 @@ cudaError_t launch_backward(const PlanView& p, const T* gr, const T* gp, T* gs, 
             auto k = k_bwd_rows_inv<T, EE, 256>;
             if constexpr (sizeof(T) == 4)
                 if (s.threads > 256) k = k_bwd_rows_inv<T, EE, 512>;
+            if constexpr (sizeof(T) == 4 && EE == 16)
+                if (p.nphi == 4096 && s.threads == 256) k = k_bwd_rows_inv<T, 16, 256, 12>;
             if ((err = set_smem(k, smem, true)) != cudaSuccess) return err;
             if ((err = launch_pdl(k, persistent_grid(k, s.threads, smem, nblk, p.sms), s.threads, smem, st, 
                 B, (const T*)p.wpre, gs, p.nu, p.nphi, ln, tw, p.err, mB ? *mB : CUtensorMap{}, mB != nullptr)) != cudaSuccess) return err;

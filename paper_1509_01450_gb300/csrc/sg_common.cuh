@@ -600,11 +600,14 @@ __device__ __forceinline__ void sg_pass16_tw(V (&v)[16], V w)
     sg_dft<16, DIR>(v);
 }
 
-template <int E, int DIR, typename V, typename Sync = SgSyncBlock>
-__device__ __forceinline__ void sg_fft(V (&v)[E], V* sm, int N, int log2N, int t, const SgTwid<V>& tws,
+template <int E, int DIR, int LG = 0, typename V, typename Sync = SgSyncBlock>
+__device__ __forceinline__ void sg_fft(V (&v)[E], V* sm, int N_, int log2N_, int t, const SgTwid<V>& tws,
                                        const Sync& sync = Sync())
 {
     static_assert(E == 16, "register twiddles need 16 elements per thread");
+    // LG > 0: the length 2^LG is a compile-time constant, so every exchange
+    // index and stride folds into immediates and the passes unroll
+    const int N = LG > 0 ? (1 << LG) : N_, log2N = LG > 0 ? LG : log2N_;
     const int NT = N / E;
     const int rem = log2N & 3;
     const int n16 = (log2N >> 2) - (rem == 0 ? 1 : 0);
@@ -627,19 +630,22 @@ __device__ __forceinline__ void sg_fft(V (&v)[E], V* sm, int N, int log2N, int t
         sg_pass_store<8, E>(v, sm, t, NT, 1);
     else
         sg_pass_store<16, E>(v, sm, t, NT, 1);
-    int Ns = rem == 0 ? 16 : (1 << rem);
-    // the radix-16 passes share one copy of their code (a small instruction
-    // footprint matters more here than the loop overhead)
-#pragma unroll 1
-    for (int p = 0; p < n16; p++) {
-        if (p > 0) {
-            sg_pass_store<16, E>(v, sm, t, NT, Ns);
-            Ns *= 16;
-        }
+    auto pass = [&](int p) {
+        const int Ns = p > 0 ? (rem == 0 ? 16 : (1 << rem)) << (4 * (p - 1)) : 1;  // stride of pass p's stores
+        if (p > 0) sg_pass_store<16, E>(v, sm, t, NT, Ns);
         sync();
         sg_pass_load<16, E>(v, sm, t, NT, N);
         sync();
         sg_pass16_tw<DIR>(v, p == 0 ? tws.w[0] : (p == 1 ? tws.w[1] : tws.w[2]));
+    };
+    if constexpr (LG > 0) {
+#pragma unroll
+        for (int p = 0; p < n16; p++) pass(p);
+    } else {
+        // the radix-16 passes share one copy of their code (a small
+        // instruction footprint matters more here than the loop overhead)
+#pragma unroll 1
+        for (int p = 0; p < n16; p++) pass(p);
     }
 }
 
@@ -786,11 +792,12 @@ __device__ __forceinline__ void sg_dft8(C2* a)
 // Two transforms of length N (E = 16 points per thread each), twiddles from
 // the registers of sg_fft_twiddles (the same for both).  Same exchange
 // pattern as sg_fft; sm holds sg_padded(N) C2 elements (16 bytes each).
-template <int DIR, typename Sync = SgSyncBlock>
-__device__ __forceinline__ void sg_fft_pair(C2 (&v)[16], C2* sm, int N, int log2N, int t, const SgTwid<float2>& tws,
-                                            const Sync& sync = Sync())
+template <int DIR, int LG = 0, typename Sync = SgSyncBlock>
+__device__ __forceinline__ void sg_fft_pair(C2 (&v)[16], C2* sm, int N_, int log2N_, int t,
+                                            const SgTwid<float2>& tws, const Sync& sync = Sync())
 {
     constexpr int E = 16;
+    const int N = LG > 0 ? (1 << LG) : N_, log2N = LG > 0 ? LG : log2N_;  // as in sg_fft
     const int NT = N / E;
     const int rem = log2N & 3;
     const int n16 = (log2N >> 2) - (rem == 0 ? 1 : 0);
@@ -824,13 +831,9 @@ __device__ __forceinline__ void sg_fft_pair(C2 (&v)[16], C2* sm, int N, int log2
         sg_pass_store<8, E>(v, sm, t, NT, 1);
     else
         sg_pass_store<16, E>(v, sm, t, NT, 1);
-    int Ns = rem == 0 ? 16 : (1 << rem);
-#pragma unroll 1
-    for (int p = 0; p < n16; p++) {
-        if (p > 0) {
-            sg_pass_store<16, E>(v, sm, t, NT, Ns);
-            Ns *= 16;
-        }
+    auto pass = [&](int p) {
+        const int Ns = p > 0 ? (rem == 0 ? 16 : (1 << rem)) << (4 * (p - 1)) : 1;
+        if (p > 0) sg_pass_store<16, E>(v, sm, t, NT, Ns);
         sync();
         sg_pass_load<16, E>(v, sm, t, NT, N);
         sync();
@@ -838,6 +841,13 @@ __device__ __forceinline__ void sg_fft_pair(C2 (&v)[16], C2* sm, int N, int log2
         if (DIR > 0) w.y = -w.y;
         sg_twiddle_powers<16>(v, c2_bcast(w));
         sg_dft<16, DIR>(v);
+    };
+    if constexpr (LG > 0) {
+#pragma unroll
+        for (int p = 0; p < n16; p++) pass(p);
+    } else {
+#pragma unroll 1
+        for (int p = 0; p < n16; p++) pass(p);
     }
 }
 

@@ -198,3 +198,25 @@ def test_spiral_clump_512x1024(torch_cuda, oracle_mod, dtype, tol):
     t = np.random.default_rng(0).choice(cfg.nu * cfg.nphi, 64, replace=False)
     dr, dp = oracle_mod.direct_sum(sigma, Kr, Kp, targets=t)
     assert oracle_mod.rel_l2(Fr.ravel()[t], Fp.ravel()[t], dr, dp) < tol
+
+
+@pytest.mark.parametrize("nu,nphi,r_in,r_out", [(4, 4096, 0.5, 2.0), (8, 4096, 0.5, 2.0), (2048, 16, 0.01, 100.0),
+                                                 (2048, 64, 0.01, 100.0)])
+def test_fixed_length_passes(torch_cuda, oracle_mod, nu, nphi, r_in, r_out):
+    """FP32 transforms of 4096 points run passes whose length is fixed at
+    compile time: 4096-point rows with few (and, at N_u = 4, fewer than one
+    per block) row blocks, and 4096-point columns with few modes, against
+    the oracle, forward and adjoint."""
+    torch = torch_cuda
+    plan, u_min, du = make_plan(nu, nphi, r_in, r_out, "float32")
+    Kr, Kp = oracle_mod.kernels(nu, nphi, du)
+    sigma = np.abs(workloads.random_field(nu, nphi, nu + nphi)) + 0.1
+    Fr_ref, Fp_ref = oracle_mod.fft_conv(sigma, Kr, Kp)
+    Fr, Fp = _forward(torch, plan, sigma)
+    plan.check()
+    assert oracle_mod.rel_l2(Fr, Fp, Fr_ref, Fp_ref) < FP32_TOL
+    gr, gp = workloads.random_field(nu, nphi, 5), workloads.random_field(nu, nphi, 6)
+    ref = oracle_mod.fft_conv_T(gr, gp, Kr, Kp)
+    gs = plan.backward(torch.tensor(gr, dtype=torch.float32, device="cuda"),
+                       torch.tensor(gp, dtype=torch.float32, device="cuda"))
+    assert np.linalg.norm(gs.double().cpu().numpy() - ref) / np.linalg.norm(ref) < FP32_TOL
