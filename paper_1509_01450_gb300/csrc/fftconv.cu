@@ -1336,6 +1336,51 @@ __global__ void __launch_bounds__(512) k_spec_cols(const double2* __restrict__ W
 }
 
 // ===========================================================================
+// FP32 pass kernels whose transform length 2^LG is fixed at compile time.
+// Each length's instances are compiled in a translation unit of their own
+// (fftconv_lg<LG>.cu, which includes this file for its kernels only) and
+// reached through fixed_pass_kernels(); other lengths and FP64 take the
+// run-time instances.  Block sizes are those of the run-time launches: 256
+// threads up to 4096 points, one 512-thread transform beyond.
+// ===========================================================================
+struct FixedPassKernels {
+    decltype(&k_fwd_rows<float, 16, 256, 0>) fwd_rows;
+    decltype(&k_fwd_cols<float, 16, 256, 0>) fwd_cols;
+    decltype(&k_fwd_rows_inv<float, 16, 256, 0>) fwd_rows_inv;
+    decltype(&k_bwd_rows<float, 16, 0>) bwd_rows;
+    decltype(&k_bwd_cols<float, 16, 256, 0>) bwd_cols;
+    decltype(&k_bwd_rows_inv<float, 16, 256, 0>) bwd_rows_inv;
+    int threads;  // block size of the row and column instances
+};
+
+template <int LG>
+FixedPassKernels make_fixed_pass_kernels()
+{
+    constexpr int NB = (1 << LG) / 16 > 256 ? 512 : 256;
+    return FixedPassKernels{k_fwd_rows<float, 16, NB, LG>,  k_fwd_cols<float, 16, NB, LG>,
+                            k_fwd_rows_inv<float, 16, NB, LG>, k_bwd_rows<float, 16, LG>,
+                            k_bwd_cols<float, 16, NB, LG>,  k_bwd_rows_inv<float, 16, NB, LG>, NB};
+}
+
+// defined in fftconv_lg<LG>.cu
+FixedPassKernels fixed_pass_kernels_lg8();
+FixedPassKernels fixed_pass_kernels_lg9();
+FixedPassKernels fixed_pass_kernels_lg10();
+FixedPassKernels fixed_pass_kernels_lg11();
+FixedPassKernels fixed_pass_kernels_lg12();
+FixedPassKernels fixed_pass_kernels_lg13();
+
+#ifndef SG_FFTCONV_KERNELS_ONLY
+// the instances for transforms of 2^lg points, or null
+static const FixedPassKernels* fixed_pass_kernels(int lg)
+{
+    static const FixedPassKernels table[6] = {fixed_pass_kernels_lg8(),  fixed_pass_kernels_lg9(),
+                                              fixed_pass_kernels_lg10(), fixed_pass_kernels_lg11(),
+                                              fixed_pass_kernels_lg12(), fixed_pass_kernels_lg13()};
+    return lg >= 8 && lg <= 13 ? &table[lg - 8] : nullptr;
+}
+
+// ===========================================================================
 // Host launchers
 // ===========================================================================
 struct Shape {
@@ -1561,8 +1606,9 @@ cudaError_t launch_forward(const PlanView& p, const T* sigma, T* Fr, T* Fp, cuda
             auto k = k_fwd_rows<T, EE, 256>;
             if constexpr (sizeof(T) == 4)  // FP64 blocks are at most 256 threads
                 if (s.threads > 256) k = k_fwd_rows<T, EE, 512>;
-            if constexpr (sizeof(T) == 4 && EE == 16)  // the 4096-point rows, length fixed at compile time
-                if (p.nphi == 4096 && s.threads == 256) k = k_fwd_rows<T, 16, 256, 12>;
+            if constexpr (sizeof(T) == 4 && EE == 16)  // length fixed at compile time
+                if (const FixedPassKernels* f = fixed_pass_kernels(ln))
+                    if (s.threads == f->threads) k = f->fwd_rows;
             if ((err = set_smem(k, smem, true)) != cudaSuccess) return err;
             if ((err = launch_pdl(k, persistent_grid(k, s.threads, smem, nblk, p.sms), s.threads, smem, st, 
                 sigma, (const T*)p.wpre, A, p.nu, p.nphi, ln, tw, p.err, mA ? *mA : CUtensorMap{}, mA != nullptr,
@@ -1579,7 +1625,8 @@ cudaError_t launch_forward(const PlanView& p, const T* sigma, T* Fr, T* Fp, cuda
             if constexpr (sizeof(T) == 4)  // FP64 columns are at most 256 threads
                 if (L / EE > 256) k = k_fwd_cols<T, EE, 512>;
             if constexpr (sizeof(T) == 4 && EE == 16)
-                if (L == 4096) k = k_fwd_cols<T, 16, 256, 12>;
+                if (const FixedPassKernels* f = fixed_pass_kernels(lL))
+                    if (L / EE <= f->threads) k = f->fwd_cols;
             if ((err = set_smem(k, smem, true)) != cudaSuccess) return err;
             if ((err = launch_pdl(k, p.nphi / 2, L / EE, smem, st, A, (const V*)p.kr, (const V*)p.kp, B, C, p.nu, p.nphi, lL, tw, p.err)) != cudaSuccess) return err;
         });
@@ -1599,7 +1646,8 @@ cudaError_t launch_forward(const PlanView& p, const T* sigma, T* Fr, T* Fp, cuda
             if constexpr (sizeof(T) == 4)  // FP64 blocks are at most 256 threads
                 if (s.threads > 256) k = k_fwd_rows_inv<T, EE, 512>;
             if constexpr (sizeof(T) == 4 && EE == 16)
-                if (p.nphi == 4096 && s.threads == 256) k = k_fwd_rows_inv<T, 16, 256, 12>;
+                if (const FixedPassKernels* f = fixed_pass_kernels(ln))
+                    if (s.threads == f->threads) k = f->fwd_rows_inv;
             if ((err = set_smem(k, smem, true)) != cudaSuccess) return err;
             if ((err = launch_pdl(k, persistent_grid(k, s.threads, smem, nblk, p.sms), s.threads, smem, st, 
                 B, C, (const T*)p.wpost, Fr, Fp, p.nu, p.nphi, ln, tw, p.err, um ? *mB : CUtensorMap{},
@@ -1631,7 +1679,8 @@ cudaError_t launch_backward(const PlanView& p, const T* gr, const T* gp, T* gs, 
         SG_DISPATCH_E(s.E, {
             auto k = k_bwd_rows<T, EE>;
             if constexpr (sizeof(T) == 4 && EE == 16)
-                if (p.nphi == 4096 && s.threads == 512) k = k_bwd_rows<T, 16, 12>;
+                if (const FixedPassKernels* f = fixed_pass_kernels(ln))
+                    if (s.threads == 512) k = f->bwd_rows;
             if ((err = set_smem(k, smem, true)) != cudaSuccess) return err;
             if ((err = launch_pdl(k, persistent_grid(k, s.threads, smem, nblk, p.sms), s.threads, smem, st, 
                 gr, gp, (const T*)p.wpost, A, C, p.nu, p.nphi, ln, tw, p.err, um ? *mA : CUtensorMap{},
@@ -1647,7 +1696,8 @@ cudaError_t launch_backward(const PlanView& p, const T* gr, const T* gp, T* gs, 
             if constexpr (sizeof(T) == 4)  // FP64 columns are at most 256 threads
                 if (L / EE > 256) k = k_bwd_cols<T, EE, 512>;
             if constexpr (sizeof(T) == 4 && EE == 16)
-                if (L == 4096) k = k_bwd_cols<T, 16, 256, 12>;
+                if (const FixedPassKernels* f = fixed_pass_kernels(lL))
+                    if (L / EE <= f->threads) k = f->bwd_cols;
             if ((err = set_smem(k, smem, true)) != cudaSuccess) return err;
             if ((err = launch_pdl(k, p.nphi / 2, L / EE, smem, st, A, C, (const V*)p.kr, (const V*)p.kp, B, p.nu, p.nphi, lL, tw, p.err)) != cudaSuccess) return err;
         });
@@ -1664,7 +1714,8 @@ cudaError_t launch_backward(const PlanView& p, const T* gr, const T* gp, T* gs, 
             if constexpr (sizeof(T) == 4)
                 if (s.threads > 256) k = k_bwd_rows_inv<T, EE, 512>;
             if constexpr (sizeof(T) == 4 && EE == 16)
-                if (p.nphi == 4096 && s.threads == 256) k = k_bwd_rows_inv<T, 16, 256, 12>;
+                if (const FixedPassKernels* f = fixed_pass_kernels(ln))
+                    if (s.threads == f->threads) k = f->bwd_rows_inv;
             if ((err = set_smem(k, smem, true)) != cudaSuccess) return err;
             if ((err = launch_pdl(k, persistent_grid(k, s.threads, smem, nblk, p.sms), s.threads, smem, st, 
                 B, (const T*)p.wpre, gs, p.nu, p.nphi, ln, tw, p.err, mB ? *mB : CUtensorMap{}, mB != nullptr)) != cudaSuccess) return err;
@@ -1712,5 +1763,6 @@ template cudaError_t launch_spectra<float2>(const PlanView&, const double*, cons
                                             float2*, cudaStream_t);
 template cudaError_t launch_spectra<double2>(const PlanView&, const double*, const double*, double2*, double2*,
                                              double2*, cudaStream_t);
+#endif  // SG_FFTCONV_KERNELS_ONLY
 
 }  // namespace sg

@@ -1,0 +1,8 @@
+// fftconv_lg10.cu -- the FP32 pass kernels for transforms of 1024 points with
+// the length fixed at compile time (see FixedPassKernels in fftconv.cu).
+#define SG_FFTCONV_KERNELS_ONLY
+#include "fftconv.cu"
+
+namespace sg {
+FixedPassKernels fixed_pass_kernels_lg10() { return make_fixed_pass_kernels<10>(); }
+}  // namespace sg

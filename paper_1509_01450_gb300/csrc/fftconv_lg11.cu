@@ -1,0 +1,8 @@
+// fftconv_lg11.cu -- the FP32 pass kernels for transforms of 2048 points with
+// the length fixed at compile time (see FixedPassKernels in fftconv.cu).
+#define SG_FFTCONV_KERNELS_ONLY
+#include "fftconv.cu"
+
+namespace sg {
+FixedPassKernels fixed_pass_kernels_lg11() { return make_fixed_pass_kernels<11>(); }
+}  // namespace sg

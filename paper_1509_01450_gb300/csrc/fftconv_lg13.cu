@@ -1,0 +1,8 @@
+// fftconv_lg13.cu -- the FP32 pass kernels for transforms of 8192 points with
+// the length fixed at compile time (see FixedPassKernels in fftconv.cu).
+#define SG_FFTCONV_KERNELS_ONLY
+#include "fftconv.cu"
+
+namespace sg {
+FixedPassKernels fixed_pass_kernels_lg13() { return make_fixed_pass_kernels<13>(); }
+}  // namespace sg

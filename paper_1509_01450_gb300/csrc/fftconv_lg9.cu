@@ -1,0 +1,8 @@
+// fftconv_lg9.cu -- the FP32 pass kernels for transforms of 512 points with
+// the length fixed at compile time (see FixedPassKernels in fftconv.cu).
+#define SG_FFTCONV_KERNELS_ONLY
+#include "fftconv.cu"
+
+namespace sg {
+FixedPassKernels fixed_pass_kernels_lg9() { return make_fixed_pass_kernels<9>(); }
+}  // namespace sg
