@@ -354,7 +354,7 @@ sg_status sg_kernels_build(sg_plan* p, const sg_build_opts* opts, cudaStream_t s
         const int brow[4] = {0, 1, nu - 2, nu - 1};
         for (int a = 0; a < 4; a++)
             for (int b = 0; b < 4; b++) p->ecoef[4 * a + b] = c[4 * a + b] * exp(-wp * (brow[b] - nu / 2) * p->du);
-        const size_t n = (size_t)(nphi / 2 + 1) * (2 * nu + 1) * p->elem;
+        const size_t n = (size_t)(nphi / 2 + 1) * sg_edge_stride(nu, (int)p->elem) * p->elem;
         sg_status st = SG_OK;
         if ((!p->egr && (st = dev_alloc(p, &p->egr, n))) || (!p->egp && (st = dev_alloc(p, &p->egp, n)))) return st;
     }

@@ -79,6 +79,14 @@ __device__ __forceinline__ void khat_at(const V* kr, const V* kp, int t, int e, 
     }
 }
 
+// coefficients of the one-sided edge-slope update: [a][b], the slope change
+// of source row a in {-1, 0, N_u-1, N_u} per weighted sigma of row b in
+// {0, 1, N_u-2, N_u-1}
+template <typename T>
+struct EdgeCoef {
+    T c[16];
+};
+
 // shared-memory carve-up of the column kernels (16-byte aligned regions)
 __host__ __device__ __forceinline__ size_t sg_align16(size_t b) { return (b + 15) & ~(size_t)15; }
 
@@ -412,16 +420,24 @@ __host__ __device__ __forceinline__ size_t cols_smem_bytes(int nu)
 #define SG_COLS_BOUNDS(T, NTB) __launch_bounds__(NTB, (sizeof(T) == 4 && NTB == 256) ? SG_COLS_MINB : 1)
 // the forward column pass with its length fixed at 4096: 80 registers fit
 // three blocks per SM (the shared memory of N_u = 2048 allows three)
-#define SG_FCOLS_BOUNDS(T, NTB, LG) \
-    __launch_bounds__(NTB, (sizeof(T) == 4 && NTB == 256) ? (LG == 12 ? 3 : SG_COLS_MINB) : 1)
+#define SG_FCOLS_BOUNDS(T, NTB, LG, EDGE) \
+    __launch_bounds__(NTB, (sizeof(T) == 4 && NTB == 256) ? ((LG == 12 && !EDGE) ? 3 : SG_COLS_MINB) : 1)
 
-template <typename T, int E, int NTB, int LG = 0>
-__global__ void SG_FCOLS_BOUNDS(T, NTB, LG) k_fwd_cols(const typename CX<T>::t* __restrict__ A,
+// EDGE (FP32, 16 points per thread): the one-sided edge-slope update of
+// k_edge_fwd is applied here, before the stores: the mode's two rows of the
+// edge tables (gr and gp; for mode 0 gr of modes 0 and N_phi/2) arrive with
+// the spectra into an area after the exchange area, and s^_a comes from the
+// four edge rows of the landed column.  egr, egp, wpre and ecoef are unused
+// otherwise.
+template <typename T, int E, int NTB, int LG = 0, bool EDGE = false>
+__global__ void SG_FCOLS_BOUNDS(T, NTB, LG, EDGE) k_fwd_cols(const typename CX<T>::t* __restrict__ A,
                                                   const typename CX<T>::t* __restrict__ Kr,
                                                   const typename CX<T>::t* __restrict__ Kp,
                                                   typename CX<T>::t* __restrict__ Br,
                                                   typename CX<T>::t* __restrict__ Cp, int nu, int nphi, int log2L,
-                                                  const typename CX<T>::t* __restrict__ tw, int* err)
+                                                  const typename CX<T>::t* __restrict__ tw, int* err,
+                                                  const T* __restrict__ egr, const T* __restrict__ egp,
+                                                  const T* __restrict__ wpre, EdgeCoef<T> ecoef)
 {
     const unsigned long long wlim = sg_wait_budget(err);  // read once, early
     if constexpr (LG > 0) {  // the length is a compile-time constant
@@ -445,13 +461,20 @@ __global__ void SG_FCOLS_BOUNDS(T, NTB, LG) k_fwd_cols(const typename CX<T>::t* 
     __syncthreads();
     const uint32_t ab = (uint32_t)(nu * sizeof(V)), kb = (uint32_t)(KS * sizeof(V));
     const uint64_t drop = sg_policy_evict_first();
+    const int GS = sg_edge_stride(nu, sizeof(T));
+    const uint32_t gb = (uint32_t)(GS * sizeof(T));
+    T* const g_s = reinterpret_cast<T*>(smraw + cols_smem_bytes<T>(nu));  // EDGE: 2 GS entries
     if (t == 0) {
         // the spectra (written only by the build) before the previous pass ends
-        sg_mbar_expect_tx(&bar[1], 2 * kb);
+        sg_mbar_expect_tx(&bar[1], 2 * kb + (EDGE ? 2 * gb : 0));
         sg_bulk_g2s_hint(kr_s, Kr + (size_t)m * KS, kb, &bar[1], drop);
         // mode 0 holds (DC, Nyquist): bring the Nyquist mode's Khat_r instead
         // of Khat_phi, which vanishes at both
         sg_bulk_g2s_hint(kp_s, (m == 0 ? Kr + (size_t)half * KS : Kp + (size_t)m * KS), kb, &bar[1], drop);
+        if constexpr (EDGE) {  // likewise the edge tables' rows
+            sg_bulk_g2s_hint(g_s, egr + (size_t)m * GS, gb, &bar[1], drop);
+            sg_bulk_g2s_hint(g_s + GS, (m == 0 ? egr + (size_t)half * GS : egp + (size_t)m * GS), gb, &bar[1], drop);
+        }
     }
     sg_grid_dep_launch();
     sg_grid_dep_wait();  // A is the previous pass's result
@@ -469,6 +492,19 @@ __global__ void SG_FCOLS_BOUNDS(T, NTB, LG) k_fwd_cols(const typename CX<T>::t* 
     V v[E];
 #pragma unroll
     for (int e = 0; e < E; e++) v[e] = (e < E / 2) ? sm[t + e * NT] : V{0, 0};  // rows >= nu: zero pad
+    __shared__ V es[4];  // EDGE: s^_a
+    if constexpr (EDGE) {
+        if (t == 0) {  // read before the transform's first exchange (behind its first barrier)
+            const V ab4[4] = {sm[0], sm[1], sm[nu - 2], sm[nu - 1]};
+#pragma unroll
+            for (int a = 0; a < 4; a++) {
+                V acc{0, 0};
+#pragma unroll
+                for (int b = 0; b < 4; b++) acc = V{acc.x + ecoef.c[4 * a + b] * ab4[b].x, acc.y + ecoef.c[4 * a + b] * ab4[b].y};
+                es[a] = acc;
+            }
+        }
+    }
     if constexpr (sizeof(T) == 4 && E == 16) {
         fft<E, -1, LG>(v, sm, L, log2L, t, twd);  // the spectra land meanwhile
         if (__syncthreads_or(!sg_mbar_wait_bounded(&bar[1], 0, err, 1, wlim))) return;
@@ -500,6 +536,34 @@ __global__ void SG_FCOLS_BOUNDS(T, NTB, LG) k_fwd_cols(const typename CX<T>::t* 
         }
         // both inverse transforms; their first exchange waits for every spectrum read
         sg_fft_pair<+1, LG>(w, reinterpret_cast<C2*>(smraw), L, log2L, t, twd.h);
+        if constexpr (EDGE) {
+            // row i: += wpre[i] sum_a (gr[i - a] s^_a, -i gp[i - a] s^_a), i - a + N_u
+            // = i + 1 + N_u, i + N_u, i + 1, i for a = -1, 0, N_u - 1, N_u
+            const T* g0 = g_s;
+            const T* g1 = g_s + GS;
+#pragma unroll
+            for (int e = 0; e < E / 2; e++) {
+                const int i = t + e * NT;
+                const int idx[4] = {i + 1 + nu, i + nu, i + 1, i};
+                const T wi = wpre[i];
+                V dr{0, 0}, dq{0, 0};
+#pragma unroll
+                for (int a = 0; a < 4; a++) {
+                    const V sa = es[a];
+                    const T x0 = g0[idx[a]], x1 = g1[idx[a]];
+                    if (m == 0) {  // DC spectrum on the real parts, Nyquist on the imaginary ones
+                        dr.x += x0 * sa.x;
+                        dr.y += x1 * sa.y;
+                    } else {
+                        dr.x += x0 * sa.x;
+                        dr.y += x0 * sa.y;
+                        dq.x += x1 * sa.y;  // -i gp s = gp (s.y - i s.x)
+                        dq.y -= x1 * sa.x;
+                    }
+                }
+                w[e] = C2{w[e].x + f2(wi * dr.x, wi * dq.x), w[e].y + f2(wi * dr.y, wi * dq.y)};
+            }
+        }
 #pragma unroll
         for (int e = 0; e < E / 2; e++) {  // crop to N_u rows
             sg_st_hint(Br + (size_t)m * nu + t + e * NT, c2_lo(w[e]), keep);
@@ -760,18 +824,13 @@ __global__ void __launch_bounds__(NTB, (sizeof(T) == 4 && NTB == 256) ? 2 : 1) k
 // the Nyquist ones, and both azimuthal spectra vanish there.
 // ===========================================================================
 template <typename T>
-struct EdgeCoef {
-    T c[16];
-};
-
-template <typename T>
 __global__ void __launch_bounds__(256) k_edge_fwd(const typename CX<T>::t* __restrict__ A, typename CX<T>::t* B,
                                                   typename CX<T>::t* C, const T* __restrict__ gr,
                                                   const T* __restrict__ gp, const T* __restrict__ wpre,
                                                   EdgeCoef<T> coef, int nu, int nphi)
 {
     typedef typename CX<T>::t V;
-    const int m = blockIdx.x, half = nphi / 2, K = 2 * nu + 1;
+    const int m = blockIdx.x, half = nphi / 2, K = sg_edge_stride(nu, sizeof(T));
     const int brow[4] = {0, 1, nu - 2, nu - 1};
     V ab[4], sa[4];
 #pragma unroll
@@ -825,7 +884,7 @@ __global__ void __launch_bounds__(256) k_edge_bwd(const typename CX<T>::t* __res
 {
     typedef typename CX<T>::t V;
     __shared__ T red[8][8];
-    const int m = blockIdx.x, half = nphi / 2, K = 2 * nu + 1;
+    const int m = blockIdx.x, half = nphi / 2, K = sg_edge_stride(nu, sizeof(T));
     const T* g0 = gr + (size_t)m * K;
     const T* gN = gr + (size_t)half * K;
     const T* p0 = gp + (size_t)m * K;
@@ -1346,6 +1405,7 @@ __global__ void __launch_bounds__(512) k_spec_cols(const double2* __restrict__ W
 struct FixedPassKernels {
     decltype(&k_fwd_rows<float, 16, 256, 0>) fwd_rows;
     decltype(&k_fwd_cols<float, 16, 256, 0>) fwd_cols;
+    decltype(&k_fwd_cols<float, 16, 256, 0>) fwd_cols_edge;  // with the edge-slope update
     decltype(&k_fwd_rows_inv<float, 16, 256, 0>) fwd_rows_inv;
     decltype(&k_bwd_rows<float, 16, 0>) bwd_rows;
     decltype(&k_bwd_cols<float, 16, 256, 0>) bwd_cols;
@@ -1357,9 +1417,10 @@ template <int LG>
 FixedPassKernels make_fixed_pass_kernels()
 {
     constexpr int NB = (1 << LG) / 16 > 256 ? 512 : 256;
-    return FixedPassKernels{k_fwd_rows<float, 16, NB, LG>,  k_fwd_cols<float, 16, NB, LG>,
-                            k_fwd_rows_inv<float, 16, NB, LG>, k_bwd_rows<float, 16, LG>,
-                            k_bwd_cols<float, 16, NB, LG>,  k_bwd_rows_inv<float, 16, NB, LG>, NB};
+    return FixedPassKernels{k_fwd_rows<float, 16, NB, LG>,       k_fwd_cols<float, 16, NB, LG>,
+                            k_fwd_cols<float, 16, NB, LG, true>, k_fwd_rows_inv<float, 16, NB, LG>,
+                            k_bwd_rows<float, 16, LG>,           k_bwd_cols<float, 16, NB, LG>,
+                            k_bwd_rows_inv<float, 16, NB, LG>,   NB};
 }
 
 // defined in fftconv_lg<LG>.cu
@@ -1616,22 +1677,33 @@ cudaError_t launch_forward(const PlanView& p, const T* sigma, T* Fr, T* Fp, cuda
         });
     }
     if (ev && (err = cudaEventRecord(ev[1], st)) != cudaSuccess) return err;
+    bool edges_done = false;  // the column pass applied the edge-slope update itself
     {
         PassRange range_("sg forward columns");
         const int L = 2 * p.nu, E = L >= 16 ? 16 : L;
-        const size_t smem = cols_smem_bytes<T>(p.nu);
+        EdgeCoef<T> coef;
+        for (int j = 0; j < 16; j++) coef.c[j] = p.edges ? (T)p.ecoef[j] : (T)0;
         SG_DISPATCH_E(E, {
+            const bool fuse = sizeof(T) == 4 && EE == 16 && p.edges;
             auto k = k_fwd_cols<T, EE, 256>;
             if constexpr (sizeof(T) == 4)  // FP64 columns are at most 256 threads
                 if (L / EE > 256) k = k_fwd_cols<T, EE, 512>;
-            if constexpr (sizeof(T) == 4 && EE == 16)
+            if constexpr (sizeof(T) == 4 && EE == 16) {
+                if (fuse) k = L / EE > 256 ? k_fwd_cols<T, 16, 512, 0, true> : k_fwd_cols<T, 16, 256, 0, true>;
                 if (const FixedPassKernels* f = fixed_pass_kernels(lL))
-                    if (L / EE <= f->threads) k = f->fwd_cols;
+                    if (L / EE <= f->threads) k = fuse ? f->fwd_cols_edge : f->fwd_cols;
+            }
+            const size_t smem =
+                cols_smem_bytes<T>(p.nu) + (fuse ? 2 * (size_t)sg_edge_stride(p.nu, sizeof(T)) * sizeof(T) : 0);
             if ((err = set_smem(k, smem, true)) != cudaSuccess) return err;
-            if ((err = launch_pdl(k, p.nphi / 2, L / EE, smem, st, A, (const V*)p.kr, (const V*)p.kp, B, C, p.nu, p.nphi, lL, tw, p.err)) != cudaSuccess) return err;
+            if ((err = launch_pdl(k, p.nphi / 2, L / EE, smem, st, A, (const V*)p.kr, (const V*)p.kp, B, C, p.nu,
+                                  p.nphi, lL, tw, p.err, (const T*)p.egr, (const T*)p.egp, (const T*)p.wpre,
+                                  coef)) != cudaSuccess)
+                return err;
+            edges_done = fuse;
         });
     }
-    if (p.edges && (err = launch_edges<T>(p, false, st)) != cudaSuccess) return err;
+    if (p.edges && !edges_done && (err = launch_edges<T>(p, false, st)) != cudaSuccess) return err;
     if (ev && (err = cudaEventRecord(ev[2], st)) != cudaSuccess) return err;
     {
         PassRange range_("sg forward inverse rows");

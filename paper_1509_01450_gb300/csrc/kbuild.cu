@@ -614,7 +614,8 @@ cudaError_t launch_cells(int nu, int nphi, double du, double rtol, double* cells
 }
 
 // k_edge_spec: the phi-spectra of the radial slope kernels for the
-// one-sided edge slopes.  For k in [-N_u, N_u] and mode m in [0, N_phi/2]:
+// one-sided edge slopes.  For k in [-N_u, N_u] and mode m in [0, N_phi/2]
+// (rows of sg_edge_stride elements):
 //   gr[m][k + N_u] = G beta^k / N_phi  sum_q K^{r,r}[k, q]   cos(2 pi m q / N_phi),
 //   gp[m][k + N_u] = G beta^k / N_phi  sum_q K^{phi,r}[k, q] sin(2 pi m q / N_phi),
 // the forward phi-DFTs of the two kernels being gr and -i gp (K^{r,r} is even
@@ -631,6 +632,7 @@ __global__ void k_edge_spec(int nu, int nphi, double du, double G, const double*
     const double* K4 = cells + 4 * per + (long)kk * nphi;  // K^{phi,r}[k, .]
     const int stride = SG_NMAX / nphi;
     const double sc = G * exp(k * du) / nphi;
+    const int ks = sg_edge_stride(nu, sizeof(T));
     for (int m = threadIdx.x; m <= half; m += blockDim.x) {
         double c = K1[0] + ((m & 1) ? -K1[half] : K1[half]), s = 0.0;
         for (int q = 1; q < half; q++) {
@@ -638,8 +640,8 @@ __global__ void k_edge_spec(int nu, int nphi, double du, double G, const double*
             c += 2.0 * K1[q] * w.x;
             s -= 2.0 * K4[q] * w.y;
         }
-        gr[(long)m * (2 * nu + 1) + kk] = (T)(sc * c);
-        gp[(long)m * (2 * nu + 1) + kk] = (T)(sc * s);
+        gr[(long)m * ks + kk] = (T)(sc * c);
+        gp[(long)m * ks + kk] = (T)(sc * s);
     }
 }
 

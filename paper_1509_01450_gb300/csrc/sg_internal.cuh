@@ -54,7 +54,7 @@ struct sg_plan {
     int report[4];      // last build: flag bits, failed offsets, one failed (k, q)
     // one-sided radial slopes at the first and last rows (radial_edges = 1)
     int edges;
-    void* egr;          // working dtype, [nphi/2 + 1][2 nu + 1]: G beta^k / N_phi times the
+    void* egr;          // working dtype, [nphi/2 + 1][sg_edge_stride]: G beta^k / N_phi times the
     void* egp;          // phi-DFT of K^{r,r}[k, .] (cosine sum) and of K^{phi,r}[k, .] (sine sum)
     double ecoef[16];   // [a][b]: slope change of row a in {-1, 0, nu-1, nu} per weighted
                         // sigma of row b in {0, 1, nu-2, nu-1}
@@ -122,6 +122,13 @@ cudaError_t launch_spectra(const PlanView& p, const double* nsr, const double* n
 
 // kbuild.cu
 cudaError_t launch_cells(int nu, int nphi, double du, double rtol, double* cells, int* flag, cudaStream_t st);
+// row stride (elements) of the edge tables: the 2 nu + 1 offsets rounded up
+// to 16 bytes, so that one mode's row moves by one bulk copy
+__host__ __device__ inline int sg_edge_stride(int nu, int elem)
+{
+    const int per = 16 / elem;
+    return (2 * nu + 1 + per - 1) / per * per;
+}
 // the phi-spectra of the radial slope kernels for the one-sided edge slopes
 template <typename T>
 cudaError_t launch_edge_spectra(int nu, int nphi, double du, double G, const double* cells, const void* tw64, T* gr,
