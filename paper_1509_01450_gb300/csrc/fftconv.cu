@@ -30,6 +30,11 @@
 // 0..N_u of the L-point spectrum; Khat_r is Hermitian in kappa
 // (Khat_r[L - kappa] = conj Khat_r[kappa]) and Khat_phi anti-Hermitian.
 // Khat_phi vanishes at modes 0 and N_phi/2 (odd kernel).
+//
+// Plans with one-sided radial edge slopes add a rank-4 update per mode
+// after P2 (inside P2 for FP32 with 16 points per thread) and its transpose
+// after P2b.  FP32 transforms of 2^8 .. 2^13 points run instances with the
+// length fixed at compile time, compiled in fftconv_lg<LG>.cu.
 #include <map>
 #include <mutex>
 #include <tuple>
