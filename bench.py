@@ -384,8 +384,12 @@ def run_ours(args):
             for _ in range(3):
                 pv.forces(sigma, Fr, Fp)
             ems = timed(lambda: pv.forces(sigma, Fr, Fp), max(20, min(args.steps, 200)))
+            for _ in range(3):
+                pv.backward(gr, gp, gs)
+            ebms = timed(lambda: pv.backward(gr, gp, gs), max(20, min(args.steps, 200)))
             entry.update({"value": ws * cells / (ems * 1e-3), "unit": "cells/s", "ms_per_step": ems,
-                          "extra_ms_vs_default": ems - ms})
+                          "extra_ms_vs_default": ems - ms, "backward_ms_per_step": ebms,
+                          "backward_extra_ms_vs_default": ebms - bwd_ms})
         variants[name] = entry
         del pv
 

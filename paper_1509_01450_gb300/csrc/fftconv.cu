@@ -1068,13 +1068,21 @@ __host__ __device__ __forceinline__ size_t bcols_smem_bytes(int nu)
     return sg_align16(sg_padded(L) * sizeof(V)) + (size_t)nu * sizeof(V) + 2 * (size_t)KS * sizeof(V);
 }
 
-template <typename T, int E, int NTB, int LG = 0>
+// EDGE (FP32, 16 points per thread, L >= 32): the transposed edge-slope
+// update of k_edge_bwd is applied here: the mode's rows of the edge tables
+// arrive with the spectra, each thread sums its rows' terms of t_a from the
+// landed columns, and the owners of rows 0, 1, N_u-2, N_u-1 add
+// sum_a coef[a][b] t_a before their stores.  egr, egp, wpre and ecoef are
+// unused otherwise.
+template <typename T, int E, int NTB, int LG = 0, bool EDGE = false>
 __global__ void SG_COLS_BOUNDS(T, NTB) k_bwd_cols(const typename CX<T>::t* __restrict__ A,
                                                   const typename CX<T>::t* __restrict__ C,
                                                   const typename CX<T>::t* __restrict__ Kr,
                                                   const typename CX<T>::t* __restrict__ Kp,
                                                   typename CX<T>::t* __restrict__ B, int nu, int nphi, int log2L,
-                                                  const typename CX<T>::t* __restrict__ tw, int* err)
+                                                  const typename CX<T>::t* __restrict__ tw, int* err,
+                                                  const T* __restrict__ egr, const T* __restrict__ egp,
+                                                  const T* __restrict__ wpre, EdgeCoef<T> ecoef)
 {
     const unsigned long long wlim = sg_wait_budget(err);  // read once, early
     if constexpr (LG > 0) {  // the length is a compile-time constant
@@ -1099,10 +1107,17 @@ __global__ void SG_COLS_BOUNDS(T, NTB) k_bwd_cols(const typename CX<T>::t* __res
     __syncthreads();
     const uint32_t ab = (uint32_t)(nu * sizeof(V)), kb = (uint32_t)(KS * sizeof(V));
     const uint64_t drop = sg_policy_evict_first();
+    const int GS = sg_edge_stride(nu, sizeof(T));
+    const uint32_t gb = (uint32_t)(GS * sizeof(T));
+    T* const g_s = reinterpret_cast<T*>(smraw + bcols_smem_bytes<T>(nu));  // EDGE: 2 GS entries
     if (t == 0) {  // the spectra first (written only by the build)
-        sg_mbar_expect_tx(&bar[1], ab + 2 * kb);
+        sg_mbar_expect_tx(&bar[1], ab + 2 * kb + (EDGE ? 2 * gb : 0));
         sg_bulk_g2s_hint(kr_s, Kr + (size_t)m * KS, kb, &bar[1], drop);
         sg_bulk_g2s_hint(kp_s, (m == 0 ? Kr + (size_t)half * KS : Kp + (size_t)m * KS), kb, &bar[1], drop);
+        if constexpr (EDGE) {  // likewise the edge tables' rows
+            sg_bulk_g2s_hint(g_s, egr + (size_t)m * GS, gb, &bar[1], drop);
+            sg_bulk_g2s_hint(g_s + GS, (m == 0 ? egr + (size_t)half * GS : egp + (size_t)m * GS), gb, &bar[1], drop);
+        }
     }
     sg_grid_dep_launch();
     sg_grid_dep_wait();  // A and C are the previous pass's results
@@ -1123,6 +1138,39 @@ __global__ void SG_COLS_BOUNDS(T, NTB) k_bwd_cols(const typename CX<T>::t* __res
 #pragma unroll
         for (int e = 0; e < E; e++)
             w[e] = (e < E / 2) ? c2(sm[t + e * NT], cs[t + e * NT]) : c2(V{0, 0}, V{0, 0});
+        __shared__ T red[NTB / 32][8];  // EDGE: per-warp sums of t_a
+        if constexpr (EDGE) {
+            // this thread's rows' terms of t_a = sum_i wpre[i] (gr[i - a] A_i + i gp[i - a] C_i)
+            const T* g0 = g_s;
+            const T* g1 = g_s + GS;
+            T acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+#pragma unroll
+            for (int e = 0; e < E / 2; e++) {
+                const int i = t + e * NT;
+                const int idx[4] = {i + 1 + nu, i + nu, i + 1, i};
+                const T wi = wpre[i];
+                const V a = c2_lo(w[e]), c = c2_hi(w[e]);
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    const T x0 = wi * g0[idx[q]], x1 = wi * g1[idx[q]];
+                    if (m == 0) {  // DC spectrum on the real parts, Nyquist on the imaginary ones
+                        acc[2 * q] += x0 * a.x;
+                        acc[2 * q + 1] += x1 * a.y;
+                    } else {
+                        acc[2 * q] += x0 * a.x - x1 * c.y;  // i gp c = gp (-c.y + i c.x)
+                        acc[2 * q + 1] += x0 * a.y + x1 * c.x;
+                    }
+                }
+            }
+#pragma unroll
+            for (int v = 0; v < 8; v++)
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) acc[v] += __shfl_xor_sync(0xffffffffu, acc[v], o);
+            if ((t & 31) == 0)
+#pragma unroll
+                for (int v = 0; v < 8; v++) red[t >> 5][v] = acc[v];
+            // read after the transforms' barriers
+        }
         sg_fft_pair<-1, LG>(w, reinterpret_cast<C2*>(smraw), L, log2L, t, twd.h);  // waits for the landing reads
         V y[E];
         if (m == 0) {
@@ -1149,6 +1197,25 @@ __global__ void SG_COLS_BOUNDS(T, NTB) k_bwd_cols(const typename CX<T>::t* __res
             }
         }
         fft<E, +1, LG>(y, sm, L, log2L, t, twd);  // waits for the mirror reads
+        if constexpr (EDGE) {
+            // rows 0, 1 are element 0 of threads 0, 1; rows N_u-2, N_u-1 element
+            // E/2-1 of threads NT-2, NT-1 (N_u = 8 NT, NT >= 2)
+            auto update = [&](int b) {
+                T tx[4] = {0, 0, 0, 0}, ty[4] = {0, 0, 0, 0};
+                for (int w8 = 0; w8 < (int)(blockDim.x >> 5); w8++)
+#pragma unroll
+                    for (int q = 0; q < 4; q++) {
+                        tx[q] += red[w8][2 * q];
+                        ty[q] += red[w8][2 * q + 1];
+                    }
+                V d{0, 0};
+#pragma unroll
+                for (int q = 0; q < 4; q++) d = V{d.x + ecoef.c[4 * q + b] * tx[q], d.y + ecoef.c[4 * q + b] * ty[q]};
+                return d;
+            };
+            if (t < 2) y[0] = cadd(y[0], update(t));
+            if (t >= NT - 2) y[E / 2 - 1] = cadd(y[E / 2 - 1], update(t - NT + 4));
+        }
 #pragma unroll
         for (int e = 0; e < E / 2; e++) sg_st_hint(B + (size_t)m * nu + t + e * NT, y[e], keep);
         return;
@@ -1414,6 +1481,7 @@ struct FixedPassKernels {
     decltype(&k_fwd_rows_inv<float, 16, 256, 0>) fwd_rows_inv;
     decltype(&k_bwd_rows<float, 16, 0>) bwd_rows;
     decltype(&k_bwd_cols<float, 16, 256, 0>) bwd_cols;
+    decltype(&k_bwd_cols<float, 16, 256, 0>) bwd_cols_edge;  // with the transposed edge-slope update
     decltype(&k_bwd_rows_inv<float, 16, 256, 0>) bwd_rows_inv;
     int threads;  // block size of the row and column instances
 };
@@ -1425,7 +1493,8 @@ FixedPassKernels make_fixed_pass_kernels()
     return FixedPassKernels{k_fwd_rows<float, 16, NB, LG>,       k_fwd_cols<float, 16, NB, LG>,
                             k_fwd_cols<float, 16, NB, LG, true>, k_fwd_rows_inv<float, 16, NB, LG>,
                             k_bwd_rows<float, 16, LG>,           k_bwd_cols<float, 16, NB, LG>,
-                            k_bwd_rows_inv<float, 16, NB, LG>,   NB};
+                            k_bwd_cols<float, 16, NB, LG, true>, k_bwd_rows_inv<float, 16, NB, LG>,
+                            NB};
 }
 
 // defined in fftconv_lg<LG>.cu
@@ -1745,6 +1814,7 @@ cudaError_t launch_backward(const PlanView& p, const T* gr, const T* gp, T* gs, 
     V* C = (V*)p.wc;
     const int ln = sg_ilog2(p.nphi), lL = sg_ilog2(2 * p.nu);
     cudaError_t err;
+    bool edges_done = false;  // the column pass applied the transposed edge update itself
     {
         PassRange range_("sg adjoint rows");
         Shape s = shape_for<V>(p.nphi, row_min_threads(sizeof(T)));
@@ -1767,19 +1837,30 @@ cudaError_t launch_backward(const PlanView& p, const T* gr, const T* gp, T* gs, 
     {
         PassRange range_("sg adjoint columns");
         const int L = 2 * p.nu, E = L >= 16 ? 16 : L;
-        const size_t smem = bcols_smem_bytes<T>(p.nu);
+        EdgeCoef<T> coef;
+        for (int j = 0; j < 16; j++) coef.c[j] = p.edges ? (T)p.ecoef[j] : (T)0;
         SG_DISPATCH_E(E, {
+            // the transposed edge update inside the pass needs whole warps (L >= 512)
+            const bool fuse = sizeof(T) == 4 && EE == 16 && p.edges && L >= 512;
             auto k = k_bwd_cols<T, EE, 256>;
             if constexpr (sizeof(T) == 4)  // FP64 columns are at most 256 threads
                 if (L / EE > 256) k = k_bwd_cols<T, EE, 512>;
-            if constexpr (sizeof(T) == 4 && EE == 16)
+            if constexpr (sizeof(T) == 4 && EE == 16) {
+                if (fuse) k = L / EE > 256 ? k_bwd_cols<T, 16, 512, 0, true> : k_bwd_cols<T, 16, 256, 0, true>;
                 if (const FixedPassKernels* f = fixed_pass_kernels(lL))
-                    if (L / EE <= f->threads) k = f->bwd_cols;
+                    if (L / EE <= f->threads) k = fuse ? f->bwd_cols_edge : f->bwd_cols;
+            }
+            const size_t smem =
+                bcols_smem_bytes<T>(p.nu) + (fuse ? 2 * (size_t)sg_edge_stride(p.nu, sizeof(T)) * sizeof(T) : 0);
             if ((err = set_smem(k, smem, true)) != cudaSuccess) return err;
-            if ((err = launch_pdl(k, p.nphi / 2, L / EE, smem, st, A, C, (const V*)p.kr, (const V*)p.kp, B, p.nu, p.nphi, lL, tw, p.err)) != cudaSuccess) return err;
+            if ((err = launch_pdl(k, p.nphi / 2, L / EE, smem, st, A, C, (const V*)p.kr, (const V*)p.kp, B, p.nu,
+                                  p.nphi, lL, tw, p.err, (const T*)p.egr, (const T*)p.egp, (const T*)p.wpre,
+                                  coef)) != cudaSuccess)
+                return err;
+            edges_done = fuse;
         });
     }
-    if (p.edges && (err = launch_edges<T>(p, true, st)) != cudaSuccess) return err;
+    if (p.edges && !edges_done && (err = launch_edges<T>(p, true, st)) != cudaSuccess) return err;
     {
         PassRange range_("sg adjoint inverse rows");
         Shape s = shape_for<V>(p.nphi, sizeof(T) == 8 ? 64 : 256);

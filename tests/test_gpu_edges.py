@@ -148,3 +148,27 @@ def test_other_entry_points_and_kinds(torch_cuda, oracle_mod):
     Fr_ref, Fp_ref = oracle_mod.direct_sum(sigma, Kr, Kp)
     Fr, Fp = plan2.forces(torch.tensor(sigma, device="cuda"))
     assert oracle_mod.rel_l2(Fr.cpu().numpy(), Fp.cpu().numpy(), Fr_ref, Fp_ref) < 1e-12
+
+
+@pytest.mark.parametrize("nu,nphi", [(256, 64), (512, 128), (2048, 32)])
+def test_fp32_adjoint_with_the_update_in_the_column_pass(torch_cuda, oracle_mod, nu, nphi):
+    """FP32 columns of 512 points or more apply the transposed edge update
+    inside the adjoint's column pass; the FP64 adjoint (the separate kernel,
+    pinned to the oracle's transposed map above) is the reference."""
+    torch = torch_cuda
+    p32, grid, u_min, du = _setup(oracle_mod, nu, nphi, 0.1, 10.0, "float32", 1)
+    p64, _, _, _ = _setup(oracle_mod, nu, nphi, 0.1, 10.0, "float64", 1)
+    gr, gp = workloads.random_field(nu, nphi, 31), workloads.random_field(nu, nphi, 32)
+    g32 = p32.backward(torch.tensor(gr, dtype=torch.float32, device="cuda"),
+                       torch.tensor(gp, dtype=torch.float32, device="cuda"))
+    g64 = p64.backward(torch.tensor(gr, device="cuda"), torch.tensor(gp, device="cuda"))
+    p32.check()
+    ref = g64.cpu().numpy()
+    assert np.linalg.norm(g32.double().cpu().numpy() - ref) / np.linalg.norm(ref) < 1e-5
+    # and the FP32 forward and adjoint are each other's transpose
+    s = torch.tensor(workloads.random_field(nu, nphi, 33), dtype=torch.float32, device="cuda")
+    Fr, Fp = p32.forces(s)
+    lhs = float((torch.tensor(gr, device="cuda") * Fr.double()).sum() + (torch.tensor(gp, device="cuda") * Fp.double()).sum())
+    rhs = float((g32.double() * s.double()).sum())
+    scale = float((torch.tensor(gr, device="cuda").abs() * Fr.double().abs()).sum())
+    assert abs(lhs - rhs) < 1e-5 * scale
