@@ -764,49 +764,49 @@ __global__ void __launch_bounds__(NTB, (sizeof(T) == 4 && NTB == 256) ? 2 : 1) k
                     }
                 }
             }
-            continue;
-        }
+        } else {
 #pragma unroll 1
-        for (int h = 0; h < 2; h++) {
-            const int r = 2 * slot + h;  // row of the block
-            V v[E];
-#pragma unroll
-            for (int e = 0; e < E; e++) {
-                const int n = t + e * NT;
-                V z;
-                if (e < E / 2) {
-                    if (n == 0) {
-                        z = V{Sb[r].x, 0};
-                    } else {
-                        const V a = Sb[n * R + r], b = Sc[n * R + r];
-                        z = V{a.x - b.y, a.y + b.x};  // a + i b
-                    }
-                } else {
-                    if (n == half) {
-                        z = V{Sb[r].y, 0};
-                    } else {
-                        const V a = Sb[(N - n) * R + r], b = Sc[(N - n) * R + r];
-                        z = V{a.x + b.y, -a.y + b.x};  // conj a + i conj b
-                    }
-                }
-                v[e] = z;
-            }
-            if (h == 1) {
-                __syncthreads();  // the stage is read: it takes the next block's rows
-                if (more && (!use_map || threadIdx.x < 32)) {
-                    if (use_map) sg_fence_proxy_async();
-                    issue(rb + gridDim.x);
-                }
-            }
-            fft<E, +1, LG>(v, sm, N, log2n, t, twd, ssync);
-            const int i = rb * R + r;
-            if (i < nu) {
-                const T w = wpost[i];
+            for (int h = 0; h < 2; h++) {
+                const int r = 2 * slot + h;  // row of the block
+                V v[E];
 #pragma unroll
                 for (int e = 0; e < E; e++) {
                     const int n = t + e * NT;
-                    Fr[(size_t)i * N + n] = v[e].x * w;
-                    Fp[(size_t)i * N + n] = v[e].y * w;
+                    V z;
+                    if (e < E / 2) {
+                        if (n == 0) {
+                            z = V{Sb[r].x, 0};
+                        } else {
+                            const V a = Sb[n * R + r], b = Sc[n * R + r];
+                            z = V{a.x - b.y, a.y + b.x};  // a + i b
+                        }
+                    } else {
+                        if (n == half) {
+                            z = V{Sb[r].y, 0};
+                        } else {
+                            const V a = Sb[(N - n) * R + r], b = Sc[(N - n) * R + r];
+                            z = V{a.x + b.y, -a.y + b.x};  // conj a + i conj b
+                        }
+                    }
+                    v[e] = z;
+                }
+                if (h == 1) {
+                    __syncthreads();  // the stage is read: it takes the next block's rows
+                    if (more && (!use_map || threadIdx.x < 32)) {
+                        if (use_map) sg_fence_proxy_async();
+                        issue(rb + gridDim.x);
+                    }
+                }
+                fft<E, +1, LG>(v, sm, N, log2n, t, twd, ssync);
+                const int i = rb * R + r;
+                if (i < nu) {
+                    const T w = wpost[i];
+#pragma unroll
+                    for (int e = 0; e < E; e++) {
+                        const int n = t + e * NT;
+                        Fr[(size_t)i * N + n] = v[e].x * w;
+                        Fp[(size_t)i * N + n] = v[e].y * w;
+                    }
                 }
             }
         }
@@ -1474,15 +1474,30 @@ __global__ void __launch_bounds__(512) k_spec_cols(const double2* __restrict__ W
 // run-time instances.  Block sizes are those of the run-time launches: 256
 // threads up to 4096 points, one 512-thread transform beyond.
 // ===========================================================================
+// the six FP32 pass kernels' signatures (spelled out: naming an instance
+// here would refer to kernels that each translation unit does not define)
+typedef void (*FwdRowsFn)(const float*, const float*, float2*, int, int, int, const float2*, int*, CUtensorMap,
+                          int, int);
+typedef void (*FwdColsFn)(const float2*, const float2*, const float2*, float2*, float2*, int, int, int,
+                          const float2*, int*, const float*, const float*, const float*, EdgeCoef<float>);
+typedef void (*FwdRowsInvFn)(const float2*, const float2*, const float*, float*, float*, int, int, int,
+                             const float2*, int*, CUtensorMap, CUtensorMap, int);
+typedef void (*BwdRowsFn)(const float*, const float*, const float*, float2*, float2*, int, int, int, const float2*,
+                          int*, CUtensorMap, CUtensorMap, int);
+typedef void (*BwdColsFn)(const float2*, const float2*, const float2*, const float2*, float2*, int, int, int,
+                          const float2*, int*, const float*, const float*, const float*, EdgeCoef<float>);
+typedef void (*BwdRowsInvFn)(const float2*, const float*, float*, int, int, int, const float2*, int*, CUtensorMap,
+                             int);
+
 struct FixedPassKernels {
-    decltype(&k_fwd_rows<float, 16, 256, 0>) fwd_rows;
-    decltype(&k_fwd_cols<float, 16, 256, 0>) fwd_cols;
-    decltype(&k_fwd_cols<float, 16, 256, 0>) fwd_cols_edge;  // with the edge-slope update
-    decltype(&k_fwd_rows_inv<float, 16, 256, 0>) fwd_rows_inv;
-    decltype(&k_bwd_rows<float, 16, 0>) bwd_rows;
-    decltype(&k_bwd_cols<float, 16, 256, 0>) bwd_cols;
-    decltype(&k_bwd_cols<float, 16, 256, 0>) bwd_cols_edge;  // with the transposed edge-slope update
-    decltype(&k_bwd_rows_inv<float, 16, 256, 0>) bwd_rows_inv;
+    FwdRowsFn fwd_rows;
+    FwdColsFn fwd_cols;
+    FwdColsFn fwd_cols_edge;  // with the edge-slope update
+    FwdRowsInvFn fwd_rows_inv;
+    BwdRowsFn bwd_rows;
+    BwdColsFn bwd_cols;
+    BwdColsFn bwd_cols_edge;  // with the transposed edge-slope update
+    BwdRowsInvFn bwd_rows_inv;
     int threads;  // block size of the row and column instances
 };
 

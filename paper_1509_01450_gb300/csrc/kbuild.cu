@@ -168,9 +168,9 @@ __device__ __forceinline__ double warp_sum(double v)
 __global__ void __launch_bounds__(128) k_cells(int nu, int nphi, double du, double rtol, double* __restrict__ cells,
                                                int* __restrict__ flag)
 {
-    __shared__ double4 stack_all[4][SG_STACK];
+    __shared__ double4_16a stack_all[4][SG_STACK];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    double4* stack = stack_all[wib];
+    double4_16a* stack = stack_all[wib];
     const double beta = exp(du), dphi = 2.0 * M_PI / nphi;
     const int nq = nphi / 2 + 1;
     const long noff = (long)(2 * nu + 1) * nq;
@@ -189,11 +189,11 @@ __global__ void __launch_bounds__(128) k_cells(int nu, int nphi, double du, doub
         double res[6] = {0, 0, 0, 0, 0, 0};
         int sp = 0, nrect = 0, bad = 0;
         // rectangles in (eta - eta_c, xi - xi_c)
-        stack[0] = make_double4(-hw, hw, -0.5 * dphi, 0.5 * dphi);
+        stack[0] = make_double4_16a(-hw, hw, -0.5 * dphi, 0.5 * dphi);
         sp = 1;
         while (sp > 0) {
             __syncwarp();
-            const double4 R = stack[--sp];
+            const double4_16a R = stack[--sp];
             __syncwarp();
             nrect++;
             const double he = 0.5 * (R.y - R.x), me = 0.5 * (R.y + R.x);
@@ -247,22 +247,22 @@ __global__ void __launch_bounds__(128) k_cells(int nu, int nphi, double du, doub
                 __syncwarp();
                 if (le > 2.0 * lx) {
                     if (lane == 0) {
-                        stack[sp + 0] = make_double4(R.x, me, R.z, R.w);
-                        stack[sp + 1] = make_double4(me, R.y, R.z, R.w);
+                        stack[sp + 0] = make_double4_16a(R.x, me, R.z, R.w);
+                        stack[sp + 1] = make_double4_16a(me, R.y, R.z, R.w);
                     }
                     sp += 2;
                 } else if (lx > 2.0 * le) {
                     if (lane == 0) {
-                        stack[sp + 0] = make_double4(R.x, R.y, R.z, mx);
-                        stack[sp + 1] = make_double4(R.x, R.y, mx, R.w);
+                        stack[sp + 0] = make_double4_16a(R.x, R.y, R.z, mx);
+                        stack[sp + 1] = make_double4_16a(R.x, R.y, mx, R.w);
                     }
                     sp += 2;
                 } else {
                     if (lane == 0) {
-                        stack[sp + 0] = make_double4(R.x, me, R.z, mx);
-                        stack[sp + 1] = make_double4(me, R.y, R.z, mx);
-                        stack[sp + 2] = make_double4(R.x, me, mx, R.w);
-                        stack[sp + 3] = make_double4(me, R.y, mx, R.w);
+                        stack[sp + 0] = make_double4_16a(R.x, me, R.z, mx);
+                        stack[sp + 1] = make_double4_16a(me, R.y, R.z, mx);
+                        stack[sp + 2] = make_double4_16a(R.x, me, mx, R.w);
+                        stack[sp + 3] = make_double4_16a(me, R.y, mx, R.w);
                     }
                     sp += 4;
                 }

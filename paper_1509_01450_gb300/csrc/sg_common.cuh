@@ -666,18 +666,9 @@ __device__ __forceinline__ F2 f2(float a, float b)
     asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(a), "f"(b));
     return r;
 }
-__device__ __forceinline__ float f2_lo(F2 a)
-{
-    float x, y;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(x), "=f"(y) : "l"(a.v));
-    return x;
-}
-__device__ __forceinline__ float f2_hi(F2 a)
-{
-    float x, y;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(x), "=f"(y) : "l"(a.v));
-    return y;
-}
+// the halves of a pair (f2 packs its first value into the low 32 bits)
+__device__ __forceinline__ float f2_lo(F2 a) { return __uint_as_float((unsigned)(a.v & 0xffffffffull)); }
+__device__ __forceinline__ float f2_hi(F2 a) { return __uint_as_float((unsigned)(a.v >> 32)); }
 __device__ __forceinline__ F2 operator+(F2 a, F2 b)
 {
     F2 r;
