@@ -1068,10 +1068,11 @@ __host__ __device__ __forceinline__ size_t bcols_smem_bytes(int nu)
     return sg_align16(sg_padded(L) * sizeof(V)) + (size_t)nu * sizeof(V) + 2 * (size_t)KS * sizeof(V);
 }
 
-// EDGE (FP32, 16 points per thread, L >= 32): the transposed edge-slope
+// EDGE (FP32, 16 points per thread, L >= 512): the transposed edge-slope
 // update of k_edge_bwd is applied here: the mode's rows of the edge tables
-// arrive with the spectra, each thread sums its rows' terms of t_a from the
-// landed columns, and the owners of rows 0, 1, N_u-2, N_u-1 add
+// arrive with the spectra (into the exchange area, which is free until the
+// first transform), each thread sums its rows' terms of t_a from the landed
+// columns, and the owners of rows 0, 1, N_u-2, N_u-1 add
 // sum_a coef[a][b] t_a before their stores.  egr, egp, wpre and ecoef are
 // unused otherwise.
 template <typename T, int E, int NTB, int LG = 0, bool EDGE = false>
@@ -1109,7 +1110,10 @@ __global__ void SG_COLS_BOUNDS(T, NTB) k_bwd_cols(const typename CX<T>::t* __res
     const uint64_t drop = sg_policy_evict_first();
     const int GS = sg_edge_stride(nu, sizeof(T));
     const uint32_t gb = (uint32_t)(GS * sizeof(T));
-    T* const g_s = reinterpret_cast<T*>(smraw + bcols_smem_bytes<T>(nu));  // EDGE: 2 GS entries
+    // EDGE: 2 GS entries, read before the first exchange: they land in the
+    // exchange area after the two columns (16 N_u + 8 GS bytes fit in its
+    // 16 sg_padded(L) for N_u >= 8)
+    T* const g_s = reinterpret_cast<T*>(smraw + 2 * (size_t)nu * sizeof(V));
     if (t == 0) {  // the spectra first (written only by the build)
         sg_mbar_expect_tx(&bar[1], ab + 2 * kb + (EDGE ? 2 * gb : 0));
         sg_bulk_g2s_hint(kr_s, Kr + (size_t)m * KS, kb, &bar[1], drop);
@@ -1865,8 +1869,7 @@ cudaError_t launch_backward(const PlanView& p, const T* gr, const T* gp, T* gs, 
                 if (const FixedPassKernels* f = fixed_pass_kernels(lL))
                     if (L / EE <= f->threads) k = fuse ? f->bwd_cols_edge : f->bwd_cols;
             }
-            const size_t smem =
-                bcols_smem_bytes<T>(p.nu) + (fuse ? 2 * (size_t)sg_edge_stride(p.nu, sizeof(T)) * sizeof(T) : 0);
+            const size_t smem = bcols_smem_bytes<T>(p.nu);  // the edge rows share the exchange area
             if ((err = set_smem(k, smem, true)) != cudaSuccess) return err;
             if ((err = launch_pdl(k, p.nphi / 2, L / EE, smem, st, A, C, (const V*)p.kr, (const V*)p.kp, B, p.nu,
                                   p.nphi, lL, tw, p.err, (const T*)p.egr, (const T*)p.egp, (const T*)p.wpre,
