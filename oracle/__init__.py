@@ -17,6 +17,9 @@ polar coordinates":
                             literal three-term form.
 * ``kernel_cells_tpz``   -- Eq. 41-43: the same kernels with the trapezoidal
                             rule in phi (the paper's SIM with N_tpz).
+* ``potential_cells``    -- the same construction for the potential, which
+                            the paper says carries over (Sec. 6); and
+                            ``potential``, the potential at the centres.
 * ``particle_cells``     -- Eq. 35-37 and Sec. 5.2: the particle method, the
                             modified particle method and the softened
                             particle kernel of the comparison (BM08), as
@@ -69,6 +72,11 @@ def _load():
         lib.sgo_cells_table.restype = ctypes.c_int
         lib.sgo_cells_table_tpz.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                             ctypes.c_double, dp, ctypes.c_int]
+        lib.sgo_cell_pot.argtypes = [ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, dp]
+        lib.sgo_cell_pot.restype = ctypes.c_int
+        lib.sgo_cells_table_pot.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, dp,
+                                            ctypes.c_int]
+        lib.sgo_cells_table_pot.restype = ctypes.c_int
         lib.sgo_cells_table_tpz.restype = ctypes.c_int
         lib.sgo_direct_sum.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, dp, dp, dp, lp, ctypes.c_long,
                                        dp, dp, ctypes.c_int]
@@ -196,6 +204,35 @@ def particle_cells(nu: int, nphi: int, du: float, kind: str, soften: float = 0.0
 def particle_kernels(nu: int, nphi: int, du: float, kind: str, soften: float = 0.0):
     """Folded kernels (Kr, Kphi) of a particle method."""
     return fold(particle_cells(nu, nphi, du, kind, soften), math.exp(du), 2.0 * math.pi / nphi)
+
+
+def potential_cell(du: float, nphi: int, k: int, q: int, rtol: float = 2e-14) -> np.ndarray:
+    """The potential's cells for the offset (k, q) (the paper's method
+    carried over to the potential, Sec. 6): [-int eta / F, -int eta (eta -
+    beta^-k) / F, -int eta (xi + q dphi) / F, 0, 0, 0] over the source cell
+    in d eta d xi."""
+    out = np.zeros(NC)
+    bad = _load().sgo_cell_pot(float(du), int(nphi), int(k), int(q), float(rtol), _dp(out))
+    if bad:
+        raise RuntimeError(f"oracle quadrature did not converge for k={k} q={q}")
+    return out
+
+
+def potential_cells(nu: int, nphi: int, du: float, rtol: float = 2e-14, nthreads: int = 0) -> np.ndarray:
+    """Table [6, 2Nu+1, Nphi] of ``potential_cell`` (slots 3-5 zero)."""
+    out = np.zeros((NC, 2 * nu + 1, nphi))
+    bad = _load().sgo_cells_table_pot(int(nu), int(nphi), float(du), float(rtol), _dp(out), int(nthreads))
+    if bad:
+        raise RuntimeError(f"oracle quadrature did not converge for {bad} integrals")
+    return out
+
+
+def potential(sigma: np.ndarray, cells: np.ndarray, grid: Grid, G: float = 1.0):
+    """Phi at the cell centres: r_i times the convolution of sigma with the
+    folded potential kernel (the slope terms fold as for the forces)."""
+    Kp, _ = fold(cells, grid.beta, grid.dphi)
+    Phi, _ = fft_conv(sigma, Kp, np.zeros_like(Kp), G)
+    return grid.r[:, None] * Phi
 
 
 def kernel_cells_tpz(nu: int, nphi: int, du: float, n_tpz: int, rtol: float = 2e-14, nthreads: int = 0) -> np.ndarray:

@@ -278,6 +278,7 @@ typedef struct {
     double half_dphi;
     double qd;             /* q * dphi, q taken in (-N/2, N/2] */
     int self;              /* k == 0 and q == 0 */
+    int pot;               /* the potential's cells instead of the forces' */
     double rtol;
     int* bad; /* count of integrals that ran out of panels */
 } cell_t;
@@ -308,6 +309,10 @@ static void f_eta(double del, const void* vctx, double out[NV])
     double om = ic->vc - e1 * ic->c;
     double ir0 = -eta * om / F3;
     double ip0 = eta * eta * ic->s / F3;
+    if (cl->pot) { /* the potential: -eta / F and its slope factors */
+        ir0 = -eta / sqrt(F2);
+        ip0 = 0.0;
+    }
     out[0] = ir0;
     out[1] = ir0 * del;
     out[2] = ir0 * ic->t;
@@ -329,6 +334,13 @@ static void f_tau(double tau, const void* vctx, double out[NV])
     double om = ic->s * ic->s - ic->c * as * sh;
     double dr = as * sh - ic->vc;
     double ir0 = -eta * om / F3, ip0 = eta * eta * ic->s / F3;
+    if (ic->cell->pot) { /* (-eta / F) d eta = -eta d tau: smooth */
+        out[0] = -eta;
+        out[1] = -eta * dr;
+        out[2] = -eta * ic->t;
+        out[3] = out[4] = out[5] = 0.0;
+        return;
+    }
     out[0] = ir0 * F;
     out[1] = ir0 * dr * F;
     out[2] = ir0 * ic->t * F;
@@ -371,9 +383,11 @@ static void f_xi(double t, const void* vctx, double out[NV])
         bp[npan] = tb;
         st_ = adapt(f_tau, &ic, bp, npan + 1, INNER_FRAC * cell->rtol, 0.0, 0, out, abs_);
         /* the lobe term of K^{r,0} removed from the integrand in f_tau */
-        double Fa = sqrt((cell->eta_lo - ic.c) * (cell->eta_lo - ic.c) + ic.s * ic.s);
-        double Fb = sqrt((cell->eta_hi - ic.c) * (cell->eta_hi - ic.c) + ic.s * ic.s);
-        out[0] += ic.c * ic.c * (1.0 / Fa - 1.0 / Fb);
+        if (!cell->pot) {
+            double Fa = sqrt((cell->eta_lo - ic.c) * (cell->eta_lo - ic.c) + ic.s * ic.s);
+            double Fb = sqrt((cell->eta_hi - ic.c) * (cell->eta_hi - ic.c) + ic.s * ic.s);
+            out[0] += ic.c * ic.c * (1.0 / Fa - 1.0 / Fb);
+        }
     } else {
         double bp[3];
         int nb = 0;
@@ -463,6 +477,7 @@ static void cell_setup(cell_t* cell, double du, int nphi, int k, int qs, double 
     cell->half_dphi = 0.5 * dphi;
     cell->qd = qs * dphi;
     cell->self = (k == 0 && qs == 0);
+    cell->pot = 0;
     cell->rtol = rtol;
     cell->bad = bad;
 }
@@ -472,7 +487,7 @@ static void cell_setup(cell_t* cell, double du, int nphi, int k, int qs, double 
  * dphi = 2 pi / N_phi.  q is any integer (reduced to (-N/2, N/2]).  Returns
  * 0, or the number of sub-integrals that ran out of panels.
  */
-int sgo_cell(double du, int nphi, int k, int q, double rtol, double out6[NC])
+static int cell_of(double du, int nphi, int k, int q, double rtol, int pot, double out6[NC])
 {
     gl_init();
     int qs = ((q % nphi) + nphi) % nphi;
@@ -480,6 +495,7 @@ int sgo_cell(double du, int nphi, int k, int q, double rtol, double out6[NC])
     int bad = 0;
     cell_t cell;
     cell_setup(&cell, du, nphi, k, qs, rtol, &bad);
+    cell.pot = pot;
     double bp[3], abs_[NV], out[NV];
     int nb = 0, st;
     if (cell.self) {
@@ -507,6 +523,23 @@ int sgo_cell(double du, int nphi, int k, int q, double rtol, double out6[NC])
     return bad;
 }
 
+int sgo_cell(double du, int nphi, int k, int q, double rtol, double out6[NC])
+{
+    return cell_of(du, nphi, k, q, rtol, 0, out6);
+}
+
+/*
+ * The potential's cells for the offset (k, q): out6[0..2] = -int eta / F,
+ * -int eta (eta - beta^-k) / F, -int eta (xi + q dphi) / F over the source
+ * cell (d eta d xi), out6[3..5] = 0.  With them the potential at the centre
+ * of target row i is Phi = G r_i sum sigma (K^{P,0} + slope terms), the
+ * slopes entering as for the forces.
+ */
+int sgo_cell_pot(double du, int nphi, int k, int q, double rtol, double out6[NC])
+{
+    return cell_of(du, nphi, k, q, rtol, 1, out6);
+}
+
 /*
  * Kernel table for k in [-Nu, Nu], q in [0, Nphi):
  * out[c][(k + Nu) * Nphi + q], c = 0..5.  The cells with q in (Nphi/2, Nphi)
@@ -514,7 +547,19 @@ int sgo_cell(double du, int nphi, int k, int q, double rtol, double out6[NC])
  * K^{phi,phi} even, K^{r,phi}, K^{phi,0}, K^{phi,r} odd).  Returns the number
  * of integrals that ran out of panels (0 when all converged).
  */
+static int cells_table_of(int nu, int nphi, double du, double rtol, int pot, double* out, int nthreads);
+
 int sgo_cells_table(int nu, int nphi, double du, double rtol, double* out, int nthreads)
+{
+    return cells_table_of(nu, nphi, du, rtol, 0, out, nthreads);
+}
+
+int sgo_cells_table_pot(int nu, int nphi, double du, double rtol, double* out, int nthreads)
+{
+    return cells_table_of(nu, nphi, du, rtol, 1, out, nthreads);
+}
+
+static int cells_table_of(int nu, int nphi, double du, double rtol, int pot, double* out, int nthreads)
 {
     gl_init();
     long nk = 2L * nu + 1, per = nk * nphi, nq = nphi / 2 + 1;
@@ -527,7 +572,7 @@ int sgo_cells_table(int nu, int nphi, double du, double rtol, double* out, int n
         int k = (int)(idx / nq) - nu;
         int q = (int)(idx % nq);
         double v[NC];
-        bad += sgo_cell(du, nphi, k, q, rtol, v);
+        bad += cell_of(du, nphi, k, q, rtol, pot, v);
         long row = (long)(k + nu) * nphi;
         int qm = (nphi - q) % nphi;
         for (int c = 0; c < NC; c++) {
