@@ -76,10 +76,22 @@ typedef enum {
                                     own exact terms sigma K^{.,0}_{0,0} +
                                     r_i delta^r K^{.,r}_{0,0} + delta^phi
                                     K^{.,phi}_{0,0} */
-    SG_KERNEL_SOFTENED = 3       /* the particle kernel with a softening length
+    SG_KERNEL_SOFTENED = 3,      /* the particle kernel with a softening length
                                     eps = soften * r_i added in quadrature to
                                     the distance (the BM08 comparison method of
                                     Sec. 5.2), own cell included */
+    SG_KERNEL_POTENTIAL = 4      /* the gravitational potential instead of the
+                                    forces (the paper's Sec. 6 notes that the
+                                    method carries over): the same cells and
+                                    slopes with the integrand -eta / F, so
+                                    Phi_i = G r_i sum sigma K^P; sg_forces then
+                                    writes Phi into F_r and zeros into F_phi
+                                    (up to the rounding of the inverse
+                                    transform), and the adjoint is that map's
+                                    transpose.  Build FP32 plans with
+                                    weight_p = 1: Phi carries r_i and the
+                                    kernel grows like r'/r toward outer
+                                    sources, which p = 1 evens out */
 } sg_kernel_kind;
 
 /* Options of the one-time kernel preparation (Sec. 2: "prepared only once
@@ -140,7 +152,8 @@ sg_status sg_plan_create(sg_plan** out, int N_u, int N_phi, double u_min, double
  * Returns SG_ERR_TIMEOUT (the plan is still usable) if a cell integral
  * could not reach the tolerance within the quadrature's budget, and
  * SG_ERR_ARG for an unknown kind, soften <= 0 with SG_KERNEL_SOFTENED,
- * n_tpz outside [0, 1024], radial_edges not 0 or 1, or |weight_p| > 8.
+ * n_tpz outside [0, 1024] (or n_tpz > 0 with another kind than
+ * SG_KERNEL_SIM), radial_edges not 0 or 1, or |weight_p| > 8.
  * Allocates and frees FP64 scratch for the spectra; radial_edges = 1 also
  * allocates the plan's edge tables, 2 (N_phi/2 + 1)(2 N_u + 1) values of
  * the working dtype.

@@ -105,6 +105,40 @@ def kuzmin_truncated_Fr(r, r_in, r_out, M=1.0, a=1.0):
     return np.array(out)
 
 
+def kuzmin_phi(r, M=1.0, a=1.0, G=1.0):
+    """Potential of the Kuzmin disk in its plane, -G M / sqrt(r^2 + a^2)."""
+    r = np.asarray(r, dtype=np.float64)
+    return -G * M / np.sqrt(r * r + a * a)
+
+
+def ring_phi(r, rp):
+    """In-plane potential at radius r per unit (sigma r' dr') of a thin ring of
+    radius r' (G = 1): -int_0^{2pi} dpsi / sqrt(r^2 + r'^2 - 2 r r' cos psi)
+    = -4 K(m) / (r + r'), m = 4 r r' / (r + r')^2."""
+    from scipy.special import ellipkm1
+
+    r = np.asarray(r, dtype=np.float64)
+    rp = np.asarray(rp, dtype=np.float64)
+    p = ((r - rp) / (r + rp)) ** 2  # 1 - m
+    return -4.0 * ellipkm1(p) / (r + rp)
+
+
+def kuzmin_truncated_phi(r, r_in, r_out, M=1.0, a=1.0):
+    """Potential of the part of a Kuzmin disk in r_in <= r' <= r_out: the
+    closed form minus the rings r' < r_in and r' > r_out (targets r must lie
+    inside (r_in, r_out), where neither integral meets the logarithmic
+    singularity of its ring)."""
+    from scipy.integrate import quad
+
+    out = []
+    for rr in np.atleast_1d(np.asarray(r, dtype=np.float64)):
+        f = lambda rp: float(kuzmin_sigma(rp, M, a)) * rp * float(ring_phi(rr, rp))
+        inner = quad(f, 0.0, r_in, limit=200, epsabs=0.0, epsrel=1e-12)[0]
+        outer = quad(f, r_out, np.inf, limit=200, epsabs=0.0, epsrel=1e-12)[0]
+        out.append(float(kuzmin_phi(rr, M, a)) - inner - outer)
+    return np.array(out)
+
+
 # --------------------------------------------------------------------------
 # sigma_{D_n} family (Eq. 50-53), exact recursion
 # --------------------------------------------------------------------------

@@ -303,11 +303,11 @@ sg_status sg_kernels_build(sg_plan* p, const sg_build_opts* opts, cudaStream_t s
         wp = opts->weight_p;
         if (wp < -8 || wp > 8) return SG_ERR_ARG;
         kind = opts->kind;
-        if (kind < SG_KERNEL_SIM || kind > SG_KERNEL_SOFTENED) return SG_ERR_ARG;
+        if (kind < SG_KERNEL_SIM || kind > SG_KERNEL_POTENTIAL) return SG_ERR_ARG;
         soften = opts->soften;
         if (kind == SG_KERNEL_SOFTENED && !(soften > 0.0 && soften < 1e3)) return SG_ERR_ARG;
         ntpz = opts->n_tpz;
-        if (ntpz < 0 || ntpz > 1024) return SG_ERR_ARG;
+        if (ntpz < 0 || ntpz > 1024 || (ntpz > 0 && kind != SG_KERNEL_SIM)) return SG_ERR_ARG;
         edges = opts->radial_edges;
         if (edges != 0 && edges != 1) return SG_ERR_ARG;
     }
@@ -324,6 +324,8 @@ sg_status sg_kernels_build(sg_plan* p, const sg_build_opts* opts, cudaStream_t s
         for (int i = 0; i < nu; i++) {
             pre[i] = exp(wp * (i - iref) * p->du);
             post[i] = exp(-wp * (i - iref) * p->du);
+            // the potential carries the target radius: Phi_i = G r_i sum sigma K^P
+            if (kind == SG_KERNEL_POTENTIAL) post[i] *= 0.5 * exp(p->u_min + i * p->du) * (1.0 + exp(p->du));
         }
         if (p->dtype == SG_F32) {
             std::vector<float> a(nu), b(nu);
@@ -373,9 +375,9 @@ sg_status sg_kernels_build(sg_plan* p, const sg_build_opts* opts, cudaStream_t s
         ret = SG_ERR_CUDA;
         goto done;
     }
-    if ((kind == SG_KERNEL_SIM ? launch_cells(nu, nphi, p->du, rtol, p->cells, flag, stream)
-                               : launch_point_cells(nu, nphi, p->du, kind, soften, rtol, p->cells, flag, stream)) !=
-            cudaSuccess ||
+    if ((kind == SG_KERNEL_SIM || kind == SG_KERNEL_POTENTIAL
+             ? launch_cells(nu, nphi, p->du, rtol, p->cells, flag, stream, kind == SG_KERNEL_POTENTIAL)
+             : launch_point_cells(nu, nphi, p->du, kind, soften, rtol, p->cells, flag, stream)) != cudaSuccess ||
         (kind == SG_KERNEL_SIM && ntpz > 0 &&
          launch_cells_tpz(nu, nphi, p->du, ntpz, rtol, p->cells, flag, stream) != cudaSuccess) ||
         launch_fold(nu, nphi, p->du, p->G, wp, p->cells, p->keff, nsr, nsp, stream) != cudaSuccess ||

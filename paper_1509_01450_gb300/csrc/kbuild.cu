@@ -34,6 +34,12 @@
 // and a fine rule must agree.  K^{r,phi}, K^{phi,0}, K^{phi,r} vanish on
 // the self cell by symmetry (Sec. 3.2.2 and App. A).
 //
+// The potential (SG_KERNEL_POTENTIAL): k_cells and k_self_cell with the
+// integrand -eta / F in place of the radial force's (the slope factors
+// (eta - beta^-k) and (xi + q dphi) as for the forces; the azimuthal slots
+// zero).  In the own cell's polar rule it behaves like 1 / rho, which the
+// rule's rho weight absorbs.
+//
 // k_point_cells: the particle kinds of sg_kernel_kind (Eq. 35-37 and the
 // softened comparison method of Sec. 5.2).  The source centre of offset
 // (k, q) sits at eta_c = beta^-k, xi_c = -q' dphi (q' = q taken into
@@ -135,7 +141,7 @@ static cudaError_t upload_rules()
 // (or 1 - cos xi directly when cos xi <= 0) and eta - 1 = em1 + del, so they
 // keep full relative precision near the singular point eta = 1, xi = 0.
 __device__ __forceinline__ void acc6(double del, double eta_c, double em1, double dp, double c, double s, double w,
-                                     double* I, double* A)
+                                     double* I, double* A, int pot = 0)
 {
     const double vc = c > 0.0 ? s * s / (1.0 + c) : 1.0 - c;  // 1 - cos xi
     const double e1 = em1 + del;                               // eta - 1
@@ -145,8 +151,9 @@ __device__ __forceinline__ void acc6(double del, double eta_c, double em1, doubl
     const double F2 = d * d + s * s;
     const double iF = 1.0 / sqrt(F2);
     const double iF3 = iF * iF * iF;
-    const double ir0 = -eta * om * iF3;
-    const double ip0 = eta * eta * s * iF3;
+    // pot: the potential's integrand -eta / F in the first three slots
+    const double ir0 = pot ? -eta * iF : -eta * om * iF3;
+    const double ip0 = pot ? 0.0 : eta * eta * s * iF3;
     const double v[6] = {ir0, ir0 * del, ir0 * dp, ip0, ip0 * del, ip0 * dp};
 #pragma unroll
     for (int c6 = 0; c6 < 6; c6++) {
@@ -166,7 +173,7 @@ __device__ __forceinline__ double warp_sum(double v)
 #define SG_MAXRECT 20000
 
 __global__ void __launch_bounds__(128) k_cells(int nu, int nphi, double du, double rtol, double* __restrict__ cells,
-                                               int* __restrict__ flag)
+                                               int* __restrict__ flag, int pot)
 {
     __shared__ double4_16a stack_all[4][SG_STACK];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -205,7 +212,7 @@ __global__ void __launch_bounds__(128) k_cells(int nu, int nphi, double du, doub
                 double st, ct;
                 sincos(t, &st, &ct);
                 acc6(del, eta_c, em1, t, ct * cc - st * sc, st * cc + ct * sc, he * hx * c_w8[a] * c_w8[b], I8,
-                     nullptr);
+                     nullptr, pot);
             }
             for (int p = lane; p < 144; p += 32) {
                 const int a = p / 12, b = p % 12;
@@ -213,7 +220,7 @@ __global__ void __launch_bounds__(128) k_cells(int nu, int nphi, double du, doub
                 double st, ct;
                 sincos(t, &st, &ct);
                 acc6(del, eta_c, em1, t, ct * cc - st * sc, st * cc + ct * sc, he * hx * c_w12[a] * c_w12[b], I12,
-                     A12);
+                     A12, pot);
             }
             bool ok = true;
 #pragma unroll
@@ -396,13 +403,20 @@ __global__ void __launch_bounds__(128) k_cells_tpz(int nu, int nphi, double du, 
 //   f(p) + f(-p) = -2 (Ns Gs + Nd Gd),  f(p) - f(-p) = -2 (Ns Gd + Nd Gs),
 // Ns = vc - x^2 cos y, Nd = -x (1 - 2 vc), Gs = (F_+^-3 + F_-^-3) / 2 and
 // Gd = (F_+^-3 - F_-^-3) / 2 = -B (3 A^2 + B^2) / ((F_+^3 + F_-^3) F_+^3 F_-^3).
-__device__ __forceinline__ void self_pair(double x, double y, double* v)
+__device__ __forceinline__ void self_pair(double x, double y, double* v, int pot)
 {
     const double s = sin(y), sh = sin(0.5 * y);
     const double vc = 2.0 * sh * sh;
     const double c = 1.0 - vc;
     const double P = (x + vc) * (x + vc) + s * s;
     const double M = (x - vc) * (x - vc) + s * s;
+    if (pot) {  // the potential: -eta / F at p and -p (both ~ 1/rho: the polar rule absorbs it)
+        const double a = (1.0 + x) / sqrt(P), b = (1.0 - x) / sqrt(M);
+        v[0] = -(a + b);      // K^{P,0}
+        v[1] = -x * (a - b);  // K^{P,r}: (eta - 1) = x at p, -x at -p
+        v[2] = 0.0;           // K^{P,phi}: odd in y, zero over the cell
+        return;
+    }
     const double Fp3 = P * sqrt(P), Fm3 = M * sqrt(M);
     const double A = 0.5 * (P + M), B = 2.0 * x * vc;
     const double Gs = 0.5 * (1.0 / Fp3 + 1.0 / Fm3);
@@ -435,7 +449,7 @@ __device__ void block_sum3(double* acc, double* out)
 // triangle of each opposite pair (rays to x = m for |theta| < pi/4, to
 // y = m for pi/4 < theta < 3 pi/4), np x np composite 16-point panels in
 // (angle, radius), integrand self_pair.
-__device__ void self_square(double m, int np, double* out)
+__device__ void self_square(double m, int np, double* out, int pot)
 {
     const double thc = 0.25 * M_PI;
     double acc[3] = {0, 0, 0};
@@ -456,7 +470,7 @@ __device__ void self_square(double m, int np, double* out)
         const double rho = rmax * tau;
         const double w = thw * 0.5 * (u1 - u0) * c_w16[b] * rmax * rmax * tau;
         double v[3];
-        self_pair(rho * ct, rho * st, v);
+        self_pair(rho * ct, rho * st, v, pot);
 #pragma unroll
         for (int c3 = 0; c3 < 3; c3++) acc[c3] += w * v[c3];
     }
@@ -467,7 +481,7 @@ __device__ void self_square(double m, int np, double* out)
 // over [m, L] in geometric panels (ratio), the short one over [-w, w] in
 // nshort panels; radial = 1 means the long coordinate is x = eta - 1.
 // (Its point reflection is the opposite strip, which self_pair includes.)
-__device__ void self_strip(double m, double L, double w, double ratio, int nshort, int radial, double* out)
+__device__ void self_strip(double m, double L, double w, double ratio, int nshort, int radial, double* out, int pot)
 {
     double acc[3] = {0, 0, 0};
     double a = m;
@@ -482,9 +496,9 @@ __device__ void self_strip(double m, double L, double w, double ratio, int nshor
             const double wt = 0.5 * (b - a) * c_w16[ia] * 0.5 * (s1 - s0) * c_w16[ib];
             double v[3];
             if (radial)
-                self_pair(l, sh, v);
+                self_pair(l, sh, v, pot);
             else
-                self_pair(sh, l, v);
+                self_pair(sh, l, v, pot);
 #pragma unroll
             for (int c3 = 0; c3 < 3; c3++) acc[c3] += wt * v[c3];
         }
@@ -497,26 +511,26 @@ __device__ void self_strip(double m, double L, double w, double ratio, int nshor
 // side 2 min(h, d) about the singular point plus the two strips beyond it,
 // at a coarse and a fine resolution; the fine value is kept and the two
 // must agree.
-__device__ void self_cell_rule(double h, double d, int fine, double* out)
+__device__ void self_cell_rule(double h, double d, int fine, double* out, int pot)
 {
     const double m = fmin(h, d);
     double sq[3], st[3] = {0, 0, 0};
-    self_square(m, fine ? 8 : 4, sq);
+    self_square(m, fine ? 8 : 4, sq, pot);
     const double ratio = fine ? 1.4142135623730951 : 2.0;
     const int ns = fine ? 8 : 4;
-    if (h > m) self_strip(m, h, d, ratio, ns, 1, st);
-    if (d > m) self_strip(m, d, h, ratio, ns, 0, st);
+    if (h > m) self_strip(m, h, d, ratio, ns, 1, st, pot);
+    if (d > m) self_strip(m, d, h, ratio, ns, 0, st, pot);
     for (int c3 = 0; c3 < 3; c3++) out[c3] = sq[c3] + st[c3];
 }
 
 __global__ void __launch_bounds__(256) k_self_cell(int nu, int nphi, double du, double rtol,
-                                                   double* __restrict__ cells, int* __restrict__ flag)
+                                                   double* __restrict__ cells, int* __restrict__ flag, int pot)
 {
     const double dphi = 2.0 * M_PI / nphi;
     const double h = tanh(0.5 * du), d = 0.5 * dphi;  // (beta - 1)/(beta + 1) without cancellation
     double coarse[3], fine[3];
-    self_cell_rule(h, d, 0, coarse);
-    self_cell_rule(h, d, 1, fine);
+    self_cell_rule(h, d, 0, coarse, pot);
+    self_cell_rule(h, d, 1, fine, pot);
     if (threadIdx.x == 0) {
         const long per = (long)(2 * nu + 1) * nphi;
         const long at = (long)nu * nphi;  // k = 0, q = 0
@@ -597,7 +611,7 @@ __global__ void k_fold(int nu, int nphi, double du, double G, int p, const doubl
     }
 }
 
-cudaError_t launch_cells(int nu, int nphi, double du, double rtol, double* cells, int* flag, cudaStream_t st)
+cudaError_t launch_cells(int nu, int nphi, double du, double rtol, double* cells, int* flag, cudaStream_t st, int pot)
 {
     cudaError_t e = upload_rules();
     if (e != cudaSuccess) return e;
@@ -608,8 +622,8 @@ cudaError_t launch_cells(int nu, int nphi, double du, double rtol, double* cells
     long blocks = (noff + 3) / 4;
     const long cap = (long)nsm * 32;
     if (blocks > cap) blocks = cap;
-    k_cells<<<(int)blocks, 128, 0, st>>>(nu, nphi, du, rtol, cells, flag);
-    k_self_cell<<<1, 256, 0, st>>>(nu, nphi, du, rtol, cells, flag);
+    k_cells<<<(int)blocks, 128, 0, st>>>(nu, nphi, du, rtol, cells, flag, pot);
+    k_self_cell<<<1, 256, 0, st>>>(nu, nphi, du, rtol, cells, flag, pot);
     return cudaGetLastError();
 }
 
@@ -681,7 +695,7 @@ cudaError_t launch_point_cells(int nu, int nphi, double du, int kind, double sof
     if (kind == SG_KERNEL_PARTICLE_PLUS) {
         cudaError_t e = upload_rules();  // the own cell's Gauss-Legendre rules
         if (e != cudaSuccess) return e;
-        k_self_cell<<<1, 256, 0, st>>>(nu, nphi, du, rtol, cells, flag);
+        k_self_cell<<<1, 256, 0, st>>>(nu, nphi, du, rtol, cells, flag, 0);
     }
     return cudaGetLastError();
 }

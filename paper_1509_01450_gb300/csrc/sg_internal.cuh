@@ -121,7 +121,9 @@ cudaError_t launch_spectra(const PlanView& p, const double* nsr, const double* n
                            cudaStream_t st);
 
 // kbuild.cu
-cudaError_t launch_cells(int nu, int nphi, double du, double rtol, double* cells, int* flag, cudaStream_t st);
+// pot: the potential's cells (SG_KERNEL_POTENTIAL) instead of the forces'
+cudaError_t launch_cells(int nu, int nphi, double du, double rtol, double* cells, int* flag, cudaStream_t st,
+                         int pot = 0);
 // row stride (elements) of the edge tables: the 2 nu + 1 offsets rounded up
 // to 16 bytes, so that one mode's row moves by one bulk copy
 __host__ __device__ inline int sg_edge_stride(int nu, int elem)

@@ -35,8 +35,9 @@ SG_KERNEL_SIM = 0            # second order: exact cell integrals, central slope
 SG_KERNEL_PARTICLE = 1       # point mass at each source centre (Eq. 35)
 SG_KERNEL_PARTICLE_PLUS = 2  # point masses plus the own cell's exact terms (Eq. 36-37)
 SG_KERNEL_SOFTENED = 3       # point masses with softening eps = soften r_i (BM08 comparison)
+SG_KERNEL_POTENTIAL = 4      # the potential Phi (into F_r; F_phi zero) with the same construction
 KERNEL_KINDS = {"sim": SG_KERNEL_SIM, "particle": SG_KERNEL_PARTICLE, "particle+": SG_KERNEL_PARTICLE_PLUS,
-                "softened": SG_KERNEL_SOFTENED}
+                "softened": SG_KERNEL_SOFTENED, "potential": SG_KERNEL_POTENTIAL}
 
 
 class BuildOpts(ctypes.Structure):
@@ -132,9 +133,10 @@ class Plan:
               radial_edges: int = 0, stream=None):
         """Build the kernels.  kind: "sim" (default; n_tpz > 0 for the
         trapezoidal rule of Eq. 41-43 with n_tpz trapezoids), "particle",
-        "particle+" or "softened" (with soften = eps / r_i), or an
-        SG_KERNEL_* code.  radial_edges = 1: one-sided radial slopes at the
-        first and last rows instead of ghost rows."""
+        "particle+" or "softened" (with soften = eps / r_i), "potential"
+        (Phi into F_r; weight_p = 1 for FP32), or an SG_KERNEL_* code.
+        radial_edges = 1: one-sided radial slopes at the first and last rows
+        instead of ghost rows."""
         code = KERNEL_KINDS[kind] if isinstance(kind, str) else int(kind)
         opts = BuildOpts(rtol, weight_p, code, soften, n_tpz, radial_edges)
         _check(lib().sg_kernels_build(self.handle, ctypes.byref(opts), _stream(stream)), "sg_kernels_build")

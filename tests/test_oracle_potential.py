@@ -15,8 +15,6 @@ import math
 
 import numpy as np
 import pytest
-from scipy.integrate import quad
-from scipy.special import ellipk
 
 import workloads
 from oracle import analytic as A
@@ -78,21 +76,6 @@ def test_potential_cells_match_closed_forms(oracle_mod, k, q):
     assert not np.any(got[3:])
 
 
-def _kuzmin_truncated_phi(r, r_in, r_out):
-    """-1 / sqrt(r^2 + 1) minus the potential of the Kuzmin mass inside r_in
-    and outside r_out (rings: -2 dm K(m) / (pi (r + r')), m = 4 r r' / (r + r')^2)."""
-    def ring(rp, x):
-        m = 4 * x * rp / (x + rp) ** 2
-        return -2.0 * ellipk(m) / (math.pi * (x + rp)) * A.kuzmin_sigma(rp) * 2 * math.pi * rp
-
-    out = []
-    for x in r:
-        inner = quad(lambda rp: ring(rp, x), 0.0, r_in, limit=200, epsabs=0, epsrel=1e-12)[0]
-        outer = quad(lambda rp: ring(rp, x), r_out, np.inf, limit=200, epsabs=0, epsrel=1e-12)[0]
-        out.append(-1.0 / math.sqrt(x * x + 1.0) - inner - outer)
-    return np.array(out)
-
-
 def test_kuzmin_potential_second_order_interior(oracle_mod):
     errs = []
     for n in (32, 64, 128):
@@ -102,7 +85,7 @@ def test_kuzmin_potential_second_order_interior(oracle_mod):
         sig = workloads.kuzmin(grid.r, grid.phi)
         Phi = oracle_mod.potential(sig, cells, grid)
         m = (grid.r >= 0.2) & (grid.r <= 5.0)
-        truth = _kuzmin_truncated_phi(grid.r[m], 0.05, 20.0)
+        truth = A.kuzmin_truncated_phi(grid.r[m], 0.05, 20.0)
         errs.append(np.abs(Phi[m, 0] - truth).max() / np.abs(truth).max())
         assert np.ptp(Phi, axis=1).max() < 1e-13 * np.abs(Phi).max()  # axisymmetric
     orders = [math.log2(a / b) for a, b in zip(errs[:-1], errs[1:])]
@@ -126,3 +109,13 @@ def test_potential_gradient_is_the_radial_force(oracle_mod):
         gaps.append(np.abs(dPhi[m] - Fr[1:-1][m]).max() / np.abs(Fr[1:-1][m]).max())
     orders = [math.log2(a / b) for a, b in zip(gaps[:-1], gaps[1:])]
     assert orders[-1] > 1.8 and gaps[-1] < 2e-3, (gaps, orders)
+
+
+@pytest.mark.parametrize("r,rp", [(1.0, 0.3), (0.5, 2.0), (3.0, 2.9), (0.2, 20.0)])
+def test_ring_potential_closed_form(r, rp):
+    """The ring potential's elliptic form against the angle integral itself."""
+    from scipy.integrate import quad
+
+    ref = -quad(lambda p: 1.0 / math.sqrt(r * r + rp * rp - 2 * r * rp * math.cos(p)), 0.0, 2 * math.pi,
+                epsabs=0, epsrel=1e-13, limit=400)[0]
+    assert abs(A.ring_phi(r, rp) - ref) < 1e-12 * abs(ref)
