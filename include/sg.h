@@ -80,7 +80,7 @@ typedef enum {
                                     eps = soften * r_i added in quadrature to
                                     the distance (the BM08 comparison method of
                                     Sec. 5.2), own cell included */
-    SG_KERNEL_POTENTIAL = 4      /* the gravitational potential instead of the
+    SG_KERNEL_POTENTIAL = 4,     /* the gravitational potential instead of the
                                     forces (the paper's Sec. 6 notes that the
                                     method carries over): the same cells and
                                     slopes with the integrand -eta / F, so
@@ -92,6 +92,22 @@ typedef enum {
                                     weight_p = 1: Phi carries r_i and the
                                     kernel grows like r'/r toward outer
                                     sources, which p = 1 evens out */
+    SG_KERNEL_CARTESIAN = 5      /* the Cartesian second-order scheme of
+                                    Sec. 3.1.1 (Eq. 6-15, closed forms of
+                                    App. A) on square cells of side du: the
+                                    plan's rows are x (N_x = N_u, zero-padded
+                                    by the passes), its columns y with
+                                    N_phi = 2 N_y, the last N_y of them the
+                                    padding that makes the periodic direction
+                                    a linear convolution.  sigma must be zero
+                                    in columns N_y .. N_phi - 1; F there is
+                                    not a force.  F_r is F^x, F_phi is F^y;
+                                    central slopes with sigma zero outside
+                                    the grid, as for SG_KERNEL_SIM; u_min is
+                                    unused.  weight_p and radial_edges must
+                                    be 0; sg_plan_cells returns zeros (the
+                                    kernels are folded from their closed
+                                    forms directly) */
 } sg_kernel_kind;
 
 /* Options of the one-time kernel preparation (Sec. 2: "prepared only once
@@ -153,7 +169,8 @@ sg_status sg_plan_create(sg_plan** out, int N_u, int N_phi, double u_min, double
  * could not reach the tolerance within the quadrature's budget, and
  * SG_ERR_ARG for an unknown kind, soften <= 0 with SG_KERNEL_SOFTENED,
  * n_tpz outside [0, 1024] (or n_tpz > 0 with another kind than
- * SG_KERNEL_SIM), radial_edges not 0 or 1, or |weight_p| > 8.
+ * SG_KERNEL_SIM), radial_edges not 0 or 1, |weight_p| > 8, or weight_p or
+ * radial_edges not 0 with SG_KERNEL_CARTESIAN.
  * Allocates and frees FP64 scratch for the spectra; radial_edges = 1 also
  * allocates the plan's edge tables, 2 (N_phi/2 + 1)(2 N_u + 1) values of
  * the working dtype.

@@ -303,13 +303,14 @@ sg_status sg_kernels_build(sg_plan* p, const sg_build_opts* opts, cudaStream_t s
         wp = opts->weight_p;
         if (wp < -8 || wp > 8) return SG_ERR_ARG;
         kind = opts->kind;
-        if (kind < SG_KERNEL_SIM || kind > SG_KERNEL_POTENTIAL) return SG_ERR_ARG;
+        if (kind < SG_KERNEL_SIM || kind > SG_KERNEL_CARTESIAN) return SG_ERR_ARG;
         soften = opts->soften;
         if (kind == SG_KERNEL_SOFTENED && !(soften > 0.0 && soften < 1e3)) return SG_ERR_ARG;
         ntpz = opts->n_tpz;
         if (ntpz < 0 || ntpz > 1024 || (ntpz > 0 && kind != SG_KERNEL_SIM)) return SG_ERR_ARG;
         edges = opts->radial_edges;
         if (edges != 0 && edges != 1) return SG_ERR_ARG;
+        if (kind == SG_KERNEL_CARTESIAN && (wp != 0 || edges != 0)) return SG_ERR_ARG;
     }
     // beta^{p (i - i_ref)} must stay in range for both dtypes
     if (fabs((double)wp * p->du * p->nu) > 60.0) return SG_ERR_UNSUPPORTED;
@@ -375,12 +376,18 @@ sg_status sg_kernels_build(sg_plan* p, const sg_build_opts* opts, cudaStream_t s
         ret = SG_ERR_CUDA;
         goto done;
     }
-    if ((kind == SG_KERNEL_SIM || kind == SG_KERNEL_POTENTIAL
-             ? launch_cells(nu, nphi, p->du, rtol, p->cells, flag, stream, kind == SG_KERNEL_POTENTIAL)
-             : launch_point_cells(nu, nphi, p->du, kind, soften, rtol, p->cells, flag, stream)) != cudaSuccess ||
-        (kind == SG_KERNEL_SIM && ntpz > 0 &&
-         launch_cells_tpz(nu, nphi, p->du, ntpz, rtol, p->cells, flag, stream) != cudaSuccess) ||
-        launch_fold(nu, nphi, p->du, p->G, wp, p->cells, p->keff, nsr, nsp, stream) != cudaSuccess ||
+    if (kind == SG_KERNEL_CARTESIAN) {
+        if (launch_cart_fold(nu, nphi, p->du, p->G, p->cells, p->keff, nsr, nsp, stream) != cudaSuccess) {
+            ret = SG_ERR_CUDA;
+            goto done;
+        }
+    } else if ((kind == SG_KERNEL_SIM || kind == SG_KERNEL_POTENTIAL
+                    ? launch_cells(nu, nphi, p->du, rtol, p->cells, flag, stream, kind == SG_KERNEL_POTENTIAL)
+                    : launch_point_cells(nu, nphi, p->du, kind, soften, rtol, p->cells, flag, stream)) !=
+                   cudaSuccess ||
+               (kind == SG_KERNEL_SIM && ntpz > 0 &&
+                launch_cells_tpz(nu, nphi, p->du, ntpz, rtol, p->cells, flag, stream) != cudaSuccess) ||
+               launch_fold(nu, nphi, p->du, p->G, wp, p->cells, p->keff, nsr, nsp, stream) != cudaSuccess ||
         (edges && (p->dtype == SG_F32 ? launch_edge_spectra<float>(nu, nphi, p->du, p->G, p->cells, p->tw64,
                                                                    (float*)p->egr, (float*)p->egp, stream)
                                       : launch_edge_spectra<double>(nu, nphi, p->du, p->G, p->cells, p->tw64,

@@ -72,6 +72,21 @@
 //                + (K^{.,phi}[k,q+1] - K^{.,phi}[k,q-1]) / (2 dphi),
 // then the weighted, normalised kernel G beta^{p k} K^eff / (L N_phi) is
 // placed cyclically at row k mod L (L = 2 N_u, row N_u left zero).
+//
+// k_cart_fold: the Cartesian scheme of Sec. 3.1.1 (SG_KERNEL_CARTESIAN) on
+// square cells of side h = du.  The six cell integrals of Eq. 13-15 and
+// their y forms have the closed forms of App. A: double differences over
+// the source cell's corners (X, Y relative to the target centre) of
+// -ln(Y + R), -ln(X + R), Y ln(X + R), X ln(Y + R) and -R, R = |(X, Y)|,
+// plus k h or q h times the zeroth kernel.  They fold with central slopes
+// (beta = 1):
+//   K^eff[k,q] = K^{.,0} + (K^{.,x}[k+1] - K^{.,x}[k-1]) / 2h
+//                        + (K^{.,y}[q+1] - K^{.,y}[q-1]) / 2h,
+// evaluated directly at every true offset, so the table needs no ring in
+// q.  Row k lands at k mod 2 N_x as for the polar grid; offset q at
+// q mod N_phi for |q| < N_phi / 2, with column N_phi / 2 left zero: sigma
+// zero in its last N_phi / 2 columns then makes the periodic transform in
+// the second direction a linear convolution over the first N_phi / 2.
 #include <math.h>
 #include <stdio.h>
 
@@ -697,6 +712,84 @@ cudaError_t launch_point_cells(int nu, int nphi, double du, int kind, double sof
         if (e != cudaSuccess) return e;
         k_self_cell<<<1, 256, 0, st>>>(nu, nphi, du, rtol, cells, flag, 0);
     }
+    return cudaGetLastError();
+}
+
+// ln(a + sqrt(a^2 + b^2)) for b != 0; for a < 0 as ln(b^2) - ln(R - a),
+// which does not cancel
+__device__ __forceinline__ double cart_lsum(double a, double b)
+{
+    const double R = hypot(a, b);
+    return a >= 0.0 ? log(a + R) : 2.0 * log(fabs(b)) - log(R - a);
+}
+
+// The six cell integrals at offset (k, q) on square cells of side h, in
+// the order K^{x,0}, K^{x,x}, K^{x,y}, K^{y,0}, K^{y,x}, K^{y,y}.  Corners
+// sit at half-integer multiples of h, so no corner has X = 0 or Y = 0.
+__device__ void cart_cell(int k, int q, double h, double K[6])
+{
+    const double xs[2] = {(-k - 0.5) * h, (-k + 0.5) * h}, ys[2] = {(-q - 0.5) * h, (-q + 0.5) * h};
+    double a0 = 0, b0 = 0, ax = 0, by = 0, mr = 0;
+#pragma unroll
+    for (int u = 0; u < 2; u++)
+#pragma unroll
+        for (int w = 0; w < 2; w++) {
+            const double X = xs[u], Y = ys[w], sg = (u == w) ? 1.0 : -1.0;
+            const double ly = cart_lsum(Y, X), lx = cart_lsum(X, Y);
+            a0 -= sg * ly;     // -ln(Y + R)
+            b0 -= sg * lx;     // -ln(X + R)
+            ax += sg * Y * lx; //  Y ln(X + R)
+            by += sg * X * ly; //  X ln(Y + R)
+            mr -= sg * hypot(X, Y);
+        }
+    K[0] = a0;
+    K[1] = k * h * a0 + ax;
+    K[2] = q * h * a0 + mr;
+    K[3] = b0;
+    K[4] = k * h * b0 + mr;
+    K[5] = q * h * b0 + by;
+}
+
+__global__ void k_cart_fold(int nu, int nphi, double h, double G, double* __restrict__ keff,
+                            double* __restrict__ nsr, double* __restrict__ nsp)
+{
+    const int L = 2 * nu;
+    const long total = (long)L * nphi;
+    const long perk = (long)(2 * nu - 1) * nphi;
+    const double norm = G / ((double)L * nphi), i2h = 0.5 / h;
+    for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+        const int kk = (int)(idx / nphi), qs = (int)(idx % nphi);
+        double Kx = 0.0, Ky = 0.0;
+        if (kk != nu && qs != nphi / 2) {
+            const int k = kk < nu ? kk : kk - L, q = qs < nphi / 2 ? qs : qs - nphi;
+            double c[6], xu[6], xd[6], yu[6], yd[6];
+            cart_cell(k, q, h, c);
+            cart_cell(k + 1, q, h, xu);
+            cart_cell(k - 1, q, h, xd);
+            cart_cell(k, q + 1, h, yu);
+            cart_cell(k, q - 1, h, yd);
+            Kx = c[0] + (xu[1] - xd[1]) * i2h + (yu[2] - yd[2]) * i2h;
+            Ky = c[3] + (xu[4] - xd[4]) * i2h + (yu[5] - yd[5]) * i2h;
+        }
+        if (kk != nu) {
+            const int k = kk < nu ? kk : kk - L;
+            keff[(long)(k + nu - 1) * nphi + qs] = Kx;
+            keff[perk + (long)(k + nu - 1) * nphi + qs] = Ky;
+        }
+        nsr[idx] = Kx * norm;
+        nsp[idx] = Ky * norm;
+    }
+}
+
+cudaError_t launch_cart_fold(int nu, int nphi, double h, double G, double* cells, double* keff, double* nsr,
+                             double* nsp, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(cells, 0, (size_t)6 * (2 * nu + 1) * nphi * sizeof(double), st);
+    if (e != cudaSuccess) return e;
+    const long total = (long)2 * nu * nphi;
+    long blocks = (total + 255) / 256;
+    if (blocks > 65535) blocks = 65535;
+    k_cart_fold<<<(int)blocks, 256, 0, st>>>(nu, nphi, h, G, keff, nsr, nsp);
     return cudaGetLastError();
 }
 

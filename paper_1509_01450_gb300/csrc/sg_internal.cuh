@@ -141,6 +141,10 @@ cudaError_t launch_cells_tpz(int nu, int nphi, double du, int ntpz, double rtol,
 // the particle kinds' tables (sg_kernel_kind 1-3; for 2 with the exact own cell)
 cudaError_t launch_point_cells(int nu, int nphi, double du, int kind, double soften, double rtol, double* cells,
                                int* flag, cudaStream_t st);
+// the folded Cartesian kernels (SG_KERNEL_CARTESIAN) straight into keff and
+// the spectra's inputs; the cell table is zeroed
+cudaError_t launch_cart_fold(int nu, int nphi, double h, double G, double* cells, double* keff, double* nsr,
+                             double* nsp, cudaStream_t st);
 cudaError_t launch_fold(int nu, int nphi, double du, double G, int p, const double* cells, double* keff,
                         double* nsr, double* nsp, cudaStream_t st);
 void gauss_legendre(int n, double* x, double* w);

@@ -36,8 +36,9 @@ SG_KERNEL_PARTICLE = 1       # point mass at each source centre (Eq. 35)
 SG_KERNEL_PARTICLE_PLUS = 2  # point masses plus the own cell's exact terms (Eq. 36-37)
 SG_KERNEL_SOFTENED = 3       # point masses with softening eps = soften r_i (BM08 comparison)
 SG_KERNEL_POTENTIAL = 4      # the potential Phi (into F_r; F_phi zero) with the same construction
+SG_KERNEL_CARTESIAN = 5      # the Cartesian scheme on N_x x (2 N_y) with the y-padding zero
 KERNEL_KINDS = {"sim": SG_KERNEL_SIM, "particle": SG_KERNEL_PARTICLE, "particle+": SG_KERNEL_PARTICLE_PLUS,
-                "softened": SG_KERNEL_SOFTENED, "potential": SG_KERNEL_POTENTIAL}
+                "softened": SG_KERNEL_SOFTENED, "potential": SG_KERNEL_POTENTIAL, "cartesian": SG_KERNEL_CARTESIAN}
 
 
 class BuildOpts(ctypes.Structure):
@@ -134,7 +135,9 @@ class Plan:
         """Build the kernels.  kind: "sim" (default; n_tpz > 0 for the
         trapezoidal rule of Eq. 41-43 with n_tpz trapezoids), "particle",
         "particle+" or "softened" (with soften = eps / r_i), "potential"
-        (Phi into F_r; weight_p = 1 for FP32), or an SG_KERNEL_* code.
+        (Phi into F_r; weight_p = 1 for FP32), "cartesian" (square cells of
+        side du; N_phi = 2 N_y with sigma zero in the last N_y columns), or
+        an SG_KERNEL_* code.
         radial_edges = 1: one-sided radial slopes at the first and last rows
         instead of ghost rows."""
         code = KERNEL_KINDS[kind] if isinstance(kind, str) else int(kind)
