@@ -78,6 +78,9 @@ def _load():
                                             ctypes.c_int]
         lib.sgo_cells_table_pot.restype = ctypes.c_int
         lib.sgo_cells_table_tpz.restype = ctypes.c_int
+        lib.sgo_wedge_table.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                        dp, ctypes.c_int]
+        lib.sgo_wedge_table.restype = ctypes.c_int
         lib.sgo_direct_sum.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, dp, dp, dp, lp, ctypes.c_long,
                                        dp, dp, ctypes.c_int]
         lib.sgo_direct_sum.restype = None
@@ -233,6 +236,59 @@ def potential(sigma: np.ndarray, cells: np.ndarray, grid: Grid, G: float = 1.0):
     Kp, _ = fold(cells, grid.beta, grid.dphi)
     Phi, _ = fft_conv(sigma, Kp, np.zeros_like(Kp), G)
     return grid.r[:, None] * Phi
+
+
+# --------------------------------------------------------------------------
+# The origin wedge (Sec. 3.2.1, third terms of Eq. 27-29)
+# --------------------------------------------------------------------------
+def wedge_cells(nu: int, nphi: int, du: float, pot: bool = False, rtol: float = 2e-14,
+                nthreads: int = 0) -> np.ndarray:
+    """Table [6, Nu, Nphi] of the wedge kernels K-bar seen from grid row i
+    (slots as the cell table: K^{r,0}, K^{r,r}, K^{r,phi}, K^{phi,0},
+    K^{phi,r}, K^{phi,phi}; the potential's three and zeros with pot).  The
+    wedge is [0, r_in] x one azimuthal cell, with r_in the grid's inner face
+    and its centre at r_in / 2 (sg_oracle.c)."""
+    out = np.zeros((NC, nu, nphi))
+    bad = _load().sgo_wedge_table(int(nu), int(nphi), float(du), float(rtol), int(bool(pot)), _dp(out),
+                                  int(nthreads))
+    if bad:
+        raise RuntimeError(f"oracle quadrature did not converge for {bad} integrals")
+    return out
+
+
+def wedge_sums(sigma: np.ndarray, sigma_w: np.ndarray, wcells: np.ndarray, grid: Grid, G: float = 1.0):
+    """The third terms of Eq. 27-29 (and A8-A10) as literal single sums over
+    the wedge cells j':
+        F_i,j += G sum_j' [sigma_w[j'] Kb^{.,0}[i, j - j'] + r_i dr_w[j'] Kb^{.,r}[i, j - j']
+                            + dphi_w[j'] Kb^{.,phi}[i, j - j']],
+    with the wedge's radial slope one-sided toward the first grid row,
+    dr_w = (sigma[0] - sigma_w) / (r_0 - r_in / 2), and its azimuthal slope
+    central and periodic."""
+    nu, nphi = sigma.shape
+    sigma_w = np.asarray(sigma_w, dtype=np.float64)
+    r_w = 0.5 * grid.faces[0]
+    dr = (np.asarray(sigma[0], dtype=np.float64) - sigma_w) / (grid.r[0] - r_w)
+    dp = (np.roll(sigma_w, -1) - np.roll(sigma_w, 1)) / (2.0 * grid.dphi)
+    Fr = np.zeros((nu, nphi))
+    Fp = np.zeros((nu, nphi))
+    j = np.arange(nphi)
+    ri = grid.r[:, None]
+    for jp in range(nphi):
+        col = (j - jp) % nphi
+        Fr += sigma_w[jp] * wcells[0][:, col] + ri * dr[jp] * wcells[1][:, col] + dp[jp] * wcells[2][:, col]
+        Fp += sigma_w[jp] * wcells[3][:, col] + ri * dr[jp] * wcells[4][:, col] + dp[jp] * wcells[5][:, col]
+    return G * Fr, G * Fp
+
+
+def wedge_forces(sigma: np.ndarray, sigma_w: np.ndarray, cells: np.ndarray, wcells: np.ndarray, grid: Grid,
+                 G: float = 1.0):
+    """Forces on the grid with the origin wedge below its first row: the grid's
+    own sums with one-sided radial slopes at its first and last rows (no ghost
+    rows: the region below the first row is the wedge's) plus the wedge's
+    single sums."""
+    Fr, Fp = onesided_forces(sigma, cells, grid, G)
+    Wr, Wp = wedge_sums(sigma, sigma_w, wcells, grid, G)
+    return Fr + Wr, Fp + Wp
 
 
 def kernel_cells_tpz(nu: int, nphi: int, du: float, n_tpz: int, rtol: float = 2e-14, nthreads: int = 0) -> np.ndarray:

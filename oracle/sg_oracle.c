@@ -584,6 +584,61 @@ static int cells_table_of(int nu, int nphi, double du, double rtol, int pot, dou
 }
 
 /*
+ * The origin wedge R^_j' = [0, r_in] x [phi_{j'-1/2}, phi_{j'+1/2}] (Sec. 3.2.1
+ * and the third terms of Eq. 27-29, kernels K-bar) seen from the centre of
+ * grid row i: the same six integrals over eta in [0, eta_w], eta_w = r_in / r_i
+ * = 2 / (beta^i (1 + beta)), with the slope factors measured from the wedge's
+ * centre eta_w / 2 (the arithmetic mean of its faces 0 and r_in).  The wedge
+ * lies inside every target radius, so no integrand is singular.  Table
+ * out[c][i * Nphi + q], i in [0, Nu), q in [0, Nphi), mirrored as
+ * sgo_cells_table; returns the number of integrals that ran out of panels.
+ */
+static int wedge_cell_of(double du, int nphi, int i, int q, double rtol, int pot, double out6[NC])
+{
+    int qs = ((q % nphi) + nphi) % nphi;
+    if (2 * qs > nphi) qs -= nphi;
+    int bad = 0;
+    cell_t cell;
+    cell_setup(&cell, du, nphi, 1, qs, rtol, &bad); /* azimuth and tolerances; eta limits below */
+    const double beta = exp(du), eta_w = 2.0 / (exp(du * i) * (1.0 + beta));
+    cell.eta_lo = 0.0;
+    cell.eta_hi = eta_w;
+    cell.eta_c = 0.5 * eta_w;
+    cell.em1 = 0.5 * eta_w - 1.0;
+    cell.hw = 0.5 * eta_w;
+    cell.self = 0;
+    cell.pot = pot;
+    double bp[2] = {-cell.half_dphi, cell.half_dphi}, abs_[NV], out[NV];
+    int st = adapt(f_xi, &cell, bp, 2, rtol, 0.0, 1, out, abs_);
+    if (st < 0) bad++;
+    for (int c = 0; c < NC; c++) out6[c] = out[c];
+    return bad;
+}
+
+int sgo_wedge_table(int nu, int nphi, double du, double rtol, int pot, double* out, int nthreads)
+{
+    gl_init();
+    long per = (long)nu * nphi, nq = nphi / 2 + 1;
+    int bad = 0;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : bad)
+#endif
+    for (long idx = 0; idx < nu * nq; idx++) {
+        int i = (int)(idx / nq), q = (int)(idx % nq);
+        double v[NC];
+        bad += wedge_cell_of(du, nphi, i, q, rtol, pot, v);
+        long row = (long)i * nphi;
+        int qm = (nphi - q) % nphi;
+        for (int c = 0; c < NC; c++) {
+            out[c * per + row + q] = v[c];
+            if (qm != q) out[c * per + row + qm] = (c == 2 || c == 3 || c == 4) ? -v[c] : v[c];
+        }
+    }
+    return bad;
+}
+
+/*
  * The trapezoidal form of the kernels (Eq. 41-43 for K^{r,0}, K^{r,r},
  * K^{r,phi}, the same rule for K^{phi,phi} of App. A): for every cell but
  * the own one, the eta-integrals at the N_tpz + 1 azimuths
