@@ -136,7 +136,16 @@ typedef struct {
                       mode runs after the column pass (and its transpose in
                       the adjoint), and the forces keep second order up to
                       the radial edges when sigma does not vanish there */
-    int reserved[2];
+    int wedge;     /* 0 (default); 1: the origin wedge of Sec. 3.2.1, the cells
+                      [0, r_in] x [phi_{j-1/2}, phi_{j+1/2}] below the first
+                      row (r_in = e^{u_min}), enter through the third terms of
+                      Eq. 27-29: single sums over N_phi wedge densities given
+                      per call to sg_forces_wedge.  The wedge's density is its
+                      value at r_in / 2, its radial slope one-sided toward
+                      the first row, its azimuthal slope central.  Needs
+                      radial_edges = 1 (the wedge replaces the inner ghost
+                      row) and SG_KERNEL_SIM or SG_KERNEL_POTENTIAL */
+    int reserved[1];
 } sg_build_opts;
 
 /*
@@ -169,8 +178,12 @@ sg_status sg_plan_create(sg_plan** out, int N_u, int N_phi, double u_min, double
  * could not reach the tolerance within the quadrature's budget, and
  * SG_ERR_ARG for an unknown kind, soften <= 0 with SG_KERNEL_SOFTENED,
  * n_tpz outside [0, 1024] (or n_tpz > 0 with another kind than
- * SG_KERNEL_SIM), radial_edges not 0 or 1, |weight_p| > 8, or weight_p or
- * radial_edges not 0 with SG_KERNEL_CARTESIAN.
+ * SG_KERNEL_SIM), radial_edges not 0 or 1, |weight_p| > 8, weight_p or
+ * radial_edges not 0 with SG_KERNEL_CARTESIAN, or wedge not 0 or 1 (1 without
+ * radial_edges = 1, or with a kind other than SG_KERNEL_SIM and
+ * SG_KERNEL_POTENTIAL).  wedge = 1 also allocates the plan's wedge tables,
+ * 4 (N_phi/2 + 1) N_u values of the working dtype, and for the build an FP64
+ * scratch of 6 N_u N_phi values.
  * Allocates and frees FP64 scratch for the spectra; radial_edges = 1 also
  * allocates the plan's edge tables, 2 (N_phi/2 + 1)(2 N_u + 1) values of
  * the working dtype.
@@ -195,6 +208,26 @@ sg_status sg_forces(sg_plan* plan, const void* sigma, void* F_r, void* F_phi, cu
  */
 sg_status sg_forces_backward(sg_plan* plan, const void* gF_r, const void* gF_phi, void* gsigma,
                              cudaStream_t stream);
+
+/*
+ * Forces with the origin wedge (a plan built with wedge = 1): as sg_forces,
+ * plus the wedge's single sums (the third terms of Eq. 27-29 and A8-A10)
+ * over sigma_w, the N_phi wedge densities (device, working dtype, contiguous,
+ * aligned to the element size; the caller keeps ownership).  The update runs
+ * between the column and inverse-row passes.  sg_forces, sg_forces_timed,
+ * sg_forces_backward, sg_forces_host and sg_forces_batched return
+ * SG_ERR_UNSUPPORTED on such a plan.  SG_ERR_ARG if the plan has no wedge,
+ * for null, misaligned or aliased buffers.
+ */
+sg_status sg_forces_wedge(sg_plan* plan, const void* sigma, const void* sigma_w, void* F_r, void* F_phi,
+                          cudaStream_t stream);
+
+/*
+ * The adjoint of sg_forces_wedge: gsigma (N_u x N_phi) and gsigma_w (N_phi)
+ * from gF_r, gF_phi.  Same rules as sg_forces_backward.
+ */
+sg_status sg_forces_wedge_backward(sg_plan* plan, const void* gF_r, const void* gF_phi, void* gsigma,
+                                   void* gsigma_w, cudaStream_t stream);
 
 /*
  * Same as sg_forces with HOST buffers, then synchronises the stream and
@@ -294,9 +327,10 @@ sg_status sg_plan_cells(sg_plan* plan, double* cells_h, cudaStream_t stream);
 /*
  * Convergence report of the last sg_kernels_build: report[0] = bit 1 if some
  * cell integrals stopped at the quadrature budget, bit 2 if the self-cell
- * rule did not reach its tolerance; report[1] = number of such offsets;
- * report[2], report[3] = (k, q) of one of them.  All zero after a clean
- * build.
+ * rule did not reach its tolerance, bit 4 if some wedge integrals stopped at
+ * the budget; report[1] = number of such offsets; report[2], report[3] =
+ * (k, q) of one of them (for a wedge cell: (target row, q)).  All zero after
+ * a clean build.
  */
 sg_status sg_plan_build_report(const sg_plan* plan, int report[4]);
 

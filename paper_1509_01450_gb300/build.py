@@ -19,7 +19,7 @@ OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsgdisk.so")
 # fftconv_lg<LG>.cu compile the fixed-length instances of fftconv.cu's pass
 # kernels, one transform length each, in parallel with the rest
-SOURCES = ["api.cu", "kbuild.cu", "fftconv.cu", "noalloc.cu"] + [f"fftconv_lg{lg}.cu" for lg in range(8, 14)]
+SOURCES = ["api.cu", "kbuild.cu", "fftconv.cu", "noalloc.cu", "wedge.cu"] + [f"fftconv_lg{lg}.cu" for lg in range(8, 14)]
 HEADERS = ["sg_common.cuh", "sg_internal.cuh", "fftconv.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

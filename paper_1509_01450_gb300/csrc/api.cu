@@ -41,7 +41,7 @@ static void free_plan(sg_plan* p)
     if (p->bfork) cudaEventDestroy(p->bfork);
     if (p->bstream) cudaStreamDestroy(p->bstream);
     void* bufs[] = {p->tw, p->wa, p->wb, p->wc, p->kr, p->kp, p->wpre, p->wpost, p->tw64, p->cells, p->keff,
-                    p->h_sigma, p->h_fr, p->h_fp, p->derr, p->egr, p->egp};
+                    p->h_sigma, p->h_fr, p->h_fp, p->derr, p->egr, p->egp, p->wtab, p->wtmp};
     for (void* b : bufs)
         if (b) cudaFree(b);
     free(p);
@@ -220,7 +220,7 @@ sg_status sg_plan_save(const sg_plan* p, const char* path, cudaStream_t stream)
 {
     if (!p || !path) return SG_ERR_ARG;
     if (!p->built) return SG_ERR_NOT_BUILT;
-    if (p->edges) return SG_ERR_UNSUPPORTED;  // the file holds no edge tables
+    if (p->edges || p->wedge) return SG_ERR_UNSUPPORTED;  // the file holds no edge or wedge tables
     const size_t kb = spectrum_bytes(p), wb = (size_t)p->nu * p->elem;
     std::vector<unsigned char> buf(2 * kb + 2 * wb);
     SG_TRY(cudaMemcpyAsync(buf.data(), p->kr, kb, cudaMemcpyDeviceToHost, stream));
@@ -297,7 +297,7 @@ sg_status sg_kernels_build(sg_plan* p, const sg_build_opts* opts, cudaStream_t s
 {
     if (!p) return SG_ERR_ARG;
     double rtol = 1e-14, soften = 0.0;
-    int wp = 0, kind = SG_KERNEL_SIM, ntpz = 0, edges = 0;
+    int wp = 0, kind = SG_KERNEL_SIM, ntpz = 0, edges = 0, wedge = 0;
     if (opts) {
         if (opts->rtol > 0.0) rtol = opts->rtol;
         wp = opts->weight_p;
@@ -311,6 +311,11 @@ sg_status sg_kernels_build(sg_plan* p, const sg_build_opts* opts, cudaStream_t s
         edges = opts->radial_edges;
         if (edges != 0 && edges != 1) return SG_ERR_ARG;
         if (kind == SG_KERNEL_CARTESIAN && (wp != 0 || edges != 0)) return SG_ERR_ARG;
+        wedge = opts->wedge;
+        if (wedge != 0 && wedge != 1) return SG_ERR_ARG;
+        // the wedge takes the place of the inner ghost row: one-sided edge
+        // slopes, and the kinds whose cells are integrals over the source
+        if (wedge && (!edges || (kind != SG_KERNEL_SIM && kind != SG_KERNEL_POTENTIAL))) return SG_ERR_ARG;
     }
     // beta^{p (i - i_ref)} must stay in range for both dtypes
     if (fabs((double)wp * p->du * p->nu) > 60.0) return SG_ERR_UNSUPPORTED;
@@ -361,13 +366,22 @@ sg_status sg_kernels_build(sg_plan* p, const sg_build_opts* opts, cudaStream_t s
         sg_status st = SG_OK;
         if ((!p->egr && (st = dev_alloc(p, &p->egr, n))) || (!p->egp && (st = dev_alloc(p, &p->egp, n)))) return st;
     }
+    p->wedge = 0;
+    if (wedge) {
+        const size_t n = (size_t)4 * (nphi / 2 + 1) * nu * p->elem;
+        sg_status st = SG_OK;
+        if ((!p->wtab && (st = dev_alloc(p, &p->wtab, n))) ||
+            (!p->wtmp && (st = dev_alloc(p, &p->wtmp, (size_t)(nphi / 2) * sizeof(double2)))))
+            return st;
+    }
     int* flag = nullptr;
-    double *nsr = nullptr, *nsp = nullptr;
+    double *nsr = nullptr, *nsp = nullptr, *wcells = nullptr;
     double2* W = nullptr;
     sg_status ret = SG_OK;
     if (cudaMalloc(&flag, 4 * sizeof(int)) != cudaSuccess || cudaMalloc(&nsr, (size_t)L * nphi * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&nsp, (size_t)L * nphi * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&W, (size_t)(nphi / 2 + 1) * L * sizeof(double2)) != cudaSuccess) {
+        cudaMalloc(&W, (size_t)(nphi / 2 + 1) * L * sizeof(double2)) != cudaSuccess ||
+        (wedge && cudaMalloc(&wcells, (size_t)6 * nu * nphi * sizeof(double)) != cudaSuccess)) {
         cudaGetLastError();
         ret = SG_ERR_ALLOC;
         goto done;
@@ -396,6 +410,14 @@ sg_status sg_kernels_build(sg_plan* p, const sg_build_opts* opts, cudaStream_t s
         ret = SG_ERR_CUDA;
         goto done;
     }
+    if (wedge && (p->dtype == SG_F32
+                      ? launch_wedge_tables<float>(nu, nphi, p->du, p->G, rtol, kind == SG_KERNEL_POTENTIAL, wcells,
+                                                   p->tw64, (float*)p->wtab, flag, stream)
+                      : launch_wedge_tables<double>(nu, nphi, p->du, p->G, rtol, kind == SG_KERNEL_POTENTIAL, wcells,
+                                                    p->tw64, (double*)p->wtab, flag, stream)) != cudaSuccess) {
+        ret = SG_ERR_CUDA;
+        goto done;
+    }
     {
         PlanView v = view(p);
         cudaError_t e = p->dtype == SG_F32
@@ -414,9 +436,11 @@ sg_status sg_kernels_build(sg_plan* p, const sg_build_opts* opts, cudaStream_t s
         }
         p->built = 1;
         p->edges = edges;
+        p->wedge = wedge;
         if (p->report[0]) ret = SG_ERR_TIMEOUT;
     }
 done:
+    if (wcells) cudaFree(wcells);
     if (flag) cudaFree(flag);
     if (nsr) cudaFree(nsr);
     if (nsp) cudaFree(nsp);
@@ -431,7 +455,44 @@ static sg_status check_fields(const sg_plan* p, const void* a, const void* b, co
     const void* ptrs[3] = {a, b, c};
     for (const void* q : ptrs)
         if (!q || ((uintptr_t)q & 15)) return SG_ERR_ARG;
+    if (p->wedge) return SG_ERR_UNSUPPORTED;  // the wedge densities come through sg_forces_wedge
     return SG_OK;
+}
+
+sg_status sg_forces_wedge(sg_plan* p, const void* sigma, const void* sigma_w, void* Fr, void* Fp, cudaStream_t stream)
+{
+    if (!p) return SG_ERR_ARG;
+    if (!p->built) return SG_ERR_NOT_BUILT;
+    if (!p->wedge) return SG_ERR_ARG;
+    const void* ptrs[3] = {sigma, Fr, Fp};
+    for (const void* q : ptrs)
+        if (!q || ((uintptr_t)q & 15)) return SG_ERR_ARG;
+    if (!sigma_w || ((uintptr_t)sigma_w % p->elem)) return SG_ERR_ARG;
+    if (sigma == Fr || sigma == Fp || Fr == Fp || sigma_w == Fr || sigma_w == Fp) return SG_ERR_ARG;
+    PlanView v = view(p);
+    v.sigw = sigma_w;
+    cudaError_t e = p->dtype == SG_F32 ? launch_forward<float>(v, (const float*)sigma, (float*)Fr, (float*)Fp, stream)
+                                       : launch_forward<double>(v, (const double*)sigma, (double*)Fr, (double*)Fp, stream);
+    return e == cudaSuccess ? SG_OK : SG_ERR_CUDA;
+}
+
+sg_status sg_forces_wedge_backward(sg_plan* p, const void* gr, const void* gp, void* gs, void* gs_w,
+                                   cudaStream_t stream)
+{
+    if (!p) return SG_ERR_ARG;
+    if (!p->built) return SG_ERR_NOT_BUILT;
+    if (!p->wedge) return SG_ERR_ARG;
+    const void* ptrs[3] = {gr, gp, gs};
+    for (const void* q : ptrs)
+        if (!q || ((uintptr_t)q & 15)) return SG_ERR_ARG;
+    if (!gs_w || ((uintptr_t)gs_w % p->elem)) return SG_ERR_ARG;
+    if (gs == gr || gs == gp || gs_w == gr || gs_w == gp || gs_w == gs) return SG_ERR_ARG;
+    PlanView v = view(p);
+    v.gsigw = gs_w;
+    cudaError_t e = p->dtype == SG_F32
+                        ? launch_backward<float>(v, (const float*)gr, (const float*)gp, (float*)gs, stream)
+                        : launch_backward<double>(v, (const double*)gr, (const double*)gp, (double*)gs, stream);
+    return e == cudaSuccess ? SG_OK : SG_ERR_CUDA;
 }
 
 sg_status sg_forces(sg_plan* p, const void* sigma, void* Fr, void* Fp, cudaStream_t stream)
@@ -501,6 +562,7 @@ sg_status sg_forces_host(sg_plan* p, const void* sigma_h, void* Fr_h, void* Fp_h
 {
     if (!p || !sigma_h || !Fr_h || !Fp_h) return SG_ERR_ARG;
     if (!p->built) return SG_ERR_NOT_BUILT;
+    if (p->wedge) return SG_ERR_UNSUPPORTED;
     const size_t bytes = (size_t)p->nu * p->nphi * p->elem;
     // Pinned, mapped buffers: the row pass reads sigma and the inverse-row
     // pass writes F_r, F_phi over the host link directly (no staging copies).

@@ -1797,6 +1797,7 @@ cudaError_t launch_forward(const PlanView& p, const T* sigma, T* Fr, T* Fp, cuda
         });
     }
     if (p.edges && !edges_done && (err = launch_edges<T>(p, false, st)) != cudaSuccess) return err;
+    if (p.wedge && (err = launch_wedge<T>(p, false, st)) != cudaSuccess) return err;
     if (ev && (err = cudaEventRecord(ev[2], st)) != cudaSuccess) return err;
     {
         PassRange range_("sg forward inverse rows");
@@ -1879,6 +1880,7 @@ cudaError_t launch_backward(const PlanView& p, const T* gr, const T* gp, T* gs, 
         });
     }
     if (p.edges && !edges_done && (err = launch_edges<T>(p, true, st)) != cudaSuccess) return err;
+    if (p.wedge && (err = launch_wedge<T>(p, true, st)) != cudaSuccess) return err;
     {
         PassRange range_("sg adjoint inverse rows");
         Shape s = shape_for<V>(p.nphi, sizeof(T) == 8 ? 64 : 256);

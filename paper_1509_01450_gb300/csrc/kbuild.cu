@@ -187,6 +187,99 @@ __device__ __forceinline__ double warp_sum(double v)
 #define SG_STACK 64
 #define SG_MAXRECT 20000
 
+// The six integrals over one source cell, (eta - eta_c, xi - xi_c) in
+// [-hw, hw] x [-dphi/2, dphi/2] (sc, cc = sin, cos xi_c; em1 = eta_c - 1),
+// by one warp: 8- and 12-point Gauss-Legendre products per rectangle,
+// bisected until they agree.  Returns 1 if the rectangle budget ran out.
+__device__ int cell_quad(double eta_c, double em1, double hw, double sc, double cc, double dphi, double rtol, int pot,
+                         double4_16a* stack, int lane, double res[6])
+{
+    int sp = 0, nrect = 0, bad = 0;
+#pragma unroll
+    for (int c6 = 0; c6 < 6; c6++) res[c6] = 0.0;
+    // rectangles in (eta - eta_c, xi - xi_c)
+    stack[0] = make_double4_16a(-hw, hw, -0.5 * dphi, 0.5 * dphi);
+    sp = 1;
+    while (sp > 0) {
+        __syncwarp();
+        const double4_16a R = stack[--sp];
+        __syncwarp();
+        nrect++;
+        const double he = 0.5 * (R.y - R.x), me = 0.5 * (R.y + R.x);
+        const double hx = 0.5 * (R.w - R.z), mx = 0.5 * (R.w + R.z);
+        double I8[6] = {0, 0, 0, 0, 0, 0}, I12[6] = {0, 0, 0, 0, 0, 0}, A12[6] = {0, 0, 0, 0, 0, 0};
+        for (int p = lane; p < 64; p += 32) {
+            const int a = p >> 3, b = p & 7;
+            const double del = me + he * c_x8[a], t = mx + hx * c_x8[b];
+            double st, ct;
+            sincos(t, &st, &ct);
+            acc6(del, eta_c, em1, t, ct * cc - st * sc, st * cc + ct * sc, he * hx * c_w8[a] * c_w8[b], I8,
+                 nullptr, pot);
+        }
+        for (int p = lane; p < 144; p += 32) {
+            const int a = p / 12, b = p % 12;
+            const double del = me + he * c_x12[a], t = mx + hx * c_x12[b];
+            double st, ct;
+            sincos(t, &st, &ct);
+            acc6(del, eta_c, em1, t, ct * cc - st * sc, st * cc + ct * sc, he * hx * c_w12[a] * c_w12[b], I12,
+                 A12, pot);
+        }
+        bool ok = true;
+#pragma unroll
+        for (int c6 = 0; c6 < 6; c6++) {
+            I8[c6] = warp_sum(I8[c6]);
+            I12[c6] = warp_sum(I12[c6]);
+            A12[c6] = warp_sum(A12[c6]);
+        }
+#pragma unroll
+        for (int c6 = 0; c6 < 6; c6++) {
+            // the radial and azimuthal kernels of each kind form one force
+            // vector: measure both against its size (so a component that
+            // nearly vanishes, on the curve eta cos xi = 1, needs no more
+            // than the vector's precision), plus the rounding level of a
+            // 144-term sum
+            const double scale = A12[c6] + A12[(c6 + 3) % 6];
+            if (fabs(I12[c6] - I8[c6]) > (rtol + 64.0 * 2.220446049250313e-16) * scale) ok = false;
+        }
+        if (!ok && (sp + 4 > SG_STACK || nrect >= SG_MAXRECT)) {
+            ok = true;
+            bad = 1;
+        }
+        if (ok) {
+#pragma unroll
+            for (int c6 = 0; c6 < 6; c6++) res[c6] += I12[c6];
+        } else {
+            // split the side that is longer in physical length (the
+            // azimuthal side measures (xi extent) x eta); both when the
+            // rectangle is roughly square
+            const double le = R.y - R.x, lx = (R.w - R.z) * (eta_c + me);
+            __syncwarp();
+            if (le > 2.0 * lx) {
+                if (lane == 0) {
+                    stack[sp + 0] = make_double4_16a(R.x, me, R.z, R.w);
+                    stack[sp + 1] = make_double4_16a(me, R.y, R.z, R.w);
+                }
+                sp += 2;
+            } else if (lx > 2.0 * le) {
+                if (lane == 0) {
+                    stack[sp + 0] = make_double4_16a(R.x, R.y, R.z, mx);
+                    stack[sp + 1] = make_double4_16a(R.x, R.y, mx, R.w);
+                }
+                sp += 2;
+            } else {
+                if (lane == 0) {
+                    stack[sp + 0] = make_double4_16a(R.x, me, R.z, mx);
+                    stack[sp + 1] = make_double4_16a(me, R.y, R.z, mx);
+                    stack[sp + 2] = make_double4_16a(R.x, me, mx, R.w);
+                    stack[sp + 3] = make_double4_16a(me, R.y, mx, R.w);
+                }
+                sp += 4;
+            }
+        }
+    }
+    return bad;
+}
+
 __global__ void __launch_bounds__(128) k_cells(int nu, int nphi, double du, double rtol, double* __restrict__ cells,
                                                int* __restrict__ flag, int pot)
 {
@@ -208,88 +301,8 @@ __global__ void __launch_bounds__(128) k_cells(int nu, int nphi, double du, doub
         // exact at the quarter points
         double sc, cc;
         sincospi(-2.0 * q / nphi, &sc, &cc);
-        double res[6] = {0, 0, 0, 0, 0, 0};
-        int sp = 0, nrect = 0, bad = 0;
-        // rectangles in (eta - eta_c, xi - xi_c)
-        stack[0] = make_double4_16a(-hw, hw, -0.5 * dphi, 0.5 * dphi);
-        sp = 1;
-        while (sp > 0) {
-            __syncwarp();
-            const double4_16a R = stack[--sp];
-            __syncwarp();
-            nrect++;
-            const double he = 0.5 * (R.y - R.x), me = 0.5 * (R.y + R.x);
-            const double hx = 0.5 * (R.w - R.z), mx = 0.5 * (R.w + R.z);
-            double I8[6] = {0, 0, 0, 0, 0, 0}, I12[6] = {0, 0, 0, 0, 0, 0}, A12[6] = {0, 0, 0, 0, 0, 0};
-            for (int p = lane; p < 64; p += 32) {
-                const int a = p >> 3, b = p & 7;
-                const double del = me + he * c_x8[a], t = mx + hx * c_x8[b];
-                double st, ct;
-                sincos(t, &st, &ct);
-                acc6(del, eta_c, em1, t, ct * cc - st * sc, st * cc + ct * sc, he * hx * c_w8[a] * c_w8[b], I8,
-                     nullptr, pot);
-            }
-            for (int p = lane; p < 144; p += 32) {
-                const int a = p / 12, b = p % 12;
-                const double del = me + he * c_x12[a], t = mx + hx * c_x12[b];
-                double st, ct;
-                sincos(t, &st, &ct);
-                acc6(del, eta_c, em1, t, ct * cc - st * sc, st * cc + ct * sc, he * hx * c_w12[a] * c_w12[b], I12,
-                     A12, pot);
-            }
-            bool ok = true;
-#pragma unroll
-            for (int c6 = 0; c6 < 6; c6++) {
-                I8[c6] = warp_sum(I8[c6]);
-                I12[c6] = warp_sum(I12[c6]);
-                A12[c6] = warp_sum(A12[c6]);
-            }
-#pragma unroll
-            for (int c6 = 0; c6 < 6; c6++) {
-                // the radial and azimuthal kernels of each kind form one force
-                // vector: measure both against its size (so a component that
-                // nearly vanishes, on the curve eta cos xi = 1, needs no more
-                // than the vector's precision), plus the rounding level of a
-                // 144-term sum
-                const double scale = A12[c6] + A12[(c6 + 3) % 6];
-                if (fabs(I12[c6] - I8[c6]) > (rtol + 64.0 * 2.220446049250313e-16) * scale) ok = false;
-            }
-            if (!ok && (sp + 4 > SG_STACK || nrect >= SG_MAXRECT)) {
-                ok = true;
-                bad = 1;
-            }
-            if (ok) {
-#pragma unroll
-                for (int c6 = 0; c6 < 6; c6++) res[c6] += I12[c6];
-            } else {
-                // split the side that is longer in physical length (the
-                // azimuthal side measures (xi extent) x eta); both when the
-                // rectangle is roughly square
-                const double le = R.y - R.x, lx = (R.w - R.z) * (eta_c + me);
-                __syncwarp();
-                if (le > 2.0 * lx) {
-                    if (lane == 0) {
-                        stack[sp + 0] = make_double4_16a(R.x, me, R.z, R.w);
-                        stack[sp + 1] = make_double4_16a(me, R.y, R.z, R.w);
-                    }
-                    sp += 2;
-                } else if (lx > 2.0 * le) {
-                    if (lane == 0) {
-                        stack[sp + 0] = make_double4_16a(R.x, R.y, R.z, mx);
-                        stack[sp + 1] = make_double4_16a(R.x, R.y, mx, R.w);
-                    }
-                    sp += 2;
-                } else {
-                    if (lane == 0) {
-                        stack[sp + 0] = make_double4_16a(R.x, me, R.z, mx);
-                        stack[sp + 1] = make_double4_16a(me, R.y, R.z, mx);
-                        stack[sp + 2] = make_double4_16a(R.x, me, mx, R.w);
-                        stack[sp + 3] = make_double4_16a(me, R.y, mx, R.w);
-                    }
-                    sp += 4;
-                }
-            }
-        }
+        double res[6];
+        const int bad = cell_quad(eta_c, em1, hw, sc, cc, dphi, rtol, pot, stack, lane, res);
         if (lane == 0) {
             const long row = (long)(k + nu) * nphi;
             const int qm = (nphi - q) & (nphi - 1);
@@ -714,6 +727,119 @@ cudaError_t launch_point_cells(int nu, int nphi, double du, int kind, double sof
     }
     return cudaGetLastError();
 }
+
+// k_wedge_cells: the origin wedge [0, r_in] x [phi_{j'-1/2}, phi_{j'+1/2}]
+// below the grid (Sec. 3.2.1; the kernels K-bar of the third terms of
+// Eq. 27-29) seen from the centre of grid row i: the six integrals of k_cells
+// over eta in [0, eta_w], eta_w = r_in / r_i = 2 / (beta^i (1 + beta)), the
+// slope factors measured from the wedge centre eta_w / 2 (the mean of its
+// faces 0 and r_in).  The wedge lies inside every target radius, so no
+// integrand is singular.  Table [6][N_u][N_phi], mirrored in q as k_cells.
+__global__ void __launch_bounds__(128) k_wedge_cells(int nu, int nphi, double du, double rtol, int pot,
+                                                     double* __restrict__ wcells, int* __restrict__ flag)
+{
+    __shared__ double4_16a stack_all[4][SG_STACK];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    double4_16a* stack = stack_all[wib];
+    const double beta = exp(du), dphi = 2.0 * M_PI / nphi;
+    const int nq = nphi / 2 + 1;
+    const long noff = (long)nu * nq, per = (long)nu * nphi;
+    for (long off = (long)blockIdx.x * 4 + wib; off < noff; off += (long)gridDim.x * 4) {
+        const int i = (int)(off / nq), q = (int)(off % nq);
+        const double eta_w = 2.0 / (exp(du * i) * (1.0 + beta)), eta_c = 0.5 * eta_w;
+        double sc, cc;
+        sincospi(-2.0 * q / nphi, &sc, &cc);
+        double res[6];
+        const int bad = cell_quad(eta_c, eta_c - 1.0, eta_c, sc, cc, dphi, rtol, pot, stack, lane, res);
+        if (lane == 0) {
+            const long row = (long)i * nphi;
+            const int qm = (nphi - q) & (nphi - 1);
+#pragma unroll
+            for (int c6 = 0; c6 < 6; c6++) {
+                wcells[c6 * per + row + q] = res[c6];
+                const bool odd = (c6 == 2 || c6 == 3 || c6 == 4);
+                if (qm != q) wcells[c6 * per + row + qm] = odd ? -res[c6] : res[c6];
+            }
+            if (bad) {
+                atomicOr(flag, 4);
+                atomicAdd(flag + 1, 1);
+                atomicExch(flag + 2, i);
+                atomicExch(flag + 3, q);
+            }
+        }
+    }
+}
+
+// k_wedge_spec: the wedge's single sums as two phi-convolutions per target
+// row, one with sigma_w and one with the first grid row sigma_0 (through the
+// wedge's one-sided radial slope (sigma_0 - sigma_w) / (r_0 - r_in / 2),
+// times r_i: rho_i = r_i / (r_0 - r_in / 2) = beta^{i-1} (1 + beta)), the
+// azimuthal slope folded in:
+//   W[i, q] = Kb^{.,0} + (Kb^{.,phi}[q+1] - Kb^{.,phi}[q-1]) / 2 dphi - rho_i Kb^{.,r},
+//   V[i, q] = rho_i Kb^{.,r}.
+// Their phi-DFTs, G / N_phi times, are real for the radial component (even in
+// q) and -i times real for the azimuthal one (odd): tables
+// tab[t][m][i], t = Wr, Wphi, Vr, Vphi, m in [0, N_phi/2].  One block per
+// row, one thread per mode; FP64 sums over q in [0, N_phi/2] with the mirror.
+template <typename T>
+__global__ void k_wedge_spec(int nu, int nphi, double du, double G, const double* __restrict__ wcells,
+                             const double2* __restrict__ tw64, T* __restrict__ tab)
+{
+    const int i = blockIdx.x, half = nphi / 2;
+    const long per = (long)nu * nphi;
+    const double* K[6];
+#pragma unroll
+    for (int c6 = 0; c6 < 6; c6++) K[c6] = wcells + c6 * per + (long)i * nphi;
+    const double beta = exp(du), rho = exp(du * (i - 1)) * (1.0 + beta), i2d = nphi / (4.0 * M_PI);
+    const int stride = SG_NMAX / nphi;
+    const double sc = G / nphi;
+    const long tsz = (long)(half + 1) * nu;
+    auto Wr = [&](int q) {
+        const int qp = (q + 1) & (nphi - 1), qm = (q - 1) & (nphi - 1);
+        return K[0][q] + (K[2][qp] - K[2][qm]) * i2d - rho * K[1][q];
+    };
+    auto Wp = [&](int q) {
+        const int qp = (q + 1) & (nphi - 1), qm = (q - 1) & (nphi - 1);
+        return K[3][q] + (K[5][qp] - K[5][qm]) * i2d - rho * K[4][q];
+    };
+    for (int m = threadIdx.x; m <= half; m += blockDim.x) {
+        const double sg = (m & 1) ? -1.0 : 1.0;
+        double wr = Wr(0) + sg * Wr(half), vr = rho * (K[1][0] + sg * K[1][half]), wp = 0.0, vp = 0.0;
+        for (int q = 1; q < half; q++) {
+            const double2 w = tw64[(long)((m * q) & (nphi - 1)) * stride];  // e^{-2 pi i m q / N_phi}
+            wr += 2.0 * Wr(q) * w.x;
+            vr += 2.0 * rho * K[1][q] * w.x;
+            wp -= 2.0 * Wp(q) * w.y;
+            vp -= 2.0 * rho * K[4][q] * w.y;
+        }
+        const long at = (long)m * nu + i;
+        tab[0 * tsz + at] = (T)(sc * wr);
+        tab[1 * tsz + at] = (T)(sc * wp);
+        tab[2 * tsz + at] = (T)(sc * vr);
+        tab[3 * tsz + at] = (T)(sc * vp);
+    }
+}
+
+template <typename T>
+cudaError_t launch_wedge_tables(int nu, int nphi, double du, double G, double rtol, int pot, double* wcells,
+                                const void* tw64, T* tab, int* flag, cudaStream_t st)
+{
+    cudaError_t e = upload_rules();
+    if (e != cudaSuccess) return e;
+    int dev, nsm;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const long noff = (long)nu * (nphi / 2 + 1);
+    long blocks = (noff + 3) / 4;
+    if (blocks > (long)nsm * 32) blocks = (long)nsm * 32;
+    k_wedge_cells<<<(int)blocks, 128, 0, st>>>(nu, nphi, du, rtol, pot, wcells, flag);
+    k_wedge_spec<T><<<nu, 256, 0, st>>>(nu, nphi, du, G, wcells, (const double2*)tw64, tab);
+    return cudaGetLastError();
+}
+template cudaError_t launch_wedge_tables<float>(int, int, double, double, double, int, double*, const void*, float*,
+                                                int*, cudaStream_t);
+template cudaError_t launch_wedge_tables<double>(int, int, double, double, double, int, double*, const void*,
+                                                 double*, int*, cudaStream_t);
 
 // ln(a + sqrt(a^2 + b^2)) for b != 0; for a < 0 as ln(b^2) - ln(R - a),
 // which does not cancel

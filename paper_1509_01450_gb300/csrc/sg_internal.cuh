@@ -58,6 +58,10 @@ struct sg_plan {
     void* egp;          // phi-DFT of K^{r,r}[k, .] (cosine sum) and of K^{phi,r}[k, .] (sine sum)
     double ecoef[16];   // [a][b]: slope change of row a in {-1, 0, nu-1, nu} per weighted
                         // sigma of row b in {0, 1, nu-2, nu-1}
+    // the origin wedge below the first row (sg_build_opts.wedge = 1)
+    int wedge;
+    void* wtab;         // working dtype, [4][nphi/2 + 1][nu]: Wr, Wphi, Vr, Vphi spectra (wedge.cu)
+    void* wtmp;         // double2 [nphi/2]: the adjoint's per-mode sums
 };
 
 namespace sg {
@@ -79,6 +83,11 @@ struct PlanView {
     const void* egr;
     const void* egp;
     const double* ecoef;
+    int wedge;              // the origin wedge: wtab, wtmp, and per call sigw / gsigw
+    const void* wtab;
+    void* wtmp;
+    const void* sigw;       // forward: the wedge densities (N_phi, working dtype), set per call
+    void* gsigw;            // adjoint: their gradient, set per call
 };
 
 inline PlanView view(const sg_plan* p)
@@ -102,6 +111,11 @@ inline PlanView view(const sg_plan* p)
     v.egr = p->egr;
     v.egp = p->egp;
     v.ecoef = p->ecoef;
+    v.wedge = p->wedge;
+    v.wtab = p->wtab;
+    v.wtmp = p->wtmp;
+    v.sigw = nullptr;
+    v.gsigw = nullptr;
     return v;
 }
 
@@ -113,6 +127,10 @@ cudaError_t launch_forward(const PlanView& p, const T* sigma, T* Fr, T* Fp, cuda
                            cudaEvent_t* ev = nullptr, bool sigma_direct = false);
 template <typename T>
 cudaError_t launch_backward(const PlanView& p, const T* gr, const T* gp, T* gs, cudaStream_t st);
+// wedge.cu: the origin wedge's update between the column and inverse-row
+// passes (forward: p.sigw; adjoint: writes p.gsigw)
+template <typename T>
+cudaError_t launch_wedge(const PlanView& p, bool adjoint, cudaStream_t st);
 // Tensor maps of the row passes over the buffers bufs[3] (the layout of wa,
 // wb, wc); out[k].R = 0 where a map cannot be made.
 void make_row_maps(int nu, int nphi, size_t elem, void* const bufs[3], SgRowMaps out[2]);
@@ -141,6 +159,11 @@ cudaError_t launch_cells_tpz(int nu, int nphi, double du, int ntpz, double rtol,
 // the particle kinds' tables (sg_kernel_kind 1-3; for 2 with the exact own cell)
 cudaError_t launch_point_cells(int nu, int nphi, double du, int kind, double soften, double rtol, double* cells,
                                int* flag, cudaStream_t st);
+// the origin wedge's cells ([6][nu][nphi] FP64 scratch) and its four spectra
+// tables (wedge.cu reads them); flag bit 4 marks a cell that ran out of budget
+template <typename T>
+cudaError_t launch_wedge_tables(int nu, int nphi, double du, double G, double rtol, int pot, double* wcells,
+                                const void* tw64, T* tab, int* flag, cudaStream_t st);
 // the folded Cartesian kernels (SG_KERNEL_CARTESIAN) straight into keff and
 // the spectra's inputs; the cell table is zeroed
 cudaError_t launch_cart_fold(int nu, int nphi, double h, double G, double* cells, double* keff, double* nsr,

@@ -21,7 +21,7 @@ SG_F32, SG_F64 = 0, 1
 EXPORTS = ("sg_plan_create", "sg_kernels_build", "sg_forces", "sg_forces_backward", "sg_forces_host", "sg_forces_timed",
            "sg_forces_batched", "sg_batch_reserve", "sg_plan_destroy", "sg_status_string", "sg_plan_info",
            "sg_plan_kernels", "sg_plan_cells", "sg_plan_device_bytes", "sg_plan_build_report", "sg_forces_noalloc", "sg_plan_check",
-           "sg_plan_set_wait_limit", "sg_plan_save", "sg_plan_load")
+           "sg_plan_set_wait_limit", "sg_plan_save", "sg_plan_load", "sg_forces_wedge", "sg_forces_wedge_backward")
 
 
 class SgError(RuntimeError):
@@ -44,7 +44,7 @@ KERNEL_KINDS = {"sim": SG_KERNEL_SIM, "particle": SG_KERNEL_PARTICLE, "particle+
 class BuildOpts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("weight_p", ctypes.c_int), ("kind", ctypes.c_int),
                 ("soften", ctypes.c_double), ("n_tpz", ctypes.c_int), ("radial_edges", ctypes.c_int),
-                ("reserved", ctypes.c_int * 2)]
+                ("wedge", ctypes.c_int), ("reserved", ctypes.c_int * 1)]
 
 
 class BatchItem(ctypes.Structure):
@@ -70,6 +70,8 @@ def lib():
         L.sg_forces_host.argtypes = [vp, vp, vp, vp, vp]
         L.sg_forces_timed.argtypes = [vp, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_float)]
         L.sg_forces_noalloc.argtypes = [vp, vp, vp, vp, vp]
+        L.sg_forces_wedge.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.sg_forces_wedge_backward.argtypes = [vp, vp, vp, vp, vp, vp]
         L.sg_forces_batched.argtypes = [ctypes.POINTER(BatchItem), ip, vp]
         L.sg_batch_reserve.argtypes = [ip]
         L.sg_plan_destroy.argtypes = [vp]
@@ -131,7 +133,7 @@ class Plan:
 
     # -- one-time preparation ------------------------------------------------
     def build(self, rtol: float = 1e-14, weight_p: int = 0, kind="sim", soften: float = 0.0, n_tpz: int = 0,
-              radial_edges: int = 0, stream=None):
+              radial_edges: int = 0, wedge: int = 0, stream=None):
         """Build the kernels.  kind: "sim" (default; n_tpz > 0 for the
         trapezoidal rule of Eq. 41-43 with n_tpz trapezoids), "particle",
         "particle+" or "softened" (with soften = eps / r_i), "potential"
@@ -139,9 +141,10 @@ class Plan:
         side du; N_phi = 2 N_y with sigma zero in the last N_y columns), or
         an SG_KERNEL_* code.
         radial_edges = 1: one-sided radial slopes at the first and last rows
-        instead of ghost rows."""
+        instead of ghost rows.  wedge = 1 (with radial_edges = 1): the origin
+        wedge below the first row, whose densities forces_wedge takes."""
         code = KERNEL_KINDS[kind] if isinstance(kind, str) else int(kind)
-        opts = BuildOpts(rtol, weight_p, code, soften, n_tpz, radial_edges)
+        opts = BuildOpts(rtol, weight_p, code, soften, n_tpz, radial_edges, wedge)
         _check(lib().sg_kernels_build(self.handle, ctypes.byref(opts), _stream(stream)), "sg_kernels_build")
         return self
 
@@ -157,6 +160,35 @@ class Plan:
         self._check_field(sigma)
         _check(lib().sg_forces(self.handle, _ptr(sigma), _ptr(F_r), _ptr(F_phi), _stream(stream)), "sg_forces")
         return F_r, F_phi
+
+    def forces_wedge(self, sigma, sigma_w, F_r=None, F_phi=None, stream=None):
+        """sg_forces_wedge: the forces with the origin wedge's densities
+        sigma_w (N_phi values on the device)."""
+        F_r = self._new() if F_r is None else F_r
+        F_phi = self._new() if F_phi is None else F_phi
+        self._check_field(sigma)
+        self._check_wedge_row(sigma_w)
+        _check(lib().sg_forces_wedge(self.handle, _ptr(sigma), _ptr(sigma_w), _ptr(F_r), _ptr(F_phi),
+                                     _stream(stream)), "sg_forces_wedge")
+        return F_r, F_phi
+
+    def backward_wedge(self, gF_r, gF_phi, gsigma=None, gsigma_w=None, stream=None):
+        """sg_forces_wedge_backward: (gsigma, gsigma_w)."""
+        import torch
+
+        gsigma = self._new() if gsigma is None else gsigma
+        if gsigma_w is None:
+            gsigma_w = torch.empty(self.nphi, dtype=self.dtype, device="cuda")
+        self._check_field(gF_r)
+        self._check_field(gF_phi)
+        self._check_wedge_row(gsigma_w)
+        _check(lib().sg_forces_wedge_backward(self.handle, _ptr(gF_r), _ptr(gF_phi), _ptr(gsigma), _ptr(gsigma_w),
+                                              _stream(stream)), "sg_forces_wedge_backward")
+        return gsigma, gsigma_w
+
+    def _check_wedge_row(self, t):
+        if tuple(t.shape) != (self.nphi,) or t.dtype != self.dtype or not t.is_cuda or not t.is_contiguous():
+            raise ValueError(f"expected a contiguous CUDA {self.dtype} tensor of shape ({self.nphi},)")
 
     def forces_noalloc(self, sigma, F_r, F_phi, stream=None):
         """sg_forces using the library's fixed scratch array: no device
