@@ -39,7 +39,7 @@ BYTES_PER_CELL = {"rows": 8.0, "cols": 20.0, "inv_rows": 16.0}
 # DRAM bytes (read + write) of one column-pass launch at 2048 x 4096 FP32, from
 # one ncu capture (profiles/k_fwd_2048x4096_full.md), valid only for the
 # kernel sources it was taken on (sha256 prefix of fftconv.cu + sg_common.cuh).
-COLS_TRAFFIC = {"sources_sha256": "f783cc4927af0baf", "bytes_per_launch": 100.792576e6 + 7.111936e6}
+COLS_TRAFFIC = {"sources_sha256": "887d45fe35f2d2c5", "bytes_per_launch": 100.791040e6 + 6.891008e6}
 
 
 def kernel_sources_sha(texts=None) -> str:
@@ -369,27 +369,48 @@ def run_ours(args):
     rel_fp32_p2 = math.sqrt(num / den)
     del plan64, plan_p2, s64, f64r, f64p
 
-    # ---- build options: one-sided edge slopes (one more kernel per step) and
-    # the kernel variants (same passes; only the one-time build differs) ------
+    # ---- build options: one-sided edge slopes and the origin wedge (one more
+    # kernel per step each), the potential and the Cartesian scheme (the same
+    # passes on other tables), and the kernel variants (only the one-time
+    # build differs) -----------------------------------------------------------
     variants = {}
+    sigma_w = torch.full((NPHI,), float(sigma_np[0].mean()), dtype=torch.float32, device=dev)
+    gsw = torch.empty_like(sigma_w)
+    sigma_cart = torch.zeros_like(sigma)  # N_x x 2 N_y with the y-padding zero
+    sigma_cart[:, : NPHI // 2] = sigma[:, : NPHI // 2]
     for name, kw in (("sim_ntpz19", {"n_tpz": 19}), ("particle", {"kind": "particle"}),
                      ("particle_plus", {"kind": "particle+"}),
                      ("softened", {"kind": "softened", "soften": 0.015 * 64 / NU}),
-                     ("radial_edges_onesided", {"radial_edges": 1})):
+                     ("radial_edges_onesided", {"radial_edges": 1}),
+                     ("origin_wedge", {"radial_edges": 1, "wedge": 1}),
+                     ("potential", {"kind": "potential", "weight_p": 1}),
+                     ("cartesian", {"kind": "cartesian"})):
         t0 = time.time()
-        pv = Plan(NU, NPHI, u_min, du, 1.0, "float32").build(**kw)
+        h = 2.0 / NU if name == "cartesian" else du  # Cartesian: [-1, 1] in x, square cells
+        pv = Plan(NU, NPHI, u_min, h, 1.0, "float32").build(**kw)
         torch.cuda.synchronize()
         entry = {"build_s": time.time() - t0}
-        if name == "radial_edges_onesided":
+        if name in ("radial_edges_onesided", "origin_wedge", "potential", "cartesian"):
+            if name == "origin_wedge":
+                fwd = lambda: pv.forces_wedge(sigma, sigma_w, Fr, Fp)
+                bwd = lambda: pv.backward_wedge(gr, gp, gs, gsw)
+            else:
+                s_in = sigma_cart if name == "cartesian" else sigma
+                fwd = lambda: pv.forces(s_in, Fr, Fp)
+                bwd = lambda: pv.backward(gr, gp, gs)
             for _ in range(3):
-                pv.forces(sigma, Fr, Fp)
-            ems = timed(lambda: pv.forces(sigma, Fr, Fp), max(20, min(args.steps, 200)))
+                fwd()
+            ems = timed(fwd, max(20, min(args.steps, 200)))
             for _ in range(3):
-                pv.backward(gr, gp, gs)
-            ebms = timed(lambda: pv.backward(gr, gp, gs), max(20, min(args.steps, 200)))
-            entry.update({"value": ws * cells / (ems * 1e-3), "unit": "cells/s", "ms_per_step": ems,
+                bwd()
+            ebms = timed(bwd, max(20, min(args.steps, 200)))
+            # the Cartesian plan's cells are N_x x N_y: half the plan's columns
+            ccells = cells // 2 if name == "cartesian" else cells
+            entry.update({"value": ws * ccells / (ems * 1e-3), "unit": "cells/s", "ms_per_step": ems,
                           "extra_ms_vs_default": ems - ms, "backward_ms_per_step": ebms,
                           "backward_extra_ms_vs_default": ebms - bwd_ms})
+            if name == "cartesian":
+                entry["grid"] = f"{NU} x {NPHI // 2} square cells (plan {NU} x {NPHI}, y zero-padded)"
         variants[name] = entry
         del pv
 

@@ -61,7 +61,7 @@ struct sg_plan {
     // the origin wedge below the first row (sg_build_opts.wedge = 1)
     int wedge;
     void* wtab;         // working dtype, [4][nphi/2 + 1][nu]: Wr, Wphi, Vr, Vphi spectra (wedge.cu)
-    void* wtmp;         // double2 [nphi/2]: the adjoint's per-mode sums
+    void* wtmp;         // [nphi/2] complex values of the working dtype (16 B each allocated): the adjoint's per-mode sums
 };
 
 namespace sg {

@@ -17,13 +17,16 @@
 // imaginary parts the m = N_phi/2 ones, and the azimuthal terms vanish.
 // The adjoint forms the transposed sums t(m) per mode, adds the V part to
 // row 0 of the backward column spectra and returns gsigma_w as the inverse
-// phi-DFT of the W part.  The DFTs of the one wedge row run in FP64 from
-// the FP64 twiddle table (N_phi^2 / 2 products: negligible next to a pass).
+// phi-DFT of the W part.  All arithmetic is in the plan's dtype with the
+// plan's twiddle table (GB300's FP64 rate would make FP64 sums here cost
+// more than a pass); the direct DFTs of the one wedge row take N_phi^2 / 2
+// products, spread over one block per mode (forward) or per output (adjoint).
 #include "sg_internal.cuh"
 
 namespace sg {
 
-__device__ __forceinline__ double blk_sum(double v, double* red)
+template <typename T>
+__device__ __forceinline__ T blk_sum(T v, T* red)
 {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -31,7 +34,7 @@ __device__ __forceinline__ double blk_sum(double v, double* red)
     __syncthreads();
     if (lane == 0) red[wid] = v;
     __syncthreads();
-    double s = 0.0;
+    T s = 0;
     for (int w = 0; w < nw; w++) s += red[w];
     return s;
 }
@@ -40,21 +43,21 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_wedge_fwd(const typename CX<T>::t* __restrict__ A, typename CX<T>::t* B,
                                                    typename CX<T>::t* C, const T* __restrict__ sigw,
                                                    const T* __restrict__ tab, const T* __restrict__ wpre,
-                                                   const double2* __restrict__ tw64, int nu, int nphi)
+                                                   const typename CX<T>::t* __restrict__ tw, int nu, int nphi)
 {
     typedef typename CX<T>::t V;
-    __shared__ double red[8];
+    __shared__ T red[8];
     const int m = blockIdx.x, half = nphi / 2, stride = SG_NMAX / nphi;
     const long tsz = (long)(half + 1) * nu;
     // s^_w(m) = sum_j sigma_w[j] e^{-2 pi i m j / N_phi}; mode 0: (DC, Nyquist)
-    double sx = 0.0, sy = 0.0;
+    T sx = 0, sy = 0;
     for (int j = threadIdx.x; j < nphi; j += blockDim.x) {
-        const double v = (double)sigw[j];
+        const T v = sigw[j];
         if (m == 0) {
             sx += v;
             sy += (j & 1) ? -v : v;
         } else {
-            const double2 w = tw64[(long)((m * j) & (nphi - 1)) * stride];
+            const V w = tw[(long)((m * j) & (nphi - 1)) * stride];
             sx += v * w.x;
             sy += v * w.y;
         }
@@ -62,8 +65,8 @@ __global__ void __launch_bounds__(256) k_wedge_fwd(const typename CX<T>::t* __re
     sx = blk_sum(sx, red);
     sy = blk_sum(sy, red);
     const V a = A[(size_t)m * nu];
-    const double i0 = 1.0 / (double)wpre[0];
-    const double ax = a.x * i0, ay = a.y * i0;
+    const T i0 = (T)1 / wpre[0];
+    const T ax = a.x * i0, ay = a.y * i0;
     const T* Wr = tab + 0 * tsz + (long)m * nu;
     const T* Wp = tab + 1 * tsz + (long)m * nu;
     const T* Vr = tab + 2 * tsz + (long)m * nu;
@@ -71,19 +74,19 @@ __global__ void __launch_bounds__(256) k_wedge_fwd(const typename CX<T>::t* __re
     const T* WrN = tab + 0 * tsz + (long)half * nu;  // Nyquist (mode 0 only)
     const T* VrN = tab + 2 * tsz + (long)half * nu;
     for (int i = threadIdx.x; i < nu; i += blockDim.x) {
-        const double w = (double)wpre[i];
+        const T w = wpre[i];
         V b = B[(size_t)m * nu + i];
         if (m == 0) {
-            b.x += (T)(w * ((double)Wr[i] * sx + (double)Vr[i] * ax));
-            b.y += (T)(w * ((double)WrN[i] * sy + (double)VrN[i] * ay));
+            b.x += w * (Wr[i] * sx + Vr[i] * ax);
+            b.y += w * (WrN[i] * sy + VrN[i] * ay);
         } else {
-            b.x += (T)(w * ((double)Wr[i] * sx + (double)Vr[i] * ax));
-            b.y += (T)(w * ((double)Wr[i] * sy + (double)Vr[i] * ay));
+            b.x += w * (Wr[i] * sx + Vr[i] * ax);
+            b.y += w * (Wr[i] * sy + Vr[i] * ay);
             // -i (p s) = p (s.y - i s.x)
-            const double px = (double)Wp[i] * sx + (double)Vp[i] * ax, py = (double)Wp[i] * sy + (double)Vp[i] * ay;
+            const T px = Wp[i] * sx + Vp[i] * ax, py = Wp[i] * sy + Vp[i] * ay;
             V c = C[(size_t)m * nu + i];
-            c.x += (T)(w * py);
-            c.y -= (T)(w * px);
+            c.x += w * py;
+            c.y -= w * px;
             C[(size_t)m * nu + i] = c;
         }
         B[(size_t)m * nu + i] = b;
@@ -98,10 +101,10 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_wedge_bwd(const typename CX<T>::t* __restrict__ A,
                                                    const typename CX<T>::t* __restrict__ C, typename CX<T>::t* B,
                                                    const T* __restrict__ tab, const T* __restrict__ wpre,
-                                                   double2* __restrict__ tw_out, int nu, int nphi)
+                                                   typename CX<T>::t* __restrict__ t_out, int nu, int nphi)
 {
     typedef typename CX<T>::t V;
-    __shared__ double red[8];
+    __shared__ T red[8];
     const int m = blockIdx.x, half = nphi / 2;
     const long tsz = (long)(half + 1) * nu;
     const T* Wr = tab + 0 * tsz + (long)m * nu;
@@ -110,22 +113,22 @@ __global__ void __launch_bounds__(256) k_wedge_bwd(const typename CX<T>::t* __re
     const T* Vp = tab + 3 * tsz + (long)m * nu;
     const T* WrN = tab + 0 * tsz + (long)half * nu;
     const T* VrN = tab + 2 * tsz + (long)half * nu;
-    double wx = 0, wy = 0, vx = 0, vy = 0;
+    T wx = 0, wy = 0, vx = 0, vy = 0;
     for (int i = threadIdx.x; i < nu; i += blockDim.x) {
-        const double w = (double)wpre[i];
+        const T w = wpre[i];
         const V a = A[(size_t)m * nu + i];
         if (m == 0) {
-            wx += w * (double)Wr[i] * a.x;
-            wy += w * (double)WrN[i] * a.y;
-            vx += w * (double)Vr[i] * a.x;
-            vy += w * (double)VrN[i] * a.y;
+            wx += w * Wr[i] * a.x;
+            wy += w * WrN[i] * a.y;
+            vx += w * Vr[i] * a.x;
+            vy += w * VrN[i] * a.y;
         } else {
             const V c = C[(size_t)m * nu + i];
             // i p c = p (-c.y + i c.x)
-            wx += w * ((double)Wr[i] * a.x - (double)Wp[i] * c.y);
-            wy += w * ((double)Wr[i] * a.y + (double)Wp[i] * c.x);
-            vx += w * ((double)Vr[i] * a.x - (double)Vp[i] * c.y);
-            vy += w * ((double)Vr[i] * a.y + (double)Vp[i] * c.x);
+            wx += w * (Wr[i] * a.x - Wp[i] * c.y);
+            wy += w * (Wr[i] * a.y + Wp[i] * c.x);
+            vx += w * (Vr[i] * a.x - Vp[i] * c.y);
+            vy += w * (Vr[i] * a.y + Vp[i] * c.x);
         }
     }
     wx = blk_sum(wx, red);
@@ -133,31 +136,37 @@ __global__ void __launch_bounds__(256) k_wedge_bwd(const typename CX<T>::t* __re
     vx = blk_sum(vx, red);
     vy = blk_sum(vy, red);
     if (threadIdx.x == 0) {
-        const double i0 = 1.0 / (double)wpre[0];
+        const T i0 = (T)1 / wpre[0];
         V b = B[(size_t)m * nu];
-        b.x += (T)(vx * i0);
-        b.y += (T)(vy * i0);
+        b.x += vx * i0;
+        b.y += vy * i0;
         B[(size_t)m * nu] = b;
-        tw_out[m] = make_double2(wx, wy);
+        t_out[m] = V{wx, wy};
     }
 }
 
 // gsigma_w[j] = sum over all modes of t(m) e^{+2 pi i m j / N_phi} for the
-// real sequence whose half spectrum t holds (mode 0 packed (DC, Nyquist)).
+// real sequence whose half spectrum t holds (mode 0 packed (DC, Nyquist)):
+// one block per output j, the modes split over its threads.
 template <typename T>
-__global__ void k_wedge_idft(const double2* __restrict__ t, const double2* __restrict__ tw64, T* __restrict__ gsw,
-                             int nphi)
+__global__ void __launch_bounds__(256) k_wedge_idft(const typename CX<T>::t* __restrict__ t,
+                                                    const typename CX<T>::t* __restrict__ tw, T* __restrict__ gsw,
+                                                    int nphi)
 {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x, half = nphi / 2, stride = SG_NMAX / nphi;
-    if (j >= nphi) return;
-    const double2 t0 = t[0];
-    double s = t0.x + ((j & 1) ? -t0.y : t0.y), r = 0.0;
-    for (int m = 1; m < half; m++) {
-        const double2 w = tw64[(long)((m * j) & (nphi - 1)) * stride];  // e^{-i theta}
-        const double2 v = t[m];
+    typedef typename CX<T>::t V;
+    __shared__ T red[8];
+    const int j = blockIdx.x, half = nphi / 2, stride = SG_NMAX / nphi;
+    T r = 0;
+    for (int m = 1 + threadIdx.x; m < half; m += blockDim.x) {
+        const V w = tw[(long)((m * j) & (nphi - 1)) * stride];  // e^{-i theta}
+        const V v = t[m];
         r += v.x * w.x + v.y * w.y;  // Re(v e^{+i theta})
     }
-    gsw[j] = (T)(s + 2.0 * r);
+    r = blk_sum(r, red);
+    if (threadIdx.x == 0) {
+        const V t0 = t[0];
+        gsw[j] = t0.x + ((j & 1) ? -t0.y : t0.y) + 2 * r;
+    }
 }
 
 template <typename T>
@@ -167,14 +176,13 @@ cudaError_t launch_wedge(const PlanView& p, bool adjoint, cudaStream_t st)
     if (adjoint) {
         if (!p.gsigw) return cudaErrorInvalidValue;
         k_wedge_bwd<T><<<p.nphi / 2, 256, 0, st>>>((const V*)p.wa, (const V*)p.wc, (V*)p.wb, (const T*)p.wtab,
-                                                   (const T*)p.wpre, (double2*)p.wtmp, p.nu, p.nphi);
-        k_wedge_idft<T><<<(p.nphi + 255) / 256, 256, 0, st>>>((const double2*)p.wtmp, (const double2*)p.tw64,
-                                                              (T*)p.gsigw, p.nphi);
+                                                   (const T*)p.wpre, (V*)p.wtmp, p.nu, p.nphi);
+        k_wedge_idft<T><<<p.nphi, 256, 0, st>>>((const V*)p.wtmp, (const V*)p.tw, (T*)p.gsigw, p.nphi);
     } else {
         if (!p.sigw) return cudaErrorInvalidValue;
         k_wedge_fwd<T><<<p.nphi / 2, 256, 0, st>>>((const V*)p.wa, (V*)p.wb, (V*)p.wc, (const T*)p.sigw,
-                                                   (const T*)p.wtab, (const T*)p.wpre, (const double2*)p.tw64,
-                                                   p.nu, p.nphi);
+                                                   (const T*)p.wtab, (const T*)p.wpre, (const V*)p.tw, p.nu,
+                                                   p.nphi);
     }
     return cudaGetLastError();
 }
