@@ -39,7 +39,7 @@ BYTES_PER_CELL = {"rows": 8.0, "cols": 20.0, "inv_rows": 16.0}
 # DRAM bytes (read + write) of one column-pass launch at 2048 x 4096 FP32, from
 # one ncu capture (profiles/k_fwd_2048x4096_full.md), valid only for the
 # kernel sources it was taken on (sha256 prefix of fftconv.cu + sg_common.cuh).
-COLS_TRAFFIC = {"sources_sha256": "887d45fe35f2d2c5", "bytes_per_launch": 100.791040e6 + 6.891008e6}
+COLS_TRAFFIC = {"sources_sha256": "5f95a5c5a059a456", "bytes_per_launch": 100.791808e6 + 6.804480e6}
 
 
 def kernel_sources_sha(texts=None) -> str:

@@ -92,6 +92,15 @@ struct EdgeCoef {
     T c[16];
 };
 
+// The origin wedge's update fused into the forward column pass: the wedge
+// row's phi-spectrum per mode (swh, written by k_wedge_dft before the row
+// pass) and the plan's wedge tables [4][N_phi/2 + 1][N_u] (Wr, Wphi, Vr, Vphi).
+template <typename T>
+struct WedgeArgs {
+    const typename CX<T>::t* swh;
+    const T* tab;
+};
+
 // shared-memory carve-up of the column kernels (16-byte aligned regions)
 __host__ __device__ __forceinline__ size_t sg_align16(size_t b) { return (b + 15) & ~(size_t)15; }
 
@@ -433,8 +442,11 @@ __host__ __device__ __forceinline__ size_t cols_smem_bytes(int nu)
 // edge tables (gr and gp; for mode 0 gr of modes 0 and N_phi/2) arrive with
 // the spectra into an area after the exchange area, and s^_a comes from the
 // four edge rows of the landed column.  egr, egp, wpre and ecoef are unused
-// otherwise.
-template <typename T, int E, int NTB, int LG = 0, bool EDGE = false>
+// otherwise.  WEDGE (with EDGE): the origin wedge's rank-2 update of
+// k_wedge_fwd is added in the same place, its table rows read straight from
+// global memory by the threads that own the rows, s^_w from swh and a_0 from
+// row 0 of the landed column.
+template <typename T, int E, int NTB, int LG = 0, bool EDGE = false, bool WEDGE = false>
 __global__ void SG_FCOLS_BOUNDS(T, NTB, LG, EDGE) k_fwd_cols(const typename CX<T>::t* __restrict__ A,
                                                   const typename CX<T>::t* __restrict__ Kr,
                                                   const typename CX<T>::t* __restrict__ Kp,
@@ -442,7 +454,7 @@ __global__ void SG_FCOLS_BOUNDS(T, NTB, LG, EDGE) k_fwd_cols(const typename CX<T
                                                   typename CX<T>::t* __restrict__ Cp, int nu, int nphi, int log2L,
                                                   const typename CX<T>::t* __restrict__ tw, int* err,
                                                   const T* __restrict__ egr, const T* __restrict__ egp,
-                                                  const T* __restrict__ wpre, EdgeCoef<T> ecoef)
+                                                  const T* __restrict__ wpre, EdgeCoef<T> ecoef, WedgeArgs<T> wdg)
 {
     const unsigned long long wlim = sg_wait_budget(err);  // read once, early
     if constexpr (LG > 0) {  // the length is a compile-time constant
@@ -497,10 +509,15 @@ __global__ void SG_FCOLS_BOUNDS(T, NTB, LG, EDGE) k_fwd_cols(const typename CX<T
     V v[E];
 #pragma unroll
     for (int e = 0; e < E; e++) v[e] = (e < E / 2) ? sm[t + e * NT] : V{0, 0};  // rows >= nu: zero pad
-    __shared__ V es[4];  // EDGE: s^_a
+    __shared__ V es[6];  // EDGE: s^_a; WEDGE: a_0 and s^_w in es[4], es[5]
     if constexpr (EDGE) {
         if (t == 0) {  // read before the transform's first exchange (behind its first barrier)
             const V ab4[4] = {sm[0], sm[1], sm[nu - 2], sm[nu - 1]};
+            if constexpr (WEDGE) {
+                const T i0 = (T)1 / wpre[0];
+                es[4] = V{ab4[0].x * i0, ab4[0].y * i0};
+                es[5] = wdg.swh[m];
+            }
 #pragma unroll
             for (int a = 0; a < 4; a++) {
                 V acc{0, 0};
@@ -564,6 +581,23 @@ __global__ void SG_FCOLS_BOUNDS(T, NTB, LG, EDGE) k_fwd_cols(const typename CX<T
                         dr.y += x0 * sa.y;
                         dq.x += x1 * sa.y;  // -i gp s = gp (s.y - i s.x)
                         dq.y -= x1 * sa.x;
+                    }
+                }
+                if constexpr (WEDGE) {
+                    // += (Wr s^_w + Vr a_0, -i (Wphi s^_w + Vphi a_0)); mode 0: Nyquist tables on .y
+                    const long tsz = (long)(half + 1) * nu;
+                    const V a0 = es[4], sw = es[5];
+                    const T* tb = wdg.tab + (long)m * nu + i;
+                    const T wr = tb[0], wp = tb[tsz], vr = tb[2 * tsz], vp = tb[3 * tsz];
+                    if (m == 0) {
+                        const T* tn = wdg.tab + (long)half * nu + i;
+                        dr.x += wr * sw.x + vr * a0.x;
+                        dr.y += tn[0] * sw.y + tn[2 * tsz] * a0.y;
+                    } else {
+                        dr.x += wr * sw.x + vr * a0.x;
+                        dr.y += wr * sw.y + vr * a0.y;
+                        dq.x += wp * sw.y + vp * a0.y;
+                        dq.y -= wp * sw.x + vp * a0.x;
                     }
                 }
                 w[e] = C2{w[e].x + f2(wi * dr.x, wi * dq.x), w[e].y + f2(wi * dr.y, wi * dq.y)};
@@ -1483,7 +1517,8 @@ __global__ void __launch_bounds__(512) k_spec_cols(const double2* __restrict__ W
 typedef void (*FwdRowsFn)(const float*, const float*, float2*, int, int, int, const float2*, int*, CUtensorMap,
                           int, int);
 typedef void (*FwdColsFn)(const float2*, const float2*, const float2*, float2*, float2*, int, int, int,
-                          const float2*, int*, const float*, const float*, const float*, EdgeCoef<float>);
+                          const float2*, int*, const float*, const float*, const float*, EdgeCoef<float>,
+                          WedgeArgs<float>);
 typedef void (*FwdRowsInvFn)(const float2*, const float2*, const float*, float*, float*, int, int, int,
                              const float2*, int*, CUtensorMap, CUtensorMap, int);
 typedef void (*BwdRowsFn)(const float*, const float*, const float*, float2*, float2*, int, int, int, const float2*,
@@ -1497,6 +1532,7 @@ struct FixedPassKernels {
     FwdRowsFn fwd_rows;
     FwdColsFn fwd_cols;
     FwdColsFn fwd_cols_edge;  // with the edge-slope update
+    FwdColsFn fwd_cols_edge_wedge;  // with the edge-slope and origin-wedge updates
     FwdRowsInvFn fwd_rows_inv;
     BwdRowsFn bwd_rows;
     BwdColsFn bwd_cols;
@@ -1510,7 +1546,8 @@ FixedPassKernels make_fixed_pass_kernels()
 {
     constexpr int NB = (1 << LG) / 16 > 256 ? 512 : 256;
     return FixedPassKernels{k_fwd_rows<float, 16, NB, LG>,       k_fwd_cols<float, 16, NB, LG>,
-                            k_fwd_cols<float, 16, NB, LG, true>, k_fwd_rows_inv<float, 16, NB, LG>,
+                            k_fwd_cols<float, 16, NB, LG, true>, k_fwd_cols<float, 16, NB, LG, true, true>,
+                            k_fwd_rows_inv<float, 16, NB, LG>,
                             k_bwd_rows<float, 16, LG>,           k_bwd_cols<float, 16, NB, LG>,
                             k_bwd_cols<float, 16, NB, LG, true>, k_bwd_rows_inv<float, 16, NB, LG>,
                             NB};
@@ -1750,6 +1787,11 @@ cudaError_t launch_forward(const PlanView& p, const T* sigma, T* Fr, T* Fp, cuda
     const int ln = sg_ilog2(p.nphi), lL = sg_ilog2(2 * p.nu);
     cudaError_t err;
     if (ev && (err = cudaEventRecord(ev[0], st)) != cudaSuccess) return err;
+    // FP32 columns of 16 points per thread with one-sided edges take the
+    // wedge's update inside the column pass; the wedge row's spectrum is
+    // formed first, ahead of the chained passes
+    const bool wedge_fused = sizeof(T) == 4 && 2 * p.nu >= 16 && p.edges && p.wedge;
+    if (wedge_fused && (err = launch_wedge_dft<T>(p, st)) != cudaSuccess) return err;
     {
         PassRange range_("sg forward rows");
         Shape s = shape_for<V>(p.nphi, sizeof(T) == 8 ? 64 : 256);
@@ -1778,26 +1820,31 @@ cudaError_t launch_forward(const PlanView& p, const T* sigma, T* Fr, T* Fp, cuda
         for (int j = 0; j < 16; j++) coef.c[j] = p.edges ? (T)p.ecoef[j] : (T)0;
         SG_DISPATCH_E(E, {
             const bool fuse = sizeof(T) == 4 && EE == 16 && p.edges;
+            const bool fusew = fuse && p.wedge;  // == wedge_fused
             auto k = k_fwd_cols<T, EE, 256>;
             if constexpr (sizeof(T) == 4)  // FP64 columns are at most 256 threads
                 if (L / EE > 256) k = k_fwd_cols<T, EE, 512>;
             if constexpr (sizeof(T) == 4 && EE == 16) {
                 if (fuse) k = L / EE > 256 ? k_fwd_cols<T, 16, 512, 0, true> : k_fwd_cols<T, 16, 256, 0, true>;
+                if (fusew)
+                    k = L / EE > 256 ? k_fwd_cols<T, 16, 512, 0, true, true> : k_fwd_cols<T, 16, 256, 0, true, true>;
                 if (const FixedPassKernels* f = fixed_pass_kernels(lL))
-                    if (L / EE <= f->threads) k = fuse ? f->fwd_cols_edge : f->fwd_cols;
+                    if (L / EE <= f->threads)
+                        k = fusew ? f->fwd_cols_edge_wedge : fuse ? f->fwd_cols_edge : f->fwd_cols;
             }
             const size_t smem =
                 cols_smem_bytes<T>(p.nu) + (fuse ? 2 * (size_t)sg_edge_stride(p.nu, sizeof(T)) * sizeof(T) : 0);
             if ((err = set_smem(k, smem, true)) != cudaSuccess) return err;
+            const WedgeArgs<T> wdg{(const V*)p.wtmp, (const T*)p.wtab};
             if ((err = launch_pdl(k, p.nphi / 2, L / EE, smem, st, A, (const V*)p.kr, (const V*)p.kp, B, C, p.nu,
                                   p.nphi, lL, tw, p.err, (const T*)p.egr, (const T*)p.egp, (const T*)p.wpre,
-                                  coef)) != cudaSuccess)
+                                  coef, wdg)) != cudaSuccess)
                 return err;
             edges_done = fuse;
         });
     }
     if (p.edges && !edges_done && (err = launch_edges<T>(p, false, st)) != cudaSuccess) return err;
-    if (p.wedge && (err = launch_wedge<T>(p, false, st)) != cudaSuccess) return err;
+    if (p.wedge && !wedge_fused && (err = launch_wedge<T>(p, false, st)) != cudaSuccess) return err;
     if (ev && (err = cudaEventRecord(ev[2], st)) != cudaSuccess) return err;
     {
         PassRange range_("sg forward inverse rows");

@@ -131,6 +131,9 @@ cudaError_t launch_backward(const PlanView& p, const T* gr, const T* gp, T* gs, 
 // passes (forward: p.sigw; adjoint: writes p.gsigw)
 template <typename T>
 cudaError_t launch_wedge(const PlanView& p, bool adjoint, cudaStream_t st);
+// the wedge row's phi-spectrum per mode into p.wtmp (for the fused update)
+template <typename T>
+cudaError_t launch_wedge_dft(const PlanView& p, cudaStream_t st);
 // Tensor maps of the row passes over the buffers bufs[3] (the layout of wa,
 // wb, wc); out[k].R = 0 where a map cannot be made.
 void make_row_maps(int nu, int nphi, size_t elem, void* const bufs[3], SgRowMaps out[2]);

@@ -25,6 +25,30 @@
 
 namespace sg {
 
+// e^{-2 pi i (a b mod N) / N} from the plan's table (length SG_NMAX)
+template <typename V>
+__device__ __forceinline__ V tw_at(const V* tw, long a, long b, int nphi)
+{
+    return tw[((a * b) & (nphi - 1)) * (SG_NMAX / nphi)];
+}
+
+// sum_j x[j] e^{-2 pi i m j / N} over this thread's j = threadIdx.x + k
+// blockDim.x: the twiddle advances by a product per step (two table loads
+// per thread instead of one scattered load per term)
+template <typename T, typename V>
+__device__ __forceinline__ void dft_partial(const T* __restrict__ x, const V* __restrict__ tw, int m, int nphi,
+                                            T& sx, T& sy)
+{
+    V w = tw_at(tw, m, threadIdx.x, nphi);
+    const V st = tw_at(tw, m, blockDim.x, nphi);
+    for (int j = threadIdx.x; j < nphi; j += blockDim.x) {
+        const T v = x[j];
+        sx += v * w.x;
+        sy += v * w.y;
+        w = V{w.x * st.x - w.y * st.y, w.x * st.y + w.y * st.x};
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ T blk_sum(T v, T* red)
 {
@@ -47,20 +71,18 @@ __global__ void __launch_bounds__(256) k_wedge_fwd(const typename CX<T>::t* __re
 {
     typedef typename CX<T>::t V;
     __shared__ T red[8];
-    const int m = blockIdx.x, half = nphi / 2, stride = SG_NMAX / nphi;
+    const int m = blockIdx.x, half = nphi / 2;
     const long tsz = (long)(half + 1) * nu;
     // s^_w(m) = sum_j sigma_w[j] e^{-2 pi i m j / N_phi}; mode 0: (DC, Nyquist)
     T sx = 0, sy = 0;
-    for (int j = threadIdx.x; j < nphi; j += blockDim.x) {
-        const T v = sigw[j];
-        if (m == 0) {
+    if (m == 0) {
+        for (int j = threadIdx.x; j < nphi; j += blockDim.x) {
+            const T v = sigw[j];
             sx += v;
             sy += (j & 1) ? -v : v;
-        } else {
-            const V w = tw[(long)((m * j) & (nphi - 1)) * stride];
-            sx += v * w.x;
-            sy += v * w.y;
         }
+    } else {
+        dft_partial(sigw, tw, m, nphi, sx, sy);
     }
     sx = blk_sum(sx, red);
     sy = blk_sum(sy, red);
@@ -155,12 +177,14 @@ __global__ void __launch_bounds__(256) k_wedge_idft(const typename CX<T>::t* __r
 {
     typedef typename CX<T>::t V;
     __shared__ T red[8];
-    const int j = blockIdx.x, half = nphi / 2, stride = SG_NMAX / nphi;
+    const int j = blockIdx.x, half = nphi / 2;
     T r = 0;
+    V w = tw_at(tw, 1 + threadIdx.x, j, nphi);  // e^{-i theta}, theta = 2 pi m j / N
+    const V st = tw_at(tw, blockDim.x, j, nphi);
     for (int m = 1 + threadIdx.x; m < half; m += blockDim.x) {
-        const V w = tw[(long)((m * j) & (nphi - 1)) * stride];  // e^{-i theta}
         const V v = t[m];
         r += v.x * w.x + v.y * w.y;  // Re(v e^{+i theta})
+        w = V{w.x * st.x - w.y * st.y, w.x * st.y + w.y * st.x};
     }
     r = blk_sum(r, red);
     if (threadIdx.x == 0) {
@@ -168,6 +192,41 @@ __global__ void __launch_bounds__(256) k_wedge_idft(const typename CX<T>::t* __r
         gsw[j] = t0.x + ((j & 1) ? -t0.y : t0.y) + 2 * r;
     }
 }
+
+// s^_w(m) for every mode, for the update fused into the forward column
+// pass: one block per mode, mode 0 packed (DC, Nyquist).
+template <typename T>
+__global__ void __launch_bounds__(256) k_wedge_dft(const T* __restrict__ sigw, const typename CX<T>::t* __restrict__ tw,
+                                                   typename CX<T>::t* __restrict__ swh, int nphi)
+{
+    typedef typename CX<T>::t V;
+    __shared__ T red[8];
+    const int m = blockIdx.x;
+    T sx = 0, sy = 0;
+    if (m == 0) {
+        for (int j = threadIdx.x; j < nphi; j += blockDim.x) {
+            const T v = sigw[j];
+            sx += v;
+            sy += (j & 1) ? -v : v;
+        }
+    } else {
+        dft_partial(sigw, tw, m, nphi, sx, sy);
+    }
+    sx = blk_sum(sx, red);
+    sy = blk_sum(sy, red);
+    if (threadIdx.x == 0) swh[m] = V{sx, sy};
+}
+
+template <typename T>
+cudaError_t launch_wedge_dft(const PlanView& p, cudaStream_t st)
+{
+    typedef typename CX<T>::t V;
+    if (!p.sigw) return cudaErrorInvalidValue;
+    k_wedge_dft<T><<<p.nphi / 2, 256, 0, st>>>((const T*)p.sigw, (const V*)p.tw, (V*)p.wtmp, p.nphi);
+    return cudaGetLastError();
+}
+template cudaError_t launch_wedge_dft<float>(const PlanView&, cudaStream_t);
+template cudaError_t launch_wedge_dft<double>(const PlanView&, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_wedge(const PlanView& p, bool adjoint, cudaStream_t st)
