@@ -69,3 +69,33 @@ def test_bad_scalars_and_nulls(L):
     assert L.sg_plan_destroy(None) == 1
     assert L.sg_forces_batched(None, -1, None) == 1
     assert L.sg_forces_batched(None, 0, None) == 0  # empty batch is a no-op
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The binding's ctypes structures against the C compiler's layout of
+    sg_build_opts and sg_batch_item (gcc on include/sg.h)."""
+    import shutil
+    import subprocess
+
+    from paper_1509_01450_gb300 import sg
+
+    gcc = shutil.which("gcc")
+    cuda_inc = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "include")
+    if gcc is None or not os.path.exists(os.path.join(cuda_inc, "cuda_runtime_api.h")):
+        pytest.skip("gcc or the CUDA headers are not available")
+    fields = [f for f, _ in sg.BuildOpts._fields_]
+    src = tmp_path / "layout.c"
+    lines = ['#include <stdio.h>', '#include "sg.h"', "int main(void) {",
+             '  printf("%zu\\n", sizeof(sg_build_opts));']
+    lines += [f'  printf("%zu\\n", offsetof(sg_build_opts, {f}));' for f in fields]
+    lines += ['  printf("%zu\\n", sizeof(sg_batch_item));']
+    lines += [f'  printf("%zu\\n", offsetof(sg_batch_item, {f}));' for f, _ in sg.BatchItem._fields_]
+    lines += ["  return 0;", "}"]
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([gcc, "-std=c99", "-I", os.path.join(ROOT, "include"), "-I", cuda_inc, str(src), "-o", str(exe)],
+                   check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    want = [ctypes.sizeof(sg.BuildOpts)] + [getattr(sg.BuildOpts, f).offset for f in fields]
+    want += [ctypes.sizeof(sg.BatchItem)] + [getattr(sg.BatchItem, f).offset for f, _ in sg.BatchItem._fields_]
+    assert got == want

@@ -3,8 +3,8 @@ azimuthal cell below the grid's first row, Sec. 3.2.1, and the third terms
 of Eq. 27-29 with the kernels K-bar), against things other than the
 oracle's own integrator:
 
-* the wedge kernels by 2-D quadrature of the raw integrands in physical
-  coordinates (r', phi');
+* the wedge kernels, the forces' and the potential's, by 2-D quadrature of
+  the raw integrands in physical coordinates (r', phi');
 * the wedge's single sums against a brute-force quadrature of the
   piecewise-linear wedge density (the value at the wedge centre r_in / 2,
   the one-sided radial slope toward the first row, the central azimuthal
@@ -99,3 +99,20 @@ def test_kuzmin_with_the_wedge_second_order(oracle_mod):
     order = math.log2(errs[-2] / errs[-1])
     assert order > 1.7 and errs[-1] < 4e-4, (errs, order)
     assert min(errs0) > 0.5, errs0
+
+
+@pytest.mark.parametrize("i,q", [(0, 0), (0, 2), (3, -1), (6, 8)])
+def test_potential_wedge_cells_against_quadrature(oracle_mod, i, q):
+    """The potential's wedge kernels: -int r' / (r_i d) and its two slope
+    moments over the wedge of outer radius 1, in physical coordinates."""
+    W = oracle_mod.wedge_cells(NU, NPHI, DU, pot=True)
+    beta = math.exp(DU)
+    ri = 0.5 * beta ** i * (1.0 + beta)
+    dphi = 2 * math.pi / NPHI
+    lo, hi = (-q - 0.5) * dphi, (-q + 0.5) * dphi
+    f0 = lambda r, p: -r / (ri * math.sqrt(r * r + ri * ri - 2 * r * ri * math.cos(p)))
+    fs = [f0, lambda r, p: f0(r, p) * (r - 0.5) / ri, lambda r, p: f0(r, p) * (p + q * dphi)]
+    ref = np.array([dblquad(f, lo, hi, 0.0, 1.0, epsabs=0, epsrel=1e-12)[0] for f in fs])
+    got = W[:3, i, q % NPHI]
+    assert np.all(np.abs(got - ref) <= 1e-10 * abs(ref[0])), (got, ref)
+    assert not np.any(W[3:])
