@@ -216,9 +216,8 @@ sg_status sg_forces_backward(sg_plan* plan, const void* gF_r, const void* gF_phi
  * aligned to the element size; the caller keeps ownership).  The update runs
  * inside the forward column pass (FP32, N_u >= 8) or between the column
  * and inverse-row passes.  sg_forces, sg_forces_timed, sg_forces_backward,
- * sg_forces_host and sg_forces_batched return SG_ERR_UNSUPPORTED on such a
- * plan, and sg_forces_noalloc returns SG_ERR_CUDA (its launch is refused
- * before any work is enqueued).  SG_ERR_ARG if the plan has no wedge,
+ * sg_forces_host, sg_forces_batched and sg_forces_noalloc return
+ * SG_ERR_UNSUPPORTED on such a plan.  SG_ERR_ARG if the plan has no wedge,
  * for null, misaligned or aliased buffers.
  */
 sg_status sg_forces_wedge(sg_plan* plan, const void* sigma, const void* sigma_w, void* F_r, void* F_phi,

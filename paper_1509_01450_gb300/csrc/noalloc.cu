@@ -59,6 +59,7 @@ extern "C" sg_status sg_forces_noalloc(sg_plan* p, const void* sigma, void* F_r,
 {
     if (!p) return SG_ERR_ARG;
     if (!p->built) return SG_ERR_NOT_BUILT;
+    if (p->wedge) return SG_ERR_UNSUPPORTED;  // the wedge densities come through sg_forces_wedge
     const void* ptrs[3] = {sigma, F_r, F_phi};
     for (const void* q : ptrs)
         if (!q || ((uintptr_t)q & 15)) return SG_ERR_ARG;

@@ -149,6 +149,9 @@ def test_options(torch_cuda, oracle_mod, tmp_path):
         forces_batched([(plan, s, torch.empty_like(s), torch.empty_like(s))])
     assert ei.value.status == sg.SG_ERR_UNSUPPORTED
     with pytest.raises(SgError) as ei:
+        plan.forces_noalloc(s, torch.empty_like(s), torch.empty_like(s))
+    assert ei.value.status == sg.SG_ERR_UNSUPPORTED
+    with pytest.raises(SgError) as ei:
         plan.save(str(tmp_path / "wedge_plan.bin"))
     assert ei.value.status == sg.SG_ERR_UNSUPPORTED
     # a plan without the wedge refuses the wedge entry point
