@@ -30,6 +30,15 @@ polar coordinates":
 * ``direct_sum_T``       -- its transpose (adjoint), for the sigma-gradient.
 * ``fft_conv``           -- the same convolution with numpy's FFT as a
                             library step (zero-padded in u, periodic in phi).
+* ``onesided_forces``    -- the sums with one-sided radial slopes at the
+                            first and last rows (no ghost rows).
+* ``wedge_cells``,        -- the origin wedge below the grid (Sec. 3.2.1,
+  ``wedge_sums``,            the third terms of Eq. 27-29): its kernels seen
+  ``wedge_forces``           from every row, its single sums, and the grid's
+                            one-sided sums plus them.
+* ``cartesian``          -- Sec. 3.1.1 and App. A: the Cartesian scheme's
+                            closed-form kernels, literal sums, fold and
+                            zero-padded convolution (its own module).
 * ``analytic``           -- closed-form disks used as truth (Sec. 5.1).
 """
 from __future__ import annotations
