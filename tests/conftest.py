@@ -1,7 +1,7 @@
 """Shared test configuration.
 
-Markers: ``gpu`` marks tests that need a CUDA device (run on the GPU machine with
-``-m gpu``); everything else runs on the CPU with ``-m "not gpu"``.
+Markers: ``gpu`` marks tests that need a CUDA device (run them on a GB300
+with ``-m gpu``); everything else runs on the CPU with ``-m "not gpu"``.
 """
 import os
 import sys
