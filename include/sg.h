@@ -58,7 +58,7 @@ typedef enum { SG_F32 = 0, SG_F64 = 1 } sg_dtype;
 
 typedef struct sg_plan sg_plan;
 
-/* Which force kernels the plan convolves with (Sec. 3.2 and 5.2).  All
+/* Which force kernels the plan convolves with (Sec. 3.2 and 5.3).  All
    of them feed the same fold, spectra and passes; only the table of the six
    per-offset kernels differs.  Source cell (i', j') of target (i, j), offset
    (k, q) = (i - i', j - j'); M = sigma A' is the source cell's mass with
@@ -79,7 +79,7 @@ typedef enum {
     SG_KERNEL_SOFTENED = 3,      /* the particle kernel with a softening length
                                     eps = soften * r_i added in quadrature to
                                     the distance (the BM08 comparison method of
-                                    Sec. 5.2), own cell included */
+                                    Sec. 5.3), own cell included */
     SG_KERNEL_POTENTIAL = 4,     /* the gravitational potential instead of the
                                     forces (the paper's Sec. 6 notes that the
                                     method carries over): the same cells and
@@ -110,8 +110,8 @@ typedef enum {
                                     forms directly) */
 } sg_kernel_kind;
 
-/* Options of the one-time kernel preparation (Sec. 2: "prepared only once
-   for a fixed grid").  Pass NULL for the defaults; a zero-filled struct
+/* Options of the one-time kernel preparation (Sec. 2: the kernels depend
+   only on the grid, so they are built once and kept).  Pass NULL for the defaults; a zero-filled struct
    gives them too. */
 typedef struct {
     double rtol;   /* relative tolerance of the cell quadrature; default 1e-14 */

@@ -12,7 +12,7 @@ polar coordinates":
 * ``grid``               -- Sec. 3.2.1: log-spaced faces, arithmetic centres.
 * ``kernel_cells``       -- Eq. 30-32, A11-A13: the six exact cell integrals
                             (C, adaptive Gauss-Legendre; see sg_oracle.c).
-* ``slopes``             -- Eq. 25 with central differences (Sec. 5.2).
+* ``slopes``             -- Eq. 25 with central differences (Sec. 5.3).
 * ``three_sum``          -- Eq. 26-29 and A8-A10 on the single grid, the
                             literal three-term form.
 * ``kernel_cells_tpz``   -- Eq. 41-43: the same kernels with the trapezoidal
@@ -20,7 +20,7 @@ polar coordinates":
 * ``potential_cells``    -- the same construction for the potential, which
                             the paper says carries over (Sec. 6); and
                             ``potential``, the potential at the centres.
-* ``particle_cells``     -- Eq. 35-37 and Sec. 5.2: the particle method, the
+* ``particle_cells``     -- Eq. 35-37 and Sec. 5.3: the particle method, the
                             modified particle method and the softened
                             particle kernel of the comparison (BM08), as
                             cell tables of the same shape.
@@ -186,7 +186,7 @@ def particle_cells(nu: int, nphi: int, du: float, kind: str, soften: float = 0.0
                       ``kernel_cell``) at (0, 0); ``fold`` turns the slope
                       ones into the sigma differences of delta^r, delta^phi.
     kind "softened":  eps^2 = (soften r_i)^2 added to d^2, own cell included
-                      (the comparison method of Sec. 5.2).
+                      (the comparison method of Sec. 5.3).
     """
     if kind not in PARTICLE_KINDS:
         raise ValueError(kind)
@@ -324,7 +324,7 @@ def kernels_tpz(nu: int, nphi: int, du: float, n_tpz: int, rtol: float = 2e-14, 
 # Eq. 25 slopes and the three-term sums of Eq. 26-29 / A8-A10
 # --------------------------------------------------------------------------
 def slopes(sigma: np.ndarray, grid: Grid, edges: str = "ghost"):
-    """Slopes of the piecewise-linear density (Eq. 25; Sec. 5.2 uses central
+    """Slopes of the piecewise-linear density (Eq. 25; Sec. 5.3 uses central
     differences).
 
     edges = "ghost" (the default): sigma is zero outside the grid and the

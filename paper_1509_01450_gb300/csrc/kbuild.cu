@@ -1,6 +1,6 @@
 // kbuild.cu -- FP64 construction of the cell-integrated force kernels
-// (run once per grid; Sec. 2 of the paper: the kernels are "prepared only
-// once ... and stored").
+// (run once per grid: by Sec. 2 the kernels depend only on the grid, so
+// they are built once and kept).
 //
 // In the dimensionless variables of Eq. 33, eta = rbar / r_i and
 // xi = phibar - phi_j, with F^2 = (eta - cos xi)^2 + sin^2 xi, the six
@@ -41,7 +41,7 @@
 // rule's rho weight absorbs.
 //
 // k_point_cells: the particle kinds of sg_kernel_kind (Eq. 35-37 and the
-// softened comparison method of Sec. 5.2).  The source centre of offset
+// softened comparison method of Sec. 5.3).  The source centre of offset
 // (k, q) sits at eta_c = beta^-k, xi_c = -q' dphi (q' = q taken into
 // (-N_phi/2, N_phi/2]); its mass in units of sigma r_i^2 is
 // a = eta_c^2 2 tanh(du/2) dphi (A' / r_i^2 of the cell with arithmetic

@@ -30,7 +30,7 @@ class SgError(RuntimeError):
         super().__init__(f"{what}: {status_string(status)} ({status})")
 
 
-# sg_kernel_kind: which force kernels a plan is built with (Sec. 3.2, 5.2)
+# sg_kernel_kind: which force kernels a plan is built with (Sec. 3.2, 5.3)
 SG_KERNEL_SIM = 0            # second order: exact cell integrals, central slopes, singular own cell
 SG_KERNEL_PARTICLE = 1       # point mass at each source centre (Eq. 35)
 SG_KERNEL_PARTICLE_PLUS = 2  # point masses plus the own cell's exact terms (Eq. 36-37)

@@ -1,5 +1,5 @@
 """The kernel variants built by the CUDA kernel builder: the particle-method
-kernels (Eq. 35-37, and the softened comparison method of Sec. 5.2) and the
+kernels (Eq. 35-37, and the softened comparison method of Sec. 5.3) and the
 trapezoidal SIM kernels (Eq. 41-43), against the oracle's tables: the raw
 tables, the folded kernels, the forces (FP64 within 1e-12 relative L2, FP32
 within 1e-5) and the convergence orders of Table 1 through the CUDA path."""
@@ -158,7 +158,7 @@ def test_tpz_forces_against_the_oracle(torch_cuda, oracle_mod, nu, nphi, dtype, 
 
 
 def test_sim_tpz19_orders_through_the_cuda_path(torch_cuda):
-    """Table 1's SIM column (N_tpz = 19, Sec. 5.2) for the sigma_{D_5} disk
+    """Table 1's SIM column (N_tpz = 19, Sec. 5.3) for the sigma_{D_5} disk
     from FP64 forces computed by the library."""
     from paper_1509_01450_gb300 import Plan
 

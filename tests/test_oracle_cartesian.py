@@ -97,7 +97,7 @@ def test_dn_second_order(nd):
     N = 64, 128, 256.  D_5: the maximum error converges at second order;
     D_2, whose second derivative is singular at the rim: the mean error at
     second order, the maximum at about 1.5 (as the paper finds on the polar
-    grid, Sec. 5.2)."""
+    grid, Sec. 5.3)."""
     alpha, xc, yc, M = 0.25, 0.1, -0.05, 0.5
     emax, emean = [], []
     for n in (64, 128, 256):

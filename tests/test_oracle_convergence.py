@@ -3,7 +3,7 @@
 * Kuzmin disk (the closed form F_r = -r/(r^2+1)^{3/2}, with the mass the
   finite grid does not hold removed by ring integrals): second-order
   convergence on interior targets.
-* sigma_{D_2} and sigma_{D_5} disks of Sec. 5.2 (alpha = 0.25 centred at
+* sigma_{D_2} and sigma_{D_5} disks of Sec. 5.3 (alpha = 0.25 centred at
   (0.5, 0.1) on the destination grid [0.01, 1] x [0, 2 pi)): fitted orders in
   the L1, L2, Linf norms of Eq. 47-49 compared with the SIM column of Table 1
   (tests/golden/table1_sim_orders.txt).

@@ -1,5 +1,5 @@
 """Pins for the oracle's particle-method kernels (Eq. 35-37 and the softened
-comparison method of Sec. 5.2), against things other than their own formula:
+comparison method of Sec. 5.3), against things other than their own formula:
 
 * the far field: a source cell's exact integrals (Eq. 30, A11; pinned in
   test_oracle_kernels) approach the point mass at its centre with a relative
@@ -115,5 +115,5 @@ def test_particle_orders_against_table1(particle_orders):
             got, _ = particle_orders[(disk, kind, norm, comp)]
             tol = 0.15 if kind != "particle+" else 0.3  # the paper fits over N = 64 .. 1024
             assert abs(got - float(want)) < tol, (disk, kind, norm, comp, got, want)
-        # the modified method is the more accurate one (Sec. 5.2)
+        # the modified method is the more accurate one (Sec. 5.3)
         assert particle_orders[(disk, "particle+", norm, comp)][1] < particle_orders[(disk, "particle", norm, comp)][1]

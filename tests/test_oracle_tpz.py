@@ -8,7 +8,7 @@ own quadrature:
 * the trapezoidal rule's second order: the gap to the exact cell integrals
   falls like N_tpz^-2;
 * K^{phi,0}, K^{phi,r} and the own cell stay exact;
-* the SIM orders of Table 1 with N_tpz = 19, the value of Sec. 5.2.
+* the SIM orders of Table 1 with N_tpz = 19, the value of Sec. 5.3.
 """
 import math
 
