@@ -97,6 +97,33 @@ def test_adjoint_dot_identity(torch_cuda, oracle_mod):
     assert abs(lhs - rhs) < 1e-12 * float((gr.abs() * Fr.abs()).sum() + (gp.abs() * Fp.abs()).sum())
 
 
+@pytest.mark.parametrize("nu,nphi", [(256, 128), (512, 64)])
+def test_fp32_against_fp64_where_the_column_passes_fuse(torch_cuda, oracle_mod, nu, nphi):
+    """FP32 columns of 512 points or more: the forward applies the wedge
+    update inside the column pass, the adjoint beside the fused edge update.
+    The FP64 plan (separate kernels, pinned to the oracle above) is the
+    reference for both gradients."""
+    torch = torch_cuda
+    p32, grid, du = _setup(oracle_mod, nu, nphi, 0.1, 10.0, "float32", 1)
+    p64, _, _ = _setup(oracle_mod, nu, nphi, 0.1, 10.0, "float64", 1)
+    sigma, sigma_w = _inputs(grid, 21)
+    F32 = p32.forces_wedge(torch.tensor(sigma, dtype=torch.float32, device="cuda"),
+                           torch.tensor(sigma_w, dtype=torch.float32, device="cuda"))
+    F64 = p64.forces_wedge(torch.tensor(sigma, device="cuda"), torch.tensor(sigma_w, device="cuda"))
+    p32.check()
+    num = sum(float(((a.double() - b) ** 2).sum()) for a, b in zip(F32, F64))
+    den = sum(float((b ** 2).sum()) for b in F64)
+    assert math.sqrt(num / den) < 1e-5
+    gr, gp = workloads.random_field(nu, nphi, 22), workloads.random_field(nu, nphi, 23)
+    g32, gw32 = p32.backward_wedge(torch.tensor(gr, dtype=torch.float32, device="cuda"),
+                                   torch.tensor(gp, dtype=torch.float32, device="cuda"))
+    g64, gw64 = p64.backward_wedge(torch.tensor(gr, device="cuda"), torch.tensor(gp, device="cuda"))
+    p32.check()
+    for a, b in ((g32, g64), (gw32, gw64)):
+        ref = b.cpu().numpy()
+        assert np.linalg.norm(a.double().cpu().numpy() - ref) / np.linalg.norm(ref) < 1e-5
+
+
 def test_potential_with_the_wedge(torch_cuda, oracle_mod):
     torch = torch_cuda
     nu, nphi = 64, 128
