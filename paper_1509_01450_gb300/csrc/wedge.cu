@@ -12,7 +12,9 @@
 //   B[m][i] += wpre[i] (Wr[m][i] s^_w + Vr[m][i] a_0),
 //   C[m][i] += wpre[i] (-i) (Wphi[m][i] s^_w + Vphi[m][i] a_0),
 // with s^_w the phi-DFT of sigma_w and a_0 = A[m][0] / wpre[0] that of
-// sigma_0, applied between the column pass and the inverse-row pass.  Mode 0
+// sigma_0, applied between the column pass and the inverse-row pass by
+// k_wedge_fwd, or, for FP32 columns of 16 points per thread, inside the
+// forward column pass with s^_w formed ahead by k_wedge_dft.  Mode 0
 // packs (DC, Nyquist) as the passes do: real parts use the m = 0 tables,
 // imaginary parts the m = N_phi/2 ones, and the azimuthal terms vanish.
 // The adjoint forms the transposed sums t(m) per mode, adds the V part to
