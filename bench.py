@@ -36,10 +36,10 @@ NU, NPHI, R_IN, R_OUT, SEED = 2048, 4096, 0.01, 100.0, 1509
 # algorithmic bytes per cell of the three forward passes in FP32 (reads and
 # writes of the minimal data each pass must move, symmetry-reduced spectra)
 BYTES_PER_CELL = {"rows": 8.0, "cols": 20.0, "inv_rows": 16.0}
-# DRAM bytes (read + write) of one column-pass launch at 2048 x 4096 FP32, from
-# one ncu capture (profiles/k_fwd_2048x4096_full.md), valid only for the
-# kernel sources it was taken on (sha256 prefix of fftconv.cu + sg_common.cuh).
-COLS_TRAFFIC = {"sources_sha256": "5f95a5c5a059a456", "bytes_per_launch": 100.791808e6 + 6.804480e6}
+# DRAM bytes (read + write) of one launch of the dominant pass at 2048 x 4096
+# FP32, from one ncu capture of this command (--passes-only), valid only for
+# the kernel sources it was taken on (kernel_sources_sha below).
+PASS_TRAFFIC = {"pass": "cols", "sources_sha256": "5f95a5c5a059a456", "bytes_per_launch": 100.791808e6 + 6.804480e6}
 
 
 def kernel_sources_sha(texts=None) -> str:
@@ -256,6 +256,44 @@ def batch_throughput(torch, dev, flush, n_disks: int = 256, seed: int = 1450, re
             "graph_value": cells / (graph_ms * 1e-3), "graph_ms": graph_ms, "launches": 3 * n_disks}
 
 
+def run_passes_only(args):
+    """The forward and adjoint passes of the bench workload alone, for an
+    external profiler: one plan, W + K forward steps, then W + K adjoint
+    steps (same density, L2 flushed before each), the plan's error flag
+    checked at the end.  Prints one JSON line of mean step times; it is not
+    a bench line."""
+    import torch
+
+    import workloads
+    from paper_1509_01450_gb300 import Plan, build as cuda_build
+
+    cuda_build.build()
+    dev = torch.device("cuda", 0)
+    u_min, du = workloads.grid_params(NU, R_IN, R_OUT)
+    r, phi = workloads.centres(NU, NPHI, u_min, du)
+    plan = Plan(NU, NPHI, u_min, du, 1.0, "float32").build()
+    sigma = torch.tensor(workloads.lognormal_disk(r, phi, SEED), dtype=torch.float32, device=dev)
+    Fr, Fp = torch.empty_like(sigma), torch.empty_like(sigma)
+    gs = torch.empty_like(sigma)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    out = {"workload": WORKLOAD, "mode": "passes only"}
+    for name, fn in (("forward_ms", lambda: plan.forces(sigma, Fr, Fp)), ("backward_ms", lambda: plan.backward(Fr, Fp, gs))):
+        for _ in range(args.warmup):
+            flush.zero_()
+            fn()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for a, b in ev:
+            flush.zero_()
+            a.record()
+            fn()
+            b.record()
+        torch.cuda.synchronize()
+        out[name] = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    plan.check()
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -328,8 +366,9 @@ def run_ours(args):
     achieved = BYTES_PER_CELL[dom_name] * cells / (dom_ms * 1e-3) / 1e9
     total_bytes = sum(BYTES_PER_CELL.values()) * cells
     traffic = None
-    if dom_name == "cols" and (NU, NPHI) == (2048, 4096) and kernel_sources_sha() == COLS_TRAFFIC["sources_sha256"]:
-        traffic = COLS_TRAFFIC["bytes_per_launch"]
+    if (dom_name == PASS_TRAFFIC["pass"] and (NU, NPHI) == (2048, 4096)
+            and kernel_sources_sha() == PASS_TRAFFIC["sources_sha256"]):
+        traffic = PASS_TRAFFIC["bytes_per_launch"]
 
     # ---- adjoint and FP64, same protocol ----------------------------------
     def timed(fn, n):
@@ -482,6 +521,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 256-disk batching measurement")
     ap.add_argument("--size", default=None, help="NUxNPHI override (profiling runs only; not a bench line)")
+    ap.add_argument("--passes-only", action="store_true",
+                    help="time only the forward and adjoint passes (for profiler captures; not a bench line)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -491,6 +532,8 @@ def main():
         WORKLOAD = f"lognormal-grf-{NU}x{NPHI} (profiling size)"
     if args.impl == "reference":
         return run_reference(args)
+    if args.passes_only:
+        return run_passes_only(args)
     return run_ours(args)
 
 

@@ -40,7 +40,8 @@ static void free_plan(sg_plan* p)
     if (p->bjoin) cudaEventDestroy(p->bjoin);
     if (p->bfork) cudaEventDestroy(p->bfork);
     if (p->bstream) cudaStreamDestroy(p->bstream);
-    void* bufs[] = {p->tw, p->wa, p->wb, p->wc, p->kr, p->kp, p->wpre, p->wpost, p->tw64, p->cells, p->keff,
+    // wc lies inside wb's allocation
+    void* bufs[] = {p->tw, p->wa, p->wb, p->kr, p->kp, p->wpre, p->wpost, p->tw64, p->cells, p->keff,
                     p->h_sigma, p->h_fr, p->h_fp, p->derr, p->egr, p->egp, p->wtab, p->wtmp};
     for (void* b : bufs)
         if (b) cudaFree(b);
@@ -128,8 +129,8 @@ sg_status sg_plan_create(sg_plan** out, int nu, int nphi, double u_min, double d
     const size_t nk = (size_t)(nphi / 2 + 1) * (nu + 2);
     sg_status st;
     if ((st = dev_alloc(p, &p->tw, SG_NMAX * cx)) || (st = dev_alloc(p, &p->tw64, SG_NMAX * sizeof(double2))) ||
-        (st = dev_alloc(p, &p->wa, nhalf * cx)) || (st = dev_alloc(p, &p->wb, nhalf * cx)) ||
-        (st = dev_alloc(p, &p->wc, nhalf * cx)) || (st = dev_alloc(p, &p->kr, nk * cx)) ||
+        (st = dev_alloc(p, &p->wa, nhalf * cx)) || (st = dev_alloc(p, &p->wb, 2 * nhalf * cx)) ||
+        (st = dev_alloc(p, &p->kr, nk * cx)) ||
         (st = dev_alloc(p, &p->kp, nk * cx)) || (st = dev_alloc(p, &p->wpre, nu * p->elem)) ||
         (st = dev_alloc(p, &p->wpost, nu * p->elem)) || (st = dev_alloc(p, (void**)&p->derr, 16)) ||
         (st = dev_alloc(p, (void**)&p->cells, (size_t)6 * (2 * nu + 1) * nphi * sizeof(double))) ||
@@ -146,9 +147,11 @@ sg_status sg_plan_create(sg_plan** out, int nu, int nphi, double u_min, double d
         free_plan(p);
         return SG_ERR_CUDA;
     }
+    p->wc = (unsigned char*)p->wb + nhalf * cx;
     {
         void* const bufs[3] = {p->wa, p->wb, p->wc};
         make_row_maps(nu, nphi, p->elem, bufs, p->maps);
+        p->have_imaps = dtype == SG_F32 && make_pair_maps(nu, nphi, p->wa, p->wb, p->imaps) ? 1 : 0;
     }
     std::vector<double> re, im;
     twiddles(re, im);

@@ -232,10 +232,16 @@ __device__ __forceinline__ void st_pair(double2* p, double2 a, double2 b)
     p[1] = b;
 }
 
-__device__ __forceinline__ unsigned char* align128(unsigned char* p)
+// p advanced to the next multiple of A bytes of the shared window.  The
+// offset is added to the shared-memory pointer itself: a pointer rebuilt from
+// an integer would be generic, and every access through it would take the
+// L1TEX path (long-scoreboard waits) instead of a shared-memory instruction.
+template <unsigned A = 128>
+__device__ __forceinline__ unsigned char* align_smem(unsigned char* p)
 {
-    return reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(p) + 127) & ~(uintptr_t)127);
+    return p + ((A - (sg_smem_u32(p) & (A - 1))) & (A - 1));
 }
+__device__ __forceinline__ unsigned char* align128(unsigned char* p) { return align_smem<128>(p); }
 // modes per tensor-copy box
 __host__ __device__ __forceinline__ int row_box_modes(int half) { return half < 256 ? half : 256; }
 
@@ -603,10 +609,19 @@ __global__ void SG_FCOLS_BOUNDS(T, NTB, LG, EDGE) k_fwd_cols(const typename CX<T
                 w[e] = C2{w[e].x + f2(wi * dr.x, wi * dq.x), w[e].y + f2(wi * dr.y, wi * dq.y)};
             }
         }
+        if constexpr (LG > 0) {
+            // the pair layout: {B, C} of each row in 16 bytes (Br holds the pairs)
+            float4* P = reinterpret_cast<float4*>(Br) + (size_t)m * nu;
 #pragma unroll
-        for (int e = 0; e < E / 2; e++) {  // crop to N_u rows
-            sg_st_hint(Br + (size_t)m * nu + t + e * NT, c2_lo(w[e]), keep);
-            sg_st_hint(Cp + (size_t)m * nu + t + e * NT, c2_hi(w[e]), keep);
+            for (int e = 0; e < E / 2; e++)  // crop to N_u rows
+                sg_st_hint(P + t + e * NT, make_float4(f2_lo(w[e].x), f2_lo(w[e].y), f2_hi(w[e].x), f2_hi(w[e].y)),
+                           keep);
+        } else {
+#pragma unroll
+            for (int e = 0; e < E / 2; e++) {  // crop to N_u rows
+                sg_st_hint(Br + (size_t)m * nu + t + e * NT, c2_lo(w[e]), keep);
+                sg_st_hint(Cp + (size_t)m * nu + t + e * NT, c2_hi(w[e]), keep);
+            }
         }
         return;
     } else {
@@ -862,11 +877,12 @@ __global__ void __launch_bounds__(NTB, (sizeof(T) == 4 && NTB == 256) ? 2 : 1) k
 // packs (DC, Nyquist): its real parts use the DC spectra, its imaginary parts
 // the Nyquist ones, and both azimuthal spectra vanish there.
 // ===========================================================================
+// ps: element stride (in complex values) of B and C: 1, or 2 in the pair layout
 template <typename T>
 __global__ void __launch_bounds__(256) k_edge_fwd(const typename CX<T>::t* __restrict__ A, typename CX<T>::t* B,
                                                   typename CX<T>::t* C, const T* __restrict__ gr,
                                                   const T* __restrict__ gp, const T* __restrict__ wpre,
-                                                  EdgeCoef<T> coef, int nu, int nphi)
+                                                  EdgeCoef<T> coef, int nu, int nphi, int ps)
 {
     typedef typename CX<T>::t V;
     const int m = blockIdx.x, half = nphi / 2, K = sg_edge_stride(nu, sizeof(T));
@@ -902,11 +918,11 @@ __global__ void __launch_bounds__(256) k_edge_fwd(const typename CX<T>::t* __res
                 dp.x += p0[idx[a]] * sa[a].y;  // -i gp s = gp (s.y - i s.x)
                 dp.y -= p0[idx[a]] * sa[a].x;
             }
-            V c = C[(size_t)m * nu + i];
-            C[(size_t)m * nu + i] = V{c.x + w * dp.x, c.y + w * dp.y};
+            V c = C[((size_t)m * nu + i) * ps];
+            C[((size_t)m * nu + i) * ps] = V{c.x + w * dp.x, c.y + w * dp.y};
         }
-        V b = B[(size_t)m * nu + i];
-        B[(size_t)m * nu + i] = V{b.x + w * dr.x, b.y + w * dr.y};
+        V b = B[((size_t)m * nu + i) * ps];
+        B[((size_t)m * nu + i) * ps] = V{b.x + w * dr.x, b.y + w * dr.y};
     }
 }
 
@@ -915,11 +931,13 @@ __global__ void __launch_bounds__(256) k_edge_fwd(const typename CX<T>::t* __res
 // column pass's result,
 //   t_a = sum_i wpre[i] (gr_m[i - a] A[m][i] + i gp_m[i - a] C[m][i]),
 //   B[m][b] += sum_a coef[a][b] t_a   for b in {0, 1, N_u-2, N_u-1}.
+// ps: element stride (in complex values) of A and C: 1, or 2 in the pair layout
 template <typename T>
 __global__ void __launch_bounds__(256) k_edge_bwd(const typename CX<T>::t* __restrict__ A,
                                                   const typename CX<T>::t* __restrict__ C, typename CX<T>::t* B,
                                                   const T* __restrict__ gr, const T* __restrict__ gp,
-                                                  const T* __restrict__ wpre, EdgeCoef<T> coef, int nu, int nphi)
+                                                  const T* __restrict__ wpre, EdgeCoef<T> coef, int nu, int nphi,
+                                                  int ps)
 {
     typedef typename CX<T>::t V;
     __shared__ T red[8][8];
@@ -931,7 +949,7 @@ __global__ void __launch_bounds__(256) k_edge_bwd(const typename CX<T>::t* __res
     for (int i = threadIdx.x; i < nu; i += blockDim.x) {
         const int idx[4] = {i + 1 + nu, i + nu, i + 1, i};
         const T w = wpre[i];
-        const V a = A[(size_t)m * nu + i];
+        const V a = A[((size_t)m * nu + i) * ps];
         if (m == 0) {
 #pragma unroll
             for (int q = 0; q < 4; q++) {
@@ -939,7 +957,7 @@ __global__ void __launch_bounds__(256) k_edge_bwd(const typename CX<T>::t* __res
                 acc[2 * q + 1] += w * gN[idx[q]] * a.y;
             }
         } else {
-            const V c = C[(size_t)m * nu + i];
+            const V c = C[((size_t)m * nu + i) * ps];
 #pragma unroll
             for (int q = 0; q < 4; q++) {
                 const T r = w * g0[idx[q]], p = w * p0[idx[q]];
@@ -1148,8 +1166,11 @@ __global__ void SG_COLS_BOUNDS(T, NTB) k_bwd_cols(const typename CX<T>::t* __res
     // exchange area after the two columns (16 N_u + 8 GS bytes fit in its
     // 16 sg_padded(L) for N_u >= 8)
     T* const g_s = reinterpret_cast<T*>(smraw + 2 * (size_t)nu * sizeof(V));
+    // LG > 0: A and C arrive as one column of the pair layout (A holds the
+    // pairs), on bar[0]
+    constexpr bool pairs = LG > 0;
     if (t == 0) {  // the spectra first (written only by the build)
-        sg_mbar_expect_tx(&bar[1], ab + 2 * kb + (EDGE ? 2 * gb : 0));
+        sg_mbar_expect_tx(&bar[1], (pairs ? 0 : ab) + 2 * kb + (EDGE ? 2 * gb : 0));
         sg_bulk_g2s_hint(kr_s, Kr + (size_t)m * KS, kb, &bar[1], drop);
         sg_bulk_g2s_hint(kp_s, (m == 0 ? Kr + (size_t)half * KS : Kp + (size_t)m * KS), kb, &bar[1], drop);
         if constexpr (EDGE) {  // likewise the edge tables' rows
@@ -1160,9 +1181,14 @@ __global__ void SG_COLS_BOUNDS(T, NTB) k_bwd_cols(const typename CX<T>::t* __res
     sg_grid_dep_launch();
     sg_grid_dep_wait();  // A and C are the previous pass's results
     if (t == 0) {
-        sg_mbar_expect_tx(&bar[0], ab);
-        sg_bulk_g2s_hint(sm, A + (size_t)m * nu, ab, &bar[0], drop);
-        sg_bulk_g2s_hint(cs, C + (size_t)m * nu, ab, &bar[1], drop);
+        if constexpr (pairs) {
+            sg_mbar_expect_tx(&bar[0], 2 * ab);
+            sg_bulk_g2s_hint(sm, A + (size_t)2 * m * nu, 2 * ab, &bar[0], drop);
+        } else {
+            sg_mbar_expect_tx(&bar[0], ab);
+            sg_bulk_g2s_hint(sm, A + (size_t)m * nu, ab, &bar[0], drop);
+            sg_bulk_g2s_hint(cs, C + (size_t)m * nu, ab, &bar[1], drop);
+        }
     }
     const Twd<E, V> twd = make_twd<E>(log2L, t, tw);
     const uint64_t keep = sg_policy_evict_last();
@@ -1173,9 +1199,18 @@ __global__ void SG_COLS_BOUNDS(T, NTB) k_bwd_cols(const typename CX<T>::t* __res
     if constexpr (paired) {
         if (__syncthreads_or(!sg_mbar_wait_bounded(&bar[1], 0, err, 1, wlim))) return;
         C2 w[E];  // (X_a, X_c) of each frequency, paired
+        if constexpr (pairs) {
+            const float4* q = reinterpret_cast<const float4*>(sm);
 #pragma unroll
-        for (int e = 0; e < E; e++)
-            w[e] = (e < E / 2) ? c2(sm[t + e * NT], cs[t + e * NT]) : c2(V{0, 0}, V{0, 0});
+            for (int e = 0; e < E; e++) {
+                const float4 u = e < E / 2 ? q[t + e * NT] : make_float4(0.f, 0.f, 0.f, 0.f);
+                w[e] = C2{f2(u.x, u.z), f2(u.y, u.w)};
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < E; e++)
+                w[e] = (e < E / 2) ? c2(sm[t + e * NT], cs[t + e * NT]) : c2(V{0, 0}, V{0, 0});
+        }
         __shared__ T red[NTB / 32][8];  // EDGE: per-warp sums of t_a
         if constexpr (EDGE) {
             // this thread's rows' terms of t_a = sum_i wpre[i] (gr[i - a] A_i + i gp[i - a] C_i)
@@ -1505,52 +1540,312 @@ __global__ void __launch_bounds__(512) k_spec_cols(const double2* __restrict__ W
 }
 
 // ===========================================================================
+// FP32 row passes with the transform length N = 2^LG fixed at compile time,
+// moving the mode-major spectra in whole 32-byte L2 sectors.  A copy of
+// 16-byte pieces (one mode of two FP32 complex rows) runs at half the rate
+// of 32-byte ones, on the TMA unit and the load-store path alike, so every
+// thread or stage row here carries four complex values of one mode.
+//
+// One block per unit of rows: TPG = GT / (N/16) paired transforms
+// (sg_fft_pair: two complex FFTs in lockstep on the f32x2 instructions) of
+// GT = 256 threads (512 for 8192 points).  The unit's input lands in the
+// block's one shared-memory area by bulk or tensor copies, is read into
+// registers, and the area then serves as the transforms' exchange areas.
+// Blocks are small enough for three per SM (80 registers, 70 KB), so that
+// while one waits for its copies the others compute, as in the column pass.
+//
+//  k_rows_r2c<LG, BWD>: per transform four real rows in two complex FFTs,
+//    split into their half spectra.  Forward (P1): rows i0..i0+3 of sigma,
+//    z1 = w_i0 sigma_i0 + i w_i0+1 sigma_i0+1, z2 likewise for i0+2, i0+3;
+//    A[m][i0..i0+3] (8 bytes each) leave in one 256-bit store.  Adjoint
+//    (P1b): z1 = wpost_i0 (gF_r + i gF_phi)_i0, z2 for i0+1; the (A, C)
+//    pairs of both rows leave in one 256-bit store.
+//  k_rows_c2r<LG, BWD>: per transform one paired inverse FFT, staged by
+//    tensor copies whose box rows are 32 bytes (one mode of the transform's
+//    rows), stored with the 32-byte swizzle so that the stage reads are free
+//    of bank conflicts.  Forward (P3): rows (i0, i0+1) of the (B, C) pairs,
+//    Z = B + i C each; F_r, F_phi = Re, Im Z times wpost.  Adjoint (P3b):
+//    rows i0..i0+3 of B, Z = S_i0 + i S_i0+1 and S_i0+2 + i S_i0+3; gsigma
+//    = Re, Im times wpre.
+//
+// The pair layout P keeps two complex values per (mode, row) in 16 bytes:
+// P[m nu + i] = {X_i, Y_i}, m < N_phi/2 (forward X = B, Y = C; adjoint
+// X = A, Y = C); the single layout S[m nu + i] keeps one (forward A,
+// adjoint B).  Mode 0 packs (DC, Nyquist) in both.
+// ===========================================================================
+template <int LG>
+struct RowUnit {
+    static constexpr int N = 1 << LG, NT = N / 16;
+    static constexpr int GT = LG <= 12 ? 256 : 512;  // threads per block
+    static constexpr int TPG = GT / NT;              // paired transforms per block
+    static constexpr int MINB = LG <= 12 ? 3 : 1;    // blocks per SM the registers are bounded for
+    // the area: the transforms' exchange areas (C2 elements), plus the 1 KB alignment slack
+    static constexpr size_t SMEM = (size_t)TPG * (N + N / 16 + 1) * 16 + 1024;
+};
+
+// The half spectra of the real pairs packed in a paired transform: w holds
+// FFT(z1) in the low lanes and FFT(z2) in the high lanes (z = a + i b); on
+// return A[e] = (X_a of z1, X_a of z2) and B[e] = (X_b of z1, X_b of z2) at
+// m = t + e NT < N/2, mode 0 packed (DC, Nyquist).  sm is the transform's
+// exchange area (sg_padded(N) C2 elements), free on entry and on return.
+template <typename Sync>
+__device__ __forceinline__ void split_real_pair2(const C2 (&w)[16], C2* sm, int N, int t, C2 (&A)[8], C2 (&B)[8],
+                                                 const Sync& sync)
+{
+    const int NT = N / 16;
+#pragma unroll
+    for (int e = 0; e < 16; e++) sm[sg_pad(t + e * NT)] = w[e];
+    sync();
+    const F2 h = f2(0.5f, 0.5f);
+#pragma unroll
+    for (int e = 0; e < 8; e++) {
+        const int m = t + e * NT;
+        const C2 z = w[e];
+        const C2 zm = sm[sg_pad((N - m) & (N - 1))];  // Z[N - m]; conj of it below
+        if (m == 0) {
+            const C2 zn = sm[sg_pad(N / 2)];
+            A[e] = C2{z.x, zn.x};
+            B[e] = C2{z.y, zn.y};
+        } else {
+            A[e] = C2{(z.x + zm.x) * h, (z.y - zm.y) * h};  // (Z + conj Z[N-m]) / 2
+            B[e] = C2{(z.y + zm.y) * h, (zm.x - z.x) * h};  // (Z - conj Z[N-m]) / 2i
+        }
+    }
+    sync();  // every mirror read is done: the area is free
+}
+
+template <int LG>
+__host__ __device__ __forceinline__ size_t rows_unit_smem_bytes()
+{
+    return RowUnit<LG>::SMEM;
+}
+
+// DIRECT (forward only): sigma is memory the GPU reaches only by plain loads
+// (pinned host memory), read straight into registers without bulk copies
+template <int LG, bool BWD, bool DIRECT = false>
+__global__ void __launch_bounds__(RowUnit<LG>::GT, RowUnit<LG>::MINB)
+    k_rows_r2c(const float* __restrict__ x0, const float* __restrict__ x1, const float* __restrict__ wrow,
+               float2* __restrict__ out, int nu, const float2* __restrict__ tw, int* err)
+{
+    typedef RowUnit<LG> RU;
+    constexpr int N = RU::N, NT = RU::NT, TPG = RU::TPG;
+    constexpr int RPT = BWD ? 2 : 4;  // rows per transform
+    constexpr int R = RPT * TPG;      // rows per block
+    const unsigned long long wlim = sg_wait_budget(err);  // read once, early
+    extern __shared__ __align__(128) unsigned char smraw[];
+    __shared__ __align__(8) uint64_t bar;
+    unsigned char* const area = align128(smraw);
+    const int tr = threadIdx.x / NT, t = threadIdx.x % NT;  // transform, thread in it
+    const int u = blockIdx.x;                                // the unit: rows u R .. u R + R - 1
+    const int i0 = u * R + tr * RPT;
+    const Twd<16, float2> twd = make_twd<16>(LG, t, tw);
+    if (threadIdx.x == 0) sg_mbar_init(&bar, 1);
+    __syncthreads();
+    // the weights: forward w_i0..i0+3, adjoint (w_i0, w_i0, w_i1, w_i1); loaded while the rows land
+    float wt[4];
+#pragma unroll
+    for (int r = 0; r < 4; r++) wt[r] = __ldg(&wrow[i0 + (BWD ? r / 2 : r)]);
+    sg_grid_dep_launch();
+    sg_grid_dep_wait();  // the inputs may come from the previous kernel on the stream
+    if (!DIRECT && threadIdx.x == 0) {
+        // forward: rows u R .. u R + R - 1 of sigma; adjoint: the same rows of gF_r, then of gF_phi
+        const uint64_t pol = sg_policy_evict_first();
+        const uint32_t bytes = (uint32_t)R * N * 4;
+        float* dst = reinterpret_cast<float*>(area);
+        sg_mbar_expect_tx(&bar, BWD ? 2 * bytes : bytes);
+        sg_bulk_g2s_hint(dst, x0 + (size_t)u * R * N, bytes, &bar, pol);
+        if constexpr (BWD) sg_bulk_g2s_hint(dst + (size_t)R * N, x1 + (size_t)u * R * N, bytes, &bar, pol);
+    }
+    if (!DIRECT && __syncthreads_or(!sg_mbar_wait_bounded(&bar, 0, err, 1, wlim))) return;  // inputs never arrived
+    // the four real rows (p, q, r, s) of this transform: z1 = p + i q, z2 = r + i s
+    const float *rp, *rq, *rr, *rs;
+    if constexpr (DIRECT) {
+        rp = x0 + (size_t)i0 * N;
+        rq = rp + N;
+        rr = rp + 2 * N;
+        rs = rp + 3 * N;
+    } else {
+        const float* in = reinterpret_cast<const float*>(area);
+        if constexpr (BWD) {
+            rp = in + (size_t)tr * 2 * N;        // gF_r row i0
+            rr = rp + N;                          // gF_r row i0 + 1
+            rq = in + (size_t)(R + tr * 2) * N;  // gF_phi row i0
+            rs = rq + N;                          // gF_phi row i0 + 1
+        } else {
+            rp = in + (size_t)tr * 4 * N;
+            rq = rp + N;
+            rr = rp + 2 * N;
+            rs = rp + 3 * N;
+        }
+    }
+    const F2 wx = f2(wt[0], wt[2]), wy = f2(wt[1], wt[3]);
+    C2 w[16];
+#pragma unroll
+    for (int e = 0; e < 16; e++) {
+        const int n = t + e * NT;
+        w[e] = C2{f2(rp[n], rr[n]) * wx, f2(rq[n], rs[n]) * wy};
+    }
+    __syncthreads();  // every transform has read its rows: the area holds the exchange areas
+    C2* const sm = reinterpret_cast<C2*>(area) + (size_t)tr * sg_padded(N);
+    const SgSyncBlock bsync;
+    sg_fft_pair<-1, LG>(w, sm, N, LG, t, twd.h, bsync);
+    C2 xa[8], xb[8];
+    split_real_pair2(w, sm, N, t, xa, xb, bsync);
+    // forward: A[m][i0..i0+3]; adjoint: {A, C} of rows i0, i0+1 (32 bytes, aligned)
+    const uint64_t keep = sg_policy_evict_last();  // the column pass reads the spectra from L2
+#pragma unroll
+    for (int e = 0; e < 8; e++) {
+        const size_t mi = (size_t)(t + e * NT) * nu + i0;
+        float* q = reinterpret_cast<float*>(out) + (BWD ? 4 : 2) * mi;
+        sg_st256_hint(q, make_float4(f2_lo(xa[e].x), f2_lo(xa[e].y), f2_lo(xb[e].x), f2_lo(xb[e].y)),
+                      make_float4(f2_hi(xa[e].x), f2_hi(xa[e].y), f2_hi(xb[e].x), f2_hi(xb[e].y)), keep);
+    }
+}
+
+// map: 2-D tensor map over the input (forward: the pair layout, two 8-byte
+// units per row; adjoint: the single layout, one unit per row) with boxes
+// of 4 units x min(N/2, 256) modes and the 32-byte swizzle
+template <int LG, bool BWD>
+__global__ void __launch_bounds__(RowUnit<LG>::GT, RowUnit<LG>::MINB)
+    k_rows_c2r(const __grid_constant__ CUtensorMap map, const float* __restrict__ wrow, float* __restrict__ y0,
+               float* __restrict__ y1, int nu, const float2* __restrict__ tw, int* err)
+{
+    typedef RowUnit<LG> RU;
+    constexpr int N = RU::N, NT = RU::NT, TPG = RU::TPG, half = N / 2;
+    constexpr int RPT = BWD ? 4 : 2;  // rows per transform
+    constexpr int R = RPT * TPG;      // rows per block
+    constexpr int MB = half < 256 ? half : 256, NBOX = half / MB;
+    const unsigned long long wlim = sg_wait_budget(err);  // read once, early
+    extern __shared__ __align__(128) unsigned char smraw[];
+    __shared__ __align__(8) uint64_t bar;
+    unsigned char* const area = align_smem<1024>(smraw);  // the swizzle repeats every 256 bytes
+    const int tr = threadIdx.x / NT, t = threadIdx.x % NT;
+    const int u = blockIdx.x;
+    const int i0 = u * R + tr * RPT;
+    const Twd<16, float2> twd = make_twd<16>(LG, t, tw);
+    if (threadIdx.x == 0) sg_mbar_init(&bar, 1);
+    __syncthreads();
+    // the output rows' weights: forward (w_i0, w_i0, w_i0+1, w_i0+1), adjoint w_i0..i0+3
+    float wt[4];
+#pragma unroll
+    for (int r = 0; r < 4; r++) wt[r] = __ldg(&wrow[i0 + (BWD ? r : r / 2)]);
+    sg_grid_dep_launch();
+    sg_grid_dep_wait();  // the spectra are the previous pass's results
+    if (threadIdx.x < 32) {
+        // transform j's rows land at j N x 16 bytes, mode n of them at 32 n
+        const int lane = threadIdx.x;
+        if (lane == 0) sg_mbar_expect_tx(&bar, (uint32_t)(TPG * half * 32));
+        __syncwarp();
+        const uint64_t drop = sg_policy_evict_first();  // the spectra are consumed here
+        for (int j = lane; j < TPG * NBOX; j += 32) {
+            const int s = j / NBOX, b = j % NBOX;
+            sg_tma_load_2d(area + (size_t)s * N * 16 + (size_t)b * MB * 32, &map, (BWD ? 1 : 2) * (u * R + s * RPT),
+                           b * MB, &bar, drop);
+        }
+    }
+    if (__syncthreads_or(!sg_mbar_wait_bounded(&bar, 0, err, 1, wlim))) return;  // inputs never arrived
+    const float4* const S4 = reinterpret_cast<const float4*>(area) + (size_t)tr * N;  // this transform's modes
+    // Z of both lanes at frequency n.  Each mode holds two 16-byte units u0,
+    // u1 (forward: {B, C} of rows i0, i0+1; adjoint: {S_i0, S_i0+1}, {S_i0+2,
+    // S_i0+3}), the halves of modes with bit 2 set swapped by the swizzle.
+    // With u = (p.x, p.y, q.x, q.y): Z = p + i q below N/2 and conj p + i
+    // conj q above (q of mode 0 vanishes in the forward direction: the
+    // azimuthal kernel is odd)
+    C2 w[16];
+#pragma unroll
+    for (int e = 0; e < 16; e++) {
+        const int n = t + e * NT;
+        const int mo = e < 8 ? n : (n == half ? 0 : N - n);  // n = N/2 reads mode 0 (Nyquist)
+        const int sw = (mo >> 2) & 1;
+        const float4 u0 = S4[2 * mo + sw], u1 = S4[2 * mo + (sw ^ 1)];
+        if (n == 0)
+            w[e] = C2{f2(u0.x, u1.x), f2(u0.z, u1.z)};
+        else if (n == half)
+            w[e] = C2{f2(u0.y, u1.y), f2(u0.w, u1.w)};
+        else if (e < 8)
+            w[e] = C2{f2(u0.x - u0.w, u1.x - u1.w), f2(u0.y + u0.z, u1.y + u1.z)};
+        else
+            w[e] = C2{f2(u0.x + u0.w, u1.x + u1.w), f2(u0.z - u0.y, u1.z - u1.y)};
+    }
+    __syncthreads();  // the exchange areas lie over the other transforms' stages
+    sg_fft_pair<+1, LG>(w, reinterpret_cast<C2*>(area) + (size_t)tr * sg_padded(N), N, LG, t, twd.h);
+    // the four output rows: forward (F_r, F_phi) of i0, then of i0+1;
+    // adjoint gsigma of i0 .. i0+3; values Re, Im of the low, then high lanes
+    float* o[4];
+    if constexpr (BWD) {
+#pragma unroll
+        for (int r = 0; r < 4; r++) o[r] = y0 + (size_t)(i0 + r) * N;
+    } else {
+        o[0] = y0 + (size_t)i0 * N;
+        o[1] = y1 + (size_t)i0 * N;
+        o[2] = y0 + (size_t)(i0 + 1) * N;
+        o[3] = y1 + (size_t)(i0 + 1) * N;
+    }
+#pragma unroll
+    for (int e = 0; e < 16; e++) {
+        const int n = t + e * NT;
+        o[0][n] = f2_lo(w[e].x) * wt[0];
+        o[1][n] = f2_lo(w[e].y) * wt[1];
+        o[2][n] = f2_hi(w[e].x) * wt[2];
+        o[3][n] = f2_hi(w[e].y) * wt[3];
+    }
+}
+
+// ===========================================================================
 // FP32 pass kernels whose transform length 2^LG is fixed at compile time.
 // Each length's instances are compiled in a translation unit of their own
 // (fftconv_lg<LG>.cu, which includes this file for its kernels only) and
-// reached through fixed_pass_kernels(); other lengths and FP64 take the
-// run-time instances.  Block sizes are those of the run-time launches: 256
-// threads up to 4096 points, one 512-thread transform beyond.
+// reached through fixed_pass_kernels().  A plan whose row length N_phi and
+// column length 2 N_u both have instances runs all its passes on them, with
+// the column spectra in the pair layout; other plans take the run-time
+// instances and separate B, C buffers.  Row blocks are 256 threads up to
+// 4096 points (several slots below), one 512-thread transform beyond;
+// column blocks are one transform of 2 N_u / 16 threads.
 // ===========================================================================
-// the six FP32 pass kernels' signatures (spelled out: naming an instance
-// here would refer to kernels that each translation unit does not define)
-typedef void (*FwdRowsFn)(const float*, const float*, float2*, int, int, int, const float2*, int*, CUtensorMap,
-                          int, int);
+// the pass kernels' signatures (spelled out: naming an instance here would
+// refer to kernels that each translation unit does not define)
+typedef void (*RowsR2CFn)(const float*, const float*, const float*, float2*, int, const float2*, int*);
+typedef void (*RowsC2RFn)(CUtensorMap, const float*, float*, float*, int, const float2*, int*);
 typedef void (*FwdColsFn)(const float2*, const float2*, const float2*, float2*, float2*, int, int, int,
                           const float2*, int*, const float*, const float*, const float*, EdgeCoef<float>,
                           WedgeArgs<float>);
-typedef void (*FwdRowsInvFn)(const float2*, const float2*, const float*, float*, float*, int, int, int,
-                             const float2*, int*, CUtensorMap, CUtensorMap, int);
-typedef void (*BwdRowsFn)(const float*, const float*, const float*, float2*, float2*, int, int, int, const float2*,
-                          int*, CUtensorMap, CUtensorMap, int);
 typedef void (*BwdColsFn)(const float2*, const float2*, const float2*, const float2*, float2*, int, int, int,
                           const float2*, int*, const float*, const float*, const float*, EdgeCoef<float>);
-typedef void (*BwdRowsInvFn)(const float2*, const float*, float*, int, int, int, const float2*, int*, CUtensorMap,
-                             int);
 
 struct FixedPassKernels {
-    FwdRowsFn fwd_rows;
+    RowsR2CFn fwd_rows;         // k_rows_r2c, forward
+    RowsR2CFn fwd_rows_direct;  // the same reading sigma from host memory the GPU can reach
+    RowsR2CFn bwd_rows;         // k_rows_r2c, adjoint
+    RowsC2RFn fwd_rows_inv;  // k_rows_c2r, forward
+    RowsC2RFn bwd_rows_inv;  // k_rows_c2r, adjoint
+    size_t r2c_smem, c2r_smem;
     FwdColsFn fwd_cols;
-    FwdColsFn fwd_cols_edge;  // with the edge-slope update
+    FwdColsFn fwd_cols_edge;        // with the edge-slope update
     FwdColsFn fwd_cols_edge_wedge;  // with the edge-slope and origin-wedge updates
-    FwdRowsInvFn fwd_rows_inv;
-    BwdRowsFn bwd_rows;
     BwdColsFn bwd_cols;
     BwdColsFn bwd_cols_edge;  // with the transposed edge-slope update
-    BwdRowsInvFn bwd_rows_inv;
-    int threads;  // block size of the row and column instances
+    int threads;  // block size of the row instances
+    int slots;    // paired transforms per row block (RowUnit::TPG)
 };
 
 template <int LG>
 FixedPassKernels make_fixed_pass_kernels()
 {
     constexpr int NB = (1 << LG) / 16 > 256 ? 512 : 256;
-    return FixedPassKernels{k_fwd_rows<float, 16, NB, LG>,       k_fwd_cols<float, 16, NB, LG>,
-                            k_fwd_cols<float, 16, NB, LG, true>, k_fwd_cols<float, 16, NB, LG, true, true>,
-                            k_fwd_rows_inv<float, 16, NB, LG>,
-                            k_bwd_rows<float, 16, LG>,           k_bwd_cols<float, 16, NB, LG>,
-                            k_bwd_cols<float, 16, NB, LG, true>, k_bwd_rows_inv<float, 16, NB, LG>,
-                            NB};
+    return FixedPassKernels{k_rows_r2c<LG, false>,
+                            k_rows_r2c<LG, false, true>,
+                            k_rows_r2c<LG, true>,
+                            k_rows_c2r<LG, false>,
+                            k_rows_c2r<LG, true>,
+                            rows_unit_smem_bytes<LG>(),
+                            rows_unit_smem_bytes<LG>(),
+                            k_fwd_cols<float, 16, NB, LG>,
+                            k_fwd_cols<float, 16, NB, LG, true>,
+                            k_fwd_cols<float, 16, NB, LG, true, true>,
+                            k_bwd_cols<float, 16, NB, LG>,
+                            k_bwd_cols<float, 16, NB, LG, true>,
+                            RowUnit<LG>::GT,
+                            RowUnit<LG>::TPG};
 }
 
 // defined in fftconv_lg<LG>.cu
@@ -1736,6 +2031,25 @@ void make_row_maps(int nu, int nphi, size_t elem, void* const bufs[3], SgRowMaps
     }
 }
 
+bool make_pair_maps(int nu, int nphi, void* wa, void* wb, CUtensorMap out[2])
+{
+    EncodeTiledFn enc = tensor_map_encoder();
+    if (!enc || nphi < 32) return false;
+    const int half = nphi / 2, MB = row_box_modes(half);
+    for (int k = 0; k < 2; k++) {
+        const int c = k == 0 ? 2 : 1;  // 8-byte units per row: (X, Y) pairs, single values
+        const cuuint64_t dims[2] = {(cuuint64_t)c * nu, (cuuint64_t)half};
+        const cuuint64_t strides[1] = {(cuuint64_t)c * nu * 8};
+        const cuuint32_t box[2] = {4, (cuuint32_t)MB};
+        const cuuint32_t estr[2] = {1, 1};
+        if (enc(&out[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, k == 0 ? wb : wa, dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return false;
+    }
+    return true;
+}
+
 // the map of buffer b for row blocks of R rows, or null
 static const CUtensorMap* row_map(const PlanView& p, int R, int b, int nphi)
 {
@@ -1766,20 +2080,45 @@ static cudaError_t launch_edges(const PlanView& p, bool adjoint, cudaStream_t st
     PassRange range_(adjoint ? "sg adjoint edge slopes" : "sg forward edge slopes");
     EdgeCoef<T> coef;
     for (int j = 0; j < 16; j++) coef.c[j] = (T)p.ecoef[j];
+    // the pair layout: wb holds (B, C) forward and (A, C) in the adjoint, wa the adjoint's B
+    const int ps = p.pairs ? 2 : 1;
+    V* const X = (V*)p.wb;
+    V* const Y = p.pairs ? (V*)p.wb + 1 : (V*)p.wc;
     if (adjoint)
-        k_edge_bwd<T><<<p.nphi / 2, 256, 0, st>>>((const V*)p.wa, (const V*)p.wc, (V*)p.wb, (const T*)p.egr,
-                                                  (const T*)p.egp, (const T*)p.wpre, coef, p.nu, p.nphi);
+        k_edge_bwd<T><<<p.nphi / 2, 256, 0, st>>>(p.pairs ? X : (const V*)p.wa, Y, p.pairs ? (V*)p.wa : X,
+                                                  (const T*)p.egr, (const T*)p.egp, (const T*)p.wpre, coef, p.nu,
+                                                  p.nphi, ps);
     else
-        k_edge_fwd<T><<<p.nphi / 2, 256, 0, st>>>((const V*)p.wa, (V*)p.wb, (V*)p.wc, (const T*)p.egr,
-                                                  (const T*)p.egp, (const T*)p.wpre, coef, p.nu, p.nphi);
+        k_edge_fwd<T><<<p.nphi / 2, 256, 0, st>>>((const V*)p.wa, X, Y, (const T*)p.egr, (const T*)p.egp,
+                                                  (const T*)p.wpre, coef, p.nu, p.nphi, ps);
     return cudaGetLastError();
 }
 
+// The fixed-length instances of both transform lengths, when every pass of
+// the plan can run on them: FP32, N_phi and 2 N_u of 256 .. 8192 points, the
+// pair layout's tensor maps made, N_u a multiple of the row blocks.  The
+// passes then keep the column spectra in the pair layout.
 template <typename T>
-cudaError_t launch_forward(const PlanView& p, const T* sigma, T* Fr, T* Fp, cudaStream_t st, cudaEvent_t* ev,
+static bool fixed_path(const PlanView& p, const FixedPassKernels*& fr, const FixedPassKernels*& fc)
+{
+    fr = fc = nullptr;
+    if (sizeof(T) != 4 || !p.imaps) return false;
+    const FixedPassKernels* a = fixed_pass_kernels(sg_ilog2(p.nphi));
+    const FixedPassKernels* b = fixed_pass_kernels(sg_ilog2(2 * p.nu));
+    if (!a || !b || p.nu % (4 * a->slots) != 0) return false;
+    fr = a;
+    fc = b;
+    return true;
+}
+
+template <typename T>
+cudaError_t launch_forward(const PlanView& p0, const T* sigma, T* Fr, T* Fp, cudaStream_t st, cudaEvent_t* ev,
                            bool sigma_direct)
 {
     typedef typename CX<T>::t V;
+    const FixedPassKernels *fr, *fc;
+    PlanView p = p0;
+    p.pairs = fixed_path<T>(p0, fr, fc) ? 1 : 0;
     const V* tw = (const V*)p.tw;
     V* A = (V*)p.wa;
     V* B = (V*)p.wb;
@@ -1794,22 +2133,30 @@ cudaError_t launch_forward(const PlanView& p, const T* sigma, T* Fr, T* Fp, cuda
     if (wedge_fused && (err = launch_wedge_dft<T>(p, st)) != cudaSuccess) return err;
     {
         PassRange range_("sg forward rows");
-        Shape s = shape_for<V>(p.nphi, sizeof(T) == 8 ? 64 : 256);
-        const int R = 2 * s.slots, nblk = (p.nu + R - 1) / R;
-        const size_t smem = rows_fwd_smem_bytes<V>(p.nphi, s.slots);
-        const CUtensorMap* mA = row_map(p, R, 0, p.nphi);
-        SG_DISPATCH_E(s.E, {
-            auto k = k_fwd_rows<T, EE, 256>;
-            if constexpr (sizeof(T) == 4)  // FP64 blocks are at most 256 threads
-                if (s.threads > 256) k = k_fwd_rows<T, EE, 512>;
-            if constexpr (sizeof(T) == 4 && EE == 16)  // length fixed at compile time
-                if (const FixedPassKernels* f = fixed_pass_kernels(ln))
-                    if (s.threads == f->threads) k = f->fwd_rows;
-            if ((err = set_smem(k, smem, true)) != cudaSuccess) return err;
-            if ((err = launch_pdl(k, persistent_grid(k, s.threads, smem, nblk, p.sms), s.threads, smem, st, 
-                sigma, (const T*)p.wpre, A, p.nu, p.nphi, ln, tw, p.err, mA ? *mA : CUtensorMap{}, mA != nullptr,
-                sigma_direct ? 1 : 0)) != cudaSuccess) return err;
-        });
+        if (p.pairs) {
+            const int nblk = p.nu / (4 * fr->slots);
+            auto k = sigma_direct ? fr->fwd_rows_direct : fr->fwd_rows;
+            if ((err = set_smem(k, fr->r2c_smem, true)) != cudaSuccess) return err;
+            if ((err = launch_pdl(k, nblk, fr->threads,
+                                  fr->r2c_smem, st, (const float*)sigma, (const float*)nullptr, (const float*)p.wpre,
+                                  (float2*)p.wa, p.nu, (const float2*)p.tw, p.err)) != cudaSuccess)
+                return err;
+        } else {
+            Shape s = shape_for<V>(p.nphi, sizeof(T) == 8 ? 64 : 256);
+            const int R = 2 * s.slots, nblk = (p.nu + R - 1) / R;
+            const size_t smem = rows_fwd_smem_bytes<V>(p.nphi, s.slots);
+            const CUtensorMap* mA = row_map(p, R, 0, p.nphi);
+            SG_DISPATCH_E(s.E, {
+                auto k = k_fwd_rows<T, EE, 256>;
+                if constexpr (sizeof(T) == 4)  // FP64 blocks are at most 256 threads
+                    if (s.threads > 256) k = k_fwd_rows<T, EE, 512>;
+                if ((err = set_smem(k, smem, true)) != cudaSuccess) return err;
+                if ((err = launch_pdl(k, persistent_grid(k, s.threads, smem, nblk, p.sms), s.threads, smem, st,
+                                      sigma, (const T*)p.wpre, A, p.nu, p.nphi, ln, tw, p.err,
+                                      mA ? *mA : CUtensorMap{}, mA != nullptr, sigma_direct ? 1 : 0)) != cudaSuccess)
+                    return err;
+            });
+        }
     }
     if (ev && (err = cudaEventRecord(ev[1], st)) != cudaSuccess) return err;
     bool edges_done = false;  // the column pass applied the edge-slope update itself
@@ -1818,6 +2165,7 @@ cudaError_t launch_forward(const PlanView& p, const T* sigma, T* Fr, T* Fp, cuda
         const int L = 2 * p.nu, E = L >= 16 ? 16 : L;
         EdgeCoef<T> coef;
         for (int j = 0; j < 16; j++) coef.c[j] = p.edges ? (T)p.ecoef[j] : (T)0;
+        const WedgeArgs<T> wdg{(const V*)p.wtmp, (const T*)p.wtab};
         SG_DISPATCH_E(E, {
             const bool fuse = sizeof(T) == 4 && EE == 16 && p.edges;
             const bool fusew = fuse && p.wedge;  // == wedge_fused
@@ -1828,14 +2176,12 @@ cudaError_t launch_forward(const PlanView& p, const T* sigma, T* Fr, T* Fp, cuda
                 if (fuse) k = L / EE > 256 ? k_fwd_cols<T, 16, 512, 0, true> : k_fwd_cols<T, 16, 256, 0, true>;
                 if (fusew)
                     k = L / EE > 256 ? k_fwd_cols<T, 16, 512, 0, true, true> : k_fwd_cols<T, 16, 256, 0, true, true>;
-                if (const FixedPassKernels* f = fixed_pass_kernels(lL))
-                    if (L / EE <= f->threads)
-                        k = fusew ? f->fwd_cols_edge_wedge : fuse ? f->fwd_cols_edge : f->fwd_cols;
+                if (p.pairs)  // the fixed-length instance writes the (B, C) pairs into wb
+                    k = fusew ? fc->fwd_cols_edge_wedge : fuse ? fc->fwd_cols_edge : fc->fwd_cols;
             }
             const size_t smem =
                 cols_smem_bytes<T>(p.nu) + (fuse ? 2 * (size_t)sg_edge_stride(p.nu, sizeof(T)) * sizeof(T) : 0);
             if ((err = set_smem(k, smem, true)) != cudaSuccess) return err;
-            const WedgeArgs<T> wdg{(const V*)p.wtmp, (const T*)p.wtab};
             if ((err = launch_pdl(k, p.nphi / 2, L / EE, smem, st, A, (const V*)p.kr, (const V*)p.kp, B, C, p.nu,
                                   p.nphi, lL, tw, p.err, (const T*)p.egr, (const T*)p.egp, (const T*)p.wpre,
                                   coef, wdg)) != cudaSuccess)
@@ -1848,33 +2194,44 @@ cudaError_t launch_forward(const PlanView& p, const T* sigma, T* Fr, T* Fp, cuda
     if (ev && (err = cudaEventRecord(ev[2], st)) != cudaSuccess) return err;
     {
         PassRange range_("sg forward inverse rows");
-        Shape s = shape_for<V>(p.nphi, sizeof(T) == 8 ? 64 : 256);
-        const int R = 2 * s.slots, nblk = (p.nu + R - 1) / R;
-        const size_t smem = rows_inv_smem_bytes<V>(p.nphi, s.slots);
-        const CUtensorMap* mB = row_map(p, R, 1, p.nphi);
-        const CUtensorMap* mC = row_map(p, R, 2, p.nphi);
-        const bool um = mB && mC;
-        SG_DISPATCH_E(s.E, {
-            auto k = k_fwd_rows_inv<T, EE, 256>;
-            if constexpr (sizeof(T) == 4)  // FP64 blocks are at most 256 threads
-                if (s.threads > 256) k = k_fwd_rows_inv<T, EE, 512>;
-            if constexpr (sizeof(T) == 4 && EE == 16)
-                if (const FixedPassKernels* f = fixed_pass_kernels(ln))
-                    if (s.threads == f->threads) k = f->fwd_rows_inv;
-            if ((err = set_smem(k, smem, true)) != cudaSuccess) return err;
-            if ((err = launch_pdl(k, persistent_grid(k, s.threads, smem, nblk, p.sms), s.threads, smem, st, 
-                B, C, (const T*)p.wpost, Fr, Fp, p.nu, p.nphi, ln, tw, p.err, um ? *mB : CUtensorMap{},
-                um ? *mC : CUtensorMap{}, um)) != cudaSuccess) return err;
-        });
+        if (p.pairs) {
+            const int nblk = p.nu / (2 * fr->slots);
+            auto k = fr->fwd_rows_inv;
+            if ((err = set_smem(k, fr->c2r_smem, true)) != cudaSuccess) return err;
+            if ((err = launch_pdl(k, nblk, fr->threads,
+                                  fr->c2r_smem, st, p.imaps[0], (const float*)p.wpost, (float*)Fr, (float*)Fp, p.nu,
+                                  (const float2*)p.tw, p.err)) != cudaSuccess)
+                return err;
+        } else {
+            Shape s = shape_for<V>(p.nphi, sizeof(T) == 8 ? 64 : 256);
+            const int R = 2 * s.slots, nblk = (p.nu + R - 1) / R;
+            const size_t smem = rows_inv_smem_bytes<V>(p.nphi, s.slots);
+            const CUtensorMap* mB = row_map(p, R, 1, p.nphi);
+            const CUtensorMap* mC = row_map(p, R, 2, p.nphi);
+            const bool um = mB && mC;
+            SG_DISPATCH_E(s.E, {
+                auto k = k_fwd_rows_inv<T, EE, 256>;
+                if constexpr (sizeof(T) == 4)  // FP64 blocks are at most 256 threads
+                    if (s.threads > 256) k = k_fwd_rows_inv<T, EE, 512>;
+                if ((err = set_smem(k, smem, true)) != cudaSuccess) return err;
+                if ((err = launch_pdl(k, persistent_grid(k, s.threads, smem, nblk, p.sms), s.threads, smem, st, B,
+                                      C, (const T*)p.wpost, Fr, Fp, p.nu, p.nphi, ln, tw, p.err,
+                                      um ? *mB : CUtensorMap{}, um ? *mC : CUtensorMap{}, um)) != cudaSuccess)
+                    return err;
+            });
+        }
     }
     if (ev && (err = cudaEventRecord(ev[3], st)) != cudaSuccess) return err;
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_backward(const PlanView& p, const T* gr, const T* gp, T* gs, cudaStream_t st)
+cudaError_t launch_backward(const PlanView& p0, const T* gr, const T* gp, T* gs, cudaStream_t st)
 {
     typedef typename CX<T>::t V;
+    const FixedPassKernels *fr, *fc;
+    PlanView p = p0;
+    p.pairs = fixed_path<T>(p0, fr, fc) ? 1 : 0;
     const V* tw = (const V*)p.tw;
     V* A = (V*)p.wa;
     V* B = (V*)p.wb;
@@ -1884,22 +2241,30 @@ cudaError_t launch_backward(const PlanView& p, const T* gr, const T* gp, T* gs, 
     bool edges_done = false;  // the column pass applied the transposed edge update itself
     {
         PassRange range_("sg adjoint rows");
-        Shape s = shape_for<V>(p.nphi, row_min_threads(sizeof(T)));
-        const int R = s.slots, nblk = (p.nu + R - 1) / R;
-        const size_t smem = row_smem_bytes<V>(p.nphi, s.slots);
-        const CUtensorMap* mA = row_map(p, R, 0, p.nphi);
-        const CUtensorMap* mC = row_map(p, R, 2, p.nphi);
-        const bool um = mA && mC;
-        SG_DISPATCH_E(s.E, {
-            auto k = k_bwd_rows<T, EE>;
-            if constexpr (sizeof(T) == 4 && EE == 16)
-                if (const FixedPassKernels* f = fixed_pass_kernels(ln))
-                    if (s.threads == 512) k = f->bwd_rows;
-            if ((err = set_smem(k, smem, true)) != cudaSuccess) return err;
-            if ((err = launch_pdl(k, persistent_grid(k, s.threads, smem, nblk, p.sms), s.threads, smem, st, 
-                gr, gp, (const T*)p.wpost, A, C, p.nu, p.nphi, ln, tw, p.err, um ? *mA : CUtensorMap{},
-                um ? *mC : CUtensorMap{}, um)) != cudaSuccess) return err;
-        });
+        if (p.pairs) {  // (A, C) pairs into wb
+            const int nblk = p.nu / (2 * fr->slots);
+            auto k = fr->bwd_rows;
+            if ((err = set_smem(k, fr->r2c_smem, true)) != cudaSuccess) return err;
+            if ((err = launch_pdl(k, nblk, fr->threads,
+                                  fr->r2c_smem, st, (const float*)gr, (const float*)gp, (const float*)p.wpost,
+                                  (float2*)p.wb, p.nu, (const float2*)p.tw, p.err)) != cudaSuccess)
+                return err;
+        } else {
+            Shape s = shape_for<V>(p.nphi, row_min_threads(sizeof(T)));
+            const int R = s.slots, nblk = (p.nu + R - 1) / R;
+            const size_t smem = row_smem_bytes<V>(p.nphi, s.slots);
+            const CUtensorMap* mA = row_map(p, R, 0, p.nphi);
+            const CUtensorMap* mC = row_map(p, R, 2, p.nphi);
+            const bool um = mA && mC;
+            SG_DISPATCH_E(s.E, {
+                auto k = k_bwd_rows<T, EE>;
+                if ((err = set_smem(k, smem, true)) != cudaSuccess) return err;
+                if ((err = launch_pdl(k, persistent_grid(k, s.threads, smem, nblk, p.sms), s.threads, smem, st, gr,
+                                      gp, (const T*)p.wpost, A, C, p.nu, p.nphi, ln, tw, p.err,
+                                      um ? *mA : CUtensorMap{}, um ? *mC : CUtensorMap{}, um)) != cudaSuccess)
+                    return err;
+            });
+        }
     }
     {
         PassRange range_("sg adjoint columns");
@@ -1914,14 +2279,14 @@ cudaError_t launch_backward(const PlanView& p, const T* gr, const T* gp, T* gs, 
                 if (L / EE > 256) k = k_bwd_cols<T, EE, 512>;
             if constexpr (sizeof(T) == 4 && EE == 16) {
                 if (fuse) k = L / EE > 256 ? k_bwd_cols<T, 16, 512, 0, true> : k_bwd_cols<T, 16, 256, 0, true>;
-                if (const FixedPassKernels* f = fixed_pass_kernels(lL))
-                    if (L / EE <= f->threads) k = fuse ? f->bwd_cols_edge : f->bwd_cols;
+                if (p.pairs) k = fuse ? fc->bwd_cols_edge : fc->bwd_cols;  // reads the (A, C) pairs of wb
             }
             const size_t smem = bcols_smem_bytes<T>(p.nu);  // the edge rows share the exchange area
             if ((err = set_smem(k, smem, true)) != cudaSuccess) return err;
-            if ((err = launch_pdl(k, p.nphi / 2, L / EE, smem, st, A, C, (const V*)p.kr, (const V*)p.kp, B, p.nu,
-                                  p.nphi, lL, tw, p.err, (const T*)p.egr, (const T*)p.egp, (const T*)p.wpre,
-                                  coef)) != cudaSuccess)
+            // the pair layout: the (A, C) pairs in wb, B into wa
+            if ((err = launch_pdl(k, p.nphi / 2, L / EE, smem, st, p.pairs ? B : A, C, (const V*)p.kr,
+                                  (const V*)p.kp, p.pairs ? A : B, p.nu, p.nphi, lL, tw, p.err, (const T*)p.egr,
+                                  (const T*)p.egp, (const T*)p.wpre, coef)) != cudaSuccess)
                 return err;
             edges_done = fuse;
         });
@@ -1930,21 +2295,30 @@ cudaError_t launch_backward(const PlanView& p, const T* gr, const T* gp, T* gs, 
     if (p.wedge && (err = launch_wedge<T>(p, true, st)) != cudaSuccess) return err;
     {
         PassRange range_("sg adjoint inverse rows");
-        Shape s = shape_for<V>(p.nphi, sizeof(T) == 8 ? 64 : 256);
-        const int R = 2 * s.slots, nblk = (p.nu + R - 1) / R;
-        const size_t smem = rows_bwd_inv_smem_bytes<V>(p.nphi, s.slots);
-        const CUtensorMap* mB = row_map(p, R, 1, p.nphi);
-        SG_DISPATCH_E(s.E, {
-            auto k = k_bwd_rows_inv<T, EE, 256>;
-            if constexpr (sizeof(T) == 4)
-                if (s.threads > 256) k = k_bwd_rows_inv<T, EE, 512>;
-            if constexpr (sizeof(T) == 4 && EE == 16)
-                if (const FixedPassKernels* f = fixed_pass_kernels(ln))
-                    if (s.threads == f->threads) k = f->bwd_rows_inv;
-            if ((err = set_smem(k, smem, true)) != cudaSuccess) return err;
-            if ((err = launch_pdl(k, persistent_grid(k, s.threads, smem, nblk, p.sms), s.threads, smem, st, 
-                B, (const T*)p.wpre, gs, p.nu, p.nphi, ln, tw, p.err, mB ? *mB : CUtensorMap{}, mB != nullptr)) != cudaSuccess) return err;
-        });
+        if (p.pairs) {  // B from wa
+            const int nblk = p.nu / (4 * fr->slots);
+            auto k = fr->bwd_rows_inv;
+            if ((err = set_smem(k, fr->c2r_smem, true)) != cudaSuccess) return err;
+            if ((err = launch_pdl(k, nblk, fr->threads,
+                                  fr->c2r_smem, st, p.imaps[1], (const float*)p.wpre, (float*)gs, (float*)nullptr,
+                                  p.nu, (const float2*)p.tw, p.err)) != cudaSuccess)
+                return err;
+        } else {
+            Shape s = shape_for<V>(p.nphi, sizeof(T) == 8 ? 64 : 256);
+            const int R = 2 * s.slots, nblk = (p.nu + R - 1) / R;
+            const size_t smem = rows_bwd_inv_smem_bytes<V>(p.nphi, s.slots);
+            const CUtensorMap* mB = row_map(p, R, 1, p.nphi);
+            SG_DISPATCH_E(s.E, {
+                auto k = k_bwd_rows_inv<T, EE, 256>;
+                if constexpr (sizeof(T) == 4)
+                    if (s.threads > 256) k = k_bwd_rows_inv<T, EE, 512>;
+                if ((err = set_smem(k, smem, true)) != cudaSuccess) return err;
+                if ((err = launch_pdl(k, persistent_grid(k, s.threads, smem, nblk, p.sms), s.threads, smem, st, B,
+                                      (const T*)p.wpre, gs, p.nu, p.nphi, ln, tw, p.err, mB ? *mB : CUtensorMap{},
+                                      mB != nullptr)) != cudaSuccess)
+                    return err;
+            });
+        }
     }
     return cudaGetLastError();
 }

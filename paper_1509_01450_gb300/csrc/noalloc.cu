@@ -82,10 +82,12 @@ extern "C" sg_status sg_forces_noalloc(sg_plan* p, const void* sigma, void* F_r,
         if (!p->have_na_maps) {
             void* const bufs[3] = {v.wa, v.wb, v.wc};
             make_row_maps(p->nu, p->nphi, p->elem, bufs, p->na_maps);
+            p->have_na_imaps = p->dtype == SG_F32 && make_pair_maps(p->nu, p->nphi, v.wa, v.wb, p->na_imaps) ? 1 : 0;
             p->have_na_maps = 1;
         }
     }
     v.maps = p->na_maps;
+    v.imaps = p->have_na_imaps ? p->na_imaps : nullptr;
     cudaError_t e = p->dtype == SG_F32
                         ? launch_forward<float>(v, (const float*)sigma, (float*)F_r, (float*)F_phi, stream)
                         : launch_forward<double>(v, (const double*)sigma, (double*)F_r, (double*)F_phi, stream);

@@ -386,6 +386,13 @@ __device__ __forceinline__ void sg_st_hint(float4* a, float4 v, uint64_t pol)
                  "f"(v.z), "f"(v.w), "l"(pol)
                  : "memory");
 }
+// 32 bytes (a whole L2 sector) from one thread: a, then b; p 32-byte aligned
+__device__ __forceinline__ void sg_st256_hint(float* p, float4 a, float4 b, uint64_t pol)
+{
+    asm volatile("st.global.L2::cache_hint.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8}, %9;" ::"l"(p), "f"(a.x),
+                 "f"(a.y), "f"(a.z), "f"(a.w), "f"(b.x), "f"(b.y), "f"(b.z), "f"(b.w), "l"(pol)
+                 : "memory");
+}
 // read-only loads (data not written during the kernel)
 __device__ __forceinline__ float4 sg_ld_hint(const float4* a, uint64_t pol)
 {

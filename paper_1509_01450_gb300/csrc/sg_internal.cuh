@@ -27,8 +27,8 @@ struct sg_plan {
     // working-dtype device buffers
     void* tw;        // twiddle table, SG_NMAX complex
     void* wa;        // half spectra, mode-major X[m nu + i], nu * nphi/2 complex
-    void* wb;        // same
-    void* wc;        // same
+    void* wb;        // same; wb and wc are one allocation (wc = wb + nu nphi/2 values), which
+    void* wc;        // the fixed-length FP32 passes use as one buffer of (B, C) or (A, C) pairs
     void* kr;        // Khat_r, (nphi/2 + 1) x (nu + 2) complex
     void* kp;        // Khat_phi, same shape
     void* wpre;      // beta^{p (i - i_ref)}, nu reals
@@ -47,6 +47,12 @@ struct sg_plan {
     SgRowMaps maps[2];     // for R = slots and 2 slots rows per row block
     SgRowMaps na_maps[2];  // the same over the allocation-free scratch
     int have_na_maps;
+    // tensor maps of the fixed-length FP32 inverse row passes (make_pair_maps):
+    // [0] over wb in the pair layout, [1] over wa; have_imaps = 0 if none
+    CUtensorMap imaps[2];
+    int have_imaps;
+    CUtensorMap na_imaps[2];  // the same over the allocation-free scratch
+    int have_na_imaps;
     cudaStream_t bstream;         // this plan's items of a batch run here, concurrently with other plans'
     cudaEvent_t bfork, bjoin;     // fork from / join back to the batch caller's stream
     cudaEvent_t ev[4];  // pass timing (sg_forces_timed), created on first use
@@ -79,6 +85,9 @@ struct PlanView {
     const void* wpost;
     int* err;
     const SgRowMaps* maps;  // [2] over wa, wb, wc, or null
+    const CUtensorMap* imaps;  // [2] of make_pair_maps over wb (pairs) and wa, or null
+    int pairs;              // set by the launchers: the column spectra are in the pair layout
+                            // (forward: wb holds (B, C); adjoint: wb holds (A, C), wa holds B)
     int edges;              // one-sided radial edge slopes: egr, egp, ecoef below
     const void* egr;
     const void* egp;
@@ -107,6 +116,8 @@ inline PlanView view(const sg_plan* p)
     v.wpost = p->wpost;
     v.err = p->derr;
     v.maps = p->maps;
+    v.imaps = p->have_imaps ? p->imaps : nullptr;
+    v.pairs = 0;
     v.edges = p->edges;
     v.egr = p->egr;
     v.egp = p->egp;
@@ -137,6 +148,11 @@ cudaError_t launch_wedge_dft(const PlanView& p, cudaStream_t st);
 // Tensor maps of the row passes over the buffers bufs[3] (the layout of wa,
 // wb, wc); out[k].R = 0 where a map cannot be made.
 void make_row_maps(int nu, int nphi, size_t elem, void* const bufs[3], SgRowMaps out[2]);
+// Tensor maps of the fixed-length FP32 inverse row passes: out[0] over wb as
+// the pair layout (two 8-byte units per row), out[1] over wa (one unit per
+// row); boxes of 4 units x min(N_phi/2, 256) modes with the 32-byte swizzle.
+// False if they cannot be made (the passes then use the run-time instances).
+bool make_pair_maps(int nu, int nphi, void* wa, void* wb, CUtensorMap out[2]);
 template <typename VO>
 cudaError_t launch_spectra(const PlanView& p, const double* nsr, const double* nsp, double2* W, VO* Kr, VO* Kp,
                            cudaStream_t st);

@@ -65,11 +65,12 @@ __device__ __forceinline__ T blk_sum(T v, T* red)
     return s;
 }
 
+// ps: element stride (in complex values) of B and C: 1, or 2 in the pair layout
 template <typename T>
 __global__ void __launch_bounds__(256) k_wedge_fwd(const typename CX<T>::t* __restrict__ A, typename CX<T>::t* B,
                                                    typename CX<T>::t* C, const T* __restrict__ sigw,
                                                    const T* __restrict__ tab, const T* __restrict__ wpre,
-                                                   const typename CX<T>::t* __restrict__ tw, int nu, int nphi)
+                                                   const typename CX<T>::t* __restrict__ tw, int nu, int nphi, int ps)
 {
     typedef typename CX<T>::t V;
     __shared__ T red[8];
@@ -99,7 +100,7 @@ __global__ void __launch_bounds__(256) k_wedge_fwd(const typename CX<T>::t* __re
     const T* VrN = tab + 2 * tsz + (long)half * nu;
     for (int i = threadIdx.x; i < nu; i += blockDim.x) {
         const T w = wpre[i];
-        V b = B[(size_t)m * nu + i];
+        V b = B[((size_t)m * nu + i) * ps];
         if (m == 0) {
             b.x += w * (Wr[i] * sx + Vr[i] * ax);
             b.y += w * (WrN[i] * sy + VrN[i] * ay);
@@ -108,12 +109,12 @@ __global__ void __launch_bounds__(256) k_wedge_fwd(const typename CX<T>::t* __re
             b.y += w * (Wr[i] * sy + Vr[i] * ay);
             // -i (p s) = p (s.y - i s.x)
             const T px = Wp[i] * sx + Vp[i] * ax, py = Wp[i] * sy + Vp[i] * ay;
-            V c = C[(size_t)m * nu + i];
+            V c = C[((size_t)m * nu + i) * ps];
             c.x += w * py;
             c.y -= w * px;
-            C[(size_t)m * nu + i] = c;
+            C[((size_t)m * nu + i) * ps] = c;
         }
-        B[(size_t)m * nu + i] = b;
+        B[((size_t)m * nu + i) * ps] = b;
     }
 }
 
@@ -121,11 +122,12 @@ __global__ void __launch_bounds__(256) k_wedge_fwd(const typename CX<T>::t* __re
 // gF_phi and B the backward column pass's result,
 //   t_W(m) = sum_i wpre[i] (Wr[m][i] A[m][i] + i Wphi[m][i] C[m][i]),  t_V likewise,
 //   B[m][0] += t_V(m) / wpre[0],   tw[m] = t_W(m).
+// ps: element stride (in complex values) of A and C: 1, or 2 in the pair layout
 template <typename T>
 __global__ void __launch_bounds__(256) k_wedge_bwd(const typename CX<T>::t* __restrict__ A,
                                                    const typename CX<T>::t* __restrict__ C, typename CX<T>::t* B,
                                                    const T* __restrict__ tab, const T* __restrict__ wpre,
-                                                   typename CX<T>::t* __restrict__ t_out, int nu, int nphi)
+                                                   typename CX<T>::t* __restrict__ t_out, int nu, int nphi, int ps)
 {
     typedef typename CX<T>::t V;
     __shared__ T red[8];
@@ -140,14 +142,14 @@ __global__ void __launch_bounds__(256) k_wedge_bwd(const typename CX<T>::t* __re
     T wx = 0, wy = 0, vx = 0, vy = 0;
     for (int i = threadIdx.x; i < nu; i += blockDim.x) {
         const T w = wpre[i];
-        const V a = A[(size_t)m * nu + i];
+        const V a = A[((size_t)m * nu + i) * ps];
         if (m == 0) {
             wx += w * Wr[i] * a.x;
             wy += w * WrN[i] * a.y;
             vx += w * Vr[i] * a.x;
             vy += w * VrN[i] * a.y;
         } else {
-            const V c = C[(size_t)m * nu + i];
+            const V c = C[((size_t)m * nu + i) * ps];
             // i p c = p (-c.y + i c.x)
             wx += w * (Wr[i] * a.x - Wp[i] * c.y);
             wy += w * (Wr[i] * a.y + Wp[i] * c.x);
@@ -234,16 +236,19 @@ template <typename T>
 cudaError_t launch_wedge(const PlanView& p, bool adjoint, cudaStream_t st)
 {
     typedef typename CX<T>::t V;
+    // the pair layout: wb holds (B, C) forward and (A, C) in the adjoint, wa the adjoint's B
+    const int ps = p.pairs ? 2 : 1;
+    V* const X = (V*)p.wb;
+    V* const Y = p.pairs ? (V*)p.wb + 1 : (V*)p.wc;
     if (adjoint) {
         if (!p.gsigw) return cudaErrorInvalidValue;
-        k_wedge_bwd<T><<<p.nphi / 2, 256, 0, st>>>((const V*)p.wa, (const V*)p.wc, (V*)p.wb, (const T*)p.wtab,
-                                                   (const T*)p.wpre, (V*)p.wtmp, p.nu, p.nphi);
+        k_wedge_bwd<T><<<p.nphi / 2, 256, 0, st>>>(p.pairs ? X : (const V*)p.wa, Y, p.pairs ? (V*)p.wa : X,
+                                                   (const T*)p.wtab, (const T*)p.wpre, (V*)p.wtmp, p.nu, p.nphi, ps);
         k_wedge_idft<T><<<p.nphi, 256, 0, st>>>((const V*)p.wtmp, (const V*)p.tw, (T*)p.gsigw, p.nphi);
     } else {
         if (!p.sigw) return cudaErrorInvalidValue;
-        k_wedge_fwd<T><<<p.nphi / 2, 256, 0, st>>>((const V*)p.wa, (V*)p.wb, (V*)p.wc, (const T*)p.sigw,
-                                                   (const T*)p.wtab, (const T*)p.wpre, (const V*)p.tw, p.nu,
-                                                   p.nphi);
+        k_wedge_fwd<T><<<p.nphi / 2, 256, 0, st>>>((const V*)p.wa, X, Y, (const T*)p.sigw, (const T*)p.wtab,
+                                                   (const T*)p.wpre, (const V*)p.tw, p.nu, p.nphi, ps);
     }
     return cudaGetLastError();
 }
