@@ -4,6 +4,9 @@ Each translation unit under csrc/ is compiled by nvcc in parallel, then
 linked into paper_1509_01450_gb300/libsgdisk.so.  Usage:
 
     python -m paper_1509_01450_gb300.build [--force] [--verbose-ptxas]
+
+Extra nvcc options may come from the environment variable SG_NVCC_FLAGS
+(split on white space); the objects are rebuilt whenever they change.
 """
 from __future__ import annotations
 
@@ -42,6 +45,15 @@ def build(force: bool = False, verbose_ptxas: bool = False) -> str:
     os.makedirs(OBJ, exist_ok=True)
     hdrs = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(HERE, "..", "include", "sg.h")]
     flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
+    extra = os.environ.get("SG_NVCC_FLAGS", "").split()
+    flags += extra
+    # a change of the extra options rebuilds every object
+    stamp = os.path.join(OBJ, "flags.txt")
+    old = open(stamp).read() if os.path.exists(stamp) else None
+    if old != " ".join(extra):
+        force = True
+        with open(stamp, "w") as f:
+            f.write(" ".join(extra))
     if verbose_ptxas:
         flags += ["-Xptxas", "-v"]
     jobs = []

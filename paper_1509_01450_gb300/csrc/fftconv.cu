@@ -122,12 +122,14 @@ __device__ __forceinline__ Twd<E, V> make_twd(int log2N, int t, const V* __restr
 }
 // LG > 0: the transform length 2^LG is fixed at compile time (FP32, 16
 // points per thread), see sg_fft
-template <int E, int DIR, int LG = 0, typename V, typename Sync = SgSyncBlock>
+// ZH: the thread elements e >= E/2 are zero (register-twiddle transforms
+// skip their terms in the first pass)
+template <int E, int DIR, int LG = 0, bool ZH = false, typename V, typename Sync = SgSyncBlock>
 __device__ __forceinline__ void fft(V (&v)[E], V* sm, int N, int log2N, int t, const Twd<E, V>& w,
                                     const Sync& sync = Sync())
 {
     if constexpr (E == 16 && sizeof(V) == 8)
-        sg_fft<E, DIR, LG>(v, sm, N, log2N, t, w.h, sync);
+        sg_fft<E, DIR, LG, ZH>(v, sm, N, log2N, t, w.h, sync);
     else
         sg_fft<E, DIR>(v, sm, N, log2N, t, w.tab, sync);
 }
@@ -534,7 +536,7 @@ __global__ void SG_FCOLS_BOUNDS(T, NTB, LG, EDGE) k_fwd_cols(const typename CX<T
         }
     }
     if constexpr (sizeof(T) == 4 && E == 16) {
-        fft<E, -1, LG>(v, sm, L, log2L, t, twd);  // the spectra land meanwhile
+        fft<E, -1, LG, true>(v, sm, L, log2L, t, twd);  // rows >= N_u are zero; the spectra land meanwhile
         if (__syncthreads_or(!sg_mbar_wait_bounded(&bar[1], 0, err, 1, wlim))) return;
         C2 w[E];  // (Y_r, Y_phi) of each frequency, paired
         if (m == 0) {
@@ -1244,7 +1246,8 @@ __global__ void SG_COLS_BOUNDS(T, NTB) k_bwd_cols(const typename CX<T>::t* __res
                 for (int v = 0; v < 8; v++) red[t >> 5][v] = acc[v];
             // read after the transforms' barriers
         }
-        sg_fft_pair<-1, LG>(w, reinterpret_cast<C2*>(smraw), L, log2L, t, twd.h);  // waits for the landing reads
+        // rows >= N_u are zero; the transform's first exchange waits for the landing reads
+        sg_fft_pair<-1, LG, true>(w, reinterpret_cast<C2*>(smraw), L, log2L, t, twd.h);
         V y[E];
         if (m == 0) {
             // X_a is the FFT of (DC + i Nyquist); the phi kernel vanishes at
@@ -1573,12 +1576,17 @@ __global__ void __launch_bounds__(512) k_spec_cols(const double2* __restrict__ W
 // X = A, Y = C); the single layout S[m nu + i] keeps one (forward A,
 // adjoint B).  Mode 0 packs (DC, Nyquist) in both.
 // ===========================================================================
+// blocks per SM the fixed-length row passes' registers are bounded for
+// (3: 80 registers, the shared memory of three 70 KB areas)
+#ifndef SG_ROWS_MINB
+#define SG_ROWS_MINB 3
+#endif
 template <int LG>
 struct RowUnit {
     static constexpr int N = 1 << LG, NT = N / 16;
     static constexpr int GT = LG <= 12 ? 256 : 512;  // threads per block
     static constexpr int TPG = GT / NT;              // paired transforms per block
-    static constexpr int MINB = LG <= 12 ? 3 : 1;    // blocks per SM the registers are bounded for
+    static constexpr int MINB = LG <= 12 ? SG_ROWS_MINB : 1;
     // the area: the transforms' exchange areas (C2 elements), plus the 1 KB alignment slack
     static constexpr size_t SMEM = (size_t)TPG * (N + N / 16 + 1) * 16 + 1024;
 };

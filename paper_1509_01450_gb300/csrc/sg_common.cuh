@@ -199,6 +199,104 @@ __device__ __forceinline__ void sg_dft16(V* a)
     t = a[11]; a[11] = a[14]; a[14] = t;
 }
 
+// The butterflies of a first pass whose inputs r >= R/2 are zero (the
+// zero-padded half of a transform): the same outputs, without the
+// additions of zeros (which IEEE signed zeros keep the compiler from
+// folding).  a4 below is the pair (a0, a1) of a 4-point DFT with a2 = a3 = 0.
+// x + DIR i d and x - DIR i d, the factor folded into the additions
+template <int DIR, typename V>
+__device__ __forceinline__ V cadd_i(V x, V d)
+{
+    return DIR > 0 ? V{x.x - d.y, x.y + d.x} : V{x.x + d.y, x.y - d.x};
+}
+template <int DIR, typename V>
+__device__ __forceinline__ V csub_i(V x, V d)
+{
+    return DIR > 0 ? V{x.x + d.y, x.y - d.x} : V{x.x - d.y, x.y + d.x};
+}
+
+template <int DIR, typename V>
+__device__ __forceinline__ void sg_dft4v_zh(V& a0, V& a1, V& a2, V& a3)
+{
+    const V b0 = a0, b1 = a1;
+    a0 = cadd(b0, b1);
+    a2 = csub(b0, b1);
+    a1 = cadd_i<DIR>(b0, b1);
+    a3 = csub_i<DIR>(b0, b1);
+}
+
+template <int R, int DIR, typename V>
+__device__ __forceinline__ void sg_dft_zh(V* a)
+{
+    if (R == 2) a[1] = a[0];
+    if (R == 4) sg_dft4v_zh<DIR>(a[0], a[1], a[2], a[3]);
+    if (R == 8) {
+        // sg_dft8 with a4..a7 = 0: the two 4-point halves are (a0, a2) and (a1, a3)
+        V e0 = a[0], e2 = a[2], o1 = a[1], o3 = a[3];
+        sg_dft4v_zh<DIR>(e0, e2, a[4], a[6]);
+        a[0] = e0;
+        a[2] = e2;
+        sg_dft4v_zh<DIR>(o1, o3, a[5], a[7]);
+        a[1] = o1;
+        a[3] = o3;
+        const V q1 = sg_mulw8<DIR, 1>(a[3]);
+        const V d2 = a[5];
+        const V q3 = sg_mulw8<DIR, 3>(a[7]);
+        const V f0 = a[0], f1 = a[2], f2_ = a[4], f3 = a[6], g0 = a[1];
+        a[0] = cadd(f0, g0);
+        a[4] = csub(f0, g0);
+        a[1] = cadd(f1, q1);
+        a[5] = csub(f1, q1);
+        a[2] = cadd_i<DIR>(f2_, d2);
+        a[6] = csub_i<DIR>(f2_, d2);
+        a[3] = cadd(f3, q3);
+        a[7] = csub(f3, q3);
+    }
+    if (R == 16) {
+        // sg_dft16 with a8..a15 = 0: its first four 4-point DFTs lose half their terms
+        sg_dft4v_zh<DIR>(a[0], a[4], a[8], a[12]);
+        sg_dft4v_zh<DIR>(a[1], a[5], a[9], a[13]);
+        sg_dft4v_zh<DIR>(a[2], a[6], a[10], a[14]);
+        sg_dft4v_zh<DIR>(a[3], a[7], a[11], a[15]);
+        a[5] = sg_mulw16<DIR, 1>(a[5]);
+        a[9] = sg_mulw16<DIR, 2>(a[9]);
+        a[13] = sg_mulw16<DIR, 3>(a[13]);
+        a[6] = sg_mulw16<DIR, 2>(a[6]);
+        a[10] = sg_mulw16<DIR, 4>(a[10]);
+        a[14] = sg_mulw16<DIR, 6>(a[14]);
+        a[7] = sg_mulw16<DIR, 3>(a[7]);
+        a[11] = sg_mulw16<DIR, 6>(a[11]);
+        a[15] = sg_mulw16<DIR, 9>(a[15]);
+        sg_dft4v<DIR>(a[0], a[1], a[2], a[3]);
+        sg_dft4v<DIR>(a[4], a[5], a[6], a[7]);
+        sg_dft4v<DIR>(a[8], a[9], a[10], a[11]);
+        sg_dft4v<DIR>(a[12], a[13], a[14], a[15]);
+        V t;
+        t = a[1]; a[1] = a[4]; a[4] = t;
+        t = a[2]; a[2] = a[8]; a[8] = t;
+        t = a[3]; a[3] = a[12]; a[12] = t;
+        t = a[6]; a[6] = a[9]; a[9] = t;
+        t = a[7]; a[7] = a[13]; a[13] = t;
+        t = a[11]; a[11] = a[14]; a[14] = t;
+    }
+}
+
+// The untwiddled first pass (Ns = 1) of a transform whose thread elements
+// e >= E/2 are zero: butterfly s takes v[s + r E/R], zero for r >= R/2.
+template <int R, int E, int DIR, typename V>
+__device__ __forceinline__ void sg_pass_first_zh(V (&v)[E])
+{
+#pragma unroll
+    for (int s = 0; s < E / R; s++) {
+        V a[R];
+#pragma unroll
+        for (int r = 0; r < R / 2; r++) a[r] = v[s + r * (E / R)];
+        sg_dft_zh<R, DIR>(a);
+#pragma unroll
+        for (int r = 0; r < R; r++) v[s + r * (E / R)] = a[r];
+    }
+}
+
 template <int R, int DIR, typename V>
 __device__ __forceinline__ void sg_dft(V* a)
 {
@@ -607,7 +705,9 @@ __device__ __forceinline__ void sg_pass16_tw(V (&v)[16], V w)
     sg_dft<16, DIR>(v);
 }
 
-template <int E, int DIR, int LG = 0, typename V, typename Sync = SgSyncBlock>
+// ZH: the thread elements e >= E/2 are zero on entry (a zero-padded half);
+// the first pass skips their terms
+template <int E, int DIR, int LG = 0, bool ZH = false, typename V, typename Sync = SgSyncBlock>
 __device__ __forceinline__ void sg_fft(V (&v)[E], V* sm, int N_, int log2N_, int t, const SgTwid<V>& tws,
                                        const Sync& sync = Sync())
 {
@@ -619,7 +719,16 @@ __device__ __forceinline__ void sg_fft(V (&v)[E], V* sm, int N_, int log2N_, int
     const int rem = log2N & 3;
     const int n16 = (log2N >> 2) - (rem == 0 ? 1 : 0);
     const V* none = nullptr;
-    if (rem == 1)
+    if constexpr (ZH) {
+        if (rem == 1)
+            sg_pass_first_zh<2, E, DIR>(v);
+        else if (rem == 2)
+            sg_pass_first_zh<4, E, DIR>(v);
+        else if (rem == 3)
+            sg_pass_first_zh<8, E, DIR>(v);
+        else
+            sg_pass_first_zh<16, E, DIR>(v);
+    } else if (rem == 1)
         sg_pass_compute<2, E, DIR>(v, t, NT, 1, none);
     else if (rem == 2)
         sg_pass_compute<4, E, DIR>(v, t, NT, 1, none);
@@ -730,6 +839,18 @@ __device__ __forceinline__ void sg_dft4v(C2& a0, C2& a1, C2& a2, C2& a3)
     }
 }
 
+// (a.x + i a.y)(c + i s) with c, s the same in both lanes: four paired
+// instructions, the real part's negated product taken from -s
+__device__ __forceinline__ C2 cmul_cs(C2 a, F2 c, F2 s, F2 ns) { return C2{f2_fma(a.x, c, a.y * ns), f2_fma(a.x, s, a.y * c)}; }
+
+// a times the twiddle w shared by both lanes (its parts broadcast to the two
+// lanes; the sign of -w.y flipped in the integer unit)
+__device__ __forceinline__ C2 cmul_b(C2 a, float2 w)
+{
+    const float nwy = __int_as_float(__float_as_int(w.y) ^ (int)0x80000000);
+    return cmul_cs(a, f2(w.x, w.x), f2(w.y, w.y), f2(nwy, nwy));
+}
+
 // e^{DIR 2 pi i j / 16} a for the constant twiddles of the radix-16 butterfly
 template <int DIR, int J>
 __device__ __forceinline__ C2 sg_mulw16(C2 a)
@@ -750,8 +871,27 @@ __device__ __forceinline__ C2 sg_mulw16(C2 a)
         const F2 z = f2(0.f, 0.f);
         return DIR > 0 ? C2{z - a.y, a.x} : C2{a.y, z - a.x};
     }
-    const F2 cc = f2(c, c), ss = f2(s, s);
-    return C2{a.x * cc - a.y * ss, f2_fma(a.x, ss, a.y * cc)};
+    return cmul_cs(a, f2(c, c), f2(s, s), f2(-s, -s));
+}
+
+// v[r] *= w^r (r = 1..15) for two transforms sharing the twiddle w: the
+// powers come from the same product tree as sg_twiddle_powers, in scalar
+// FP32 (one lane's work, not two), and multiply both lanes by cmul_b
+__device__ __forceinline__ void sg_twiddle_powers_b(C2 (&v)[16], float2 w1)
+{
+    float2 w[16];
+    w[1] = w1;
+    w[2] = cmul(w1, w1);
+    w[3] = cmul(w[2], w1);
+    w[4] = cmul(w[2], w[2]);
+    w[5] = cmul(w[4], w1);
+    w[6] = cmul(w[4], w[2]);
+    w[7] = cmul(w[4], w[3]);
+    w[8] = cmul(w[4], w[4]);
+#pragma unroll
+    for (int r = 9; r < 16; r++) w[r] = cmul(w[8], w[r - 8]);
+#pragma unroll
+    for (int r = 1; r < 16; r++) v[r] = cmul_b(v[r], w[r]);
 }
 
 // e^{DIR i pi k / 4} a, k = 1, 3, for the radix-8 butterfly
@@ -790,7 +930,7 @@ __device__ __forceinline__ void sg_dft8(C2* a)
 // Two transforms of length N (E = 16 points per thread each), twiddles from
 // the registers of sg_fft_twiddles (the same for both).  Same exchange
 // pattern as sg_fft; sm holds sg_padded(N) C2 elements (16 bytes each).
-template <int DIR, int LG = 0, typename Sync = SgSyncBlock>
+template <int DIR, int LG = 0, bool ZH = false, typename Sync = SgSyncBlock>
 __device__ __forceinline__ void sg_fft_pair(C2 (&v)[16], C2* sm, int N_, int log2N_, int t,
                                             const SgTwid<float2>& tws, const Sync& sync = Sync())
 {
@@ -801,6 +941,10 @@ __device__ __forceinline__ void sg_fft_pair(C2 (&v)[16], C2* sm, int N_, int log
     const int n16 = (log2N >> 2) - (rem == 0 ? 1 : 0);
     auto first = [&](auto Rc) {
         constexpr int R = decltype(Rc)::value;
+        if constexpr (ZH) {  // elements e >= 8 are zero (see sg_fft)
+            sg_pass_first_zh<R, E, DIR>(v);
+            return;
+        }
 #pragma unroll
         for (int s = 0; s < E / R; s++) {
             C2 a[R];
@@ -837,7 +981,7 @@ __device__ __forceinline__ void sg_fft_pair(C2 (&v)[16], C2* sm, int N_, int log
         sync();
         float2 w = p == 0 ? tws.w[0] : (p == 1 ? tws.w[1] : tws.w[2]);
         if (DIR > 0) w.y = -w.y;
-        sg_twiddle_powers<16>(v, c2_bcast(w));
+        sg_twiddle_powers_b(v, w);
         sg_dft<16, DIR>(v);
     };
     if constexpr (LG > 0) {
