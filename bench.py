@@ -207,6 +207,50 @@ def run_reference(args):
     return 0
 
 
+def host_link(torch, dev, h2d_bytes: int, d2h_bytes: int, reps: int = 20):
+    """The host link's own ceiling for the end-to-end step's traffic: plain
+    pinned copies (cudaMemcpyAsync through torch) of h2d_bytes in and
+    d2h_bytes out, each alone and both at once on two streams, timed with
+    CUDA events (GB/s per direction)."""
+    hi = torch.empty(h2d_bytes // 4, dtype=torch.float32).pin_memory()
+    ho = torch.empty(d2h_bytes // 4, dtype=torch.float32).pin_memory()
+    di = torch.empty(h2d_bytes // 4, dtype=torch.float32, device=dev)
+    do = torch.empty(d2h_bytes // 4, dtype=torch.float32, device=dev)
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def run(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    def both():
+        with torch.cuda.stream(s1):
+            di.copy_(hi, non_blocking=True)
+        with torch.cuda.stream(s2):
+            ho.copy_(do, non_blocking=True)
+        torch.cuda.current_stream().wait_stream(s1)
+        torch.cuda.current_stream().wait_stream(s2)
+
+    t_in = run(lambda: di.copy_(hi, non_blocking=True))
+    t_out = run(lambda: ho.copy_(do, non_blocking=True))
+    t_both = run(both)
+    # one call reads all of sigma before its column pass and writes F only
+    # after it: its copies follow one another (serial_ms); the two
+    # directions overlap only across consecutive calls (concurrent_ms)
+    return {"h2d_gbs": h2d_bytes / (t_in * 1e-3) / 1e9, "d2h_gbs": d2h_bytes / (t_out * 1e-3) / 1e9,
+            "h2d_ms": t_in, "d2h_ms": t_out, "serial_ms": t_in + t_out, "concurrent_ms": t_both,
+            "bound_ms_per_step": t_in + t_out,
+            "how": f"pinned cudaMemcpyAsync of {h2d_bytes} B host-to-device and {d2h_bytes} B device-to-host, "
+                   "alone and concurrently on two streams"}
+
+
 def batch_throughput(torch, dev, flush, n_disks: int = 256, seed: int = 1450, reps: int = 10):
     """cells/s of the batching form: n_disks exponential disks with spirals,
     N_u in {128..1024} and N_phi in {256..2048} drawn per disk, one plan per
@@ -387,6 +431,11 @@ def run_ours(args):
     for _ in range(3):
         plan.backward(gr, gp, gs)
     bwd_ms = timed(lambda: plan.backward(gr, gp, gs), max(20, min(args.steps, 200)))
+    bpasses = []
+    for _ in range(max(20, min(args.steps, 200))):
+        flush.zero_()
+        bpasses.append(plan.backward_timed(gr, gp, gs))
+    bwd_pass_ms = {k: statistics.mean(b[i] for b in bpasses) for i, k in enumerate(("rows", "cols", "inv_rows"))}
     plan64 = Plan(NU, min(NPHI, 4096), u_min, du, 1.0, "float64").build()
     s64 = sigma.double()
     f64r, f64p = torch.empty_like(s64), torch.empty_like(s64)
@@ -470,6 +519,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / n_e2e
     e2e_value = ws * cells / (e2e_ms * 1e-3)
+    link = host_link(torch, dev, cells * 4, 2 * cells * 4)
 
     # ---- batching form: 256 uneven disks through sg_forces_batched ----------
     batch = None if args.no_batch else batch_throughput(torch, dev, flush)
@@ -490,7 +540,9 @@ def run_ours(args):
                               "achieved_gbs": total_bytes / (ms * 1e-3) / 1e9,
                               "frac": total_bytes / (ms * 1e-3) / 1e9 / peak},
             "pass_ms": {"rows": p_rows, "cols": p_cols, "inv_rows": p_inv},
-            "backward": {"value": ws * cells / (bwd_ms * 1e-3), "unit": "cells/s", "ms_per_step": bwd_ms},
+            "backward": {"value": ws * cells / (bwd_ms * 1e-3), "unit": "cells/s", "ms_per_step": bwd_ms,
+                         "pass_ms": bwd_pass_ms,
+                         "path_roofline_frac": total_bytes / (bwd_ms * 1e-3) / 1e9 / peak},
             "fp64": {"value": ws * cells / (fp64_ms * 1e-3), "unit": "cells/s", "ms_per_step": fp64_ms,
                      "fp32_speedup": fp64_ms / ms},
             "accuracy": {"fp32_vs_fp64_gpu_rel_l2": rel_fp32_vs_fp64, "fp32_weight_p2_vs_fp64_gpu_rel_l2": rel_fp32_p2},
@@ -498,7 +550,8 @@ def run_ours(args):
             "build_options": variants,
             "batched": batch,
             "e2e": {"value": e2e_value, "unit": "cells/s", "ms_per_step": e2e_ms,
-                    "h2d_bytes_per_step": cells * 4, "d2h_bytes_per_step": 2 * cells * 4},
+                    "h2d_bytes_per_step": cells * 4, "d2h_bytes_per_step": 2 * cells * 4,
+                    "host_link": link, "frac_of_link_bound": link["bound_ms_per_step"] / e2e_ms},
             "gpu_launches": 3 * args.steps,
             "clocks": clocks,
             "wall_s_timed_region": wall,

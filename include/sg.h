@@ -254,20 +254,32 @@ sg_status sg_forces_timed(sg_plan* plan, const void* sigma, void* F_r, void* F_p
                           float ms[4]);
 
 /*
+ * sg_forces_backward with per-pass timing, as sg_forces_timed: ms[0..2] are
+ * the adjoint's row, column and inverse-row passes (any edge or wedge
+ * update counted with the columns), ms[3] the whole span.  Synchronises the
+ * stream.  Same results and errors as sg_forces_backward.
+ */
+sg_status sg_forces_backward_timed(sg_plan* plan, const void* gF_r, const void* gF_phi, void* gsigma,
+                                   cudaStream_t stream, float ms[4]);
+
+/*
  * sg_forces for callers that cannot allocate device memory when they compute
  * forces (their memory belongs to another framework's allocator, or their
  * loop may not allocate or synchronise): the scratch that sg_forces takes
  * from the plan comes instead from a fixed 24 MiB array that the library
- * reserves on every device it is loaded on, until the process exits.  The
+ * reserves on each device where it is used, until the process exits.  The
  * paper has no counterpart; this is a deployment variant of sg_forces with
  * the same arguments and results.
- *   - Allocates nothing.  The plan must be built (that allocated earlier).
+ *   - Allocates nothing, and loads no module.  The plan must be built or
+ *     loaded (that allocated earlier): sg_kernels_build and sg_plan_load look
+ *     up the array's device address on the plan's device and run one forward
+ *     pass through it, which loads the array's module and the pass kernels'
+ *     (under lazy module loading a module loads, and may allocate, at its
+ *     first use).
  *   - Supported up to 3 N_u (N_phi/2) complex values of scratch: N_u N_phi <=
  *     2^21 cells in SG_F32, 2^20 in SG_F64; larger plans get
  *     SG_ERR_UNSUPPORTED.  The plan's device must be the current device
  *     (SG_ERR_ARG otherwise).
- *   - The first call on each device looks up the array's device address
- *     with that device current; make it before any stream capture.
  *   - All calls on a device share the array: calls whose work overlaps on
  *     the GPU (other streams, other threads) race and must be serialised.
  *     Nothing in it needs to start at zero.

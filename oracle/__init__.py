@@ -422,6 +422,101 @@ def onesided_forces(sigma: np.ndarray, cells: np.ndarray, grid: Grid, G: float =
     return Fr + G * grid.r[:, None] * Frr, Fp + G * grid.r[:, None] * Fpr
 
 
+def _edge_slope_difference(sigma: np.ndarray, grid: Grid):
+    """The one-sided minus the ghost-row radial slopes on the four rows where
+    they differ: rows (-1, 0, Nu-1, Nu) and their difference rows (for the
+    ghost rows -1 and Nu the one-sided set has no slope: minus the ghost one)."""
+    nu = sigma.shape[0]
+    dg, _, rows_g = slopes(sigma, grid, "ghost")
+    do, _, _ = slopes(sigma, grid, "onesided")
+    diff = -dg
+    diff[1:nu + 1] += do  # rows_g[n] = n - 1
+    keep = [0, 1, nu, nu + 1]
+    return diff[keep], rows_g[keep]
+
+
+def onesided_forces_at(sigma: np.ndarray, cells: np.ndarray, grid: Grid, targets, G: float = 1.0):
+    """onesided_forces at the flat target cells i*Nphi + j only, for grids too
+    large for the whole field: the convolution by the direct sum at the
+    targets plus, per target, the radial slope terms of Eq. 28 / A9 for the
+    slope difference on the four rows where it is not zero,
+        G r_i sum_{ip, j'} diff[ip, j'] K^{.,r}[i - ip, j - j']."""
+    nu, nphi = sigma.shape
+    t = np.asarray(targets, dtype=np.int64)
+    Kr, Kp = fold(cells, grid.beta, grid.dphi)
+    Fr, Fp = direct_sum(sigma, Kr, Kp, G, targets=t)
+    diff, rows = _edge_slope_difference(sigma, grid)
+    ti, tj = t // nphi, t % nphi
+    q = (tj[:, None] - np.arange(nphi)[None, :]) % nphi
+    for d, ip in zip(diff, rows):
+        k = (ti - ip + nu)[:, None]
+        Fr = Fr + G * grid.r[ti] * (cells[1][k, q] * d[None, :]).sum(axis=1)
+        Fp = Fp + G * grid.r[ti] * (cells[4][k, q] * d[None, :]).sum(axis=1)
+    return Fr, Fp
+
+
+def onesided_forces_T(gFr: np.ndarray, gFp: np.ndarray, cells: np.ndarray, grid: Grid, G: float = 1.0):
+    """Transpose of onesided_forces: the correlation with the folded kernels
+    (fft_conv_T) plus the transpose of the slope-difference terms.  The slope
+    difference of each column is linear in that column's rows (0, 1, Nu-2,
+    Nu-1): diff[ip] = sum_b D[ip, b] sigma[b] (D from _edge_slope_difference
+    on unit rows), so with, for each of the four slope rows ip,
+        t[ip, j'] = G sum_{i, j} r_i (gFr[i, j] K^{r,r}[i - ip, j - j'] + gFphi[i, j] K^{phi,r}[i - ip, j - j'])
+    (a circular correlation along phi per row, taken by numpy's FFT),
+        gsigma[b] += sum_ip D[ip, b] t[ip]."""
+    nu, nphi = gFr.shape
+    Kr, Kp = fold(cells, grid.beta, grid.dphi)
+    gs = fft_conv_T(gFr, gFp, Kr, Kp, G)
+    brows = [0, 1, nu - 2, nu - 1]
+    D = np.zeros((4, 4))
+    col = Grid(nu, 1, grid.u_min, grid.du)  # the radial slopes do not depend on N_phi
+    for b, rb in enumerate(brows):
+        e = np.zeros((nu, 1))
+        e[rb, 0] = 1.0
+        d, rows = _edge_slope_difference(e, col)
+        D[:, b] = d[:, 0]
+    ar = np.fft.rfft(gFr * grid.r[:, None], axis=1)
+    ap = np.fft.rfft(gFp * grid.r[:, None], axis=1)
+    t = np.zeros((4, nphi))
+    for a, ip in enumerate(rows):
+        k = np.arange(nu) - ip + nu
+        c = (ar * np.conj(np.fft.rfft(cells[1][k], axis=1))).sum(axis=0) + \
+            (ap * np.conj(np.fft.rfft(cells[4][k], axis=1))).sum(axis=0)
+        t[a] = G * np.fft.irfft(c, n=nphi)
+    for b, rb in enumerate(brows):
+        gs[rb] += D[:, b] @ t
+    return gs
+
+
+def wedge_sums_at(sigma: np.ndarray, sigma_w: np.ndarray, wcells: np.ndarray, grid: Grid, targets,
+                  G: float = 1.0):
+    """wedge_sums at the flat target cells i*Nphi + j only: the same single
+    sums over the wedge cells j', per target."""
+    nu, nphi = sigma.shape
+    t = np.asarray(targets, dtype=np.int64)
+    sigma_w = np.asarray(sigma_w, dtype=np.float64)
+    r_w = 0.5 * grid.faces[0]
+    dr = (np.asarray(sigma[0], dtype=np.float64) - sigma_w) / (grid.r[0] - r_w)
+    dp = (np.roll(sigma_w, -1) - np.roll(sigma_w, 1)) / (2.0 * grid.dphi)
+    ti, tj = t // nphi, t % nphi
+    q = (tj[:, None] - np.arange(nphi)[None, :]) % nphi
+    ri = grid.r[ti][:, None]
+    out = []
+    for c0, cr, cp in ((0, 1, 2), (3, 4, 5)):
+        terms = sigma_w[None, :] * wcells[c0][ti[:, None], q] + ri * dr[None, :] * wcells[cr][ti[:, None], q] + \
+            dp[None, :] * wcells[cp][ti[:, None], q]
+        out.append(G * terms.sum(axis=1))
+    return out[0], out[1]
+
+
+def wedge_forces_at(sigma: np.ndarray, sigma_w: np.ndarray, cells: np.ndarray, wcells: np.ndarray, grid: Grid,
+                    targets, G: float = 1.0):
+    """wedge_forces at the flat target cells only."""
+    Fr, Fp = onesided_forces_at(sigma, cells, grid, targets, G)
+    Wr, Wp = wedge_sums_at(sigma, sigma_w, wcells, grid, targets, G)
+    return Fr + Wr, Fp + Wp
+
+
 def fold(cells: np.ndarray, beta: float, dphi: float):
     """Collapse the three sums into one kernel per component.
 

@@ -292,6 +292,10 @@ sg_status sg_plan_load(sg_plan** out, const char* path, cudaStream_t stream)
     p->rtol = h.rtol;
     p->loaded = 1;
     p->built = 1;
+    if ((st = noalloc_prepare(p, stream)) != SG_OK) {
+        sg_plan_destroy(p);
+        return st;
+    }
     *out = p;
     return SG_OK;
 }
@@ -442,6 +446,7 @@ sg_status sg_kernels_build(sg_plan* p, const sg_build_opts* opts, cudaStream_t s
         p->wedge = wedge;
         if (p->report[0]) ret = SG_ERR_TIMEOUT;
     }
+    if (ret == SG_OK) ret = noalloc_prepare(p, stream);
 done:
     if (wcells) cudaFree(wcells);
     if (flag) cudaFree(flag);
@@ -509,11 +514,9 @@ sg_status sg_forces(sg_plan* p, const void* sigma, void* Fr, void* Fp, cudaStrea
     return e == cudaSuccess ? SG_OK : SG_ERR_CUDA;
 }
 
-sg_status sg_forces_timed(sg_plan* p, const void* sigma, void* Fr, void* Fp, cudaStream_t stream, float ms[4])
+// the plan's four timing events, created on first use
+static sg_status timing_events(sg_plan* p)
 {
-    sg_status st = check_fields(p, sigma, Fr, Fp);
-    if (st) return st;
-    if (!ms || sigma == Fr || sigma == Fp || Fr == Fp) return SG_ERR_ARG;
     if (!p->have_ev) {
         for (int i = 0; i < 4; i++)
             if (cudaEventCreate(&p->ev[i]) != cudaSuccess) {
@@ -522,16 +525,46 @@ sg_status sg_forces_timed(sg_plan* p, const void* sigma, void* Fr, void* Fp, cud
             }
         p->have_ev = 1;
     }
+    return SG_OK;
+}
+
+// the three pass durations and the span from the recorded events
+static sg_status event_times(sg_plan* p, float ms[4])
+{
+    SG_TRY(cudaEventSynchronize(p->ev[3]));
+    for (int i = 0; i < 3; i++) SG_TRY(cudaEventElapsedTime(&ms[i], p->ev[i], p->ev[i + 1]));
+    SG_TRY(cudaEventElapsedTime(&ms[3], p->ev[0], p->ev[3]));
+    return SG_OK;
+}
+
+sg_status sg_forces_timed(sg_plan* p, const void* sigma, void* Fr, void* Fp, cudaStream_t stream, float ms[4])
+{
+    sg_status st = check_fields(p, sigma, Fr, Fp);
+    if (st) return st;
+    if (!ms || sigma == Fr || sigma == Fp || Fr == Fp) return SG_ERR_ARG;
+    if ((st = timing_events(p))) return st;
     PlanView v = view(p);
     cudaError_t e =
         p->dtype == SG_F32
             ? launch_forward<float>(v, (const float*)sigma, (float*)Fr, (float*)Fp, stream, p->ev)
             : launch_forward<double>(v, (const double*)sigma, (double*)Fr, (double*)Fp, stream, p->ev);
     if (e != cudaSuccess) return SG_ERR_CUDA;
-    SG_TRY(cudaEventSynchronize(p->ev[3]));
-    for (int i = 0; i < 3; i++) SG_TRY(cudaEventElapsedTime(&ms[i], p->ev[i], p->ev[i + 1]));
-    SG_TRY(cudaEventElapsedTime(&ms[3], p->ev[0], p->ev[3]));
-    return SG_OK;
+    return event_times(p, ms);
+}
+
+sg_status sg_forces_backward_timed(sg_plan* p, const void* gr, const void* gp, void* gs, cudaStream_t stream,
+                                   float ms[4])
+{
+    sg_status st = check_fields(p, gr, gp, gs);
+    if (st) return st;
+    if (!ms || gs == gr || gs == gp) return SG_ERR_ARG;
+    if ((st = timing_events(p))) return st;
+    PlanView v = view(p);
+    cudaError_t e = p->dtype == SG_F32
+                        ? launch_backward<float>(v, (const float*)gr, (const float*)gp, (float*)gs, stream, p->ev)
+                        : launch_backward<double>(v, (const double*)gr, (const double*)gp, (double*)gs, stream, p->ev);
+    if (e != cudaSuccess) return SG_ERR_CUDA;
+    return event_times(p, ms);
 }
 
 sg_status sg_forces_backward(sg_plan* p, const void* gr, const void* gp, void* gs, cudaStream_t stream)

@@ -1633,7 +1633,7 @@ __host__ __device__ __forceinline__ size_t rows_unit_smem_bytes()
 template <int LG, bool BWD, bool DIRECT = false>
 __global__ void __launch_bounds__(RowUnit<LG>::GT, RowUnit<LG>::MINB)
     k_rows_r2c(const float* __restrict__ x0, const float* __restrict__ x1, const float* __restrict__ wrow,
-               float2* __restrict__ out, int nu, const float2* __restrict__ tw, int* err)
+               float2* __restrict__ out, int nu, const float2* __restrict__ tw, int* err, int wave)
 {
     typedef RowUnit<LG> RU;
     constexpr int N = RU::N, NT = RU::NT, TPG = RU::TPG;
@@ -1663,6 +1663,13 @@ __global__ void __launch_bounds__(RowUnit<LG>::GT, RowUnit<LG>::MINB)
         sg_mbar_expect_tx(&bar, BWD ? 2 * bytes : bytes);
         sg_bulk_g2s_hint(dst, x0 + (size_t)u * R * N, bytes, &bar, pol);
         if constexpr (BWD) sg_bulk_g2s_hint(dst + (size_t)R * N, x1 + (size_t)u * R * N, bytes, &bar, pol);
+        // the unit one wave later (wave = blocks resident at once) has its
+        // rows brought into L2 now, so that its block does not wait on DRAM
+        const int un = u + wave;
+        if (un * R < nu) {
+            sg_prefetch_l2(x0 + (size_t)un * R * N, bytes);
+            if constexpr (BWD) sg_prefetch_l2(x1 + (size_t)un * R * N, bytes);
+        }
     }
     if (!DIRECT && __syncthreads_or(!sg_mbar_wait_bounded(&bar, 0, err, 1, wlim))) return;  // inputs never arrived
     // the four real rows (p, q, r, s) of this transform: z1 = p + i q, z2 = r + i s
@@ -1812,7 +1819,7 @@ __global__ void __launch_bounds__(RowUnit<LG>::GT, RowUnit<LG>::MINB)
 // ===========================================================================
 // the pass kernels' signatures (spelled out: naming an instance here would
 // refer to kernels that each translation unit does not define)
-typedef void (*RowsR2CFn)(const float*, const float*, const float*, float2*, int, const float2*, int*);
+typedef void (*RowsR2CFn)(const float*, const float*, const float*, float2*, int, const float2*, int*, int);
 typedef void (*RowsC2RFn)(CUtensorMap, const float*, float*, float*, int, const float2*, int*);
 typedef void (*FwdColsFn)(const float2*, const float2*, const float2*, float2*, float2*, int, int, int,
                           const float2*, int*, const float*, const float*, const float*, EdgeCoef<float>,
@@ -1960,6 +1967,30 @@ static cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int block, siz
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
+// Blocks of a kernel resident on the GPU at once (occupancy x SMs), cached
+// per kernel, device and launch shape.
+template <typename K>
+static int resident_blocks(K kernel, int threads, size_t smem, int sms)
+{
+    LaunchCache& c = launch_cache();
+    const auto key = std::make_tuple((const void*)kernel, current_device(), threads, smem);
+    int occ = 0;
+    {
+        std::lock_guard<std::mutex> lock(c.mu);
+        auto it = c.occ.find(key);
+        if (it != c.occ.end()) occ = it->second;
+    }
+    if (occ == 0) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, smem) != cudaSuccess || occ < 1) {
+            cudaGetLastError();
+            occ = 1;
+        }
+        std::lock_guard<std::mutex> lock(c.mu);
+        c.occ[key] = occ;
+    }
+    return occ * (sms > 0 ? sms : 1);
 }
 
 // Grid of a persistent row pass: as many blocks as fit on the GPU at once
@@ -2145,9 +2176,10 @@ cudaError_t launch_forward(const PlanView& p0, const T* sigma, T* Fr, T* Fp, cud
             const int nblk = p.nu / (4 * fr->slots);
             auto k = sigma_direct ? fr->fwd_rows_direct : fr->fwd_rows;
             if ((err = set_smem(k, fr->r2c_smem, true)) != cudaSuccess) return err;
-            if ((err = launch_pdl(k, nblk, fr->threads,
-                                  fr->r2c_smem, st, (const float*)sigma, (const float*)nullptr, (const float*)p.wpre,
-                                  (float2*)p.wa, p.nu, (const float2*)p.tw, p.err)) != cudaSuccess)
+            const int wave = resident_blocks(k, fr->threads, fr->r2c_smem, p.sms);
+            if ((err = launch_pdl(k, nblk, fr->threads, fr->r2c_smem, st, (const float*)sigma, (const float*)nullptr,
+                                  (const float*)p.wpre, (float2*)p.wa, p.nu, (const float2*)p.tw, p.err, wave)) !=
+                cudaSuccess)
                 return err;
         } else {
             Shape s = shape_for<V>(p.nphi, sizeof(T) == 8 ? 64 : 256);
@@ -2234,7 +2266,7 @@ cudaError_t launch_forward(const PlanView& p0, const T* sigma, T* Fr, T* Fp, cud
 }
 
 template <typename T>
-cudaError_t launch_backward(const PlanView& p0, const T* gr, const T* gp, T* gs, cudaStream_t st)
+cudaError_t launch_backward(const PlanView& p0, const T* gr, const T* gp, T* gs, cudaStream_t st, cudaEvent_t* ev)
 {
     typedef typename CX<T>::t V;
     const FixedPassKernels *fr, *fc;
@@ -2247,15 +2279,17 @@ cudaError_t launch_backward(const PlanView& p0, const T* gr, const T* gp, T* gs,
     const int ln = sg_ilog2(p.nphi), lL = sg_ilog2(2 * p.nu);
     cudaError_t err;
     bool edges_done = false;  // the column pass applied the transposed edge update itself
+    if (ev && (err = cudaEventRecord(ev[0], st)) != cudaSuccess) return err;
     {
         PassRange range_("sg adjoint rows");
         if (p.pairs) {  // (A, C) pairs into wb
             const int nblk = p.nu / (2 * fr->slots);
             auto k = fr->bwd_rows;
             if ((err = set_smem(k, fr->r2c_smem, true)) != cudaSuccess) return err;
-            if ((err = launch_pdl(k, nblk, fr->threads,
-                                  fr->r2c_smem, st, (const float*)gr, (const float*)gp, (const float*)p.wpost,
-                                  (float2*)p.wb, p.nu, (const float2*)p.tw, p.err)) != cudaSuccess)
+            const int wave = resident_blocks(k, fr->threads, fr->r2c_smem, p.sms);
+            if ((err = launch_pdl(k, nblk, fr->threads, fr->r2c_smem, st, (const float*)gr, (const float*)gp,
+                                  (const float*)p.wpost, (float2*)p.wb, p.nu, (const float2*)p.tw, p.err, wave)) !=
+                cudaSuccess)
                 return err;
         } else {
             Shape s = shape_for<V>(p.nphi, row_min_threads(sizeof(T)));
@@ -2274,6 +2308,7 @@ cudaError_t launch_backward(const PlanView& p0, const T* gr, const T* gp, T* gs,
             });
         }
     }
+    if (ev && (err = cudaEventRecord(ev[1], st)) != cudaSuccess) return err;
     {
         PassRange range_("sg adjoint columns");
         const int L = 2 * p.nu, E = L >= 16 ? 16 : L;
@@ -2301,6 +2336,7 @@ cudaError_t launch_backward(const PlanView& p0, const T* gr, const T* gp, T* gs,
     }
     if (p.edges && !edges_done && (err = launch_edges<T>(p, true, st)) != cudaSuccess) return err;
     if (p.wedge && (err = launch_wedge<T>(p, true, st)) != cudaSuccess) return err;
+    if (ev && (err = cudaEventRecord(ev[2], st)) != cudaSuccess) return err;
     {
         PassRange range_("sg adjoint inverse rows");
         if (p.pairs) {  // B from wa
@@ -2328,6 +2364,7 @@ cudaError_t launch_backward(const PlanView& p0, const T* gr, const T* gp, T* gs,
             });
         }
     }
+    if (ev && (err = cudaEventRecord(ev[3], st)) != cudaSuccess) return err;
     return cudaGetLastError();
 }
 
@@ -2364,8 +2401,10 @@ template cudaError_t launch_forward<float>(const PlanView&, const float*, float*
                                            bool);
 template cudaError_t launch_forward<double>(const PlanView&, const double*, double*, double*, cudaStream_t,
                                               cudaEvent_t*, bool);
-template cudaError_t launch_backward<float>(const PlanView&, const float*, const float*, float*, cudaStream_t);
-template cudaError_t launch_backward<double>(const PlanView&, const double*, const double*, double*, cudaStream_t);
+template cudaError_t launch_backward<float>(const PlanView&, const float*, const float*, float*, cudaStream_t,
+                                            cudaEvent_t*);
+template cudaError_t launch_backward<double>(const PlanView&, const double*, const double*, double*, cudaStream_t,
+                                             cudaEvent_t*);
 template cudaError_t launch_spectra<float2>(const PlanView&, const double*, const double*, double2*, float2*,
                                             float2*, cudaStream_t);
 template cudaError_t launch_spectra<double2>(const PlanView&, const double*, const double*, double2*, double2*,

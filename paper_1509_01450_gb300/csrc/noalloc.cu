@@ -10,14 +10,17 @@
 // this call then allocates nothing.
 //
 // The scratch is SG_NOALLOC_BYTES of __device__ memory that every GPU which
-// loads this library reserves until the process exits.  All calls on a
-// device share it, so calls whose work overlaps on the GPU (two streams, or
-// two threads) race on it and must be serialised by the caller.  The first
-// call on each device looks up the array's device address
-// (cudaGetSymbolAddress) with that device current; make that first call
-// before any stream capture.  No part of the scratch needs to start at
-// zero: the row pass writes every element the column pass reads, and the
-// column pass writes every element the inverse row pass reads.
+// loads this file's module reserves until the process exits.  All calls on
+// a device share it, so calls whose work overlaps on the GPU (two streams,
+// or two threads) race on it and must be serialised by the caller.  Building
+// or loading a plan (sg_kernels_build, sg_plan_load) looks up the array's
+// device address (cudaGetSymbolAddress) with the plan's device current and
+// runs one forward pass through it, which loads this module and the pass
+// kernels' modules; under lazy module loading a module is loaded, and may
+// allocate, at its first use, and that first use is then the build's.  No
+// part of the scratch needs to start at zero: the row pass writes every
+// element the column pass reads, and the column pass writes every element
+// the inverse row pass reads.
 #include <mutex>
 
 #include "sg_internal.cuh"
@@ -37,6 +40,8 @@ static std::mutex g_scratch_mutex;
 
 // Device address of the scratch on the current device (looked up once per
 // device; host code cannot use the symbol's host-side name as an address).
+// Under lazy module loading the first lookup also loads this file's module
+// and with it the array.
 static sg_status scratch_address(void** out)
 {
     int dev = -1;
@@ -55,20 +60,14 @@ static sg_status scratch_address(void** out)
     return SG_OK;
 }
 
-extern "C" sg_status sg_forces_noalloc(sg_plan* p, const void* sigma, void* F_r, void* F_phi, cudaStream_t stream)
+// one half-spectrum buffer of the plan, and whether three fit the scratch
+static size_t half_bytes(const sg_plan* p) { return (size_t)p->nu * (p->nphi / 2) * 2 * p->elem; }
+static bool fits(const sg_plan* p) { return 3 * half_bytes(p) <= SG_NOALLOC_BYTES; }
+
+// the forward passes over the scratch (arguments checked by the caller)
+static sg_status noalloc_forward(sg_plan* p, const void* sigma, void* F_r, void* F_phi, cudaStream_t stream)
 {
-    if (!p) return SG_ERR_ARG;
-    if (!p->built) return SG_ERR_NOT_BUILT;
-    if (p->wedge) return SG_ERR_UNSUPPORTED;  // the wedge densities come through sg_forces_wedge
-    const void* ptrs[3] = {sigma, F_r, F_phi};
-    for (const void* q : ptrs)
-        if (!q || ((uintptr_t)q & 15)) return SG_ERR_ARG;
-    if (sigma == F_r || sigma == F_phi || F_r == F_phi) return SG_ERR_ARG;
-    int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess) return SG_ERR_CUDA;
-    if (dev != p->device) return SG_ERR_ARG;  // the plan's spectra live on p->device
-    const size_t half = (size_t)p->nu * (p->nphi / 2) * 2 * p->elem;  // one half-spectrum buffer
-    if (3 * half > SG_NOALLOC_BYTES) return SG_ERR_UNSUPPORTED;
+    const size_t half = half_bytes(p);
     void* scratch = nullptr;
     sg_status st = scratch_address(&scratch);
     if (st) return st;
@@ -92,4 +91,47 @@ extern "C" sg_status sg_forces_noalloc(sg_plan* p, const void* sigma, void* F_r,
                         ? launch_forward<float>(v, (const float*)sigma, (float*)F_r, (float*)F_phi, stream)
                         : launch_forward<double>(v, (const double*)sigma, (double*)F_r, (double*)F_phi, stream);
     return e == cudaSuccess ? SG_OK : SG_ERR_CUDA;
+}
+
+namespace sg {
+// Called by the plan build and load, which allocate anyway: resolve the
+// scratch address on the plan's device and run one forward pass through
+// the scratch on a zero density, so that every module of the path is loaded
+// (under lazy module loading a module loads, and may allocate, at its first
+// use) and every launch attribute set; sg_forces_noalloc then loads and
+// allocates nothing.  Plans the entry point refuses are skipped.
+sg_status noalloc_prepare(sg_plan* p, cudaStream_t stream)
+{
+    if (p->wedge || !fits(p)) return SG_OK;
+    const size_t field = (size_t)p->nu * p->nphi * p->elem;
+    unsigned char* buf = nullptr;
+    if (cudaMalloc(&buf, 3 * field) != cudaSuccess) {
+        cudaGetLastError();
+        return SG_ERR_ALLOC;
+    }
+    sg_status st = SG_OK;
+    if (cudaMemsetAsync(buf, 0, field, stream) != cudaSuccess)
+        st = SG_ERR_CUDA;
+    else
+        st = noalloc_forward(p, buf, buf + field, buf + 2 * field, stream);
+    if (cudaStreamSynchronize(stream) != cudaSuccess && st == SG_OK) st = SG_ERR_CUDA;
+    cudaFree(buf);
+    return st;
+}
+}  // namespace sg
+
+extern "C" sg_status sg_forces_noalloc(sg_plan* p, const void* sigma, void* F_r, void* F_phi, cudaStream_t stream)
+{
+    if (!p) return SG_ERR_ARG;
+    if (!p->built) return SG_ERR_NOT_BUILT;
+    if (p->wedge) return SG_ERR_UNSUPPORTED;  // the wedge densities come through sg_forces_wedge
+    const void* ptrs[3] = {sigma, F_r, F_phi};
+    for (const void* q : ptrs)
+        if (!q || ((uintptr_t)q & 15)) return SG_ERR_ARG;
+    if (sigma == F_r || sigma == F_phi || F_r == F_phi) return SG_ERR_ARG;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return SG_ERR_CUDA;
+    if (dev != p->device) return SG_ERR_ARG;  // the plan's spectra live on p->device
+    if (!fits(p)) return SG_ERR_UNSUPPORTED;
+    return noalloc_forward(p, sigma, F_r, F_phi, stream);
 }

@@ -403,6 +403,13 @@ __device__ __forceinline__ uint64_t sg_globaltimer_ns()
     return t;
 }
 
+// Prefetch of a contiguous range into L2 (no shared memory, no completion):
+// address and size multiples of 16 bytes
+__device__ __forceinline__ void sg_prefetch_l2(const void* src, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 // Bulk copy with an L2 eviction-priority policy (sg_policy_*).
 __device__ __forceinline__ void sg_bulk_g2s_hint(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
                                                  uint64_t policy)

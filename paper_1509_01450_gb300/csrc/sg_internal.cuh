@@ -136,8 +136,11 @@ template <typename T>
 // (mapped pinned host memory); the row pass then reads it without bulk copies
 cudaError_t launch_forward(const PlanView& p, const T* sigma, T* Fr, T* Fp, cudaStream_t st,
                            cudaEvent_t* ev = nullptr, bool sigma_direct = false);
+// ev: optional 4 events recorded before P1b, after P1b, after P2b (and the
+// edge or wedge update), after P3b
 template <typename T>
-cudaError_t launch_backward(const PlanView& p, const T* gr, const T* gp, T* gs, cudaStream_t st);
+cudaError_t launch_backward(const PlanView& p, const T* gr, const T* gp, T* gs, cudaStream_t st,
+                            cudaEvent_t* ev = nullptr);
 // wedge.cu: the origin wedge's update between the column and inverse-row
 // passes (forward: p.sigw; adjoint: writes p.gsigw)
 template <typename T>
@@ -153,6 +156,8 @@ void make_row_maps(int nu, int nphi, size_t elem, void* const bufs[3], SgRowMaps
 // row); boxes of 4 units x min(N_phi/2, 256) modes with the 32-byte swizzle.
 // False if they cannot be made (the passes then use the run-time instances).
 bool make_pair_maps(int nu, int nphi, void* wa, void* wb, CUtensorMap out[2]);
+// noalloc.cu: the allocation-free entry point's set-up at plan build and load
+sg_status noalloc_prepare(sg_plan* p, cudaStream_t stream);
 template <typename VO>
 cudaError_t launch_spectra(const PlanView& p, const double* nsr, const double* nsp, double2* W, VO* Kr, VO* Kp,
                            cudaStream_t st);

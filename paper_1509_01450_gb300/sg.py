@@ -19,6 +19,7 @@ SG_OK, SG_ERR_ARG, SG_ERR_ALLOC, SG_ERR_CUDA, SG_ERR_UNSUPPORTED, SG_ERR_NOT_BUI
 SG_F32, SG_F64 = 0, 1
 
 EXPORTS = ("sg_plan_create", "sg_kernels_build", "sg_forces", "sg_forces_backward", "sg_forces_host", "sg_forces_timed",
+           "sg_forces_backward_timed",
            "sg_forces_batched", "sg_batch_reserve", "sg_plan_destroy", "sg_status_string", "sg_plan_info",
            "sg_plan_kernels", "sg_plan_cells", "sg_plan_device_bytes", "sg_plan_build_report", "sg_forces_noalloc", "sg_plan_check",
            "sg_plan_set_wait_limit", "sg_plan_save", "sg_plan_load", "sg_forces_wedge", "sg_forces_wedge_backward")
@@ -69,6 +70,7 @@ def lib():
         L.sg_forces_backward.argtypes = [vp, vp, vp, vp, vp]
         L.sg_forces_host.argtypes = [vp, vp, vp, vp, vp]
         L.sg_forces_timed.argtypes = [vp, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_float)]
+        L.sg_forces_backward_timed.argtypes = [vp, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_float)]
         L.sg_forces_noalloc.argtypes = [vp, vp, vp, vp, vp]
         L.sg_forces_wedge.argtypes = [vp, vp, vp, vp, vp, vp]
         L.sg_forces_wedge_backward.argtypes = [vp, vp, vp, vp, vp, vp]
@@ -157,7 +159,8 @@ class Plan:
     def forces(self, sigma, F_r=None, F_phi=None, stream=None):
         F_r = self._new() if F_r is None else F_r
         F_phi = self._new() if F_phi is None else F_phi
-        self._check_field(sigma)
+        for t in (sigma, F_r, F_phi):
+            self._check_field(t)
         _check(lib().sg_forces(self.handle, _ptr(sigma), _ptr(F_r), _ptr(F_phi), _stream(stream)), "sg_forces")
         return F_r, F_phi
 
@@ -166,7 +169,8 @@ class Plan:
         sigma_w (N_phi values on the device)."""
         F_r = self._new() if F_r is None else F_r
         F_phi = self._new() if F_phi is None else F_phi
-        self._check_field(sigma)
+        for t in (sigma, F_r, F_phi):
+            self._check_field(t)
         self._check_wedge_row(sigma_w)
         _check(lib().sg_forces_wedge(self.handle, _ptr(sigma), _ptr(sigma_w), _ptr(F_r), _ptr(F_phi),
                                      _stream(stream)), "sg_forces_wedge")
@@ -179,8 +183,8 @@ class Plan:
         gsigma = self._new() if gsigma is None else gsigma
         if gsigma_w is None:
             gsigma_w = torch.empty(self.nphi, dtype=self.dtype, device="cuda")
-        self._check_field(gF_r)
-        self._check_field(gF_phi)
+        for t in (gF_r, gF_phi, gsigma):
+            self._check_field(t)
         self._check_wedge_row(gsigma_w)
         _check(lib().sg_forces_wedge_backward(self.handle, _ptr(gF_r), _ptr(gF_phi), _ptr(gsigma), _ptr(gsigma_w),
                                               _stream(stream)), "sg_forces_wedge_backward")
@@ -195,7 +199,8 @@ class Plan:
         allocation in the call (for callers that may not allocate then).
         Calls that overlap on the GPU share that scratch and must not run
         concurrently."""
-        self._check_field(sigma)
+        for t in (sigma, F_r, F_phi):
+            self._check_field(t)
         _check(lib().sg_forces_noalloc(self.handle, _ptr(sigma), _ptr(F_r), _ptr(F_phi), _stream(stream)),
                "sg_forces_noalloc")
         return F_r, F_phi
@@ -203,16 +208,28 @@ class Plan:
     def forces_timed(self, sigma, F_r, F_phi, stream=None):
         """sg_forces with per-pass CUDA-event timing; returns (rows, cols,
         inverse rows, span) in ms (synchronises the stream)."""
-        self._check_field(sigma)
+        for t in (sigma, F_r, F_phi):
+            self._check_field(t)
         ms = (ctypes.c_float * 4)()
         _check(lib().sg_forces_timed(self.handle, _ptr(sigma), _ptr(F_r), _ptr(F_phi), _stream(stream), ms),
                "sg_forces_timed")
         return tuple(ms)
 
-    def backward(self, gF_r, gF_phi, gsigma=None, stream=None):
-        gsigma = self._new() if gsigma is None else gsigma
+    def backward_timed(self, gF_r, gF_phi, gsigma, stream=None):
+        """sg_forces_backward with per-pass CUDA-event timing; returns (rows,
+        cols, inverse rows, span) in ms (synchronises the stream)."""
         self._check_field(gF_r)
         self._check_field(gF_phi)
+        self._check_field(gsigma)
+        ms = (ctypes.c_float * 4)()
+        _check(lib().sg_forces_backward_timed(self.handle, _ptr(gF_r), _ptr(gF_phi), _ptr(gsigma), _stream(stream),
+                                              ms), "sg_forces_backward_timed")
+        return tuple(ms)
+
+    def backward(self, gF_r, gF_phi, gsigma=None, stream=None):
+        gsigma = self._new() if gsigma is None else gsigma
+        for t in (gF_r, gF_phi, gsigma):
+            self._check_field(t)
         _check(lib().sg_forces_backward(self.handle, _ptr(gF_r), _ptr(gF_phi), _ptr(gsigma), _stream(stream)),
                "sg_forces_backward")
         return gsigma
@@ -307,7 +324,8 @@ def forces_batched(items, stream=None):
     """items: list of (plan, sigma, F_r, F_phi) with device tensors."""
     arr = (BatchItem * len(items))()
     for n, (p, s, fr, fp) in enumerate(items):
-        p._check_field(s)
+        for t in (s, fr, fp):
+            p._check_field(t)
         arr[n] = BatchItem(p.handle.value, s.data_ptr(), fr.data_ptr(), fp.data_ptr())
     _check(lib().sg_forces_batched(arr, len(items), _stream(stream)), "sg_forces_batched")
 

@@ -64,3 +64,52 @@ def test_kuzmin_full_grid_second_order(oracle_mod):
     order = {k: math.log2(v[-2] / v[-1]) for k, v in errs.items()}
     assert order["onesided"] > 1.7 and errs["onesided"][-1] < 1e-4, errs
     assert order["ghost"] < 0.5 and errs["ghost"][-1] > 0.1, errs  # the ghost rows' dipole at r_in
+
+
+@pytest.mark.parametrize("nu,nphi", [(8, 16), (16, 32)])
+def test_sampled_form_equals_the_whole_field(oracle_mod, nu, nphi):
+    """onesided_forces_at (the sums at chosen cells, for grids too large for
+    the whole field) gives the whole-field values at every cell."""
+    u_min, du = workloads.grid_params(nu, 0.1, 10.0)
+    grid = oracle_mod.Grid(nu, nphi, u_min, du)
+    cells = oracle_mod.kernel_cells(nu, nphi, du)
+    sigma = workloads.random_field(nu, nphi, 3)
+    Fr, Fp = oracle_mod.onesided_forces(sigma, cells, grid, 1.3)
+    t = np.random.default_rng(1).permutation(nu * nphi)
+    ar, ap = oracle_mod.onesided_forces_at(sigma, cells, grid, t, 1.3)
+    scale = np.abs(Fr).max() + np.abs(Fp).max()
+    assert np.abs(ar - Fr.ravel()[t]).max() < 1e-14 * scale and np.abs(ap - Fp.ravel()[t]).max() < 1e-14 * scale
+
+
+@pytest.mark.parametrize("nu,nphi", [(6, 8), (8, 16)])
+def test_transpose_is_the_transposed_dense_map(oracle_mod, nu, nphi):
+    """onesided_forces_T against the dense matrix of onesided_forces (built
+    column by column from unit densities), transposed."""
+    u_min, du = workloads.grid_params(nu, 0.1, 10.0)
+    grid = oracle_mod.Grid(nu, nphi, u_min, du)
+    cells = oracle_mod.kernel_cells(nu, nphi, du)
+    n = nu * nphi
+    M = np.zeros((2 * n, n))
+    for c in range(n):
+        e = np.zeros(n)
+        e[c] = 1.0
+        fr, fp = oracle_mod.onesided_forces(e.reshape(nu, nphi), cells, grid, 0.7)
+        M[:n, c], M[n:, c] = fr.ravel(), fp.ravel()
+    gr, gp = workloads.random_field(nu, nphi, 11), workloads.random_field(nu, nphi, 12)
+    ref = (M.T @ np.concatenate([gr.ravel(), gp.ravel()])).reshape(nu, nphi)
+    got = oracle_mod.onesided_forces_T(gr, gp, cells, grid, 0.7)
+    assert np.abs(got - ref).max() < 1e-13 * np.abs(ref).max()
+
+
+def test_transpose_dot_identity(oracle_mod):
+    nu, nphi = 32, 64
+    u_min, du = workloads.grid_params(nu, 0.01, 100.0)
+    grid = oracle_mod.Grid(nu, nphi, u_min, du)
+    cells = oracle_mod.kernel_cells(nu, nphi, du)
+    sigma = workloads.random_field(nu, nphi, 21)
+    gr, gp = workloads.random_field(nu, nphi, 22), workloads.random_field(nu, nphi, 23)
+    Fr, Fp = oracle_mod.onesided_forces(sigma, cells, grid)
+    gs = oracle_mod.onesided_forces_T(gr, gp, cells, grid)
+    lhs = float((gr * Fr).sum() + (gp * Fp).sum())
+    rhs = float((gs * sigma).sum())
+    assert abs(lhs - rhs) < 1e-13 * float(np.abs(gr * Fr).sum() + np.abs(gp * Fp).sum())

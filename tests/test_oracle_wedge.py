@@ -116,3 +116,20 @@ def test_potential_wedge_cells_against_quadrature(oracle_mod, i, q):
     got = W[:3, i, q % NPHI]
     assert np.all(np.abs(got - ref) <= 1e-10 * abs(ref[0])), (got, ref)
     assert not np.any(W[3:])
+
+
+def test_sampled_form_equals_the_whole_field(oracle_mod):
+    """wedge_forces_at (at chosen cells, for grids too large for the whole
+    field) gives the whole-field values."""
+    nu, nphi = 16, 32
+    u_min, du = workloads.grid_params(nu, 0.1, 10.0)
+    grid = oracle_mod.Grid(nu, nphi, u_min, du)
+    cells = oracle_mod.kernel_cells(nu, nphi, du)
+    wcells = oracle_mod.wedge_cells(nu, nphi, du)
+    sigma = np.abs(workloads.random_field(nu, nphi, 4)) + 0.1
+    sigma_w = 0.5 + np.random.default_rng(4).random(nphi)
+    Fr, Fp = oracle_mod.wedge_forces(sigma, sigma_w, cells, wcells, grid)
+    t = np.random.default_rng(2).permutation(nu * nphi)[: nu * nphi // 2]
+    ar, ap = oracle_mod.wedge_forces_at(sigma, sigma_w, cells, wcells, grid, t)
+    scale = np.abs(Fr).max() + np.abs(Fp).max()
+    assert np.abs(ar - Fr.ravel()[t]).max() < 1e-14 * scale and np.abs(ap - Fp.ravel()[t]).max() < 1e-14 * scale
