@@ -403,17 +403,14 @@ def onesided_forces(sigma: np.ndarray, cells: np.ndarray, grid: Grid, G: float =
     nu, nphi = sigma.shape
     Kr, Kp = fold(cells, grid.beta, grid.dphi)
     Fr, Fp = fft_conv(sigma, Kr, Kp, G)
-    dg, _, rows_g = slopes(sigma, grid, "ghost")
-    do, _, _ = slopes(sigma, grid, "onesided")
-    diff = -dg
-    diff[1:nu + 1] += do  # rows_g[n] = n - 1
+    # the two slope sets differ on those four rows only (elsewhere both are
+    # the same central difference, up to the rounding of its two forms)
+    diff, rows_d = _edge_slope_difference(sigma, grid)
     i = np.arange(nu)[:, None]
     j = np.arange(nphi)[None, :]
     Frr = np.zeros((nu, nphi))
     Fpr = np.zeros((nu, nphi))
-    for n, ip in enumerate(rows_g):
-        if not np.any(diff[n]):
-            continue
+    for n, ip in enumerate(rows_d):
         for jp in range(nphi):
             k = i - ip + nu
             q = (j - jp) % nphi

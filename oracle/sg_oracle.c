@@ -501,11 +501,13 @@ static int cell_of(double du, int nphi, int k, int q, double rtol, int pot, doub
     if (cell.self) {
         /* rounding in the near-singular inner integrals, relative to a cell
            value that shrinks with the cell, sets a floor on what this cell
-           can resolve: try 1e-14, then 1e-13, then 1e-12 */
+           can resolve: try 1e-14, then 1e-13, ... up to 1e-10 (cells of
+           about 0.003 radians on a side, N_phi = 2048 and beyond, need
+           1e-11 or 1e-10) */
         bp[nb++] = 0.0;
         bp[nb++] = cell.half_dphi;
-        double floors[3] = {1e-14, 1e-13, 1e-12};
-        for (int attempt = 0; attempt < 3; attempt++) {
+        double floors[5] = {1e-14, 1e-13, 1e-12, 1e-11, 1e-10};
+        for (int attempt = 0; attempt < 5; attempt++) {
             cell.rtol = rtol > floors[attempt] ? rtol : floors[attempt];
             bad = 0;
             /* a log-singular endpoint needs about 60 bisections; more
