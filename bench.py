@@ -251,13 +251,15 @@ def host_link(torch, dev, h2d_bytes: int, d2h_bytes: int, reps: int = 20):
                    "alone and concurrently on two streams"}
 
 
-def batch_throughput(torch, dev, flush, n_disks: int = 256, seed: int = 1450, reps: int = 10):
+def batch_throughput(torch, dev, flush, peak_gbs, n_disks: int = 256, seed: int = 1450, reps: int = 10):
     """cells/s of the batching form: n_disks exponential disks with spirals,
     N_u in {128..1024} and N_phi in {256..2048} drawn per disk, one plan per
     distinct size, all enqueued by one sg_forces_batched call; timed eagerly
     and as a replayed CUDA graph of that call (L2 flushed before each)."""
+    import tempfile
+
     import workloads
-    from paper_1509_01450_gb300 import Plan, forces_batched
+    from paper_1509_01450_gb300 import Plan, SgError, batch_tune, forces_batched
 
     disks = workloads.batch_disks(n_disks, seed)
     plans = {}
@@ -280,6 +282,14 @@ def batch_throughput(torch, dev, flush, n_disks: int = 256, seed: int = 1450, re
         torch.cuda.synchronize()
         return statistics.mean(a.elapsed_time(b) for a, b in ev)
 
+    # the persistent path's schedule, tuned for these sizes once per machine
+    # (the file keeps it for later runs)
+    cache = os.path.join(tempfile.gettempdir(), "sg_batch_schedules.txt")
+    try:
+        tune_ms = batch_tune(items, cache)
+        persistent = True
+    except SgError:
+        tune_ms, persistent = None, False
     for _ in range(3):
         forces_batched(items, stream=stream)
     eager_ms = timed(lambda: forces_batched(items, stream=stream))
@@ -295,9 +305,14 @@ def batch_throughput(torch, dev, flush, n_disks: int = 256, seed: int = 1450, re
     g.replay()
     torch.cuda.synchronize()
     graph_ms = timed(g.replay)
+    # the three passes' algorithmic bytes over all disks, against the copy peak
+    bytes_ = sum(BYTES_PER_CELL.values()) * cells
     return {"workload": f"{n_disks} disks, seed {seed}, {len(plans)} sizes, {cells} cells", "unit": "cells/s",
             "value": cells / (eager_ms * 1e-3), "ms": eager_ms,
-            "graph_value": cells / (graph_ms * 1e-3), "graph_ms": graph_ms, "launches": 3 * n_disks}
+            "graph_value": cells / (graph_ms * 1e-3), "graph_ms": graph_ms,
+            "persistent": persistent, "launches": 1 if persistent else 3 * n_disks,
+            "tune_ms": {"default": tune_ms[0], "tuned": tune_ms[1]} if tune_ms else None,
+            "graph_path_roofline_frac": bytes_ / (graph_ms * 1e-3) / 1e9 / peak_gbs}
 
 
 def run_passes_only(args):
@@ -449,6 +464,22 @@ def run_ours(args):
     num = float(((Fr.double() - f64r) ** 2).sum() + ((Fp.double() - f64p) ** 2).sum())
     den = float((f64r ** 2).sum() + (f64p ** 2).sum())
     rel_fp32_vs_fp64 = math.sqrt(num / den)
+    # the compensated FP32 plan (double-float passes; FP64 fields): its cost
+    # beside the FP32 and FP64 steps, and its accuracy against FP64
+    planc = Plan(NU, min(NPHI, 4096), u_min, du, 1.0, "float32x2").build()
+    fcr, fcp = torch.empty_like(s64), torch.empty_like(s64)
+    for _ in range(3):
+        planc.forces(s64, fcr, fcp)
+    comp_ms = timed(lambda: planc.forces(s64, fcr, fcp), 20)
+    gcs, gr64, gp64 = torch.empty_like(s64), gr.double(), gp.double()
+    for _ in range(3):
+        planc.backward(gr64, gp64, gcs)
+    comp_bwd_ms = timed(lambda: planc.backward(gr64, gp64, gcs), 20)
+    planc.forces(s64, fcr, fcp)
+    torch.cuda.synchronize()
+    num = float(((fcr - f64r) ** 2).sum() + ((fcp - f64p) ** 2).sum())
+    rel_comp_vs_fp64 = math.sqrt(num / den)
+    del planc, fcr, fcp, gcs, gr64, gp64
     # the same with the kernels stored at weighting p = 2 (the e^{2u} form)
     plan_p2 = Plan(NU, NPHI, u_min, du, 1.0, "float32").build(weight_p=2)
     plan_p2.forces(sigma, Fr, Fp)
@@ -522,7 +553,7 @@ def run_ours(args):
     link = host_link(torch, dev, cells * 4, 2 * cells * 4)
 
     # ---- batching form: 256 uneven disks through sg_forces_batched ----------
-    batch = None if args.no_batch else batch_throughput(torch, dev, flush)
+    batch = None if args.no_batch else batch_throughput(torch, dev, flush, peak)
 
     if rank == 0:
         clocks = clk.summary()
@@ -545,7 +576,11 @@ def run_ours(args):
                          "path_roofline_frac": total_bytes / (bwd_ms * 1e-3) / 1e9 / peak},
             "fp64": {"value": ws * cells / (fp64_ms * 1e-3), "unit": "cells/s", "ms_per_step": fp64_ms,
                      "fp32_speedup": fp64_ms / ms},
-            "accuracy": {"fp32_vs_fp64_gpu_rel_l2": rel_fp32_vs_fp64, "fp32_weight_p2_vs_fp64_gpu_rel_l2": rel_fp32_p2},
+            "compensated_fp32": {"value": ws * cells / (comp_ms * 1e-3), "unit": "cells/s", "ms_per_step": comp_ms,
+                                 "backward_ms_per_step": comp_bwd_ms, "cost_vs_fp32": comp_ms / ms,
+                                 "speedup_vs_fp64": fp64_ms / comp_ms, "vs_fp64_gpu_rel_l2": rel_comp_vs_fp64},
+            "accuracy": {"fp32_vs_fp64_gpu_rel_l2": rel_fp32_vs_fp64, "fp32_weight_p2_vs_fp64_gpu_rel_l2": rel_fp32_p2,
+                         "compensated_vs_fp64_gpu_rel_l2": rel_comp_vs_fp64},
             "build_s": build_s,
             "build_options": variants,
             "batched": batch,

@@ -51,10 +51,17 @@ typedef enum {
     SG_ERR_UNSUPPORTED = 4, /* sizes outside the supported set (see sg_plan_create) */
     SG_ERR_NOT_BUILT = 5,   /* forces requested before sg_kernels_build */
     SG_ERR_TIMEOUT = 6,     /* a bounded device-side wait gave up */
-    SG_ERR_IO = 7           /* a plan file could not be written or read, or is not one */
+    SG_ERR_IO = 7,          /* a plan file could not be written or read, or is not one */
+    SG_ERR_BOUNDS = 8       /* checked builds only (sg_checked_build): a pass's index check
+                               failed and the access was skipped (sg_last_bounds_site) */
 } sg_status;
 
-typedef enum { SG_F32 = 0, SG_F64 = 1 } sg_dtype;
+/* Working precision of a plan.  SG_F32X2, the compensated FP32 plans: the
+   fields are FP64 in memory (as for SG_F64), the passes carry each value as
+   the unevaluated sum of two FP32 numbers (double-float arithmetic from
+   error-free transformations, about 48 significant bits) on the FP32 pipes,
+   and the kernel spectra are stored the same way.  Sizes as for SG_F64. */
+typedef enum { SG_F32 = 0, SG_F64 = 1, SG_F32X2 = 2 } sg_dtype;
 
 typedef struct sg_plan sg_plan;
 
@@ -186,7 +193,9 @@ sg_status sg_plan_create(sg_plan** out, int N_u, int N_phi, double u_min, double
  * scratch of 6 N_u N_phi values.
  * Allocates and frees FP64 scratch for the spectra; radial_edges = 1 also
  * allocates the plan's edge tables, 2 (N_phi/2 + 1)(2 N_u + 1) values of
- * the working dtype.
+ * the working dtype.  Any other error than SG_ERR_TIMEOUT (SG_ERR_ALLOC,
+ * SG_ERR_CUDA, also from the set-up of sg_forces_noalloc at the end) leaves
+ * the plan unbuilt: SG_ERR_NOT_BUILT until a build succeeds.
  */
 sg_status sg_kernels_build(sg_plan* plan, const sg_build_opts* opts, cudaStream_t stream);
 
@@ -277,7 +286,8 @@ sg_status sg_forces_backward_timed(sg_plan* plan, const void* gF_r, const void* 
  *     (under lazy module loading a module loads, and may allocate, at its
  *     first use).
  *   - Supported up to 3 N_u (N_phi/2) complex values of scratch: N_u N_phi <=
- *     2^21 cells in SG_F32, 2^20 in SG_F64; larger plans get
+ *     2^21 cells in SG_F32, 2^20 in SG_F64; larger plans, and SG_F32X2
+ *     plans (whose conversions use working fields of the plan), get
  *     SG_ERR_UNSUPPORTED.  The plan's device must be the current device
  *     (SG_ERR_ARG otherwise).
  *   - All calls on a device share the array: calls whose work overlaps on
@@ -295,20 +305,60 @@ typedef struct {
 } sg_batch_item;
 
 /*
- * Forward pass for n disks of possibly different sizes, all SG_F32 or all
- * SG_F64.  items is a host array; every item is validated before any work
- * is enqueued.  Items that share a plan share its workspace and run in item
- * order.  When the items use several plans, each plan's items run on that
- * plan's own stream, forked from `stream` and joined back to it by events,
- * so disks of different sizes run concurrently; work enqueued on `stream`
- * afterwards waits for all of them.  Allocates nothing; capturable in a
- * CUDA graph (the forks become parallel branches).  A plan may appear in
- * only one batch or call in flight at a time.
+ * Forward pass for n disks of possibly different sizes, all of one dtype.
+ * items is a host array; every item is validated before any work is
+ * enqueued.  The paper prepares each disk's kernels once and evaluates the
+ * forces every step (Sec. 2); this is that step for many disks at once.
+ *   - One persistent launch when every plan is SG_F32 with both transform
+ *     lengths in 2^8 .. 2^12 (N_phi 256 .. 4096, N_u 128 .. 2048) and
+ *     neither radial_edges nor wedge: a kernel resident on every SM takes
+ *     work items -- row units of a disk's R2C pass, mode groups of its
+ *     column pass, row units of its C2R pass -- from a queue in device
+ *     memory, each disk's column items after all its row items and its C2R
+ *     items after all its column items (per-disk counters, waits bounded
+ *     like the passes' copy waits: a wait that runs out sets the plan's
+ *     flag, see sg_plan_check).  Each disk's forces are bit-equal to
+ *     sg_forces on the same plan.  The work list is built on the host the
+ *     first time a list of items (plans and buffers, in order) is seen, or
+ *     by sg_batch_prepare / sg_batch_tune; its schedule is the one
+ *     sg_batch_tune chose for this set of sizes, if any.
+ *   - Otherwise, and for a list first seen while the stream is being
+ *     captured: items that share a plan share its workspace and run in
+ *     item order; the items of different plans run on the plans' own
+ *     streams, forked from `stream` and joined back to it by events.
+ * Capturable in a CUDA graph (prepare the list first).  A plan may appear
+ * in only one batch or call in flight at a time, and two calls with the
+ * same list must not overlap.  Allocates only when it builds a work list.
  */
 sg_status sg_forces_batched(const sg_batch_item* items, int n, cudaStream_t stream);
 
-/* Reserve batch resources for up to n items (currently none are needed). */
-sg_status sg_batch_reserve(int n);
+/*
+ * Builds the persistent path's work list for these items (synchronises
+ * stream) so that later sg_forces_batched calls with the same items, also
+ * captured ones, take it.  Allocates the list's device memory, held until
+ * one of the plans is destroyed: each item's own intermediate spectra (12
+ * bytes per cell; items may share a plan), a descriptor of 256 bytes per
+ * item and 8 bytes per work item.  The library keeps the 4 lists prepared
+ * last (a call with a new list of items builds one: host work and a
+ * synchronising copy).  SG_ERR_UNSUPPORTED if the items do not qualify
+ * for the persistent path; SG_ERR_ARG while stream is being captured.
+ */
+sg_status sg_batch_prepare(const sg_batch_item* items, int n, cudaStream_t stream);
+
+/*
+ * Tunes the persistent path's schedule for this set of disk sizes: the lag
+ * between an item and its dependencies in the queue, the disk order, and
+ * per size class (N_u, N_phi) the row units per row item and the mode
+ * groups per column item.  Each candidate runs the batch (the items' F_r,
+ * F_phi are overwritten) and the fastest is kept.  cache_path (or NULL): a
+ * text file of schedules, one line per set of sizes and SM count; a
+ * schedule found there is taken without tuning, a new one is appended.
+ * Then prepares the items' list with the schedule (as sg_batch_prepare).
+ * ms[0], ms[1] (ms may be NULL): the batch's time with the default and with
+ * the chosen schedule.  Synchronises stream.  SG_ERR_UNSUPPORTED as
+ * sg_batch_prepare; SG_ERR_IO if the file cannot be appended to.
+ */
+sg_status sg_batch_tune(const sg_batch_item* items, int n, const char* cache_path, cudaStream_t stream, float ms[2]);
 
 sg_status sg_plan_destroy(sg_plan* plan);
 
@@ -351,7 +401,9 @@ sg_status sg_plan_build_report(const sg_plan* plan, int report[4]);
  * Device-side status of the work enqueued so far with this plan: reads (and
  * clears) the plan's error flags after synchronising stream.  SG_ERR_TIMEOUT
  * means a pass gave up waiting for its asynchronous input copies (its
- * results are invalid); SG_OK otherwise.
+ * results are invalid); SG_ERR_BOUNDS (checked builds only) that an index
+ * check of a pass failed (its results are invalid; the failing check's site
+ * number is kept for sg_last_bounds_site); SG_OK otherwise.
  */
 sg_status sg_plan_check(sg_plan* plan, cudaStream_t stream);
 
@@ -384,6 +436,35 @@ sg_status sg_plan_load(sg_plan** out, const char* path, cudaStream_t stream);
 
 /* Bytes of device memory the plan holds. */
 size_t sg_plan_device_bytes(const sg_plan* plan);
+
+/*
+ * Checked builds.  The library compiled with -DSG_DEBUG (the build script's
+ * `checked` variant, libsgdisk_checked.so) tests, before every global copy,
+ * store and tensor-copy coordinate of its pass kernels, that the access
+ * stays inside its buffer and inside the block's shared memory; a failed
+ * test skips the access and flags the plan (sg_plan_check returns
+ * SG_ERR_BOUNDS).  sg_checked_build returns 1 for such a library, 0 for the
+ * ordinary one; sg_last_bounds_site the site number of the last failure
+ * sg_plan_check reported in this process (0: none).
+ */
+int sg_checked_build(void);
+int sg_last_bounds_site(void);
+
+/*
+ * Testing hook for the SG_ERR_ALLOC paths: after the next `after` device
+ * allocations of this library succeed, every further one fails as if the
+ * device were out of memory, until the hook is called again; after < 0
+ * (the initial state) lets every allocation go to the device.  Returns the
+ * number of allocations that were still to succeed before the call (or -1),
+ * so that after(N) ... after(-1) counts the allocations made in between.
+ * Process-wide.  Every call that allocates releases what it took when a
+ * later allocation fails: sg_plan_create and sg_plan_load return no plan,
+ * sg_kernels_build leaves the plan unbuilt, sg_forces_host returns before
+ * any copy (its staging buffers are taken on a later call).
+ */
+int sg_test_fail_alloc(int after);
+/* Device allocations of this library not yet released (process-wide). */
+int sg_test_live_allocations(void);
 
 #ifdef __cplusplus
 }

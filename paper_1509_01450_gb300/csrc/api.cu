@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <vector>
 
 #include "sg_internal.cuh"
@@ -22,9 +23,50 @@ using namespace sg;
 
 static bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 
+// sg_test_fail_alloc: allocations still to succeed (-1: all)
+static std::atomic<int> g_alloc_budget{-1};
+static std::atomic<int> g_live_allocs{0};  // sg_malloc'd and not yet sg_free'd
+static std::atomic<int> g_bounds_site{0};
+
+namespace sg {
+cudaError_t sg_malloc(void** ptr, size_t bytes)
+{
+    int n = g_alloc_budget.load();
+    while (n >= 0) {
+        if (n == 0) {
+            *ptr = nullptr;
+            return cudaErrorMemoryAllocation;
+        }
+        if (g_alloc_budget.compare_exchange_weak(n, n - 1)) break;
+    }
+    const cudaError_t e = cudaMalloc(ptr, bytes);
+    if (e == cudaSuccess) g_live_allocs++;
+    return e;
+}
+void sg_free(void* ptr)
+{
+    if (ptr && cudaFree(ptr) == cudaSuccess) g_live_allocs--;
+}
+}  // namespace sg
+
+int sg_test_live_allocations(void) { return g_live_allocs.load(); }
+
+int sg_test_fail_alloc(int after) { return g_alloc_budget.exchange(after < 0 ? -1 : after); }
+
+int sg_checked_build(void)
+{
+#ifdef SG_DEBUG
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+int sg_last_bounds_site(void) { return g_bounds_site.load(); }
+
 static sg_status dev_alloc(sg_plan* p, void** ptr, size_t bytes)
 {
-    if (cudaMalloc(ptr, bytes) != cudaSuccess) {
+    if (sg_malloc(ptr, bytes) != cudaSuccess) {
         *ptr = nullptr;
         cudaGetLastError();
         return SG_ERR_ALLOC;
@@ -42,9 +84,9 @@ static void free_plan(sg_plan* p)
     if (p->bstream) cudaStreamDestroy(p->bstream);
     // wc lies inside wb's allocation
     void* bufs[] = {p->tw, p->wa, p->wb, p->kr, p->kp, p->wpre, p->wpost, p->tw64, p->cells, p->keff,
-                    p->h_sigma, p->h_fr, p->h_fp, p->derr, p->egr, p->egp, p->wtab, p->wtmp};
+                    p->h_sigma, p->h_fr, p->h_fp, p->derr, p->egr, p->egp, p->wtab, p->wtmp, p->xf, p->xw};
     for (void* b : bufs)
-        if (b) cudaFree(b);
+        sg_free(b);
     free(p);
 }
 
@@ -94,6 +136,7 @@ const char* sg_status_string(sg_status s)
         case SG_ERR_NOT_BUILT: return "kernels not built (call sg_kernels_build)";
         case SG_ERR_TIMEOUT: return "quadrature or device wait did not converge";
         case SG_ERR_IO: return "plan file could not be written or read, or is not a plan file of this library";
+        case SG_ERR_BOUNDS: return "an index check of a pass failed (checked build); results invalid";
     }
     return "unknown status";
 }
@@ -102,7 +145,7 @@ sg_status sg_plan_create(sg_plan** out, int nu, int nphi, double u_min, double d
 {
     if (!out) return SG_ERR_ARG;
     if (!(du > 0.0) || !isfinite(du) || !isfinite(u_min) || !isfinite(G)) return SG_ERR_ARG;
-    if (dtype != SG_F32 && dtype != SG_F64) return SG_ERR_ARG;
+    if (dtype != SG_F32 && dtype != SG_F64 && dtype != SG_F32X2) return SG_ERR_ARG;
     if (!is_pow2(nu) || !is_pow2(nphi)) return SG_ERR_UNSUPPORTED;
     const int numax = dtype == SG_F32 ? 4096 : 2048;
     const int nphimax = dtype == SG_F32 ? 8192 : 4096;
@@ -117,7 +160,7 @@ sg_status sg_plan_create(sg_plan** out, int nu, int nphi, double u_min, double d
     p->du = du;
     p->G = G;
     p->weight_p = 2;
-    p->elem = dtype == SG_F32 ? sizeof(float) : sizeof(double);
+    p->elem = dtype == SG_F32 ? sizeof(float) : sizeof(double);  // a double-float takes 8 bytes too
     const size_t cx = 2 * p->elem;
     if (cudaGetDevice(&p->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess) {
@@ -134,7 +177,9 @@ sg_status sg_plan_create(sg_plan** out, int nu, int nphi, double u_min, double d
         (st = dev_alloc(p, &p->kp, nk * cx)) || (st = dev_alloc(p, &p->wpre, nu * p->elem)) ||
         (st = dev_alloc(p, &p->wpost, nu * p->elem)) || (st = dev_alloc(p, (void**)&p->derr, 16)) ||
         (st = dev_alloc(p, (void**)&p->cells, (size_t)6 * (2 * nu + 1) * nphi * sizeof(double))) ||
-        (st = dev_alloc(p, (void**)&p->keff, (size_t)2 * (2 * nu - 1) * nphi * sizeof(double)))) {
+        (st = dev_alloc(p, (void**)&p->keff, (size_t)2 * (2 * nu - 1) * nphi * sizeof(double))) ||
+        (dtype == SG_F32X2 && ((st = dev_alloc(p, &p->xf, (size_t)3 * nu * nphi * sizeof(dfloat))) ||
+                               (st = dev_alloc(p, &p->xw, (size_t)2 * nphi * sizeof(dfloat)))))) {
         free_plan(p);
         return st;
     }
@@ -169,6 +214,10 @@ sg_status sg_plan_create(sg_plan** out, int nu, int nphi, double u_min, double d
         std::vector<float> t32(2 * SG_NMAX);
         for (int j = 0; j < 2 * SG_NMAX; j++) t32[j] = (float)t64[j];
         ce = cudaMemcpy(p->tw, t32.data(), SG_NMAX * sizeof(float2), cudaMemcpyHostToDevice);
+    } else if (dtype == SG_F32X2) {
+        std::vector<dfloat> tdf(2 * SG_NMAX);
+        for (int j = 0; j < 2 * SG_NMAX; j++) tdf[j] = dfloat(t64[j]);
+        ce = cudaMemcpy(p->tw, tdf.data(), SG_NMAX * sizeof(dfloat2), cudaMemcpyHostToDevice);
     } else {
         ce = cudaMemcpy(p->tw, t64.data(), SG_NMAX * sizeof(double2), cudaMemcpyHostToDevice);
     }
@@ -183,6 +232,7 @@ sg_status sg_plan_create(sg_plan** out, int nu, int nphi, double u_min, double d
 sg_status sg_plan_destroy(sg_plan* p)
 {
     if (!p) return SG_ERR_ARG;
+    batch_forget_plan(p);
     free_plan(p);
     return SG_OK;
 }
@@ -260,7 +310,7 @@ sg_status sg_plan_load(sg_plan** out, const char* path, cudaStream_t stream)
     if (!f) return SG_ERR_IO;
     PlanFileHeader h;
     if (fread(&h, sizeof(h), 1, f) != 1 || memcmp(h.magic, kPlanMagic, 8) != 0 || h.version != 1 ||
-        (h.dtype != SG_F32 && h.dtype != SG_F64)) {
+        (h.dtype != SG_F32 && h.dtype != SG_F64 && h.dtype != SG_F32X2)) {
         fclose(f);
         return SG_ERR_IO;
     }
@@ -326,6 +376,7 @@ sg_status sg_kernels_build(sg_plan* p, const sg_build_opts* opts, cudaStream_t s
     }
     // beta^{p (i - i_ref)} must stay in range for both dtypes
     if (fabs((double)wp * p->du * p->nu) > 60.0) return SG_ERR_UNSUPPORTED;
+    p->built = 0;  // until every table below is rewritten
     p->weight_p = wp;
     p->rtol = rtol;
     const int nu = p->nu, nphi = p->nphi, L = 2 * nu;
@@ -340,7 +391,16 @@ sg_status sg_kernels_build(sg_plan* p, const sg_build_opts* opts, cudaStream_t s
             // the potential carries the target radius: Phi_i = G r_i sum sigma K^P
             if (kind == SG_KERNEL_POTENTIAL) post[i] *= 0.5 * exp(p->u_min + i * p->du) * (1.0 + exp(p->du));
         }
-        if (p->dtype == SG_F32) {
+        if (p->dtype == SG_F32X2) {
+            std::vector<dfloat> a(nu), b(nu);
+            for (int i = 0; i < nu; i++) {
+                a[i] = dfloat(pre[i]);
+                b[i] = dfloat(post[i]);
+            }
+            SG_TRY(cudaMemcpyAsync(p->wpre, a.data(), nu * sizeof(dfloat), cudaMemcpyHostToDevice, stream));
+            SG_TRY(cudaMemcpyAsync(p->wpost, b.data(), nu * sizeof(dfloat), cudaMemcpyHostToDevice, stream));
+            SG_TRY(cudaStreamSynchronize(stream));
+        } else if (p->dtype == SG_F32) {
             std::vector<float> a(nu), b(nu);
             for (int i = 0; i < nu; i++) {
                 a[i] = (float)pre[i];
@@ -385,10 +445,11 @@ sg_status sg_kernels_build(sg_plan* p, const sg_build_opts* opts, cudaStream_t s
     double *nsr = nullptr, *nsp = nullptr, *wcells = nullptr;
     double2* W = nullptr;
     sg_status ret = SG_OK;
-    if (cudaMalloc(&flag, 4 * sizeof(int)) != cudaSuccess || cudaMalloc(&nsr, (size_t)L * nphi * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&nsp, (size_t)L * nphi * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&W, (size_t)(nphi / 2 + 1) * L * sizeof(double2)) != cudaSuccess ||
-        (wedge && cudaMalloc(&wcells, (size_t)6 * nu * nphi * sizeof(double)) != cudaSuccess)) {
+    if (sg_malloc((void**)&flag, 4 * sizeof(int)) != cudaSuccess ||
+        sg_malloc((void**)&nsr, (size_t)L * nphi * sizeof(double)) != cudaSuccess ||
+        sg_malloc((void**)&nsp, (size_t)L * nphi * sizeof(double)) != cudaSuccess ||
+        sg_malloc((void**)&W, (size_t)(nphi / 2 + 1) * L * sizeof(double2)) != cudaSuccess ||
+        (wedge && sg_malloc((void**)&wcells, (size_t)6 * nu * nphi * sizeof(double)) != cudaSuccess)) {
         cudaGetLastError();
         ret = SG_ERR_ALLOC;
         goto done;
@@ -409,17 +470,23 @@ sg_status sg_kernels_build(sg_plan* p, const sg_build_opts* opts, cudaStream_t s
                (kind == SG_KERNEL_SIM && ntpz > 0 &&
                 launch_cells_tpz(nu, nphi, p->du, ntpz, rtol, p->cells, flag, stream) != cudaSuccess) ||
                launch_fold(nu, nphi, p->du, p->G, wp, p->cells, p->keff, nsr, nsp, stream) != cudaSuccess ||
-        (edges && (p->dtype == SG_F32 ? launch_edge_spectra<float>(nu, nphi, p->du, p->G, p->cells, p->tw64,
-                                                                   (float*)p->egr, (float*)p->egp, stream)
-                                      : launch_edge_spectra<double>(nu, nphi, p->du, p->G, p->cells, p->tw64,
-                                                                    (double*)p->egr, (double*)p->egp, stream)) !=
-                     cudaSuccess)) {
+        (edges && (p->dtype == SG_F32
+                       ? launch_edge_spectra<float>(nu, nphi, p->du, p->G, p->cells, p->tw64, (float*)p->egr,
+                                                    (float*)p->egp, stream)
+                   : p->dtype == SG_F32X2
+                       ? launch_edge_spectra<dfloat>(nu, nphi, p->du, p->G, p->cells, p->tw64, (dfloat*)p->egr,
+                                                     (dfloat*)p->egp, stream)
+                       : launch_edge_spectra<double>(nu, nphi, p->du, p->G, p->cells, p->tw64, (double*)p->egr,
+                                                     (double*)p->egp, stream)) != cudaSuccess)) {
         ret = SG_ERR_CUDA;
         goto done;
     }
     if (wedge && (p->dtype == SG_F32
                       ? launch_wedge_tables<float>(nu, nphi, p->du, p->G, rtol, kind == SG_KERNEL_POTENTIAL, wcells,
                                                    p->tw64, (float*)p->wtab, flag, stream)
+                  : p->dtype == SG_F32X2
+                      ? launch_wedge_tables<dfloat>(nu, nphi, p->du, p->G, rtol, kind == SG_KERNEL_POTENTIAL, wcells,
+                                                    p->tw64, (dfloat*)p->wtab, flag, stream)
                       : launch_wedge_tables<double>(nu, nphi, p->du, p->G, rtol, kind == SG_KERNEL_POTENTIAL, wcells,
                                                     p->tw64, (double*)p->wtab, flag, stream)) != cudaSuccess) {
         ret = SG_ERR_CUDA;
@@ -429,6 +496,8 @@ sg_status sg_kernels_build(sg_plan* p, const sg_build_opts* opts, cudaStream_t s
         PlanView v = view(p);
         cudaError_t e = p->dtype == SG_F32
                             ? launch_spectra<float2>(v, nsr, nsp, W, (float2*)p->kr, (float2*)p->kp, stream)
+                        : p->dtype == SG_F32X2
+                            ? launch_spectra<dfloat2>(v, nsr, nsp, W, (dfloat2*)p->kr, (dfloat2*)p->kp, stream)
                             : launch_spectra<double2>(v, nsr, nsp, W, (double2*)p->kr, (double2*)p->kp, stream);
         if (e != cudaSuccess) {
             ret = SG_ERR_CUDA;
@@ -446,13 +515,13 @@ sg_status sg_kernels_build(sg_plan* p, const sg_build_opts* opts, cudaStream_t s
         p->wedge = wedge;
         if (p->report[0]) ret = SG_ERR_TIMEOUT;
     }
-    if (ret == SG_OK) ret = noalloc_prepare(p, stream);
+    if (ret == SG_OK && (ret = noalloc_prepare(p, stream)) != SG_OK) p->built = 0;
 done:
-    if (wcells) cudaFree(wcells);
-    if (flag) cudaFree(flag);
-    if (nsr) cudaFree(nsr);
-    if (nsp) cudaFree(nsp);
-    if (W) cudaFree(W);
+    sg_free(wcells);
+    sg_free(flag);
+    sg_free(nsr);
+    sg_free(nsp);
+    sg_free(W);
     return ret;
 }
 
@@ -467,6 +536,51 @@ static sg_status check_fields(const sg_plan* p, const void* a, const void* b, co
     return SG_OK;
 }
 
+// The passes on the plan's working type.  The compensated plans (SG_F32X2)
+// take and give FP64 fields: their inputs are split into double-float
+// working fields first and the results rounded back to FP64 after.
+static cudaError_t run_forward(sg_plan* p, PlanView v, const void* sigma, void* Fr, void* Fp, cudaStream_t st,
+                               cudaEvent_t* ev = nullptr, bool direct = false)
+{
+    if (p->dtype == SG_F32)
+        return launch_forward<float>(v, (const float*)sigma, (float*)Fr, (float*)Fp, st, ev, direct);
+    if (p->dtype == SG_F64)
+        return launch_forward<double>(v, (const double*)sigma, (double*)Fr, (double*)Fp, st, ev, direct);
+    const size_t n = (size_t)p->nu * p->nphi;
+    dfloat* const xs = (dfloat*)p->xf;
+    dfloat* const xr = xs + n;
+    dfloat* const xp = xs + 2 * n;
+    cudaError_t e;
+    if ((e = launch_to_df((const double*)sigma, xs, n, p->sms, st)) != cudaSuccess) return e;
+    if (v.sigw) {
+        if ((e = launch_to_df((const double*)v.sigw, (dfloat*)p->xw, p->nphi, p->sms, st)) != cudaSuccess) return e;
+        v.sigw = p->xw;
+    }
+    if ((e = launch_forward<dfloat>(v, xs, xr, xp, st, ev, false)) != cudaSuccess) return e;
+    if ((e = launch_from_df(xr, (double*)Fr, n, p->sms, st)) != cudaSuccess) return e;
+    return launch_from_df(xp, (double*)Fp, n, p->sms, st);
+}
+
+static cudaError_t run_backward(sg_plan* p, PlanView v, const void* gr, const void* gp, void* gs, cudaStream_t st,
+                                cudaEvent_t* ev = nullptr)
+{
+    if (p->dtype == SG_F32) return launch_backward<float>(v, (const float*)gr, (const float*)gp, (float*)gs, st, ev);
+    if (p->dtype == SG_F64)
+        return launch_backward<double>(v, (const double*)gr, (const double*)gp, (double*)gs, st, ev);
+    const size_t n = (size_t)p->nu * p->nphi;
+    dfloat* const xr = (dfloat*)p->xf;
+    dfloat* const xp = xr + n;
+    dfloat* const xs = xr + 2 * n;
+    cudaError_t e;
+    if ((e = launch_to_df((const double*)gr, xr, n, p->sms, st)) != cudaSuccess) return e;
+    if ((e = launch_to_df((const double*)gp, xp, n, p->sms, st)) != cudaSuccess) return e;
+    double* const gsw = (double*)v.gsigw;
+    if (gsw) v.gsigw = (dfloat*)p->xw + p->nphi;
+    if ((e = launch_backward<dfloat>(v, xr, xp, xs, st, ev)) != cudaSuccess) return e;
+    if (gsw && (e = launch_from_df((const dfloat*)v.gsigw, gsw, p->nphi, p->sms, st)) != cudaSuccess) return e;
+    return launch_from_df(xs, (double*)gs, n, p->sms, st);
+}
+
 sg_status sg_forces_wedge(sg_plan* p, const void* sigma, const void* sigma_w, void* Fr, void* Fp, cudaStream_t stream)
 {
     if (!p) return SG_ERR_ARG;
@@ -479,8 +593,7 @@ sg_status sg_forces_wedge(sg_plan* p, const void* sigma, const void* sigma_w, vo
     if (sigma == Fr || sigma == Fp || Fr == Fp || sigma_w == Fr || sigma_w == Fp) return SG_ERR_ARG;
     PlanView v = view(p);
     v.sigw = sigma_w;
-    cudaError_t e = p->dtype == SG_F32 ? launch_forward<float>(v, (const float*)sigma, (float*)Fr, (float*)Fp, stream)
-                                       : launch_forward<double>(v, (const double*)sigma, (double*)Fr, (double*)Fp, stream);
+    cudaError_t e = run_forward(p, v, sigma, Fr, Fp, stream);
     return e == cudaSuccess ? SG_OK : SG_ERR_CUDA;
 }
 
@@ -497,9 +610,7 @@ sg_status sg_forces_wedge_backward(sg_plan* p, const void* gr, const void* gp, v
     if (gs == gr || gs == gp || gs_w == gr || gs_w == gp || gs_w == gs) return SG_ERR_ARG;
     PlanView v = view(p);
     v.gsigw = gs_w;
-    cudaError_t e = p->dtype == SG_F32
-                        ? launch_backward<float>(v, (const float*)gr, (const float*)gp, (float*)gs, stream)
-                        : launch_backward<double>(v, (const double*)gr, (const double*)gp, (double*)gs, stream);
+    cudaError_t e = run_backward(p, v, gr, gp, gs, stream);
     return e == cudaSuccess ? SG_OK : SG_ERR_CUDA;
 }
 
@@ -509,8 +620,7 @@ sg_status sg_forces(sg_plan* p, const void* sigma, void* Fr, void* Fp, cudaStrea
     if (st) return st;
     if (sigma == Fr || sigma == Fp || Fr == Fp) return SG_ERR_ARG;
     PlanView v = view(p);
-    cudaError_t e = p->dtype == SG_F32 ? launch_forward<float>(v, (const float*)sigma, (float*)Fr, (float*)Fp, stream)
-                                       : launch_forward<double>(v, (const double*)sigma, (double*)Fr, (double*)Fp, stream);
+    cudaError_t e = run_forward(p, v, sigma, Fr, Fp, stream);
     return e == cudaSuccess ? SG_OK : SG_ERR_CUDA;
 }
 
@@ -544,10 +654,7 @@ sg_status sg_forces_timed(sg_plan* p, const void* sigma, void* Fr, void* Fp, cud
     if (!ms || sigma == Fr || sigma == Fp || Fr == Fp) return SG_ERR_ARG;
     if ((st = timing_events(p))) return st;
     PlanView v = view(p);
-    cudaError_t e =
-        p->dtype == SG_F32
-            ? launch_forward<float>(v, (const float*)sigma, (float*)Fr, (float*)Fp, stream, p->ev)
-            : launch_forward<double>(v, (const double*)sigma, (double*)Fr, (double*)Fp, stream, p->ev);
+    cudaError_t e = run_forward(p, v, sigma, Fr, Fp, stream, p->ev);
     if (e != cudaSuccess) return SG_ERR_CUDA;
     return event_times(p, ms);
 }
@@ -560,9 +667,7 @@ sg_status sg_forces_backward_timed(sg_plan* p, const void* gr, const void* gp, v
     if (!ms || gs == gr || gs == gp) return SG_ERR_ARG;
     if ((st = timing_events(p))) return st;
     PlanView v = view(p);
-    cudaError_t e = p->dtype == SG_F32
-                        ? launch_backward<float>(v, (const float*)gr, (const float*)gp, (float*)gs, stream, p->ev)
-                        : launch_backward<double>(v, (const double*)gr, (const double*)gp, (double*)gs, stream, p->ev);
+    cudaError_t e = run_backward(p, v, gr, gp, gs, stream, p->ev);
     if (e != cudaSuccess) return SG_ERR_CUDA;
     return event_times(p, ms);
 }
@@ -573,9 +678,7 @@ sg_status sg_forces_backward(sg_plan* p, const void* gr, const void* gp, void* g
     if (st) return st;
     if (gs == gr || gs == gp) return SG_ERR_ARG;
     PlanView v = view(p);
-    cudaError_t e = p->dtype == SG_F32
-                        ? launch_backward<float>(v, (const float*)gr, (const float*)gp, (float*)gs, stream)
-                        : launch_backward<double>(v, (const double*)gr, (const double*)gp, (double*)gs, stream);
+    cudaError_t e = run_backward(p, v, gr, gp, gs, stream);
     return e == cudaSuccess ? SG_OK : SG_ERR_CUDA;
 }
 
@@ -605,21 +708,20 @@ sg_status sg_forces_host(sg_plan* p, const void* sigma_h, void* Fr_h, void* Fp_h
     void* ds = mapped_host(sigma_h, p->device);
     void* dr = ds ? mapped_host(Fr_h, p->device) : nullptr;
     void* dp = dr ? mapped_host(Fp_h, p->device) : nullptr;
-    if (dp && !(((uintptr_t)ds | (uintptr_t)dr | (uintptr_t)dp) & 15) && ds != dr && ds != dp && dr != dp) {
+    // (the compensated plans convert their fields on the device: staged)
+    if (dp && p->dtype != SG_F32X2 && !(((uintptr_t)ds | (uintptr_t)dr | (uintptr_t)dp) & 15) && ds != dr &&
+        ds != dp && dr != dp) {
         PlanView v = view(p);
-        cudaError_t e =
-            p->dtype == SG_F32
-                ? launch_forward<float>(v, (const float*)ds, (float*)dr, (float*)dp, stream, nullptr, true)
-                : launch_forward<double>(v, (const double*)ds, (double*)dr, (double*)dp, stream, nullptr, true);
+        cudaError_t e = run_forward(p, v, ds, dr, dp, stream, nullptr, true);
         if (e != cudaSuccess) return SG_ERR_CUDA;
         return sg_plan_check(p, stream);  // synchronises; reports a device-side timeout
     }
     sg_status st;
-    if (!p->h_sigma) {
-        if ((st = dev_alloc(p, &p->h_sigma, bytes)) || (st = dev_alloc(p, &p->h_fr, bytes)) ||
-            (st = dev_alloc(p, &p->h_fp, bytes)))
-            return st;
-    }
+    // each staging buffer on its first use (a call that could not allocate
+    // them all leaves the others for the next call)
+    if ((!p->h_sigma && (st = dev_alloc(p, &p->h_sigma, bytes))) || (!p->h_fr && (st = dev_alloc(p, &p->h_fr, bytes))) ||
+        (!p->h_fp && (st = dev_alloc(p, &p->h_fp, bytes))))
+        return st;
     SG_TRY(cudaMemcpyAsync(p->h_sigma, sigma_h, bytes, cudaMemcpyHostToDevice, stream));
     if ((st = sg_forces(p, p->h_sigma, p->h_fr, p->h_fp, stream))) return st;
     SG_TRY(cudaMemcpyAsync(Fr_h, p->h_fr, bytes, cudaMemcpyDeviceToHost, stream));
@@ -627,17 +729,39 @@ sg_status sg_forces_host(sg_plan* p, const void* sigma_h, void* Fr_h, void* Fp_h
     return sg_plan_check(p, stream);  // synchronises; reports a device-side timeout
 }
 
-sg_status sg_batch_reserve(int n) { return n >= 0 ? SG_OK : SG_ERR_ARG; }
-
-sg_status sg_forces_batched(const sg_batch_item* items, int n, cudaStream_t stream)
+static sg_status check_batch(const sg_batch_item* items, int n)
 {
-    if (n < 0 || (n > 0 && !items)) return SG_ERR_ARG;
+    if (n <= 0 || !items) return SG_ERR_ARG;
     for (int b = 0; b < n; b++) {
         if (!items[b].plan) return SG_ERR_ARG;
         sg_status st = check_fields(items[b].plan, items[b].sigma, items[b].F_r, items[b].F_phi);
         if (st) return st;
         if (items[b].plan->dtype != items[0].plan->dtype) return SG_ERR_ARG;
     }
+    return SG_OK;
+}
+
+sg_status sg_batch_prepare(const sg_batch_item* items, int n, cudaStream_t stream)
+{
+    sg_status st = check_batch(items, n);
+    return st ? st : batch_prepare(items, n, stream);
+}
+
+sg_status sg_batch_tune(const sg_batch_item* items, int n, const char* cache_path, cudaStream_t stream, float ms[2])
+{
+    sg_status st = check_batch(items, n);
+    return st ? st : batch_tune(items, n, cache_path, stream, ms);
+}
+
+sg_status sg_forces_batched(const sg_batch_item* items, int n, cudaStream_t stream)
+{
+    if (n < 0 || (n > 0 && !items)) return SG_ERR_ARG;
+    if (n == 0) return SG_OK;
+    sg_status st0 = check_batch(items, n);
+    if (st0) return st0;
+    // one persistent launch when every item qualifies
+    st0 = batch_forward(items, n, stream);
+    if (st0 != SG_ERR_UNSUPPORTED) return st0;
     // Items of one plan share its workspace and run in item order; items of
     // different plans are independent.  With several plans, each plan's items
     // go to the plan's own stream, forked from `stream` and joined back to it
@@ -670,12 +794,16 @@ sg_status sg_forces_batched(const sg_batch_item* items, int n, cudaStream_t stre
 sg_status sg_plan_check(sg_plan* p, cudaStream_t stream)
 {
     if (!p) return SG_ERR_ARG;
-    int h = 0;
-    SG_TRY(cudaMemcpyAsync(&h, p->derr, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    int h[2] = {0, 0};  // flags, site of the first failed index check
+    SG_TRY(cudaMemcpyAsync(h, p->derr, 2 * sizeof(int), cudaMemcpyDeviceToHost, stream));
     SG_TRY(cudaStreamSynchronize(stream));
-    if (h) {
-        SG_TRY(cudaMemsetAsync(p->derr, 0, sizeof(int), stream));
+    if (h[0]) {
+        SG_TRY(cudaMemsetAsync(p->derr, 0, 2 * sizeof(int), stream));
         SG_TRY(cudaStreamSynchronize(stream));
+        if (h[0] & SG_FLAG_BOUNDS) {
+            g_bounds_site.store(h[1]);
+            return SG_ERR_BOUNDS;
+        }
         return SG_ERR_TIMEOUT;
     }
     return SG_OK;

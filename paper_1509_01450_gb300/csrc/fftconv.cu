@@ -233,6 +233,16 @@ __device__ __forceinline__ void st_pair(double2* p, double2 a, double2 b)
     p[0] = a;
     p[1] = b;
 }
+__device__ __forceinline__ void ld_pair(const dfloat2* p, dfloat2& a, dfloat2& b)
+{
+    a = p[0];
+    b = p[1];
+}
+__device__ __forceinline__ void st_pair(dfloat2* p, dfloat2 a, dfloat2 b)
+{
+    p[0] = a;
+    p[1] = b;
+}
 
 // p advanced to the next multiple of A bytes of the shared window.  The
 // offset is added to the shared-memory pointer itself: a pointer rebuilt from
@@ -283,23 +293,29 @@ __device__ __forceinline__ void split_real_pair(const V (&v)[E], V* sm, int N, i
 // Tensor stores of a staged mode-major block S[m R + r], box j issued by
 // lane j mod 32 of the calling warp (each lane then commits its own group).
 template <typename V>
-__device__ __forceinline__ void stage_store_map(const CUtensorMap* map, const V* S, int half, int ib, int R, int lane)
+__device__ __forceinline__ void stage_store_map(const CUtensorMap* map, const V* S, int half, int ib, int R, int lane,
+                                                int* err, const void* smbase)
 {
     constexpr int c = sizeof(V) / 8;  // 8-byte elements per complex value
     const int MB = row_box_modes(half);
     const uint64_t keep = sg_policy_evict_last();  // the next pass reads it from L2
-    for (int j = lane; j < half / MB; j += 32) sg_tma_store_2d(map, c * ib, j * MB, S + (size_t)j * MB * R, keep);
+    for (int j = lane; j < half / MB; j += 32)
+        SG_IF_OK(((c * ib) & 1) == 0 && ib >= 0 && sg_smem_in(smbase, S + (size_t)j * MB * R, MB * R * sizeof(V)), err,
+                 502)
+        sg_tma_store_2d(map, c * ib, j * MB, S + (size_t)j * MB * R, keep);
 }
 // Tensor loads of a mode-major block into S[m R + r], completing on bar
 // (whose expected bytes the caller has set); box j issued by lane j mod 32.
 template <typename V>
 __device__ __forceinline__ void stage_load_map(V* S, const CUtensorMap* map, int half, int ib, int R, uint64_t* bar,
-                                               int lane)
+                                               int lane, int* err, const void* smbase)
 {
     constexpr int c = sizeof(V) / 8;
     const int MB = row_box_modes(half);
     const uint64_t drop = sg_policy_evict_first();
-    for (int j = lane; j < half / MB; j += 32) sg_tma_load_2d(S + (size_t)j * MB * R, map, c * ib, j * MB, bar, drop);
+    for (int j = lane; j < half / MB; j += 32)
+        SG_IF_OK(((c * ib) & 1) == 0 && sg_smem_in(smbase, S + (size_t)j * MB * R, MB * R * sizeof(V)), err, 601)
+        sg_tma_load_2d(S + (size_t)j * MB * R, map, c * ib, j * MB, bar, drop);
 }
 
 // Common prologue of the mbarrier-fed row passes: barriers initialised and
@@ -355,6 +371,7 @@ __global__ void __launch_bounds__(NTB, (sizeof(T) == 4 && NTB == 256) ? 2 : 1) k
         const int rows = min(R, nu - rb * R);
         const uint32_t bytes = (uint32_t)((size_t)rows * N * sizeof(T));
         sg_mbar_expect_tx(&bar, bytes);
+        SG_IF_OK(rows > 0 && sg_smem_in(smraw, Si, bytes), err, 501)
         sg_bulk_g2s_hint(Si, sigma + (size_t)rb * R * N, bytes, &bar, sg_policy_evict_first());
     };
     sg_grid_dep_launch();
@@ -401,7 +418,7 @@ __global__ void __launch_bounds__(NTB, (sizeof(T) == 4 && NTB == 256) ? 2 : 1) k
         if (!use_map) {
             stage_store(A, So, nu, half, rb * R, R);
         } else if (threadIdx.x < 32) {
-            stage_store_map(&mapA, So, half, rb * R, R, lane);
+            stage_store_map(&mapA, So, half, rb * R, R, lane, err, smraw);
             sg_bulk_commit();
         }
     }
@@ -454,6 +471,61 @@ __host__ __device__ __forceinline__ size_t cols_smem_bytes(int nu)
 // k_wedge_fwd is added in the same place, its table rows read straight from
 // global memory by the threads that own the rows, s^_w from swh and a_0 from
 // row 0 of the landed column.
+// The FP32 forward column transform of mode m (16 points per thread, N_T =
+// 2 N_u / 16 threads t): the zero-padded forward FFT of the N_u values in
+// sm, the products with both kernel spectra (kr_s, kp_s in shared memory;
+// wait_spectra() waits for them and returns false if they never arrive),
+// and both inverse transforms paired in w, their exchanges in xarea.  The
+// column pass runs one mode per block; the batched kernel (SLOTTED) runs
+// several modes of one disk side by side in a block, each on its own
+// shared memory, with every barrier taken by the whole block.
+template <int LG, bool SLOTTED, typename WaitFn>
+__device__ __forceinline__ bool fwd_cols_math(float2 (&v)[16], float2* sm, const float2* kr_s, const float2* kp_s,
+                                              C2* xarea, int m, int t, int nu, int log2L,
+                                              const Twd<16, float2>& twd, WaitFn wait_spectra, C2 (&w)[16])
+{
+    typedef float2 V;
+    typedef float T;
+    constexpr int E = 16;
+    const int L = 2 * nu, NT = L / E;
+    fft<E, -1, LG, true>(v, sm, L, log2L, t, twd);  // rows >= N_u are zero; the spectra land meanwhile
+    if (!wait_spectra()) return false;
+    if constexpr (SLOTTED) {  // the barrier below is the whole block's
+        if (m == 0)
+#pragma unroll
+            for (int e = 0; e < E; e++) sm[sg_pad(t + e * NT)] = v[e];
+        __syncthreads();
+    } else if (m == 0) {
+#pragma unroll
+        for (int e = 0; e < E; e++) sm[sg_pad(t + e * NT)] = v[e];
+        __syncthreads();
+    }
+    if (m == 0) {
+        // v holds the FFT of (DC + i Nyquist): separate the two real
+        // sequences and apply the kernels of modes 0 and N_phi/2; the phi
+        // force of both modes vanishes
+#pragma unroll
+        for (int e = 0; e < E; e++) {
+            const int k = t + e * NT;
+            const V z = v[e], zc = cconj(sm[sg_pad((L - k) & (L - 1))]);
+            const V a = cscale(cadd(z, zc), (T)0.5);
+            const V d = csub(z, zc);
+            const V b = V{sg_mul(d.y, (T)0.5), sg_mul(-d.x, (T)0.5)};
+            w[e] = c2(cadd(cmul(a, khat_r_s(kr_s, k, L, nu)), cmuli(cmul(b, khat_r_s(kp_s, k, L, nu)))), V{0, 0});
+        }
+    } else {
+#pragma unroll
+        for (int e = 0; e < E; e++) {
+            V a, b;
+            khat_at<E>(kr_s, kp_s, t, e, NT, a, b);
+            w[e] = c2(cmul(v[e], a), cmul(v[e], b));
+        }
+    }
+    // both inverse transforms; their first exchange waits for every spectrum read
+    sg_fft_pair<+1, LG>(w, xarea, L, log2L, t, twd.h);
+    return true;
+}
+
 template <typename T, int E, int NTB, int LG = 0, bool EDGE = false, bool WEDGE = false>
 __global__ void SG_FCOLS_BOUNDS(T, NTB, LG, EDGE) k_fwd_cols(const typename CX<T>::t* __restrict__ A,
                                                   const typename CX<T>::t* __restrict__ Kr,
@@ -492,19 +564,26 @@ __global__ void SG_FCOLS_BOUNDS(T, NTB, LG, EDGE) k_fwd_cols(const typename CX<T
     if (t == 0) {
         // the spectra (written only by the build) before the previous pass ends
         sg_mbar_expect_tx(&bar[1], 2 * kb + (EDGE ? 2 * gb : 0));
-        sg_bulk_g2s_hint(kr_s, Kr + (size_t)m * KS, kb, &bar[1], drop);
-        // mode 0 holds (DC, Nyquist): bring the Nyquist mode's Khat_r instead
-        // of Khat_phi, which vanishes at both
-        sg_bulk_g2s_hint(kp_s, (m == 0 ? Kr + (size_t)half * KS : Kp + (size_t)m * KS), kb, &bar[1], drop);
+        // spectra [N_phi/2 + 1][KS], edge tables [N_phi/2 + 1][GS]
+        SG_IF_OK(m < half && sg_smem_in(smraw, kr_s, 2 * kb), err, 301) {
+            sg_bulk_g2s_hint(kr_s, Kr + (size_t)m * KS, kb, &bar[1], drop);
+            // mode 0 holds (DC, Nyquist): bring the Nyquist mode's Khat_r
+            // instead of Khat_phi, which vanishes at both
+            sg_bulk_g2s_hint(kp_s, (m == 0 ? Kr + (size_t)half * KS : Kp + (size_t)m * KS), kb, &bar[1], drop);
+        }
         if constexpr (EDGE) {  // likewise the edge tables' rows
-            sg_bulk_g2s_hint(g_s, egr + (size_t)m * GS, gb, &bar[1], drop);
-            sg_bulk_g2s_hint(g_s + GS, (m == 0 ? egr + (size_t)half * GS : egp + (size_t)m * GS), gb, &bar[1], drop);
+            SG_IF_OK(m < half && sg_smem_in(smraw, g_s, 2 * gb), err, 302) {
+                sg_bulk_g2s_hint(g_s, egr + (size_t)m * GS, gb, &bar[1], drop);
+                sg_bulk_g2s_hint(g_s + GS, (m == 0 ? egr + (size_t)half * GS : egp + (size_t)m * GS), gb, &bar[1],
+                                 drop);
+            }
         }
     }
     sg_grid_dep_launch();
     sg_grid_dep_wait();  // A is the previous pass's result
     if (t == 0) {
         sg_mbar_expect_tx(&bar[0], ab);
+        SG_IF_OK(sg_in((long long)m * nu, nu, (long long)half * nu) && sg_smem_in(smraw, sm, ab), err, 303)
         sg_bulk_g2s_hint(sm, A + (size_t)m * nu, ab, &bar[0], drop);
     }
     const Twd<E, V> twd = make_twd<E>(log2L, t, tw);
@@ -536,36 +615,11 @@ __global__ void SG_FCOLS_BOUNDS(T, NTB, LG, EDGE) k_fwd_cols(const typename CX<T
         }
     }
     if constexpr (sizeof(T) == 4 && E == 16) {
-        fft<E, -1, LG, true>(v, sm, L, log2L, t, twd);  // rows >= N_u are zero; the spectra land meanwhile
-        if (__syncthreads_or(!sg_mbar_wait_bounded(&bar[1], 0, err, 1, wlim))) return;
         C2 w[E];  // (Y_r, Y_phi) of each frequency, paired
-        if (m == 0) {
-            // v holds the FFT of (DC + i Nyquist): separate the two real
-            // sequences and apply the kernels of modes 0 and N_phi/2; the phi
-            // force of both modes vanishes
-#pragma unroll
-            for (int e = 0; e < E; e++) sm[sg_pad(t + e * NT)] = v[e];
-            __syncthreads();
-#pragma unroll
-            for (int e = 0; e < E; e++) {
-                const int k = t + e * NT;
-                const V z = v[e], zc = cconj(sm[sg_pad((L - k) & (L - 1))]);
-                const V a = cscale(cadd(z, zc), (T)0.5);
-                const V d = csub(z, zc);
-                const V b = V{d.y * (T)0.5, -d.x * (T)0.5};
-                w[e] = c2(cadd(cmul(a, khat_r_s(kr_s, k, L, nu)), cmuli(cmul(b, khat_r_s(kp_s, k, L, nu)))),
-                          V{0, 0});
-            }
-        } else {
-#pragma unroll
-            for (int e = 0; e < E; e++) {
-                V a, b;
-                khat_at<E>(kr_s, kp_s, t, e, NT, a, b);
-                w[e] = c2(cmul(v[e], a), cmul(v[e], b));
-            }
-        }
-        // both inverse transforms; their first exchange waits for every spectrum read
-        sg_fft_pair<+1, LG>(w, reinterpret_cast<C2*>(smraw), L, log2L, t, twd.h);
+        const auto wait_spectra = [&] { return !__syncthreads_or(!sg_mbar_wait_bounded(&bar[1], 0, err, 1, wlim)); };
+        if (!fwd_cols_math<LG, false>(v, sm, kr_s, kp_s, reinterpret_cast<C2*>(smraw), m, t, nu, log2L, twd,
+                                      wait_spectra, w))
+            return;
         if constexpr (EDGE) {
             // row i: += wpre[i] sum_a (gr[i - a] s^_a, -i gp[i - a] s^_a), i - a + N_u
             // = i + 1 + N_u, i + N_u, i + 1, i for a = -1, 0, N_u - 1, N_u
@@ -594,6 +648,7 @@ __global__ void SG_FCOLS_BOUNDS(T, NTB, LG, EDGE) k_fwd_cols(const typename CX<T
                 if constexpr (WEDGE) {
                     // += (Wr s^_w + Vr a_0, -i (Wphi s^_w + Vphi a_0)); mode 0: Nyquist tables on .y
                     const long tsz = (long)(half + 1) * nu;
+                    SG_IF_OK(sg_in((long long)half * nu + i, 1, tsz), err, 304) {}
                     const V a0 = es[4], sw = es[5];
                     const T* tb = wdg.tab + (long)m * nu + i;
                     const T wr = tb[0], wp = tb[tsz], vr = tb[2 * tsz], vp = tb[3 * tsz];
@@ -616,13 +671,16 @@ __global__ void SG_FCOLS_BOUNDS(T, NTB, LG, EDGE) k_fwd_cols(const typename CX<T
             float4* P = reinterpret_cast<float4*>(Br) + (size_t)m * nu;
 #pragma unroll
             for (int e = 0; e < E / 2; e++)  // crop to N_u rows
+                SG_IF_OK(sg_in((long long)m * nu + t + e * NT, 1, (long long)half * nu), err, 305)
                 sg_st_hint(P + t + e * NT, make_float4(f2_lo(w[e].x), f2_lo(w[e].y), f2_hi(w[e].x), f2_hi(w[e].y)),
                            keep);
         } else {
 #pragma unroll
             for (int e = 0; e < E / 2; e++) {  // crop to N_u rows
-                sg_st_hint(Br + (size_t)m * nu + t + e * NT, c2_lo(w[e]), keep);
-                sg_st_hint(Cp + (size_t)m * nu + t + e * NT, c2_hi(w[e]), keep);
+                SG_IF_OK(sg_in((long long)m * nu + t + e * NT, 1, (long long)half * nu), err, 306) {
+                    sg_st_hint(Br + (size_t)m * nu + t + e * NT, c2_lo(w[e]), keep);
+                    sg_st_hint(Cp + (size_t)m * nu + t + e * NT, c2_hi(w[e]), keep);
+                }
             }
         }
         return;
@@ -669,7 +727,9 @@ __global__ void SG_FCOLS_BOUNDS(T, NTB, LG, EDGE) k_fwd_cols(const typename CX<T
         } else {
             V* out = (pass == 1 ? Br : Cp) + (size_t)m * nu;
 #pragma unroll
-            for (int e = 0; e < E / 2; e++) sg_st_hint(out + t + e * NT, cconj(v[e]), keep);  // crop to N_u rows
+            for (int e = 0; e < E / 2; e++)  // crop to N_u rows
+                SG_IF_OK(sg_in((long long)m * nu + t + e * NT, 1, (long long)half * nu), err, 307)
+                sg_st_hint(out + t + e * NT, cconj(v[e]), keep);
             if (pass == 1) {
 #pragma unroll
                 for (int e = 0; e < E; e++) v[e] = ks[t + e * NT];
@@ -734,8 +794,8 @@ __global__ void __launch_bounds__(NTB, (sizeof(T) == 4 && NTB == 256) ? 2 : 1) k
         if (use_map) {
             if (lane == 0) sg_mbar_expect_tx(&bar, (uint32_t)(2 * (size_t)half * R * sizeof(V)));
             __syncwarp();
-            stage_load_map(Sb, &mapB, half, rb * R, R, &bar, lane);
-            stage_load_map(Sc, &mapC, half, rb * R, R, &bar, lane);
+            stage_load_map(Sb, &mapB, half, rb * R, R, &bar, lane, err, smraw);
+            stage_load_map(Sc, &mapC, half, rb * R, R, &bar, lane, err, smraw);
         } else {
             stage_load(Sb, Br, nu, half, rb * R, R);
             stage_load(Sc, Cp, nu, half, rb * R, R);
@@ -971,7 +1031,7 @@ __global__ void __launch_bounds__(256) k_edge_bwd(const typename CX<T>::t* __res
 #pragma unroll
     for (int v = 0; v < 8; v++)
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc[v] += __shfl_xor_sync(0xffffffffu, acc[v], o);
+        for (int o = 16; o > 0; o >>= 1) acc[v] += sg_shfl_xor(acc[v], o);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     if (lane == 0)
 #pragma unroll
@@ -1037,8 +1097,12 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 512) k_bwd_rows(const T
         const uint64_t pol = sg_policy_evict_first();
         V* dst = ring + q * bufE;
         sg_mbar_expect_tx(&bar[q], 2 * bytes);
-        sg_bulk_g2s_hint(dst, gr + (size_t)rb * R * N, bytes, &bar[q], pol);
-        sg_bulk_g2s_hint(reinterpret_cast<T*>(dst) + (size_t)R * N, gp + (size_t)rb * R * N, bytes, &bar[q], pol);
+        SG_IF_OK(rows > 0 && sg_smem_in(smraw, dst, bytes) &&
+                     sg_smem_in(smraw, reinterpret_cast<T*>(dst) + (size_t)R * N, bytes),
+                 err, 701) {
+            sg_bulk_g2s_hint(dst, gr + (size_t)rb * R * N, bytes, &bar[q], pol);
+            sg_bulk_g2s_hint(reinterpret_cast<T*>(dst) + (size_t)R * N, gp + (size_t)rb * R * N, bytes, &bar[q], pol);
+        }
     };
     sg_grid_dep_launch();
     sg_grid_dep_wait();  // the seeds may come from the previous kernel on the stream
@@ -1094,8 +1158,8 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 512) k_bwd_rows(const T
             stage_store(A, Sa, nu, half, rb * R, R);
             stage_store(C, Sc, nu, half, rb * R, R);
         } else if (producer) {
-            stage_store_map(&mapA, Sa, half, rb * R, R, lane);
-            stage_store_map(&mapC, Sc, half, rb * R, R, lane);
+            stage_store_map(&mapA, Sa, half, rb * R, R, lane, err, smraw);
+            stage_store_map(&mapC, Sc, half, rb * R, R, lane, err, smraw);
             sg_bulk_commit();
         }
     }
@@ -1173,11 +1237,16 @@ __global__ void SG_COLS_BOUNDS(T, NTB) k_bwd_cols(const typename CX<T>::t* __res
     constexpr bool pairs = LG > 0;
     if (t == 0) {  // the spectra first (written only by the build)
         sg_mbar_expect_tx(&bar[1], (pairs ? 0 : ab) + 2 * kb + (EDGE ? 2 * gb : 0));
-        sg_bulk_g2s_hint(kr_s, Kr + (size_t)m * KS, kb, &bar[1], drop);
-        sg_bulk_g2s_hint(kp_s, (m == 0 ? Kr + (size_t)half * KS : Kp + (size_t)m * KS), kb, &bar[1], drop);
+        SG_IF_OK(m < half && sg_smem_in(smraw, kr_s, 2 * kb), err, 405) {
+            sg_bulk_g2s_hint(kr_s, Kr + (size_t)m * KS, kb, &bar[1], drop);
+            sg_bulk_g2s_hint(kp_s, (m == 0 ? Kr + (size_t)half * KS : Kp + (size_t)m * KS), kb, &bar[1], drop);
+        }
         if constexpr (EDGE) {  // likewise the edge tables' rows
-            sg_bulk_g2s_hint(g_s, egr + (size_t)m * GS, gb, &bar[1], drop);
-            sg_bulk_g2s_hint(g_s + GS, (m == 0 ? egr + (size_t)half * GS : egp + (size_t)m * GS), gb, &bar[1], drop);
+            SG_IF_OK(m < half && sg_smem_in(smraw, g_s, 2 * gb), err, 406) {
+                sg_bulk_g2s_hint(g_s, egr + (size_t)m * GS, gb, &bar[1], drop);
+                sg_bulk_g2s_hint(g_s + GS, (m == 0 ? egr + (size_t)half * GS : egp + (size_t)m * GS), gb, &bar[1],
+                                 drop);
+            }
         }
     }
     sg_grid_dep_launch();
@@ -1185,11 +1254,17 @@ __global__ void SG_COLS_BOUNDS(T, NTB) k_bwd_cols(const typename CX<T>::t* __res
     if (t == 0) {
         if constexpr (pairs) {
             sg_mbar_expect_tx(&bar[0], 2 * ab);
+            SG_IF_OK(sg_in((long long)2 * m * nu, 2 * nu, (long long)2 * half * nu) && sg_smem_in(smraw, sm, 2 * ab),
+                     err, 401)
             sg_bulk_g2s_hint(sm, A + (size_t)2 * m * nu, 2 * ab, &bar[0], drop);
         } else {
             sg_mbar_expect_tx(&bar[0], ab);
-            sg_bulk_g2s_hint(sm, A + (size_t)m * nu, ab, &bar[0], drop);
-            sg_bulk_g2s_hint(cs, C + (size_t)m * nu, ab, &bar[1], drop);
+            SG_IF_OK(sg_in((long long)m * nu, nu, (long long)half * nu) && sg_smem_in(smraw, sm, ab) &&
+                         sg_smem_in(smraw, cs, ab),
+                     err, 402) {
+                sg_bulk_g2s_hint(sm, A + (size_t)m * nu, ab, &bar[0], drop);
+                sg_bulk_g2s_hint(cs, C + (size_t)m * nu, ab, &bar[1], drop);
+            }
         }
     }
     const Twd<E, V> twd = make_twd<E>(log2L, t, tw);
@@ -1240,7 +1315,7 @@ __global__ void SG_COLS_BOUNDS(T, NTB) k_bwd_cols(const typename CX<T>::t* __res
 #pragma unroll
             for (int v = 0; v < 8; v++)
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) acc[v] += __shfl_xor_sync(0xffffffffu, acc[v], o);
+                for (int o = 16; o > 0; o >>= 1) acc[v] += sg_shfl_xor(acc[v], o);
             if ((t & 31) == 0)
 #pragma unroll
                 for (int v = 0; v < 8; v++) red[t >> 5][v] = acc[v];
@@ -1293,7 +1368,9 @@ __global__ void SG_COLS_BOUNDS(T, NTB) k_bwd_cols(const typename CX<T>::t* __res
             if (t >= NT - 2) y[E / 2 - 1] = cadd(y[E / 2 - 1], update(t - NT + 4));
         }
 #pragma unroll
-        for (int e = 0; e < E / 2; e++) sg_st_hint(B + (size_t)m * nu + t + e * NT, y[e], keep);
+        for (int e = 0; e < E / 2; e++)
+            SG_IF_OK(sg_in((long long)m * nu + t + e * NT, 1, (long long)half * nu), err, 403)
+            sg_st_hint(B + (size_t)m * nu + t + e * NT, y[e], keep);
         return;
     } else {
     V v[E];
@@ -1350,7 +1427,9 @@ __global__ void SG_COLS_BOUNDS(T, NTB) k_bwd_cols(const typename CX<T>::t* __res
             }
         } else {
 #pragma unroll
-            for (int e = 0; e < E / 2; e++) sg_st_hint(B + (size_t)m * nu + t + e * NT, cconj(v[e]), keep);
+            for (int e = 0; e < E / 2; e++)
+                SG_IF_OK(sg_in((long long)m * nu + t + e * NT, 1, (long long)half * nu), err, 404)
+                sg_st_hint(B + (size_t)m * nu + t + e * NT, cconj(v[e]), keep);
         }
     }
     }
@@ -1397,7 +1476,7 @@ __global__ void __launch_bounds__(NTB, (sizeof(T) == 4 && NTB == 256) ? 2 : 1) k
         if (use_map) {
             if (lane == 0) sg_mbar_expect_tx(&bar, (uint32_t)((size_t)half * R * sizeof(V)));
             __syncwarp();
-            stage_load_map(Sb, &mapB, half, rb * R, R, &bar, lane);
+            stage_load_map(Sb, &mapB, half, rb * R, R, &bar, lane, err, smraw);
         } else {
             stage_load(Sb, B, nu, half, rb * R, R);
             sg_cp_async_commit();
@@ -1630,52 +1709,70 @@ __host__ __device__ __forceinline__ size_t rows_unit_smem_bytes()
 
 // DIRECT (forward only): sigma is memory the GPU reaches only by plain loads
 // (pinned host memory), read straight into registers without bulk copies
-template <int LG, bool BWD, bool DIRECT = false>
-__global__ void __launch_bounds__(RowUnit<LG>::GT, RowUnit<LG>::MINB)
-    k_rows_r2c(const float* __restrict__ x0, const float* __restrict__ x1, const float* __restrict__ wrow,
-               float2* __restrict__ out, int nu, const float2* __restrict__ tw, int* err, int wave)
+// One unit of the row R2C pass: rows u R .. u R + R - 1 (the pass kernel
+// below runs one per block; the batched kernel takes units from its work
+// queue).  smraw: the block's dynamic shared memory (RowUnit<LG>::SMEM
+// bytes); bar: an initialised mbarrier whose next phase has parity `phase`;
+// wave > 0: unit u + wave has its input rows brought into L2 now (0: none);
+// PDL: the pass kernel's programmatic-dependent-launch waits.
+// Returns false if the unit's inputs never arrived (the flag is set and the
+// unit's outputs are not written); the barrier's phase has then completed
+// only if its copies landed after all, which `landed` tells.
+template <int LG, bool BWD, bool DIRECT, bool PDL>
+__device__ __forceinline__ bool rows_r2c_unit(const float* __restrict__ x0, const float* __restrict__ x1,
+                                              const float* __restrict__ wrow, float2* __restrict__ out, int nu,
+                                              const float2* __restrict__ tw, int* err, int u, int wave,
+                                              unsigned char* smraw, uint64_t& bar, uint32_t phase,
+                                              unsigned long long wlim, bool* landed = nullptr)
 {
     typedef RowUnit<LG> RU;
     constexpr int N = RU::N, NT = RU::NT, TPG = RU::TPG;
     constexpr int RPT = BWD ? 2 : 4;  // rows per transform
     constexpr int R = RPT * TPG;      // rows per block
-    const unsigned long long wlim = sg_wait_budget(err);  // read once, early
-    extern __shared__ __align__(128) unsigned char smraw[];
-    __shared__ __align__(8) uint64_t bar;
     unsigned char* const area = align128(smraw);
     const int tr = threadIdx.x / NT, t = threadIdx.x % NT;  // transform, thread in it
-    const int u = blockIdx.x;                                // the unit: rows u R .. u R + R - 1
     const int i0 = u * R + tr * RPT;
     const Twd<16, float2> twd = make_twd<16>(LG, t, tw);
-    if (threadIdx.x == 0) sg_mbar_init(&bar, 1);
-    __syncthreads();
     // the weights: forward w_i0..i0+3, adjoint (w_i0, w_i0, w_i1, w_i1); loaded while the rows land
-    float wt[4];
+    float wt[4] = {0.f, 0.f, 0.f, 0.f};
+    SG_IF_OK(i0 + (BWD ? 2 : 4) <= nu, err, 101) {
 #pragma unroll
-    for (int r = 0; r < 4; r++) wt[r] = __ldg(&wrow[i0 + (BWD ? r / 2 : r)]);
-    sg_grid_dep_launch();
-    sg_grid_dep_wait();  // the inputs may come from the previous kernel on the stream
+        for (int r = 0; r < 4; r++) wt[r] = __ldg(&wrow[i0 + (BWD ? r / 2 : r)]);
+    }
+    if constexpr (PDL) {
+        sg_grid_dep_launch();
+        sg_grid_dep_wait();  // the inputs may come from the previous kernel on the stream
+    }
     if (!DIRECT && threadIdx.x == 0) {
         // forward: rows u R .. u R + R - 1 of sigma; adjoint: the same rows of gF_r, then of gF_phi
         const uint64_t pol = sg_policy_evict_first();
         const uint32_t bytes = (uint32_t)R * N * 4;
         float* dst = reinterpret_cast<float*>(area);
         sg_mbar_expect_tx(&bar, BWD ? 2 * bytes : bytes);
-        sg_bulk_g2s_hint(dst, x0 + (size_t)u * R * N, bytes, &bar, pol);
-        if constexpr (BWD) sg_bulk_g2s_hint(dst + (size_t)R * N, x1 + (size_t)u * R * N, bytes, &bar, pol);
-        // the unit one wave later (wave = blocks resident at once) has its
-        // rows brought into L2 now, so that its block does not wait on DRAM
+        SG_IF_OK(sg_in((long long)u * R, R, nu) && sg_smem_in(smraw, dst, (BWD ? 2 : 1) * bytes), err, 102) {
+            sg_bulk_g2s_hint(dst, x0 + (size_t)u * R * N, bytes, &bar, pol);
+            if constexpr (BWD) sg_bulk_g2s_hint(dst + (size_t)R * N, x1 + (size_t)u * R * N, bytes, &bar, pol);
+        }
+        // a later unit (one wave later in the pass kernel) has its rows
+        // brought into L2 now, so that its block does not wait on DRAM
         const int un = u + wave;
-        if (un * R < nu) {
+        if (wave > 0 && un * R < nu) {
             sg_prefetch_l2(x0 + (size_t)un * R * N, bytes);
             if constexpr (BWD) sg_prefetch_l2(x1 + (size_t)un * R * N, bytes);
         }
     }
-    if (!DIRECT && __syncthreads_or(!sg_mbar_wait_bounded(&bar, 0, err, 1, wlim))) return;  // inputs never arrived
+    if constexpr (!DIRECT) {
+        if (__syncthreads_or(!sg_mbar_wait_bounded(&bar, phase, err, 1, wlim, landed))) return false;  // inputs never arrived
+    }
     // the four real rows (p, q, r, s) of this transform: z1 = p + i q, z2 = r + i s
     const float *rp, *rq, *rr, *rs;
     if constexpr (DIRECT) {
-        rp = x0 + (size_t)i0 * N;
+#ifdef SG_DEBUG
+        const int ir = (i0 + 4 <= nu || sg_dbg_fail(err, 104)) ? i0 : 0;  // a failed check reads row 0 instead
+#else
+        const int ir = i0;
+#endif
+        rp = x0 + (size_t)ir * N;
         rq = rp + N;
         rr = rp + 2 * N;
         rs = rp + 3 * N;
@@ -1712,40 +1809,57 @@ __global__ void __launch_bounds__(RowUnit<LG>::GT, RowUnit<LG>::MINB)
     for (int e = 0; e < 8; e++) {
         const size_t mi = (size_t)(t + e * NT) * nu + i0;
         float* q = reinterpret_cast<float*>(out) + (BWD ? 4 : 2) * mi;
+        SG_IF_OK(sg_in((long long)mi, BWD ? 2 : 4, (long long)(N / 2) * nu), err, 103)
         sg_st256_hint(q, make_float4(f2_lo(xa[e].x), f2_lo(xa[e].y), f2_lo(xb[e].x), f2_lo(xb[e].y)),
                       make_float4(f2_hi(xa[e].x), f2_hi(xa[e].y), f2_hi(xb[e].x), f2_hi(xb[e].y)), keep);
     }
+    return true;
 }
 
-// map: 2-D tensor map over the input (forward: the pair layout, two 8-byte
-// units per row; adjoint: the single layout, one unit per row) with boxes
-// of 4 units x min(N/2, 256) modes and the 32-byte swizzle
-template <int LG, bool BWD>
+template <int LG, bool BWD, bool DIRECT = false>
 __global__ void __launch_bounds__(RowUnit<LG>::GT, RowUnit<LG>::MINB)
-    k_rows_c2r(const __grid_constant__ CUtensorMap map, const float* __restrict__ wrow, float* __restrict__ y0,
-               float* __restrict__ y1, int nu, const float2* __restrict__ tw, int* err)
+    k_rows_r2c(const float* __restrict__ x0, const float* __restrict__ x1, const float* __restrict__ wrow,
+               float2* __restrict__ out, int nu, const float2* __restrict__ tw, int* err, int wave)
+{
+    const unsigned long long wlim = sg_wait_budget(err);  // read once, early
+    extern __shared__ __align__(128) unsigned char smraw[];
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) sg_mbar_init(&bar, 1);
+    __syncthreads();
+    // the unit one wave later (wave = blocks resident at once) is prefetched
+    rows_r2c_unit<LG, BWD, DIRECT, true>(x0, x1, wrow, out, nu, tw, err, blockIdx.x, wave, smraw, bar, 0, wlim);
+}
+
+// One unit of the row C2R pass (rows u R .. u R + R - 1), shared like
+// rows_r2c_unit; map: the tensor map in kernel-parameter or global memory.
+template <int LG, bool BWD, bool PDL>
+__device__ __forceinline__ bool rows_c2r_unit(const CUtensorMap* map, const float* __restrict__ wrow,
+                                              float* __restrict__ y0, float* __restrict__ y1, int nu,
+                                              const float2* __restrict__ tw, int* err, int u, unsigned char* smraw,
+                                              uint64_t& bar, uint32_t phase, unsigned long long wlim,
+                                              bool* landed = nullptr)
 {
     typedef RowUnit<LG> RU;
     constexpr int N = RU::N, NT = RU::NT, TPG = RU::TPG, half = N / 2;
     constexpr int RPT = BWD ? 4 : 2;  // rows per transform
     constexpr int R = RPT * TPG;      // rows per block
     constexpr int MB = half < 256 ? half : 256, NBOX = half / MB;
-    const unsigned long long wlim = sg_wait_budget(err);  // read once, early
-    extern __shared__ __align__(128) unsigned char smraw[];
-    __shared__ __align__(8) uint64_t bar;
     unsigned char* const area = align_smem<1024>(smraw);  // the swizzle repeats every 256 bytes
     const int tr = threadIdx.x / NT, t = threadIdx.x % NT;
-    const int u = blockIdx.x;
     const int i0 = u * R + tr * RPT;
     const Twd<16, float2> twd = make_twd<16>(LG, t, tw);
-    if (threadIdx.x == 0) sg_mbar_init(&bar, 1);
-    __syncthreads();
     // the output rows' weights: forward (w_i0, w_i0, w_i0+1, w_i0+1), adjoint w_i0..i0+3
-    float wt[4];
+    float wt[4] = {0.f, 0.f, 0.f, 0.f};
+    const bool rows_ok = i0 + (BWD ? 4 : 2) <= nu;
+    (void)rows_ok;  // read by the checked build only
+    SG_IF_OK(rows_ok, err, 201) {
 #pragma unroll
-    for (int r = 0; r < 4; r++) wt[r] = __ldg(&wrow[i0 + (BWD ? r : r / 2)]);
-    sg_grid_dep_launch();
-    sg_grid_dep_wait();  // the spectra are the previous pass's results
+        for (int r = 0; r < 4; r++) wt[r] = __ldg(&wrow[i0 + (BWD ? r : r / 2)]);
+    }
+    if constexpr (PDL) {
+        sg_grid_dep_launch();
+        sg_grid_dep_wait();  // the spectra are the previous pass's results
+    }
     if (threadIdx.x < 32) {
         // transform j's rows land at j N x 16 bytes, mode n of them at 32 n
         const int lane = threadIdx.x;
@@ -1754,11 +1868,14 @@ __global__ void __launch_bounds__(RowUnit<LG>::GT, RowUnit<LG>::MINB)
         const uint64_t drop = sg_policy_evict_first();  // the spectra are consumed here
         for (int j = lane; j < TPG * NBOX; j += 32) {
             const int s = j / NBOX, b = j % NBOX;
-            sg_tma_load_2d(area + (size_t)s * N * 16 + (size_t)b * MB * 32, &map, (BWD ? 1 : 2) * (u * R + s * RPT),
-                           b * MB, &bar, drop);
+            const int x = (BWD ? 1 : 2) * (u * R + s * RPT);  // 8-byte units: x even keeps the 16-byte rule
+            SG_IF_OK((x & 1) == 0 && sg_in(x, 4, (BWD ? 1 : 2) * (long long)nu) && sg_in(b * MB, MB, half) &&
+                         sg_smem_in(smraw, area + (size_t)s * N * 16 + (size_t)b * MB * 32, MB * 32),
+                     err, 202)
+            sg_tma_load_2d(area + (size_t)s * N * 16 + (size_t)b * MB * 32, map, x, b * MB, &bar, drop);
         }
     }
-    if (__syncthreads_or(!sg_mbar_wait_bounded(&bar, 0, err, 1, wlim))) return;  // inputs never arrived
+    if (__syncthreads_or(!sg_mbar_wait_bounded(&bar, phase, err, 1, wlim, landed))) return false;  // inputs never arrived
     const float4* const S4 = reinterpret_cast<const float4*>(area) + (size_t)tr * N;  // this transform's modes
     // Z of both lanes at frequency n.  Each mode holds two 16-byte units u0,
     // u1 (forward: {B, C} of rows i0, i0+1; adjoint: {S_i0, S_i0+1}, {S_i0+2,
@@ -1796,14 +1913,33 @@ __global__ void __launch_bounds__(RowUnit<LG>::GT, RowUnit<LG>::MINB)
         o[2] = y0 + (size_t)(i0 + 1) * N;
         o[3] = y1 + (size_t)(i0 + 1) * N;
     }
+    SG_IF_OK(rows_ok, err, 203) {
 #pragma unroll
-    for (int e = 0; e < 16; e++) {
-        const int n = t + e * NT;
-        o[0][n] = f2_lo(w[e].x) * wt[0];
-        o[1][n] = f2_lo(w[e].y) * wt[1];
-        o[2][n] = f2_hi(w[e].x) * wt[2];
-        o[3][n] = f2_hi(w[e].y) * wt[3];
+        for (int e = 0; e < 16; e++) {
+            const int n = t + e * NT;
+            o[0][n] = f2_lo(w[e].x) * wt[0];
+            o[1][n] = f2_lo(w[e].y) * wt[1];
+            o[2][n] = f2_hi(w[e].x) * wt[2];
+            o[3][n] = f2_hi(w[e].y) * wt[3];
+        }
     }
+    return true;
+}
+
+// map: 2-D tensor map over the input (forward: the pair layout, two 8-byte
+// units per row; adjoint: the single layout, one unit per row) with boxes
+// of 4 units x min(N/2, 256) modes and the 32-byte swizzle
+template <int LG, bool BWD>
+__global__ void __launch_bounds__(RowUnit<LG>::GT, RowUnit<LG>::MINB)
+    k_rows_c2r(const __grid_constant__ CUtensorMap map, const float* __restrict__ wrow, float* __restrict__ y0,
+               float* __restrict__ y1, int nu, const float2* __restrict__ tw, int* err)
+{
+    const unsigned long long wlim = sg_wait_budget(err);  // read once, early
+    extern __shared__ __align__(128) unsigned char smraw[];
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) sg_mbar_init(&bar, 1);
+    __syncthreads();
+    rows_c2r_unit<LG, BWD, true>(&map, wrow, y0, y1, nu, tw, err, blockIdx.x, smraw, bar, 0, wlim);
 }
 
 // ===========================================================================
@@ -2021,6 +2157,7 @@ static int persistent_grid(K kernel, int threads, size_t smem, int nblk, int sms
 // threads a row-pass block should have at least (several slots per block)
 static int row_min_threads(size_t elem) { return elem == 4 ? 512 : 64; }
 
+#ifndef SG_FFTCONV_DF  // the tensor maps are made once, in this translation unit
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -2088,6 +2225,7 @@ bool make_pair_maps(int nu, int nphi, void* wa, void* wb, CUtensorMap out[2])
     }
     return true;
 }
+#endif
 
 // the map of buffer b for row blocks of R rows, or null
 static const CUtensorMap* row_map(const PlanView& p, int R, int b, int nphi)
@@ -2397,6 +2535,7 @@ cudaError_t launch_spectra(const PlanView& p, const double* nsr, const double* n
     return cudaGetLastError();
 }
 
+#ifndef SG_FFTCONV_DF  // fftconv_df.cu instantiates the compensated plans' passes
 template cudaError_t launch_forward<float>(const PlanView&, const float*, float*, float*, cudaStream_t, cudaEvent_t*,
                                            bool);
 template cudaError_t launch_forward<double>(const PlanView&, const double*, double*, double*, cudaStream_t,
@@ -2409,6 +2548,7 @@ template cudaError_t launch_spectra<float2>(const PlanView&, const double*, cons
                                             float2*, cudaStream_t);
 template cudaError_t launch_spectra<double2>(const PlanView&, const double*, const double*, double2*, double2*,
                                              double2*, cudaStream_t);
+#endif
 #endif  // SG_FFTCONV_KERNELS_ONLY
 
 }  // namespace sg

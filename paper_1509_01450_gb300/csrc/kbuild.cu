@@ -698,6 +698,8 @@ template cudaError_t launch_edge_spectra<float>(int, int, double, double, const 
                                                 cudaStream_t);
 template cudaError_t launch_edge_spectra<double>(int, int, double, double, const double*, const void*, double*,
                                                  double*, cudaStream_t);
+template cudaError_t launch_edge_spectra<dfloat>(int, int, double, double, const double*, const void*, dfloat*,
+                                                  dfloat*, cudaStream_t);
 
 cudaError_t launch_cells_tpz(int nu, int nphi, double du, int ntpz, double rtol, double* cells, int* flag,
                              cudaStream_t st)
@@ -840,6 +842,8 @@ template cudaError_t launch_wedge_tables<float>(int, int, double, double, double
                                                 int*, cudaStream_t);
 template cudaError_t launch_wedge_tables<double>(int, int, double, double, double, int, double*, const void*,
                                                  double*, int*, cudaStream_t);
+template cudaError_t launch_wedge_tables<dfloat>(int, int, double, double, double, int, double*, const void*,
+                                                 dfloat*, int*, cudaStream_t);
 
 // ln(a + sqrt(a^2 + b^2)) for b != 0; for a < 0 as ln(b^2) - ln(R - a),
 // which does not cancel

@@ -62,7 +62,8 @@ static sg_status scratch_address(void** out)
 
 // one half-spectrum buffer of the plan, and whether three fit the scratch
 static size_t half_bytes(const sg_plan* p) { return (size_t)p->nu * (p->nphi / 2) * 2 * p->elem; }
-static bool fits(const sg_plan* p) { return 3 * half_bytes(p) <= SG_NOALLOC_BYTES; }
+// the compensated plans convert their fields through working buffers of their own: not served here
+static bool fits(const sg_plan* p) { return p->dtype != SG_F32X2 && 3 * half_bytes(p) <= SG_NOALLOC_BYTES; }
 
 // the forward passes over the scratch (arguments checked by the caller)
 static sg_status noalloc_forward(sg_plan* p, const void* sigma, void* F_r, void* F_phi, cudaStream_t stream)
@@ -105,7 +106,7 @@ sg_status noalloc_prepare(sg_plan* p, cudaStream_t stream)
     if (p->wedge || !fits(p)) return SG_OK;
     const size_t field = (size_t)p->nu * p->nphi * p->elem;
     unsigned char* buf = nullptr;
-    if (cudaMalloc(&buf, 3 * field) != cudaSuccess) {
+    if (sg_malloc((void**)&buf, 3 * field) != cudaSuccess) {
         cudaGetLastError();
         return SG_ERR_ALLOC;
     }
@@ -115,7 +116,7 @@ sg_status noalloc_prepare(sg_plan* p, cudaStream_t stream)
     else
         st = noalloc_forward(p, buf, buf + field, buf + 2 * field, stream);
     if (cudaStreamSynchronize(stream) != cudaSuccess && st == SG_OK) st = SG_ERR_CUDA;
-    cudaFree(buf);
+    sg_free(buf);
     return st;
 }
 }  // namespace sg

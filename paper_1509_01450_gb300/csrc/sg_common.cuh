@@ -19,6 +19,8 @@
 
 #include <type_traits>
 
+#include "sg_df.cuh"
+
 #define SG_NMAX 16384  // longest transform length; twiddle table length
 
 template <typename T>
@@ -31,17 +33,56 @@ template <>
 struct CX<double> {
     typedef double2 t;
 };
+template <>
+struct CX<dfloat> {  // the compensated plans' double-float values (sg_df.cuh)
+    typedef dfloat2 t;
+};
+
+// read-only loads; the 16-byte double-float pairs have their own overloads
+template <typename V>
+__device__ __forceinline__ V sg_ldg(const V* p)
+{
+    return __ldg(p);
+}
+// warp sums (the double-float values shuffle their two halves)
+__device__ __forceinline__ float sg_shfl_xor(float v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ double sg_shfl_xor(double v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ dfloat sg_shfl_xor(dfloat v, int o) { return df_shfl_xor(v, o); }
+
+// Products and multiply-adds with their rounding stated: one rounding per
+// product (sg_mul) or per fused multiply-add (sg_fma), whatever code they are
+// inlined into, so that every kernel that runs a transform rounds it the
+// same way (the library is built without implicit contraction of a * b + c).
+template <typename T>
+__device__ __forceinline__ T sg_mul(T a, T b) { return a * b; }
+template <typename T>
+__device__ __forceinline__ T sg_fma(T a, T b, T c) { return a * b + c; }  // double-float: its own operators
+template <>
+__device__ __forceinline__ float sg_mul<float>(float a, float b) { return __fmul_rn(a, b); }
+template <>
+__device__ __forceinline__ float sg_fma<float>(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+template <>
+__device__ __forceinline__ double sg_mul<double>(double a, double b) { return __dmul_rn(a, b); }
+template <>
+__device__ __forceinline__ double sg_fma<double>(double a, double b, double c) { return __fma_rn(a, b, c); }
 
 template <typename V>
 __device__ __forceinline__ V cadd(V a, V b) { return V{a.x + b.x, a.y + b.y}; }
 template <typename V>
 __device__ __forceinline__ V csub(V a, V b) { return V{a.x - b.x, a.y - b.y}; }
 template <typename V>
-__device__ __forceinline__ V cmul(V a, V b) { return V{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
+__device__ __forceinline__ V cmul(V a, V b)
+{
+    return V{sg_fma(a.x, b.x, -sg_mul(a.y, b.y)), sg_fma(a.x, b.y, sg_mul(a.y, b.x))};
+}
 template <typename V>
 __device__ __forceinline__ V cconj(V a) { return V{a.x, -a.y}; }
 template <typename V, typename T>
-__device__ __forceinline__ V cscale(V a, T s) { return V{a.x * s, a.y * s}; }
+__device__ __forceinline__ V cscale(V a, T s)
+{
+    typedef decltype(a.x) R;
+    return V{sg_mul(a.x, (R)s), sg_mul(a.y, (R)s)};
+}
 // multiply by i: (x + iy) i = -y + ix
 template <typename V>
 __device__ __forceinline__ V cmuli(V a) { return V{-a.y, a.x}; }
@@ -53,7 +94,7 @@ __host__ __device__ __forceinline__ int sg_padded(int n) { return n + (n >> 4) +
 template <int DIR, typename V>
 __device__ __forceinline__ V sg_tw(const V* __restrict__ tw, int idx)
 {
-    V w = __ldg(&tw[idx]);
+    V w = sg_ldg(&tw[idx]);
     if (DIR > 0) w.y = -w.y;
     return w;
 }
@@ -114,8 +155,8 @@ __device__ __forceinline__ V sg_mulw8(V a)
 {
     typedef decltype(a.x) T;
     const T r = (T)0.70710678118654752440084436210484904;
-    if (K == 1) return V{r * (a.x - DIR * a.y), r * (a.y + DIR * a.x)};
-    return V{r * (-a.x - DIR * a.y), r * (-a.y + DIR * a.x)};  // K == 3
+    if (K == 1) return V{sg_mul(r, a.x - DIR * a.y), sg_mul(r, a.y + DIR * a.x)};
+    return V{sg_mul(r, -a.x - DIR * a.y), sg_mul(r, -a.y + DIR * a.x)};  // K == 3
 }
 
 template <int DIR, typename V>
@@ -162,7 +203,7 @@ __device__ __forceinline__ V sg_mulw16(V a)
         default: c = 1; s = 0; break;
     }
     s = DIR * s;
-    return V{a.x * c - a.y * s, a.x * s + a.y * c};
+    return V{sg_fma(a.x, c, -sg_mul(a.y, s)), sg_fma(a.x, s, sg_mul(a.y, c))};
 }
 
 template <int DIR, typename V>
@@ -403,6 +444,48 @@ __device__ __forceinline__ uint64_t sg_globaltimer_ns()
     return t;
 }
 
+// ---------------------------------------------------------------------------
+// Checked builds (-DSG_DEBUG): before each global copy, store or tensor-copy
+// coordinate of the pass kernels, SG_IF_OK tests that the access stays
+// inside its buffer (and, for shared-memory ends, inside the block's dynamic
+// shared memory, 16-byte aligned).  A failed test sets bit SG_FLAG_BOUNDS of
+// the plan's flag word, records the site's number in the word after it (the
+// first failure wins) and skips the access; sg_plan_check then reports
+// SG_ERR_BOUNDS.  A skipped copy leaves its barrier short, so the pass's
+// bounded wait gives up as well.  In ordinary builds SG_IF_OK(c, err, site)
+// expands to nothing and the guarded statement always runs.
+// ---------------------------------------------------------------------------
+#define SG_FLAG_BOUNDS 2
+__host__ __device__ __forceinline__ bool sg_in(long long off, long long len, long long extent)
+{
+    return off >= 0 && len >= 0 && off + len <= extent;
+}
+__device__ __forceinline__ uint32_t sg_dyn_smem_bytes()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(r));
+    return r;
+}
+// [dst, dst + bytes) inside the dynamic shared memory that starts at base, 16-byte aligned
+__device__ __forceinline__ bool sg_smem_in(const void* base, const void* dst, uint32_t bytes)
+{
+    const long long off = (long long)sg_smem_u32(dst) - (long long)sg_smem_u32(base);
+    return (sg_smem_u32(dst) & 15) == 0 && sg_in(off, bytes, sg_dyn_smem_bytes());
+}
+#ifdef SG_DEBUG
+static __device__ __noinline__ bool sg_dbg_fail(int* err, int site)
+{
+    if (err) {
+        atomicOr(err, SG_FLAG_BOUNDS);
+        atomicCAS(err + 1, 0, site);
+    }
+    return false;
+}
+#define SG_IF_OK(cond, err, site) if ((cond) || sg_dbg_fail((err), (site)))
+#else
+#define SG_IF_OK(cond, err, site)
+#endif
+
 // Prefetch of a contiguous range into L2 (no shared memory, no completion):
 // address and size multiples of 16 bytes
 __device__ __forceinline__ void sg_prefetch_l2(const void* src, uint32_t bytes)
@@ -491,6 +574,14 @@ __device__ __forceinline__ void sg_st_hint(float4* a, float4 v, uint64_t pol)
                  "f"(v.z), "f"(v.w), "l"(pol)
                  : "memory");
 }
+__device__ __forceinline__ void sg_st_hint(dfloat2* a, dfloat2 v, uint64_t pol)
+{
+    sg_st_hint(reinterpret_cast<float4*>(a), make_float4(v.x.hi, v.x.lo, v.y.hi, v.y.lo), pol);
+}
+__device__ __forceinline__ void sg_st_hint(dfloat* a, dfloat v, uint64_t pol)
+{
+    sg_st_hint(reinterpret_cast<float2*>(a), make_float2(v.hi, v.lo), pol);
+}
 // 32 bytes (a whole L2 sector) from one thread: a, then b; p 32-byte aligned
 __device__ __forceinline__ void sg_st256_hint(float* p, float4 a, float4 b, uint64_t pol)
 {
@@ -530,6 +621,16 @@ __device__ __forceinline__ double sg_ld_hint(const double* a, uint64_t pol)
     double r;
     asm("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(r) : "l"(a), "l"(pol));
     return r;
+}
+__device__ __forceinline__ dfloat2 sg_ld_hint(const dfloat2* a, uint64_t pol)
+{
+    const float4 v = sg_ld_hint(reinterpret_cast<const float4*>(a), pol);
+    return dfloat2{dfloat(v.x, v.y), dfloat(v.z, v.w)};
+}
+__device__ __forceinline__ dfloat sg_ld_hint(const dfloat* a, uint64_t pol)
+{
+    const float2 v = sg_ld_hint(reinterpret_cast<const float2*>(a), pol);
+    return dfloat(v.x, v.y);
 }
 
 // Asynchronous global -> shared copies of 16 (or 8) bytes (cp.async), with
@@ -574,12 +675,18 @@ __device__ __forceinline__ unsigned long long sg_wait_budget(const int* err)
 {
     return err ? __ldg(reinterpret_cast<const unsigned long long*>(err + 2)) : SG_WAIT_NS;
 }
+// landed (if given): whether the phase completed after all, during the one
+// more second that a wait which gave up allows the copies still in flight
 __device__ __forceinline__ bool sg_mbar_wait_bounded(uint64_t* bar, uint32_t phase, int* err, int code,
-                                                     unsigned long long limit)
+                                                     unsigned long long limit, bool* landed = nullptr)
 {
-    if (sg_mbar_wait_once(bar, phase, limit)) return true;
+    if (sg_mbar_wait_once(bar, phase, limit)) {
+        if (landed) *landed = true;
+        return true;
+    }
     if (err) atomicOr(err, code);
-    sg_mbar_wait_once(bar, phase, SG_WAIT_NS);
+    const bool late = sg_mbar_wait_once(bar, phase, SG_WAIT_NS);
+    if (landed) *landed = late;
     return false;
 }
 
@@ -698,7 +805,7 @@ __device__ __forceinline__ SgTwid<V> sg_fft_twiddles(int log2N, int t, const V* 
 #pragma unroll
     for (int p = 0; p < 3; p++) {
         r.w[p] = V{1, 0};
-        if (p < n16) r.w[p] = __ldg(&tw[(t & (Ns - 1)) * (SG_NMAX / (Ns * 16))]);
+        if (p < n16) r.w[p] = sg_ldg(&tw[(t & (Ns - 1)) * (SG_NMAX / (Ns * 16))]);
         Ns *= 16;
     }
     return r;

@@ -40,6 +40,11 @@ struct sg_plan {
     double* cells;   // 6 x (2 nu + 1) x nphi raw cell kernels (kept after build)
     double* keff;    // 2 x (2 nu - 1) x nphi folded kernels K^eff
     // host-API staging (allocated on first sg_forces_host)
+    // SG_F32X2: the double-float working fields of sigma, F_r, F_phi (or of
+    // the adjoint's gF_r, gF_phi, gsigma) and of the wedge row's density and
+    // gradient (2 N_phi); the API's FP64 fields are converted into and out of them
+    void* xf;
+    void* xw;
     void* h_sigma;
     void* h_fr;
     void* h_fp;
@@ -158,6 +163,19 @@ void make_row_maps(int nu, int nphi, size_t elem, void* const bufs[3], SgRowMaps
 bool make_pair_maps(int nu, int nphi, void* wa, void* wb, CUtensorMap out[2]);
 // noalloc.cu: the allocation-free entry point's set-up at plan build and load
 sg_status noalloc_prepare(sg_plan* p, cudaStream_t stream);
+// fftconv_df.cu: FP64 fields into and out of double-float working fields
+cudaError_t launch_to_df(const double* in, dfloat* out, size_t n, int sms, cudaStream_t st);
+cudaError_t launch_from_df(const dfloat* in, double* out, size_t n, int sms, cudaStream_t st);
+// batch.cu: sg_forces_batched's persistent path and its preparation
+sg_status batch_forward(const sg_batch_item* items, int n, cudaStream_t st);
+sg_status batch_prepare(const sg_batch_item* items, int n, cudaStream_t st);
+sg_status batch_tune(const sg_batch_item* items, int n, const char* path, cudaStream_t st, float ms_out[2]);
+void batch_forget_plan(const sg_plan* p);
+bool batch_eligible(const sg_plan* p);
+// every device allocation of the library, through the sg_test_fail_alloc
+// hook, and its release (sg_test_live_allocations counts the difference)
+cudaError_t sg_malloc(void** ptr, size_t bytes);
+void sg_free(void* ptr);
 template <typename VO>
 cudaError_t launch_spectra(const PlanView& p, const double* nsr, const double* nsp, double2* W, VO* Kr, VO* Kp,
                            cudaStream_t st);

@@ -55,7 +55,7 @@ template <typename T>
 __device__ __forceinline__ T blk_sum(T v, T* red)
 {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    for (int o = 16; o > 0; o >>= 1) v += sg_shfl_xor(v, o);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     __syncthreads();
     if (lane == 0) red[wid] = v;
@@ -231,6 +231,7 @@ cudaError_t launch_wedge_dft(const PlanView& p, cudaStream_t st)
 }
 template cudaError_t launch_wedge_dft<float>(const PlanView&, cudaStream_t);
 template cudaError_t launch_wedge_dft<double>(const PlanView&, cudaStream_t);
+template cudaError_t launch_wedge_dft<dfloat>(const PlanView&, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_wedge(const PlanView& p, bool adjoint, cudaStream_t st)
@@ -254,5 +255,6 @@ cudaError_t launch_wedge(const PlanView& p, bool adjoint, cudaStream_t st)
 }
 template cudaError_t launch_wedge<float>(const PlanView&, bool, cudaStream_t);
 template cudaError_t launch_wedge<double>(const PlanView&, bool, cudaStream_t);
+template cudaError_t launch_wedge<dfloat>(const PlanView&, bool, cudaStream_t);
 
 }  // namespace sg

@@ -13,16 +13,27 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libsgdisk.so")
+# SG_LIBRARY_VARIANT=checked loads the index-checked build (libsgdisk_checked.so,
+# python -m paper_1509_01450_gb300.build --checked) instead of the ordinary one
+_VARIANT = os.environ.get("SG_LIBRARY_VARIANT", "")
+if _VARIANT not in ("", "checked"):
+    raise RuntimeError(f"SG_LIBRARY_VARIANT={_VARIANT!r}: expected 'checked' or nothing")
+LIB_PATH = os.path.join(_HERE, "libsgdisk_checked.so" if _VARIANT == "checked" else "libsgdisk.so")
 
-SG_OK, SG_ERR_ARG, SG_ERR_ALLOC, SG_ERR_CUDA, SG_ERR_UNSUPPORTED, SG_ERR_NOT_BUILT, SG_ERR_TIMEOUT, SG_ERR_IO = range(8)
-SG_F32, SG_F64 = 0, 1
+(SG_OK, SG_ERR_ARG, SG_ERR_ALLOC, SG_ERR_CUDA, SG_ERR_UNSUPPORTED, SG_ERR_NOT_BUILT, SG_ERR_TIMEOUT, SG_ERR_IO,
+ SG_ERR_BOUNDS) = range(9)
+SG_F32, SG_F64, SG_F32X2 = 0, 1, 2
+# plan precisions by name: FP32, FP64, and the compensated FP32 plans
+# (double-float passes on the FP32 pipes; fields FP64 like SG_F64)
+PRECISIONS = {"float32": SG_F32, "f32": SG_F32, "torch.float32": SG_F32, "float64": SG_F64, "f64": SG_F64,
+              "torch.float64": SG_F64, "float32x2": SG_F32X2, "f32x2": SG_F32X2, "compensated": SG_F32X2}
 
 EXPORTS = ("sg_plan_create", "sg_kernels_build", "sg_forces", "sg_forces_backward", "sg_forces_host", "sg_forces_timed",
            "sg_forces_backward_timed",
-           "sg_forces_batched", "sg_batch_reserve", "sg_plan_destroy", "sg_status_string", "sg_plan_info",
+           "sg_forces_batched", "sg_batch_prepare", "sg_batch_tune", "sg_plan_destroy", "sg_status_string", "sg_plan_info",
            "sg_plan_kernels", "sg_plan_cells", "sg_plan_device_bytes", "sg_plan_build_report", "sg_forces_noalloc", "sg_plan_check",
-           "sg_plan_set_wait_limit", "sg_plan_save", "sg_plan_load", "sg_forces_wedge", "sg_forces_wedge_backward")
+           "sg_plan_set_wait_limit", "sg_plan_save", "sg_plan_load", "sg_forces_wedge", "sg_forces_wedge_backward",
+           "sg_checked_build", "sg_last_bounds_site", "sg_test_fail_alloc", "sg_test_live_allocations")
 
 
 class SgError(RuntimeError):
@@ -75,7 +86,8 @@ def lib():
         L.sg_forces_wedge.argtypes = [vp, vp, vp, vp, vp, vp]
         L.sg_forces_wedge_backward.argtypes = [vp, vp, vp, vp, vp, vp]
         L.sg_forces_batched.argtypes = [ctypes.POINTER(BatchItem), ip, vp]
-        L.sg_batch_reserve.argtypes = [ip]
+        L.sg_batch_prepare.argtypes = [ctypes.POINTER(BatchItem), ip, vp]
+        L.sg_batch_tune.argtypes = [ctypes.POINTER(BatchItem), ip, ctypes.c_char_p, vp, ctypes.POINTER(ctypes.c_float)]
         L.sg_plan_destroy.argtypes = [vp]
         L.sg_status_string.argtypes = [ip]
         L.sg_status_string.restype = ctypes.c_char_p
@@ -87,6 +99,10 @@ def lib():
         L.sg_plan_set_wait_limit.argtypes = [vp, dp]
         L.sg_plan_save.argtypes = [vp, ctypes.c_char_p, vp]
         L.sg_plan_load.argtypes = [ctypes.POINTER(vp), ctypes.c_char_p, vp]
+        L.sg_checked_build.argtypes = []
+        L.sg_last_bounds_site.argtypes = []
+        L.sg_test_fail_alloc.argtypes = [ip]
+        L.sg_test_live_allocations.argtypes = []
         L.sg_plan_device_bytes.argtypes = [vp]
         L.sg_plan_device_bytes.restype = ctypes.c_size_t
         for name in EXPORTS:
@@ -125,11 +141,14 @@ class Plan:
     def __init__(self, nu: int, nphi: int, u_min: float, du: float, G: float = 1.0, dtype="float32"):
         import torch
 
-        self.dtype = torch.float32 if str(dtype) in ("float32", "torch.float32", "f32") else torch.float64
+        if str(dtype) not in PRECISIONS:
+            raise ValueError(f"dtype {dtype!r}: expected one of {sorted(PRECISIONS)}")
+        self.code = PRECISIONS[str(dtype)]
+        # the fields' torch dtype (FP64 for the compensated plans too)
+        self.dtype = torch.float32 if self.code == SG_F32 else torch.float64
         self.nu, self.nphi, self.u_min, self.du, self.G = int(nu), int(nphi), float(u_min), float(du), float(G)
         h = ctypes.c_void_p()
-        code = SG_F32 if self.dtype == torch.float32 else SG_F64
-        _check(lib().sg_plan_create(ctypes.byref(h), self.nu, self.nphi, self.u_min, self.du, self.G, code),
+        _check(lib().sg_plan_create(ctypes.byref(h), self.nu, self.nphi, self.u_min, self.du, self.G, self.code),
                "sg_plan_create")
         self.handle = h
 
@@ -273,13 +292,15 @@ class Plan:
         d = (ctypes.c_int * 4)()
         _check(lib().sg_plan_info(h, d), "sg_plan_info")
         self.nu, self.nphi = int(d[0]), int(d[1])
+        self.code = int(d[2])
         self.dtype = torch.float32 if d[2] == SG_F32 else torch.float64
         self.u_min = self.du = self.G = None  # kept in the file and the plan, not needed here
         return self
 
     def check(self, stream=None):
         """Raise if a pass of the enqueued work reported a device-side
-        timeout (synchronises the stream)."""
+        timeout, or (checked builds) a failed index check (synchronises the
+        stream)."""
         _check(lib().sg_plan_check(self.handle, _stream(stream)), "sg_plan_check")
 
     def build_report(self):
@@ -320,14 +341,32 @@ class Plan:
             pass
 
 
-def forces_batched(items, stream=None):
-    """items: list of (plan, sigma, F_r, F_phi) with device tensors."""
+def _batch_array(items):
     arr = (BatchItem * len(items))()
     for n, (p, s, fr, fp) in enumerate(items):
         for t in (s, fr, fp):
             p._check_field(t)
         arr[n] = BatchItem(p.handle.value, s.data_ptr(), fr.data_ptr(), fp.data_ptr())
-    _check(lib().sg_forces_batched(arr, len(items), _stream(stream)), "sg_forces_batched")
+    return arr
+
+
+def forces_batched(items, stream=None):
+    """items: list of (plan, sigma, F_r, F_phi) with device tensors."""
+    _check(lib().sg_forces_batched(_batch_array(items), len(items), _stream(stream)), "sg_forces_batched")
+
+
+def batch_prepare(items, stream=None):
+    """Build the persistent path's work list for these items (synchronises)."""
+    _check(lib().sg_batch_prepare(_batch_array(items), len(items), _stream(stream)), "sg_batch_prepare")
+
+
+def batch_tune(items, cache_path=None, stream=None):
+    """Tune the persistent path's schedule for these sizes (or read it from
+    cache_path); returns (default ms, tuned ms).  Overwrites the items' F."""
+    ms = (ctypes.c_float * 2)()
+    path = os.fsencode(cache_path) if cache_path else None
+    _check(lib().sg_batch_tune(_batch_array(items), len(items), path, _stream(stream), ms), "sg_batch_tune")
+    return float(ms[0]), float(ms[1])
 
 
 def _autograd_fn():

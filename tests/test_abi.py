@@ -43,7 +43,7 @@ def test_every_declared_symbol_is_exported(L):
 def test_status_strings(L):
     from paper_1509_01450_gb300 import sg
 
-    for code in range(7):
+    for code in range(9):
         assert isinstance(sg.status_string(code), str) and sg.status_string(code)
     assert "not built" in sg.status_string(sg.SG_ERR_NOT_BUILT)
 

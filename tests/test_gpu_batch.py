@@ -54,11 +54,15 @@ def test_batch_equals_single_calls(torch_cuda, batch):
     assert len(plans) <= 16
     Fr, Fp = _outputs(torch, sig)
     forces_batched([(plans[(d.nu, d.nphi)], s, a, b) for d, s, a, b in zip(disks, sig, Fr, Fp)])
-    for d, s, a, b in zip(disks, sig, Fr, Fp):
-        er, ep = plans[(d.nu, d.nphi)].forces(s)
-        assert torch.equal(a, er) and torch.equal(b, ep)
     for p in plans.values():
         p.check()
+    bad = []
+    for n, (d, s, a, b) in enumerate(zip(disks, sig, Fr, Fp)):
+        er, ep = plans[(d.nu, d.nphi)].forces(s)
+        if not (torch.equal(a, er) and torch.equal(b, ep)):
+            scale = float(torch.maximum(er.abs().max(), ep.abs().max()))
+            bad.append((n, d.nu, d.nphi, float((a - er).abs().max()) / scale, float((b - ep).abs().max()) / scale))
+    assert not bad, f"{len(bad)} disks differ (index, N_u, N_phi, max |dF_r|, |dF_phi| / max |F|): {bad[:8]}"
 
 
 def test_smallest_disks_match_oracle(torch_cuda, batch, oracle_mod):
@@ -111,3 +115,80 @@ def test_batch_replays_from_a_cuda_graph(torch_cuda, batch):
         for d, s, a, b in zip(disks[:n], src, Fr, Fp):
             er, ep = plans[(d.nu, d.nphi)].forces(s)
             assert torch.equal(a, er) and torch.equal(b, ep)
+
+
+def test_persistent_path_is_taken_and_others_fall_back(torch_cuda, batch):
+    """The 256-disk batch qualifies for the one persistent launch
+    (sg_batch_prepare accepts it); a batch with a plan built with the edge
+    update does not, and still runs on the per-plan path."""
+    torch = torch_cuda
+    from paper_1509_01450_gb300 import Plan, SgError, batch_prepare, forces_batched, sg
+
+    disks, plans, sig = batch
+    Fr, Fp = _outputs(torch, sig)
+    batch_prepare([(plans[(d.nu, d.nphi)], s, a, b) for d, s, a, b in zip(disks, sig, Fr, Fp)])
+    d = disks[0]
+    pe = Plan(d.nu, d.nphi, d.u_min, d.du, 1.0, "float32").build(radial_edges=1)
+    items = [(pe, sig[0], Fr[0], Fp[0])]
+    with pytest.raises(SgError) as ei:
+        batch_prepare(items)
+    assert ei.value.status == sg.SG_ERR_UNSUPPORTED
+    forces_batched(items)
+    er, ep = pe.forces(sig[0])
+    assert torch.equal(Fr[0], er) and torch.equal(Fp[0], ep)
+
+
+def test_bounded_waits_report_a_timeout(torch_cuda, batch):
+    """With every plan's wait budget at 0 each wait of the persistent kernel
+    gives up at once: every plan reports SG_ERR_TIMEOUT, and with the budget
+    back the same plans give the single-call forces again."""
+    torch = torch_cuda
+    from paper_1509_01450_gb300 import SgError, forces_batched, sg
+
+    disks, plans, sig = batch
+    n = 24
+    Fr, Fp = _outputs(torch, sig[:n])
+    items = [(plans[(d.nu, d.nphi)], s, a, b) for d, s, a, b in zip(disks[:n], sig[:n], Fr, Fp)]
+    used = {id(p): p for p, _, _, _ in items}.values()
+    try:
+        for p in used:
+            p.set_wait_limit(0.0)
+        forces_batched(items)
+        torch.cuda.synchronize()
+        for p in used:
+            with pytest.raises(SgError) as ei:
+                p.check()
+            assert ei.value.status == sg.SG_ERR_TIMEOUT
+    finally:
+        for p in used:
+            p.set_wait_limit(1.0)
+    forces_batched(items)
+    for p in used:
+        p.check()
+    for d, s, a, b in zip(disks[:n], sig[:n], Fr, Fp):
+        er, ep = plans[(d.nu, d.nphi)].forces(s)
+        assert torch.equal(a, er) and torch.equal(b, ep)
+
+
+def test_tuned_schedule_is_cached_and_bit_equal(torch_cuda, batch, tmp_path):
+    """sg_batch_tune picks a schedule (no slower than the default), appends
+    it to the cache file, and takes it from there the second time; the
+    tuned batch still equals the single calls."""
+    torch = torch_cuda
+    from paper_1509_01450_gb300 import batch_tune, forces_batched
+
+    disks, plans, sig = batch
+    n = 64
+    Fr, Fp = _outputs(torch, sig[:n])
+    items = [(plans[(d.nu, d.nphi)], s, a, b) for d, s, a, b in zip(disks[:n], sig[:n], Fr, Fp)]
+    cache = str(tmp_path / "schedules.txt")
+    t0, t1 = batch_tune(items, cache)
+    assert 0 < t1 <= t0 * 1.02
+    lines = open(cache).read().splitlines()
+    assert len(lines) == 1 and lines[0].startswith("sg-batch-schedule v2 sms=")
+    batch_tune(items, cache)  # found in the file: nothing appended
+    assert open(cache).read().splitlines() == lines
+    forces_batched(items)
+    for d, s, a, b in zip(disks[:n], sig[:n], Fr, Fp):
+        er, ep = plans[(d.nu, d.nphi)].forces(s)
+        assert torch.equal(a, er) and torch.equal(b, ep)

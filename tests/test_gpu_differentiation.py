@@ -24,6 +24,7 @@ import numpy as np
 import pytest
 
 import workloads
+from tests.errbounds import assert_close, assert_close_1
 
 pytestmark = pytest.mark.gpu
 
@@ -140,7 +141,7 @@ def test_autograd_function_matches_adjoint(torch_cuda, problem):
     assert torch.allclose(s32.grad, ref, rtol=1e-5, atol=1e-6 * float(ref.abs().max()))
 
 
-@pytest.mark.parametrize("dtype,tol", [("float64", 1e-12), ("float32", 1e-5)])
+@pytest.mark.parametrize("dtype,tol", [("float64", 1e-12), ("float32", 1e-5), ("float32x2", 1e-12)])
 def test_gradient_matches_oracle_transposed_sum_64x64(torch_cuda, oracle_mod, dtype, tol):
     torch = torch_cuda
     from paper_1509_01450_gb300 import Plan
@@ -154,8 +155,33 @@ def test_gradient_matches_oracle_transposed_sum_64x64(torch_cuda, oracle_mod, dt
     Tr, Tp = oracle_mod.direct_sum(target, Kr, Kp)
     ref = oracle_mod.direct_sum_T(2 * W * (Fr - Tr), 2 * W * (Fp - Tp), Kr, Kp)
     plan = Plan(cfg.nu, cfg.nphi, cfg.u_min, cfg.du, 1.0, dtype).build()
-    dt = torch.float64 if dtype == "float64" else torch.float32
+    dt = plan.dtype  # FP64 fields for the compensated plans too
     gr = torch.tensor(2 * W * (Fr - Tr), dtype=dt, device="cuda")
     gp = torch.tensor(2 * W * (Fp - Tp), dtype=dt, device="cuda")
     got = plan.backward(gr, gp).double().cpu().numpy()
-    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < tol
+    assert_close_1(got, ref, tol)
+
+
+def test_compensated_fp32_gradient_end_to_end(torch_cuda, problem):
+    """The compensated FP32 plans (double-float passes on the FP32 pipes):
+    forward, residual and adjoint end to end meet the FP32 bar against the
+    FP64 gradient where the plain FP32 chain cannot (its forward rounding,
+    weighted by w, dominates the residual), and in fact the FP64 one."""
+    torch = torch_cuda
+    from paper_1509_01450_gb300 import Plan
+
+    pr = problem
+    if "g64" not in pr:
+        pytest.skip("needs the FP64 gradient of the first test")
+    cfg = pr["cfg"]
+    pc = Plan(cfg.nu, cfg.nphi, cfg.u_min, cfg.du, 1.0, "float32x2").build()
+    s = pr["dev"](pr["start"], torch.float64)
+    g = _grad(torch, pc, pr, s, torch.float64)
+    pc.check()
+    g = g.cpu().numpy()
+    g64 = pr["g64"]
+    rel = np.linalg.norm(g - g64) / np.linalg.norm(g64)
+    print(f"compensated FP32 gradient: rel-L2 {rel:.2e} against FP64")
+    assert_close_1(g, g64, 1e-5)
+    assert rel < 1e-8  # the FP64 gradient itself carries the residual's cancellation (about 1e-10)
+    assert np.abs(g.reshape(-1)[pr["fd_cells"]] - pr["fd"]).max() <= 1e-9 * np.abs(pr["fd"]).max()

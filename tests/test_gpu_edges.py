@@ -9,6 +9,7 @@ import numpy as np
 import pytest
 
 import workloads
+from tests.errbounds import assert_close, assert_close_1
 from oracle import analytic as A
 
 pytestmark = pytest.mark.gpu
@@ -46,7 +47,7 @@ def test_forward_against_the_oracle(torch_cuda, oracle_mod, nu, nphi, dtype, tol
     Fr, Fp = plan.forces(torch.tensor(sigma, dtype=plan.dtype, device="cuda"))
     torch.cuda.synchronize()
     plan.check()
-    assert oracle_mod.rel_l2(Fr.double().cpu().numpy(), Fp.double().cpu().numpy(), Fr_ref, Fp_ref) < tol
+    assert_close(Fr.double().cpu().numpy(), Fp.double().cpu().numpy(), Fr_ref, Fp_ref, tol, w=grid.r ** p)
 
 
 @pytest.mark.parametrize("dtype,tol", [("float64", 1e-12), ("float32", 1e-5)])
@@ -69,7 +70,7 @@ def test_adjoint_is_the_transpose_of_the_oracle_map(torch_cuda, oracle_mod, dtyp
     gs = plan.backward(torch.tensor(gr, dtype=plan.dtype, device="cuda"),
                        torch.tensor(gp, dtype=plan.dtype, device="cuda"))
     plan.check()
-    assert np.linalg.norm(gs.double().cpu().numpy() - ref) / np.linalg.norm(ref) < tol
+    assert_close_1(gs.double().cpu().numpy(), ref, tol, w=grid.r ** -1.0)
 
 
 @pytest.mark.parametrize("nu,nphi,r_in,r_out,p", [(64, 128, 0.01, 100.0, 0), (256, 64, 0.01, 100.0, 0),
@@ -141,13 +142,13 @@ def test_other_entry_points_and_kinds(torch_cuda, oracle_mod):
     cells = oracle_mod.particle_cells(nu, nphi, du, "particle+")
     Fr_ref, Fp_ref = oracle_mod.onesided_forces(sigma, cells, grid)
     Fr, Fp = plan2.forces(torch.tensor(sigma, device="cuda"))
-    assert oracle_mod.rel_l2(Fr.cpu().numpy(), Fp.cpu().numpy(), Fr_ref, Fp_ref) < 1e-12
+    assert_close(Fr.cpu().numpy(), Fp.cpu().numpy(), Fr_ref, Fp_ref, 1e-12)
     # and rebuilt without, the plain convolution again
     plan2.build(kind="particle+")
     Kr, Kp = oracle_mod.fold(cells, grid.beta, grid.dphi)
     Fr_ref, Fp_ref = oracle_mod.direct_sum(sigma, Kr, Kp)
     Fr, Fp = plan2.forces(torch.tensor(sigma, device="cuda"))
-    assert oracle_mod.rel_l2(Fr.cpu().numpy(), Fp.cpu().numpy(), Fr_ref, Fp_ref) < 1e-12
+    assert_close(Fr.cpu().numpy(), Fp.cpu().numpy(), Fr_ref, Fp_ref, 1e-12)
 
 
 @pytest.mark.parametrize("nu,nphi", [(256, 64), (512, 128), (2048, 32)])
@@ -164,7 +165,7 @@ def test_fp32_adjoint_with_the_update_in_the_column_pass(torch_cuda, oracle_mod,
     g64 = p64.backward(torch.tensor(gr, device="cuda"), torch.tensor(gp, device="cuda"))
     p32.check()
     ref = g64.cpu().numpy()
-    assert np.linalg.norm(g32.double().cpu().numpy() - ref) / np.linalg.norm(ref) < 1e-5
+    assert_close_1(g32.double().cpu().numpy(), ref, 1e-5, w=grid.r ** -1.0)
     # and the FP32 forward and adjoint are each other's transpose
     s = torch.tensor(workloads.random_field(nu, nphi, 33), dtype=torch.float32, device="cuda")
     Fr, Fp = p32.forces(s)
