@@ -37,9 +37,9 @@ NU, NPHI, R_IN, R_OUT, SEED = 2048, 4096, 0.01, 100.0, 1509
 # writes of the minimal data each pass must move, symmetry-reduced spectra)
 BYTES_PER_CELL = {"rows": 8.0, "cols": 20.0, "inv_rows": 16.0}
 # DRAM bytes (read + write) of one launch of the dominant pass at 2048 x 4096
-# FP32, from one ncu capture of this command (--passes-only), valid only for
-# the kernel sources it was taken on (kernel_sources_sha below).
-PASS_TRAFFIC = {"pass": "cols", "sources_sha256": "5f95a5c5a059a456", "bytes_per_launch": 100.791808e6 + 6.804480e6}
+# FP32, from one ncu capture of the bench command itself, valid only for the
+# kernel sources it was taken on (kernel_sources_sha below).
+PASS_TRAFFIC = {"pass": "cols", "sources_sha256": "966bb673635938c4", "bytes_per_launch": 100.792576e6 + 7.342848e6}
 
 
 def kernel_sources_sha(texts=None) -> str:
