@@ -5,8 +5,9 @@ exp(0.5 g) e^{-r/3}, g a seeded unit-variance k^-3 Gaussian field), FP32, with
 kernel spectra built once in FP64 before timing.  A timed step is one forward
 evaluation (sg_forces: rows -> columns -> inverse rows) of the whole grid;
 the adjoint (sg_forces_backward) and the FP64 path are timed the same way and
-reported beside it.  The L2 (126 MB) is flushed by a 256 MB write before
-every timed step, outside the step's event pair.
+reported beside it.  The L2 (126 MB) is flushed before every timed step,
+outside the step's event pair, by a 256 MB write followed by a 256 MB read:
+the step starts on a cold L2 that holds no dirty line of the flush.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -251,6 +252,22 @@ def host_link(torch, dev, h2d_bytes: int, d2h_bytes: int, reps: int = 20):
                    "alone and concurrently on two streams"}
 
 
+class L2Flush:
+    """Empties L2 between timed steps: a 256 MB write (the flush), then a
+    256 MB read, so that the step starts on a cold L2 holding no dirty lines
+    of the flush (whose write-back would otherwise fall into the step)."""
+
+    def __init__(self, torch, dev, mb: int = 256):
+        n = mb * 1024 * 1024 // 4
+        self.w = torch.empty(n, dtype=torch.float32, device=dev)
+        self.r = torch.ones(n, dtype=torch.float32, device=dev)
+        self.torch = torch
+
+    def __call__(self):
+        self.w.zero_()
+        self.torch.sum(self.r)
+
+
 def batch_throughput(torch, dev, flush, peak_gbs, n_disks: int = 256, seed: int = 1450, reps: int = 10):
     """cells/s of the batching form: n_disks exponential disks with spirals,
     N_u in {128..1024} and N_phi in {256..2048} drawn per disk, one plan per
@@ -275,7 +292,7 @@ def batch_throughput(torch, dev, flush, peak_gbs, n_disks: int = 256, seed: int 
     def timed(fn):
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
         for a, b in ev:
-            flush.zero_()
+            flush()
             a.record(stream)
             fn()
             b.record(stream)
@@ -334,15 +351,15 @@ def run_passes_only(args):
     sigma = torch.tensor(workloads.lognormal_disk(r, phi, SEED), dtype=torch.float32, device=dev)
     Fr, Fp = torch.empty_like(sigma), torch.empty_like(sigma)
     gs = torch.empty_like(sigma)
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    flush = L2Flush(torch, dev)
     out = {"workload": WORKLOAD, "mode": "passes only"}
     for name, fn in (("forward_ms", lambda: plan.forces(sigma, Fr, Fp)), ("backward_ms", lambda: plan.backward(Fr, Fp, gs))):
         for _ in range(args.warmup):
-            flush.zero_()
+            flush()
             fn()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
         for a, b in ev:
-            flush.zero_()
+            flush()
             a.record()
             fn()
             b.record()
@@ -380,7 +397,7 @@ def run_ours(args):
     sigma = torch.tensor(sigma_np, dtype=torch.float32, device=dev)
     Fr = torch.empty_like(sigma)
     Fp = torch.empty_like(sigma)
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    flush = L2Flush(torch, dev)
 
     def barrier():
         if ws > 1:
@@ -399,7 +416,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         w0 = time.time()
         for k in range(args.steps):
-            flush.zero_()
+            flush()
             starts[k].record(stream)
             plan.forces(sigma, Fr, Fp)
             ends[k].record(stream)
@@ -414,7 +431,7 @@ def run_ours(args):
     # ---- per-pass durations (roofline of the dominant kernel) -------------
     passes = []
     for _ in range(max(20, min(args.steps, 200))):
-        flush.zero_()
+        flush()
         passes.append(plan.forces_timed(sigma, Fr, Fp))
     p_rows = statistics.mean(p[0] for p in passes)
     p_cols = statistics.mean(p[1] for p in passes)
@@ -433,7 +450,7 @@ def run_ours(args):
     def timed(fn, n):
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
         for s, e in ev:
-            flush.zero_()
+            flush()
             s.record()
             fn()
             e.record()
@@ -448,7 +465,7 @@ def run_ours(args):
     bwd_ms = timed(lambda: plan.backward(gr, gp, gs), max(20, min(args.steps, 200)))
     bpasses = []
     for _ in range(max(20, min(args.steps, 200))):
-        flush.zero_()
+        flush()
         bpasses.append(plan.backward_timed(gr, gp, gs))
     bwd_pass_ms = {k: statistics.mean(b[i] for b in bpasses) for i, k in enumerate(("rows", "cols", "inv_rows"))}
     plan64 = Plan(NU, min(NPHI, 4096), u_min, du, 1.0, "float64").build()
@@ -562,7 +579,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "nu": NU, "nphi": NPHI, "r_in": R_IN, "r_out": R_OUT, "seed": SEED,
-                       "kernel_weight_p": 0, "l2": "flushed by a 256 MB write before every timed step",
+                       "kernel_weight_p": 0, "l2": "flushed by a 256 MB write, then a 256 MB read, before every timed step (cold, clean L2)",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
             "roofline": {"bound": "hbm", "kernel": f"forward {dom_name} pass", "achieved": achieved, "peak": peak,
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,

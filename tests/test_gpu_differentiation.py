@@ -184,4 +184,11 @@ def test_compensated_fp32_gradient_end_to_end(torch_cuda, problem):
     print(f"compensated FP32 gradient: rel-L2 {rel:.2e} against FP64")
     assert_close_1(g, g64, 1e-5)
     assert rel < 1e-8  # the FP64 gradient itself carries the residual's cancellation (about 1e-10)
+    # plain FP32 end to end, with the kernels stored at weighting p = 0, 1, 2
+    for p in (0, 1, 2):
+        p32 = Plan(cfg.nu, cfg.nphi, cfg.u_min, cfg.du, 1.0, "float32").build(weight_p=p)
+        g32 = _grad(torch, p32, pr, pr["dev"](pr["start"], torch.float32), torch.float32).double().cpu().numpy()
+        r32 = np.linalg.norm(g32 - g64) / np.linalg.norm(g64)
+        print(f"plain FP32 gradient at p = {p}: rel-L2 {r32:.2e} against FP64")
+        assert rel < r32
     assert np.abs(g.reshape(-1)[pr["fd_cells"]] - pr["fd"]).max() <= 1e-9 * np.abs(pr["fd"]).max()
