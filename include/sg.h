@@ -21,13 +21,15 @@
  *
  * Layout of every field (sigma, F_r, F_phi and their gradients): row-major
  * [N_u][N_phi], phi fastest, in the plan's dtype (float for SG_F32, double
- * for SG_F64), 16-byte aligned, caller-owned device memory (or host memory
- * for the *_host entry points).
+ * for SG_F64 and SG_F32X2), 16-byte aligned, caller-owned device memory (or
+ * host memory for the *_host entry points).
  *
  * Execution: every call that takes a stream enqueues asynchronous work on it
- * and returns without synchronising, except where stated.  sg_forces,
- * sg_forces_backward and sg_forces_batched allocate nothing and may be
- * captured in a CUDA graph.  A plan must not be used by two streams at once.
+ * and returns without synchronising, except where stated.  sg_forces and
+ * sg_forces_backward allocate nothing and may be captured in a CUDA graph;
+ * so may sg_forces_batched once its list of items is prepared (it allocates
+ * and synchronises only when it builds a list).  A plan must not be used by
+ * two streams at once.
  *
  * Errors: no exception crosses this boundary; every call returns an
  * sg_status.  A CUDA launch error is reported as SG_ERR_CUDA; errors of
