@@ -43,7 +43,7 @@ def _fails_at_each(torch, sg, L, fn, n, make=None, after=None):
     made afresh each time (before the hook is set): SG_ERR_ALLOC each time,
     and every allocation released once the objects are gone (the library's
     own count of live allocations; the device's free memory also moves with
-    the driver's and torch's caches)."""
+    the CUDA driver's and torch's own caches)."""
     torch.cuda.synchronize()
     live0 = L.sg_test_live_allocations()
     for k in range(n):
