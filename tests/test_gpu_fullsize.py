@@ -1,5 +1,6 @@
 """Parity at the full 2048 x 4096 size, in the launch configuration the
-benchmark times (FP32 forward and adjoint, and FP64), on sampled target and
+benchmark times (FP32 forward and adjoint, FP64, and the compensated FP32
+plans at the FP64 bar), on sampled target and
 source cells that the FP64 oracle computes one by one (direct sums over its
 own kernel table)."""
 import math
@@ -30,7 +31,7 @@ def full(oracle_mod):
     return torch, cfg, sigma, tg, Fr, Fp, Kr, Kp
 
 
-@pytest.mark.parametrize("dtype,tol", [("float32", 1e-5), ("float64", 1e-12)])
+@pytest.mark.parametrize("dtype,tol", [("float32", 1e-5), ("float64", 1e-12), ("float32x2", 1e-12)])
 def test_full_size_sampled_targets(oracle_mod, full, dtype, tol):
     torch, cfg, sigma, tg, Fr_ref, Fp_ref, _, _ = full
     from paper_1509_01450_gb300 import Plan
@@ -49,7 +50,7 @@ def test_full_size_sampled_targets(oracle_mod, full, dtype, tol):
     assert torch.equal(Fr, Fr2) and torch.equal(Fp, Fp2) and all(m > 0 for m in ms)
 
 
-@pytest.mark.parametrize("dtype,tol", [("float32", 1e-5), ("float64", 1e-12)])
+@pytest.mark.parametrize("dtype,tol", [("float32", 1e-5), ("float64", 1e-12), ("float32x2", 1e-12)])
 def test_full_size_adjoint_sampled_sources(oracle_mod, full, dtype, tol):
     torch, cfg, sigma, tg, _, _, Kr, Kp = full
     from paper_1509_01450_gb300 import Plan
