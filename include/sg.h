@@ -154,7 +154,18 @@ typedef struct {
                       the first row, its azimuthal slope central.  Needs
                       radial_edges = 1 (the wedge replaces the inner ghost
                       row) and SG_KERNEL_SIM or SG_KERNEL_POTENTIAL */
-    int reserved[1];
+    int short_dft; /* 0 (default): every azimuthal transform by FFT.  1: the
+                      forward call's two azimuthal (row) transforms, sigma ->
+                      half spectra (P1) and the column pass's spectra -> F_r,
+                      F_phi (P3), as products with the N_phi x N_phi real DFT
+                      matrix on the tensor cores (tcgen05, kind::tf32): every
+                      operand split into a TF32 part and an FP32 remainder,
+                      three products per pair (hi hi + hi lo + lo hi), FP32
+                      accumulation, so the result keeps FP32 accuracy.  Only
+                      SG_F32 plans with 32 <= N_phi <= 256 (else
+                      SG_ERR_UNSUPPORTED).  The adjoint keeps the FFT; the
+                      option is not kept by sg_plan_save, and sg_forces_batched
+                      runs such plans' items through per-plan launches */
 } sg_build_opts;
 
 /*
@@ -435,6 +446,21 @@ sg_status sg_plan_set_wait_limit(sg_plan* plan, double seconds);
  */
 sg_status sg_plan_save(const sg_plan* plan, const char* path, cudaStream_t stream);
 sg_status sg_plan_load(sg_plan** out, const char* path, cudaStream_t stream);
+
+/*
+ * The tensor-core DFT matrices of short_dft plans with N_phi points per row,
+ * computed on the host (no device needed): out receives 4 N_phi^2 floats,
+ * first the forward matrix D (y = x D: y[0] = X(0), y[1] = X(N/2), y[2m],
+ * y[2m+1] = Re, Im X(m) of X(m) = sum_n x_n e^{-2 pi i n m / N}), then the
+ * inverse matrix E (F = b E for the packed half spectrum b of a real row:
+ * E[0][k] = 1, E[1][k] = (-1)^k, E[2m][k] = 2 cos, E[2m+1][k] = -2 sin of
+ * 2 pi m k / N).  Each matrix is stored as its TF32 part, then its FP32
+ * remainder, each as [N / NT column tiles][N / 32 K chunks][NT x 32 values]
+ * with NT = min(N, 64), a tile's entry (output column j, input index k) at
+ * 32 (8 (j / 8) + k / 4) + 4 (j % 8) + k % 4 (core matrices of 8 x 4 values,
+ * K-major).  SG_ERR_UNSUPPORTED unless 32 <= N_phi <= 256 is a power of two.
+ */
+sg_status sg_dft_tc_matrices(int N_phi, float* out);
 
 /* Bytes of device memory the plan holds. */
 size_t sg_plan_device_bytes(const sg_plan* plan);

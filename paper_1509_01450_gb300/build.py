@@ -27,8 +27,8 @@ OBJ_CHECKED = os.path.join(HERE, "_build_checked")
 LIB_CHECKED = os.path.join(HERE, "libsgdisk_checked.so")
 # fftconv_lg<LG>.cu compile the fixed-length instances of fftconv.cu's pass
 # kernels, one transform length each, in parallel with the rest
-SOURCES = ["api.cu", "batch.cu", "kbuild.cu", "fftconv.cu", "fftconv_df.cu", "noalloc.cu", "wedge.cu"] + [f"fftconv_lg{lg}.cu" for lg in range(8, 14)]
-HEADERS = ["sg_common.cuh", "sg_df.cuh", "sg_internal.cuh", "fftconv.cu"]
+SOURCES = ["api.cu", "batch.cu", "dft_tc.cu", "kbuild.cu", "fftconv.cu", "fftconv_df.cu", "noalloc.cu", "wedge.cu"] + [f"fftconv_lg{lg}.cu" for lg in range(8, 14)]
+HEADERS = ["sg_common.cuh", "sg_df.cuh", "sg_internal.cuh", "sg_tc.cuh", "fftconv.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

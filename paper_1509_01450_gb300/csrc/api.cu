@@ -84,7 +84,8 @@ static void free_plan(sg_plan* p)
     if (p->bstream) cudaStreamDestroy(p->bstream);
     // wc lies inside wb's allocation
     void* bufs[] = {p->tw, p->wa, p->wb, p->kr, p->kp, p->wpre, p->wpost, p->tw64, p->cells, p->keff,
-                    p->h_sigma, p->h_fr, p->h_fp, p->derr, p->egr, p->egp, p->wtab, p->wtmp, p->xf, p->xw};
+                    p->h_sigma, p->h_fr, p->h_fp, p->derr, p->egr, p->egp, p->wtab, p->wtmp, p->xf, p->xw,
+                    p->tcm};
     for (void* b : bufs)
         sg_free(b);
     free(p);
@@ -229,6 +230,14 @@ sg_status sg_plan_create(sg_plan** out, int nu, int nphi, double u_min, double d
     return SG_OK;
 }
 
+sg_status sg_dft_tc_matrices(int N_phi, float* out)
+{
+    if (!out) return SG_ERR_ARG;
+    if (!dft_tc_supported(N_phi)) return SG_ERR_UNSUPPORTED;
+    dft_tc_matrices(N_phi, out);
+    return SG_OK;
+}
+
 sg_status sg_plan_destroy(sg_plan* p)
 {
     if (!p) return SG_ERR_ARG;
@@ -354,7 +363,7 @@ sg_status sg_kernels_build(sg_plan* p, const sg_build_opts* opts, cudaStream_t s
 {
     if (!p) return SG_ERR_ARG;
     double rtol = 1e-14, soften = 0.0;
-    int wp = 0, kind = SG_KERNEL_SIM, ntpz = 0, edges = 0, wedge = 0;
+    int wp = 0, kind = SG_KERNEL_SIM, ntpz = 0, edges = 0, wedge = 0, short_dft = 0;
     if (opts) {
         if (opts->rtol > 0.0) rtol = opts->rtol;
         wp = opts->weight_p;
@@ -373,6 +382,9 @@ sg_status sg_kernels_build(sg_plan* p, const sg_build_opts* opts, cudaStream_t s
         // the wedge takes the place of the inner ghost row: one-sided edge
         // slopes, and the kinds whose cells are integrals over the source
         if (wedge && (!edges || (kind != SG_KERNEL_SIM && kind != SG_KERNEL_POTENTIAL))) return SG_ERR_ARG;
+        short_dft = opts->short_dft;
+        if (short_dft != 0 && short_dft != 1) return SG_ERR_ARG;
+        if (short_dft && (p->dtype != SG_F32 || !dft_tc_supported(p->nphi))) return SG_ERR_UNSUPPORTED;
     }
     // beta^{p (i - i_ref)} must stay in range for both dtypes
     if (fabs((double)wp * p->du * p->nu) > 60.0) return SG_ERR_UNSUPPORTED;
@@ -432,6 +444,16 @@ sg_status sg_kernels_build(sg_plan* p, const sg_build_opts* opts, cudaStream_t s
         const size_t n = (size_t)(nphi / 2 + 1) * sg_edge_stride(nu, (int)p->elem) * p->elem;
         sg_status st = SG_OK;
         if ((!p->egr && (st = dev_alloc(p, &p->egr, n))) || (!p->egp && (st = dev_alloc(p, &p->egp, n)))) return st;
+    }
+    p->short_dft = 0;
+    if (short_dft) {
+        // the split DFT matrices of both forward row passes (host FP64, rounded)
+        std::vector<float> m(dft_tc_matrix_floats(nphi));
+        dft_tc_matrices(nphi, m.data());
+        sg_status st = SG_OK;
+        if (!p->tcm && (st = dev_alloc(p, &p->tcm, m.size() * sizeof(float)))) return st;
+        SG_TRY(cudaMemcpyAsync(p->tcm, m.data(), m.size() * sizeof(float), cudaMemcpyHostToDevice, stream));
+        SG_TRY(cudaStreamSynchronize(stream));
     }
     p->wedge = 0;
     if (wedge) {
@@ -513,6 +535,7 @@ sg_status sg_kernels_build(sg_plan* p, const sg_build_opts* opts, cudaStream_t s
         p->built = 1;
         p->edges = edges;
         p->wedge = wedge;
+        p->short_dft = short_dft;
         if (p->report[0]) ret = SG_ERR_TIMEOUT;
     }
     if (ret == SG_OK && (ret = noalloc_prepare(p, stream)) != SG_OK) p->built = 0;

@@ -237,7 +237,7 @@ static int row_slots(int lg) { return SG_BATCH_THREADS / ((1 << lg) / 16); }
 
 bool batch_eligible(const sg_plan* p)
 {
-    if (p->dtype != SG_F32 || !p->built || p->edges || p->wedge || !p->have_imaps) return false;
+    if (p->dtype != SG_F32 || !p->built || p->edges || p->wedge || p->short_dft || !p->have_imaps) return false;
     const int lgr = sg_ilog2(p->nphi), lgc = sg_ilog2(2 * p->nu);
     if (lgr < 8 || lgr > 12 || lgc < 8 || lgc > 12) return false;
     return p->nu % (4 * row_slots(lgr)) == 0;

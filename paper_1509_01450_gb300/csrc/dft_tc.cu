@@ -1,0 +1,412 @@
+// dft_tc.cu -- the azimuthal transforms of the forward passes as dense
+// DFT-matrix products on the tensor cores (build option short_dft, FP32
+// plans with 32 <= N_phi <= 256).
+//
+// Sec. 2 writes the forces as convolutions that are periodic in phi; the
+// row passes take each row's discrete Fourier transform in phi (P1) and,
+// after the column pass, the inverse transform back (P3).  For short rows the
+// transform is a product with the N_phi x N_phi real DFT matrix:
+//
+//   P1: y_i = x_i D,  x_i = sigma row i,
+//       D[n][0] = 1, D[n][1] = (-1)^n, D[n][2m] = cos(2 pi n m / N),
+//       D[n][2m+1] = -sin(2 pi n m / N)  (0 < m < N/2),
+//       so that (y_i[2m], y_i[2m+1]) = X_i(m) and (y_i[0], y_i[1]) = (X_i(0),
+//       X_i(N/2)): the half spectrum with mode 0 holding (DC, Nyquist), times
+//       the row weight w_i, goes to A[m nu + i].
+//   P3: F_r,i = b_i E wpost_i, F_phi,i = c_i E wpost_i, with b_i[2m], b_i[2m+1]
+//       = Re, Im B_i(m) (mode 0: DC, Nyquist) and c_i from C likewise,
+//       E[0][k] = 1, E[1][k] = (-1)^k, E[2m][k] = 2 cos(2 pi m k / N),
+//       E[2m+1][k] = -2 sin(2 pi m k / N): the real inverse transform of the
+//       Hermitian spectrum whose half is B (or C).
+//
+// The products run as tcgen05 MMAs of kind::tf32 (M = 128 rows per CTA, N =
+// NT output columns per CTA, K = 8 per instruction) accumulating in FP32 in
+// tensor memory.  Every operand is split in two TF32 parts, v = hi + lo with
+// hi = v rounded to TF32 and lo = v - hi (exact in FP32); the product takes
+// the three terms hi hi + hi lo + lo hi, which leaves an error of about
+// 2^-21 of each operand, so the transform keeps FP32 accuracy.  The matrices
+// are built in FP64 on the host and split there; the rows are split by the
+// threads as they stage them.
+//
+// Shared-memory operands are K-major without swizzling: core matrices of 8
+// rows x 4 values (128 contiguous bytes), the KC = 32 values of one K chunk
+// as 8 core matrices side by side (128 bytes apart), the 8-row groups 1024
+// bytes apart.  Each chunk is double-buffered: the threads stage chunk c + 1
+// while the tensor core multiplies chunk c, and a buffer is refilled only
+// after the MMAs that read it have signalled their completion on its
+// mbarrier (a bounded wait).
+#include "sg_internal.cuh"
+#include "sg_tc.cuh"
+
+#include <math.h>
+#include <string.h>
+
+namespace sg {
+
+namespace {
+
+constexpr int TC_M = 128;   // rows per CTA (tensor-memory lanes), one thread per row
+constexpr int TC_KC = 32;   // K values per staged chunk
+constexpr int TC_ABYTES = TC_M * TC_KC * 4;  // one A operand part of one chunk: 16 KB
+// Main accumulators per product.  The tensor core's FP32 accumulation loses
+// up to about one unit in the last place of the running sum per MMA step;
+// spreading the K chunks over several accumulators (and the correction terms,
+// 2^-11 of the main ones, into one of their own) divides the steps each one
+// takes, and the epilogue adds them with rounding to nearest.
+constexpr int TC_SLOTS = 3;
+
+__host__ __device__ constexpr uint32_t tc_pow2(int n)
+{
+    return n <= 32 ? 32u : n <= 64 ? 64u : n <= 128 ? 128u : n <= 256 ? 256u : 512u;
+}
+
+// Offset (in values) of (row r, k) in a K-major core-matrix tile whose rows
+// hold TC_KC values: core matrix (r / 8, k / 4) at 32 (8 (r / 8) + k / 4).
+__host__ __device__ inline int tc_off(int r, int k) { return ((r >> 3) * (TC_KC / 4) + (k >> 2)) * 32 + (r & 7) * 4 + (k & 3); }
+
+template <int NT>
+__host__ __device__ constexpr int tc_mbytes()
+{
+    return NT * TC_KC * 4;  // one matrix part of one chunk
+}
+
+// bytes of one staging buffer: G row operands (hi, lo each) and the matrix (hi, lo)
+template <int NT, int G>
+__host__ __device__ constexpr int tc_buf_bytes()
+{
+    return 2 * G * TC_ABYTES + 2 * tc_mbytes<NT>();
+}
+
+template <int NT, int G>
+constexpr size_t tc_smem_bytes()
+{
+    return 2 * (size_t)tc_buf_bytes<NT, G>() + 1024;  // two buffers, alignment slack
+}
+
+__device__ __forceinline__ float4 tc_hi(float4 v)
+{
+    return make_float4(__uint_as_float(sg_tf32_bits(__float_as_uint(v.x))),
+                       __uint_as_float(sg_tf32_bits(__float_as_uint(v.y))),
+                       __uint_as_float(sg_tf32_bits(__float_as_uint(v.z))),
+                       __uint_as_float(sg_tf32_bits(__float_as_uint(v.w))));
+}
+__device__ __forceinline__ float4 tc_sub(float4 a, float4 b)
+{
+    return make_float4(__fsub_rn(a.x, b.x), __fsub_rn(a.y, b.y), __fsub_rn(a.z, b.z), __fsub_rn(a.w, b.w));
+}
+
+// Stage four values (k .. k + 3 of row r) of one row operand: the TF32 part
+// into hi, the remainder into lo.
+__device__ __forceinline__ void tc_stage4(float* hi, float* lo, int r, int k, float4 v)
+{
+    const float4 h = tc_hi(v);
+    *reinterpret_cast<float4*>(hi + tc_off(r, k)) = h;
+    *reinterpret_cast<float4*>(lo + tc_off(r, k)) = tc_sub(v, h);
+}
+
+}  // namespace
+
+// The transform kernel.  DIR 0 (P1): x = sigma rows, one product (G = 1),
+// output A[m nu + i] = w_i (y[2m], y[2m+1]).  DIR 1 (P3): two products (G =
+// 2) with the same matrix, b from B and c from C (PAIRS: the pair layout
+// P[m nu + i] = {B, C}, 16 bytes; otherwise B and C apart), outputs F_r, F_phi
+// rows times w_i.  Grid: (ceil(nu / 128), N / NT); block 128 threads, thread
+// r owning row blockIdx.x 128 + r and tensor-memory lane r.  mat: [part (hi,
+// lo)][column tile][K chunk][NT x KC in the core-matrix layout].
+template <int NT, int DIR, bool PAIRS>
+__global__ void __launch_bounds__(TC_M, 1)
+    k_dft_tc(const float* __restrict__ x, const float4* __restrict__ P, const float2* __restrict__ Bs,
+             const float2* __restrict__ Cs, const float* __restrict__ mat, const float* __restrict__ w,
+             float2* __restrict__ A, float* __restrict__ Fr, float* __restrict__ Fp, int nu, int N, int* err)
+{
+    constexpr int G = DIR == 0 ? 1 : 2;  // products per CTA (row operands sharing the matrix)
+    constexpr int BUF = tc_buf_bytes<NT, G>();
+    constexpr int MB = tc_mbytes<NT>();
+    // accumulators: TC_SLOTS for the hi hi terms (chunk c into slot c mod S),
+    // one more for the two correction terms, each G x NT columns
+    constexpr uint32_t NCOLS = tc_pow2((TC_SLOTS + 1) * G * NT);
+    const unsigned long long wlim = sg_wait_budget(err);
+    extern __shared__ __align__(1024) unsigned char smraw[];
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ uint32_t tbase_s;
+    unsigned char* const area = reinterpret_cast<unsigned char*>(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
+    const int r = threadIdx.x, warp = r >> 5;
+    const int i = blockIdx.x * TC_M + r;
+    const bool row_ok = i < nu;
+    const int ct = blockIdx.y, nct = N / NT, nch = N / TC_KC;
+    if (warp == 0) {
+        sg_tc_alloc(&tbase_s, NCOLS);
+        sg_tc_relinquish();
+    }
+    if (r == 0) {
+        sg_mbar_init(&bar[0], 1);
+        sg_mbar_init(&bar[1], 1);
+    }
+    sg_tc_fence_before();
+    __syncthreads();
+    sg_tc_fence_after();
+    const uint32_t tbase = tbase_s;
+    const uint32_t idesc = sg_tc_idesc_tf32(TC_M, NT);
+    const int S = nch < TC_SLOTS ? nch : TC_SLOTS;  // main accumulators in use
+    const float wi = row_ok ? __ldg(&w[i]) : 0.f;
+    bool ok = true;
+    int issued = 0;  // chunks whose MMAs have been committed
+    for (int c = 0; c < nch && ok; c++) {
+        unsigned char* const buf = area + (size_t)(c & 1) * BUF;
+        float* const ahi = reinterpret_cast<float*>(buf);  // [g][hi, lo] row operands, then the matrix
+        float* const mhi = reinterpret_cast<float*>(buf + 2 * G * TC_ABYTES);
+        float* const mlo = mhi + MB / 4;
+        // this chunk's row values into registers first, so that their loads
+        // overlap the wait for the buffer
+        float4 v[G * TC_KC / 4];
+        if constexpr (DIR == 0) {
+            const float4* src = reinterpret_cast<const float4*>(x + (size_t)(row_ok ? i : 0) * N + c * TC_KC);
+#pragma unroll
+            for (int q = 0; q < TC_KC / 4; q++) v[q] = row_ok ? __ldg(src + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+        } else {
+            // modes c KC / 2 .. + KC / 2 - 1 of row i: b values in v[0 ..), c values in v[KC / 4 ..)
+            const int m0 = c * (TC_KC / 2);
+#pragma unroll
+            for (int q = 0; q < TC_KC / 4; q++) {
+                float4 b2 = make_float4(0.f, 0.f, 0.f, 0.f), c2 = b2;
+                if (row_ok) {
+                    const size_t e0 = (size_t)(m0 + 2 * q) * nu + i, e1 = e0 + nu;
+                    if constexpr (PAIRS) {
+                        const float4 p0 = __ldg(P + e0), p1 = __ldg(P + e1);
+                        b2 = make_float4(p0.x, p0.y, p1.x, p1.y);
+                        c2 = make_float4(p0.z, p0.w, p1.z, p1.w);
+                    } else {
+                        const float2 b0 = __ldg(Bs + e0), b1 = __ldg(Bs + e1);
+                        const float2 c0 = __ldg(Cs + e0), c1 = __ldg(Cs + e1);
+                        b2 = make_float4(b0.x, b0.y, b1.x, b1.y);
+                        c2 = make_float4(c0.x, c0.y, c1.x, c1.y);
+                    }
+                }
+                v[q] = b2;
+                v[TC_KC / 4 + q] = c2;
+            }
+        }
+        if (c >= 2) {  // the MMAs of chunk c - 2 read this buffer
+            bool landed = false;
+            const bool in_time = sg_mbar_wait_bounded(&bar[c & 1], ((c - 2) >> 1) & 1, err, 1, wlim, &landed);
+            if (__syncthreads_or(!in_time)) {
+                ok = false;
+                break;
+            }
+        }
+#pragma unroll
+        for (int g = 0; g < G; g++) {
+            float* hi = ahi + (size_t)g * 2 * (TC_ABYTES / 4);
+            float* lo = hi + TC_ABYTES / 4;
+#pragma unroll
+            for (int q = 0; q < TC_KC / 4; q++) tc_stage4(hi, lo, r, 4 * q, v[g * (TC_KC / 4) + q]);
+        }
+        // the matrix chunk: both parts, already in the core-matrix layout
+        {
+            const float4* mh = reinterpret_cast<const float4*>(mat + ((size_t)ct * nch + c) * (MB / 4));
+            const float4* ml = reinterpret_cast<const float4*>(mat + ((size_t)(nct + ct) * nch + c) * (MB / 4));
+            float4* dh = reinterpret_cast<float4*>(mhi);
+            float4* dl = reinterpret_cast<float4*>(mlo);
+#pragma unroll
+            for (int q = r; q < MB / 16; q += TC_M) {
+                dh[q] = __ldg(mh + q);
+                dl[q] = __ldg(ml + q);
+            }
+        }
+        sg_fence_proxy_async_smem();  // the stores above, for the tensor core's reads
+        __syncthreads();
+        if (r == 0) {
+            sg_tc_fence_after();
+            const uint32_t mh_a = sg_smem_u32(mhi), ml_a = sg_smem_u32(mlo);
+#pragma unroll
+            for (int s = 0; s < TC_KC / 8; s++) {  // K = 8 values (two core matrices) per MMA
+                const uint64_t bh = sg_tc_smem_desc(mh_a + 256 * s, 128, 1024);
+                const uint64_t bl = sg_tc_smem_desc(ml_a + 256 * s, 128, 1024);
+#pragma unroll
+                for (int g = 0; g < G; g++) {
+                    const uint32_t ah_a = sg_smem_u32(ahi + (size_t)g * 2 * (TC_ABYTES / 4)) + 256 * s;
+                    const uint64_t ah = sg_tc_smem_desc(ah_a, 128, 1024);
+                    const uint64_t al = sg_tc_smem_desc(ah_a + TC_ABYTES, 128, 1024);
+                    const uint32_t dm = tbase + (uint32_t)(((c % S) * G + g) * NT);  // this chunk's main slot
+                    const uint32_t dc = tbase + (uint32_t)((TC_SLOTS * G + g) * NT);  // the corrections
+                    sg_tc_mma_tf32(dm, ah, bh, idesc, (c >= S || s > 0) ? 1u : 0u);
+                    sg_tc_mma_tf32(dc, ah, bl, idesc, (c > 0 || s > 0) ? 1u : 0u);
+                    sg_tc_mma_tf32(dc, al, bh, idesc, 1u);
+                }
+            }
+            sg_tc_commit(&bar[c & 1]);
+        }
+        issued = c + 1;
+    }
+    // the last committed chunk's completion covers every MMA issued before it;
+    // after a wait that gave up this is the one more bounded wait for the
+    // MMAs still in flight, before the tensor memory is freed
+    if (issued > 0) {
+        const int c = issued - 1;
+        bool landed = false;
+        const bool in_time = sg_mbar_wait_bounded(&bar[c & 1], (c >> 1) & 1, err, 1, wlim, &landed);
+        if (__syncthreads_or(!in_time)) ok = false;
+    }
+    if (ok) {
+        sg_tc_fence_after();
+        const uint32_t lane_base = tbase + ((uint32_t)(warp * 32) << 16);
+#pragma unroll
+        for (int g = 0; g < G; g++) {
+#pragma unroll
+            for (int cb = 0; cb < NT / 32; cb++) {
+                // the sum of the accumulators, in FP32 with rounding to nearest:
+                // the corrections first, then the main slots
+                float y[32], t[32];
+                sg_tc_ld32(lane_base + (uint32_t)((TC_SLOTS * G + g) * NT + cb * 32), y);
+                sg_tc_wait_ld();
+                for (int k = 0; k < S; k++) {
+                    sg_tc_ld32(lane_base + (uint32_t)((k * G + g) * NT + cb * 32), t);
+                    sg_tc_wait_ld();
+#pragma unroll
+                    for (int q = 0; q < 32; q++) y[q] = __fadd_rn(y[q], t[q]);
+                }
+                const int j0 = ct * NT + cb * 32;  // first output column
+                if constexpr (DIR == 0) {
+                    SG_IF_OK(!row_ok || (j0 / 2 + 16 <= N / 2), err, 401)
+                    if (row_ok) {
+#pragma unroll
+                        for (int q = 0; q < 16; q++)
+                            A[(size_t)(j0 / 2 + q) * nu + i] = make_float2(__fmul_rn(y[2 * q], wi),
+                                                                           __fmul_rn(y[2 * q + 1], wi));
+                    }
+                } else {
+                    float* o = (g == 0 ? Fr : Fp) + (size_t)(row_ok ? i : 0) * N + j0;
+                    SG_IF_OK(!row_ok || j0 + 32 <= N, err, 402)
+                    if (row_ok) {
+#pragma unroll
+                        for (int q = 0; q < 8; q++)
+                            reinterpret_cast<float4*>(o)[q] =
+                                make_float4(__fmul_rn(y[4 * q], wi), __fmul_rn(y[4 * q + 1], wi),
+                                            __fmul_rn(y[4 * q + 2], wi), __fmul_rn(y[4 * q + 3], wi));
+                    }
+                }
+            }
+        }
+    }
+    sg_tc_fence_before();
+    __syncthreads();  // every tensor-memory read is done (or none happens)
+    if (warp == 0) sg_tc_dealloc(tbase, NCOLS);
+}
+
+// ---- host side ----------------------------------------------------------------
+
+static int tc_nt(int N) { return N < 64 ? N : 64; }
+
+bool dft_tc_supported(int nphi) { return nphi >= 32 && nphi <= 256 && (nphi & (nphi - 1)) == 0; }
+
+size_t dft_tc_matrix_floats(int nphi) { return (size_t)4 * nphi * nphi; }
+
+static float tf32_round(float v)
+{
+    uint32_t u;
+    memcpy(&u, &v, 4);
+    u = sg_tf32_bits(u);
+    float h;
+    memcpy(&h, &u, 4);
+    return h;
+}
+
+// Both matrices (P1's D, P3's E) for rows of N values, each as [part][column
+// tile][K chunk][NT x KC core-matrix tile] with the operand's row index the
+// output column and K the input index: out[0 .. 2 N^2) holds D, out[2 N^2 ..
+// 4 N^2) holds E.  Entries are formed in FP64 (the angle reduced exactly:
+// 2 pi (n m mod N) / N) and split into the TF32 part and the FP32 remainder.
+void dft_tc_matrices(int N, float* out)
+{
+    const int NT = tc_nt(N), nch = N / TC_KC;
+    const size_t part = (size_t)N * N;
+    for (int dir = 0; dir < 2; dir++) {
+        float* hi = out + (size_t)dir * 2 * part;
+        float* lo = hi + part;
+        for (int j = 0; j < N; j++)       // output column: the operand's row
+            for (int k = 0; k < N; k++) {  // input index: K
+                // P1: D[k][j]; P3: E[k][j] (k the packed spectrum index, j the point)
+                const int n = dir == 0 ? k : j;    // point index
+                const int q = dir == 0 ? j : k;    // packed spectrum index
+                const int m = q >> 1;
+                double val;
+                if (q == 0)
+                    val = 1.0;
+                else if (q == 1)
+                    val = (n & 1) ? -1.0 : 1.0;
+                else {
+                    const double a = 6.283185307179586476925286766559 * (double)(((long long)n * m) % N) / (double)N;
+                    val = (q & 1) ? -sin(a) : cos(a);
+                    if (dir == 1) val *= 2.0;
+                }
+                const float h = tf32_round((float)val);
+                const float l = (float)(val - (double)h);
+                const int t = j / NT, jj = j % NT, c = k / TC_KC, kk = k % TC_KC;
+                const size_t at = ((size_t)t * nch + c) * ((size_t)NT * TC_KC) + tc_off(jj, kk);
+                hi[at] = h;
+                lo[at] = l;
+            }
+    }
+}
+
+template <typename K>
+static cudaError_t tc_set_smem(K kernel, size_t smem)
+{
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+// P1 on the tensor cores: sigma rows (row-major, N_phi each) -> A.
+cudaError_t launch_dft_r2c(const PlanView& p, const float* sigma, cudaStream_t st)
+{
+    const int N = p.nphi, NT = tc_nt(N);
+    const dim3 grid((p.nu + TC_M - 1) / TC_M, N / NT);
+    cudaError_t e;
+    if (NT == 64) {
+        auto k = k_dft_tc<64, 0, false>;
+        const size_t smem = tc_smem_bytes<64, 1>();
+        if ((e = tc_set_smem(k, smem)) != cudaSuccess) return e;
+        k<<<grid, TC_M, smem, st>>>(sigma, nullptr, nullptr, nullptr, (const float*)p.tcm, (const float*)p.wpre,
+                                    (float2*)p.wa, nullptr, nullptr, p.nu, N, p.err);
+    } else {
+        auto k = k_dft_tc<32, 0, false>;
+        const size_t smem = tc_smem_bytes<32, 1>();
+        if ((e = tc_set_smem(k, smem)) != cudaSuccess) return e;
+        k<<<grid, TC_M, smem, st>>>(sigma, nullptr, nullptr, nullptr, (const float*)p.tcm, (const float*)p.wpre,
+                                    (float2*)p.wa, nullptr, nullptr, p.nu, N, p.err);
+    }
+    return cudaGetLastError();
+}
+
+// P3 on the tensor cores: the column pass's B and C (pairs: one buffer of
+// {B, C} at wb; otherwise B at wb, C at wc) -> F_r, F_phi rows.
+cudaError_t launch_dft_c2r(const PlanView& p, float* Fr, float* Fp, cudaStream_t st)
+{
+    const int N = p.nphi, NT = tc_nt(N);
+    const dim3 grid((p.nu + TC_M - 1) / TC_M, N / NT);
+    const float* E = (const float*)p.tcm + 2 * (size_t)N * N;
+    const float4* P = (const float4*)p.wb;
+    const float2 *B = (const float2*)p.wb, *C = (const float2*)p.wc;
+    cudaError_t e;
+#define SG_TC_C2R(NTV, PR)                                                                                    \
+    do {                                                                                                      \
+        auto k = k_dft_tc<NTV, 1, PR>;                                                                        \
+        const size_t smem = tc_smem_bytes<NTV, 2>();                                                          \
+        if ((e = tc_set_smem(k, smem)) != cudaSuccess) return e;                                              \
+        k<<<grid, TC_M, smem, st>>>(nullptr, P, B, C, E, (const float*)p.wpost, nullptr, Fr, Fp, p.nu, N, p.err); \
+    } while (0)
+    if (NT == 64) {
+        if (p.pairs)
+            SG_TC_C2R(64, true);
+        else
+            SG_TC_C2R(64, false);
+    } else {
+        if (p.pairs)
+            SG_TC_C2R(32, true);
+        else
+            SG_TC_C2R(32, false);
+    }
+#undef SG_TC_C2R
+    return cudaGetLastError();
+}
+
+}  // namespace sg

@@ -2310,7 +2310,9 @@ cudaError_t launch_forward(const PlanView& p0, const T* sigma, T* Fr, T* Fp, cud
     if (wedge_fused && (err = launch_wedge_dft<T>(p, st)) != cudaSuccess) return err;
     {
         PassRange range_("sg forward rows");
-        if (p.pairs) {
+        if (sizeof(T) == 4 && p.tcm) {
+            if ((err = launch_dft_r2c(p, (const float*)sigma, st)) != cudaSuccess) return err;
+        } else if (p.pairs) {
             const int nblk = p.nu / (4 * fr->slots);
             auto k = sigma_direct ? fr->fwd_rows_direct : fr->fwd_rows;
             if ((err = set_smem(k, fr->r2c_smem, true)) != cudaSuccess) return err;
@@ -2372,7 +2374,9 @@ cudaError_t launch_forward(const PlanView& p0, const T* sigma, T* Fr, T* Fp, cud
     if (ev && (err = cudaEventRecord(ev[2], st)) != cudaSuccess) return err;
     {
         PassRange range_("sg forward inverse rows");
-        if (p.pairs) {
+        if (sizeof(T) == 4 && p.tcm) {
+            if ((err = launch_dft_c2r(p, (float*)Fr, (float*)Fp, st)) != cudaSuccess) return err;
+        } else if (p.pairs) {
             const int nblk = p.nu / (2 * fr->slots);
             auto k = fr->fwd_rows_inv;
             if ((err = set_smem(k, fr->c2r_smem, true)) != cudaSuccess) return err;

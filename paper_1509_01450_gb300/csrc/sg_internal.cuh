@@ -73,6 +73,10 @@ struct sg_plan {
     int wedge;
     void* wtab;         // working dtype, [4][nphi/2 + 1][nu]: Wr, Wphi, Vr, Vphi spectra (wedge.cu)
     void* wtmp;         // [nphi/2] complex values of the working dtype (16 B each allocated): the adjoint's per-mode sums
+    // the forward row passes as dense DFT-matrix products on the tensor cores
+    // (sg_build_opts.short_dft = 1; FP32, 32 <= nphi <= 256)
+    int short_dft;
+    void* tcm;          // FP32 [4 nphi^2]: the split matrices of dft_tc_matrices
 };
 
 namespace sg {
@@ -102,6 +106,7 @@ struct PlanView {
     void* wtmp;
     const void* sigw;       // forward: the wedge densities (N_phi, working dtype), set per call
     void* gsigw;            // adjoint: their gradient, set per call
+    const void* tcm;        // FP32 plans with short_dft: the tensor-core DFT matrices; null otherwise
 };
 
 inline PlanView view(const sg_plan* p)
@@ -132,6 +137,7 @@ inline PlanView view(const sg_plan* p)
     v.wtmp = p->wtmp;
     v.sigw = nullptr;
     v.gsigw = nullptr;
+    v.tcm = p->short_dft ? p->tcm : nullptr;
     return v;
 }
 
@@ -172,6 +178,12 @@ sg_status batch_prepare(const sg_batch_item* items, int n, cudaStream_t st);
 sg_status batch_tune(const sg_batch_item* items, int n, const char* path, cudaStream_t st, float ms_out[2]);
 void batch_forget_plan(const sg_plan* p);
 bool batch_eligible(const sg_plan* p);
+// dft_tc.cu: the forward row passes as tensor-core DFT-matrix products
+bool dft_tc_supported(int nphi);
+size_t dft_tc_matrix_floats(int nphi);
+void dft_tc_matrices(int nphi, float* out);  // host: D then E, each [hi, lo][tile][chunk][NT x 32]
+cudaError_t launch_dft_r2c(const PlanView& p, const float* sigma, cudaStream_t st);
+cudaError_t launch_dft_c2r(const PlanView& p, float* Fr, float* Fp, cudaStream_t st);
 // every device allocation of the library, through the sg_test_fail_alloc
 // hook, and its release (sg_test_live_allocations counts the difference)
 cudaError_t sg_malloc(void** ptr, size_t bytes);

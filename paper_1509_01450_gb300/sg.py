@@ -33,7 +33,8 @@ EXPORTS = ("sg_plan_create", "sg_kernels_build", "sg_forces", "sg_forces_backwar
            "sg_forces_batched", "sg_batch_prepare", "sg_batch_tune", "sg_plan_destroy", "sg_status_string", "sg_plan_info",
            "sg_plan_kernels", "sg_plan_cells", "sg_plan_device_bytes", "sg_plan_build_report", "sg_forces_noalloc", "sg_plan_check",
            "sg_plan_set_wait_limit", "sg_plan_save", "sg_plan_load", "sg_forces_wedge", "sg_forces_wedge_backward",
-           "sg_checked_build", "sg_last_bounds_site", "sg_test_fail_alloc", "sg_test_live_allocations")
+           "sg_checked_build", "sg_last_bounds_site", "sg_test_fail_alloc", "sg_test_live_allocations",
+           "sg_dft_tc_matrices")
 
 
 class SgError(RuntimeError):
@@ -56,7 +57,7 @@ KERNEL_KINDS = {"sim": SG_KERNEL_SIM, "particle": SG_KERNEL_PARTICLE, "particle+
 class BuildOpts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("weight_p", ctypes.c_int), ("kind", ctypes.c_int),
                 ("soften", ctypes.c_double), ("n_tpz", ctypes.c_int), ("radial_edges", ctypes.c_int),
-                ("wedge", ctypes.c_int), ("reserved", ctypes.c_int * 1)]
+                ("wedge", ctypes.c_int), ("short_dft", ctypes.c_int)]
 
 
 class BatchItem(ctypes.Structure):
@@ -103,6 +104,7 @@ def lib():
         L.sg_last_bounds_site.argtypes = []
         L.sg_test_fail_alloc.argtypes = [ip]
         L.sg_test_live_allocations.argtypes = []
+        L.sg_dft_tc_matrices.argtypes = [ip, ctypes.POINTER(ctypes.c_float)]
         L.sg_plan_device_bytes.argtypes = [vp]
         L.sg_plan_device_bytes.restype = ctypes.c_size_t
         for name in EXPORTS:
@@ -154,7 +156,7 @@ class Plan:
 
     # -- one-time preparation ------------------------------------------------
     def build(self, rtol: float = 1e-14, weight_p: int = 0, kind="sim", soften: float = 0.0, n_tpz: int = 0,
-              radial_edges: int = 0, wedge: int = 0, stream=None):
+              radial_edges: int = 0, wedge: int = 0, short_dft: int = 0, stream=None):
         """Build the kernels.  kind: "sim" (default; n_tpz > 0 for the
         trapezoidal rule of Eq. 41-43 with n_tpz trapezoids), "particle",
         "particle+" or "softened" (with soften = eps / r_i), "potential"
@@ -163,9 +165,11 @@ class Plan:
         an SG_KERNEL_* code.
         radial_edges = 1: one-sided radial slopes at the first and last rows
         instead of ghost rows.  wedge = 1 (with radial_edges = 1): the origin
-        wedge below the first row, whose densities forces_wedge takes."""
+        wedge below the first row, whose densities forces_wedge takes.
+        short_dft = 1 (FP32, 32 <= N_phi <= 256): the forward row transforms
+        as split-TF32 DFT-matrix products on the tensor cores."""
         code = KERNEL_KINDS[kind] if isinstance(kind, str) else int(kind)
-        opts = BuildOpts(rtol, weight_p, code, soften, n_tpz, radial_edges, wedge)
+        opts = BuildOpts(rtol, weight_p, code, soften, n_tpz, radial_edges, wedge, short_dft)
         _check(lib().sg_kernels_build(self.handle, ctypes.byref(opts), _stream(stream)), "sg_kernels_build")
         return self
 
@@ -339,6 +343,17 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def dft_tc_matrices(nphi: int):
+    """sg_dft_tc_matrices: the split tensor-core DFT matrices of short_dft
+    plans (host only), as a float32 numpy array of 4 nphi^2 values."""
+    import numpy as np
+
+    out = np.zeros(4 * nphi * nphi, dtype=np.float32)
+    _check(lib().sg_dft_tc_matrices(int(nphi), out.ctypes.data_as(ctypes.POINTER(ctypes.c_float))),
+           "sg_dft_tc_matrices")
+    return out
 
 
 def _batch_array(items):
