@@ -155,15 +155,16 @@ typedef struct {
                       radial_edges = 1 (the wedge replaces the inner ghost
                       row) and SG_KERNEL_SIM or SG_KERNEL_POTENTIAL */
     int short_dft; /* 0 (default): every azimuthal transform by FFT.  1: the
-                      forward call's two azimuthal (row) transforms, sigma ->
-                      half spectra (P1) and the column pass's spectra -> F_r,
-                      F_phi (P3), as products with the N_phi x N_phi real DFT
-                      matrix on the tensor cores (tcgen05, kind::tf32): every
-                      operand split into a TF32 part and an FP32 remainder,
-                      three products per pair (hi hi + hi lo + lo hi), FP32
-                      accumulation, so the result keeps FP32 accuracy.  Only
-                      SG_F32 plans with 32 <= N_phi <= 256 (else
-                      SG_ERR_UNSUPPORTED).  The adjoint keeps the FFT; the
+                      azimuthal (row) transforms of the forward call (sigma ->
+                      half spectra, the column pass's spectra -> F_r, F_phi)
+                      and of the adjoint (gF_r, gF_phi -> half spectra, the
+                      column pass's spectrum -> gsigma) as products with the
+                      N_phi x N_phi real DFT matrix on the tensor cores
+                      (tcgen05, kind::tf32): every operand split into a TF32
+                      part and an FP32 remainder, three products per pair
+                      (hi hi + hi lo + lo hi), FP32 accumulation, so the
+                      result keeps FP32 accuracy.  Only SG_F32 plans with
+                      32 <= N_phi <= 256 (else SG_ERR_UNSUPPORTED).  The
                       option is not kept by sg_plan_save, and sg_forces_batched
                       runs such plans' items through per-plan launches */
 } sg_build_opts;

@@ -1,6 +1,6 @@
-// dft_tc.cu -- the azimuthal transforms of the forward passes as dense
-// DFT-matrix products on the tensor cores (build option short_dft, FP32
-// plans with 32 <= N_phi <= 256).
+// dft_tc.cu -- the azimuthal transforms of the forward and adjoint passes
+// as dense DFT-matrix products on the tensor cores (build option short_dft,
+// FP32 plans with 32 <= N_phi <= 256).
 //
 // Sec. 2 writes the forces as convolutions that are periodic in phi; the
 // row passes take each row's discrete Fourier transform in phi (P1) and,
@@ -18,6 +18,9 @@
 //       E[0][k] = 1, E[1][k] = (-1)^k, E[2m][k] = 2 cos(2 pi m k / N),
 //       E[2m+1][k] = -2 sin(2 pi m k / N): the real inverse transform of the
 //       Hermitian spectrum whose half is B (or C).
+//   The adjoint's row passes are the same two products: P1b takes gF_r and
+//   gF_phi through D (times wpost) to the half spectra A and C, P3b the
+//   column pass's B through E (times wpre) to gsigma.
 //
 // The products run as tcgen05 MMAs of kind::tf32 (M = 128 rows per CTA, N =
 // NT output columns per CTA, K = 8 per instruction) accumulating in FP32 in
@@ -106,25 +109,40 @@ __device__ __forceinline__ void tc_stage4(float* hi, float* lo, int r, int k, fl
 
 }  // namespace
 
-// The transform kernel.  DIR 0 (P1): x = sigma rows, one product (G = 1),
-// output A[m nu + i] = w_i (y[2m], y[2m+1]).  DIR 1 (P3): two products (G =
-// 2) with the same matrix, b from B and c from C (PAIRS: the pair layout
-// P[m nu + i] = {B, C}, 16 bytes; otherwise B and C apart), outputs F_r, F_phi
-// rows times w_i.  Grid: (ceil(nu / 128), N / NT); block 128 threads, thread
-// r owning row blockIdx.x 128 + r and tensor-memory lane r.  mat: [part (hi,
-// lo)][column tile][K chunk][NT x KC in the core-matrix layout].
-template <int NT, int DIR, bool PAIRS>
-__global__ void __launch_bounds__(TC_M, 1)
-    k_dft_tc(const float* __restrict__ x, const float4* __restrict__ P, const float2* __restrict__ Bs,
-             const float2* __restrict__ Cs, const float* __restrict__ mat, const float* __restrict__ w,
-             float2* __restrict__ A, float* __restrict__ Fr, float* __restrict__ Fp, int nu, int N, int* err)
+// Arguments of the transform kernel (one struct: the four row passes take
+// different subsets).  Row fields are row-major, N values per row; spectra
+// are mode-major, element (m, i) at m nu + i, mode 0 holding (DC, Nyquist).
+struct TcArgs {
+    const float* x[2];    // DIR 0: the G input row fields
+    const float4* pin;    // DIR 1, PAIRS: {X, Y} pairs (16 bytes per element)
+    const float2* in[2];  // DIR 1 otherwise: the G single-layout spectra
+    const float* mat;     // [part (hi, lo)][column tile][K chunk][NT x KC core-matrix tile]
+    const float* w;       // the row weights (nu values), applied to the outputs
+    float4* pout;         // DIR 0, G = 2, PAIRS: the output pairs
+    float2* out[2];       // DIR 0 otherwise: the G single-layout output spectra
+    float* y[2];          // DIR 1: the G output row fields
+    int nu, N;
+    int* err;
+};
+
+// The transform kernel: G products of 128-row tiles with one matrix.
+//   DIR 0 (P1, P1b): rows -> half spectra.  Forward G = 1: sigma -> A.
+//     Adjoint G = 2: gF_r, gF_phi -> A, C (PAIRS: {A, C} pairs).
+//   DIR 1 (P3, P3b): half spectra -> rows.  Forward G = 2: B, C (PAIRS: the
+//     {B, C} pairs) -> F_r, F_phi.  Adjoint G = 1: B -> gsigma.
+// Outputs are scaled by the row weight w_i.  Grid: (ceil(nu / 128), N / NT);
+// block 128 threads, thread r owning row blockIdx.x 128 + r and tensor-memory
+// lane r.
+template <int NT, int DIR, int G, bool PAIRS>
+__global__ void __launch_bounds__(TC_M, 1) k_dft_tc(const TcArgs a)
 {
-    constexpr int G = DIR == 0 ? 1 : 2;  // products per CTA (row operands sharing the matrix)
     constexpr int BUF = tc_buf_bytes<NT, G>();
     constexpr int MB = tc_mbytes<NT>();
     // accumulators: TC_SLOTS for the hi hi terms (chunk c into slot c mod S),
     // one more for the two correction terms, each G x NT columns
     constexpr uint32_t NCOLS = tc_pow2((TC_SLOTS + 1) * G * NT);
+    const int nu = a.nu, N = a.N;
+    int* const err = a.err;
     const unsigned long long wlim = sg_wait_budget(err);
     extern __shared__ __align__(1024) unsigned char smraw[];
     __shared__ __align__(8) uint64_t bar[2];
@@ -148,7 +166,7 @@ __global__ void __launch_bounds__(TC_M, 1)
     const uint32_t tbase = tbase_s;
     const uint32_t idesc = sg_tc_idesc_tf32(TC_M, NT);
     const int S = nch < TC_SLOTS ? nch : TC_SLOTS;  // main accumulators in use
-    const float wi = row_ok ? __ldg(&w[i]) : 0.f;
+    const float wi = row_ok ? __ldg(&a.w[i]) : 0.f;
     bool ok = true;
     int issued = 0;  // chunks whose MMAs have been committed
     for (int c = 0; c < nch && ok; c++) {
@@ -157,33 +175,37 @@ __global__ void __launch_bounds__(TC_M, 1)
         float* const mhi = reinterpret_cast<float*>(buf + 2 * G * TC_ABYTES);
         float* const mlo = mhi + MB / 4;
         // this chunk's row values into registers first, so that their loads
-        // overlap the wait for the buffer
+        // overlap the wait for the buffer: v[g KC / 4 + q] = values 4 q .. 4 q + 3
         float4 v[G * TC_KC / 4];
         if constexpr (DIR == 0) {
-            const float4* src = reinterpret_cast<const float4*>(x + (size_t)(row_ok ? i : 0) * N + c * TC_KC);
 #pragma unroll
-            for (int q = 0; q < TC_KC / 4; q++) v[q] = row_ok ? __ldg(src + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int g = 0; g < G; g++) {
+                const float4* src = reinterpret_cast<const float4*>(a.x[g] + (size_t)(row_ok ? i : 0) * N + c * TC_KC);
+#pragma unroll
+                for (int q = 0; q < TC_KC / 4; q++)
+                    v[g * (TC_KC / 4) + q] = row_ok ? __ldg(src + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
         } else {
-            // modes c KC / 2 .. + KC / 2 - 1 of row i: b values in v[0 ..), c values in v[KC / 4 ..)
+            // modes c KC / 2 .. + KC / 2 - 1 of row i, two per float4
             const int m0 = c * (TC_KC / 2);
 #pragma unroll
             for (int q = 0; q < TC_KC / 4; q++) {
-                float4 b2 = make_float4(0.f, 0.f, 0.f, 0.f), c2 = b2;
+#pragma unroll
+                for (int g = 0; g < G; g++) v[g * (TC_KC / 4) + q] = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (row_ok) {
                     const size_t e0 = (size_t)(m0 + 2 * q) * nu + i, e1 = e0 + nu;
-                    if constexpr (PAIRS) {
-                        const float4 p0 = __ldg(P + e0), p1 = __ldg(P + e1);
-                        b2 = make_float4(p0.x, p0.y, p1.x, p1.y);
-                        c2 = make_float4(p0.z, p0.w, p1.z, p1.w);
+                    if constexpr (PAIRS && G == 2) {
+                        const float4 p0 = __ldg(a.pin + e0), p1 = __ldg(a.pin + e1);
+                        v[q] = make_float4(p0.x, p0.y, p1.x, p1.y);
+                        v[TC_KC / 4 + q] = make_float4(p0.z, p0.w, p1.z, p1.w);
                     } else {
-                        const float2 b0 = __ldg(Bs + e0), b1 = __ldg(Bs + e1);
-                        const float2 c0 = __ldg(Cs + e0), c1 = __ldg(Cs + e1);
-                        b2 = make_float4(b0.x, b0.y, b1.x, b1.y);
-                        c2 = make_float4(c0.x, c0.y, c1.x, c1.y);
+#pragma unroll
+                        for (int g = 0; g < G; g++) {
+                            const float2 b0 = __ldg(a.in[g] + e0), b1 = __ldg(a.in[g] + e1);
+                            v[g * (TC_KC / 4) + q] = make_float4(b0.x, b0.y, b1.x, b1.y);
+                        }
                     }
                 }
-                v[q] = b2;
-                v[TC_KC / 4 + q] = c2;
             }
         }
         if (c >= 2) {  // the MMAs of chunk c - 2 read this buffer
@@ -203,8 +225,8 @@ __global__ void __launch_bounds__(TC_M, 1)
         }
         // the matrix chunk: both parts, already in the core-matrix layout
         {
-            const float4* mh = reinterpret_cast<const float4*>(mat + ((size_t)ct * nch + c) * (MB / 4));
-            const float4* ml = reinterpret_cast<const float4*>(mat + ((size_t)(nct + ct) * nch + c) * (MB / 4));
+            const float4* mh = reinterpret_cast<const float4*>(a.mat + ((size_t)ct * nch + c) * (MB / 4));
+            const float4* ml = reinterpret_cast<const float4*>(a.mat + ((size_t)(nct + ct) * nch + c) * (MB / 4));
             float4* dh = reinterpret_cast<float4*>(mhi);
             float4* dl = reinterpret_cast<float4*>(mlo);
 #pragma unroll
@@ -251,38 +273,47 @@ __global__ void __launch_bounds__(TC_M, 1)
         sg_tc_fence_after();
         const uint32_t lane_base = tbase + ((uint32_t)(warp * 32) << 16);
 #pragma unroll
-        for (int g = 0; g < G; g++) {
+        for (int cb = 0; cb < NT / 32; cb++) {
+            // each product's sum of accumulators, in FP32 with rounding to
+            // nearest: the corrections first, then the main slots
+            float y[G][32];
 #pragma unroll
-            for (int cb = 0; cb < NT / 32; cb++) {
-                // the sum of the accumulators, in FP32 with rounding to nearest:
-                // the corrections first, then the main slots
-                float y[32], t[32];
-                sg_tc_ld32(lane_base + (uint32_t)((TC_SLOTS * G + g) * NT + cb * 32), y);
+            for (int g = 0; g < G; g++) {
+                float t[32];
+                sg_tc_ld32(lane_base + (uint32_t)((TC_SLOTS * G + g) * NT + cb * 32), y[g]);
                 sg_tc_wait_ld();
                 for (int k = 0; k < S; k++) {
                     sg_tc_ld32(lane_base + (uint32_t)((k * G + g) * NT + cb * 32), t);
                     sg_tc_wait_ld();
 #pragma unroll
-                    for (int q = 0; q < 32; q++) y[q] = __fadd_rn(y[q], t[q]);
+                    for (int q = 0; q < 32; q++) y[g][q] = __fadd_rn(y[g][q], t[q]);
                 }
-                const int j0 = ct * NT + cb * 32;  // first output column
-                if constexpr (DIR == 0) {
-                    SG_IF_OK(!row_ok || (j0 / 2 + 16 <= N / 2), err, 401)
-                    if (row_ok) {
 #pragma unroll
-                        for (int q = 0; q < 16; q++)
-                            A[(size_t)(j0 / 2 + q) * nu + i] = make_float2(__fmul_rn(y[2 * q], wi),
-                                                                           __fmul_rn(y[2 * q + 1], wi));
+                for (int q = 0; q < 32; q++) y[g][q] = __fmul_rn(y[g][q], wi);
+            }
+            const int j0 = ct * NT + cb * 32;  // first output column
+            if constexpr (DIR == 0) {  // columns j0 .. j0 + 31: modes j0 / 2 .. j0 / 2 + 15
+                SG_IF_OK(!row_ok || (j0 / 2 + 16 <= N / 2), err, 401)
+                if (row_ok) {
+#pragma unroll
+                    for (int q = 0; q < 16; q++) {
+                        const size_t e = (size_t)(j0 / 2 + q) * nu + i;
+                        if constexpr (PAIRS && G == 2)
+                            a.pout[e] = make_float4(y[0][2 * q], y[0][2 * q + 1], y[G - 1][2 * q], y[G - 1][2 * q + 1]);
+                        else
+#pragma unroll
+                            for (int g = 0; g < G; g++) a.out[g][e] = make_float2(y[g][2 * q], y[g][2 * q + 1]);
                     }
-                } else {
-                    float* o = (g == 0 ? Fr : Fp) + (size_t)(row_ok ? i : 0) * N + j0;
-                    SG_IF_OK(!row_ok || j0 + 32 <= N, err, 402)
-                    if (row_ok) {
+                }
+            } else {
+                SG_IF_OK(!row_ok || j0 + 32 <= N, err, 402)
+                if (row_ok) {
+#pragma unroll
+                    for (int g = 0; g < G; g++) {
+                        float4* o = reinterpret_cast<float4*>(a.y[g] + (size_t)i * N + j0);
 #pragma unroll
                         for (int q = 0; q < 8; q++)
-                            reinterpret_cast<float4*>(o)[q] =
-                                make_float4(__fmul_rn(y[4 * q], wi), __fmul_rn(y[4 * q + 1], wi),
-                                            __fmul_rn(y[4 * q + 2], wi), __fmul_rn(y[4 * q + 3], wi));
+                            o[q] = make_float4(y[g][4 * q], y[g][4 * q + 1], y[g][4 * q + 2], y[g][4 * q + 3]);
                     }
                 }
             }
@@ -349,64 +380,78 @@ void dft_tc_matrices(int N, float* out)
     }
 }
 
-template <typename K>
-static cudaError_t tc_set_smem(K kernel, size_t smem)
+template <int NT, int DIR, int G, bool PAIRS>
+static cudaError_t tc_launch(const TcArgs& a, cudaStream_t st)
 {
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto k = k_dft_tc<NT, DIR, G, PAIRS>;
+    const size_t smem = tc_smem_bytes<NT, G>();
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const dim3 grid((a.nu + TC_M - 1) / TC_M, a.N / NT);
+    k<<<grid, TC_M, smem, st>>>(a);
+    return cudaGetLastError();
 }
 
-// P1 on the tensor cores: sigma rows (row-major, N_phi each) -> A.
+template <int DIR, int G, bool PAIRS>
+static cudaError_t tc_launch_nt(const TcArgs& a, cudaStream_t st)
+{
+    return tc_nt(a.N) == 64 ? tc_launch<64, DIR, G, PAIRS>(a, st) : tc_launch<32, DIR, G, PAIRS>(a, st);
+}
+
+static TcArgs tc_args(const PlanView& p, int dir, const float* w)
+{
+    TcArgs a{};
+    a.mat = (const float*)p.tcm + (size_t)dir * 2 * p.nphi * p.nphi;
+    a.w = w;
+    a.nu = p.nu;
+    a.N = p.nphi;
+    a.err = p.err;
+    return a;
+}
+
+// P1 on the tensor cores: sigma rows -> A (wa), weighted by wpre.
 cudaError_t launch_dft_r2c(const PlanView& p, const float* sigma, cudaStream_t st)
 {
-    const int N = p.nphi, NT = tc_nt(N);
-    const dim3 grid((p.nu + TC_M - 1) / TC_M, N / NT);
-    cudaError_t e;
-    if (NT == 64) {
-        auto k = k_dft_tc<64, 0, false>;
-        const size_t smem = tc_smem_bytes<64, 1>();
-        if ((e = tc_set_smem(k, smem)) != cudaSuccess) return e;
-        k<<<grid, TC_M, smem, st>>>(sigma, nullptr, nullptr, nullptr, (const float*)p.tcm, (const float*)p.wpre,
-                                    (float2*)p.wa, nullptr, nullptr, p.nu, N, p.err);
-    } else {
-        auto k = k_dft_tc<32, 0, false>;
-        const size_t smem = tc_smem_bytes<32, 1>();
-        if ((e = tc_set_smem(k, smem)) != cudaSuccess) return e;
-        k<<<grid, TC_M, smem, st>>>(sigma, nullptr, nullptr, nullptr, (const float*)p.tcm, (const float*)p.wpre,
-                                    (float2*)p.wa, nullptr, nullptr, p.nu, N, p.err);
-    }
-    return cudaGetLastError();
+    TcArgs a = tc_args(p, 0, (const float*)p.wpre);
+    a.x[0] = sigma;
+    a.out[0] = (float2*)p.wa;
+    return tc_launch_nt<0, 1, false>(a, st);
 }
 
-// P3 on the tensor cores: the column pass's B and C (pairs: one buffer of
-// {B, C} at wb; otherwise B at wb, C at wc) -> F_r, F_phi rows.
+// P3 on the tensor cores: the column pass's B and C (pairs: the {B, C} pairs
+// at wb; otherwise B at wb, C at wc) -> F_r, F_phi, weighted by wpost.
 cudaError_t launch_dft_c2r(const PlanView& p, float* Fr, float* Fp, cudaStream_t st)
 {
-    const int N = p.nphi, NT = tc_nt(N);
-    const dim3 grid((p.nu + TC_M - 1) / TC_M, N / NT);
-    const float* E = (const float*)p.tcm + 2 * (size_t)N * N;
-    const float4* P = (const float4*)p.wb;
-    const float2 *B = (const float2*)p.wb, *C = (const float2*)p.wc;
-    cudaError_t e;
-#define SG_TC_C2R(NTV, PR)                                                                                    \
-    do {                                                                                                      \
-        auto k = k_dft_tc<NTV, 1, PR>;                                                                        \
-        const size_t smem = tc_smem_bytes<NTV, 2>();                                                          \
-        if ((e = tc_set_smem(k, smem)) != cudaSuccess) return e;                                              \
-        k<<<grid, TC_M, smem, st>>>(nullptr, P, B, C, E, (const float*)p.wpost, nullptr, Fr, Fp, p.nu, N, p.err); \
-    } while (0)
-    if (NT == 64) {
-        if (p.pairs)
-            SG_TC_C2R(64, true);
-        else
-            SG_TC_C2R(64, false);
-    } else {
-        if (p.pairs)
-            SG_TC_C2R(32, true);
-        else
-            SG_TC_C2R(32, false);
-    }
-#undef SG_TC_C2R
-    return cudaGetLastError();
+    TcArgs a = tc_args(p, 1, (const float*)p.wpost);
+    a.pin = (const float4*)p.wb;
+    a.in[0] = (const float2*)p.wb;
+    a.in[1] = (const float2*)p.wc;
+    a.y[0] = Fr;
+    a.y[1] = Fp;
+    return p.pairs ? tc_launch_nt<1, 2, true>(a, st) : tc_launch_nt<1, 2, false>(a, st);
+}
+
+// P1b on the tensor cores: gF_r, gF_phi rows -> A, C weighted by wpost
+// (pairs: the {A, C} pairs into wb; otherwise A into wa, C into wc).
+cudaError_t launch_dft_r2c_adjoint(const PlanView& p, const float* gr, const float* gp, cudaStream_t st)
+{
+    TcArgs a = tc_args(p, 0, (const float*)p.wpost);
+    a.x[0] = gr;
+    a.x[1] = gp;
+    a.pout = (float4*)p.wb;
+    a.out[0] = (float2*)p.wa;
+    a.out[1] = (float2*)p.wc;
+    return p.pairs ? tc_launch_nt<0, 2, true>(a, st) : tc_launch_nt<0, 2, false>(a, st);
+}
+
+// P3b on the tensor cores: B (pairs: at wa; otherwise at wb) -> gsigma,
+// weighted by wpre.
+cudaError_t launch_dft_c2r_adjoint(const PlanView& p, float* gs, cudaStream_t st)
+{
+    TcArgs a = tc_args(p, 1, (const float*)p.wpre);
+    a.in[0] = (const float2*)(p.pairs ? p.wa : p.wb);
+    a.y[0] = gs;
+    return tc_launch_nt<1, 1, false>(a, st);
 }
 
 }  // namespace sg

@@ -2424,7 +2424,9 @@ cudaError_t launch_backward(const PlanView& p0, const T* gr, const T* gp, T* gs,
     if (ev && (err = cudaEventRecord(ev[0], st)) != cudaSuccess) return err;
     {
         PassRange range_("sg adjoint rows");
-        if (p.pairs) {  // (A, C) pairs into wb
+        if (sizeof(T) == 4 && p.tcm) {
+            if ((err = launch_dft_r2c_adjoint(p, (const float*)gr, (const float*)gp, st)) != cudaSuccess) return err;
+        } else if (p.pairs) {  // (A, C) pairs into wb
             const int nblk = p.nu / (2 * fr->slots);
             auto k = fr->bwd_rows;
             if ((err = set_smem(k, fr->r2c_smem, true)) != cudaSuccess) return err;
@@ -2481,7 +2483,9 @@ cudaError_t launch_backward(const PlanView& p0, const T* gr, const T* gp, T* gs,
     if (ev && (err = cudaEventRecord(ev[2], st)) != cudaSuccess) return err;
     {
         PassRange range_("sg adjoint inverse rows");
-        if (p.pairs) {  // B from wa
+        if (sizeof(T) == 4 && p.tcm) {
+            if ((err = launch_dft_c2r_adjoint(p, (float*)gs, st)) != cudaSuccess) return err;
+        } else if (p.pairs) {  // B from wa
             const int nblk = p.nu / (4 * fr->slots);
             auto k = fr->bwd_rows_inv;
             if ((err = set_smem(k, fr->c2r_smem, true)) != cudaSuccess) return err;

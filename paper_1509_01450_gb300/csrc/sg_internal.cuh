@@ -73,7 +73,7 @@ struct sg_plan {
     int wedge;
     void* wtab;         // working dtype, [4][nphi/2 + 1][nu]: Wr, Wphi, Vr, Vphi spectra (wedge.cu)
     void* wtmp;         // [nphi/2] complex values of the working dtype (16 B each allocated): the adjoint's per-mode sums
-    // the forward row passes as dense DFT-matrix products on the tensor cores
+    // the row passes as dense DFT-matrix products on the tensor cores
     // (sg_build_opts.short_dft = 1; FP32, 32 <= nphi <= 256)
     int short_dft;
     void* tcm;          // FP32 [4 nphi^2]: the split matrices of dft_tc_matrices
@@ -178,12 +178,14 @@ sg_status batch_prepare(const sg_batch_item* items, int n, cudaStream_t st);
 sg_status batch_tune(const sg_batch_item* items, int n, const char* path, cudaStream_t st, float ms_out[2]);
 void batch_forget_plan(const sg_plan* p);
 bool batch_eligible(const sg_plan* p);
-// dft_tc.cu: the forward row passes as tensor-core DFT-matrix products
+// dft_tc.cu: the row passes (forward and adjoint) as tensor-core DFT-matrix products
 bool dft_tc_supported(int nphi);
 size_t dft_tc_matrix_floats(int nphi);
 void dft_tc_matrices(int nphi, float* out);  // host: D then E, each [hi, lo][tile][chunk][NT x 32]
 cudaError_t launch_dft_r2c(const PlanView& p, const float* sigma, cudaStream_t st);
 cudaError_t launch_dft_c2r(const PlanView& p, float* Fr, float* Fp, cudaStream_t st);
+cudaError_t launch_dft_r2c_adjoint(const PlanView& p, const float* gr, const float* gp, cudaStream_t st);
+cudaError_t launch_dft_c2r_adjoint(const PlanView& p, float* gs, cudaStream_t st);
 // every device allocation of the library, through the sg_test_fail_alloc
 // hook, and its release (sg_test_live_allocations counts the difference)
 cudaError_t sg_malloc(void** ptr, size_t bytes);

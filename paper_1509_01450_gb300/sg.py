@@ -166,8 +166,9 @@ class Plan:
         radial_edges = 1: one-sided radial slopes at the first and last rows
         instead of ghost rows.  wedge = 1 (with radial_edges = 1): the origin
         wedge below the first row, whose densities forces_wedge takes.
-        short_dft = 1 (FP32, 32 <= N_phi <= 256): the forward row transforms
-        as split-TF32 DFT-matrix products on the tensor cores."""
+        short_dft = 1 (FP32, 32 <= N_phi <= 256): the row transforms of the
+        forward and adjoint calls as split-TF32 DFT-matrix products on the
+        tensor cores."""
         code = KERNEL_KINDS[kind] if isinstance(kind, str) else int(kind)
         opts = BuildOpts(rtol, weight_p, code, soften, n_tpz, radial_edges, wedge, short_dft)
         _check(lib().sg_kernels_build(self.handle, ctypes.byref(opts), _stream(stream)), "sg_kernels_build")

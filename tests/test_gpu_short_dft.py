@@ -1,14 +1,15 @@
 """The tensor-core DFT form of the short azimuthal transforms (build option
 short_dft: split-TF32 DFT-matrix products on tcgen05, FP32 accumulate)
 against the FP64 oracle at the FP32 bar, beside the FFT path, across the
-shapes it takes (N_phi 32 .. 256, partial 128-row tiles, one K chunk), with
-the column-pass options, the allocation-free and batched entry points, the
-refused configurations and a wait that gives up."""
+shapes it takes (N_phi 32 .. 256, partial 128-row tiles, one K chunk):
+forward and adjoint (the oracle's transposed sum, the dot identity, an
+autograd gradient), with the column-pass options, the allocation-free and
+batched entry points, the refused configurations and a wait that gives up."""
 import numpy as np
 import pytest
 
 import workloads
-from tests.errbounds import assert_close, rel_l2
+from tests.errbounds import assert_close, assert_close_1, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -180,3 +181,57 @@ def test_wait_that_gives_up_reports_a_timeout(torch_cuda):
     Fr, Fp = run(torch, tc, sigma)
     Gr, Gp = run(torch, fft, sigma)
     assert rel_l2(Fr, Fp, Gr, Gp) < FP32_TOL
+
+
+@pytest.mark.parametrize("nu,nphi", [(4, 32), (64, 128), (128, 64), (32, 256), (256, 256), (512, 32)])
+def test_adjoint_matches_oracle_transposed_sum(torch_cuda, oracle_mod, nu, nphi):
+    """P1b and P3b on the tensor cores: gsigma against the oracle's transposed
+    direct sum on random gradients, beside the FFT adjoint."""
+    torch = torch_cuda
+    tc, fft, u_min, du = plans(nu, nphi)
+    Kr, Kp = kernels(oracle_mod, nu, nphi, du)
+    gr, gp = workloads.random_field(nu, nphi, 41), workloads.random_field(nu, nphi, 42)
+    ref = oracle_mod.direct_sum_T(gr, gp, Kr, Kp)
+    tgr = torch.tensor(gr, dtype=torch.float32, device="cuda")
+    tgp = torch.tensor(gp, dtype=torch.float32, device="cuda")
+    g = tc.backward(tgr, tgp)
+    tc.check()
+    h = fft.backward(tgr, tgp)
+    got, other = g.double().cpu().numpy(), h.double().cpu().numpy()
+    e_tc = rel_l2(got, 0 * got, ref, 0 * ref)
+    e_fft = rel_l2(other, 0 * other, ref, 0 * ref)
+    print(f"short_dft adjoint {nu}x{nphi}: rel-L2 vs oracle {e_tc:.2e} (FFT rows {e_fft:.2e})")
+    assert_close_1(got, ref, FP32_TOL, what=f"short_dft adjoint {nu}x{nphi}")
+    assert rel_l2(got, 0 * got, other, 0 * other) < FP32_TOL
+
+
+def test_adjoint_dot_identity_and_gradient(torch_cuda):
+    """<F(sigma), g> = <sigma, F^T(g)> through the tensor-core passes, and
+    the autograd function's gradient of a weighted force loss against the FFT
+    plan's."""
+    torch = torch_cuda
+    from paper_1509_01450_gb300 import self_gravity
+
+    nu, nphi = 512, 256
+    tc, fft, u_min, du = plans(nu, nphi)
+    sigma = density(nu, nphi, u_min, du, 13)
+    gr, gp = workloads.random_field(nu, nphi, 51), workloads.random_field(nu, nphi, 52)
+    s = torch.tensor(sigma, dtype=torch.float32, device="cuda")
+    Fr, Fp = tc.forces(s)
+    gs = tc.backward(torch.tensor(gr, dtype=torch.float32, device="cuda"),
+                     torch.tensor(gp, dtype=torch.float32, device="cuda"))
+    tc.check()
+    lhs = float(np.sum(Fr.double().cpu().numpy() * gr) + np.sum(Fp.double().cpu().numpy() * gp))
+    rhs = float(np.sum(sigma * gs.double().cpu().numpy()))
+    assert abs(lhs - rhs) <= 1e-5 * (abs(lhs) + abs(rhs))
+
+    def grad(plan):
+        x = s.clone().requires_grad_(True)
+        Fr, Fp = self_gravity(x, plan)
+        w = torch.linspace(0.5, 1.5, nu, device="cuda")[:, None]
+        loss = (w * (Fr - 1.0) ** 2).sum() + (w * Fp ** 2).sum()
+        loss.backward()
+        return x.grad.double().cpu().numpy()
+
+    a, b = grad(tc), grad(fft)
+    assert rel_l2(a, 0 * a, b, 0 * b) < FP32_TOL
