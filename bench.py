@@ -40,6 +40,9 @@ BYTES_PER_CELL = {"rows": 8.0, "cols": 20.0, "inv_rows": 16.0}
 # DRAM bytes (read + write) of one launch of the dominant pass at 2048 x 4096
 # FP32, from one ncu capture of the bench command itself, valid only for the
 # kernel sources it was taken on (kernel_sources_sha below).
+# dense TF32 tensor rate per dense BF16 rate (nominal 1.1 / 2.25 PFLOP/s on GB300)
+TF32_PER_BF16 = 1.1 / 2.25
+
 PASS_TRAFFIC = {"pass": "cols", "sources_sha256": "966bb673635938c4", "bytes_per_launch": 100.792576e6 + 7.342848e6}
 
 
@@ -332,6 +335,50 @@ def batch_throughput(torch, dev, flush, peak_gbs, n_disks: int = 256, seed: int 
             "graph_path_roofline_frac": bytes_ / (graph_ms * 1e-3) / 1e9 / peak_gbs}
 
 
+def short_dft_measure(torch, dev, timed, n, nu: int = 4096, nphi: int = 256):
+    """The short_dft option (the row transforms as split-TF32 DFT-matrix
+    products on tcgen05) beside the FFT rows on an nu x nphi lognormal disk:
+    forward and adjoint step times (L2 flushed before each), the row passes'
+    CUDA-event times, their tensor throughput, and the two forms' agreement."""
+    import workloads
+    from paper_1509_01450_gb300 import Plan
+
+    u_min, du = workloads.grid_params(nu, R_IN, R_OUT)
+    r, phi = workloads.centres(nu, nphi, u_min, du)
+    s = torch.tensor(workloads.lognormal_disk(r, phi, SEED), dtype=torch.float32, device=dev)
+    gr, gp = torch.randn_like(s), torch.randn_like(s)
+    out = {"workload": f"lognormal-grf-{nu}x{nphi}", "unit": "cells/s"}
+    res = {}
+    for tag, opt in (("tensor_cores", 1), ("fft", 0)):
+        plan = Plan(nu, nphi, u_min, du, 1.0, "float32").build(short_dft=opt)
+        Fr, Fp, gs = torch.empty_like(s), torch.empty_like(s), torch.empty_like(s)
+        for _ in range(3):
+            plan.forces(s, Fr, Fp)
+            plan.backward(gr, gp, gs)
+        fwd = timed(lambda: plan.forces(s, Fr, Fp), n)
+        bwd = timed(lambda: plan.backward(gr, gp, gs), n)
+        passes = [plan.forces_timed(s, Fr, Fp) for _ in range(n)]
+        plan.check()
+        res[tag] = (Fr.double(), Fp.double())
+        out[tag] = {"value": nu * nphi / (fwd * 1e-3), "ms_per_step": fwd, "backward_ms_per_step": bwd,
+                    "rows_ms": statistics.mean(p[0] for p in passes), "inv_rows_ms": statistics.mean(p[2] for p in passes)}
+    (a, b), (c, d) = res["tensor_cores"], res["fft"]
+    out["rel_l2_tensor_cores_vs_fft"] = math.sqrt(float(((a - c) ** 2).sum() + ((b - d) ** 2).sum()) /
+                                                  float((c ** 2).sum() + (d ** 2).sum()))
+    # tensor work per forward step: the DFT products (2 nu N^2 flops each; P1
+    # one, P3 two), each executed as three TF32 products (hi hi, hi lo, lo hi)
+    tc = out["tensor_cores"]
+    flops = {"rows": 2.0 * nu * nphi * nphi, "inv_rows": 2 * 2.0 * nu * nphi * nphi}
+    peaks, kind = measured_peaks()
+    tf32_peak = float(peaks.get("bf16_tflops", 1900.0)) * TF32_PER_BF16
+    for k in ("rows", "inv_rows"):
+        t = tc[k + "_ms"] * 1e-3
+        tc[k + "_tflops_executed"] = 3 * flops[k] / t / 1e12
+        tc[k + "_frac_of_tf32_peak"] = 3 * flops[k] / t / 1e12 / tf32_peak
+    out["tf32_peak_tflops"] = {"value": tf32_peak, "from": f"bf16 {kind} x {TF32_PER_BF16:.3f} (nominal TF32 / BF16)"}
+    return out
+
+
 def run_passes_only(args):
     """The forward and adjoint passes of the bench workload alone, for an
     external profiler: one plan, W + K forward steps, then W + K adjoint
@@ -347,12 +394,12 @@ def run_passes_only(args):
     dev = torch.device("cuda", 0)
     u_min, du = workloads.grid_params(NU, R_IN, R_OUT)
     r, phi = workloads.centres(NU, NPHI, u_min, du)
-    plan = Plan(NU, NPHI, u_min, du, 1.0, "float32").build()
+    plan = Plan(NU, NPHI, u_min, du, 1.0, "float32").build(short_dft=1 if args.short_dft else 0)
     sigma = torch.tensor(workloads.lognormal_disk(r, phi, SEED), dtype=torch.float32, device=dev)
     Fr, Fp = torch.empty_like(sigma), torch.empty_like(sigma)
     gs = torch.empty_like(sigma)
     flush = L2Flush(torch, dev)
-    out = {"workload": WORKLOAD, "mode": "passes only"}
+    out = {"workload": WORKLOAD, "mode": "passes only", "short_dft": bool(args.short_dft)}
     for name, fn in (("forward_ms", lambda: plan.forces(sigma, Fr, Fp)), ("backward_ms", lambda: plan.backward(Fr, Fp, gs))):
         for _ in range(args.warmup):
             flush()
@@ -559,6 +606,10 @@ def run_ours(args):
         variants[name] = entry
         del pv
 
+    # ---- short azimuthal transforms on the tensor cores (build option
+    # short_dft) beside the FFT rows, on the largest N_phi = 256 grid ---------
+    short = short_dft_measure(torch, dev, timed, max(20, min(args.steps, 200)))
+
     # ---- end to end through the C ABI with host buffers --------------------
     sig_h = torch.tensor(sigma_np, dtype=torch.float32).pin_memory()
     fr_h = torch.empty_like(sig_h).pin_memory()
@@ -611,6 +662,7 @@ def run_ours(args):
             "build_s": build_s,
             "build_options": variants,
             "batched": batch,
+            "short_dft": short,
             "e2e": {"value": e2e_value, "unit": "cells/s", "ms_per_step": e2e_ms,
                     "h2d_bytes_per_step": cells * 4, "d2h_bytes_per_step": 2 * cells * 4,
                     "host_link": link, "frac_of_link_bound": link["bound_ms_per_step"] / e2e_ms},
@@ -638,6 +690,8 @@ def main():
     ap.add_argument("--size", default=None, help="NUxNPHI override (profiling runs only; not a bench line)")
     ap.add_argument("--passes-only", action="store_true",
                     help="time only the forward and adjoint passes (for profiler captures; not a bench line)")
+    ap.add_argument("--short-dft", action="store_true",
+                    help="with --passes-only: the plan's row transforms on the tensor cores (N_phi <= 256)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -48,7 +48,8 @@ namespace sg {
 
 namespace {
 
-constexpr int TC_M = 128;   // rows per CTA (tensor-memory lanes), one thread per row
+constexpr int TC_M = 128;   // rows per CTA (tensor-memory lanes)
+constexpr int TC_T = 256;   // threads per CTA: two per row, each staging half of a chunk
 constexpr int TC_KC = 32;   // K values per staged chunk
 constexpr int TC_ABYTES = TC_M * TC_KC * 4;  // one A operand part of one chunk: 16 KB
 // Main accumulators per product.  The tensor core's FP32 accumulation loses
@@ -57,6 +58,7 @@ constexpr int TC_ABYTES = TC_M * TC_KC * 4;  // one A operand part of one chunk:
 // 2^-11 of the main ones, into one of their own) divides the steps each one
 // takes, and the epilogue adds them with rounding to nearest.
 constexpr int TC_SLOTS = 3;
+constexpr int TC_MAX_CHUNKS = 8;  // N <= 256
 
 __host__ __device__ constexpr uint32_t tc_pow2(int n)
 {
@@ -73,17 +75,19 @@ __host__ __device__ constexpr int tc_mbytes()
     return NT * TC_KC * 4;  // one matrix part of one chunk
 }
 
-// bytes of one staging buffer: G row operands (hi, lo each) and the matrix (hi, lo)
-template <int NT, int G>
-__host__ __device__ constexpr int tc_buf_bytes()
+// bytes of one row staging buffer: G row operands, hi and lo parts each
+template <int G>
+__host__ __device__ constexpr int tc_rowbuf_bytes()
 {
-    return 2 * G * TC_ABYTES + 2 * tc_mbytes<NT>();
+    return 2 * G * TC_ABYTES;
 }
 
-template <int NT, int G>
-constexpr size_t tc_smem_bytes()
+// the CTA's shared memory: its column tile of the matrix (all N / KC chunks,
+// hi and lo), NB row staging buffers, alignment slack
+template <int NT, int G, int NB>
+size_t tc_smem_bytes(int N)
 {
-    return 2 * (size_t)tc_buf_bytes<NT, G>() + 1024;  // two buffers, alignment slack
+    return (size_t)(N / TC_KC) * 2 * tc_mbytes<NT>() + NB * (size_t)tc_rowbuf_bytes<G>() + 1024;
 }
 
 __device__ __forceinline__ float4 tc_hi(float4 v)
@@ -131,12 +135,12 @@ struct TcArgs {
 //   DIR 1 (P3, P3b): half spectra -> rows.  Forward G = 2: B, C (PAIRS: the
 //     {B, C} pairs) -> F_r, F_phi.  Adjoint G = 1: B -> gsigma.
 // Outputs are scaled by the row weight w_i.  Grid: (ceil(nu / 128), N / NT);
-// block 128 threads, thread r owning row blockIdx.x 128 + r and tensor-memory
-// lane r.
-template <int NT, int DIR, int G, bool PAIRS>
-__global__ void __launch_bounds__(TC_M, 1) k_dft_tc(const TcArgs a)
+// block 256 threads: threads r and r + 128 stage the two halves of each chunk
+// of row blockIdx.x 128 + r, whose results sit in tensor-memory lane r.
+template <int NT, int DIR, int G, bool PAIRS, int NB>
+__global__ void __launch_bounds__(TC_T, 1) k_dft_tc(const TcArgs a)
 {
-    constexpr int BUF = tc_buf_bytes<NT, G>();
+    constexpr int RB = tc_rowbuf_bytes<G>();
     constexpr int MB = tc_mbytes<NT>();
     // accumulators: TC_SLOTS for the hi hi terms (chunk c into slot c mod S),
     // one more for the two correction terms, each G x NT columns
@@ -145,20 +149,27 @@ __global__ void __launch_bounds__(TC_M, 1) k_dft_tc(const TcArgs a)
     int* const err = a.err;
     const unsigned long long wlim = sg_wait_budget(err);
     extern __shared__ __align__(1024) unsigned char smraw[];
-    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ __align__(8) uint64_t bar[NB];              // per row buffer: its chunk's MMAs have completed
+    __shared__ __align__(8) uint64_t lbar[TC_MAX_CHUNKS];  // per chunk: its matrix parts have landed
     __shared__ uint32_t tbase_s;
     unsigned char* const area = reinterpret_cast<unsigned char*>(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
-    const int r = threadIdx.x, warp = r >> 5;
+    const int r = threadIdx.x & (TC_M - 1), h = threadIdx.x / TC_M, warp = threadIdx.x >> 5;
     const int i = blockIdx.x * TC_M + r;
     const bool row_ok = i < nu;
-    const int ct = blockIdx.y, nct = N / NT, nch = N / TC_KC;
+    const int ct = blockIdx.y, nch = N / TC_KC;
+    constexpr int QH = TC_KC / 8;  // float4s of one row's half chunk
+    // the matrix's stored tiles are LNT = min(N, 64) columns wide; a CTA of
+    // NT = 32 columns takes half of one, which is contiguous
+    const int LNT = N < 64 ? N : 64;
+    const size_t mat_part = (size_t)N * N;
+    unsigned char* const rows_area = area + (size_t)nch * 2 * MB;
     if (warp == 0) {
         sg_tc_alloc(&tbase_s, NCOLS);
         sg_tc_relinquish();
     }
-    if (r == 0) {
-        sg_mbar_init(&bar[0], 1);
-        sg_mbar_init(&bar[1], 1);
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < NB; b++) sg_mbar_init(&bar[b], 1);
+        for (int c = 0; c < nch; c++) sg_mbar_init(&lbar[c], 1);
     }
     sg_tc_fence_before();
     __syncthreads();
@@ -167,113 +178,144 @@ __global__ void __launch_bounds__(TC_M, 1) k_dft_tc(const TcArgs a)
     const uint32_t idesc = sg_tc_idesc_tf32(TC_M, NT);
     const int S = nch < TC_SLOTS ? nch : TC_SLOTS;  // main accumulators in use
     const float wi = row_ok ? __ldg(&a.w[i]) : 0.f;
-    bool ok = true;
-    int issued = 0;  // chunks whose MMAs have been committed
-    for (int c = 0; c < nch && ok; c++) {
-        unsigned char* const buf = area + (size_t)(c & 1) * BUF;
-        float* const ahi = reinterpret_cast<float*>(buf);  // [g][hi, lo] row operands, then the matrix
-        float* const mhi = reinterpret_cast<float*>(buf + 2 * G * TC_ABYTES);
-        float* const mlo = mhi + MB / 4;
-        // this chunk's row values into registers first, so that their loads
-        // overlap the wait for the buffer: v[g KC / 4 + q] = values 4 q .. 4 q + 3
-        float4 v[G * TC_KC / 4];
+    // the whole column tile of the matrix, one pair of bulk copies per chunk,
+    // each chunk on its own barrier so that the first MMAs need only the first
+    if (threadIdx.x == 0) {
+        const uint64_t keep = sg_policy_evict_last();  // every CTA of the column tile reads it
+        const size_t tile0 = (size_t)(ct * NT / LNT), sub = (size_t)(ct * NT % LNT) * TC_KC;
+        for (int c = 0; c < nch; c++) {
+            float* const dh = reinterpret_cast<float*>(area + (size_t)c * 2 * MB);
+            const float* const gh = a.mat + (tile0 * nch + c) * ((size_t)LNT * TC_KC) + sub;
+            SG_IF_OK(tile0 * nch + c < (size_t)(N / LNT) * nch, err, 403) {
+                sg_mbar_expect_tx(&lbar[c], 2 * MB);
+                sg_bulk_g2s_hint(dh, gh, MB, &lbar[c], keep);
+                sg_bulk_g2s_hint(dh + MB / 4, gh + mat_part, MB, &lbar[c], keep);
+            }
+        }
+    }
+    // this thread's half of chunk c of row i: v[g QH + q] = values
+    // KC h / 2 + 4 q .. + 3 of product g
+    auto load_rows = [&](int c, float4 (&v)[G * QH]) {
         if constexpr (DIR == 0) {
 #pragma unroll
             for (int g = 0; g < G; g++) {
-                const float4* src = reinterpret_cast<const float4*>(a.x[g] + (size_t)(row_ok ? i : 0) * N + c * TC_KC);
+                const float4* src = reinterpret_cast<const float4*>(a.x[g] + (size_t)(row_ok ? i : 0) * N +
+                                                                    c * TC_KC + h * (TC_KC / 2));
 #pragma unroll
-                for (int q = 0; q < TC_KC / 4; q++)
-                    v[g * (TC_KC / 4) + q] = row_ok ? __ldg(src + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+                for (int q = 0; q < QH; q++)
+                    v[g * QH + q] = row_ok ? __ldg(src + q) : make_float4(0.f, 0.f, 0.f, 0.f);
             }
         } else {
-            // modes c KC / 2 .. + KC / 2 - 1 of row i, two per float4
-            const int m0 = c * (TC_KC / 2);
+            // modes c KC / 2 + h KC / 4 .. + KC / 4 - 1 of row i, two per float4
+            const int m0 = c * (TC_KC / 2) + h * (TC_KC / 4);
 #pragma unroll
-            for (int q = 0; q < TC_KC / 4; q++) {
+            for (int q = 0; q < QH; q++) {
 #pragma unroll
-                for (int g = 0; g < G; g++) v[g * (TC_KC / 4) + q] = make_float4(0.f, 0.f, 0.f, 0.f);
+                for (int g = 0; g < G; g++) v[g * QH + q] = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (row_ok) {
                     const size_t e0 = (size_t)(m0 + 2 * q) * nu + i, e1 = e0 + nu;
                     if constexpr (PAIRS && G == 2) {
                         const float4 p0 = __ldg(a.pin + e0), p1 = __ldg(a.pin + e1);
                         v[q] = make_float4(p0.x, p0.y, p1.x, p1.y);
-                        v[TC_KC / 4 + q] = make_float4(p0.z, p0.w, p1.z, p1.w);
+                        v[QH + q] = make_float4(p0.z, p0.w, p1.z, p1.w);
                     } else {
 #pragma unroll
                         for (int g = 0; g < G; g++) {
                             const float2 b0 = __ldg(a.in[g] + e0), b1 = __ldg(a.in[g] + e1);
-                            v[g * (TC_KC / 4) + q] = make_float4(b0.x, b0.y, b1.x, b1.y);
+                            v[g * QH + q] = make_float4(b0.x, b0.y, b1.x, b1.y);
                         }
                     }
                 }
             }
         }
-        if (c >= 2) {  // the MMAs of chunk c - 2 read this buffer
-            bool landed = false;
-            const bool in_time = sg_mbar_wait_bounded(&bar[c & 1], ((c - 2) >> 1) & 1, err, 1, wlim, &landed);
-            if (__syncthreads_or(!in_time)) {
-                ok = false;
-                break;
-            }
+    };
+    bool ok = true;
+    int issued = 0;   // chunks whose MMAs have been committed
+    int landed = -1;  // the last chunk whose matrix copy was waited for
+    // One chunk: rows c (in cur) staged into row buffer c mod NB while the
+    // rows of chunk c + 2 load into nxt (those of c + 1 are in flight already;
+    // with two buffers the MMAs of chunk c - 1 run meanwhile); then the MMAs
+    // of chunk c.  False if a wait gave up.
+    auto chunk = [&](int c, float4 (&cur)[G * QH], float4 (&nxt)[G * QH]) -> bool {
+        float* const ahi = reinterpret_cast<float*>(rows_area + (size_t)(c % NB) * RB);  // [g][hi, lo]
+        if (c + 2 < nch) load_rows(c + 2, nxt);
+        if (c >= NB) {  // row buffer c mod NB was read by the MMAs of chunk c - NB
+            const bool in_time = sg_mbar_wait_bounded(&bar[c % NB], ((c / NB) - 1) & 1, err, 1, wlim);
+            if (__syncthreads_or(!in_time)) return false;
         }
 #pragma unroll
         for (int g = 0; g < G; g++) {
             float* hi = ahi + (size_t)g * 2 * (TC_ABYTES / 4);
             float* lo = hi + TC_ABYTES / 4;
 #pragma unroll
-            for (int q = 0; q < TC_KC / 4; q++) tc_stage4(hi, lo, r, 4 * q, v[g * (TC_KC / 4) + q]);
-        }
-        // the matrix chunk: both parts, already in the core-matrix layout
-        {
-            const float4* mh = reinterpret_cast<const float4*>(a.mat + ((size_t)ct * nch + c) * (MB / 4));
-            const float4* ml = reinterpret_cast<const float4*>(a.mat + ((size_t)(nct + ct) * nch + c) * (MB / 4));
-            float4* dh = reinterpret_cast<float4*>(mhi);
-            float4* dl = reinterpret_cast<float4*>(mlo);
-#pragma unroll
-            for (int q = r; q < MB / 16; q += TC_M) {
-                dh[q] = __ldg(mh + q);
-                dl[q] = __ldg(ml + q);
-            }
+            for (int q = 0; q < QH; q++) tc_stage4(hi, lo, r, h * (TC_KC / 2) + 4 * q, cur[g * QH + q]);
         }
         sg_fence_proxy_async_smem();  // the stores above, for the tensor core's reads
-        __syncthreads();
-        if (r == 0) {
+        {
+            const bool in_time = sg_mbar_wait_bounded(&lbar[c], 0, err, 1, wlim);
+            landed = c;
+            if (__syncthreads_or(!in_time)) return false;
+        }
+        if (threadIdx.x == 0) {
             sg_tc_fence_after();
-            const uint32_t mh_a = sg_smem_u32(mhi), ml_a = sg_smem_u32(mlo);
+            // descriptors of the chunk's first K step; a step of 8 values
+            // (256 bytes) adds 16 to the start-address field
+            const uint64_t bh0 = sg_tc_smem_desc(sg_smem_u32(area + (size_t)c * 2 * MB), 128, 1024);
+            const uint64_t bl0 = bh0 + (MB >> 4);
+            const uint64_t ah0 = sg_tc_smem_desc(sg_smem_u32(ahi), 128, 1024);
+            const uint32_t slot = (uint32_t)(c % S);
+            // each accumulator's MMAs back to back: the main slot's K steps,
+            // then the corrections'
 #pragma unroll
-            for (int s = 0; s < TC_KC / 8; s++) {  // K = 8 values (two core matrices) per MMA
-                const uint64_t bh = sg_tc_smem_desc(mh_a + 256 * s, 128, 1024);
-                const uint64_t bl = sg_tc_smem_desc(ml_a + 256 * s, 128, 1024);
+            for (int g = 0; g < G; g++) {
+                const uint64_t ah = ah0 + (uint64_t)((g * 2 * TC_ABYTES) >> 4);
+                const uint64_t al = ah + (TC_ABYTES >> 4);
+                const uint32_t dm = tbase + (slot * G + g) * NT;                  // this chunk's main slot
+                const uint32_t dc = tbase + (uint32_t)((TC_SLOTS * G + g) * NT);  // the corrections
 #pragma unroll
-                for (int g = 0; g < G; g++) {
-                    const uint32_t ah_a = sg_smem_u32(ahi + (size_t)g * 2 * (TC_ABYTES / 4)) + 256 * s;
-                    const uint64_t ah = sg_tc_smem_desc(ah_a, 128, 1024);
-                    const uint64_t al = sg_tc_smem_desc(ah_a + TC_ABYTES, 128, 1024);
-                    const uint32_t dm = tbase + (uint32_t)(((c % S) * G + g) * NT);  // this chunk's main slot
-                    const uint32_t dc = tbase + (uint32_t)((TC_SLOTS * G + g) * NT);  // the corrections
-                    sg_tc_mma_tf32(dm, ah, bh, idesc, (c >= S || s > 0) ? 1u : 0u);
-                    sg_tc_mma_tf32(dc, ah, bl, idesc, (c > 0 || s > 0) ? 1u : 0u);
-                    sg_tc_mma_tf32(dc, al, bh, idesc, 1u);
+                for (int s = 0; s < TC_KC / 8; s++)  // K = 8 values (two core matrices) per MMA
+                    sg_tc_mma_tf32(dm, ah + 16 * s, bh0 + 16 * s, idesc, (c >= S || s > 0) ? 1u : 0u);
+#pragma unroll
+                for (int s = 0; s < TC_KC / 8; s++) {
+                    sg_tc_mma_tf32(dc, ah + 16 * s, bl0 + 16 * s, idesc, (c > 0 || s > 0) ? 1u : 0u);
+                    sg_tc_mma_tf32(dc, al + 16 * s, bh0 + 16 * s, idesc, 1u);
                 }
             }
-            sg_tc_commit(&bar[c & 1]);
+            sg_tc_commit(&bar[c % NB]);
         }
         issued = c + 1;
+        return true;
+    };
+    {
+        // three register sets in turn: the rows arrive two chunks after
+        // their loads are issued, and no prefetched value is moved
+        float4 va[G * QH], vb[G * QH], vc[G * QH];
+        load_rows(0, va);
+        if (nch > 1) load_rows(1, vb);
+        for (int c = 0; c < nch && ok; c += 3) {
+            ok = chunk(c, va, vc);
+            if (ok && c + 1 < nch) ok = chunk(c + 1, vb, va);
+            if (ok && c + 2 < nch) ok = chunk(c + 2, vc, vb);
+        }
     }
+    // matrix copies still in flight after a wait that gave up land before
+    // the shared memory is given back
+    for (int c = landed + 1; c < nch; c++) sg_mbar_wait_bounded(&lbar[c], 0, err, 1, wlim);
     // the last committed chunk's completion covers every MMA issued before it;
     // after a wait that gave up this is the one more bounded wait for the
     // MMAs still in flight, before the tensor memory is freed
     if (issued > 0) {
         const int c = issued - 1;
-        bool landed = false;
-        const bool in_time = sg_mbar_wait_bounded(&bar[c & 1], (c >> 1) & 1, err, 1, wlim, &landed);
+        const bool in_time = sg_mbar_wait_bounded(&bar[c % NB], (c / NB) & 1, err, 1, wlim);
         if (__syncthreads_or(!in_time)) ok = false;
     }
     if (ok) {
         sg_tc_fence_after();
-        const uint32_t lane_base = tbase + ((uint32_t)(warp * 32) << 16);
+        // warps w and w + 4 read the same 32 lanes (rows): the two halves of
+        // the CTA take alternate blocks of 32 columns
+        const uint32_t lane_base = tbase + ((uint32_t)((warp & 3) * 32) << 16);
 #pragma unroll
-        for (int cb = 0; cb < NT / 32; cb++) {
+        for (int cb = h; cb < NT / 32; cb += 2) {
             // each product's sum of accumulators, in FP32 with rounding to
             // nearest: the corrections first, then the main slots
             float y[G][32];
@@ -380,22 +422,26 @@ void dft_tc_matrices(int N, float* out)
     }
 }
 
-template <int NT, int DIR, int G, bool PAIRS>
+template <int NT, int DIR, int G, bool PAIRS, int NB>
 static cudaError_t tc_launch(const TcArgs& a, cudaStream_t st)
 {
-    auto k = k_dft_tc<NT, DIR, G, PAIRS>;
-    const size_t smem = tc_smem_bytes<NT, G>();
+    auto k = k_dft_tc<NT, DIR, G, PAIRS, NB>;
+    const size_t smem = tc_smem_bytes<NT, G, NB>(a.N);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const dim3 grid((a.nu + TC_M - 1) / TC_M, a.N / NT);
-    k<<<grid, TC_M, smem, st>>>(a);
+    k<<<grid, TC_T, smem, st>>>(a);
     return cudaGetLastError();
 }
 
+// columns per CTA: 64 (32 for rows of 32); two row buffers, but one for two
+// products of rows of 256, whose 128 KB matrix tile leaves room for one only
 template <int DIR, int G, bool PAIRS>
 static cudaError_t tc_launch_nt(const TcArgs& a, cudaStream_t st)
 {
-    return tc_nt(a.N) == 64 ? tc_launch<64, DIR, G, PAIRS>(a, st) : tc_launch<32, DIR, G, PAIRS>(a, st);
+    if (a.N < 64) return tc_launch<32, DIR, G, PAIRS, 2>(a, st);
+    if (G == 2 && a.N > 128) return tc_launch<64, DIR, G, PAIRS, 1>(a, st);
+    return tc_launch<64, DIR, G, PAIRS, 2>(a, st);
 }
 
 static TcArgs tc_args(const PlanView& p, int dir, const float* w)
