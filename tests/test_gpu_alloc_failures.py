@@ -6,6 +6,8 @@ failing.  Each must return SG_ERR_ALLOC, release what it took (the
 library's count of live allocations returns to where it was), and leave the
 plan usable: a rebuilt
 or reloaded plan gives the same forces as one that never failed."""
+import gc
+
 import pytest
 
 import workloads
@@ -44,6 +46,9 @@ def _fails_at_each(torch, sg, L, fn, n, make=None, after=None):
     and every allocation released once the objects are gone (the library's
     own count of live allocations; the device's free memory also moves with
     the CUDA driver's and torch's own caches)."""
+    # plans that earlier tests left in reference cycles (a traceback keeps
+    # its frames) are released now, not by a collection inside the loop
+    gc.collect()
     torch.cuda.synchronize()
     live0 = L.sg_test_live_allocations()
     for k in range(n):
@@ -59,6 +64,7 @@ def _fails_at_each(torch, sg, L, fn, n, make=None, after=None):
             after(obj)
         if obj is not None:
             obj.close()
+    gc.collect()
     torch.cuda.synchronize()
     assert L.sg_test_live_allocations() == live0
 
