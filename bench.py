@@ -279,7 +279,7 @@ def batch_throughput(torch, dev, flush, peak_gbs, n_disks: int = 256, seed: int 
     import tempfile
 
     import workloads
-    from paper_1509_01450_gb300 import Plan, SgError, batch_tune, forces_batched
+    from paper_1509_01450_gb300 import Plan, SgError, batch_prepare, batch_tune, forces_batched
 
     disks = workloads.batch_disks(n_disks, seed)
     plans = {}
@@ -325,12 +325,35 @@ def batch_throughput(torch, dev, flush, peak_gbs, n_disks: int = 256, seed: int 
     g.replay()
     torch.cuda.synchronize()
     graph_ms = timed(g.replay)
+    # the same batch with its N_phi = 256 disks on short_dft plans (their rows
+    # as tensor-core DFT products, two batched launches beside the persistent
+    # kernels), replayed from a CUDA graph
+    tcp = {}
+    for d in disks:
+        if d.nphi == 256 and (d.nu, d.nphi) not in tcp:
+            tcp[(d.nu, d.nphi)] = Plan(d.nu, d.nphi, d.u_min, d.du, 1.0, "float32").build(short_dft=1)
+    items_tc = [(tcp.get((d.nu, d.nphi), plans[(d.nu, d.nphi)]), s, a, b) for d, s, (a, b) in zip(disks, sig, outs)]
+    tc_ms = None
+    try:
+        batch_prepare(items_tc)
+        forces_batched(items_tc, stream=stream)
+        g2 = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g2):
+            forces_batched(items_tc, stream=torch.cuda.current_stream())
+        g2.replay()
+        torch.cuda.synchronize()
+        tc_ms = timed(g2.replay)
+    except SgError:
+        pass
     # the three passes' algorithmic bytes over all disks, against the copy peak
     bytes_ = sum(BYTES_PER_CELL.values()) * cells
     return {"workload": f"{n_disks} disks, seed {seed}, {len(plans)} sizes, {cells} cells", "unit": "cells/s",
             "value": cells / (eager_ms * 1e-3), "ms": eager_ms,
             "graph_value": cells / (graph_ms * 1e-3), "graph_ms": graph_ms,
-            "persistent": persistent, "launches": 1 if persistent else 3 * n_disks,
+            "short_dft_rows_256": None if tc_ms is None else {
+                "graph_ms": tc_ms, "graph_value": cells / (tc_ms * 1e-3), "launches": 5,
+                "disks": sum(1 for d in disks if d.nphi == 256)},
+            "persistent": persistent, "launches": 3 if persistent else 3 * n_disks,
             "tune_ms": {"default": tune_ms[0], "tuned": tune_ms[1]} if tune_ms else None,
             "graph_path_roofline_frac": bytes_ / (graph_ms * 1e-3) / 1e9 / peak_gbs}
 

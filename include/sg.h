@@ -165,8 +165,11 @@ typedef struct {
                       (hi hi + hi lo + lo hi), FP32 accumulation, so the
                       result keeps FP32 accuracy.  Only SG_F32 plans with
                       32 <= N_phi <= 256 (else SG_ERR_UNSUPPORTED).  The
-                      option is not kept by sg_plan_save, and sg_forces_batched
-                      runs such plans' items through per-plan launches */
+                      option is not kept by sg_plan_save.  In sg_forces_batched
+                      such plans with N_phi = 256 keep the persistent path:
+                      their row passes run as two batched tensor-core launches
+                      (before and after the column kernel), their column items
+                      in the persistent column kernel */
 } sg_build_opts;
 
 /*

@@ -237,7 +237,7 @@ static int row_slots(int lg) { return SG_BATCH_THREADS / ((1 << lg) / 16); }
 
 bool batch_eligible(const sg_plan* p)
 {
-    if (p->dtype != SG_F32 || !p->built || p->edges || p->wedge || p->short_dft || !p->have_imaps) return false;
+    if (p->dtype != SG_F32 || !p->built || p->edges || p->wedge || !p->have_imaps) return false;
     const int lgr = sg_ilog2(p->nphi), lgc = sg_ilog2(2 * p->nu);
     if (lgr < 8 || lgr > 12 || lgc < 8 || lgc > 12) return false;
     return p->nu % (4 * row_slots(lgr)) == 0;
@@ -270,6 +270,11 @@ struct BatchList {
     int2* d_items = nullptr;  // the three item lists, one after the other
     int* d_ctrl = nullptr;    // the three queue heads
     unsigned char* d_work = nullptr;  // each item's half spectra and pairs (12 bytes per cell)
+    // items whose plan takes the row passes on the tensor cores (short_dft,
+    // rows of 256): their P1 arguments, then their P3 arguments, one batched
+    // launch each; the persistent kernels take only their column items
+    TcArgs* d_tc = nullptr;
+    int ntc = 0, tc_max_nu = 0;
 };
 
 static std::mutex g_batch_mu;
@@ -283,6 +288,8 @@ static void free_list(BatchList& b)
     sg_free(b.d_items);
     sg_free(b.d_ctrl);
     sg_free(b.d_work);
+    sg_free(b.d_tc);
+    b.d_tc = nullptr;
     b.d_disks = nullptr;
     b.d_items = nullptr;
     b.d_ctrl = nullptr;
@@ -305,13 +312,16 @@ static std::vector<const void*> list_key(const sg_batch_item* items, int n)
 static std::string batch_signature(const sg_batch_item* items, int n, int sms)
 {
     std::vector<std::pair<int, int>> sz;
-    for (int b = 0; b < n; b++) sz.push_back({items[b].plan->nu, items[b].plan->nphi});
+    // a plan with tensor-core rows (short_dft) counts as its own size class ("t")
+    for (int b = 0; b < n; b++)
+        sz.push_back({items[b].plan->nu, 2 * items[b].plan->nphi + (items[b].plan->short_dft ? 1 : 0)});
     std::sort(sz.begin(), sz.end());
     std::string s = "sms=" + std::to_string(sms) + ";";
     for (size_t i = 0; i < sz.size();) {
         size_t j = i;
         while (j < sz.size() && sz[j] == sz[i]) j++;
-        s += std::to_string(sz[i].first) + "x" + std::to_string(sz[i].second) + "*" + std::to_string(j - i) + ";";
+        s += std::to_string(sz[i].first) + "x" + std::to_string(sz[i].second / 2) + (sz[i].second & 1 ? "t" : "") +
+             "*" + std::to_string(j - i) + ";";
         i = j;
     }
     return s;
@@ -384,6 +394,7 @@ static sg_status make_list(const sg_batch_item* items, int n, const BatchTuning&
     if (sg_malloc((void**)&b.d_work, work) != cudaSuccess) return SG_ERR_ALLOC;
     std::vector<BatchDisk> D(n);
     std::vector<int> n_rows(n), n_cols(n), n_inv(n);
+    std::vector<TcArgs> tc1, tc3;  // short_dft disks: P1, P3 arguments
     for (int i = 0; i < n; i++) {
         const sg_plan* p = items[i].plan;
         BatchDisk& d = D[i];
@@ -420,6 +431,33 @@ static sg_status make_list(const sg_batch_item* items, int n, const BatchTuning&
         n_rows[i] = r2c_units / d.rows_mult;
         n_inv[i] = c2r_units / d.rows_mult;
         n_cols[i] = groups / d.cols_mult;
+        if (p->short_dft) {  // rows of 256 on the tensor cores, beside the persistent kernels
+            if (p->nphi != 256) {  // eligible short_dft plans have rows of exactly 256
+                free_list(b);
+                return SG_ERR_UNSUPPORTED;
+            }
+            n_rows[i] = n_inv[i] = 0;
+            TcArgs t{};
+            t.nu = p->nu;
+            t.N = p->nphi;
+            t.err = p->derr;
+            t.mat = (const float*)p->tcm;
+            t.w = (const float*)p->wpre;
+            t.x[0] = d.sigma;
+            t.out[0] = d.A;
+            tc1.push_back(t);
+            t = TcArgs{};
+            t.nu = p->nu;
+            t.N = p->nphi;
+            t.err = p->derr;
+            t.mat = (const float*)p->tcm + 2 * (size_t)p->nphi * p->nphi;
+            t.w = (const float*)p->wpost;
+            t.pin = (const float4*)d.P;
+            t.y[0] = d.Fr;
+            t.y[1] = d.Fp;
+            tc3.push_back(t);
+            b.tc_max_nu = std::max(b.tc_max_nu, p->nu);
+        }
     }
     // each pass's items, the disks' in order of decreasing work (largest
     // first, so that the small ones fill the last wave) unless natural
@@ -438,6 +476,19 @@ static sg_status make_list(const sg_batch_item* items, int n, const BatchTuning&
         b.nitems[k] = (int)(q.size() - start);
     }
     b.ndisks = n;
+    b.ntc = (int)tc1.size();
+    if (b.ntc) {
+        tc1.insert(tc1.end(), tc3.begin(), tc3.end());
+        if (sg_malloc((void**)&b.d_tc, sizeof(TcArgs) * tc1.size()) != cudaSuccess) {
+            free_list(b);
+            return SG_ERR_ALLOC;
+        }
+        if (cudaMemcpyAsync(b.d_tc, tc1.data(), sizeof(TcArgs) * tc1.size(), cudaMemcpyHostToDevice, st) !=
+            cudaSuccess) {
+            free_list(b);
+            return SG_ERR_CUDA;
+        }
+    }
     if ((s = (sg_malloc((void**)&b.d_disks, sizeof(BatchDisk) * n) == cudaSuccess &&
                       sg_malloc((void**)&b.d_items, sizeof(int2) * q.size()) == cudaSuccess &&
                       sg_malloc((void**)&b.d_ctrl, sizeof(int) * 4) == cudaSuccess)
@@ -456,15 +507,20 @@ static sg_status make_list(const sg_batch_item* items, int n, const BatchTuning&
     return SG_OK;
 }
 
-// the three queue heads zeroed, then one launch per pass kind
+// the three queue heads zeroed, then one launch per pass kind (a row kind
+// with no items is not launched); the short_dft disks' P1 before the column
+// kernel and their P3 after it, one batched launch each
 static sg_status launch_list(const BatchList& b, cudaStream_t st)
 {
     if (cudaMemsetAsync(b.d_ctrl, 0, sizeof(int) * 4, st) != cudaSuccess) return SG_ERR_CUDA;
+    if (b.ntc && launch_dft_tc_batch(b.d_tc, b.ntc, 0, b.tc_max_nu, st) != cudaSuccess) return SG_ERR_CUDA;
     const int2* items = b.d_items;
     for (int k = 0; k < 3; k++) {
-        b.kernel[k]<<<b.grid[k], SG_BATCH_THREADS, b.smem[k], st>>>(b.d_disks, items, b.nitems[k], b.d_ctrl + k);
+        if (b.nitems[k] > 0 || k == KIND_COLS)
+            b.kernel[k]<<<b.grid[k], SG_BATCH_THREADS, b.smem[k], st>>>(b.d_disks, items, b.nitems[k], b.d_ctrl + k);
         items += b.nitems[k];
     }
+    if (b.ntc && launch_dft_tc_batch(b.d_tc + b.ntc, b.ntc, 1, b.tc_max_nu, st) != cudaSuccess) return SG_ERR_CUDA;
     return cudaGetLastError() == cudaSuccess ? SG_OK : SG_ERR_CUDA;
 }
 

@@ -113,32 +113,17 @@ __device__ __forceinline__ void tc_stage4(float* hi, float* lo, int r, int k, fl
 
 }  // namespace
 
-// Arguments of the transform kernel (one struct: the four row passes take
-// different subsets).  Row fields are row-major, N values per row; spectra
-// are mode-major, element (m, i) at m nu + i, mode 0 holding (DC, Nyquist).
-struct TcArgs {
-    const float* x[2];    // DIR 0: the G input row fields
-    const float4* pin;    // DIR 1, PAIRS: {X, Y} pairs (16 bytes per element)
-    const float2* in[2];  // DIR 1 otherwise: the G single-layout spectra
-    const float* mat;     // [part (hi, lo)][column tile][K chunk][NT x KC core-matrix tile]
-    const float* w;       // the row weights (nu values), applied to the outputs
-    float4* pout;         // DIR 0, G = 2, PAIRS: the output pairs
-    float2* out[2];       // DIR 0 otherwise: the G single-layout output spectra
-    float* y[2];          // DIR 1: the G output row fields
-    int nu, N;
-    int* err;
-};
-
 // The transform kernel: G products of 128-row tiles with one matrix.
 //   DIR 0 (P1, P1b): rows -> half spectra.  Forward G = 1: sigma -> A.
 //     Adjoint G = 2: gF_r, gF_phi -> A, C (PAIRS: {A, C} pairs).
 //   DIR 1 (P3, P3b): half spectra -> rows.  Forward G = 2: B, C (PAIRS: the
 //     {B, C} pairs) -> F_r, F_phi.  Adjoint G = 1: B -> gsigma.
-// Outputs are scaled by the row weight w_i.  Grid: (ceil(nu / 128), N / NT);
-// block 256 threads: threads r and r + 128 stage the two halves of each chunk
-// of row blockIdx.x 128 + r, whose results sit in tensor-memory lane r.
+// Outputs are scaled by the row weight w_i.  One CTA per tile: rows
+// row_tile 128 .. + 127, output columns col_tile NT .. + NT - 1; 256 threads,
+// threads r and r + 128 staging the two halves of each chunk of row
+// row_tile 128 + r, whose results sit in tensor-memory lane r.
 template <int NT, int DIR, int G, bool PAIRS, int NB>
-__global__ void __launch_bounds__(TC_T, 1) k_dft_tc(const TcArgs a)
+__device__ __forceinline__ void dft_tc_tile(const TcArgs& a, int row_tile, int col_tile)
 {
     constexpr int RB = tc_rowbuf_bytes<G>();
     constexpr int MB = tc_mbytes<NT>();
@@ -154,9 +139,9 @@ __global__ void __launch_bounds__(TC_T, 1) k_dft_tc(const TcArgs a)
     __shared__ uint32_t tbase_s;
     unsigned char* const area = reinterpret_cast<unsigned char*>(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
     const int r = threadIdx.x & (TC_M - 1), h = threadIdx.x / TC_M, warp = threadIdx.x >> 5;
-    const int i = blockIdx.x * TC_M + r;
+    const int i = row_tile * TC_M + r;
     const bool row_ok = i < nu;
-    const int ct = blockIdx.y, nch = N / TC_KC;
+    const int ct = col_tile, nch = N / TC_KC;
     constexpr int QH = TC_KC / 8;  // float4s of one row's half chunk
     // the matrix's stored tiles are LNT = min(N, 64) columns wide; a CTA of
     // NT = 32 columns takes half of one, which is contiguous
@@ -366,6 +351,24 @@ __global__ void __launch_bounds__(TC_T, 1) k_dft_tc(const TcArgs a)
     if (warp == 0) sg_tc_dealloc(tbase, NCOLS);
 }
 
+// One plan: grid (ceil(nu / 128), N / NT).
+template <int NT, int DIR, int G, bool PAIRS, int NB>
+__global__ void __launch_bounds__(TC_T, 1) k_dft_tc(const TcArgs a)
+{
+    dft_tc_tile<NT, DIR, G, PAIRS, NB>(a, blockIdx.x, blockIdx.y);
+}
+
+// The disks of a batch: grid (row tiles of the largest disk, column tiles of
+// the longest rows, disks); a CTA beyond its disk's rows or columns leaves
+// before it takes any tensor memory.
+template <int NT, int DIR, int G, bool PAIRS, int NB>
+__global__ void __launch_bounds__(TC_T, 1) k_dft_tc_batch(const TcArgs* __restrict__ args)
+{
+    const TcArgs a = args[blockIdx.z];
+    if ((int)blockIdx.x * TC_M >= a.nu || (int)blockIdx.y * NT >= a.N) return;
+    dft_tc_tile<NT, DIR, G, PAIRS, NB>(a, blockIdx.x, blockIdx.y);
+}
+
 // ---- host side ----------------------------------------------------------------
 
 static int tc_nt(int N) { return N < 64 ? N : 64; }
@@ -453,6 +456,30 @@ static TcArgs tc_args(const PlanView& p, int dir, const float* w)
     a.N = p.nphi;
     a.err = p.err;
     return a;
+}
+
+// The batched form's row passes of its short_dft disks (rows of 256): one
+// launch for all of them; dir 0: P1 (args as launch_dft_r2c's), dir 1: P3
+// with the {B, C} pairs.  d_args: n argument sets in device memory.
+cudaError_t launch_dft_tc_batch(const TcArgs* d_args, int n, int dir, int max_nu, cudaStream_t st)
+{
+    constexpr int N = 256;
+    const dim3 grid((max_nu + TC_M - 1) / TC_M, N / 64, n);
+    cudaError_t e;
+    if (dir == 0) {
+        auto k = k_dft_tc_batch<64, 0, 1, false, 2>;
+        const size_t smem = tc_smem_bytes<64, 1, 2>(N);
+        if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+            return e;
+        k<<<grid, TC_T, smem, st>>>(d_args);
+    } else {
+        auto k = k_dft_tc_batch<64, 1, 2, true, 1>;
+        const size_t smem = tc_smem_bytes<64, 2, 1>(N);
+        if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+            return e;
+        k<<<grid, TC_T, smem, st>>>(d_args);
+    }
+    return cudaGetLastError();
 }
 
 // P1 on the tensor cores: sigma rows -> A (wa), weighted by wpre.

@@ -178,7 +178,22 @@ sg_status batch_prepare(const sg_batch_item* items, int n, cudaStream_t st);
 sg_status batch_tune(const sg_batch_item* items, int n, const char* path, cudaStream_t st, float ms_out[2]);
 void batch_forget_plan(const sg_plan* p);
 bool batch_eligible(const sg_plan* p);
-// dft_tc.cu: the row passes (forward and adjoint) as tensor-core DFT-matrix products
+// dft_tc.cu: the row passes (forward and adjoint) as tensor-core DFT-matrix products.
+// Arguments of its transform kernel (the four row passes take different
+// subsets).  Row fields are row-major, N values per row; spectra are
+// mode-major, element (m, i) at m nu + i, mode 0 holding (DC, Nyquist).
+struct TcArgs {
+    const float* x[2];    // rows -> spectra: the input row fields (one or two)
+    const float4* pin;    // spectra -> rows, pair layout: {X, Y} (16 bytes per element)
+    const float2* in[2];  // spectra -> rows otherwise: the single-layout spectra
+    const float* mat;     // the direction's matrix: [part (hi, lo)][column tile][K chunk][64 x 32 core-matrix tile]
+    const float* w;       // the row weights (nu values), applied to the outputs
+    float4* pout;         // rows -> spectra, two products, pair layout: the output pairs
+    float2* out[2];       // rows -> spectra otherwise: the single-layout output spectra
+    float* y[2];          // spectra -> rows: the output row fields
+    int nu, N;
+    int* err;
+};
 bool dft_tc_supported(int nphi);
 size_t dft_tc_matrix_floats(int nphi);
 void dft_tc_matrices(int nphi, float* out);  // host: D then E, each [hi, lo][tile][chunk][NT x 32]
@@ -186,6 +201,7 @@ cudaError_t launch_dft_r2c(const PlanView& p, const float* sigma, cudaStream_t s
 cudaError_t launch_dft_c2r(const PlanView& p, float* Fr, float* Fp, cudaStream_t st);
 cudaError_t launch_dft_r2c_adjoint(const PlanView& p, const float* gr, const float* gp, cudaStream_t st);
 cudaError_t launch_dft_c2r_adjoint(const PlanView& p, float* gs, cudaStream_t st);
+cudaError_t launch_dft_tc_batch(const TcArgs* d_args, int n, int dir, int max_nu, cudaStream_t st);
 // every device allocation of the library, through the sg_test_fail_alloc
 // hook, and its release (sg_test_live_allocations counts the difference)
 cudaError_t sg_malloc(void** ptr, size_t bytes);

@@ -192,3 +192,47 @@ def test_tuned_schedule_is_cached_and_bit_equal(torch_cuda, batch, tmp_path):
     for d, s, a, b in zip(disks[:n], sig[:n], Fr, Fp):
         er, ep = plans[(d.nu, d.nphi)].forces(s)
         assert torch.equal(a, er) and torch.equal(b, ep)
+
+
+def test_tensor_core_rows_keep_the_persistent_path(torch_cuda, batch):
+    """The batch with its N_phi = 256 disks on plans built with short_dft
+    (rows as tensor-core DFT products) still qualifies for the persistent
+    path: those disks' row passes run as two batched tensor-core launches
+    around the persistent column kernel.  Every disk equals its single call
+    bit for bit, eagerly and replayed from a CUDA graph; the tensor-core
+    disks also match the FFT plans within the FP32 bar."""
+    torch = torch_cuda
+    from paper_1509_01450_gb300 import Plan, batch_prepare, forces_batched
+
+    disks, plans, sig = batch
+    tcp = {}
+    for d in disks:
+        if d.nphi == 256 and (d.nu, d.nphi) not in tcp:
+            tcp[(d.nu, d.nphi)] = Plan(d.nu, d.nphi, d.u_min, d.du, 1.0, "float32").build(short_dft=1)
+    assert tcp, "the batch has disks with rows of 256"
+    use = [tcp.get((d.nu, d.nphi), plans[(d.nu, d.nphi)]) for d in disks]
+    Fr, Fp = _outputs(torch, sig)
+    items = [(p, s, a, b) for p, s, a, b in zip(use, sig, Fr, Fp)]
+    batch_prepare(items)  # raises unless the persistent path takes these items
+    forces_batched(items)
+    torch.cuda.synchronize()
+    for p in set(use):
+        p.check()
+    for k, (p, s) in enumerate(zip(use, sig)):
+        er, ep = p.forces(s)
+        assert torch.equal(Fr[k], er) and torch.equal(Fp[k], ep), k
+        if p in tcp.values():
+            d = disks[k]
+            gr, gp = plans[(d.nu, d.nphi)].forces(s)
+            num = float(((er.double() - gr.double()) ** 2).sum() + ((ep.double() - gp.double()) ** 2).sum())
+            den = float((gr.double() ** 2).sum() + (gp.double() ** 2).sum())
+            assert (num / den) ** 0.5 < 1e-5, k
+    Gr, Gp = _outputs(torch, sig)
+    gitems = [(p, s, a, b) for p, s, a, b in zip(use, sig, Gr, Gp)]
+    batch_prepare(gitems)  # the list is built outside the capture, which then records the persistent launches
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        forces_batched(gitems, stream=torch.cuda.current_stream())
+    g.replay()
+    torch.cuda.synchronize()
+    assert all(torch.equal(a, b) for a, b in zip(Gr + Gp, Fr + Fp))
