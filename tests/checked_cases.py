@@ -1,5 +1,6 @@
 """Cases for the checked-build test (tests/test_gpu_checked.py): every pass
-kernel family of the library, small and full size.  run_all() computes them
+kernel family of the library (the tensor-core row kernels included), small
+and full size.  run_all() computes them
 with whichever library sg.lib() loads; run as a script (with
 SG_LIBRARY_VARIANT=checked) it builds and loads the index-checked library,
 runs them, checks every plan's flags, and saves the results to the .npz
@@ -29,6 +30,9 @@ CASES = [
     ("fp64-wedge-128x256", 128, 256, "float64", {"radial_edges": 1, "wedge": 1}, "w"),
     ("noalloc-256x512", 256, 512, "float32", {}, "n"),
     ("host-256x512", 256, 512, "float32", {}, "h"),
+    ("tensor-core-rows-4096x256", 4096, 256, "float32", {"short_dft": 1}, "fb"),
+    ("tensor-core-rows-128x128", 128, 128, "float32", {"short_dft": 1}, "fb"),
+    ("tensor-core-rows-64x32", 64, 32, "float32", {"short_dft": 1}, "fb"),
 ]
 
 
@@ -75,6 +79,19 @@ def run_all():
         p.check()
         out[f"batch/{n}/0"] = fr.double().cpu().numpy()
         out[f"batch/{n}/1"] = fp.double().cpu().numpy()
+    # a persistent batch whose rows of 256 run on the tensor cores
+    items = []
+    for n, (nu, nphi, tc) in enumerate([(256, 256, 1), (256, 512, 0), (128, 256, 1)]):
+        u_min, du = workloads.grid_params(nu, 0.1, 10.0)
+        p = Plan(nu, nphi, u_min, du, 1.0, "float32").build(short_dft=tc)
+        s = torch.tensor(workloads.random_field(nu, nphi, 60 + n), dtype=torch.float32, device="cuda")
+        plans.append(p)
+        items.append((p, s, torch.empty_like(s), torch.empty_like(s)))
+    forces_batched(items)
+    for n, (p, s, fr, fp) in enumerate(items):
+        p.check()
+        out[f"batch-tc/{n}/0"] = fr.double().cpu().numpy()
+        out[f"batch-tc/{n}/1"] = fp.double().cpu().numpy()
     return out
 
 
