@@ -49,15 +49,19 @@ namespace sg {
 namespace {
 
 constexpr int TC_M = 128;   // rows per CTA (tensor-memory lanes)
-constexpr int TC_T = 256;   // threads per CTA: two per row, each staging half of a chunk
+constexpr int TC_STAGE = 256;  // staging threads: two per row, each staging half of a chunk
+constexpr int TC_T = TC_STAGE + 32;  // and one more warp, whose first lane issues the MMAs
 constexpr int TC_KC = 32;   // K values per staged chunk
 constexpr int TC_ABYTES = TC_M * TC_KC * 4;  // one A operand part of one chunk: 16 KB
-// Main accumulators per product.  The tensor core's FP32 accumulation loses
-// up to about one unit in the last place of the running sum per MMA step;
-// spreading the K chunks over several accumulators (and the correction terms,
-// 2^-11 of the main ones, into one of their own) divides the steps each one
-// takes, and the epilogue adds them with rounding to nearest.
-constexpr int TC_SLOTS = 3;
+// Accumulators.  The tensor core's FP32 accumulation loses up to about one
+// unit in the last place of the running sum per MMA step, and MMAs into the
+// same accumulator wait for one another.  So each product keeps TC_ACC(G)
+// main accumulators and as many for the two correction terms (2^-11 of the
+// main ones), the K step s of every chunk going to accumulator s mod
+// TC_ACC: consecutive MMAs then write different accumulators, each main
+// accumulator takes N / (8 TC_ACC) steps, and the epilogue adds them all with
+// rounding to nearest.  2 TC_ACC G NT = 512 columns for NT = 64.
+__host__ __device__ constexpr int tc_acc(int G) { return G == 1 ? 4 : 2; }
 constexpr int TC_MAX_CHUNKS = 8;  // N <= 256
 
 __host__ __device__ constexpr uint32_t tc_pow2(int n)
@@ -76,6 +80,7 @@ __host__ __device__ constexpr int tc_mbytes()
 }
 
 // bytes of one row staging buffer: G row operands, hi and lo parts each
+// (NB of them in a ring)
 template <int G>
 __host__ __device__ constexpr int tc_rowbuf_bytes()
 {
@@ -119,22 +124,25 @@ __device__ __forceinline__ void tc_stage4(float* hi, float* lo, int r, int k, fl
 //   DIR 1 (P3, P3b): half spectra -> rows.  Forward G = 2: B, C (PAIRS: the
 //     {B, C} pairs) -> F_r, F_phi.  Adjoint G = 1: B -> gsigma.
 // Outputs are scaled by the row weight w_i.  One CTA per tile: rows
-// row_tile 128 .. + 127, output columns col_tile NT .. + NT - 1; 256 threads,
+// row_tile 128 .. + 127, output columns col_tile NT .. + NT - 1; 288 threads,
 // threads r and r + 128 staging the two halves of each chunk of row
-// row_tile 128 + r, whose results sit in tensor-memory lane r.
+// row_tile 128 + r, whose results sit in tensor-memory lane r, and thread 256
+// issuing the MMAs.
 template <int NT, int DIR, int G, bool PAIRS, int NB>
 __device__ __forceinline__ void dft_tc_tile(const TcArgs& a, int row_tile, int col_tile)
 {
     constexpr int RB = tc_rowbuf_bytes<G>();
     constexpr int MB = tc_mbytes<NT>();
-    // accumulators: TC_SLOTS for the hi hi terms (chunk c into slot c mod S),
-    // one more for the two correction terms, each G x NT columns
-    constexpr uint32_t NCOLS = tc_pow2((TC_SLOTS + 1) * G * NT);
+    // accumulators: column (j G + g) NT for the main sum j of product g,
+    // (ACC + j) G + g for its correction sum j (j < ACC)
+    constexpr int ACC = tc_acc(G);
+    constexpr uint32_t NCOLS = tc_pow2(2 * ACC * G * NT);
     const int nu = a.nu, N = a.N;
     int* const err = a.err;
     const unsigned long long wlim = sg_wait_budget(err);
     extern __shared__ __align__(1024) unsigned char smraw[];
-    __shared__ __align__(8) uint64_t bar[NB];              // per row buffer: its chunk's MMAs have completed
+    __shared__ __align__(8) uint64_t empty[NB];            // per row buffer: its chunk's MMAs have completed
+    __shared__ __align__(8) uint64_t full[NB];             // per row buffer: its chunk is staged
     __shared__ __align__(8) uint64_t lbar[TC_MAX_CHUNKS];  // per chunk: its matrix parts have landed
     __shared__ uint32_t tbase_s;
     unsigned char* const area = reinterpret_cast<unsigned char*>(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
@@ -153,7 +161,10 @@ __device__ __forceinline__ void dft_tc_tile(const TcArgs& a, int row_tile, int c
         sg_tc_relinquish();
     }
     if (threadIdx.x == 0) {
-        for (int b = 0; b < NB; b++) sg_mbar_init(&bar[b], 1);
+        for (int b = 0; b < NB; b++) {
+            sg_mbar_init(&empty[b], 1);
+            sg_mbar_init(&full[b], TC_STAGE);
+        }
         for (int c = 0; c < nch; c++) sg_mbar_init(&lbar[c], 1);
     }
     sg_tc_fence_before();
@@ -161,7 +172,6 @@ __device__ __forceinline__ void dft_tc_tile(const TcArgs& a, int row_tile, int c
     sg_tc_fence_after();
     const uint32_t tbase = tbase_s;
     const uint32_t idesc = sg_tc_idesc_tf32(TC_M, NT);
-    const int S = nch < TC_SLOTS ? nch : TC_SLOTS;  // main accumulators in use
     const float wi = row_ok ? __ldg(&a.w[i]) : 0.f;
     // the whole column tile of the matrix, one pair of bulk copies per chunk,
     // each chunk on its own barrier so that the first MMAs need only the first
@@ -214,87 +224,99 @@ __device__ __forceinline__ void dft_tc_tile(const TcArgs& a, int row_tile, int c
             }
         }
     };
-    bool ok = true;
-    int issued = 0;   // chunks whose MMAs have been committed
-    int landed = -1;  // the last chunk whose matrix copy was waited for
-    // One chunk: rows c (in cur) staged into row buffer c mod NB while the
-    // rows of chunk c + 2 load into nxt (those of c + 1 are in flight already;
-    // with two buffers the MMAs of chunk c - 1 run meanwhile); then the MMAs
-    // of chunk c.  False if a wait gave up.
-    auto chunk = [&](int c, float4 (&cur)[G * QH], float4 (&nxt)[G * QH]) -> bool {
-        float* const ahi = reinterpret_cast<float*>(rows_area + (size_t)(c % NB) * RB);  // [g][hi, lo]
-        if (c + 2 < nch) load_rows(c + 2, nxt);
-        if (c >= NB) {  // row buffer c mod NB was read by the MMAs of chunk c - NB
-            const bool in_time = sg_mbar_wait_bounded(&bar[c % NB], ((c / NB) - 1) & 1, err, 1, wlim);
-            if (__syncthreads_or(!in_time)) return false;
-        }
-#pragma unroll
-        for (int g = 0; g < G; g++) {
-            float* hi = ahi + (size_t)g * 2 * (TC_ABYTES / 4);
-            float* lo = hi + TC_ABYTES / 4;
-#pragma unroll
-            for (int q = 0; q < QH; q++) tc_stage4(hi, lo, r, h * (TC_KC / 2) + 4 * q, cur[g * QH + q]);
-        }
-        sg_fence_proxy_async_smem();  // the stores above, for the tensor core's reads
-        {
-            const bool in_time = sg_mbar_wait_bounded(&lbar[c], 0, err, 1, wlim);
-            landed = c;
-            if (__syncthreads_or(!in_time)) return false;
-        }
-        if (threadIdx.x == 0) {
-            sg_tc_fence_after();
-            // descriptors of the chunk's first K step; a step of 8 values
-            // (256 bytes) adds 16 to the start-address field
-            const uint64_t bh0 = sg_tc_smem_desc(sg_smem_u32(area + (size_t)c * 2 * MB), 128, 1024);
-            const uint64_t bl0 = bh0 + (MB >> 4);
-            const uint64_t ah0 = sg_tc_smem_desc(sg_smem_u32(ahi), 128, 1024);
-            const uint32_t slot = (uint32_t)(c % S);
-            // each accumulator's MMAs back to back: the main slot's K steps,
-            // then the corrections'
+    // Warp-specialised pipeline: warps 0-7 stage chunk c into row buffer
+    // c mod NB (after the MMAs of chunk c - NB freed it: "empty") and arrive
+    // on "full"; the last warp's first lane waits for a full buffer and the
+    // chunk's matrix, issues its MMAs and commits them to "empty".  No
+    // block-wide barrier per chunk; every wait is bounded, and a wait that
+    // gave up stops its side, which the other side then sees as a wait that
+    // gives up in turn.
+    bool fail = false;
+    if (threadIdx.x < TC_STAGE) {
+        auto stage = [&](int c, float4 (&cur)[G * QH], float4 (&nxt)[G * QH]) -> bool {
+            float* const ahi = reinterpret_cast<float*>(rows_area + (size_t)(c % NB) * RB);  // [g][hi, lo]
+            if (c + 2 < nch) load_rows(c + 2, nxt);  // chunk c + 1's rows are in flight already
+            if (c >= NB && !sg_mbar_wait_bounded(&empty[c % NB], ((c / NB) - 1) & 1, err, 1, wlim)) return false;
 #pragma unroll
             for (int g = 0; g < G; g++) {
-                const uint64_t ah = ah0 + (uint64_t)((g * 2 * TC_ABYTES) >> 4);
-                const uint64_t al = ah + (TC_ABYTES >> 4);
-                const uint32_t dm = tbase + (slot * G + g) * NT;                  // this chunk's main slot
-                const uint32_t dc = tbase + (uint32_t)((TC_SLOTS * G + g) * NT);  // the corrections
+                float* hi = ahi + (size_t)g * 2 * (TC_ABYTES / 4);
+                float* lo = hi + TC_ABYTES / 4;
 #pragma unroll
-                for (int s = 0; s < TC_KC / 8; s++)  // K = 8 values (two core matrices) per MMA
-                    sg_tc_mma_tf32(dm, ah + 16 * s, bh0 + 16 * s, idesc, (c >= S || s > 0) ? 1u : 0u);
-#pragma unroll
-                for (int s = 0; s < TC_KC / 8; s++) {
-                    sg_tc_mma_tf32(dc, ah + 16 * s, bl0 + 16 * s, idesc, (c > 0 || s > 0) ? 1u : 0u);
-                    sg_tc_mma_tf32(dc, al + 16 * s, bh0 + 16 * s, idesc, 1u);
-                }
+                for (int q = 0; q < QH; q++) tc_stage4(hi, lo, r, h * (TC_KC / 2) + 4 * q, cur[g * QH + q]);
             }
-            sg_tc_commit(&bar[c % NB]);
-        }
-        issued = c + 1;
-        return true;
-    };
-    {
+            sg_fence_proxy_async_smem();  // the stores above, for the tensor core's reads
+            sg_mbar_arrive(&full[c % NB]);
+            return true;
+        };
         // three register sets in turn: the rows arrive two chunks after
         // their loads are issued, and no prefetched value is moved
         float4 va[G * QH], vb[G * QH], vc[G * QH];
         load_rows(0, va);
         if (nch > 1) load_rows(1, vb);
-        for (int c = 0; c < nch && ok; c += 3) {
-            ok = chunk(c, va, vc);
-            if (ok && c + 1 < nch) ok = chunk(c + 1, vb, va);
-            if (ok && c + 2 < nch) ok = chunk(c + 2, vc, vb);
+        for (int c = 0; c < nch && !fail; c += 3) {
+            fail = !stage(c, va, vc);
+            if (!fail && c + 1 < nch) fail = !stage(c + 1, vb, va);
+            if (!fail && c + 2 < nch) fail = !stage(c + 2, vc, vb);
+        }
+        // the last chunk's completion covers every MMA issued before it
+        const int c = nch - 1;
+        if (!fail) fail = !sg_mbar_wait_bounded(&empty[c % NB], (c / NB) & 1, err, 1, wlim);
+    } else if (threadIdx.x == TC_STAGE) {
+        int issued = 0;   // chunks whose MMAs have been committed
+        int landed = -1;  // the last chunk whose matrix copy was waited for
+        for (int c = 0; c < nch; c++) {
+            if (!sg_mbar_wait_bounded(&full[c % NB], (c / NB) & 1, err, 1, wlim)) {
+                fail = true;
+                break;
+            }
+            const bool in_time = sg_mbar_wait_bounded(&lbar[c], 0, err, 1, wlim);
+            landed = c;
+            if (!in_time) {
+                fail = true;
+                break;
+            }
+            sg_tc_fence_after();
+            float* const ahi = reinterpret_cast<float*>(rows_area + (size_t)(c % NB) * RB);
+            // descriptors of the chunk's first K step; a step of 8 values
+            // (256 bytes) adds 16 to the start-address field
+            const uint64_t bh0 = sg_tc_smem_desc(sg_smem_u32(area + (size_t)c * 2 * MB), 128, 1024);
+            const uint64_t bl0 = bh0 + (MB >> 4);
+            const uint64_t ah0 = sg_tc_smem_desc(sg_smem_u32(ahi), 128, 1024);
+            // three rounds over the chunk's K steps (K = 8 values, two core
+            // matrices, per MMA) and products: the main terms, then each
+            // correction term; K step s writes accumulator s mod ACC, so an
+            // MMA's predecessor on the same accumulator is ACC G or more issues back
+#pragma unroll
+            for (int round = 0; round < 3; round++)
+#pragma unroll
+                for (int s = 0; s < TC_KC / 8; s++)
+#pragma unroll
+                    for (int g = 0; g < G; g++) {
+                        const uint64_t ah = ah0 + (uint64_t)((g * 2 * TC_ABYTES) >> 4) + 16 * s;
+                        const int j = s % ACC;
+                        const uint32_t first = (c == 0 && s < ACC) ? 0u : 1u;  // 0: the accumulator's first write
+                        if (round == 0)
+                            sg_tc_mma_tf32(tbase + (uint32_t)((j * G + g) * NT), ah, bh0 + 16 * s, idesc, first);
+                        else if (round == 1)
+                            sg_tc_mma_tf32(tbase + (uint32_t)(((ACC + j) * G + g) * NT), ah, bl0 + 16 * s, idesc, first);
+                        else
+                            sg_tc_mma_tf32(tbase + (uint32_t)(((ACC + j) * G + g) * NT), ah + (TC_ABYTES >> 4),
+                                           bh0 + 16 * s, idesc, 1u);
+                    }
+            sg_tc_commit(&empty[c % NB]);
+            issued = c + 1;
+        }
+        // matrix copies still in flight after a wait that gave up land, and
+        // the MMAs issued complete, before the shared and tensor memory are
+        // given back
+        for (int c = landed + 1; c < nch; c++) sg_mbar_wait_bounded(&lbar[c], 0, err, 1, wlim);
+        if (fail && issued > 0) {
+            const int c = issued - 1;
+            sg_mbar_wait_bounded(&empty[c % NB], (c / NB) & 1, err, 1, wlim);
         }
     }
-    // matrix copies still in flight after a wait that gave up land before
-    // the shared memory is given back
-    for (int c = landed + 1; c < nch; c++) sg_mbar_wait_bounded(&lbar[c], 0, err, 1, wlim);
-    // the last committed chunk's completion covers every MMA issued before it;
-    // after a wait that gave up this is the one more bounded wait for the
-    // MMAs still in flight, before the tensor memory is freed
-    if (issued > 0) {
-        const int c = issued - 1;
-        const bool in_time = sg_mbar_wait_bounded(&bar[c % NB], (c / NB) & 1, err, 1, wlim);
-        if (__syncthreads_or(!in_time)) ok = false;
-    }
-    if (ok) {
+    bool ok = !__syncthreads_or(fail);
+    if (ok && threadIdx.x < TC_STAGE) {
         sg_tc_fence_after();
         // warps w and w + 4 read the same 32 lanes (rows): the two halves of
         // the CTA take alternate blocks of 32 columns
@@ -302,15 +324,16 @@ __device__ __forceinline__ void dft_tc_tile(const TcArgs& a, int row_tile, int c
 #pragma unroll
         for (int cb = h; cb < NT / 32; cb += 2) {
             // each product's sum of accumulators, in FP32 with rounding to
-            // nearest: the corrections first, then the main slots
+            // nearest: the correction sums first, then the main ones
             float y[G][32];
 #pragma unroll
             for (int g = 0; g < G; g++) {
                 float t[32];
-                sg_tc_ld32(lane_base + (uint32_t)((TC_SLOTS * G + g) * NT + cb * 32), y[g]);
+                sg_tc_ld32(lane_base + (uint32_t)((ACC * G + g) * NT + cb * 32), y[g]);
                 sg_tc_wait_ld();
-                for (int k = 0; k < S; k++) {
-                    sg_tc_ld32(lane_base + (uint32_t)((k * G + g) * NT + cb * 32), t);
+                for (int k = 1; k < 2 * ACC; k++) {
+                    const int j = k < ACC ? ACC + k : k - ACC;  // corrections 1 .. ACC-1, then main 0 .. ACC-1
+                    sg_tc_ld32(lane_base + (uint32_t)((j * G + g) * NT + cb * 32), t);
                     sg_tc_wait_ld();
 #pragma unroll
                     for (int q = 0; q < 32; q++) y[g][q] = __fadd_rn(y[g][q], t[q]);
@@ -437,14 +460,16 @@ static cudaError_t tc_launch(const TcArgs& a, cudaStream_t st)
     return cudaGetLastError();
 }
 
-// columns per CTA: 64 (32 for rows of 32); two row buffers, but one for two
-// products of rows of 256, whose 128 KB matrix tile leaves room for one only
+// columns per CTA: 64 (32 for rows of 32); row buffers: three for one
+// product, two for two, and one for two products of rows of 256, whose
+// 128 KB matrix tile leaves room for one only
 template <int DIR, int G, bool PAIRS>
 static cudaError_t tc_launch_nt(const TcArgs& a, cudaStream_t st)
 {
-    if (a.N < 64) return tc_launch<32, DIR, G, PAIRS, 2>(a, st);
+    constexpr int NB = G == 1 ? 3 : 2;
+    if (a.N < 64) return tc_launch<32, DIR, G, PAIRS, NB>(a, st);
     if (G == 2 && a.N > 128) return tc_launch<64, DIR, G, PAIRS, 1>(a, st);
-    return tc_launch<64, DIR, G, PAIRS, 2>(a, st);
+    return tc_launch<64, DIR, G, PAIRS, NB>(a, st);
 }
 
 static TcArgs tc_args(const PlanView& p, int dir, const float* w)
@@ -467,8 +492,8 @@ cudaError_t launch_dft_tc_batch(const TcArgs* d_args, int n, int dir, int max_nu
     const dim3 grid((max_nu + TC_M - 1) / TC_M, N / 64, n);
     cudaError_t e;
     if (dir == 0) {
-        auto k = k_dft_tc_batch<64, 0, 1, false, 2>;
-        const size_t smem = tc_smem_bytes<64, 1, 2>(N);
+        auto k = k_dft_tc_batch<64, 0, 1, false, 3>;
+        const size_t smem = tc_smem_bytes<64, 1, 3>(N);
         if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
             return e;
         k<<<grid, TC_T, smem, st>>>(d_args);
