@@ -426,12 +426,6 @@ __device__ __forceinline__ void sg_mbar_expect_tx(uint64_t* bar, uint32_t bytes)
                  : "memory");
 }
 
-// one arrival (no transaction bytes) on the barrier's current phase
-__device__ __forceinline__ void sg_mbar_arrive(uint64_t* bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sg_smem_u32(bar)) : "memory");
-}
-
 __device__ __forceinline__ bool sg_mbar_try_wait(uint64_t* bar, uint32_t phase)
 {
     uint32_t ok;

@@ -62,6 +62,12 @@ __device__ __forceinline__ void sg_tc_dealloc(uint32_t taddr, uint32_t ncols)
 // Order tensor-core operations across a thread barrier.
 __device__ __forceinline__ void sg_tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void sg_tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// One arrival (no transaction bytes) on an mbarrier's current phase.
+__device__ __forceinline__ void sg_mbar_arrive(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"((uint32_t)__cvta_generic_to_shared(bar))
+                 : "memory");
+}
 // Make this thread's ordinary shared-memory stores visible to the tensor
 // core's (asynchronous proxy) reads.
 __device__ __forceinline__ void sg_fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
