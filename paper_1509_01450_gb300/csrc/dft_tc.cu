@@ -173,21 +173,21 @@ __device__ __forceinline__ void dft_tc_tile(const TcArgs& a, int row_tile, int c
     const uint32_t tbase = tbase_s;
     const uint32_t idesc = sg_tc_idesc_tf32(TC_M, NT);
     const float wi = row_ok ? __ldg(&a.w[i]) : 0.f;
-    // the whole column tile of the matrix, one pair of bulk copies per chunk,
-    // each chunk on its own barrier so that the first MMAs need only the first
-    if (threadIdx.x == 0) {
-        const uint64_t keep = sg_policy_evict_last();  // every CTA of the column tile reads it
+    // the CTA's column tile of the matrix stays resident: chunk c's two parts
+    // (hi, lo) arrive by two bulk copies on lbar[c].  The MMA thread copies
+    // two chunks ahead of its MMAs, so that the first chunks' copies do not
+    // queue behind the whole tile's
+    const uint64_t keep = sg_policy_evict_last();  // every CTA of the column tile reads it
+    auto copy_matrix = [&](int c) {
         const size_t tile0 = (size_t)(ct * NT / LNT), sub = (size_t)(ct * NT % LNT) * TC_KC;
-        for (int c = 0; c < nch; c++) {
-            float* const dh = reinterpret_cast<float*>(area + (size_t)c * 2 * MB);
-            const float* const gh = a.mat + (tile0 * nch + c) * ((size_t)LNT * TC_KC) + sub;
-            SG_IF_OK(tile0 * nch + c < (size_t)(N / LNT) * nch, err, 403) {
-                sg_mbar_expect_tx(&lbar[c], 2 * MB);
-                sg_bulk_g2s_hint(dh, gh, MB, &lbar[c], keep);
-                sg_bulk_g2s_hint(dh + MB / 4, gh + mat_part, MB, &lbar[c], keep);
-            }
+        float* const dh = reinterpret_cast<float*>(area + (size_t)c * 2 * MB);
+        const float* const gh = a.mat + (tile0 * nch + c) * ((size_t)LNT * TC_KC) + sub;
+        SG_IF_OK(tile0 * nch + c < (size_t)(N / LNT) * nch, err, 403) {
+            sg_mbar_expect_tx(&lbar[c], 2 * MB);
+            sg_bulk_g2s_hint(dh, gh, MB, &lbar[c], keep);
+            sg_bulk_g2s_hint(dh + MB / 4, gh + mat_part, MB, &lbar[c], keep);
         }
-    }
+    };
     // this thread's half of chunk c of row i: v[g QH + q] = values
     // KC h / 2 + 4 q .. + 3 of product g
     auto load_rows = [&](int c, float4 (&v)[G * QH]) {
@@ -264,6 +264,8 @@ __device__ __forceinline__ void dft_tc_tile(const TcArgs& a, int row_tile, int c
     } else if (threadIdx.x == TC_STAGE) {
         int issued = 0;   // chunks whose MMAs have been committed
         int landed = -1;  // the last chunk whose matrix copy was waited for
+        int copied = nch < 2 ? nch - 1 : 1;  // the last chunk whose matrix copy was issued
+        for (int c = 0; c <= copied; c++) copy_matrix(c);
         for (int c = 0; c < nch; c++) {
             if (!sg_mbar_wait_bounded(&full[c % NB], (c / NB) & 1, err, 1, wlim)) {
                 fail = true;
@@ -305,11 +307,12 @@ __device__ __forceinline__ void dft_tc_tile(const TcArgs& a, int row_tile, int c
                     }
             sg_tc_commit(&empty[c % NB]);
             issued = c + 1;
+            if (c + 2 < nch) copy_matrix(copied = c + 2);
         }
         // matrix copies still in flight after a wait that gave up land, and
         // the MMAs issued complete, before the shared and tensor memory are
         // given back
-        for (int c = landed + 1; c < nch; c++) sg_mbar_wait_bounded(&lbar[c], 0, err, 1, wlim);
+        for (int c = landed + 1; c <= copied; c++) sg_mbar_wait_bounded(&lbar[c], 0, err, 1, wlim);
         if (fail && issued > 0) {
             const int c = issued - 1;
             sg_mbar_wait_bounded(&empty[c % NB], (c / NB) & 1, err, 1, wlim);
