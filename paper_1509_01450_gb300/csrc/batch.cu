@@ -478,7 +478,8 @@ static sg_status make_list(const sg_batch_item* items, int n, const BatchTuning&
     b.ndisks = n;
     b.ntc = (int)tc1.size();
     if (b.ntc) {
-        tc1.insert(tc1.end(), tc3.begin(), tc3.end());
+        tc1.reserve(2 * tc3.size());
+        for (const TcArgs& t : tc3) tc1.push_back(t);
         if (sg_malloc((void**)&b.d_tc, sizeof(TcArgs) * tc1.size()) != cudaSuccess) {
             free_list(b);
             return SG_ERR_ALLOC;
