@@ -34,10 +34,12 @@
 // Shared-memory operands are K-major without swizzling: core matrices of 8
 // rows x 4 values (128 contiguous bytes), the KC = 32 values of one K chunk
 // as 8 core matrices side by side (128 bytes apart), the 8-row groups 1024
-// bytes apart.  Each chunk is double-buffered: the threads stage chunk c + 1
-// while the tensor core multiplies chunk c, and a buffer is refilled only
-// after the MMAs that read it have signalled their completion on its
-// mbarrier (a bounded wait).
+// bytes apart.  A CTA keeps its column tile of the matrix resident (bulk
+// copies two chunks ahead of the MMAs) and streams the rows through a ring
+// of row buffers: eight warps stage chunk after chunk and arrive on the
+// buffer's "full" mbarrier, one thread of a ninth warp issues the chunk's
+// MMAs and commits them to its "empty" mbarrier, and a buffer is refilled
+// only after that commit (every wait bounded).
 #include "sg_internal.cuh"
 #include "sg_tc.cuh"
 
